@@ -1,0 +1,119 @@
+"""Exact solve of the discrete pressure Poisson equation (test infrastructure; see package header).
+
+§2.3 solves the (modified) PPE on the regular grid in three steps: forward one-dimensional
+transforms along each axis in turn, division by the eigenvalues (the sum of the 1D
+eigenvalues), backward transforms. With the central finite-difference eigenvalues this is an
+exact inverse of the 2d+1-point Laplacian L_h. The oracle states that inverse in its plain
+form: it expands the source in the eigenvectors of the 1D three-point operator with the
+ghost rules of oracle.grid (one dense basis per axis), divides by the summed eigenvalues and
+sums the expansion back. No fast transform is used; numpy.linalg.solve finds the expansion
+coefficients from the dense basis.
+
+1D eigenbases on a cell-centred axis (j, k = 0..n-1; Neumann = 'W' or 'I'):
+  periodic      1, cos(2 pi k j/n), sin(2 pi k j/n), (-1)^j     lambda = -(4/h^2) sin^2(pi k/n)
+  Neumann-Neumann   cos(pi k (j+1/2)/n)                          lambda = -(4/h^2) sin^2(pi k/(2n))
+  Dirichlet-Dirichlet sin(pi (k+1)(j+1/2)/n)                     lambda = -(4/h^2) sin^2(pi (k+1)/(2n))
+  Neumann-Dirichlet cos(pi (k+1/2)(j+1/2)/n)                     lambda = -(4/h^2) sin^2(pi (2k+1)/(4n))
+  Dirichlet-Neumann sin(pi (k+1/2)(j+1/2)/n)                     same lambda
+The last two pairs put different homogeneous conditions at the two ends of one axis, which
+§2.3 does not list (it asks for the same type on both ends); they are still diagonalised
+exactly by these bases and are used for an inflow/outflow channel.
+
+Zero mode: when every axis is periodic or Neumann-Neumann the summed eigenvalue of the
+constant mode is 0. Its source coefficient is the mean of s, which is dropped (the
+compatibility projection) and the solution gets no constant part (mean(p) = 0). An optional
+corner gauge p[0,...,0] = 0 matches the reference pressure of §3.1.
+
+Parity: pinned by tests/test_oracle_poisson.py - eigenvector relations against an
+independently assembled matrix, a brute-force dense LU solve on 8x8, 16x16 and 4x4x4 grids,
+and manufactured solutions converging at second order.
+"""
+import numpy as np
+
+from .grid import NEUMANN
+
+
+def axis_kind(g, a):
+    lo, hi = g.bc_lo[a], g.bc_hi[a]
+    if lo == "P":
+        return "PP"
+    lo = "N" if lo in NEUMANN else "D"
+    hi = "N" if hi in NEUMANN else "D"
+    return lo + hi
+
+
+def eigenbasis(kind, n, h):
+    """(Phi, lam): Phi[:, k] is the k-th eigenvector of the 1D operator, lam[k] its eigenvalue."""
+    j = np.arange(n, dtype=np.float64)[:, None]
+    if kind == "PP":
+        cols, wav = [np.ones(n)], [0]
+        for k in range(1, (n - 1) // 2 + 1):
+            cols.append(np.cos(2.0 * np.pi * k * j[:, 0] / n))
+            cols.append(np.sin(2.0 * np.pi * k * j[:, 0] / n))
+            wav += [k, k]
+        if n % 2 == 0:
+            cols.append(np.cos(np.pi * j[:, 0]))
+            wav.append(n // 2)
+        Phi = np.stack(cols, axis=1)
+        lam = -(4.0 / (h * h)) * np.sin(np.pi * np.asarray(wav, dtype=np.float64) / n) ** 2
+        return Phi, lam
+    k = np.arange(n, dtype=np.float64)[None, :]
+    if kind == "NN":
+        Phi = np.cos(np.pi * k * (j + 0.5) / n)
+        lam = -(4.0 / (h * h)) * np.sin(np.pi * k[0] / (2.0 * n)) ** 2
+    elif kind == "DD":
+        Phi = np.sin(np.pi * (k + 1.0) * (j + 0.5) / n)
+        lam = -(4.0 / (h * h)) * np.sin(np.pi * (k[0] + 1.0) / (2.0 * n)) ** 2
+    elif kind == "ND":
+        Phi = np.cos(np.pi * (k + 0.5) * (j + 0.5) / n)
+        lam = -(4.0 / (h * h)) * np.sin(np.pi * (2.0 * k[0] + 1.0) / (4.0 * n)) ** 2
+    elif kind == "DN":
+        Phi = np.sin(np.pi * (k + 0.5) * (j + 0.5) / n)
+        lam = -(4.0 / (h * h)) * np.sin(np.pi * (2.0 * k[0] + 1.0) / (4.0 * n)) ** 2
+    else:
+        raise ValueError(kind)
+    return Phi, lam
+
+
+def _apply(M, x, a):
+    """Multiply the matrix M onto axis a of x."""
+    y = np.tensordot(M, x, axes=([1], [a]))
+    return np.moveaxis(y, 0, a)
+
+
+def _solve_along(M, x, a):
+    """Solve M y = x along axis a of x (dense LU per axis, all lines at once)."""
+    xa = np.moveaxis(x, a, 0)
+    shp = xa.shape
+    y = np.linalg.solve(M, xa.reshape(shp[0], -1)).reshape(shp)
+    return np.moveaxis(y, 0, a)
+
+
+def solve(s, g, gauge="mean"):
+    """Return (p, removed_mean) with L_h p = s (s minus its mean when the problem is singular).
+
+    removed_mean is the mean of s dropped by the compatibility projection (0 otherwise)."""
+    s = np.asarray(s, dtype=np.float64).reshape(g.shape)
+    bases = [eigenbasis(axis_kind(g, a), g.n[a], g.h[a]) for a in range(g.dim)]
+    coef = s
+    for a in range(g.dim):                      # step 1: forward expansion, axis by axis
+        coef = _solve_along(bases[a][0], coef, a)
+    lam = np.zeros(g.shape)                     # step 2: divide by the summed eigenvalues
+    for a in range(g.dim):
+        shape = [1] * g.dim
+        shape[a] = g.n[a]
+        lam = lam + bases[a][1].reshape(shape)
+    removed = 0.0
+    zero = tuple([0] * g.dim)
+    if g.singular():
+        removed = float(np.mean(s))
+        lam[zero] = 1.0
+        coef = coef.copy()
+        coef[zero] = 0.0
+    phat = coef / lam
+    p = phat
+    for a in range(g.dim):                      # step 3: backward expansion
+        p = _apply(bases[a][0], p, a)
+    if g.singular() and gauge == "corner":
+        p = p - p[zero]
+    return p, removed

@@ -1,0 +1,138 @@
+"""The pressure-correction sub-step of the hybrid method, end to end (test infrastructure).
+
+Steps, in the paper's order (§2.3, one pass of the IB-force iteration with a given force):
+
+1. Plan (§2.2 last paragraph: coefficients depend only on positions and are computed once):
+   - transfer rows: for every face centre of the staggered grid that carries a flux, the
+     value row (row 0 of C^-1 A, Eq. 13 with the f-unknown basis of Eq. 16) over its K
+     nearest nodes (velocity, boundary and virtual points alike, §2.3 Fig. 1);
+   - gradient rows: for every node, the first-derivative rows of C^-1 A over its K nearest
+     pressure points (cell centres; periodic images on periodic axes).
+2. Transfer of u~ = u* + dt f~ to the faces. The modified PPE (Eq. 20) has the right-hand side
+   (2/(3 dt)) div u* + (2/3) div f~ = (1/(beta dt)) div(u* + dt f~) with beta = 3/2.
+   Wall faces carry no flux (§3.3 workaround); inflow and Dirichlet faces keep the
+   transferred flux (Eq. 7: u^{n+1}.n = u*.n at an inflow).
+3. Source s = D_h U / (beta dt); discrete solve L_h p = s (oracle.poisson).
+4. Gradient of p at the nodes with the gradient rows, then (Eqs. 18-19)
+     fluid node:             u^{n+1} = u* - beta dt grad p,          f~ = 0
+     boundary/virtual node:  f~ = -u*/dt + beta grad p,              u^{n+1} = 0
+   (Eq. 18 with Eq. 19 substituted gives exactly 0 at those nodes.)
+5. Check quantity: corrected face flux U - beta dt G_h p and its divergence D_h, which is
+   round-off (or the removed mean of s, when the compatibility projection acted).
+
+Node types: 0 fluid (velocity point), 1 boundary point, 2 virtual point (§2.3).
+
+Parity: the grid-level invariants (round-off divergence, idempotence), linearity, Taylor-Green
+recovery and the IB relations are pinned in tests/test_oracle_projection.py.
+"""
+from dataclasses import dataclass
+import numpy as np
+
+from . import grid as G
+from . import knn as KNN
+from . import wls as W
+from . import poisson as P
+
+FLUID, BOUNDARY, VIRTUAL = 0, 1, 2
+
+
+@dataclass
+class Plan:
+    grid: G.Grid
+    nodes: np.ndarray           # (d, N)
+    node_type: np.ndarray       # (N,)
+    K: int
+    eps: float
+    support_factor: float
+    face_col: list              # per axis: (num_faces, K) int64 node indices
+    face_w: list                # per axis: (num_faces, K) value-row weights (0 on wall faces)
+    node_col: np.ndarray        # (N, K) cell linear indices
+    node_D: np.ndarray          # (d, N, K) derivative-row weights
+
+
+def _box(g):
+    lengths = [g.length(a) for a in range(g.dim)]
+    periodic = [g.periodic(a) for a in range(g.dim)]
+    return list(g.lo[: g.dim]), lengths, periodic
+
+
+def _wls_block(points, queries, idx, g, eps, support_factor):
+    _, lengths, periodic = _box(g)
+    nb = points[idx]                                              # (Q, K, d)
+    delta = nb - queries[:, None, :]
+    for a in range(g.dim):
+        if periodic[a]:
+            L = lengths[a]
+            da = delta[..., a]
+            delta[..., a] = np.where(da > 0.5 * L, da - L, np.where(da < -0.5 * L, da + L, da))
+    d2 = KNN.squared_distance(delta)
+    return W.rows(delta, d2, eps, support_factor)
+
+
+def build_plan(g, nodes, node_type, K=12, eps=6.3, support_factor=3.0, chunk=200000):
+    nodes = np.asarray(nodes, dtype=np.float64)
+    pts = nodes.T.copy()                                          # (N, d)
+    lo, lengths, periodic = _box(g)
+    face_col, face_w = [], []
+    for a in range(g.dim):
+        fp = g.face_points(a)
+        idx, _ = KNN.knn(pts, fp, K, lo, lengths, periodic)
+        w = np.empty(idx.shape)
+        for s0 in range(0, fp.shape[0], chunk):
+            s1 = min(s0 + chunk, fp.shape[0])
+            val, _ = _wls_block(pts, fp[s0:s1], idx[s0:s1], g, eps, support_factor)
+            w[s0:s1] = val
+        wall = g.face_is_wall(a).ravel()
+        w[wall] = 0.0
+        face_col.append(idx)
+        face_w.append(w)
+    cp = g.cell_points()
+    idx, _ = KNN.knn(cp, pts, K, lo, lengths, periodic)
+    D = np.empty((g.dim,) + idx.shape)
+    for s0 in range(0, pts.shape[0], chunk):
+        s1 = min(s0 + chunk, pts.shape[0])
+        _, grad = _wls_block(cp, pts[s0:s1], idx[s0:s1], g, eps, support_factor)
+        D[:, s0:s1, :] = np.transpose(grad, (1, 0, 2))
+    return Plan(g, nodes, np.asarray(node_type, dtype=np.uint8), K, eps, support_factor,
+                face_col, face_w, idx, D)
+
+
+def transfer(plan, u_tilde):
+    """Face fluxes U_a = sum_k w_k u~_{a,k} (value rows), wall faces 0."""
+    g = plan.grid
+    out = []
+    for a in range(g.dim):
+        U = np.sum(plan.face_w[a] * u_tilde[a][plan.face_col[a]], axis=1)
+        out.append(U.reshape(g.face_shape(a)))
+    return out
+
+
+def node_gradient(plan, p):
+    pf = np.asarray(p, dtype=np.float64).ravel()
+    vals = pf[plan.node_col]                                       # (N, K)
+    return np.sum(plan.node_D * vals[None, :, :], axis=2)          # (d, N)
+
+
+def project(plan, dt, u_star, f_ib=None, beta=1.5, gauge="mean"):
+    """One pressure-correction pass. Returns a dict with p, u, f, U (faces), s, div_after, removed."""
+    g = plan.grid
+    u_star = np.asarray(u_star, dtype=np.float64).reshape(g.dim, -1)
+    if f_ib is None:
+        u_tilde = u_star
+    else:
+        u_tilde = u_star + dt * np.asarray(f_ib, dtype=np.float64).reshape(g.dim, -1)
+    U = transfer(plan, u_tilde)
+    s = G.divergence(U, g) / (beta * dt)
+    p, removed = P.solve(s, g, gauge=gauge)
+    grad = node_gradient(plan, p)
+    ib = plan.node_type != FLUID
+    u_new = u_star - beta * dt * grad
+    u_new[:, ib] = 0.0
+    f_new = np.zeros_like(u_star)
+    f_new[:, ib] = -u_star[:, ib] / dt + beta * grad[:, ib]
+    U_new = [U[a] - beta * dt * G.face_gradient(p, g, a) for a in range(g.dim)]
+    for a in range(g.dim):
+        U_new[a][g.face_is_wall(a)] = 0.0
+    div_after = G.divergence(U_new, g)
+    return dict(p=p, u=u_new, f=f_new, U=U, s=s, grad=grad, U_new=U_new,
+                div_after=div_after, removed=removed)

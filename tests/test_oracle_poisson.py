@@ -1,0 +1,191 @@
+"""Pins of the oracle's Poisson solve against the mathematics (no GPU).
+
+* every 1D eigenbasis satisfies the three-point relation of a matrix assembled here, entry by
+  entry, from the ghost-cell rules (independent of oracle.grid);
+* the solve inverts a brute-force dense Laplacian (LU) on 8x8, 16x16 and 4x4x4 grids for every
+  boundary pairing, with a bordered system for the singular (all periodic/Neumann) cases;
+* manufactured smooth solutions converge at second order (error ratio ~4 per halving of h);
+* an eigenfunction source is solved to round-off in 2D and 3D, including 3*2^m sizes.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import grid as G
+from oracle import poisson as P
+
+KINDS = {"PP": ("P", "P"), "NN": ("W", "W"), "DD": ("D", "D"), "ND": ("I", "D"), "DN": ("D", "W")}
+
+
+def dense_1d(kind, n, h):
+    """Three-point second difference with the ghost rule of each end written out."""
+    M = np.zeros((n, n))
+    for j in range(n):
+        M[j, j] -= 2.0
+        if j > 0:
+            M[j, j - 1] += 1.0
+        if j < n - 1:
+            M[j, j + 1] += 1.0
+    if kind == "PP":
+        M[0, n - 1] += 1.0
+        M[n - 1, 0] += 1.0
+    else:
+        lo, hi = kind[0], kind[1]
+        M[0, 0] += 1.0 if lo == "N" else -1.0        # ghost p_-1 = +-p_0
+        M[n - 1, n - 1] += 1.0 if hi == "N" else -1.0
+    return M / (h * h)
+
+
+def dense_nd(kinds, n, h):
+    """Kronecker sum of the 1D matrices (C order: last axis fastest)."""
+    dim = len(n)
+    total = None
+    for a in range(dim):
+        mats = [np.eye(n[b]) for b in range(dim)]
+        mats[a] = dense_1d(kinds[a], n[a], h[a])
+        m = mats[0]
+        for b in range(1, dim):
+            m = np.kron(m, mats[b])
+        total = m if total is None else total + m
+    return total
+
+
+def make_grid(kinds, n, h):
+    dim = len(n)
+    return G.Grid(dim, tuple(n), tuple([0.0] * dim), tuple(h),
+                  tuple(KINDS[k][0] for k in kinds), tuple(KINDS[k][1] for k in kinds))
+
+
+@pytest.mark.parametrize("kind", list(KINDS))
+@pytest.mark.parametrize("n", [8, 9, 12, 16, 24, 96])
+def test_eigenbasis_matches_stencil(kind, n):
+    h = 0.37
+    M = dense_1d(kind, n, h)
+    Phi, lam = P.eigenbasis(kind, n, h)
+    assert Phi.shape == (n, n)
+    assert np.linalg.matrix_rank(Phi) == n
+    err = np.abs(M @ Phi - Phi * lam[None, :]).max()
+    assert err <= 1e-12 * 4.0 / (h * h)
+
+
+def test_eigenvalue_closed_forms():
+    """Spot values of the 1D eigenvalues from their closed forms (h = 1)."""
+    n = 8
+    _, lam = P.eigenbasis("NN", n, 1.0)
+    assert lam[0] == 0.0
+    assert abs(lam[4] - (-2.0)) < 1e-15                      # -4 sin^2(pi/4)
+    _, lam = P.eigenbasis("DD", n, 1.0)
+    assert abs(lam[n - 1] - (-4.0)) < 1e-15                  # -4 sin^2(pi/2)
+    _, lam = P.eigenbasis("PP", n, 1.0)
+    assert abs(sorted(lam)[0] - (-4.0)) < 1e-15              # Nyquist mode
+    _, lam = P.eigenbasis("ND", 1, 1.0)
+    assert abs(lam[0] - (-2.0)) < 1e-15                      # n=1: ghosts +p0, -p0
+
+
+def _bruteforce(kinds, n, h, s):
+    A = dense_nd(kinds, n, h)
+    N = A.shape[0]
+    singular = all(k in ("PP", "NN") for k in kinds)
+    if singular:
+        B = np.zeros((N + 1, N + 1))
+        B[:N, :N] = A
+        B[:N, N] = 1.0
+        B[N, :N] = 1.0
+        rhs = np.concatenate([s.ravel(), [0.0]])
+        x = np.linalg.solve(B, rhs)
+        return x[:N].reshape(n), x[N]
+    return np.linalg.solve(A, s.ravel()).reshape(n), 0.0
+
+
+@pytest.mark.parametrize("n", [(8, 8), (16, 16), (8, 12), (4, 4, 4)])
+def test_bruteforce_dense(n, rng):
+    dim = len(n)
+    for kinds in itertools.product(list(KINDS), repeat=dim):
+        if dim == 3 and len(set(kinds)) == 3 and rng.uniform() < 0.7:
+            continue  # keep the 3D sweep short
+        h = tuple(rng.uniform(0.5, 2.0) for _ in range(dim))
+        g = make_grid(kinds, n, h)
+        s = rng.normal(size=n)
+        p_ref, mu = _bruteforce(kinds, n, h, s)
+        p, removed = P.solve(s, g)
+        scale = np.abs(p_ref).max()
+        assert np.abs(p - p_ref).max() <= 1e-13 * scale * max(n), kinds
+        assert abs(removed - mu) <= 1e-12 * max(1.0, abs(mu))
+
+
+def _manufactured(kind, x, L):
+    """(p, -k^2) with p satisfying the boundary pair of kind on [0, L]."""
+    if kind == "PP":
+        k = 2 * math.pi / L
+        return np.sin(k * x), -k * k
+    if kind == "NN":
+        k = math.pi / L
+        return np.cos(k * x), -k * k
+    if kind == "DD":
+        k = math.pi / L
+        return np.sin(k * x), -k * k
+    if kind == "ND":
+        k = math.pi / (2 * L)
+        return np.cos(k * x), -k * k
+    if kind == "DN":
+        k = math.pi / (2 * L)
+        return np.sin(k * x), -k * k
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kinds", [("PP", "PP"), ("NN", "NN"), ("DD", "DD"), ("ND", "NN"),
+                                   ("DN", "PP"), ("PP", "DD"), ("ND", "DN")])
+def test_manufactured_second_order(kinds):
+    L = (2.0, 1.5)
+    errs = []
+    for m in (16, 32, 64, 128):
+        n = (m, m)
+        h = (L[0] / m, L[1] / m)
+        g = make_grid(kinds, n, h)
+        xs = [(np.arange(m) + 0.5) * h[a] for a in range(2)]
+        px, kx = _manufactured(kinds[0], xs[0], L[0])
+        py, ky = _manufactured(kinds[1], xs[1], L[1])
+        pex = np.outer(px, py)
+        s = (kx + ky) * pex
+        p, _ = P.solve(s, g)
+        if g.singular():
+            p = p - p.mean()
+            pex = pex - pex.mean()
+        errs.append(np.abs(p - pex).max())
+    ratios = [errs[i] / errs[i + 1] for i in range(len(errs) - 1)]
+    assert all(3.6 < r < 4.4 for r in ratios), (errs, ratios)
+
+
+@pytest.mark.parametrize("n", [(8, 8), (12, 16), (96, 64), (6, 8, 10), (12, 8, 6)])
+def test_eigenfunction_source(n, rng):
+    dim = len(n)
+    for kinds in itertools.product(list(KINDS), repeat=dim):
+        if dim == 3 and rng.uniform() < 0.8:
+            continue
+        h = tuple(rng.uniform(0.5, 2.0) for _ in range(dim))
+        g = make_grid(kinds, n, h)
+        ks = [int(rng.integers(0, n[a])) for a in range(dim)]
+        bases = [P.eigenbasis(kinds[a], n[a], h[a]) for a in range(dim)]
+        s = bases[0][0][:, ks[0]]
+        lam = bases[0][1][ks[0]]
+        for a in range(1, dim):
+            s = np.multiply.outer(s, bases[a][0][:, ks[a]])
+            lam = lam + bases[a][1][ks[a]]
+        p, removed = P.solve(s, g)
+        if lam == 0.0:
+            assert np.abs(p).max() <= 1e-13
+            assert abs(removed - s.mean()) <= 1e-14
+        else:
+            # dense LU of an n x n basis: round-off grows like n * eps
+            assert np.abs(p - s / lam).max() <= 1e-14 * max(n) * np.abs(s / lam).max()
+
+
+def test_corner_gauge():
+    g = make_grid(("NN", "PP"), (8, 8), (1.0, 1.0))
+    s = np.random.default_rng(1).normal(size=(8, 8))
+    p, _ = P.solve(s, g, gauge="corner")
+    assert p[0, 0] == 0.0
+    pm, _ = P.solve(s, g)
+    assert np.abs((p - p.mean()) - pm).max() < 1e-13

@@ -1,0 +1,159 @@
+"""Pins of the oracle's whole sub-step (no GPU).
+
+* D_h G_h = L_h: the corrected face flux has round-off divergence (or exactly the removed
+  mean, when the compatibility projection acted);
+* grid-level idempotence: projecting the corrected face flux again gives p = 0;
+* linearity of the whole map in (u*, f~);
+* Taylor-Green recovery: u* = TG + beta dt grad p_TG gives back p_TG and TG at second order;
+* gradient rows over cell centres are exact for a quadratic pressure;
+* IB relations of Eqs. 18-19: zero velocity and the force formula at boundary/virtual nodes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import grid as G
+from oracle import projection as PR
+from oracle import poisson as P
+from paper_2304_14690_gb300 import workloads as wl
+
+
+def grid_of(p):
+    return G.Grid(p.dim, p.n, p.lo, p.h, p.bc_lo, p.bc_hi)
+
+
+CASES = [
+    dict(dim=2, n=(24, 20), bc_lo=("P", "P"), bc_hi=("P", "P")),
+    dict(dim=2, n=(24, 20), bc_lo=("W", "W"), bc_hi=("W", "W"), obstacles=[("circle", (0.7, 0.6), 0.2)]),
+    dict(dim=2, n=(32, 16), bc_lo=("I", "W"), bc_hi=("D", "W"), obstacles=[("circle", (0.8, 0.5), 0.15)]),
+    dict(dim=2, n=(16, 24), bc_lo=("P", "D"), bc_hi=("P", "D")),
+    dict(dim=2, n=(20, 20), bc_lo=("I", "P"), bc_hi=("I", "P")),
+    dict(dim=3, n=(10, 8, 8), bc_lo=("P", "W", "W"), bc_hi=("P", "W", "W")),
+    dict(dim=3, n=(8, 8, 10), bc_lo=("W", "W", "I"), bc_hi=("W", "W", "D"),
+         obstacles=[("sphere", (0.25, 0.25, 0.3), 0.12)]),
+]
+
+
+@pytest.fixture(scope="module")
+def problems():
+    out = []
+    for i, c in enumerate(CASES):
+        p = wl.generic(seed=100 + i, with_force=True, **c)
+        out.append((p, PR.build_plan(grid_of(p), p.nodes, p.node_type, K=p.knn)))
+    return out
+
+
+def test_roundoff_divergence(problems):
+    for p, plan in problems:
+        r = PR.project(plan, p.dt, p.u_star, p.f_ib)
+        g = plan.grid
+        scale = np.abs(G.divergence(r["U"], g)).max()
+        expect = p.beta * p.dt * r["removed"]          # uniform when the mean of s was dropped
+        assert np.abs(r["div_after"] - expect).max() <= 1e-12 * scale, (p.bc_lo, p.bc_hi)
+        if not any(b == "I" for b in p.bc_lo + p.bc_hi):
+            # periodic and wall faces telescope: the source already has zero mean
+            assert abs(r["removed"]) <= 1e-12 * np.abs(r["s"]).max()
+
+
+def test_idempotent_on_grid(problems):
+    for p, plan in problems:
+        r = PR.project(plan, p.dt, p.u_star, p.f_ib)
+        g = plan.grid
+        s2 = G.divergence(r["U_new"], g) / (p.beta * p.dt)
+        p2, _ = P.solve(s2, g)
+        assert np.abs(p2).max() <= 1e-11 * np.abs(r["p"]).max()
+
+
+def test_linearity(problems, rng):
+    for p, plan in problems:
+        u1 = rng.normal(size=p.u_star.shape)
+        u2 = rng.normal(size=p.u_star.shape)
+        f1 = rng.normal(size=p.u_star.shape)
+        a, b = 0.7, -1.3
+        r1 = PR.project(plan, p.dt, u1, f1)
+        r2 = PR.project(plan, p.dt, u2, None)
+        r = PR.project(plan, p.dt, a * u1 + b * u2, a * f1)
+        for key in ("p", "u", "f"):
+            ref = a * r1[key] + b * r2[key]
+            assert np.abs(r[key] - ref).max() <= 1e-12 * np.abs(ref).max(), key
+
+
+def test_taylor_green_recovery():
+    """u* = TG + beta dt grad p_TG, p_TG = -(cos 2x + cos 2y)/4: recovers p_TG and TG."""
+    errs_p, errs_u = [], []
+    for n in (32, 64, 128):
+        prob = wl.periodic_taylor_green(n=n, seed=7)
+        x, y = prob.nodes
+        tg = np.stack([np.sin(x) * np.cos(y), -np.cos(x) * np.sin(y)])
+        gp = np.stack([0.5 * np.sin(2 * x), 0.5 * np.sin(2 * y)])
+        u_star = tg + prob.beta * prob.dt * gp
+        g = grid_of(prob)
+        plan = PR.build_plan(g, prob.nodes, prob.node_type, K=12)
+        r = PR.project(plan, prob.dt, u_star)
+        cx, cy = np.meshgrid(g.cell_centres(0), g.cell_centres(1), indexing="ij")
+        p_tg = -(np.cos(2 * cx) + np.cos(2 * cy)) / 4
+        errs_p.append(np.abs((r["p"] - r["p"].mean()) - (p_tg - p_tg.mean())).max())
+        errs_u.append(np.abs(r["u"] - tg).max())
+    assert errs_p[-1] < 2e-3 and errs_u[-1] < 2e-3, (errs_p, errs_u)
+    # WLS interpolation is second order here: each halving of h cuts the error by > 3
+    assert all(errs_p[i] / errs_p[i + 1] > 3.0 for i in range(2)), errs_p
+    assert all(errs_u[i] / errs_u[i + 1] > 3.0 for i in range(2)), errs_u
+
+
+def test_perturbed_taylor_green_converges():
+    """Config-1 style input (TG + gradient perturbation): the projection removes the perturbation."""
+    errs = []
+    for n in (32, 64, 128):
+        prob = wl.periodic_taylor_green(n=n, seed=11)
+        x, y = prob.nodes
+        tg = np.stack([np.sin(x) * np.cos(y), -np.cos(x) * np.sin(y)])
+        plan = PR.build_plan(grid_of(prob), prob.nodes, prob.node_type, K=12)
+        r = PR.project(plan, prob.dt, prob.u_star)
+        errs.append(np.abs(r["u"] - tg).max())
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 0.02, errs
+
+
+def test_gradient_rows_exact_for_quadratic():
+    prob = wl.generic(dim=2, n=(20, 16), bc_lo=("W", "D"), bc_hi=("I", "W"), seed=3)
+    g = grid_of(prob)
+    plan = PR.build_plan(g, prob.nodes, prob.node_type, K=12)
+    cx, cy = np.meshgrid(g.cell_centres(0), g.cell_centres(1), indexing="ij")
+    p = 0.3 + 1.1 * cx - 0.4 * cy + 0.8 * cx * cx - 0.5 * cx * cy + 0.25 * cy * cy
+    gr = PR.node_gradient(plan, p)
+    x, y = prob.nodes
+    ex = np.stack([1.1 + 1.6 * x - 0.5 * y, -0.4 - 0.5 * x + 0.5 * y])
+    assert np.abs(gr - ex).max() < 1e-11
+
+
+def test_transfer_exact_for_quadratic_velocity():
+    prob = wl.generic(dim=3, n=(8, 8, 8), bc_lo=("P", "W", "W"), bc_hi=("P", "W", "W"), seed=5)
+    g = grid_of(prob)
+    plan = PR.build_plan(g, prob.nodes, prob.node_type, K=27)
+    x, y, z = prob.nodes
+    u = np.stack([0.5 + y * y - 0.3 * z, 1.0 + x * z * 0.0 + y * z, 2.0 - z * z])
+    U = PR.transfer(plan, u)
+    # away from the periodic seam (x is periodic, the field is not) the quadratic is reproduced
+    fp = g.face_points(1)
+    val = 1.0 + fp[:, 1] * fp[:, 2]
+    wall = g.face_is_wall(1).ravel()
+    inner = (~wall) & (fp[:, 0] > 0.15) & (fp[:, 0] < g.length(0) - 0.15)
+    assert np.abs(U[1].ravel()[inner] - val[inner]).max() < 1e-11
+    assert np.all(U[1].ravel()[wall] == 0.0)
+
+
+def test_ib_relations(problems):
+    for p, plan in problems:
+        if not np.any(p.node_type != 0):
+            continue
+        r = PR.project(plan, p.dt, p.u_star, p.f_ib)
+        ib = p.node_type != 0
+        assert np.all(r["u"][:, ib] == 0.0)
+        assert np.all(r["f"][:, ~ib] == 0.0)
+        # Eq. 18 with the updated force gives zero velocity at IB nodes
+        resid = p.u_star[:, ib] - p.beta * p.dt * r["grad"][:, ib] + p.dt * r["f"][:, ib]
+        assert np.abs(resid).max() <= 1e-12 * np.abs(p.u_star).max() + 1e-12
+        # fluid nodes: Eq. 4
+        fl = ~ib
+        corr = p.u_star[:, fl] - p.beta * p.dt * r["grad"][:, fl]
+        assert np.abs(r["u"][:, fl] - corr).max() == 0.0
