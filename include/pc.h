@@ -1,0 +1,173 @@
+/*
+ * pc.h - C ABI of the GB300 pressure-correction library (libpc.so).
+ *
+ * The library performs the pressure-correction sub-step of Fang's hybrid projection method
+ * (arXiv 2304.14690, §2.3): weighted-least-squares (WLS) transfer of the provisional velocity
+ * u* from an irregular node cloud to the faces of a uniform staggered pressure grid, the
+ * divergence source of the modified pressure Poisson equation (Eq. 20) with the immersed-
+ * boundary force, a transform-based Poisson solve (§2.3: forward 1D transforms per axis,
+ * division by summed eigenvalues, inverse transforms), and the WLS pressure gradient back at
+ * the nodes with the velocity correction and IB-force update (Eqs. 18-19).
+ *
+ * Conventions shared by every entry point
+ *  - Grid: dim (2 or 3) axes, n[a] cells of spacing h[a] from lo[a]; cell centre
+ *    lo + (i + 1/2) h. Cell arrays are C order (last axis contiguous), one value per cell.
+ *  - Nodes: structure of arrays, [dim][num_nodes] (component a of node k at a*num_nodes + k).
+ *  - Pointers: every array argument of pc_project / pc_solve_poisson may be a device pointer
+ *    or a host pointer (pinned host memory is fastest); the library detects which. Host
+ *    arrays are copied through plan-owned device buffers on the given stream. The caller
+ *    owns all arrays; the library never keeps a pointer past the call that received it.
+ *  - Streams: cuda_stream is a cudaStream_t (NULL = legacy default stream). A plan may be
+ *    used by one stream at a time. pc_project and pc_solve_poisson allocate nothing and do
+ *    not synchronize, unless host pointers or a stats struct are passed (both need a sync).
+ *  - Errors: every entry point returns a pc_status; nothing aborts or traps. The message of
+ *    the last failure on the calling thread is pc_last_error_message().
+ */
+#ifndef PC_H
+#define PC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PC_OK = 0,
+  PC_ERR_INVALID_ARG = 1,   /* malformed descriptor or argument */
+  PC_ERR_UNSUPPORTED = 2,   /* valid but not supported (e.g. an odd cell count on a transform axis) */
+  PC_ERR_WLS_SINGULAR = 3,  /* a WLS normal matrix C (Eq. 14) is not positive definite */
+  PC_ERR_OUT_OF_MEMORY = 4, /* a device allocation failed */
+  PC_ERR_BUDGET = 5,        /* the plan would exceed the caller's device-memory budget */
+  PC_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+  PC_ERR_NOT_CONVERGED = 7, /* refinement did not reach the requested residual */
+  PC_ERR_TIMEOUT = 8        /* a bounded device-side wait gave up */
+} pc_status;
+
+/* Boundary kind of one domain face (§2.1 Eqs. 7-8, §2.3, §3.3). */
+typedef enum {
+  PC_BC_PERIODIC = 0,        /* must pair with PERIODIC on the same axis */
+  PC_BC_NEUMANN_WALL = 1,    /* homogeneous Neumann; the face flux is zero (§3.3 workaround) */
+  PC_BC_NEUMANN_INFLOW = 2,  /* homogeneous Neumann (Eq. 7); the face keeps its transferred flux */
+  PC_BC_DIRICHLET = 3        /* homogeneous Dirichlet p = 0 on the face; transferred flux */
+} pc_bc;
+
+typedef enum {
+  PC_PREC_FP64 = 0,   /* every step in FP64 */
+  PC_PREC_MIXED = 1,  /* compensated FP32 gathers, FP32 transforms, FP64 residual refinement */
+  PC_PREC_FP32 = 2    /* as MIXED with no refinement (reports the unrefined FP32 error) */
+} pc_precision;
+
+typedef enum { PC_DTYPE_F64 = 0, PC_DTYPE_F32 = 1 } pc_dtype;
+
+/* Node kinds of the double discretization (§2.3, Fig. 1). */
+typedef enum { PC_NODE_FLUID = 0, PC_NODE_BOUNDARY = 1, PC_NODE_VIRTUAL = 2 } pc_node_type;
+
+/* Obstacle metadata (circle in 2D, sphere in 3D). Used for validation and reports only:
+ * the caller classifies nodes itself (node_type). */
+typedef struct {
+  int shape; /* 0 = circle/sphere */
+  double centre[3];
+  double radius;
+} pc_obstacle;
+
+typedef struct {
+  int dim;                  /* 2 or 3 */
+  int64_t n[3];             /* cells per axis; n[a] even on every axis (transform length) */
+  double lo[3];             /* lower corner */
+  double h[3];              /* spacing; the domain length is n[a]*h[a] */
+  int bc_lo[3], bc_hi[3];   /* pc_bc per axis end */
+  int64_t num_nodes;        /* N */
+  const double *node_xyz;   /* [dim][N] node coordinates (device or host); nodes on a periodic
+                               axis must lie in [lo, lo + n h), on other axes inside the box */
+  const uint8_t *node_type; /* [N] pc_node_type (device or host) */
+  int num_obstacles;
+  const pc_obstacle *obstacles; /* host, may be NULL */
+  int knn;                  /* neighbours per WLS stencil K (>= 6 in 2D, >= 10 in 3D; <= 32) */
+  double wls_eps;           /* Gaussian weight constant eps of Eq. 17 (paper: 6.3) */
+  double support_factor;    /* support radius / local spacing (paper: 3, §2.2) */
+  double beta;              /* AB2 pressure factor 3/2 of Eq. 4 */
+  int precision;            /* pc_precision */
+  int refine_iters;         /* MIXED: number of FP64-residual refinement sweeps (fixed, >= 0) */
+  int gauge;                /* 0: mean(p) = 0; 1: p at the corner cell = 0 (§3.1). Applies only
+                               when no face is Dirichlet (the solution is then defined up to
+                               a constant) */
+  int velocity_dtype;       /* pc_dtype of u_star, f_ib_in, u_out, f_ib_out */
+} pc_problem_desc;
+
+/* Per-call diagnostics (optional). Filling it synchronizes the stream. */
+typedef struct {
+  double removed_mean;      /* mean of the source dropped by the compatibility projection */
+  double source_norm;       /* ||s||_2 over cells */
+  double residual_norm[9];  /* ||s - mean - L_h p||_2 after the first solve and each sweep */
+  int refine_iters_done;
+  double max_div_after;     /* max |D_h (U - beta dt G_h p)| over cells (faces corrected) */
+  double max_abs_u_star;    /* velocity scale */
+  double gauge_shift;       /* constant subtracted from p by the gauge */
+} pc_stats;
+
+typedef struct pc_plan pc_plan;
+
+/* Build a plan: neighbour search (§2.2 linked-list search), the WLS rows C^-1 A (§2.2
+ * Eqs. 13-17, f-unknown basis of Eq. 16) for every flux-carrying face (value row) and every
+ * node (derivative rows over the K nearest cell centres), eigenvalue and twiddle tables, and
+ * the whole workspace of pc_project. The coefficients depend only on positions and are
+ * computed once (§2.2, last paragraph). Runs on `device` on `cuda_stream` and returns when
+ * done. hbm_budget_bytes = 0 means no budget. */
+pc_status pc_plan_create(const pc_problem_desc *desc, int device, size_t hbm_budget_bytes,
+                         void *cuda_stream, pc_plan **out_plan);
+
+/* One pressure-correction pass (one iteration of the IB-force loop of §2.3 with a given
+ * force):
+ *   u~ = u* + dt f~_in          (right-hand side of Eq. 20 is (1/(beta dt)) div u~)
+ *   U  = WLS value rows (u~)    on faces; wall faces 0
+ *   s  = D_h U / (beta dt);     L_h p = s (mean of s dropped when singular)
+ *   g  = WLS derivative rows (p) at nodes
+ *   fluid node:            u_out = u* - beta dt g,  f~_out = 0                   (Eq. 4)
+ *   boundary/virtual node: f~_out = -(u*)/dt + beta g, u_out = 0               (Eqs. 18-19)
+ * u_star, f_ib_in (nullable = zero), u_out, f_ib_out (nullable): [dim][N] of velocity_dtype.
+ * p_out: cells, FP64. Returns without waiting for the GPU unless host pointers or stats. */
+pc_status pc_project(pc_plan *plan, double dt, const void *u_star, const void *f_ib_in,
+                     double *p_out, void *u_out, void *f_ib_out, pc_stats *stats,
+                     void *cuda_stream);
+
+typedef struct {
+  double dt;
+  const void *u_star;
+  const void *f_ib_in;
+  double *p_out;
+  void *u_out;
+  void *f_ib_out;
+} pc_project_args;
+
+/* count independent projections (each plan with its own arguments) on one stream; the
+ * results equal those of count separate pc_project calls. Device pointers only. */
+pc_status pc_project_batch(int count, pc_plan *const *plans, const pc_project_args *args,
+                           void *cuda_stream);
+
+/* The grid-level Poisson solve alone (§2.3 three-step algorithm): L_h p = s, cells in FP64,
+ * with the plan's precision, refinement and gauge. */
+pc_status pc_solve_poisson(pc_plan *plan, const double *s, double *p_out, pc_stats *stats,
+                           void *cuda_stream);
+
+/* WLS rows of a plan, for inspection and tests. which = 0..dim-1: value rows of the faces
+ * normal to that axis (rows = faces in C order of that face array); which = dim: derivative
+ * rows of the nodes (rows = nodes, weights [dim][rows][K]). col_out: [rows][K] int32 (node
+ * index for faces, cell linear index for nodes), w_out: FP64 host buffers. rows_out gets the
+ * row count; pass NULL buffers to query it. */
+pc_status pc_plan_rows(const pc_plan *plan, int which, int64_t *rows_out, int32_t *col_out,
+                       double *w_out);
+
+/* Device bytes held by the plan. */
+pc_status pc_plan_bytes(const pc_plan *plan, size_t *bytes_out);
+
+pc_status pc_destroy(pc_plan *plan);
+
+const char *pc_status_string(pc_status status);
+const char *pc_last_error_message(void); /* thread-local; "" when none */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PC_H */

@@ -6,8 +6,13 @@ Steps, in the paper's order (§2.3, one pass of the IB-force iteration with a gi
    - transfer rows: for every face centre of the staggered grid that carries a flux, the
      value row (row 0 of C^-1 A, Eq. 13 with the f-unknown basis of Eq. 16) over its K
      nearest nodes (velocity, boundary and virtual points alike, §2.3 Fig. 1);
-   - gradient rows: for every node, the first-derivative rows of C^-1 A over its K nearest
-     pressure points (cell centres; periodic images on periodic axes).
+   - gradient rows: for every node, the first-derivative rows of C^-1 A over the 3^d block of
+     pressure points (cell centres) around it: along each axis the cell holding the node and
+     its two neighbours, the block shifted inward at a non-periodic wall and wrapped on a
+     periodic axis. §2.3 takes this gradient "from the pressure points" by WLS without fixing
+     the stencil; a K-nearest choice can put every point into two layers next to a 3D wall,
+     where the quadratic basis is rank deficient, while a 3-per-axis block always determines
+     a quadratic exactly.
 2. Transfer of u~ = u* + dt f~ to the faces. The modified PPE (Eq. 20) has the right-hand side
    (2/(3 dt)) div u* + (2/3) div f~ = (1/(beta dt)) div(u* + dt f~) with beta = 3/2.
    Wall faces carry no flux (§3.3 workaround); inflow and Dirichlet faces keep the
@@ -46,8 +51,8 @@ class Plan:
     support_factor: float
     face_col: list              # per axis: (num_faces, K) int64 node indices
     face_w: list                # per axis: (num_faces, K) value-row weights (0 on wall faces)
-    node_col: np.ndarray        # (N, K) cell linear indices
-    node_D: np.ndarray          # (d, N, K) derivative-row weights
+    node_col: np.ndarray        # (N, 3^d) cell linear indices of the gradient block
+    node_D: np.ndarray          # (d, N, 3^d) derivative-row weights
 
 
 def _box(g):
@@ -87,7 +92,7 @@ def build_plan(g, nodes, node_type, K=12, eps=6.3, support_factor=3.0, chunk=200
         face_col.append(idx)
         face_w.append(w)
     cp = g.cell_points()
-    idx, _ = KNN.knn(cp, pts, K, lo, lengths, periodic)
+    idx = gradient_block(g, pts)
     D = np.empty((g.dim,) + idx.shape)
     for s0 in range(0, pts.shape[0], chunk):
         s1 = min(s0 + chunk, pts.shape[0])
@@ -95,6 +100,27 @@ def build_plan(g, nodes, node_type, K=12, eps=6.3, support_factor=3.0, chunk=200
         D[:, s0:s1, :] = np.transpose(grad, (1, 0, 2))
     return Plan(g, nodes, np.asarray(node_type, dtype=np.uint8), K, eps, support_factor,
                 face_col, face_w, idx, D)
+
+
+def gradient_block(g, pts):
+    """Cell linear indices (N, 3^d) of the block of 3 cells per axis around each node, listed in
+    C order of the block offsets."""
+    N = pts.shape[0]
+    per_axis = []
+    for a in range(g.dim):
+        c = np.floor((pts[:, a] - g.lo[a]) / g.h[a]).astype(np.int64)
+        c = np.clip(c, 0, g.n[a] - 1)
+        start = c - 1
+        if g.periodic(a):
+            cells = np.mod(start[:, None] + np.arange(3)[None, :], g.n[a])
+        else:
+            start = np.clip(start, 0, g.n[a] - 3)
+            cells = start[:, None] + np.arange(3)[None, :]
+        per_axis.append(cells)                                     # (N, 3)
+    idx = np.zeros((N, 1), dtype=np.int64)
+    for a in range(g.dim):
+        idx = (idx[:, :, None] * g.n[a] + per_axis[a][:, None, :]).reshape(N, -1)
+    return idx
 
 
 def transfer(plan, u_tilde):

@@ -9,9 +9,10 @@ row 0 reproduces f(x), rows 1..d its first derivatives. In 3D the basis has the 
 the complete quadratic (the extension §2.2 calls straightforward).
 
 Weight (Eq. 17): w = exp(-eps r^2 / hs^2) for r <= hs, else 0, eps = 6.3, with hs the support
-radius. §2.2 sets hs to three times the average spacing of the points. With a fixed neighbour
-count K the local average spacing is read off the K-th neighbour distance r_K:
-  2D: s = r_K sqrt(pi / K)      3D: s = r_K (4 pi / (3 K))^(1/3),      hs = support_factor * s.
+radius. §2.2 sets hs to three times the average spacing of the points. With a fixed stencil of
+K points the local average spacing is read off the distance r_K to the farthest of them:
+  2D: s = r_K sqrt(pi / K)      3D: s = r_K (4 pi / (3 K))^(1/3),      hs = support_factor * s,
+so every stencil point lies inside the support (hs > 1.5 r_K for the stencils used here).
 
 Numerical reading (exact in exact arithmetic): the offsets are scaled, xi = dx / hs, before
 forming C; derivative rows are divided by hs afterwards. The solve uses Gaussian elimination
@@ -59,16 +60,20 @@ def gaussian_weight(r2, hs, eps):
 def rows(delta, d2, eps, support_factor):
     """WLS coefficient rows for a batch of queries.
 
-    delta (Q, K, d): neighbour offsets x_k - x (minimum image); d2 (Q, K): squared distances,
-    ascending so that d2[:, -1] is the K-th. Returns (value_row (Q, K), grad_rows (Q, d, K)).
+    delta (Q, K, d): stencil offsets x_k - x (minimum image); d2 (Q, K): squared distances.
+    The local spacing comes from the farthest stencil point (the K-th neighbour of a K-nearest
+    stencil). Returns (value_row (Q, K), grad_rows (Q, d, K)).
     """
     Q, K, d = delta.shape
-    hs = support_radius(d2[:, -1], K, d, support_factor)          # (Q,)
+    hs = support_radius(d2.max(axis=1), K, d, support_factor)     # (Q,)
     w = gaussian_weight(d2, hs[:, None], eps)                       # (Q, K)
     xi = delta / hs[:, None, None]
     q = basis(xi)                                                   # (Q, K, m)
     A = np.transpose(q * w[:, :, None], (0, 2, 1))                  # (Q, m, K): [w_k q_k]
     C = A @ q                                                       # (Q, m, m): sum w q q^T
+    ev = np.linalg.eigvalsh(C)
+    if np.any(ev[:, 0] <= 1e-13 * ev[:, -1]):
+        raise np.linalg.LinAlgError("WLS normal matrix C is singular for some query")
     R = np.linalg.solve(C, A)                                       # (Q, m, K) = C^-1 A
     value = R[:, 0, :]
     grad = R[:, 1:1 + d, :] / hs[:, None, None]

@@ -1,0 +1,303 @@
+// Plan lifetime, validation and error reporting of libpc.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "pc_internal.cuh"
+
+namespace pc {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+pc_status fail(pc_status st, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+pc_status plan_alloc(Plan *p, void **ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (p->nallocs >= (int)(sizeof(p->allocs) / sizeof(p->allocs[0])))
+    return fail(PC_ERR_OUT_OF_MEMORY, "too many plan allocations");
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return fail(PC_ERR_OUT_OF_MEMORY, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  p->allocs[p->nallocs++] = *ptr;
+  p->bytes += bytes;
+  return PC_OK;
+}
+
+bool axis_length_supported(int n);
+
+static void destroy_plan(Plan *p) {
+  if (!p) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  cudaSetDevice(p->device);
+  for (int i = 0; i < p->nallocs; ++i) cudaFree(p->allocs[i]);
+  if (cur >= 0) cudaSetDevice(cur);
+  delete p;
+}
+
+static int axis_kind(int lo, int hi) {
+  if (lo == PC_BC_PERIODIC) return KIND_PP;
+  bool nlo = lo != PC_BC_DIRICHLET, nhi = hi != PC_BC_DIRICHLET;
+  if (nlo && nhi) return KIND_NN;
+  if (!nlo && !nhi) return KIND_DD;
+  return nlo ? KIND_ND : KIND_DN;
+}
+
+__global__ void check_nodes_kernel(const double *xyz, const uint8_t *type, long long N, int dim,
+                                   double lo0, double lo1, double lo2, double L0, double L1, double L2,
+                                   int per0, int per1, int per2, unsigned int *bad) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double lo[3] = {lo0, lo1, lo2}, L[3] = {L0, L1, L2};
+  const int per[3] = {per0, per1, per2};
+  for (int a = 0; a < dim; ++a) {
+    double x = xyz[(long long)a * N + i];
+    bool ok = isfinite(x) && x >= lo[a] && (per[a] ? x < lo[a] + L[a] : x <= lo[a] + L[a]);
+    if (!ok) atomicOr(bad, 1u);
+  }
+  if (type[i] > PC_NODE_VIRTUAL) atomicOr(bad, 2u);
+}
+
+static bool host_ptr(const void *ptr) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return !(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+}
+
+static pc_status create(const pc_problem_desc *d, int device, size_t budget, cudaStream_t st, Plan **out) {
+  if (!d || !out) return fail(PC_ERR_INVALID_ARG, "desc and out_plan are required");
+  *out = nullptr;
+  if (d->dim != 2 && d->dim != 3) return fail(PC_ERR_INVALID_ARG, "dim must be 2 or 3");
+  const int m = d->dim == 2 ? 6 : 10;
+  if (d->knn < m || d->knn > kMaxK) return fail(PC_ERR_INVALID_ARG, "knn must be in [%d, %d]", m, kMaxK);
+  if (d->num_nodes < d->knn) return fail(PC_ERR_INVALID_ARG, "fewer nodes than knn");
+  if (d->num_nodes > 2000000000LL) return fail(PC_ERR_UNSUPPORTED, "more than 2e9 nodes");
+  if (!d->node_xyz || !d->node_type) return fail(PC_ERR_INVALID_ARG, "node_xyz and node_type are required");
+  if (!(d->wls_eps > 0) || !(d->support_factor > 0) || !(d->beta > 0))
+    return fail(PC_ERR_INVALID_ARG, "wls_eps, support_factor and beta must be positive");
+  if (d->precision < PC_PREC_FP64 || d->precision > PC_PREC_FP32) return fail(PC_ERR_INVALID_ARG, "bad precision");
+  if (d->refine_iters < 0 || d->refine_iters > kMaxRefine) return fail(PC_ERR_INVALID_ARG, "refine_iters in [0, %d]", kMaxRefine);
+  if (d->gauge != 0 && d->gauge != 1) return fail(PC_ERR_INVALID_ARG, "gauge must be 0 or 1");
+  if (d->velocity_dtype != PC_DTYPE_F64 && d->velocity_dtype != PC_DTYPE_F32)
+    return fail(PC_ERR_INVALID_ARG, "bad velocity_dtype");
+  long long ncells = 1;
+  for (int a = 0; a < d->dim; ++a) {
+    if (d->n[a] < 4 || d->n[a] > 4096) return fail(PC_ERR_INVALID_ARG, "n[%d] must be in [4, 4096]", a);
+    if (!(d->h[a] > 0) || !std::isfinite(d->h[a]) || !std::isfinite(d->lo[a]))
+      return fail(PC_ERR_INVALID_ARG, "h[%d]/lo[%d] invalid", a, a);
+    if (d->bc_lo[a] < 0 || d->bc_lo[a] > 3 || d->bc_hi[a] < 0 || d->bc_hi[a] > 3)
+      return fail(PC_ERR_INVALID_ARG, "bad boundary kind on axis %d", a);
+    if ((d->bc_lo[a] == PC_BC_PERIODIC) != (d->bc_hi[a] == PC_BC_PERIODIC))
+      return fail(PC_ERR_INVALID_ARG, "periodic must pair with periodic (axis %d)", a);
+    if (!axis_length_supported((int)d->n[a]))
+      return fail(PC_ERR_UNSUPPORTED, "n[%d] = %lld: cells per axis must be even with n/2 = 2^a 3^b 5^c <= 2048",
+                  a, (long long)d->n[a]);
+    ncells *= d->n[a];
+  }
+  if (ncells > (1LL << 31) - 1) return fail(PC_ERR_UNSUPPORTED, "grid larger than 2^31 cells");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return fail(PC_ERR_CUDA, "device %d not available", device);
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return fail(PC_ERR_CUDA, "cannot select device %d", device);
+
+  Plan *p = new Plan();
+  p->device = device;
+  p->dim = d->dim;
+  p->N = d->num_nodes;
+  p->K = d->knn;
+  p->Kg = d->dim == 2 ? 9 : 27;
+  p->eps = d->wls_eps;
+  p->support_factor = d->support_factor;
+  p->beta = d->beta;
+  p->precision = d->precision;
+  p->refine_iters = d->refine_iters;
+  p->gauge = d->gauge;
+  p->vdtype = d->velocity_dtype;
+  p->ncells = ncells;
+  p->singular = true;
+  for (int a = 0; a < 3; ++a) {
+    p->n[a] = a < d->dim ? d->n[a] : 1;
+    p->lo[a] = a < d->dim ? d->lo[a] : 0.0;
+    p->h[a] = a < d->dim ? d->h[a] : 1.0;
+    p->bc_lo[a] = a < d->dim ? d->bc_lo[a] : 0;
+    p->bc_hi[a] = a < d->dim ? d->bc_hi[a] : 0;
+  }
+  for (int a = 0; a < d->dim; ++a) {
+    AxisInfo &ax = p->ax[a];
+    ax.n = (int)d->n[a];
+    ax.h = d->h[a];
+    ax.L = (double)d->n[a] * d->h[a];
+    ax.periodic = d->bc_lo[a] == PC_BC_PERIODIC;
+    ax.nfaces = ax.periodic ? ax.n : ax.n + 1;
+    ax.bc_lo = d->bc_lo[a];
+    ax.bc_hi = d->bc_hi[a];
+    ax.kind = axis_kind(d->bc_lo[a], d->bc_hi[a]);
+    if (d->bc_lo[a] == PC_BC_DIRICHLET || d->bc_hi[a] == PC_BC_DIRICHLET) p->singular = false;
+  }
+  for (int a = 0; a < d->dim; ++a) {
+    long long rows = 1;
+    for (int b = 0; b < d->dim; ++b) rows *= (b == a) ? p->ax[b].nfaces : p->ax[b].n;
+    p->nface_total[a] = rows;
+  }
+  auto bail = [&](pc_status s) { destroy_plan(p); return s; };
+
+  // Memory plan (all of it up front: pc_project allocates nothing).
+  const bool mixed = p->precision != PC_PREC_FP64;
+  const long long N = p->N, K = p->K, nc = ncells;
+  const int dd = p->dim;
+  size_t need = 0;
+  for (int a = 0; a < dd; ++a) need += (size_t)p->nface_total[a] * (K * (4 + 8 + (mixed ? 8 : 0)) + 8);
+  const long long Kg = p->Kg;
+  need += (size_t)N * Kg * (4 + dd * (8 + (mixed ? 8 : 0))) + N;
+  need += (size_t)nc * (8 + 8 + 4 + (mixed ? 8 : 0) + 8 + 8);
+  need += (size_t)dd * N * (mixed ? 8 : 8);
+  const size_t vsz = p->vdtype == PC_DTYPE_F64 ? 8 : 4;
+  need += (size_t)dd * N * vsz * 4 + (size_t)dd * N * 8;   // staging + node copy
+  if (budget && need > budget)
+    return bail(fail(PC_ERR_BUDGET, "plan needs %zu bytes, budget is %zu", need, budget));
+
+  for (int a = 0; a < dd; ++a) {
+    long long rows = p->nface_total[a];
+    if (plan_alloc(p, (void **)&p->fcol[a], rows * K * 4) != PC_OK ||
+        plan_alloc(p, (void **)&p->fw64[a], rows * K * 8) != PC_OK)
+      return bail(PC_ERR_OUT_OF_MEMORY);
+    if (mixed && (plan_alloc(p, (void **)&p->fwhi[a], rows * K * 4) != PC_OK ||
+                  plan_alloc(p, (void **)&p->fwlo[a], rows * K * 4) != PC_OK))
+      return bail(PC_ERR_OUT_OF_MEMORY);
+    if (plan_alloc(p, (void **)&p->U64[a], rows * 8) != PC_OK) return bail(PC_ERR_OUT_OF_MEMORY);
+  }
+  if (plan_alloc(p, (void **)&p->ncol, N * Kg * 4) != PC_OK || plan_alloc(p, (void **)&p->nD64, dd * N * Kg * 8) != PC_OK ||
+      plan_alloc(p, (void **)&p->ntype, N) != PC_OK || plan_alloc(p, (void **)&p->s64, nc * 8) != PC_OK ||
+      plan_alloc(p, (void **)&p->work64, nc * 8) != PC_OK || plan_alloc(p, (void **)&p->work32, nc * 4) != PC_OK ||
+      plan_alloc(p, (void **)&p->dstats, sizeof(DevStats)) != PC_OK ||
+      plan_alloc(p, (void **)&p->stage_p, nc * 8) != PC_OK || plan_alloc(p, (void **)&p->stage_s, nc * 8) != PC_OK ||
+      plan_alloc(p, &p->stage_u, dd * N * vsz) != PC_OK || plan_alloc(p, &p->stage_f, dd * N * vsz) != PC_OK ||
+      plan_alloc(p, &p->stage_uo, dd * N * vsz) != PC_OK || plan_alloc(p, &p->stage_fo, dd * N * vsz) != PC_OK)
+    return bail(PC_ERR_OUT_OF_MEMORY);
+  if (mixed) {
+    if (plan_alloc(p, (void **)&p->nDhi, dd * N * Kg * 4) != PC_OK || plan_alloc(p, (void **)&p->nDlo, dd * N * Kg * 4) != PC_OK ||
+        plan_alloc(p, (void **)&p->phi, nc * 4) != PC_OK || plan_alloc(p, (void **)&p->plo, nc * 4) != PC_OK ||
+        plan_alloc(p, (void **)&p->uhi, dd * N * 4) != PC_OK || plan_alloc(p, (void **)&p->ulo, dd * N * 4) != PC_OK)
+      return bail(PC_ERR_OUT_OF_MEMORY);
+  } else {
+    if (plan_alloc(p, (void **)&p->ut64, dd * N * 8) != PC_OK) return bail(PC_ERR_OUT_OF_MEMORY);
+  }
+  // node coordinates and types on the device
+  double *xyz_dev = nullptr;
+  if (plan_alloc(p, (void **)&xyz_dev, dd * N * 8) != PC_OK) return bail(PC_ERR_OUT_OF_MEMORY);
+  cudaMemcpyKind k1 = host_ptr(d->node_xyz) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaMemcpyKind k2 = host_ptr(d->node_type) ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (cudaMemcpyAsync(xyz_dev, d->node_xyz, dd * N * 8, k1, st) != cudaSuccess ||
+      cudaMemcpyAsync(p->ntype, d->node_type, N, k2, st) != cudaSuccess)
+    return bail(fail(PC_ERR_CUDA, "copy of node arrays failed"));
+  {
+    unsigned int *bad = reinterpret_cast<unsigned int *>(p->dstats);
+    cudaMemsetAsync(bad, 0, sizeof(unsigned), st);
+    check_nodes_kernel<<<grid_for(N, 256), 256, 0, st>>>(xyz_dev, p->ntype, N, dd, p->lo[0], p->lo[1], p->lo[2],
+                                                         p->ax[0].L, p->ax[1].L, dd > 2 ? p->ax[2].L : 1.0,
+                                                         p->ax[0].periodic, p->ax[1].periodic,
+                                                         dd > 2 ? (int)p->ax[2].periodic : 0, bad);
+    unsigned int hb = 0;
+    if (cudaMemcpyAsync(&hb, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return bail(fail(PC_ERR_CUDA, "node validation failed: %s", cudaGetErrorString(cudaGetLastError())));
+    if (hb & 1u) return bail(fail(PC_ERR_INVALID_ARG, "a node lies outside the domain or is not finite"));
+    if (hb & 2u) return bail(fail(PC_ERR_INVALID_ARG, "node_type values must be 0, 1 or 2"));
+  }
+  pc_status s = build_axis_tables(p);
+  if (s != PC_OK) return bail(s);
+  s = build_rows(p, xyz_dev, st);
+  if (s != PC_OK) return bail(s);
+  *out = p;
+  return PC_OK;
+}
+
+}  // namespace pc
+
+extern "C" pc_status pc_plan_create(const pc_problem_desc *desc, int device, size_t hbm_budget_bytes,
+                                    void *cuda_stream, pc_plan **out_plan) {
+  pc::Plan *p = nullptr;
+  pc_status s = pc::create(desc, device, hbm_budget_bytes, (cudaStream_t)cuda_stream, &p);
+  if (s == PC_OK) *out_plan = reinterpret_cast<pc_plan *>(p);
+  return s;
+}
+
+extern "C" pc_status pc_destroy(pc_plan *plan) {
+  pc::destroy_plan(reinterpret_cast<pc::Plan *>(plan));
+  return PC_OK;
+}
+
+extern "C" pc_status pc_plan_bytes(const pc_plan *plan, size_t *bytes_out) {
+  const pc::Plan *p = reinterpret_cast<const pc::Plan *>(plan);
+  if (!p || !bytes_out) return pc::fail(PC_ERR_INVALID_ARG, "plan and bytes_out are required");
+  *bytes_out = p->bytes;
+  return PC_OK;
+}
+
+extern "C" pc_status pc_plan_rows(const pc_plan *plan, int which, int64_t *rows_out, int32_t *col_out,
+                                  double *w_out) {
+  const pc::Plan *p = reinterpret_cast<const pc::Plan *>(plan);
+  if (!p || !rows_out) return pc::fail(PC_ERR_INVALID_ARG, "plan and rows_out are required");
+  if (which < 0 || which > p->dim) return pc::fail(PC_ERR_INVALID_ARG, "which must be in [0, dim]");
+  if (cudaSetDevice(p->device) != cudaSuccess) return pc::fail(PC_ERR_CUDA, "cannot select device");
+  const long long K = which < p->dim ? p->K : p->Kg;
+  long long rows = which < p->dim ? p->nface_total[which] : p->N;
+  *rows_out = rows;
+  if (!col_out && !w_out) return PC_OK;
+  // stored neighbour-rank major on the device; returned row major
+  std::vector<int32_t> c(rows * K);
+  std::vector<double> w((which < p->dim ? 1 : p->dim) * rows * K);
+  const int32_t *dc = which < p->dim ? p->fcol[which] : p->ncol;
+  const double *dw = which < p->dim ? p->fw64[which] : p->nD64;
+  PC_CUDA_TRY(cudaMemcpy(c.data(), dc, c.size() * 4, cudaMemcpyDeviceToHost));
+  PC_CUDA_TRY(cudaMemcpy(w.data(), dw, w.size() * 8, cudaMemcpyDeviceToHost));
+  const long long nw = which < p->dim ? 1 : p->dim;
+  for (long long r = 0; r < rows; ++r)
+    for (long long k = 0; k < K; ++k) {
+      if (col_out) col_out[r * K + k] = c[k * rows + r];
+      if (w_out)
+        for (long long a = 0; a < nw; ++a) w_out[(a * rows + r) * K + k] = w[(a * K + k) * rows + r];
+    }
+  return PC_OK;
+}
+
+extern "C" const char *pc_status_string(pc_status s) {
+  switch (s) {
+    case PC_OK: return "ok";
+    case PC_ERR_INVALID_ARG: return "invalid argument";
+    case PC_ERR_UNSUPPORTED: return "unsupported";
+    case PC_ERR_WLS_SINGULAR: return "singular WLS system";
+    case PC_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case PC_ERR_BUDGET: return "device-memory budget exceeded";
+    case PC_ERR_CUDA: return "CUDA error";
+    case PC_ERR_NOT_CONVERGED: return "refinement not converged";
+    case PC_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+extern "C" const char *pc_last_error_message(void) { return pc::g_err; }

@@ -1,0 +1,141 @@
+// Internal definitions of libpc: plan layout, error plumbing, small device helpers.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/pc.h"
+
+namespace pc {
+
+// Transform kind of one axis, from its boundary pair (§2.3: the transform follows the grid
+// type and the boundary conditions).
+enum AxisKind { KIND_PP = 0, KIND_NN = 1, KIND_DD = 2, KIND_ND = 3, KIND_DN = 4 };
+
+constexpr int kMaxRadices = 24;
+constexpr int kMaxK = 32;
+constexpr int kMaxRefine = 8;
+
+// Device-side status word values (written by kernels, read at the next sync point).
+enum DeviceFlag { FLAG_WLS_SINGULAR = 1, FLAG_KNN_SHORT = 2, FLAG_NONFINITE = 4 };
+
+struct AxisInfo {
+  int kind = 0;
+  int n = 0;        // cells
+  int M = 0;        // complex FFT length n/2
+  int nradix = 0;
+  int radix[kMaxRadices] = {0};
+  double h = 0.0;
+  double L = 0.0;   // n * h
+  bool periodic = false;
+  int nfaces = 0;   // faces normal to this axis along it (n or n+1)
+  int bc_lo = 0, bc_hi = 0;
+  // Twiddle tables, one buffer per precision: [0,M) e^{-2 pi i k/M}; [M, 2M+1) post/pre
+  // twiddle of the real-to-real wrapper (kind dependent); [2M+1, 3M+1) DCT-IV pre twiddle.
+  double2 *tw64 = nullptr;
+  float2 *tw32 = nullptr;
+  double *lam64 = nullptr;   // eigenvalue per spectral index (n entries)
+  float *lam32 = nullptr;
+};
+
+// Per-call device statistics (mirrors pc_stats fields filled on the device).
+struct DevStats {
+  double sum_s;            // sum of the source over cells
+  double sum_s2;           // sum of squares
+  double res2[kMaxRefine + 1];
+  double sum_p;            // sum of p before the gauge
+  double corner_p;
+  double max_div;
+  double max_u;
+  unsigned int flags;
+  unsigned int pad;
+};
+
+struct Plan {
+  int device = 0;
+  int dim = 2;
+  int64_t n[3] = {1, 1, 1};
+  double lo[3] = {0, 0, 0}, h[3] = {1, 1, 1};
+  int bc_lo[3] = {0, 0, 0}, bc_hi[3] = {0, 0, 0};
+  int64_t N = 0;
+  int K = 12;                  // neighbours of a face (transfer) stencil
+  int Kg = 9;                  // cells of a node (gradient) stencil: 3^dim
+  double eps = 6.3, support_factor = 3.0, beta = 1.5;
+  int precision = PC_PREC_FP64;
+  int refine_iters = 2;
+  int gauge = 0;
+  int vdtype = PC_DTYPE_F64;
+  bool singular = false;
+
+  AxisInfo ax[3];
+  int64_t ncells = 0;
+  int64_t nface_total[3] = {0, 0, 0};
+
+  // WLS rows, neighbour-rank major: entry k of row r at k*rows + r.
+  int32_t *fcol[3] = {nullptr, nullptr, nullptr};
+  double *fw64[3] = {nullptr, nullptr, nullptr};
+  float *fwhi[3] = {nullptr, nullptr, nullptr};
+  float *fwlo[3] = {nullptr, nullptr, nullptr};
+  int32_t *ncol = nullptr;     // [Kg][N] cell linear index
+  double *nD64 = nullptr;      // [dim][Kg][N]
+  float *nDhi = nullptr, *nDlo = nullptr;
+  uint8_t *ntype = nullptr;    // [N]
+
+  // Workspace (allocated once; pc_project allocates nothing).
+  double *U64[3] = {nullptr, nullptr, nullptr};  // face fluxes
+  double *s64 = nullptr;       // source
+  double *p64 = nullptr;       // pressure (refined iterate)
+  double *work64 = nullptr;    // FP64 transform workspace (cells)
+  float *work32 = nullptr;     // FP32 transform workspace (cells)
+  float *phi = nullptr, *plo = nullptr;   // split pressure for the compensated gradient
+  float *uhi = nullptr, *ulo = nullptr;   // split u~ = u* + dt f for the compensated transfer
+  double *ut64 = nullptr;                 // u~ in FP64 (FP64 path)
+  DevStats *dstats = nullptr;
+  // Staging for host pointers passed to pc_project.
+  void *stage_u = nullptr, *stage_f = nullptr, *stage_uo = nullptr, *stage_fo = nullptr;
+  double *stage_p = nullptr, *stage_s = nullptr;
+  size_t bytes = 0;
+  void *allocs[64];
+  int nallocs = 0;
+};
+
+// ----------------------------------------------------------------------------- errors
+void set_error(const char *fmt, ...);
+pc_status fail(pc_status st, const char *fmt, ...);
+
+#define PC_CUDA_TRY(expr)                                                                    \
+  do {                                                                                       \
+    cudaError_t _e = (expr);                                                                 \
+    if (_e != cudaSuccess)                                                                   \
+      return ::pc::fail(PC_ERR_CUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), \
+                        __FILE__, __LINE__);                                                 \
+  } while (0)
+
+#define PC_TRY(expr)                       \
+  do {                                     \
+    pc_status _s = (expr);                 \
+    if (_s != PC_OK) return _s;            \
+  } while (0)
+
+pc_status plan_alloc(Plan *p, void **ptr, size_t bytes);
+
+// ----------------------------------------------------------------------------- launches
+inline int grid_for(int64_t work, int threads) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > (1LL << 30)) b = 1LL << 30;
+  return (int)b;
+}
+
+// Solver entry points (poisson.cu).
+pc_status solve_fp64(Plan *p, const double *s_dev, double *p_dev, bool from_faces,
+                     cudaStream_t st);
+pc_status solve_mixed(Plan *p, const double *s_dev, double *p_dev, bool from_faces,
+                      int sweeps, cudaStream_t st);
+// Setup (setup.cu).
+pc_status build_rows(Plan *p, const double *xyz_dev, cudaStream_t st);
+// Axis tables (poisson.cu).
+pc_status build_axis_tables(Plan *p);
+
+}  // namespace pc

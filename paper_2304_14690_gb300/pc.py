@@ -1,0 +1,275 @@
+"""Python binding of libpc (include/pc.h): argument marshalling only.
+
+Every step of the pressure-correction sub-step runs inside libpc's CUDA kernels; this module
+only converts workloads and torch tensors into the C structures and pointers the ABI takes.
+If the library has not been built, importing works but every call raises: there is no
+fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpc.so")
+
+BC = {"P": 0, "W": 1, "I": 2, "D": 3}
+PRECISION = {"fp64": 0, "mixed": 1, "fp32": 2}
+DTYPE = {"f64": 0, "f32": 1}
+STATUS = ["ok", "invalid argument", "unsupported", "singular WLS system", "out of device memory",
+          "device-memory budget exceeded", "CUDA error", "refinement not converged", "timeout"]
+
+
+class PcError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"libpc status {status} ({STATUS[status] if status < len(STATUS) else '?'}): {message}")
+        self.status = status
+
+
+class Obstacle(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int), ("centre", ctypes.c_double * 3), ("radius", ctypes.c_double)]
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("n", ctypes.c_int64 * 3),
+        ("lo", ctypes.c_double * 3),
+        ("h", ctypes.c_double * 3),
+        ("bc_lo", ctypes.c_int * 3),
+        ("bc_hi", ctypes.c_int * 3),
+        ("num_nodes", ctypes.c_int64),
+        ("node_xyz", ctypes.c_void_p),
+        ("node_type", ctypes.c_void_p),
+        ("num_obstacles", ctypes.c_int),
+        ("obstacles", ctypes.POINTER(Obstacle)),
+        ("knn", ctypes.c_int),
+        ("wls_eps", ctypes.c_double),
+        ("support_factor", ctypes.c_double),
+        ("beta", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("refine_iters", ctypes.c_int),
+        ("gauge", ctypes.c_int),
+        ("velocity_dtype", ctypes.c_int),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("removed_mean", ctypes.c_double),
+        ("source_norm", ctypes.c_double),
+        ("residual_norm", ctypes.c_double * 9),
+        ("refine_iters_done", ctypes.c_int),
+        ("max_div_after", ctypes.c_double),
+        ("max_abs_u_star", ctypes.c_double),
+        ("gauge_shift", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        n = self.refine_iters_done
+        return dict(removed_mean=self.removed_mean, source_norm=self.source_norm,
+                    residual_norm=list(self.residual_norm[: n + 1]), refine_iters_done=n,
+                    max_div_after=self.max_div_after, max_abs_u_star=self.max_abs_u_star,
+                    gauge_shift=self.gauge_shift)
+
+
+class ProjectArgs(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("u_star", ctypes.c_void_p), ("f_ib_in", ctypes.c_void_p),
+                ("p_out", ctypes.c_void_p), ("u_out", ctypes.c_void_p), ("f_ib_out", ctypes.c_void_p)]
+
+
+FUNCTIONS = {
+    "pc_plan_create": (ctypes.c_int, [ctypes.POINTER(ProblemDesc), ctypes.c_int, ctypes.c_size_t,
+                                      ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "pc_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.POINTER(Stats), ctypes.c_void_p]),
+    "pc_project_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ProjectArgs), ctypes.c_void_p]),
+    "pc_solve_poisson": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.POINTER(Stats), ctypes.c_void_p]),
+    "pc_plan_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "pc_plan_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "pc_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "pc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "pc_last_error_message": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load():
+    """Load libpc.so; raises when it is missing (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libpc is not built ({LIB_PATH} missing); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in FUNCTIONS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise PcError(status, load().pc_last_error_message().decode())
+
+
+def _ptr(x, shape=None, dtype=None, name="array"):
+    """Data pointer of a dense torch tensor or numpy array (None -> NULL). The C ABI takes
+    plain pointers to dense C-order arrays, so strided views are rejected."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous (C order)")
+        if shape is not None and tuple(x.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(x.shape)}, expected {tuple(shape)}")
+        if dtype is not None and x.dtype != dtype:
+            raise ValueError(f"{name} has dtype {x.dtype}, expected {dtype}")
+        return x.data_ptr()
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{name} must be C-contiguous")
+    return x.ctypes.data
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def make_desc(problem, precision="fp64", refine_iters=2, gauge=0, velocity_dtype=None,
+              node_xyz=None, node_type=None):
+    d = ProblemDesc()
+    d.dim = problem.dim
+    for a in range(3):
+        d.n[a] = int(problem.n[a]) if a < problem.dim else 1
+        d.lo[a] = float(problem.lo[a]) if a < problem.dim else 0.0
+        d.h[a] = float(problem.h[a]) if a < problem.dim else 1.0
+        d.bc_lo[a] = BC[problem.bc_lo[a]] if a < problem.dim else 0
+        d.bc_hi[a] = BC[problem.bc_hi[a]] if a < problem.dim else 0
+    d.num_nodes = problem.num_nodes
+    d.node_xyz = _ptr(node_xyz)
+    d.node_type = _ptr(node_type)
+    d.num_obstacles = 0
+    d.obstacles = None
+    d.knn = int(problem.knn)
+    d.wls_eps = float(problem.eps)
+    d.support_factor = float(problem.support_factor)
+    d.beta = float(problem.beta)
+    d.precision = PRECISION[precision]
+    d.refine_iters = int(refine_iters)
+    d.gauge = int(gauge)
+    if velocity_dtype is None:
+        velocity_dtype = "f32" if problem.u_star.dtype == np.float32 else "f64"
+    d.velocity_dtype = DTYPE[velocity_dtype]
+    return d
+
+
+class Plan:
+    """A libpc plan for one problem geometry (nodes, grid, boundaries)."""
+
+    def __init__(self, problem, precision="fp64", refine_iters=2, gauge=0, device=0,
+                 budget_bytes=0, stream=None):
+        import torch
+        lib = load()
+        self.problem = problem
+        self.precision = precision
+        self.device = torch.device("cuda", device)
+        self.vdtype = torch.float32 if problem.u_star.dtype == np.float32 else torch.float64
+        xyz = torch.as_tensor(np.ascontiguousarray(problem.nodes, dtype=np.float64), device=self.device)
+        typ = torch.as_tensor(np.ascontiguousarray(problem.node_type, dtype=np.uint8), device=self.device)
+        self._desc = make_desc(problem, precision, refine_iters, gauge,
+                               "f32" if self.vdtype == torch.float32 else "f64", xyz, typ)
+        h = ctypes.c_void_p()
+        _check(lib.pc_plan_create(ctypes.byref(self._desc), device, budget_bytes,
+                                  _stream_handle(stream), ctypes.byref(h)))
+        self.handle = h
+        self.dim = problem.dim
+        self.N = problem.num_nodes
+        self.shape = tuple(int(v) for v in problem.n[: problem.dim])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def nbytes(self):
+        b = ctypes.c_size_t()
+        _check(load().pc_plan_bytes(self.handle, ctypes.byref(b)))
+        return b.value
+
+    def rows(self, which):
+        """(col [rows, K] int32, w) of face axis `which` (w [rows, K]) or of the nodes
+        (which == dim, w [dim, rows, K])."""
+        lib = load()
+        n = ctypes.c_int64()
+        _check(lib.pc_plan_rows(self.handle, which, ctypes.byref(n), None, None))
+        K = self.problem.knn if which < self.dim else 3 ** self.dim
+        col = np.empty((n.value, K), dtype=np.int32)
+        w = np.empty(((self.dim if which == self.dim else 1), n.value, K), dtype=np.float64)
+        _check(lib.pc_plan_rows(self.handle, which, ctypes.byref(n), col.ctypes.data, w.ctypes.data))
+        return col, (w if which == self.dim else w[0])
+
+    def alloc_outputs(self):
+        import torch
+        p = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        u = torch.empty((self.dim, self.N), dtype=self.vdtype, device=self.device)
+        f = torch.empty((self.dim, self.N), dtype=self.vdtype, device=self.device)
+        return p, u, f
+
+    def project(self, u_star, f_ib=None, dt=None, out=None, stats=False, stream=None):
+        """Run pc_project. u_star/f_ib: torch tensors (device or host) [dim, N].
+        Returns (p, u_out, f_out, stats_dict or None)."""
+        lib = load()
+        if dt is None:
+            dt = self.problem.dt
+        p, u, f = out if out is not None else self.alloc_outputs()
+        st = Stats() if stats else None
+        vshape = (self.dim, self.N)
+        _check(lib.pc_project(self.handle, float(dt), _ptr(u_star, vshape, self.vdtype, "u_star"),
+                              _ptr(f_ib, vshape, self.vdtype, "f_ib"),
+                              _ptr(p, self.shape, None, "p_out"), _ptr(u, vshape, self.vdtype, "u_out"),
+                              _ptr(f, vshape, self.vdtype, "f_out"),
+                              ctypes.byref(st) if st is not None else None, _stream_handle(stream)))
+        return p, u, f, (st.as_dict() if st is not None else None)
+
+    def solve_poisson(self, s, p_out=None, stats=False, stream=None):
+        import torch
+        lib = load()
+        if p_out is None:
+            p_out = torch.empty(self.shape, dtype=torch.float64, device=s.device)
+        st = Stats() if stats else None
+        _check(lib.pc_solve_poisson(self.handle, _ptr(s, self.shape, torch.float64, "s"),
+                                    _ptr(p_out, self.shape, torch.float64, "p_out"),
+                                    ctypes.byref(st) if st is not None else None, _stream_handle(stream)))
+        return p_out, (st.as_dict() if st is not None else None)
+
+
+def project_batch(plans, args, stream=None):
+    """pc_project_batch over (plan, dict(dt, u_star, f_ib, p, u, f)) pairs (device tensors)."""
+    lib = load()
+    n = len(plans)
+    hs = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    arr = (ProjectArgs * n)()
+    for i, a in enumerate(args):
+        arr[i].dt = float(a["dt"])
+        arr[i].u_star = _ptr(a["u_star"])
+        arr[i].f_ib_in = _ptr(a.get("f_ib"))
+        arr[i].p_out = _ptr(a["p"])
+        arr[i].u_out = _ptr(a["u"])
+        arr[i].f_ib_out = _ptr(a.get("f"))
+    _check(lib.pc_project_batch(n, hs, arr, _stream_handle(stream)))

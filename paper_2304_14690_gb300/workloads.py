@@ -44,6 +44,14 @@ class Problem:
     support_factor: float = 3.0
     obstacles: list = field(default_factory=list)   # (kind, centre tuple, radius)
 
+    def __post_init__(self):
+        # dense structure-of-arrays layout, as the C ABI expects
+        self.nodes = np.ascontiguousarray(self.nodes, dtype=np.float64)
+        self.node_type = np.ascontiguousarray(self.node_type, dtype=np.uint8)
+        self.u_star = np.ascontiguousarray(self.u_star)
+        if self.f_ib is not None:
+            self.f_ib = np.ascontiguousarray(self.f_ib, dtype=self.u_star.dtype)
+
     @property
     def num_nodes(self):
         return int(self.nodes.shape[1])

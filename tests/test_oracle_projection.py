@@ -126,6 +126,30 @@ def test_gradient_rows_exact_for_quadratic():
     assert np.abs(gr - ex).max() < 1e-11
 
 
+def test_gradient_rows_exact_near_3d_walls():
+    """3D nodes against walls and in corners: the block stencil still reproduces a quadratic."""
+    prob = wl.generic(dim=3, n=(8, 10, 6), bc_lo=("W", "D", "I"), bc_hi=("W", "W", "D"),
+                      obstacles=[("sphere", (0.25, 0.3, 0.2), 0.1)], seed=9)
+    g = grid_of(prob)
+    plan = PR.build_plan(g, prob.nodes, prob.node_type, K=prob.knn)
+    cx, cy, cz = np.meshgrid(*[g.cell_centres(a) for a in range(3)], indexing="ij")
+    p = 1.0 + 0.5 * cx - cy + 2.0 * cz + cx * cx - 0.3 * cy * cz + 0.7 * cz * cz
+    gr = PR.node_gradient(plan, p)
+    x, y, z = prob.nodes
+    ex = np.stack([0.5 + 2 * x, -1.0 - 0.3 * z, 2.0 - 0.3 * y + 1.4 * z])
+    assert np.abs(gr - ex).max() < 1e-10
+
+
+def test_gradient_block_shape():
+    g = G.Grid(2, (6, 4), (0.0, 0.0), (1.0, 1.0), ("W", "P"), ("W", "P"))
+    pts = np.array([[0.1, 0.2], [5.9, 3.9], [2.5, 1.5]])
+    idx = PR.gradient_block(g, pts)
+    rows = [sorted({int(c) // 4 for c in r}) for r in idx]
+    cols = [sorted({int(c) % 4 for c in r}) for r in idx]
+    assert rows == [[0, 1, 2], [3, 4, 5], [1, 2, 3]]     # shifted inward at walls
+    assert cols == [[0, 1, 3], [0, 2, 3], [0, 1, 2]]     # wrapped on the periodic axis
+
+
 def test_transfer_exact_for_quadratic_velocity():
     prob = wl.generic(dim=3, n=(8, 8, 8), bc_lo=("P", "W", "W"), bc_hi=("P", "W", "W"), seed=5)
     g = grid_of(prob)
