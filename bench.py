@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Throughput of the pressure-correction sub-step on one GB300 (or N replicas under torchrun).
+
+Workload: the 2D channel [0,20]x[0,10] with a cylinder (D=1 at (5,5)), 1024x512 pressure cells,
+Neumann inflow / Dirichlet outflow in x, walls in y, ~4e5 meshless nodes refined radially around
+the cylinder (seeded synthetic inputs; the paper publishes no dataset). One step = one full
+projection: WLS transfer, divergence source, transform Poisson solve with FP64-residual
+refinement, WLS gradient and correction with the IB force. Mixed precision by default.
+
+Prints one JSON line. value = pressure cells projected per second over all ranks, device-timed
+with CUDA events around each step, a 256 MB buffer written between steps to flush L2.
+  --impl reference   the plain FP64 CPU oracle on the same workload (rank 0 only)
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("projected grid-points/s and HBM % of peak at 1e-10 rel-L2 vs plain FP64 GPU; "
+          "p50/p99 ms")
+UNIT = "grid-points/s"
+WORKLOAD = "channel_cylinder 1024x512 cells, ~4.0e5 nodes, inflow/outflow x, walls y, cylinder D=1"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--refine", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2304_14690_gb300 import workloads as wl
+    return wl.channel_cylinder()
+
+
+# ----------------------------------------------------------------------------- oracle timing
+
+def oracle_timing(steps, warmup, seconds=None, max_steps=None):
+    """Time the CPU oracle's projection (plan built first, untimed). Returns (cells/s, info)."""
+    from oracle import grid as G, projection as PR
+    prob = workload()
+    g = G.Grid(prob.dim, prob.n, prob.lo, prob.h, prob.bc_lo, prob.bc_hi)
+    t0 = time.perf_counter()
+    plan = PR.build_plan(g, prob.nodes, prob.node_type, K=prob.knn)
+    plan_s = time.perf_counter() - t0
+    for _ in range(warmup):
+        PR.project(plan, prob.dt, prob.u_star)
+    times = []
+    t_start = time.perf_counter()
+    while True:
+        t = time.perf_counter()
+        PR.project(plan, prob.dt, prob.u_star)
+        times.append(time.perf_counter() - t)
+        if seconds is None and len(times) >= steps:
+            break
+        if max_steps is not None and len(times) >= max_steps:
+            break
+        if seconds is not None and time.perf_counter() - t_start >= seconds and len(times) >= 2:
+            break
+    total = sum(times)
+    cells = prob.num_cells
+    return cells * len(times) / total, dict(projections=len(times), seconds=total,
+                                            plan_seconds=plan_s, ms_per_projection=1e3 * total / len(times),
+                                            times=times)
+
+
+def cpu_baseline_subprocess(seconds):
+    """Run the oracle timing single-threaded in a fresh interpreter (BLAS pinned to 1 thread)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-baseline-only",
+           "--cpu-seconds", str(seconds)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-500:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    def __init__(self, device_index):
+        self.proc = None
+        self.path = None
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "50"]
+            if device_index is not None:
+                cmd += ["-i", str(device_index)]
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["smax"] for r in rows),
+                "samples": len(rows), "power_w_max": max(r["power"] for r in rows),
+                "reasons": sorted(reasons)}
+
+
+def _smi_id(dev, local_rank):
+    """nvidia-smi -i selector of this rank's GPU (UUID when torch exposes it)."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    return None if os.environ.get("CUDA_VISIBLE_DEVICES") else local_rank
+
+
+# ----------------------------------------------------------------------------- roofline
+
+def phase_bytes(prob, precision, refine):
+    """Algorithmic (compulsory) DRAM bytes per call of each phase, from the data each kernel must
+    read and write once: WLS rows (index + weights), gathered node/cell values, outputs."""
+    d, N, K, Kg = prob.dim, prob.num_nodes, prob.knn, 3 ** prob.dim
+    nc = prob.num_cells
+    faces = 0
+    for a in range(d):
+        nf = prob.n[a] if prob.bc_lo[a] == "P" else prob.n[a] + 1
+        faces += nf * nc // prob.n[a]
+    vb = prob.u_star.dtype.itemsize
+    mixed = precision != "fp64"
+    wbytes = 8                                   # FP64 weight, or FP32 hi + lo
+    tr = faces * (K * (4 + wbytes) + 8) + d * N * (8 if mixed else 8)
+    prep = d * N * vb + d * N * 8
+    div = faces * 8 + nc * 8
+    sweeps = refine if precision == "mixed" else 0
+    if mixed:
+        # first solve: s64 in (8), work32 out/in/out/in (4+8+4), p64 out (8); sweeps: r32 in,
+        # work32 x3, p64 read-modify-write
+        xf = nc * (8 + 4 + 8 + 4 + 8) + sweeps * nc * (4 + 4 + 8 + 4 + 16)
+        res = sweeps * nc * (8 + 8 + 4)
+        gauge = nc * (8 + 8 + 8 + 8)
+    else:
+        xf = nc * (8 + 8 + 16 + 8 + 8)
+        res = 0
+        gauge = nc * (8 + 8 + 8)
+    grad = N * (Kg * (4 + d * wbytes) + d * vb * 3 + 1) + nc * (8 if mixed else 8)
+    return {"prep": prep, "transfer": tr, "divergence": div, "transform": xf, "residual": res,
+            "gauge": gauge, "gradient": grad}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(phase):
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        return d.get(phase)
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2304_14690_gb300 import pc
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    prob = workload()
+    plan = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, device=local_rank)
+    u_dev = torch.as_tensor(prob.u_star, device=dev)
+    outs = plan.alloc_outputs()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        plan.project(u_dev, out=outs)
+    torch.cuda.synchronize(dev)
+
+    # ---- device-timed region
+    steps = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    plan.profile(True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(_smi_id(dev, local_rank))
+    t_wall = time.perf_counter()
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        evs[k][0].record(stream)
+        plan.project(u_dev, out=outs)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t_wall
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    prof = plan.profile_read()
+    plan.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    cells = prob.num_cells
+    value = world * cells * steps / (total_ms * 1e-3)
+    srt = sorted(step_ms)
+    p50 = srt[len(srt) // 2]
+    p99 = srt[min(len(srt) - 1, int(0.99 * len(srt)))]
+
+    # ---- roofline of the dominant phase (live CUDA events on the launching stream)
+    calls = max(prof["calls"], 1)
+    pb = phase_bytes(prob, args.precision, args.refine)
+    phases = {k: v / calls for k, v in prof["phase_ms"].items() if v > 0}
+    dom = max((k for k in phases if k in pb), key=lambda k: phases[k])
+    peak, peak_src = measured_peaks()
+
+    def roof(name):
+        ms = phases[name]
+        ach = pb[name] / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "phase": name, "achieved": round(ach, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": ncu_traffic(name),
+                "algorithmic_bytes": pb[name], "ms": round(ms, 5), "peak_source": peak_src}
+
+    roofline = roof(dom)
+    roofline_transform = roof("transform") if "transform" in phases else None
+
+    # ---- accuracy against the plain FP64 GPU path, and that path's own throughput
+    acc = {}
+    fp64 = None
+    if rank == 0:
+        ref = pc.Plan(prob, precision="fp64", device=local_rank)
+        ro = ref.alloc_outputs()
+        ref.project(u_dev, out=ro)
+        torch.cuda.synchronize(dev)
+
+        def rel(a, b):
+            return float(torch.linalg.vector_norm(a.double() - b.double()) / torch.linalg.vector_norm(b.double()))
+
+        acc["rel_l2_p_vs_fp64_gpu"] = rel(outs[0], ro[0])
+        acc["rel_l2_u_vs_fp64_gpu"] = rel(outs[1], ro[1])
+        _, _, _, st = plan.project(u_dev, out=outs, stats=True)
+        acc["max_div_after_rel"] = st["max_div_after"] * min(prob.h) / st["max_abs_u_star"]
+        acc["residual_norms"] = st["residual_norm"]
+        if args.precision == "mixed":
+            p32 = pc.Plan(prob, precision="fp32", device=local_rank)
+            o32 = p32.alloc_outputs()
+            p32.project(u_dev, out=o32)
+            acc["fp32_unrefined_rel_l2_p"] = rel(o32[0], ro[0])
+            p32.close()
+        # plain FP64 GPU path timed the same way
+        n64 = max(20, min(200, steps // 5))
+        e64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n64)]
+        for _ in range(3):
+            ref.project(u_dev, out=ro)
+        for k in range(n64):
+            flush.fill_(k & 0xFF)
+            e64[k][0].record(stream)
+            ref.project(u_dev, out=ro)
+            e64[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = sum(a.elapsed_time(b) for a, b in e64) / n64
+        fp64 = {"ms_per_step": round(ms64, 5), "value": cells / (ms64 * 1e-3),
+                "speedup_of_this_path": round(ms64 / (total_ms / steps), 3)}
+        ref.close()
+
+    # ---- end to end through the C ABI with pinned host buffers
+    hu = torch.as_tensor(prob.u_star).pin_memory()
+    ho = (torch.empty(plan.shape, dtype=torch.float64).pin_memory(),
+          torch.empty((prob.dim, prob.num_nodes), dtype=plan.vdtype).pin_memory(),
+          torch.empty((prob.dim, prob.num_nodes), dtype=plan.vdtype).pin_memory())
+    ne = max(10, min(200, steps // 5))
+    for _ in range(3):
+        plan.project(hu, out=ho)
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ne)]
+    torch.cuda.synchronize(dev)
+    for k in range(ne):
+        ee[k][0].record(stream)
+        plan.project(hu, out=ho)          # H2D of u*, kernels, D2H of p, u, f inside the call
+        ee[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = sum(a.elapsed_time(b) for a, b in ee) / ne
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * cells / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": int(hu.numel() * hu.element_size()),
+           "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in ho)),
+           "ms_per_step": round(e2e_ms, 5)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_subprocess(args.cpu_seconds)
+
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": round(total_ms / steps, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(prob.n), "nodes": prob.num_nodes,
+                   "precision": args.precision, "refine_iters": args.refine,
+                   "knn": prob.knn, "l2": "256 MB buffer written between timed steps",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "latency_ms": {"p50": round(p50, 5), "p99": round(p99, 5)},
+        "roofline": roofline, "roofline_transform": roofline_transform,
+        "phase_ms": {k: round(v, 5) for k, v in phases.items()},
+        "accuracy": acc, "fp64_path": fp64, "e2e": e2e,
+        "gpu_launches": int(prof["kernel_launches"] * steps / calls),
+        "clocks": clocks, "cpu_baseline": cpu, "wall_s": round(wall, 3),
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    plan.close()
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank):
+    """The oracle as it stands, on this arm's workload and metric. A step is one full projection;
+    the run is bounded to about 90 s of projections after the (untimed) plan build, so it takes
+    min(steps, what fits) steps and says how many in cpu_baseline.sample."""
+    if rank != 0:
+        return
+    val, info = oracle_timing(args.steps, min(args.warmup, 1), seconds=90.0, max_steps=args.steps)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 1), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(info["ms_per_projection"], 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "fp64 oracle", "knn": 12},
+        "cpu_baseline": {"value": round(val, 1), "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
+                         "sample": f"{info['projections']} full projections of the workload "
+                                   f"(plan built first, {info['plan_seconds']:.1f} s, untimed)"},
+        "e2e": {"value": round(val, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def _blas_threads():
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(k):
+            try:
+                return int(os.environ[k])
+            except ValueError:
+                pass
+    return os.cpu_count()
+
+
+def main():
+    args = parse()
+    if args.cpu_baseline_only:
+        val, info = oracle_timing(0, 1, seconds=args.cpu_seconds)
+        print(json.dumps({"value": round(val, 1), "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
+                          "sample": f"{info['projections']} full projections of the 1024x512 channel workload "
+                                    f"({info['seconds']:.1f} s; plan built first in {info['plan_seconds']:.1f} s, "
+                                    f"untimed), single thread"}))
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -159,6 +159,22 @@ pc_status pc_solve_poisson(pc_plan *plan, const double *s, double *p_out, pc_sta
 pc_status pc_plan_rows(const pc_plan *plan, int which, int64_t *rows_out, int32_t *col_out,
                        double *w_out);
 
+/* Optional per-phase timing with CUDA events recorded on the call's stream (for profiling and
+ * roofline reports; leave it off in production and under stream capture). Phases:
+ * 0 prep (u~ = u* + dt f~), 1 transfer (faces), 2 divergence, 3 transform passes (all solves),
+ * 4 FP64 residuals, 5 gauge, 6 gradient and correction, 7 statistics. pc_profile_read waits for
+ * the recorded events, returns the milliseconds summed over the calls made since the last read
+ * (at most 256 calls are kept), the number of calls, and the number of kernels libpc launched
+ * in them; it then resets the counters. */
+typedef struct {
+  double phase_ms[8];
+  int calls;
+  long long kernel_launches;
+} pc_profile;
+
+pc_status pc_profile_enable(pc_plan *plan, int on);
+pc_status pc_profile_read(pc_plan *plan, pc_profile *out);
+
 /* Device bytes held by the plan. */
 pc_status pc_plan_bytes(const pc_plan *plan, size_t *bytes_out);
 

@@ -44,11 +44,32 @@ pc_status plan_alloc(Plan *p, void **ptr, size_t bytes) {
 
 bool axis_length_supported(int n);
 
+void prof_begin(Plan *p, cudaStream_t st) {
+  if (!p->prof || !p->slots) { p->cur = nullptr; return; }
+  if (p->slots_used >= kProfSlots) { p->cur = nullptr; return; }
+  p->cur = &p->slots[p->slots_used++];
+  p->cur->n = 1;
+  cudaEventRecord(p->cur->ev[0], st);
+}
+
+void prof_mark(Plan *p, cudaStream_t st, int tag) {
+  ProfSlot *s = p->cur;
+  if (!s || s->n >= kProfEvents) return;
+  s->tag[s->n - 1] = tag;
+  cudaEventRecord(s->ev[s->n], st);
+  s->n++;
+}
+
 static void destroy_plan(Plan *p) {
   if (!p) return;
   int cur = -1;
   cudaGetDevice(&cur);
   cudaSetDevice(p->device);
+  if (p->slots) {
+    for (int i = 0; i < kProfSlots; ++i)
+      for (int e = 0; e < kProfEvents; ++e) cudaEventDestroy(p->slots[i].ev[e]);
+    delete[] p->slots;
+  }
   for (int i = 0; i < p->nallocs; ++i) cudaFree(p->allocs[i]);
   if (cur >= 0) cudaSetDevice(cur);
   delete p;
@@ -248,6 +269,46 @@ extern "C" pc_status pc_plan_create(const pc_problem_desc *desc, int device, siz
 
 extern "C" pc_status pc_destroy(pc_plan *plan) {
   pc::destroy_plan(reinterpret_cast<pc::Plan *>(plan));
+  return PC_OK;
+}
+
+extern "C" pc_status pc_profile_enable(pc_plan *plan, int on) {
+  pc::Plan *p = reinterpret_cast<pc::Plan *>(plan);
+  if (!p) return pc::fail(PC_ERR_INVALID_ARG, "plan is NULL");
+  if (cudaSetDevice(p->device) != cudaSuccess) return pc::fail(PC_ERR_CUDA, "cannot select device");
+  if (on && !p->slots) {
+    p->slots = new pc::ProfSlot[pc::kProfSlots];
+    for (int i = 0; i < pc::kProfSlots; ++i)
+      for (int e = 0; e < pc::kProfEvents; ++e)
+        if (cudaEventCreate(&p->slots[i].ev[e]) != cudaSuccess)
+          return pc::fail(PC_ERR_CUDA, "cudaEventCreate failed");
+  }
+  p->prof = on != 0;
+  p->slots_used = 0;
+  p->launches = 0;
+  return PC_OK;
+}
+
+extern "C" pc_status pc_profile_read(pc_plan *plan, pc_profile *out) {
+  pc::Plan *p = reinterpret_cast<pc::Plan *>(plan);
+  if (!p || !out) return pc::fail(PC_ERR_INVALID_ARG, "plan and out are required");
+  memset(out, 0, sizeof(*out));
+  if (cudaSetDevice(p->device) != cudaSuccess) return pc::fail(PC_ERR_CUDA, "cannot select device");
+  for (int i = 0; i < p->slots_used; ++i) {
+    pc::ProfSlot &s = p->slots[i];
+    if (s.n < 2) continue;
+    PC_CUDA_TRY(cudaEventSynchronize(s.ev[s.n - 1]));
+    for (int e = 0; e + 1 < s.n; ++e) {
+      float ms = 0.f;
+      PC_CUDA_TRY(cudaEventElapsedTime(&ms, s.ev[e], s.ev[e + 1]));
+      int t = s.tag[e];
+      if (t >= 0 && t < 8) out->phase_ms[t] += ms;
+    }
+    out->calls++;
+  }
+  out->kernel_launches = p->launches;
+  p->slots_used = 0;
+  p->launches = 0;
   return PC_OK;
 }
 

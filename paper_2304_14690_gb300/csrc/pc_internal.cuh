@@ -52,6 +52,16 @@ struct DevStats {
   unsigned int pad;
 };
 
+// Per-call event record of the optional profiler: segment i (between events i and i+1) belongs
+// to phase tag[i].
+constexpr int kProfEvents = 48;
+constexpr int kProfSlots = 256;
+struct ProfSlot {
+  cudaEvent_t ev[kProfEvents];
+  int tag[kProfEvents];
+  int n = 0;
+};
+
 struct Plan {
   int device = 0;
   int dim = 2;
@@ -98,7 +108,19 @@ struct Plan {
   size_t bytes = 0;
   void *allocs[64];
   int nallocs = 0;
+  // profiler (off by default)
+  bool prof = false;
+  ProfSlot *slots = nullptr;
+  int slots_used = 0;
+  ProfSlot *cur = nullptr;
+  long long launches = 0;
 };
+
+// Profiler hooks (no-ops unless enabled): begin a call record, close the running segment as
+// phase `tag`, count kernel launches.
+void prof_begin(Plan *p, cudaStream_t st);
+void prof_mark(Plan *p, cudaStream_t st, int tag);
+inline void count_launch(Plan *p, int n = 1) { p->launches += n; }
 
 // ----------------------------------------------------------------------------- errors
 void set_error(const char *fmt, ...);

@@ -304,6 +304,7 @@ static pc_status launch_pass(Plan *p, int axis, bool fwd, bool div, bool inv, in
     attr_set[sizeof(Real) == 8] = true;
   }
   axis_pass<Real><<<(unsigned)tiles, threads, smem, st>>>(A);
+  count_launch(p);
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
 }

@@ -390,28 +390,41 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
   GridDev g = grid_dev(p);
   if (p->precision == PC_PREC_FP64) {
     PC_TRY(solve_fp64_grid(p, s64, pout, st));
+    prof_mark(p, st, 3);
   } else {
     int sweeps = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
     PC_TRY(solve_fp32_grid(p, SRC_F64_, s64, DST_F64_SET_, pout, st));
+    prof_mark(p, st, 3);
     for (int it = 0; it < sweeps; ++it) {
       float *r32 = reinterpret_cast<float *>(p->work64);   // work64 is free in mixed mode
       residual_kernel<<<grid_for(nc, T), T, 0, st>>>(g, nc, s64, pout, p->singular, r32, p->dstats,
                                                      &p->dstats->res2[it]);
+      count_launch(p);
+      prof_mark(p, st, 4);
       PC_TRY(solve_fp32_grid(p, SRC_F32_, r32, DST_F64_ADD_, pout, st));
+      prof_mark(p, st, 3);
     }
   }
   if (want_final_residual) {
     int it = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
     residual_kernel<<<grid_for(nc, T), T, 0, st>>>(g, nc, s64, pout, p->singular, nullptr, p->dstats,
                                                    &p->dstats->res2[it]);
+    count_launch(p);
+    prof_mark(p, st, 7);
   }
   // gauge (singular problems), then the FP32 split of p for the mixed gradient
   int gmode = p->singular ? (p->gauge == 1 ? 2 : 1) : 0;
-  if (gmode) gauge_sum_kernel<<<grid_for(nc, T), T, 0, st>>>(nc, pout, p->dstats);
+  if (gmode) {
+    gauge_sum_kernel<<<grid_for(nc, T), T, 0, st>>>(nc, pout, p->dstats);
+    count_launch(p);
+  }
   bool mixed = p->precision != PC_PREC_FP64;
-  if (gmode || mixed)
+  if (gmode || mixed) {
     finalize_p_kernel<<<grid_for(nc, T), T, 0, st>>>(nc, pout, gmode, p->dstats, mixed ? p->phi : nullptr,
                                                      mixed ? p->plo : nullptr);
+    count_launch(p);
+  }
+  prof_mark(p, st, 5);
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
 }
@@ -452,6 +465,7 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   if (huo) duo = p->stage_uo;
   if (f_out && hfo) dfo = p->stage_fo;
 
+  prof_begin(p, st);
   PC_CUDA_TRY(cudaMemsetAsync(p->dstats, 0, sizeof(DevStats), st));
   const int T = 256;
   const bool mixed = p->precision != PC_PREC_FP64;
@@ -464,6 +478,8 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
     prep_kernel<float><<<grid_for(cnt, T), T, 0, st>>>(cnt, (const float *)du, (const float *)df, dt,
                                                         mixed ? nullptr : p->ut64, mixed ? p->uhi : nullptr,
                                                         mixed ? p->ulo : nullptr, p->dstats);
+  count_launch(p);
+  prof_mark(p, st, 0);
   for (int a = 0; a < d; ++a) {
     long long rows = p->nface_total[a];
     if (mixed)
@@ -473,10 +489,14 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
     else
       transfer64_kernel<<<grid_for(rows, T), T, 0, st>>>(rows, p->K, p->fcol[a], p->fw64[a],
                                                          p->ut64 + (long long)a * N, p->U64[a]);
+    count_launch(p);
   }
+  prof_mark(p, st, 1);
   GridDev g = grid_dev(p);
   divergence_kernel<<<grid_for(nc, T), T, 0, st>>>(g, nc, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt),
                                                    p->s64, p->dstats);
+  count_launch(p);
+  prof_mark(p, st, 2);
   PC_CUDA_TRY(cudaGetLastError());
   PC_TRY(solve_grid(p, p->s64, dp, stats != nullptr, st));
   const void *ug = du;
@@ -497,9 +517,14 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
       else gradient64_kernel<float, 3><<<grid_for(N, T), T, 0, st>>>(N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, dt, p->beta, (float *)duo, (float *)dfo);
     }
   }
-  if (stats)
+  count_launch(p);
+  prof_mark(p, st, 6);
+  if (stats) {
     div_check_kernel<<<grid_for(nc, T), T, 0, st>>>(g, nc, p->U64[0], p->U64[1], p->U64[2], dp, p->beta * dt,
                                                     p->dstats);
+    count_launch(p);
+    prof_mark(p, st, 7);
+  }
   PC_CUDA_TRY(cudaGetLastError());
   if (hp) PC_CUDA_TRY(cudaMemcpyAsync(p_out, dp, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (huo) PC_CUDA_TRY(cudaMemcpyAsync(u_out, duo, vbytes, cudaMemcpyDeviceToHost, st));
@@ -516,8 +541,11 @@ static pc_status solve_impl(Plan *p, const double *s, double *p_out, pc_stats *s
   double *dp = p_out;
   if (hs) { PC_CUDA_TRY(cudaMemcpyAsync(p->stage_s, s, nc * sizeof(double), cudaMemcpyHostToDevice, st)); ds = p->stage_s; }
   if (hp) dp = p->stage_p;
+  prof_begin(p, st);
   PC_CUDA_TRY(cudaMemsetAsync(p->dstats, 0, sizeof(DevStats), st));
   sum_kernel<<<grid_for(nc, 256), 256, 0, st>>>(nc, ds, &p->dstats->sum_s, &p->dstats->sum_s2);
+  count_launch(p);
+  prof_mark(p, st, 2);
   PC_TRY(solve_grid(p, ds, dp, stats != nullptr, st));
   if (hp) PC_CUDA_TRY(cudaMemcpyAsync(p_out, dp, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (stats) PC_TRY(fill_stats(p, stats, st));

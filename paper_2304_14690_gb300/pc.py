@@ -73,6 +73,14 @@ class Stats(ctypes.Structure):
                     gauge_shift=self.gauge_shift)
 
 
+class Profile(ctypes.Structure):
+    _fields_ = [("phase_ms", ctypes.c_double * 8), ("calls", ctypes.c_int),
+                ("kernel_launches", ctypes.c_longlong)]
+
+
+PHASES = ("prep", "transfer", "divergence", "transform", "residual", "gauge", "gradient", "stats")
+
+
 class ProjectArgs(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("u_star", ctypes.c_void_p), ("f_ib_in", ctypes.c_void_p),
                 ("p_out", ctypes.c_void_p), ("u_out", ctypes.c_void_p), ("f_ib_out", ctypes.c_void_p)]
@@ -92,6 +100,8 @@ FUNCTIONS = {
                                     ctypes.c_void_p, ctypes.c_void_p]),
     "pc_plan_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "pc_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "pc_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "pc_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
     "pc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pc_last_error_message": (ctypes.c_char_p, []),
 }
@@ -211,6 +221,16 @@ class Plan:
         b = ctypes.c_size_t()
         _check(load().pc_plan_bytes(self.handle, ctypes.byref(b)))
         return b.value
+
+    def profile(self, on=True):
+        _check(load().pc_profile_enable(self.handle, 1 if on else 0))
+
+    def profile_read(self):
+        """Per-phase milliseconds summed over the calls since the last read, calls, launches."""
+        pr = Profile()
+        _check(load().pc_profile_read(self.handle, ctypes.byref(pr)))
+        return dict(phase_ms={PHASES[i]: pr.phase_ms[i] for i in range(8)}, calls=pr.calls,
+                    kernel_launches=pr.kernel_launches)
 
     def rows(self, which):
         """(col [rows, K] int32, w) of face axis `which` (w [rows, K]) or of the nodes
