@@ -175,6 +175,12 @@ typedef struct {
 pc_status pc_profile_enable(pc_plan *plan, int on);
 pc_status pc_profile_read(pc_plan *plan, pc_profile *out);
 
+/* CUDA graphs (on by default): a pc_project call with device pointers and no stats is
+ * captured once per distinct (pointers, dt) into a CUDA graph on a plan-private stream and then
+ * replayed with a single launch on the caller's stream (up to 4 argument sets are cached per
+ * plan). Results are identical with graphs on or off. */
+pc_status pc_set_graphs(pc_plan *plan, int on);
+
 /* Device bytes held by the plan. */
 pc_status pc_plan_bytes(const pc_plan *plan, size_t *bytes_out);
 

@@ -43,8 +43,14 @@ pc_status plan_alloc(Plan *p, void **ptr, size_t bytes) {
 }
 
 bool axis_length_supported(int n);
+pc_status prepare_kernels();
 
 void prof_begin(Plan *p, cudaStream_t st) {
+  if (p->capturing) {   // phase boundaries become event-record nodes of the graph
+    p->cap_n = 1;
+    cudaEventRecordWithFlags(p->cap_ev[0], st, cudaEventRecordExternal);
+    return;
+  }
   if (!p->prof || !p->slots) { p->cur = nullptr; return; }
   if (p->slots_used >= kProfSlots) { p->cur = nullptr; return; }
   p->cur = &p->slots[p->slots_used++];
@@ -53,6 +59,13 @@ void prof_begin(Plan *p, cudaStream_t st) {
 }
 
 void prof_mark(Plan *p, cudaStream_t st, int tag) {
+  if (p->capturing) {
+    if (p->cap_n >= kProfEvents) return;
+    p->cap_tag[p->cap_n - 1] = tag;
+    cudaEventRecordWithFlags(p->cap_ev[p->cap_n], st, cudaEventRecordExternal);
+    p->cap_n++;
+    return;
+  }
   ProfSlot *s = p->cur;
   if (!s || s->n >= kProfEvents) return;
   s->tag[s->n - 1] = tag;
@@ -70,6 +83,13 @@ static void destroy_plan(Plan *p) {
       for (int e = 0; e < kProfEvents; ++e) cudaEventDestroy(p->slots[i].ev[e]);
     delete[] p->slots;
   }
+  for (int i = 0; i < kGraphCache; ++i) {
+    if (p->graphs[i].exec) cudaGraphExecDestroy(p->graphs[i].exec);
+    if (p->graphs[i].graph) cudaGraphDestroy(p->graphs[i].graph);
+  }
+  if (p->cap_ev_made)
+    for (int e = 0; e < kProfEvents; ++e) cudaEventDestroy(p->cap_ev[e]);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   for (int i = 0; i < p->nallocs; ++i) cudaFree(p->allocs[i]);
   if (cur >= 0) cudaSetDevice(cur);
   delete p;
@@ -105,6 +125,14 @@ static bool host_ptr(const void *ptr) {
     return true;
   }
   return !(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+}
+
+// Two partial sums per block of the largest reduction launch (cell grid or flat grid).
+static size_t partial_slots(const Plan *p) {
+  const long long last = p->n[p->dim - 1];
+  const long long cells_launch = ((last + 255) / 256) * (p->ncells / last);
+  const long long flat_launch = (p->ncells + 255) / 256;
+  return (size_t)(2 * (cells_launch > flat_launch ? cells_launch : flat_launch) + 64);
 }
 
 static pc_status create(const pc_problem_desc *d, int device, size_t budget, cudaStream_t st, Plan **out) {
@@ -206,23 +234,22 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
     if (plan_alloc(p, (void **)&p->fcol[a], rows * K * 4) != PC_OK ||
         plan_alloc(p, (void **)&p->fw64[a], rows * K * 8) != PC_OK)
       return bail(PC_ERR_OUT_OF_MEMORY);
-    if (mixed && (plan_alloc(p, (void **)&p->fwhi[a], rows * K * 4) != PC_OK ||
-                  plan_alloc(p, (void **)&p->fwlo[a], rows * K * 4) != PC_OK))
-      return bail(PC_ERR_OUT_OF_MEMORY);
+    if (mixed && plan_alloc(p, (void **)&p->fw2[a], rows * K * 8) != PC_OK) return bail(PC_ERR_OUT_OF_MEMORY);
     if (plan_alloc(p, (void **)&p->U64[a], rows * 8) != PC_OK) return bail(PC_ERR_OUT_OF_MEMORY);
   }
   if (plan_alloc(p, (void **)&p->ncol, N * Kg * 4) != PC_OK || plan_alloc(p, (void **)&p->nD64, dd * N * Kg * 8) != PC_OK ||
       plan_alloc(p, (void **)&p->ntype, N) != PC_OK || plan_alloc(p, (void **)&p->s64, nc * 8) != PC_OK ||
       plan_alloc(p, (void **)&p->work64, nc * 8) != PC_OK || plan_alloc(p, (void **)&p->work32, nc * 4) != PC_OK ||
       plan_alloc(p, (void **)&p->dstats, sizeof(DevStats)) != PC_OK ||
+      plan_alloc(p, (void **)&p->partials, partial_slots(p) * sizeof(double)) != PC_OK ||
+      plan_alloc(p, (void **)&p->counters, 16 * sizeof(unsigned int)) != PC_OK ||
       plan_alloc(p, (void **)&p->stage_p, nc * 8) != PC_OK || plan_alloc(p, (void **)&p->stage_s, nc * 8) != PC_OK ||
       plan_alloc(p, &p->stage_u, dd * N * vsz) != PC_OK || plan_alloc(p, &p->stage_f, dd * N * vsz) != PC_OK ||
       plan_alloc(p, &p->stage_uo, dd * N * vsz) != PC_OK || plan_alloc(p, &p->stage_fo, dd * N * vsz) != PC_OK)
     return bail(PC_ERR_OUT_OF_MEMORY);
   if (mixed) {
-    if (plan_alloc(p, (void **)&p->nDhi, dd * N * Kg * 4) != PC_OK || plan_alloc(p, (void **)&p->nDlo, dd * N * Kg * 4) != PC_OK ||
-        plan_alloc(p, (void **)&p->phi, nc * 4) != PC_OK || plan_alloc(p, (void **)&p->plo, nc * 4) != PC_OK ||
-        plan_alloc(p, (void **)&p->uhi, dd * N * 4) != PC_OK || plan_alloc(p, (void **)&p->ulo, dd * N * 4) != PC_OK)
+    if (plan_alloc(p, (void **)&p->nD2, dd * N * Kg * 8) != PC_OK || plan_alloc(p, (void **)&p->p2, nc * 8) != PC_OK ||
+        plan_alloc(p, (void **)&p->u2, dd * N * 8) != PC_OK)
       return bail(PC_ERR_OUT_OF_MEMORY);
   } else {
     if (plan_alloc(p, (void **)&p->ut64, dd * N * 8) != PC_OK) return bail(PC_ERR_OUT_OF_MEMORY);
@@ -249,6 +276,14 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
     if (hb & 1u) return bail(fail(PC_ERR_INVALID_ARG, "a node lies outside the domain or is not finite"));
     if (hb & 2u) return bail(fail(PC_ERR_INVALID_ARG, "node_type values must be 0, 1 or 2"));
   }
+  if (cudaMemsetAsync(p->counters, 0, 16 * sizeof(unsigned int), st) != cudaSuccess)
+    return bail(fail(PC_ERR_CUDA, "counter reset failed"));
+  if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(PC_ERR_CUDA, "stream creation failed"));
+  for (int e = 0; e < kProfEvents; ++e)
+    if (cudaEventCreate(&p->cap_ev[e]) != cudaSuccess) return bail(fail(PC_ERR_CUDA, "event creation failed"));
+  p->cap_ev_made = true;
+  if (prepare_kernels() != PC_OK) return bail(PC_ERR_CUDA);
   pc_status s = build_axis_tables(p);
   if (s != PC_OK) return bail(s);
   s = build_rows(p, xyz_dev, st);
@@ -309,6 +344,13 @@ extern "C" pc_status pc_profile_read(pc_plan *plan, pc_profile *out) {
   out->kernel_launches = p->launches;
   p->slots_used = 0;
   p->launches = 0;
+  return PC_OK;
+}
+
+extern "C" pc_status pc_set_graphs(pc_plan *plan, int on) {
+  pc::Plan *p = reinterpret_cast<pc::Plan *>(plan);
+  if (!p) return pc::fail(PC_ERR_INVALID_ARG, "plan is NULL");
+  p->graphs_on = on != 0;
   return PC_OK;
 }
 

@@ -1,7 +1,13 @@
 // Shared-memory transforms for the Poisson solve (§2.3 three-step algorithm).
 //
 // A CTA holds a tile of L lines of one axis in shared memory as complex slots: line l,
-// slot q at buf[l*ls + q*es] (row tiles: es = 1, ls = M + pad; column tiles: es = L, ls = 1).
+// slot q at buf[l*ls + q*es] (row tiles: es = 1, ls = M; column tiles: es = L, ls = 1).
+// Every thread works on one line of the tile: column tiles map consecutive threads to
+// consecutive lines (coalesced global access across adjacent lines), row tiles map them to
+// consecutive positions of one line. A thread covers the positions lane, lane + tpl, ... of its
+// line, tpl = threads per line (a power of two, >= M/2), so all index arithmetic is shifts,
+// masks and one multiply-high per FFT stage.
+//
 // Every real-to-real transform of length n (n even) runs through one complex FFT of length
 // M = n/2:
 //   periodic    real DFT, packed output [X0, X_{n/2}, Re X1, Im X1, Re X2, ...]
@@ -39,17 +45,31 @@ template <typename T> __device__ __forceinline__ T cscale(T a, decltype(T::x) s)
 // multiply by -i (forward) or +i (inverse)
 template <typename T> __device__ __forceinline__ T cmul_mi(T a) { return cmk<T>(a.y, -a.x); }
 template <typename T> __device__ __forceinline__ T cmul_pi(T a) { return cmk<T>(-a.y, a.x); }
+template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
 
+// Thread-to-tile map: this thread's line and its first position; tpl threads per line.
 struct TileGeom {
-  int L;   // lines in the tile
-  int M;   // complex slots per line
-  int ls;  // slot stride between lines
-  int es;  // slot stride along a line
-  bool line_fastest;  // thread mapping: consecutive threads walk lines (column tiles)
+  int L;     // lines in the tile
+  int M;     // complex slots per line
+  int ls;    // slot stride between lines
+  int es;    // slot stride along a line
+  int line;  // line of this thread
+  int lane;  // first position of this thread on its line
+  int tpl;   // threads per line (position stride)
+};
+
+// Work items a thread keeps in registers across a barrier are bounded by tpl >= M/2: every
+// FFT stage is one butterfly per thread.
+constexpr int kSlotsPerThread = 2;
+
+// One FFT stage: radix R, current span Ns, twiddle stride M/(Ns R). j / Ns is a shift when Ns
+// is a power of two, else a multiply-high by magic = ceil(2^32/Ns) (exact for j < 2^16).
+struct StageInfo {
+  int R, Ns, stride_m, shift;   // shift < 0: use magic
+  unsigned magic;
 };
 
 // Table offsets inside one axis twiddle buffer (see AxisInfo).
-__host__ __device__ inline int tw_fft(int) { return 0; }
 __host__ __device__ inline int tw_rdft(int M) { return M; }            // e^{-2 pi i k/n}, k=0..M
 __host__ __device__ inline int tw_quarter(int M) { return 2 * M + 1; }  // e^{-i pi k/(2n)}, k=0..M
 __host__ __device__ inline int tw_dct4pre(int M) { return 3 * M + 2; }  // e^{-i pi (4p+1)/(4n)}, p<M
@@ -64,12 +84,6 @@ template <typename T>
 __device__ __forceinline__ decltype(T::x) &realref(T *buf, const TileGeom &g, int line, int j) {
   using R = decltype(T::x);
   return reinterpret_cast<R *>(buf)[2 * (line * g.ls + (j >> 1) * g.es) + (j & 1)];
-}
-
-// Decode work item t into (line, j) for j in [0, per_line).
-__device__ __forceinline__ void decode(const TileGeom &g, int t, int per_line, int &line, int &j) {
-  if (g.line_fastest) { line = t % g.L; j = t / g.L; }
-  else { j = t % per_line; line = t / per_line; }
 }
 
 // Small DFT of radix R on v[0..R-1] (forward sign -1, inverse +1). Radix 3 and 5 take their
@@ -98,7 +112,7 @@ __device__ __forceinline__ void small_dft(T *v, const T *tw, int M, bool inv) {
       T acc = in[0];
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        T w = tw[((q * r) % R) * step];
+        T w = ldg(&tw[((q * r) % R) * step]);
         acc = cadd(acc, inv ? cmulc(in[r], w) : cmul(in[r], w));
       }
       v[q] = acc;
@@ -108,72 +122,61 @@ __device__ __forceinline__ void small_dft(T *v, const T *tw, int M, bool inv) {
 
 // One Stockham stage of radix R over every line of the tile (all threads of the CTA).
 template <typename T, int R, int MAXB>
-__device__ void fft_stage(T *buf, const TileGeom &g, int Ns, const T *tw, bool inv) {
+__device__ void fft_stage(T *buf, const TileGeom &g, const StageInfo &s, const T *tw, bool inv) {
   const int NBl = g.M / R;
-  const int NB = NBl * g.L;
-  const int stride_m = g.M / (Ns * R);
   T v[MAXB][R];
 #pragma unroll
   for (int b = 0; b < MAXB; ++b) {
-    int t = threadIdx.x + b * blockDim.x;
-    if (t < NB) {
-      int line, j;
-      decode(g, t, NBl, line, j);
+    int j = g.lane + b * g.tpl;
+    if (j < NBl) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b][r] = slot(buf, g, line, j + r * NBl);
+      for (int r = 0; r < R; ++r) v[b][r] = slot(buf, g, g.line, j + r * NBl);
     }
   }
   __syncthreads();
 #pragma unroll
   for (int b = 0; b < MAXB; ++b) {
-    int t = threadIdx.x + b * blockDim.x;
-    if (t < NB) {
-      int line, j;
-      decode(g, t, NBl, line, j);
-      int k = j % Ns;
+    int j = g.lane + b * g.tpl;
+    if (j < NBl) {
+      int q = s.shift >= 0 ? (j >> s.shift) : (int)__umulhi((unsigned)j, s.magic);
+      int k = j - q * s.Ns;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        T w = tw[r * k * stride_m];
+        T w = ldg(&tw[r * k * s.stride_m]);
         v[b][r] = inv ? cmulc(v[b][r], w) : cmul(v[b][r], w);
       }
       small_dft<T, R>(v[b], tw, g.M, inv);
-      int base = (j / Ns) * Ns * R + k;
+      int base = q * s.Ns * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) slot(buf, g, line, base + r * Ns) = v[b][r];
+      for (int r = 0; r < R; ++r) slot(buf, g, g.line, base + r * s.Ns) = v[b][r];
     }
   }
   __syncthreads();
 }
 
-// Every routine of this file requires blockDim.x * kSlotsPerThread >= L * M: that bounds the
-// work items a thread keeps in registers across a barrier.
-constexpr int kSlotsPerThread = 4;
-
 // Complex FFT of length g.M on every line (unnormalised).
 template <typename T>
-__device__ void fft_lines(T *buf, const TileGeom &g, const int *radix, int nradix, const T *tw,
+__device__ void fft_lines(T *buf, const TileGeom &g, const StageInfo *st, int nst, const T *tw,
                           bool inv) {
-  int Ns = 1;
-  for (int s = 0; s < nradix; ++s) {
-    int R = radix[s];
-    if (R == 4) fft_stage<T, 4, 1>(buf, g, Ns, tw, inv);
-    else if (R == 2) fft_stage<T, 2, 2>(buf, g, Ns, tw, inv);
-    else if (R == 3) fft_stage<T, 3, 2>(buf, g, Ns, tw, inv);
-    else fft_stage<T, 5, 1>(buf, g, Ns, tw, inv);
-    Ns *= R;
+  for (int s = 0; s < nst; ++s) {
+    const StageInfo si = st[s];
+    if (si.R == 4) fft_stage<T, 4, 1>(buf, g, si, tw, inv);
+    else if (si.R == 2) fft_stage<T, 2, 1>(buf, g, si, tw, inv);
+    else if (si.R == 3) fft_stage<T, 3, 1>(buf, g, si, tw, inv);
+    else fft_stage<T, 5, 1>(buf, g, si, tw, inv);
   }
 }
 
 // ----------------------------------------------------------------------------- forward
-// Where real input x_j goes among the complex slots before the FFT (F1). Returns the slot,
-// the component (0 real, 1 imaginary) and the sign.
-__device__ __forceinline__ void fwd_slot_of(int kind, int n, int j, int &q, int &comp, float &sgn) {
-  sgn = 1.f;
+// Where real input x_j goes among the complex slots before the FFT (F1): slot, component
+// (0 real, 1 imaginary) and sign.
+__device__ __forceinline__ void fwd_slot_of(int kind, int n, int j, int &q, int &comp, bool &neg) {
+  neg = false;
   if (kind == KIND_PP) { q = j >> 1; comp = j & 1; return; }
   if (kind == KIND_NN || kind == KIND_DD) {
     int v = (j & 1) ? (n - 1 - (j >> 1)) : (j >> 1);   // Makhoul reorder
     q = v >> 1; comp = v & 1;
-    if (kind == KIND_DD && (j & 1)) sgn = -1.f;         // (-1)^j
+    neg = (kind == KIND_DD) && (j & 1);                 // (-1)^j
     return;
   }
   // DCT-IV / DST-IV: z_p = (a + i b) with (a, b) = (x_2p, x_{n-1-2p}) or swapped for DST-IV
@@ -188,11 +191,9 @@ template <typename T>
 __device__ void pretwiddle(T *buf, const TileGeom &g, int kind, const T *tw) {
   if (kind != KIND_ND && kind != KIND_DN) return;
   const T *t4 = tw + tw_dct4pre(g.M);
-  for (int t = threadIdx.x; t < g.L * g.M; t += blockDim.x) {
-    int line, q;
-    decode(g, t, g.M, line, q);
-    T &z = slot(buf, g, line, q);
-    z = cmul(z, t4[q]);
+  for (int q = g.lane; q < g.M; q += g.tpl) {
+    T &z = slot(buf, g, g.line, q);
+    z = cmul(z, ldg(&t4[q]));
   }
   __syncthreads();
 }
@@ -202,6 +203,7 @@ template <typename T>
 __device__ void fwd_post(T *buf, const TileGeom &g, int kind, int n, const T *tw) {
   using R = decltype(T::x);
   const int M = g.M;
+  const int line = g.line;
   if (kind == KIND_ND || kind == KIND_DN) {
     // y_q = e^{-i pi q/n} Z_q; X_2q = Re y_q; X_{n-1-2q} = -Im y_q (DCT-IV), +Im y_q (DST-IV)
     const T *tp = tw + tw_dct4post(M);
@@ -209,18 +211,14 @@ __device__ void fwd_post(T *buf, const TileGeom &g, int kind, int n, const T *tw
     T y[MAXI];
 #pragma unroll
     for (int b = 0; b < MAXI; ++b) {
-      int t = threadIdx.x + b * blockDim.x;
-      if (t < g.L * M) {
-        int line, q; decode(g, t, M, line, q);
-        y[b] = cmul(slot(buf, g, line, q), tp[q]);
-      }
+      int q = g.lane + b * g.tpl;
+      if (q < M) y[b] = cmul(slot(buf, g, line, q), ldg(&tp[q]));
     }
     __syncthreads();
 #pragma unroll
     for (int b = 0; b < MAXI; ++b) {
-      int t = threadIdx.x + b * blockDim.x;
-      if (t < g.L * M) {
-        int line, q; decode(g, t, M, line, q);
+      int q = g.lane + b * g.tpl;
+      if (q < M) {
         realref(buf, g, line, 2 * q) = y[b].x;
         realref(buf, g, line, n - 1 - 2 * q) = (kind == KIND_ND) ? -y[b].y : y[b].y;
       }
@@ -229,11 +227,10 @@ __device__ void fwd_post(T *buf, const TileGeom &g, int kind, int n, const T *tw
     return;
   }
   // Real DFT of the (reordered) line from the half-length FFT: pairs (k, M-k), k <= M/2.
-  const int P = M / 2 + 1;          // pairs per line
+  const int P = M / 2 + 1;
   const T *w1 = tw + tw_rdft(M);
   if (kind == KIND_PP) {
-    for (int t = threadIdx.x; t < g.L * P; t += blockDim.x) {
-      int line, k; decode(g, t, P, line, k);
+    for (int k = g.lane; k < P; k += g.tpl) {
       if (k == 0) {
         T z = slot(buf, g, line, 0);
         slot(buf, g, line, 0) = cmk<T>(z.x + z.y, z.x - z.y);
@@ -243,10 +240,10 @@ __device__ void fwd_post(T *buf, const TileGeom &g, int kind, int n, const T *tw
       T zk = slot(buf, g, line, k), zm = slot(buf, g, line, km);
       // X_k = E + w^k O,  E = (Zk + conj Zm)/2,  O = -i (Zk - conj Zm)/2
       T E = cscale(cadd(zk, cconj(zm)), (R)0.5), O = cscale(cmul_mi(csub(zk, cconj(zm))), (R)0.5);
-      T Xk = cadd(E, cmul(O, w1[k]));
+      T Xk = cadd(E, cmul(O, ldg(&w1[k])));
       if (km != k) {
         T E2 = cscale(cadd(zm, cconj(zk)), (R)0.5), O2 = cscale(cmul_mi(csub(zm, cconj(zk))), (R)0.5);
-        slot(buf, g, line, km) = cadd(E2, cmul(O2, w1[km]));
+        slot(buf, g, line, km) = cadd(E2, cmul(O2, ldg(&w1[km])));
       }
       slot(buf, g, line, k) = Xk;
     }
@@ -256,34 +253,33 @@ __device__ void fwd_post(T *buf, const TileGeom &g, int kind, int n, const T *tw
   // DCT-II (and DST-II by reversal): V = real DFT of v; t_k = e^{-i pi k/(2n)} V_k;
   // X_k = Re t_k, X_{n-k} = -Im t_k.
   const T *wq = tw + tw_quarter(M);
-  constexpr int MAXP = kSlotsPerThread / 2 + 1;   // L*(M/2+1) pairs
+  constexpr int MAXP = kSlotsPerThread / 2 + 1;
   R out[MAXP][4];
   int pos[MAXP][4];
 #pragma unroll
   for (int b = 0; b < MAXP; ++b) {
-    int t = threadIdx.x + b * blockDim.x;
+    int k = g.lane + b * g.tpl;
 #pragma unroll
     for (int c = 0; c < 4; ++c) pos[b][c] = -1;
-    if (t < g.L * P) {
-      int line, k; decode(g, t, P, line, k);
+    if (k < P) {
       if (k == 0) {
         T z = slot(buf, g, line, 0);
         R V0 = z.x + z.y, VM = z.x - z.y;
-        T tM = cscale(wq[M], VM);
+        T tM = cscale(ldg(&wq[M]), VM);
         out[b][0] = V0; pos[b][0] = 0;
         out[b][1] = tM.x; pos[b][1] = M;
       } else {
         int km = M - k;
         T zk = slot(buf, g, line, k), zm = slot(buf, g, line, km);
         T E = cscale(cadd(zk, cconj(zm)), (R)0.5), O = cscale(cmul_mi(csub(zk, cconj(zm))), (R)0.5);
-        T Vk = cadd(E, cmul(O, w1[k]));
-        T tk = cmul(Vk, wq[k]);
+        T Vk = cadd(E, cmul(O, ldg(&w1[k])));
+        T tk = cmul(Vk, ldg(&wq[k]));
         out[b][0] = tk.x; pos[b][0] = k;
         out[b][1] = -tk.y; pos[b][1] = n - k;
         if (km != k) {
           T E2 = cscale(cadd(zm, cconj(zk)), (R)0.5), O2 = cscale(cmul_mi(csub(zm, cconj(zk))), (R)0.5);
-          T Vm = cadd(E2, cmul(O2, w1[km]));
-          T tm = cmul(Vm, wq[km]);
+          T Vm = cadd(E2, cmul(O2, ldg(&w1[km])));
+          T tm = cmul(Vm, ldg(&wq[km]));
           out[b][2] = tm.x; pos[b][2] = km;
           out[b][3] = -tm.y; pos[b][3] = n - km;
         }
@@ -293,16 +289,12 @@ __device__ void fwd_post(T *buf, const TileGeom &g, int kind, int n, const T *tw
   __syncthreads();
 #pragma unroll
   for (int b = 0; b < MAXP; ++b) {
-    int t = threadIdx.x + b * blockDim.x;
-    if (t < g.L * P) {
-      int line, k; decode(g, t, P, line, k);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (pos[b][c] >= 0) {
-          int i = pos[b][c];
-          if (kind == KIND_DD) i = n - 1 - i;
-          realref(buf, g, line, i) = out[b][c];
-        }
+    for (int c = 0; c < 4; ++c) {
+      if (pos[b][c] >= 0) {
+        int i = pos[b][c];
+        if (kind == KIND_DD) i = n - 1 - i;
+        realref(buf, g, line, i) = out[b][c];
       }
     }
   }
@@ -315,15 +307,15 @@ template <typename T>
 __device__ void inv_pre(T *buf, const TileGeom &g, int kind, int n, const T *tw) {
   using R = decltype(T::x);
   const int M = g.M;
+  const int line = g.line;
   if (kind == KIND_ND || kind == KIND_DN) {
     // The inverse of DCT-IV/DST-IV is the same transform times 2/n: same pre-processing.
     constexpr int MAXI = kSlotsPerThread;
     R a[MAXI], bb[MAXI];
 #pragma unroll
     for (int b = 0; b < MAXI; ++b) {
-      int t = threadIdx.x + b * blockDim.x;
-      if (t < g.L * M) {
-        int line, q; decode(g, t, M, line, q);
+      int q = g.lane + b * g.tpl;
+      if (q < M) {
         R x0 = realref(buf, g, line, 2 * q), x1 = realref(buf, g, line, n - 1 - 2 * q);
         a[b] = (kind == KIND_ND) ? x0 : x1;
         bb[b] = (kind == KIND_ND) ? x1 : x0;
@@ -333,11 +325,8 @@ __device__ void inv_pre(T *buf, const TileGeom &g, int kind, int n, const T *tw)
     const T *t4 = tw + tw_dct4pre(M);
 #pragma unroll
     for (int b = 0; b < MAXI; ++b) {
-      int t = threadIdx.x + b * blockDim.x;
-      if (t < g.L * M) {
-        int line, q; decode(g, t, M, line, q);
-        slot(buf, g, line, q) = cmul(cmk<T>(a[b], bb[b]), t4[q]);
-      }
+      int q = g.lane + b * g.tpl;
+      if (q < M) slot(buf, g, line, q) = cmul(cmk<T>(a[b], bb[b]), ldg(&t4[q]));
     }
     __syncthreads();
     return;
@@ -345,8 +334,7 @@ __device__ void inv_pre(T *buf, const TileGeom &g, int kind, int n, const T *tw)
   const int P = M / 2 + 1;
   const T *w1 = tw + tw_rdft(M);
   if (kind == KIND_PP) {
-    for (int t = threadIdx.x; t < g.L * P; t += blockDim.x) {
-      int line, k; decode(g, t, P, line, k);
+    for (int k = g.lane; k < P; k += g.tpl) {
       if (k == 0) {
         T z = slot(buf, g, line, 0);   // (X_0, X_M), both real
         R E = (R)0.5 * (z.x + z.y), O = (R)0.5 * (z.x - z.y);
@@ -357,11 +345,11 @@ __device__ void inv_pre(T *buf, const TileGeom &g, int kind, int n, const T *tw)
       T xk = slot(buf, g, line, k), xm = slot(buf, g, line, km);
       // Z_k = E + i O, E = (X_k + conj X_{M-k})/2, O = (X_k - conj X_{M-k}) conj(w^k)/2
       T E = cscale(cadd(xk, cconj(xm)), (R)0.5);
-      T O = cscale(cmulc(csub(xk, cconj(xm)), w1[k]), (R)0.5);
+      T O = cscale(cmulc(csub(xk, cconj(xm)), ldg(&w1[k])), (R)0.5);
       T Zk = cadd(E, cmul_pi(O));
       if (km != k) {
         T E2 = cscale(cadd(xm, cconj(xk)), (R)0.5);
-        T O2 = cscale(cmulc(csub(xm, cconj(xk)), w1[km]), (R)0.5);
+        T O2 = cscale(cmulc(csub(xm, cconj(xk)), ldg(&w1[km])), (R)0.5);
         slot(buf, g, line, km) = cadd(E2, cmul_pi(O2));
       }
       slot(buf, g, line, k) = Zk;
@@ -372,20 +360,17 @@ __device__ void inv_pre(T *buf, const TileGeom &g, int kind, int n, const T *tw)
   // DCT-III (DST-III through the reversal Y_i = X_{n-1-i}):
   // V_k = e^{+i pi k/(2n)} (X_k - i X_{n-k}) with X_n = 0, then the inverse real DFT wrapper.
   const T *wq = tw + tw_quarter(M);
-  constexpr int MAXP = kSlotsPerThread / 2 + 1;   // L*(M/2+1) pairs
+  constexpr int MAXP = kSlotsPerThread / 2 + 1;
   T zo[MAXP][2];
 #pragma unroll
   for (int b = 0; b < MAXP; ++b) {
-    int t = threadIdx.x + b * blockDim.x;
-    if (t < g.L * P) {
-      int line, k; decode(g, t, P, line, k);
+    int k = g.lane + b * g.tpl;
+    if (k < P) {
       auto X = [&](int i) -> R {
         if (i >= n) return (R)0;
         return realref(buf, g, line, kind == KIND_DD ? n - 1 - i : i);
       };
-      auto V = [&](int i) -> T {
-        return cmulc(cmk<T>(X(i), -X(n - i)), wq[i]);
-      };
+      auto V = [&](int i) -> T { return cmulc(cmk<T>(X(i), -X(n - i)), ldg(&wq[i])); };
       if (k == 0) {
         R V0 = X(0);
         R VM = V(M).x;   // real: sqrt(2) X_M
@@ -394,11 +379,11 @@ __device__ void inv_pre(T *buf, const TileGeom &g, int kind, int n, const T *tw)
         int km = M - k;
         T vk = V(k), vm = V(km);
         T E = cscale(cadd(vk, cconj(vm)), (R)0.5);
-        T O = cscale(cmulc(csub(vk, cconj(vm)), w1[k]), (R)0.5);
+        T O = cscale(cmulc(csub(vk, cconj(vm)), ldg(&w1[k])), (R)0.5);
         zo[b][0] = cadd(E, cmul_pi(O));
         if (km != k) {
           T E2 = cscale(cadd(vm, cconj(vk)), (R)0.5);
-          T O2 = cscale(cmulc(csub(vm, cconj(vk)), w1[km]), (R)0.5);
+          T O2 = cscale(cmulc(csub(vm, cconj(vk)), ldg(&w1[km])), (R)0.5);
           zo[b][1] = cadd(E2, cmul_pi(O2));
         }
       }
@@ -407,9 +392,8 @@ __device__ void inv_pre(T *buf, const TileGeom &g, int kind, int n, const T *tw)
   __syncthreads();
 #pragma unroll
   for (int b = 0; b < MAXP; ++b) {
-    int t = threadIdx.x + b * blockDim.x;
-    if (t < g.L * P) {
-      int line, k; decode(g, t, P, line, k);
+    int k = g.lane + b * g.tpl;
+    if (k < P) {
       slot(buf, g, line, k) = zo[b][0];
       int km = M - k;
       if (k != 0 && km != k) slot(buf, g, line, km) = zo[b][1];
@@ -423,29 +407,28 @@ template <typename T>
 __device__ void inv_post_twiddle(T *buf, const TileGeom &g, int kind, const T *tw) {
   if (kind != KIND_ND && kind != KIND_DN) return;
   const T *tp = tw + tw_dct4post(g.M);
-  for (int t = threadIdx.x; t < g.L * g.M; t += blockDim.x) {
-    int line, q; decode(g, t, g.M, line, q);
-    T &z = slot(buf, g, line, q);
-    z = cmul(z, tp[q]);
+  for (int q = g.lane; q < g.M; q += g.tpl) {
+    T &z = slot(buf, g, g.line, q);
+    z = cmul(z, ldg(&tp[q]));
   }
   __syncthreads();
 }
 
 // I3 (part 2): where output x_i is read from after the inverse FFT, with sign; the caller
 // multiplies by inv_scale(kind, n).
-__device__ __forceinline__ void inv_src_of(int kind, int n, int i, int &j, float &sgn) {
-  sgn = 1.f;
+__device__ __forceinline__ void inv_src_of(int kind, int n, int i, int &j, bool &neg) {
+  neg = false;
   if (kind == KIND_PP) { j = i; return; }
   if (kind == KIND_NN || kind == KIND_DD) {
     j = (i & 1) ? (n - 1 - (i >> 1)) : (i >> 1);
-    if (kind == KIND_DD && (i & 1)) sgn = -1.f;
+    neg = (kind == KIND_DD) && (i & 1);
     return;
   }
   // DCT-IV / DST-IV: x_2q = Re y_q, x_{n-1-2q} = -+Im y_q  (real index 2q / 2q+1 of slot q)
   if ((i & 1) == 0) { j = i; return; }
   int q = (n - 1 - i) >> 1;
   j = 2 * q + 1;
-  if (kind == KIND_ND) sgn = -1.f;
+  neg = (kind == KIND_ND);
 }
 
 // Normalisation of every inverse: 1/M of the half-length inverse FFT for the real DFT and

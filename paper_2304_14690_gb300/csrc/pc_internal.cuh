@@ -48,6 +48,8 @@ struct DevStats {
   double corner_p;
   double max_div;
   double max_u;
+  double mean_s;           // sum_s / ncells, written by the reducing block
+  double shift;            // gauge constant, written by the reducing block
   unsigned int flags;
   unsigned int pad;
 };
@@ -60,6 +62,22 @@ struct ProfSlot {
   cudaEvent_t ev[kProfEvents];
   int tag[kProfEvents];
   int n = 0;
+};
+
+// One instantiated CUDA graph of a pc_project call, keyed by its arguments. Its event-record
+// nodes (phase boundaries) are re-pointed to a profiler slot's events when profiling is on.
+constexpr int kGraphCache = 4;
+struct GraphEntry {
+  const void *u = nullptr, *f = nullptr;
+  void *p = nullptr, *uo = nullptr, *fo = nullptr;
+  double dt = 0.0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int nev = 0;
+  cudaGraphNode_t evnode[kProfEvents];
+  int tag[kProfEvents];
+  long long launches = 0;
+  unsigned long long stamp = 0;
 };
 
 struct Plan {
@@ -85,11 +103,10 @@ struct Plan {
   // WLS rows, neighbour-rank major: entry k of row r at k*rows + r.
   int32_t *fcol[3] = {nullptr, nullptr, nullptr};
   double *fw64[3] = {nullptr, nullptr, nullptr};
-  float *fwhi[3] = {nullptr, nullptr, nullptr};
-  float *fwlo[3] = {nullptr, nullptr, nullptr};
+  float2 *fw2[3] = {nullptr, nullptr, nullptr};   // (hi, lo) FP32 split of fw64 (mixed)
   int32_t *ncol = nullptr;     // [Kg][N] cell linear index
   double *nD64 = nullptr;      // [dim][Kg][N]
-  float *nDhi = nullptr, *nDlo = nullptr;
+  float2 *nD2 = nullptr;       // (hi, lo) FP32 split of nD64 (mixed)
   uint8_t *ntype = nullptr;    // [N]
 
   // Workspace (allocated once; pc_project allocates nothing).
@@ -98,16 +115,28 @@ struct Plan {
   double *p64 = nullptr;       // pressure (refined iterate)
   double *work64 = nullptr;    // FP64 transform workspace (cells)
   float *work32 = nullptr;     // FP32 transform workspace (cells)
-  float *phi = nullptr, *plo = nullptr;   // split pressure for the compensated gradient
-  float *uhi = nullptr, *ulo = nullptr;   // split u~ = u* + dt f for the compensated transfer
+  float2 *p2 = nullptr;                   // split pressure for the compensated gradient
+  float2 *u2 = nullptr;                   // split u~ = u* + dt f for the compensated transfer
   double *ut64 = nullptr;                 // u~ in FP64 (FP64 path)
   DevStats *dstats = nullptr;
+  double *partials = nullptr;      // per-block partial sums of the deterministic reductions
+  unsigned int *counters = nullptr;  // completion counters of those reductions (kept at zero)
   // Staging for host pointers passed to pc_project.
   void *stage_u = nullptr, *stage_f = nullptr, *stage_uo = nullptr, *stage_fo = nullptr;
   double *stage_p = nullptr, *stage_s = nullptr;
   size_t bytes = 0;
   void *allocs[64];
   int nallocs = 0;
+  // CUDA graphs of pc_project (on by default for device pointers without statistics)
+  bool graphs_on = true;
+  cudaStream_t cap_stream = nullptr;
+  GraphEntry graphs[kGraphCache];
+  unsigned long long graph_clock = 0;
+  bool capturing = false;
+  cudaEvent_t cap_ev[kProfEvents];
+  int cap_tag[kProfEvents];
+  int cap_n = 0;
+  bool cap_ev_made = false;
   // profiler (off by default)
   bool prof = false;
   ProfSlot *slots = nullptr;

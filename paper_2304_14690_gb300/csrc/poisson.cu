@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "fft.cuh"
+#include "numeric.cuh"
 #include "pc_internal.cuh"
 
 namespace pc {
@@ -26,15 +27,17 @@ enum DstMode { DST_WORK = 0, DST_F64_SET = 1, DST_F64_ADD = 2 };
 template <typename Real>
 struct PassArgs {
   using T = typename Cplx<Real>::T;
-  int axis, kind, n, M, nradix;
-  int radix[kMaxRadices];
+  int axis, kind, n, M, nst;
+  StageInfo st[kMaxRadices];
   const T *tw;
   int dim;
   int shape[3];
-  long long stride;     // element stride along the axis
-  long long inner;      // column tiles: number of line positions f (= stride)
-  long long lines;      // row tiles: number of lines
-  int L;                // lines per tile
+  int stride;           // element stride along the axis
+  int inner;            // column tiles: number of line positions f (= stride)
+  int lines;            // row tiles: number of lines
+  int L;                // lines per tile (power of two)
+  int lbits;            // log2(L)
+  int tpl_bits;         // log2(threads per line)
   int col;              // 1: column tile
   int tiles_per_outer;  // column tiles: ceil(inner / L)
   int do_fwd, do_div, do_inv;
@@ -47,123 +50,155 @@ struct PassArgs {
   Real out_scale;       // normalisation of the inverse (2/n)
 };
 
-template <typename Real>
-__device__ __forceinline__ long long line_base(const PassArgs<Real> &A, int tile, int l, bool &valid) {
-  if (A.col) {
-    long long o = tile / A.tiles_per_outer;
-    long long f = (long long)(tile % A.tiles_per_outer) * A.L + l;
-    valid = f < A.inner;
-    return o * (long long)A.n * A.stride + f;
-  }
-  long long line = (long long)tile * A.L + l;
-  valid = line < A.lines;
-  return line * A.n;
-}
+// Source element gi in the pass precision (FP64 sources enter FP32 passes truncated to 24 bits,
+// by integer operations; the refinement corrects what that drops).
+__device__ __forceinline__ float to_real(double v, float *) { return d2f_rz_bits(v); }
+__device__ __forceinline__ double to_real(double v, double *) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return f2d_bits(v); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
 
 template <typename Real>
-__device__ __forceinline__ Real load_src(const PassArgs<Real> &A, long long gi) {
-  if (A.src_mode == SRC_F32) return (Real)static_cast<const float *>(A.src)[gi];
-  if (A.src_mode == SRC_F64) return (Real)static_cast<const double *>(A.src)[gi];
+__device__ __forceinline__ Real load_src(const PassArgs<Real> &A, int gi) {
+  if (A.src_mode == SRC_F32) return (Real)__ldg(static_cast<const float *>(A.src) + gi);
+  if (A.src_mode == SRC_F64) return to_real(__ldg(static_cast<const double *>(A.src) + gi), (Real *)nullptr);
   return static_cast<const Real *>(A.src)[gi];
 }
 
+constexpr int kLoadsPerThread = 2 * kSlotsPerThread;   // n / tpl <= 8
+
+// One axis pass over a tile of lines: [forward transform] [eigenvalue division] [inverse].
+// Dynamic shared memory: L*M complex slots, then per line the eigenvalue sum of the other
+// axes, the line's base cell index (-1 for lines past a ragged end) and its zero-mode flag.
 template <typename Real>
 __global__ void __launch_bounds__(1024) axis_pass(PassArgs<Real> A) {
   using T = typename Cplx<Real>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *buf = reinterpret_cast<T *>(smem_raw);
+  Real *lamo = reinterpret_cast<Real *>(buf + A.L * A.M);
+  int *lbase = reinterpret_cast<int *>(lamo + A.L);
+  int *lzero = lbase + A.L;
+  const int t = threadIdx.x;
   TileGeom g;
   g.L = A.L;
   g.M = A.M;
-  if (A.col) { g.es = A.L; g.ls = 1; g.line_fastest = true; }
-  else { g.es = 1; g.ls = A.M; g.line_fastest = false; }
+  g.tpl = 1 << A.tpl_bits;
+  if (A.col) { g.es = A.L; g.ls = 1; g.line = t & (A.L - 1); g.lane = t >> A.lbits; }
+  else { g.es = 1; g.ls = A.M; g.line = t >> A.tpl_bits; g.lane = t & (g.tpl - 1); }
   const int tile = blockIdx.x;
   const int n = A.n;
-  const int items = A.L * n;
+
+  if (t < A.L) {
+    int base, valid;
+    if (A.col) {
+      int o = tile / A.tiles_per_outer;
+      int f = (tile - o * A.tiles_per_outer) * A.L + t;
+      valid = f < A.inner;
+      base = o * n * A.stride + f;
+    } else {
+      int line = tile * A.L + t;
+      valid = line < A.lines;
+      base = line * n;
+    }
+    lbase[t] = valid ? base : -1;
+    if (A.do_div && valid) {
+      int rem = base, idx[3] = {0, 0, 0};
+      for (int b = A.dim - 1; b >= 0; --b) { idx[b] = rem % A.shape[b]; rem /= A.shape[b]; }
+      Real lo = 0;
+      int zero = 1;
+      for (int b = 0; b < A.dim; ++b) {
+        if (b == A.axis) continue;
+        lo += A.lam[b][idx[b]];
+        zero &= idx[b] == 0;
+      }
+      lamo[t] = lo;
+      lzero[t] = zero;
+    }
+  }
+  __syncthreads();
+  const int line = g.line;
+  const int base = lbase[line];
+  const bool valid = base >= 0;
+  const int stride = A.stride;
   const bool fft_inv_dir = !(A.kind == KIND_ND || A.kind == KIND_DN);
 
+  // All global loads of a thread are issued before any is used (memory-level parallelism).
+  Real xin[kLoadsPerThread];
+#pragma unroll
+  for (int b = 0; b < kLoadsPerThread; ++b) {
+    const int j = g.lane + b * g.tpl;
+    xin[b] = (valid && j < n) ? load_src(A, base + j * stride) : (Real)0;
+  }
   if (A.do_fwd) {
     // F1: scatter the real line into the complex slots (Makhoul / DCT-IV ordering).
-    for (int t = threadIdx.x; t < items; t += blockDim.x) {
-      int line, j;
-      decode(g, t, n, line, j);
-      bool valid;
-      long long base = line_base(A, tile, line, valid);
-      Real x = valid ? load_src(A, base + (long long)j * A.stride) : (Real)0;
-      int q, comp;
-      float sgn;
-      fwd_slot_of(A.kind, n, j, q, comp, sgn);
-      reinterpret_cast<Real *>(&slot(buf, g, line, q))[comp] = (Real)sgn * x;
+#pragma unroll
+    for (int b = 0; b < kLoadsPerThread; ++b) {
+      const int j = g.lane + b * g.tpl;
+      if (j < n) {
+        int q, comp;
+        bool neg;
+        fwd_slot_of(A.kind, n, j, q, comp, neg);
+        reinterpret_cast<Real *>(&slot(buf, g, line, q))[comp] = neg ? -xin[b] : xin[b];
+      }
     }
     __syncthreads();
     pretwiddle(buf, g, A.kind, A.tw);
-    fft_lines(buf, g, A.radix, A.nradix, A.tw, false);
+    fft_lines(buf, g, A.st, A.nst, A.tw, false);
     fwd_post(buf, g, A.kind, n, A.tw);
   } else {
-    for (int t = threadIdx.x; t < items; t += blockDim.x) {
-      int line, j;
-      decode(g, t, n, line, j);
-      bool valid;
-      long long base = line_base(A, tile, line, valid);
-      realref(buf, g, line, j) = valid ? load_src(A, base + (long long)j * A.stride) : (Real)0;
+#pragma unroll
+    for (int b = 0; b < kLoadsPerThread; ++b) {
+      const int j = g.lane + b * g.tpl;
+      if (j < n) realref(buf, g, line, j) = xin[b];
     }
     __syncthreads();
   }
 
   if (A.do_div) {
     // p^ = s^ / (lambda_axis(j) + sum of the other axes' eigenvalues); zero mode -> 0.
-    for (int t = threadIdx.x; t < items; t += blockDim.x) {
-      int line, j;
-      decode(g, t, n, line, j);
-      bool valid;
-      long long base = line_base(A, tile, line, valid);
-      if (!valid) continue;
-      long long rem = base;   // cell index of element j = 0 of the line
-      int idx[3] = {0, 0, 0};
-      for (int b = A.dim - 1; b >= 0; --b) {
-        idx[b] = (int)(rem % A.shape[b]);
-        rem /= A.shape[b];
+    if (valid) {
+      const Real lo = lamo[line];
+      const bool z = A.singular && lzero[line];
+      const Real *la = A.lam[A.axis];
+      for (int j = g.lane; j < n; j += g.tpl) {
+        Real &v = realref(buf, g, line, j);
+        v = (z && j == 0) ? (Real)0 : v / (__ldg(la + j) + lo);
       }
-      idx[A.axis] = j;
-      Real lam = 0;
-      bool zero = true;
-      for (int b = 0; b < A.dim; ++b) {
-        lam += A.lam[b][idx[b]];
-        zero = zero && idx[b] == 0;
-      }
-      Real &v = realref(buf, g, line, j);
-      v = (A.singular && zero) ? (Real)0 : v / lam;
     }
     __syncthreads();
   }
 
   if (A.do_inv) {
     inv_pre(buf, g, A.kind, n, A.tw);
-    fft_lines(buf, g, A.radix, A.nradix, A.tw, fft_inv_dir);
+    fft_lines(buf, g, A.st, A.nst, A.tw, fft_inv_dir);
     inv_post_twiddle(buf, g, A.kind, A.tw);
-    for (int t = threadIdx.x; t < items; t += blockDim.x) {
-      int line, i;
-      decode(g, t, n, line, i);
-      bool valid;
-      long long base = line_base(A, tile, line, valid);
-      if (!valid) continue;
+    if (!valid) return;
+    double old[kLoadsPerThread];
+    if (A.dst_mode == DST_F64_ADD) {
+#pragma unroll
+      for (int b = 0; b < kLoadsPerThread; ++b) {
+        const int i = g.lane + b * g.tpl;
+        old[b] = (i < n) ? static_cast<const double *>(A.dst)[base + i * stride] : 0.0;
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < kLoadsPerThread; ++b) {
+      const int i = g.lane + b * g.tpl;
+      if (i >= n) continue;
       int j;
-      float sgn;
-      inv_src_of(A.kind, n, i, j, sgn);
-      Real x = realref(buf, g, line, j) * ((Real)sgn * A.out_scale);
-      long long gi = base + (long long)i * A.stride;
+      bool neg;
+      inv_src_of(A.kind, n, i, j, neg);
+      Real x = realref(buf, g, line, j) * (neg ? -A.out_scale : A.out_scale);
+      int gi = base + i * stride;
       if (A.dst_mode == DST_WORK) static_cast<Real *>(A.dst)[gi] = x;
-      else if (A.dst_mode == DST_F64_SET) static_cast<double *>(A.dst)[gi] = (double)x;
-      else static_cast<double *>(A.dst)[gi] += (double)x;
+      else if (A.dst_mode == DST_F64_SET) static_cast<double *>(A.dst)[gi] = to_f64(x);
+      else static_cast<double *>(A.dst)[gi] = old[b] + to_f64(x);
     }
   } else {
-    for (int t = threadIdx.x; t < items; t += blockDim.x) {
-      int line, j;
-      decode(g, t, n, line, j);
-      bool valid;
-      long long base = line_base(A, tile, line, valid);
-      if (!valid) continue;
-      static_cast<Real *>(A.dst)[base + (long long)j * A.stride] = realref(buf, g, line, j);
+    if (!valid) return;
+#pragma unroll
+    for (int b = 0; b < kLoadsPerThread; ++b) {
+      const int j = g.lane + b * g.tpl;
+      if (j < n) static_cast<Real *>(A.dst)[base + j * stride] = realref(buf, g, line, j);
     }
   }
 }
@@ -177,6 +212,12 @@ static void radix_plan(int M, int *radix, int &nr) {
   while (m % 2 == 0) { radix[nr++] = 2; m /= 2; }
   while (m % 3 == 0) { radix[nr++] = 3; m /= 3; }
   while (m % 5 == 0) { radix[nr++] = 5; m /= 5; }
+}
+
+static int ilog2(int v) {
+  int b = 0;
+  while ((1 << b) < v) ++b;
+  return b;
 }
 
 bool axis_length_supported(int n) {
@@ -245,40 +286,59 @@ static pc_status launch_pass(Plan *p, int axis, bool fwd, bool div, bool inv, in
   A.kind = ax.kind;
   A.n = ax.n;
   A.M = ax.M;
-  A.nradix = ax.nradix;
-  for (int i = 0; i < ax.nradix; ++i) A.radix[i] = ax.radix[i];
+  A.nst = ax.nradix;
+  {
+    int Ns = 1;
+    for (int i = 0; i < ax.nradix; ++i) {
+      StageInfo &si = A.st[i];
+      si.R = ax.radix[i];
+      si.Ns = Ns;
+      si.stride_m = ax.M / (Ns * si.R);
+      si.shift = ((Ns & (Ns - 1)) == 0) ? ilog2(Ns) : -1;
+      si.magic = (unsigned)(((1ULL << 32) + Ns - 1) / Ns);
+      Ns *= si.R;
+    }
+  }
   A.tw = (const T *)(sizeof(Real) == 8 ? (const void *)ax.tw64 : (const void *)ax.tw32);
   A.dim = p->dim;
-  long long stride = 1;
+  int stride = 1;
   for (int b = 0; b < p->dim; ++b) A.shape[b] = (int)p->n[b];
-  for (int b = axis + 1; b < p->dim; ++b) stride *= p->n[b];
+  for (int b = axis + 1; b < p->dim; ++b) stride *= (int)p->n[b];
   A.stride = stride;
   const int last = p->dim - 1;
   A.col = axis != last;
   const int M = ax.M;
-  // Tile size: up to 4096 complex slots; column tiles need >= 32 bytes per row segment.
-  const int budget = 4096;
+  // threads per line: a power of two >= M/4 (bounds the registers held across barriers)
+  const int tpl = 1 << ilog2((M + kSlotsPerThread - 1) / kSlotsPerThread);
+  const int max_lines = 1024 / tpl;
+  const int budget = 4096;          // complex slots per tile
+  const int want_ctas = 2 * 152;    // fill both dies of the GPU
   long long tiles;
+  int L;
   if (A.col) {
-    int W = (int)(sizeof(Real) == 8 ? 4 : 8);
-    while (W * 2 * M <= budget && W < 32) W *= 2;
-    while (W > 1 && W * M > budget) W /= 2;
-    if (W > stride) W = (int)stride;
-    A.L = W;
+    // 32-byte row segments when the grid allows it, fewer lines when CTAs would be too few
+    L = (sizeof(Real) == 8) ? 4 : 8;
+    while (L * 2 <= 32 && L * 2 * M <= budget && L * 2 <= max_lines) L *= 2;
+    long long outer = p->ncells / ((long long)stride * ax.n);
+    while (L > 1 && outer * ((stride + L - 1) / L) < want_ctas) L /= 2;
+    while (L > 1 && (L * M > budget || L > max_lines)) L /= 2;
+    if (L > stride) L = 1 << (ilog2(stride + 1) - 1);
     A.inner = stride;
-    A.tiles_per_outer = (int)((stride + W - 1) / W);
-    long long outer = p->ncells / (stride * ax.n);
+    A.tiles_per_outer = (stride + L - 1) / L;
     tiles = outer * A.tiles_per_outer;
   } else {
     long long lines = p->ncells / ax.n;
-    int L = budget / M;
+    L = budget / M;
     if (L < 1) L = 1;
-    // keep several CTAs per SM when the grid is small
-    while (L > 1 && (lines + L - 1) / L < 4 * 152) L /= 2;
-    A.L = L;
-    A.lines = lines;
+    L = 1 << (ilog2(L + 1) - 1);
+    while (L > max_lines) L /= 2;
+    while (L > 1 && (lines + L - 1) / L < want_ctas) L /= 2;
+    A.lines = (int)lines;
     tiles = (lines + L - 1) / L;
   }
+  A.L = L;
+  A.lbits = ilog2(L);
+  A.tpl_bits = ilog2(tpl);
   A.do_fwd = fwd;
   A.do_div = div;
   A.do_inv = inv;
@@ -290,22 +350,20 @@ static pc_status launch_pass(Plan *p, int axis, bool fwd, bool div, bool inv, in
   A.dst_mode = dst_mode;
   A.dst = dst;
   A.out_scale = (Real)inv_scale(ax.kind, ax.n);
-  int slots = A.L * M;
-  int threads = ((slots / kSlotsPerThread + 31) / 32) * 32;
-  if (threads < 64) threads = 64;
-  if (threads > 1024) threads = 1024;
-  // pairs of the real-DFT wrappers: L*(M/2+1) <= threads*(kSlotsPerThread/2+1) needs L <= threads
-  if (threads * kSlotsPerThread < slots || A.L > threads)
-    return fail(PC_ERR_UNSUPPORTED, "axis %d: tile of %d slots too large", axis, slots);
-  size_t smem = (size_t)slots * sizeof(T);
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[sizeof(Real) == 8]) {
-    PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set[sizeof(Real) == 8] = true;
-  }
+  const int threads = L * tpl;
+  if (threads > 1024 || L * M > 2 * budget)
+    return fail(PC_ERR_UNSUPPORTED, "axis %d: tile of %d x %d too large", axis, L, M);
+  size_t smem = (size_t)L * M * sizeof(T) + (size_t)L * (sizeof(Real) + 2 * sizeof(int));
   axis_pass<Real><<<(unsigned)tiles, threads, smem, st>>>(A);
   count_launch(p);
   PC_CUDA_TRY(cudaGetLastError());
+  return PC_OK;
+}
+
+// Kernel attributes set once per device, before any stream capture.
+pc_status prepare_kernels() {
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   return PC_OK;
 }
 

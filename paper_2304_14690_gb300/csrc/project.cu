@@ -13,8 +13,11 @@
 //  check       max |D_h (U - beta dt G_h p)| (only when statistics are requested)
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
+#include <vector>
 
+#include "numeric.cuh"
 #include "pc_internal.cuh"
 
 namespace pc {
@@ -49,6 +52,47 @@ __device__ void block_sum_add(double v, double *dst) {
     if (lane == 0) atomicAdd(dst, v);
   }
 }
+// Deterministic grid-wide sum: every block writes its partial (fixed shuffle tree), the last
+// block to finish sums all partials in block order and writes *dst, then resets the counter.
+// Results are bitwise reproducible, unlike concurrent floating-point atomics.
+__device__ bool grid_sum(double v, double *partials, unsigned int *counter, double *dst) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    v = warp_sum(v);
+    if (lane == 0) {
+      partials[bid] = v;
+      __threadfence();
+      last = atomicAdd(counter, 1u) == nblk - 1;
+    }
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double acc = 0.0;
+  for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x) acc += ((volatile double *)partials)[b];
+  acc = warp_sum(acc);
+  __syncthreads();
+  if (lane == 0) sh[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    *dst = t;
+    *counter = 0u;
+    return true;
+  }
+  return false;
+}
+
 __device__ void block_max_update(double v, double *dst) {
   __shared__ double sh[32];
   v = warp_max(v);
@@ -67,107 +111,138 @@ __device__ void block_max_update(double v, double *dst) {
 template <typename VT>
 __device__ __forceinline__ double ld(const VT *p, long long i) { return (double)p[i]; }
 
-// u~ = u* + dt f~; FP64 copy (fp64 path) or (hi, lo) FP32 pair (mixed). Also max |u*|.
-template <typename VT>
-__global__ void prep_kernel(long long count, const VT *u, const VT *f, double dt, double *ut64,
-                            float *uhi, float *ulo, DevStats *stats) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ double as_f64(double v) { return v; }
+__device__ __forceinline__ double as_f64(float v) { return f2d_bits(v); }
+__device__ __forceinline__ float2 as_pair(double v) {
+  float hi, lo;
+  split_f64(v, hi, lo);
+  return make_float2(hi, lo);
+}
+__device__ __forceinline__ float2 as_pair(float v) { return make_float2(v, 0.0f); }
+
+// u~ = u* + dt f~; FP64 copy (FP64 path, SPLIT = false) or (hi, lo) FP32 pair (mixed). Compile-
+// time variants keep the common case (no force, no statistics) free of FP64 arithmetic.
+template <typename VT, bool HAS_F, bool STATS, bool SPLIT>
+__global__ void prep_kernel(int count, const VT *__restrict__ u, const VT *__restrict__ f, double dt,
+                            double *__restrict__ ut64, float2 *__restrict__ u2, DevStats *stats) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
   double m = 0.0;
   if (i < count) {
-    double v = ld(u, i);
-    m = fabs(v);
-    if (f) v = fma(dt, ld(f, i), v);
-    if (ut64) ut64[i] = v;
-    if (uhi) {
-      float hi = (float)v;
-      uhi[i] = hi;
-      ulo[i] = (float)(v - (double)hi);
+    const VT ui = u[i];
+    if (STATS) m = fabs(as_f64(ui));
+    if (HAS_F) {
+      double v = fma(dt, as_f64(f[i]), as_f64(ui));
+      if (SPLIT) u2[i] = as_pair(v);
+      else ut64[i] = v;
+    } else {
+      if (SPLIT) u2[i] = as_pair(ui);
+      else ut64[i] = as_f64(ui);
     }
   }
-  block_max_update(m, &stats->max_u);
+  if (STATS) block_max_update(m, &stats->max_u);
+}
+
+template <typename VT>
+static void launch_prep(bool has_f, bool stats, bool split, int cnt, const VT *u, const VT *f, double dt,
+                        double *ut64, float2 *u2, DevStats *ds, cudaStream_t st) {
+  const int T = 256;
+  const int G = grid_for(cnt, T);
+#define PC_PREP(F, S, P) prep_kernel<VT, F, S, P><<<G, T, 0, st>>>(cnt, u, f, dt, ut64, u2, ds)
+  if (has_f) {
+    if (stats) { if (split) PC_PREP(true, true, true); else PC_PREP(true, true, false); }
+    else { if (split) PC_PREP(true, false, true); else PC_PREP(true, false, false); }
+  } else {
+    if (stats) { if (split) PC_PREP(false, true, true); else PC_PREP(false, true, false); }
+    else { if (split) PC_PREP(false, false, true); else PC_PREP(false, false, false); }
+  }
+#undef PC_PREP
 }
 
 // ----------------------------------------------------------------------------- transfer
-__global__ void transfer64_kernel(long long rows, int K, const int32_t *__restrict__ col,
+__global__ void transfer64_kernel(int rows, int K, const int32_t *__restrict__ col,
                                   const double *__restrict__ w, const double *__restrict__ u,
                                   double *__restrict__ U) {
-  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   double acc = 0.0;
+#pragma unroll 4
   for (int k = 0; k < K; ++k) {
-    long long at = (long long)k * rows + r;
-    acc = fma(w[at], u[col[at]], acc);
+    int at = k * rows + r;
+    acc = fma(__ldg(w + at), __ldg(u + __ldg(col + at)), acc);
   }
   U[r] = acc;
 }
 
-// Compensated dot product in FP32 arithmetic: (whi + wlo) . (uhi + ulo) accumulated as an
+// Compensated dot product in FP32 arithmetic: (w.x + w.y) . (u.x + u.y) accumulated as an
 // unevaluated pair; products by TwoProduct (fma), sums by TwoSum.
 struct DF { float hi, lo; };
-__device__ __forceinline__ void df_acc(DF &s, float whi, float wlo, float uhi, float ulo) {
-  float p = whi * uhi;
-  float e = fmaf(whi, uhi, -p);
-  e = fmaf(whi, ulo, e);
-  e = fmaf(wlo, uhi, e);
+__device__ __forceinline__ void df_acc(DF &s, float2 w, float2 u) {
+  float p = w.x * u.x;
+  float e = fmaf(w.x, u.x, -p);
+  e = fmaf(w.x, u.y, e);
+  e = fmaf(w.y, u.x, e);
   float t = s.hi + p;
   float z = t - s.hi;
   float err = (s.hi - (t - z)) + (p - z);
   s.hi = t;
   s.lo += err + e;
 }
+__device__ __forceinline__ double df_value(DF s) { return f2d_bits(s.hi) + f2d_bits(s.lo); }
 
-__global__ void transfer_mixed_kernel(long long rows, int K, const int32_t *__restrict__ col,
-                                      const float *__restrict__ whi, const float *__restrict__ wlo,
-                                      const float *__restrict__ uhi, const float *__restrict__ ulo,
+__global__ void transfer_mixed_kernel(int rows, int K, const int32_t *__restrict__ col,
+                                      const float2 *__restrict__ w2, const float2 *__restrict__ u2,
                                       double *__restrict__ U) {
-  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   DF s{0.f, 0.f};
+#pragma unroll 4
   for (int k = 0; k < K; ++k) {
-    long long at = (long long)k * rows + r;
-    int c = col[at];
-    df_acc(s, whi[at], wlo[at], uhi[c], ulo[c]);
+    int at = k * rows + r;
+    df_acc(s, __ldg(w2 + at), __ldg(u2 + __ldg(col + at)));
   }
-  U[r] = (double)s.hi + (double)s.lo;
+  U[r] = df_value(s);
 }
 
 // ----------------------------------------------------------------------------- grid geometry
+// Cells are addressed by a 3D launch (x: last axis, y: middle axis, z: first axis of a 3D grid;
+// 2D grids use x and y), so no kernel divides an index. Axes are padded to three with extent 1.
 struct GridDev {
   int dim;
-  int n[3];
+  int n[3];           // cells per axis, padded: n3[0..2] with the last axis fastest
   int nf[3];          // faces along each axis (n or n+1)
+  int cs[3];          // cell strides
+  int fs[3][3];       // fs[a][b]: stride of axis b in the face array of axis a
   int periodic[3];
   int lo_kind[3], hi_kind[3];   // 0 Neumann, 1 Dirichlet (ghost sign), ignored when periodic
   double inv_h[3], inv_h2[3];
 };
 
-__device__ __forceinline__ void unflat(const GridDev &g, long long c, int *i) {
-  for (int a = g.dim - 1; a >= 0; --a) { i[a] = (int)(c % g.n[a]); c /= g.n[a]; }
+// Cell multi-index of this thread (false when outside the grid).
+__device__ __forceinline__ bool cell_of_thread(const GridDev &g, int *i) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g.dim == 2) { i[0] = blockIdx.y; i[1] = x; i[2] = 0; return x < g.n[1]; }
+  i[0] = blockIdx.z; i[1] = blockIdx.y; i[2] = x;
+  return x < g.n[2];
 }
-// Linear index of face (i with i[axis] replaced by fi) in the face array of `axis`.
-__device__ __forceinline__ long long face_index(const GridDev &g, int axis, const int *i, int fi) {
-  long long f = 0;
-  for (int a = 0; a < g.dim; ++a) {
-    int extent = (a == axis) ? g.nf[a] : g.n[a];
-    int v = (a == axis) ? fi : i[a];
-    f = f * extent + v;
-  }
+__device__ __forceinline__ int cell_index(const GridDev &g, const int *i) {
+  return i[0] * g.cs[0] + i[1] * g.cs[1] + i[2] * g.cs[2];
+}
+// Linear index of face fi along `axis` with the other coordinates of cell i.
+__device__ __forceinline__ int face_index(const GridDev &g, int axis, const int *i, int fi) {
+  int f = 0;
+  for (int b = 0; b < 3; ++b) f += ((b == axis) ? fi : i[b]) * g.fs[axis][b];
   return f;
-}
-__device__ __forceinline__ long long cell_index(const GridDev &g, const int *i) {
-  long long c = 0;
-  for (int a = 0; a < g.dim; ++a) c = c * g.n[a] + i[a];
-  return c;
 }
 
 // s = D_h U / (beta dt), plus sum(s), sum(s^2).
-__global__ void divergence_kernel(GridDev g, long long ncells, const double *U0, const double *U1,
-                                  const double *U2, double inv_bdt, double *s, DevStats *stats) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void divergence_kernel(GridDev g, const double *U0, const double *U1,
+                                  const double *U2, double inv_bdt, double *s, DevStats *stats,
+                                  double *partials, unsigned int *counter, int want_sums,
+                                  double inv_ncells) {
+  int i[3];
   double v = 0.0;
-  if (c < ncells) {
-    int i[3];
-    unflat(g, c, i);
+  if (cell_of_thread(g, i)) {
+    const int c = cell_index(g, i);
     const double *U[3] = {U0, U1, U2};
     double acc = 0.0;
     for (int a = 0; a < g.dim; ++a) {
@@ -179,73 +254,84 @@ __global__ void divergence_kernel(GridDev g, long long ncells, const double *U0,
     v = acc * inv_bdt;
     s[c] = v;
   }
-  block_sum_add(v, &stats->sum_s);
-  block_sum_add(v * v, &stats->sum_s2);
+  if (want_sums) {
+    if (grid_sum(v, partials, counter, &stats->sum_s)) stats->mean_s = stats->sum_s * inv_ncells;
+    grid_sum(v * v, partials + (gridDim.x * gridDim.y * gridDim.z), counter + 1, &stats->sum_s2);
+  }
 }
 
-__global__ void sum_kernel(long long count, const double *x, double *sum, double *sum2) {
+// Sum and sum of squares of a cell array (the source of pc_solve_poisson), and its mean.
+__global__ void sum_kernel(long long count, const double *x, DevStats *stats, double *partials,
+                           unsigned int *counter) {
   long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double v = (c < count) ? x[c] : 0.0;
-  block_sum_add(v, sum);
-  if (sum2) block_sum_add(v * v, sum2);
+  if (grid_sum(v, partials, counter, &stats->sum_s)) stats->mean_s = stats->sum_s / (double)count;
+  grid_sum(v * v, partials + gridDim.x, counter + 1, &stats->sum_s2);
 }
 
 // L_h p at cell i (ghost rules: Neumann p_ghost = p_edge, Dirichlet -p_edge, periodic wrap).
-__device__ __forceinline__ double lap_at(const GridDev &g, const double *p, const int *i, double pc) {
+// The two neighbours of cell c along axis a (ghost rules at the domain boundary).
+__device__ __forceinline__ void neighbours(const GridDev &g, const double *p, const int *i, int c,
+                                           int a, double pc, double &pl, double &pr) {
+  const int st = g.cs[a];
+  if (i[a] > 0) pl = p[c - st];
+  else if (g.periodic[a]) pl = p[c + (g.n[a] - 1) * st];
+  else pl = g.lo_kind[a] ? -pc : pc;
+  if (i[a] < g.n[a] - 1) pr = p[c + st];
+  else if (g.periodic[a]) pr = p[c - (g.n[a] - 1) * st];
+  else pr = g.hi_kind[a] ? -pc : pc;
+}
+
+__device__ __forceinline__ double lap_at(const GridDev &g, const double *p, const int *i, int c, double pc) {
   double acc = 0.0;
-  int j[3] = {i[0], i[1], i[2]};
   for (int a = 0; a < g.dim; ++a) {
     double pl, pr;
-    if (i[a] > 0) { j[a] = i[a] - 1; pl = p[cell_index(g, j)]; }
-    else if (g.periodic[a]) { j[a] = g.n[a] - 1; pl = p[cell_index(g, j)]; }
-    else pl = g.lo_kind[a] ? -pc : pc;
-    if (i[a] < g.n[a] - 1) { j[a] = i[a] + 1; pr = p[cell_index(g, j)]; }
-    else if (g.periodic[a]) { j[a] = 0; pr = p[cell_index(g, j)]; }
-    else pr = g.hi_kind[a] ? -pc : pc;
-    j[a] = i[a];
+    neighbours(g, p, i, c, a, pc, pl, pr);
     acc = fma((pl + pr) - 2.0 * pc, g.inv_h2[a], acc);
   }
   return acc;
 }
 
-// r = s - mean(s) - L_h p in FP64, stored as FP32 for the next FP32 solve; adds ||r||^2.
-__global__ void residual_kernel(GridDev g, long long ncells, const double *s, const double *p,
-                                int singular, float *r, DevStats *stats, double *res2) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// r = s - mean(s) - L_h p in FP64, stored as FP32 (truncated by integer operations) for the
+// next FP32 solve; optionally ||r||^2.
+template <bool SINGULAR, bool WRITE_R, bool NORM>
+__global__ void residual_kernel(GridDev g, const double *__restrict__ s, const double *__restrict__ p,
+                                float *__restrict__ r, const DevStats *stats, double *res2,
+                                double *partials, unsigned int *counter) {
+  int i[3];
   double v = 0.0;
-  if (c < ncells) {
-    int i[3] = {0, 0, 0};
-    unflat(g, c, i);
-    double pc = p[c];
-    double mean = singular ? stats->sum_s / (double)ncells : 0.0;
-    v = (s[c] - mean) - lap_at(g, p, i, pc);
-    if (r) r[c] = (float)v;
+  if (cell_of_thread(g, i)) {
+    const int c = cell_index(g, i);
+    const double pc = p[c];
+    const double sc = SINGULAR ? s[c] - stats->mean_s : s[c];
+    v = sc - lap_at(g, p, i, c, pc);
+    if (WRITE_R) r[c] = d2f_rz_bits(v);
   }
-  block_sum_add(v * v, res2);
+  if (NORM) grid_sum(v * v, partials, counter, res2);
 }
 
-__global__ void gauge_sum_kernel(long long ncells, const double *p, DevStats *stats) {
+// Sum of p (and the corner value); the reducing block stores the gauge constant.
+__global__ void gauge_sum_kernel(long long ncells, const double *p, DevStats *stats, double *partials,
+                                 unsigned int *counter, int gauge_mode) {
   long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double v = (c < ncells) ? p[c] : 0.0;
   if (c == 0) stats->corner_p = v;
-  block_sum_add(v, &stats->sum_p);
+  if (grid_sum(v, partials, counter, &stats->sum_p))
+    stats->shift = (gauge_mode == 1) ? stats->sum_p / (double)ncells : p[0];
 }
 
 // p -= shift (gauge), and the (hi, lo) FP32 split of p for the compensated gradient.
-__global__ void finalize_p_kernel(long long ncells, double *p, int gauge_mode, const DevStats *stats,
-                                  float *phi, float *plo) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+template <bool GAUGE, bool SPLIT>
+__global__ void finalize_p_kernel(int ncells, double *__restrict__ p, const DevStats *stats,
+                                  float2 *__restrict__ p2) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncells) return;
-  double shift = 0.0;
-  if (gauge_mode == 1) shift = stats->sum_p / (double)ncells;
-  else if (gauge_mode == 2) shift = stats->corner_p;
-  double v = p[c] - shift;
-  p[c] = v;
-  if (phi) {
-    float hi = (float)v;
-    phi[c] = hi;
-    plo[c] = (float)(v - (double)hi);
+  double v = p[c];
+  if (GAUGE) {
+    v -= stats->shift;
+    p[c] = v;
   }
+  if (SPLIT) p2[c] = as_pair(v);
 }
 
 // ----------------------------------------------------------------------------- gradient
@@ -253,92 +339,83 @@ template <typename VT>
 __device__ __forceinline__ void store_v(VT *p, long long i, double v) { p[i] = (VT)v; }
 
 template <typename VT, int DIM>
-__global__ void gradient64_kernel(long long N, int K, const int32_t *__restrict__ col,
+__global__ void gradient64_kernel(int N, int K, const int32_t *__restrict__ col,
                                   const double *__restrict__ D, const double *__restrict__ p,
                                   const uint8_t *__restrict__ type, const VT *__restrict__ u,
-                                  double dt, double beta, VT *__restrict__ uo, VT *__restrict__ fo) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+                                  double inv_dt, double dt, double beta, VT *__restrict__ uo,
+                                  VT *__restrict__ fo) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double g[DIM];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) g[a] = 0.0;
+#pragma unroll 3
   for (int k = 0; k < K; ++k) {
-    double pv = p[col[(long long)k * N + i]];
+    double pv = __ldg(p + __ldg(col + k * N + i));
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) g[a] = fma(D[((long long)a * K + k) * N + i], pv, g[a]);
+    for (int a = 0; a < DIM; ++a) g[a] = fma(__ldg(D + (a * K + k) * N + i), pv, g[a]);
   }
   const bool ib = type[i] != PC_NODE_FLUID;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
-    double us = (double)u[(long long)a * N + i];
+    double us = (double)u[a * N + i];
     if (ib) {
-      store_v(uo, (long long)a * N + i, 0.0);
-      if (fo) store_v(fo, (long long)a * N + i, -us / dt + beta * g[a]);
+      store_v(uo, a * N + i, 0.0);
+      if (fo) store_v(fo, a * N + i, -us * inv_dt + beta * g[a]);
     } else {
-      store_v(uo, (long long)a * N + i, us - beta * dt * g[a]);
-      if (fo) store_v(fo, (long long)a * N + i, 0.0);
+      store_v(uo, a * N + i, us - beta * dt * g[a]);
+      if (fo) store_v(fo, a * N + i, 0.0);
     }
   }
 }
 
 template <typename VT, int DIM>
-__global__ void gradient_mixed_kernel(long long N, int K, const int32_t *__restrict__ col,
-                                      const float *__restrict__ Dhi, const float *__restrict__ Dlo,
-                                      const float *__restrict__ phi, const float *__restrict__ plo,
+__global__ void gradient_mixed_kernel(int N, int K, const int32_t *__restrict__ col,
+                                      const float2 *__restrict__ D2, const float2 *__restrict__ p2,
                                       const uint8_t *__restrict__ type, const VT *__restrict__ u,
-                                      double dt, double beta, VT *__restrict__ uo, VT *__restrict__ fo) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+                                      double inv_dt, double dt, double beta, VT *__restrict__ uo,
+                                      VT *__restrict__ fo) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   DF g[DIM];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) g[a] = DF{0.f, 0.f};
+#pragma unroll 3
   for (int k = 0; k < K; ++k) {
-    int c = col[(long long)k * N + i];
-    float ph = phi[c], pl = plo[c];
+    const float2 pv = __ldg(p2 + __ldg(col + k * N + i));
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      long long at = ((long long)a * K + k) * N + i;
-      df_acc(g[a], Dhi[at], Dlo[at], ph, pl);
-    }
+    for (int a = 0; a < DIM; ++a) df_acc(g[a], __ldg(D2 + (a * K + k) * N + i), pv);
   }
   const bool ib = type[i] != PC_NODE_FLUID;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
-    double ga = (double)g[a].hi + (double)g[a].lo;
-    double us = (double)u[(long long)a * N + i];
+    double ga = df_value(g[a]);
+    double us = (double)u[a * N + i];
     if (ib) {
-      store_v(uo, (long long)a * N + i, 0.0);
-      if (fo) store_v(fo, (long long)a * N + i, -us / dt + beta * ga);
+      store_v(uo, a * N + i, 0.0);
+      if (fo) store_v(fo, a * N + i, -us * inv_dt + beta * ga);
     } else {
-      store_v(uo, (long long)a * N + i, us - beta * dt * ga);
-      if (fo) store_v(fo, (long long)a * N + i, 0.0);
+      store_v(uo, a * N + i, us - beta * dt * ga);
+      if (fo) store_v(fo, a * N + i, 0.0);
     }
   }
 }
 
 // ----------------------------------------------------------------------------- check
 // max over cells of |D_h (U - beta dt G_h p)|; wall faces carry no flux and no gradient.
-__global__ void div_check_kernel(GridDev g, long long ncells, const double *U0, const double *U1,
+__global__ void div_check_kernel(GridDev g, const double *U0, const double *U1,
                                  const double *U2, const double *p, double bdt, DevStats *stats) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int i[3];
   double v = 0.0;
-  if (c < ncells) {
-    int i[3] = {0, 0, 0};
-    unflat(g, c, i);
+  if (cell_of_thread(g, i)) {
+    const int c = cell_index(g, i);
     const double *U[3] = {U0, U1, U2};
     double pc = p[c];
     double acc = 0.0;
-    int j[3] = {i[0], i[1], i[2]};
     for (int a = 0; a < g.dim; ++a) {
       // gradient on the low and high faces of the cell
       double pl, pr;
-      if (i[a] > 0) { j[a] = i[a] - 1; pl = p[cell_index(g, j)]; }
-      else if (g.periodic[a]) { j[a] = g.n[a] - 1; pl = p[cell_index(g, j)]; }
-      else pl = g.lo_kind[a] ? -pc : pc;
-      if (i[a] < g.n[a] - 1) { j[a] = i[a] + 1; pr = p[cell_index(g, j)]; }
-      else if (g.periodic[a]) { j[a] = 0; pr = p[cell_index(g, j)]; }
-      else pr = g.hi_kind[a] ? -pc : pc;
-      j[a] = i[a];
+      neighbours(g, p, i, c, a, pc, pl, pr);
       int hi = i[a] + 1;
       if (g.periodic[a] && hi == g.n[a]) hi = 0;
       double Ulo = U[a][face_index(g, a, i, i[a])] - bdt * (pc - pl) * g.inv_h[a];
@@ -369,7 +446,28 @@ static GridDev grid_dev(const Plan *p) {
       g.nf[a] = 1;
     }
   }
+  // strides (C order, last axis of the problem fastest; unused padded axes have stride 0)
+  int st = 1;
+  for (int a = p->dim - 1; a >= 0; --a) { g.cs[a] = st; st *= g.n[a]; }
+  for (int a = p->dim; a < 3; ++a) g.cs[a] = 0;
+  for (int ax = 0; ax < p->dim; ++ax) {
+    int fst = 1;
+    for (int b = p->dim - 1; b >= 0; --b) {
+      g.fs[ax][b] = fst;
+      fst *= (b == ax) ? g.nf[b] : g.n[b];
+    }
+    for (int b = p->dim; b < 3; ++b) g.fs[ax][b] = 0;
+  }
   return g;
+}
+
+// Launch shape covering every cell: x over the last axis, y/z over the others.
+static void cell_launch(const Plan *p, dim3 &grid, dim3 &block) {
+  const int last = p->dim - 1;
+  block = dim3(256);
+  unsigned gx = (unsigned)((p->n[last] + 255) / 256);
+  if (p->dim == 2) grid = dim3(gx, (unsigned)p->n[0], 1);
+  else grid = dim3(gx, (unsigned)p->n[1], (unsigned)p->n[0]);
 }
 
 static bool is_device_ptr(const void *ptr) {
@@ -383,11 +481,27 @@ static bool is_device_ptr(const void *ptr) {
 }
 
 // Grid-level solve: s64 (device) -> p (device, FP64), gauge applied; fills dstats fields.
+static void launch_residual(bool singular, bool write_r, bool norm, dim3 cg, dim3 cb, cudaStream_t st,
+                            const GridDev &g, const double *s, const double *p, float *r, DevStats *ds,
+                            double *res2, double *partials, unsigned int *counters) {
+#define PC_RES(S, W, N) residual_kernel<S, W, N><<<cg, cb, 0, st>>>(g, s, p, r, ds, res2, partials, counters)
+  if (singular) {
+    if (write_r) { if (norm) PC_RES(true, true, true); else PC_RES(true, true, false); }
+    else PC_RES(true, false, true);
+  } else {
+    if (write_r) { if (norm) PC_RES(false, true, true); else PC_RES(false, true, false); }
+    else PC_RES(false, false, true);
+  }
+#undef PC_RES
+}
+
 static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_final_residual,
                             cudaStream_t st) {
   const long long nc = p->ncells;
   const int T = 256;
   GridDev g = grid_dev(p);
+  dim3 cg, cb;
+  cell_launch(p, cg, cb);
   if (p->precision == PC_PREC_FP64) {
     PC_TRY(solve_fp64_grid(p, s64, pout, st));
     prof_mark(p, st, 3);
@@ -397,8 +511,8 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
     prof_mark(p, st, 3);
     for (int it = 0; it < sweeps; ++it) {
       float *r32 = reinterpret_cast<float *>(p->work64);   // work64 is free in mixed mode
-      residual_kernel<<<grid_for(nc, T), T, 0, st>>>(g, nc, s64, pout, p->singular, r32, p->dstats,
-                                                     &p->dstats->res2[it]);
+      launch_residual(p->singular, true, want_final_residual, cg, cb, st, g, s64, pout, r32, p->dstats,
+                      &p->dstats->res2[it], p->partials, p->counters);
       count_launch(p);
       prof_mark(p, st, 4);
       PC_TRY(solve_fp32_grid(p, SRC_F32_, r32, DST_F64_ADD_, pout, st));
@@ -407,21 +521,22 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
   }
   if (want_final_residual) {
     int it = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
-    residual_kernel<<<grid_for(nc, T), T, 0, st>>>(g, nc, s64, pout, p->singular, nullptr, p->dstats,
-                                                   &p->dstats->res2[it]);
+    launch_residual(p->singular, false, true, cg, cb, st, g, s64, pout, nullptr, p->dstats,
+                    &p->dstats->res2[it], p->partials, p->counters);
     count_launch(p);
     prof_mark(p, st, 7);
   }
   // gauge (singular problems), then the FP32 split of p for the mixed gradient
   int gmode = p->singular ? (p->gauge == 1 ? 2 : 1) : 0;
   if (gmode) {
-    gauge_sum_kernel<<<grid_for(nc, T), T, 0, st>>>(nc, pout, p->dstats);
+    gauge_sum_kernel<<<grid_for(nc, T), T, 0, st>>>(nc, pout, p->dstats, p->partials, p->counters, gmode);
     count_launch(p);
   }
   bool mixed = p->precision != PC_PREC_FP64;
   if (gmode || mixed) {
-    finalize_p_kernel<<<grid_for(nc, T), T, 0, st>>>(nc, pout, gmode, p->dstats, mixed ? p->phi : nullptr,
-                                                     mixed ? p->plo : nullptr);
+    if (gmode && mixed) finalize_p_kernel<true, true><<<grid_for(nc, T), T, 0, st>>>((int)nc, pout, p->dstats, p->p2);
+    else if (gmode) finalize_p_kernel<true, false><<<grid_for(nc, T), T, 0, st>>>((int)nc, pout, p->dstats, nullptr);
+    else finalize_p_kernel<false, true><<<grid_for(nc, T), T, 0, st>>>((int)nc, pout, p->dstats, p->p2);
     count_launch(p);
   }
   prof_mark(p, st, 5);
@@ -448,14 +563,16 @@ static pc_status fill_stats(Plan *p, pc_stats *stats, cudaStream_t st) {
 }
 
 static pc_status project_impl(Plan *p, double dt, const void *u_star, const void *f_in, double *p_out,
-                              void *u_out, void *f_out, pc_stats *stats, cudaStream_t st) {
+                              void *u_out, void *f_out, pc_stats *stats, cudaStream_t st,
+                              bool all_device = false) {
   const int d = p->dim;
   const long long N = p->N, nc = p->ncells;
   const size_t vsz = p->vdtype == PC_DTYPE_F64 ? 8 : 4;
   const size_t vbytes = (size_t)d * N * vsz;
   // host pointers are staged through plan buffers
-  const bool hu = !is_device_ptr(u_star), hf = !is_device_ptr(f_in), hp = !is_device_ptr(p_out),
-             huo = !is_device_ptr(u_out), hfo = !is_device_ptr(f_out);
+  const bool hu = !all_device && !is_device_ptr(u_star), hf = !all_device && !is_device_ptr(f_in),
+             hp = !all_device && !is_device_ptr(p_out), huo = !all_device && !is_device_ptr(u_out),
+             hfo = !all_device && !is_device_ptr(f_out);
   const void *du = u_star, *df = f_in;
   double *dp = p_out;
   void *duo = u_out, *dfo = f_out;
@@ -471,30 +588,30 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   const bool mixed = p->precision != PC_PREC_FP64;
   const long long cnt = (long long)d * N;
   if (p->vdtype == PC_DTYPE_F64)
-    prep_kernel<double><<<grid_for(cnt, T), T, 0, st>>>(cnt, (const double *)du, (const double *)df, dt,
-                                                         mixed ? nullptr : p->ut64, mixed ? p->uhi : nullptr,
-                                                         mixed ? p->ulo : nullptr, p->dstats);
+    launch_prep<double>(df != nullptr, stats != nullptr, mixed, (int)cnt, (const double *)du, (const double *)df, dt,
+                        p->ut64, p->u2, p->dstats, st);
   else
-    prep_kernel<float><<<grid_for(cnt, T), T, 0, st>>>(cnt, (const float *)du, (const float *)df, dt,
-                                                        mixed ? nullptr : p->ut64, mixed ? p->uhi : nullptr,
-                                                        mixed ? p->ulo : nullptr, p->dstats);
+    launch_prep<float>(df != nullptr, stats != nullptr, mixed, (int)cnt, (const float *)du, (const float *)df, dt,
+                       p->ut64, p->u2, p->dstats, st);
   count_launch(p);
   prof_mark(p, st, 0);
   for (int a = 0; a < d; ++a) {
     long long rows = p->nface_total[a];
     if (mixed)
-      transfer_mixed_kernel<<<grid_for(rows, T), T, 0, st>>>(rows, p->K, p->fcol[a], p->fwhi[a], p->fwlo[a],
-                                                             p->uhi + (long long)a * N, p->ulo + (long long)a * N,
-                                                             p->U64[a]);
+      transfer_mixed_kernel<<<grid_for(rows, T), T, 0, st>>>((int)rows, p->K, p->fcol[a], p->fw2[a],
+                                                             p->u2 + (long long)a * N, p->U64[a]);
     else
-      transfer64_kernel<<<grid_for(rows, T), T, 0, st>>>(rows, p->K, p->fcol[a], p->fw64[a],
+      transfer64_kernel<<<grid_for(rows, T), T, 0, st>>>((int)rows, p->K, p->fcol[a], p->fw64[a],
                                                          p->ut64 + (long long)a * N, p->U64[a]);
     count_launch(p);
   }
   prof_mark(p, st, 1);
   GridDev g = grid_dev(p);
-  divergence_kernel<<<grid_for(nc, T), T, 0, st>>>(g, nc, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt),
-                                                   p->s64, p->dstats);
+  dim3 cg, cb;
+  cell_launch(p, cg, cb);
+  divergence_kernel<<<cg, cb, 0, st>>>(g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt),
+                                       p->s64, p->dstats, p->partials, p->counters,
+                                       (p->singular || stats) ? 1 : 0, 1.0 / (double)nc);
   count_launch(p);
   prof_mark(p, st, 2);
   PC_CUDA_TRY(cudaGetLastError());
@@ -502,26 +619,25 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   const void *ug = du;
   if (p->vdtype == PC_DTYPE_F64) {
     if (mixed) {
-      if (d == 2) gradient_mixed_kernel<double, 2><<<grid_for(N, T), T, 0, st>>>(N, p->Kg, p->ncol, p->nDhi, p->nDlo, p->phi, p->plo, p->ntype, (const double *)ug, dt, p->beta, (double *)duo, (double *)dfo);
-      else gradient_mixed_kernel<double, 3><<<grid_for(N, T), T, 0, st>>>(N, p->Kg, p->ncol, p->nDhi, p->nDlo, p->phi, p->plo, p->ntype, (const double *)ug, dt, p->beta, (double *)duo, (double *)dfo);
+      if (d == 2) gradient_mixed_kernel<double, 2><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
+      else gradient_mixed_kernel<double, 3><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
     } else {
-      if (d == 2) gradient64_kernel<double, 2><<<grid_for(N, T), T, 0, st>>>(N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, dt, p->beta, (double *)duo, (double *)dfo);
-      else gradient64_kernel<double, 3><<<grid_for(N, T), T, 0, st>>>(N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, dt, p->beta, (double *)duo, (double *)dfo);
+      if (d == 2) gradient64_kernel<double, 2><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
+      else gradient64_kernel<double, 3><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
     }
   } else {
     if (mixed) {
-      if (d == 2) gradient_mixed_kernel<float, 2><<<grid_for(N, T), T, 0, st>>>(N, p->Kg, p->ncol, p->nDhi, p->nDlo, p->phi, p->plo, p->ntype, (const float *)ug, dt, p->beta, (float *)duo, (float *)dfo);
-      else gradient_mixed_kernel<float, 3><<<grid_for(N, T), T, 0, st>>>(N, p->Kg, p->ncol, p->nDhi, p->nDlo, p->phi, p->plo, p->ntype, (const float *)ug, dt, p->beta, (float *)duo, (float *)dfo);
+      if (d == 2) gradient_mixed_kernel<float, 2><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
+      else gradient_mixed_kernel<float, 3><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
     } else {
-      if (d == 2) gradient64_kernel<float, 2><<<grid_for(N, T), T, 0, st>>>(N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, dt, p->beta, (float *)duo, (float *)dfo);
-      else gradient64_kernel<float, 3><<<grid_for(N, T), T, 0, st>>>(N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, dt, p->beta, (float *)duo, (float *)dfo);
+      if (d == 2) gradient64_kernel<float, 2><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
+      else gradient64_kernel<float, 3><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
     }
   }
   count_launch(p);
   prof_mark(p, st, 6);
   if (stats) {
-    div_check_kernel<<<grid_for(nc, T), T, 0, st>>>(g, nc, p->U64[0], p->U64[1], p->U64[2], dp, p->beta * dt,
-                                                    p->dstats);
+    div_check_kernel<<<cg, cb, 0, st>>>(g, p->U64[0], p->U64[1], p->U64[2], dp, p->beta * dt, p->dstats);
     count_launch(p);
     prof_mark(p, st, 7);
   }
@@ -543,13 +659,98 @@ static pc_status solve_impl(Plan *p, const double *s, double *p_out, pc_stats *s
   if (hp) dp = p->stage_p;
   prof_begin(p, st);
   PC_CUDA_TRY(cudaMemsetAsync(p->dstats, 0, sizeof(DevStats), st));
-  sum_kernel<<<grid_for(nc, 256), 256, 0, st>>>(nc, ds, &p->dstats->sum_s, &p->dstats->sum_s2);
+  sum_kernel<<<grid_for(nc, 256), 256, 0, st>>>(nc, ds, p->dstats, p->partials, p->counters);
   count_launch(p);
   prof_mark(p, st, 2);
   PC_TRY(solve_grid(p, ds, dp, stats != nullptr, st));
   if (hp) PC_CUDA_TRY(cudaMemcpyAsync(p_out, dp, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (stats) PC_TRY(fill_stats(p, stats, st));
   if (hp) PC_CUDA_TRY(cudaStreamSynchronize(st));
+  return PC_OK;
+}
+
+static bool graph_cached(const Plan *p, double dt, const void *u, const void *f, const double *po,
+                         const void *uo, const void *fo) {
+  for (int i = 0; i < kGraphCache; ++i) {
+    const GraphEntry &c = p->graphs[i];
+    if (c.exec && c.u == u && c.f == f && c.p == po && c.uo == uo && c.fo == fo && c.dt == dt) return true;
+  }
+  return false;
+}
+
+// pc_project through a cached CUDA graph: captured once per argument set on the plan's
+// private stream, then replayed with one launch on the caller's stream.
+static pc_status project_graph(Plan *p, double dt, const void *u_star, const void *f_in, double *p_out,
+                               void *u_out, void *f_out, cudaStream_t st) {
+  GraphEntry *e = nullptr;
+  for (int i = 0; i < kGraphCache; ++i) {
+    GraphEntry &c = p->graphs[i];
+    if (c.exec && c.u == u_star && c.f == f_in && c.p == p_out && c.uo == u_out && c.fo == f_out && c.dt == dt) {
+      e = &c;
+      break;
+    }
+  }
+  if (!e) {
+    e = &p->graphs[0];
+    for (int i = 1; i < kGraphCache; ++i)
+      if (p->graphs[i].stamp < e->stamp) e = &p->graphs[i];
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    e->exec = nullptr;
+    e->graph = nullptr;
+    PC_CUDA_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    p->capturing = true;
+    const long long l0 = p->launches;
+    pc_status s = project_impl(p, dt, u_star, f_in, p_out, u_out, f_out, nullptr, p->cap_stream, true);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
+    p->capturing = false;
+    e->launches = p->launches - l0;
+    p->launches = l0;
+    if (s != PC_OK || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return s != PC_OK ? s : fail(PC_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(ce));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&e->exec, g, 0ULL);
+    if (ie != cudaSuccess) {
+      cudaGraphDestroy(g);
+      e->exec = nullptr;
+      return fail(PC_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
+    }
+    e->graph = g;
+    // map the event-record nodes back to the phase boundaries they were captured for
+    size_t nn = 0;
+    PC_CUDA_TRY(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    PC_CUDA_TRY(cudaGraphGetNodes(g, nodes.data(), &nn));
+    e->nev = p->cap_n;
+    for (int i = 0; i < e->nev; ++i) e->evnode[i] = nullptr;
+    for (size_t k = 0; k < nn; ++k) {
+      cudaGraphNodeType ty;
+      PC_CUDA_TRY(cudaGraphNodeGetType(nodes[k], &ty));
+      if (ty != cudaGraphNodeTypeEventRecord) continue;
+      cudaEvent_t ev;
+      PC_CUDA_TRY(cudaGraphEventRecordNodeGetEvent(nodes[k], &ev));
+      for (int i = 0; i < e->nev; ++i)
+        if (p->cap_ev[i] == ev) e->evnode[i] = nodes[k];
+    }
+    for (int i = 0; i + 1 < e->nev; ++i) e->tag[i] = p->cap_tag[i];
+    e->u = u_star; e->f = f_in; e->p = p_out; e->uo = u_out; e->fo = f_out; e->dt = dt;
+  }
+  e->stamp = ++p->graph_clock;
+  if (p->prof && p->slots && p->slots_used < kProfSlots) {
+    ProfSlot *slot = &p->slots[p->slots_used++];
+    slot->n = 0;
+    bool ok = true;
+    for (int i = 0; i < e->nev && ok; ++i)
+      ok = e->evnode[i] && cudaGraphExecEventRecordNodeSetEvent(e->exec, e->evnode[i], slot->ev[i]) == cudaSuccess;
+    if (ok) {
+      slot->n = e->nev;
+      for (int i = 0; i + 1 < e->nev; ++i) slot->tag[i] = e->tag[i];
+    }
+  }
+  PC_CUDA_TRY(cudaGraphLaunch(e->exec, st));
+  p->launches += e->launches;
   return PC_OK;
 }
 
@@ -566,6 +767,11 @@ extern "C" pc_status pc_project(pc_plan *plan, double dt, const void *u_star, co
   if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) {
     if (cudaSetDevice(p->device) != cudaSuccess) return pc::fail(PC_ERR_CUDA, "cannot select device %d", p->device);
   }
+  if (p->graphs_on && !stats &&
+      (pc::graph_cached(p, dt, u_star, f_ib_in, p_out, u_out, f_ib_out) ||
+       (pc::is_device_ptr(u_star) && pc::is_device_ptr(f_ib_in) && pc::is_device_ptr(p_out) &&
+        pc::is_device_ptr(u_out) && pc::is_device_ptr(f_ib_out))))
+    return pc::project_graph(p, dt, u_star, f_ib_in, p_out, u_out, f_ib_out, (cudaStream_t)cuda_stream);
   return pc::project_impl(p, dt, u_star, f_ib_in, p_out, u_out, f_ib_out, stats, (cudaStream_t)cuda_stream);
 }
 

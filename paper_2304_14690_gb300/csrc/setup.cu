@@ -238,12 +238,11 @@ __device__ __forceinline__ void record_failure(unsigned int *flags, unsigned int
   atomicMin(reinterpret_cast<unsigned long long *>(flags + 2), key);
 }
 
-__device__ __forceinline__ void split_store(double v, double *w64, float *whi, float *wlo, long long at) {
+__device__ __forceinline__ void split_store(double v, double *w64, float2 *w2, long long at) {
   w64[at] = v;
-  if (whi) {
+  if (w2) {
     float hi = (float)v;
-    whi[at] = hi;
-    wlo[at] = (float)(v - (double)hi);
+    w2[at] = make_float2(hi, (float)(v - (double)hi));
   }
 }
 
@@ -252,7 +251,7 @@ template <int DIM>
 __global__ void face_rows_kernel(KnnCtx c, WlsParams P, int axis, int nf_axis, int bc_lo_wall,
                                  int bc_hi_wall, int n_axis, long long rows, const double *glo,
                                  const double *gh, const int *gshape, int32_t *col, double *w64,
-                                 float *whi, float *wlo, unsigned int *flags) {
+                                 float2 *w2, unsigned int *flags) {
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   // face multi-index (C order of the face array)
@@ -268,7 +267,7 @@ __global__ void face_rows_kernel(KnnCtx c, WlsParams P, int axis, int nf_axis, i
   if (wall) {
     for (int k = 0; k < K; ++k) {
       col[(long long)k * rows + r] = 0;
-      split_store(0.0, w64, whi, wlo, (long long)k * rows + r);
+      split_store(0.0, w64, w2, (long long)k * rows + r);
     }
     return;
   }
@@ -288,7 +287,7 @@ __global__ void face_rows_kernel(KnnCtx c, WlsParams P, int axis, int nf_axis, i
   }
   for (int k = 0; k < K; ++k) {
     col[(long long)k * rows + r] = bi[k];
-    split_store(w[k], w64, whi, wlo, (long long)k * rows + r);
+    split_store(w[k], w64, w2, (long long)k * rows + r);
   }
 }
 
@@ -299,8 +298,7 @@ __global__ void face_rows_kernel(KnnCtx c, WlsParams P, int axis, int nf_axis, i
 // wall does not guarantee.
 template <int DIM>
 __global__ void node_rows_kernel(KnnCtx c, WlsParams P, const double *xyz, long long N,
-                                 int32_t *col, double *D64, float *Dhi, float *Dlo,
-                                 unsigned int *flags) {
+                                 int32_t *col, double *D64, float2 *D2, unsigned int *flags) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   constexpr int KB = (DIM == 2) ? 9 : 27;
@@ -344,7 +342,7 @@ __global__ void node_rows_kernel(KnnCtx c, WlsParams P, const double *xyz, long 
   for (int k = 0; k < KB; ++k) col[(long long)k * N + i] = bi[k];
   for (int a = 0; a < DIM; ++a)
     for (int k = 0; k < KB; ++k)
-      split_store(w[a * KB + k], D64, Dhi, Dlo, ((long long)a * KB + k) * N + i);
+      split_store(w[a * KB + k], D64, D2, ((long long)a * KB + k) * N + i);
 }
 
 // ----------------------------------------------------------------------------- bucket sort
@@ -484,12 +482,10 @@ pc_status build_rows(Plan *p, const double *xyz, cudaStream_t st) {
     int hi_wall = (!ax.periodic && ax.bc_hi == PC_BC_NEUMANN_WALL);
     if (d == 2)
       face_rows_kernel<2><<<grid_for(rows, 128), 128, 0, st>>>(nc, P, a, ax.nfaces, lo_wall, hi_wall, ax.n, rows, glo, gh,
-                                                               gshape, p->fcol[a], p->fw64[a], mixed ? p->fwhi[a] : nullptr,
-                                                               mixed ? p->fwlo[a] : nullptr, flags);
+                                                               gshape, p->fcol[a], p->fw64[a], mixed ? p->fw2[a] : nullptr, flags);
     else
       face_rows_kernel<3><<<grid_for(rows, 128), 128, 0, st>>>(nc, P, a, ax.nfaces, lo_wall, hi_wall, ax.n, rows, glo, gh,
-                                                               gshape, p->fcol[a], p->fw64[a], mixed ? p->fwhi[a] : nullptr,
-                                                               mixed ? p->fwlo[a] : nullptr, flags);
+                                                               gshape, p->fcol[a], p->fw64[a], mixed ? p->fw2[a] : nullptr, flags);
   }
   // cell centres as points: bucket == cell
   KnnCtx cc{};
@@ -508,11 +504,9 @@ pc_status build_rows(Plan *p, const double *xyz, cudaStream_t st) {
   P.first_row = 1;
   P.c_dim = (d == 2) ? std::sqrt(pi / 9.0) : std::pow(4.0 * pi / (3.0 * 27.0), 1.0 / 3.0);
   if (d == 2)
-    node_rows_kernel<2><<<grid_for(N, 128), 128, 0, st>>>(cc, P, xyz, N, p->ncol, p->nD64, mixed ? p->nDhi : nullptr,
-                                                          mixed ? p->nDlo : nullptr, flags);
+    node_rows_kernel<2><<<grid_for(N, 128), 128, 0, st>>>(cc, P, xyz, N, p->ncol, p->nD64, mixed ? p->nD2 : nullptr, flags);
   else
-    node_rows_kernel<3><<<grid_for(N, 128), 128, 0, st>>>(cc, P, xyz, N, p->ncol, p->nD64, mixed ? p->nDhi : nullptr,
-                                                          mixed ? p->nDlo : nullptr, flags);
+    node_rows_kernel<3><<<grid_for(N, 128), 128, 0, st>>>(cc, P, xyz, N, p->ncol, p->nD64, mixed ? p->nD2 : nullptr, flags);
   cudaError_t e = cudaGetLastError();
   unsigned int hf[4] = {0, 0, 0, 0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(hf, flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st);

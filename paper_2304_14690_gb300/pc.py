@@ -101,6 +101,7 @@ FUNCTIONS = {
     "pc_plan_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "pc_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "pc_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "pc_set_graphs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "pc_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
     "pc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pc_last_error_message": (ctypes.c_char_p, []),
@@ -221,6 +222,9 @@ class Plan:
         b = ctypes.c_size_t()
         _check(load().pc_plan_bytes(self.handle, ctypes.byref(b)))
         return b.value
+
+    def graphs(self, on=True):
+        _check(load().pc_set_graphs(self.handle, 1 if on else 0))
 
     def profile(self, on=True):
         _check(load().pc_profile_enable(self.handle, 1 if on else 0))

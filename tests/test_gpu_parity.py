@@ -180,6 +180,31 @@ def test_host_pointers_match_device(env, problems):
     plan.close()
 
 
+def test_graph_equals_direct(env, problems):
+    """The cached CUDA-graph path gives bitwise the same results as direct launches, also after
+    the arguments change (new capture) and when they come back (cache hit)."""
+    pc, torch, dev = env
+    for prob, _, _ in (problems[1], problems[7]):
+        plan = pc.Plan(prob, precision="mixed")
+        u = torch.as_tensor(prob.u_star, device=dev)
+        f = torch.as_tensor(prob.f_ib, device=dev)
+        a = plan.alloc_outputs()
+        b = plan.alloc_outputs()
+        u2 = u * 2.0
+        plan.project(u, f, out=a)                 # captured and replayed
+        plan.project(u2, f, out=b)                # other arguments: second graph
+        plan.project(u, f, out=a)                 # cache hit
+        plan.graphs(False)
+        c = plan.alloc_outputs()
+        d = plan.alloc_outputs()
+        plan.project(u, f, out=c)
+        plan.project(u2, f, out=d)
+        torch.cuda.synchronize()
+        for x, y in zip(a + b, c + d):
+            assert torch.equal(x, y)
+        plan.close()
+
+
 def test_batch_equals_single(env, problems):
     pc, torch, dev = env
     plans, args, singles = [], [], []
