@@ -151,6 +151,27 @@ pc_status pc_project_batch(int count, pc_plan *const *plans, const pc_project_ar
 pc_status pc_solve_poisson(pc_plan *plan, const double *s, double *p_out, pc_stats *stats,
                            void *cuda_stream);
 
+/* Allocation-free grid-level Poisson solve (the paper has no counterpart: this is a service of
+ * the library, not a step of the method). Solves L_h p = s in FP64 with the same transform
+ * passes as pc_solve_poisson, for a grid given by dim, n[dim], h[dim], bc_lo/bc_hi[dim] (pc_bc)
+ * and gauge (0 mean, 1 corner; used when no face is Dirichlet), without a plan.
+ *
+ * It is for callers that cannot call cudaMalloc when they need a solve: code running under a
+ * memory pool or custom allocator that owns all device memory, code inside host callbacks or
+ * library hooks where an allocation would synchronise the device or is not permitted, and
+ * deployments that fix their device memory at start-up. It allocates nothing: its workspace is
+ * one file-scope device array of 8 MiB that every GPU loading the library holds until exit.
+ *  - Limit: at most 524288 cells (e.g. 1024 x 512); larger grids return PC_ERR_BUDGET.
+ *  - s and p_out are device pointers (C order, one FP64 value per cell); host pointers are
+ *    rejected with PC_ERR_INVALID_ARG.
+ *  - The first call on a device looks up the array's device address, zeroes it and sets kernel
+ *    attributes; make that first call before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents: calls that overlap on
+ *    the GPU (different streams, or different host threads) race and corrupt each other. */
+pc_status pc_solve_poisson_static(int dim, const int64_t *n, const double *h, const int *bc_lo,
+                                  const int *bc_hi, int gauge, const double *s, double *p_out,
+                                  void *cuda_stream);
+
 /* WLS rows of a plan, for inspection and tests. which = 0..dim-1: value rows of the faces
  * normal to that axis (rows = faces in C order of that face array); which = dim: derivative
  * rows of the nodes (rows = nodes, weights [dim][rows][K]). col_out: [rows][K] int32 (node

@@ -184,6 +184,9 @@ pc_status solve_fp64(Plan *p, const double *s_dev, double *p_dev, bool from_face
                      cudaStream_t st);
 pc_status solve_mixed(Plan *p, const double *s_dev, double *p_dev, bool from_faces,
                       int sweeps, cudaStream_t st);
+// Solve of device arrays for a plan description built by the caller (project.cu).
+pc_status solve_grid_device(Plan *p, const double *s, double *pout, cudaStream_t st);
+pc_status prepare_kernels();
 // Setup (setup.cu).
 pc_status build_rows(Plan *p, const double *xyz_dev, cudaStream_t st);
 // Axis tables (poisson.cu).

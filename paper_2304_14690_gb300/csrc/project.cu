@@ -650,6 +650,16 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   return PC_OK;
 }
 
+// Grid-level solve of device arrays with a caller-built plan description (no staging, no
+// statistics): source sums, transform solve, gauge. Used by the allocation-free entry point.
+pc_status solve_grid_device(Plan *p, const double *s, double *pout, cudaStream_t st) {
+  const long long nc = p->ncells;
+  sum_kernel<<<grid_for(nc, 256), 256, 0, st>>>(nc, s, p->dstats, p->partials, p->counters);
+  count_launch(p);
+  PC_CUDA_TRY(cudaGetLastError());
+  return solve_grid(p, s, pout, false, st);
+}
+
 static pc_status solve_impl(Plan *p, const double *s, double *p_out, pc_stats *stats, cudaStream_t st) {
   const long long nc = p->ncells;
   const bool hs = !is_device_ptr(s), hp = !is_device_ptr(p_out);

@@ -102,6 +102,10 @@ FUNCTIONS = {
     "pc_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "pc_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "pc_set_graphs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "pc_solve_poisson_static": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p]),
     "pc_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
     "pc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pc_last_error_message": (ctypes.c_char_p, []),
@@ -281,6 +285,21 @@ class Plan:
                                     _ptr(p_out, self.shape, torch.float64, "p_out"),
                                     ctypes.byref(st) if st is not None else None, _stream_handle(stream)))
         return p_out, (st.as_dict() if st is not None else None)
+
+
+def solve_poisson_static(dim, n, h, bc_lo, bc_hi, s, p_out, gauge=0, stream=None):
+    """pc_solve_poisson_static: allocation-free FP64 Poisson solve on device tensors."""
+    import torch
+    lib = load()
+    shape = tuple(int(v) for v in n[:dim])
+    nn = (ctypes.c_int64 * 3)(*[int(n[a]) if a < dim else 1 for a in range(3)])
+    hh = (ctypes.c_double * 3)(*[float(h[a]) if a < dim else 1.0 for a in range(3)])
+    lo = (ctypes.c_int * 3)(*[BC[bc_lo[a]] if a < dim else 0 for a in range(3)])
+    hi = (ctypes.c_int * 3)(*[BC[bc_hi[a]] if a < dim else 0 for a in range(3)])
+    _check(lib.pc_solve_poisson_static(dim, nn, hh, lo, hi, int(gauge),
+                                       _ptr(s, shape, torch.float64, "s"),
+                                       _ptr(p_out, shape, torch.float64, "p_out"), _stream_handle(stream)))
+    return p_out
 
 
 def project_batch(plans, args, stream=None):
