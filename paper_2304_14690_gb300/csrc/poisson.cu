@@ -312,7 +312,7 @@ static pc_status launch_pass(Plan *p, int axis, bool fwd, bool div, bool inv, in
   const int tpl = 1 << ilog2((M + kSlotsPerThread - 1) / kSlotsPerThread);
   const int max_lines = 1024 / tpl;
   const int budget = 4096;          // complex slots per tile
-  const int want_ctas = 2 * 152;    // fill both dies of the GPU
+  const int want_ctas = 152;        // at least one CTA per SM on both dies
   long long tiles;
   int L;
   if (A.col) {

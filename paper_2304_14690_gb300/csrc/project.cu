@@ -189,16 +189,32 @@ __device__ __forceinline__ void df_acc(DF &s, float2 w, float2 u) {
 }
 __device__ __forceinline__ double df_value(DF s) { return f2d_bits(s.hi) + f2d_bits(s.lo); }
 
-__global__ void transfer_mixed_kernel(int rows, int K, const int32_t *__restrict__ col,
+// KC > 0: the neighbour count is a compile-time constant and the loop is unrolled, so all
+// index and weight loads are in flight before the dependent gathers (memory-level parallelism).
+template <int KC>
+__global__ void transfer_mixed_kernel(int rows, int Kr, const int32_t *__restrict__ col,
                                       const float2 *__restrict__ w2, const float2 *__restrict__ u2,
                                       double *__restrict__ U) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
+  const int K = KC > 0 ? KC : Kr;
   DF s{0.f, 0.f};
+  if (KC > 0) {
+    int c[KC > 0 ? KC : 1];
+    float2 w[KC > 0 ? KC : 1];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      c[k] = __ldg(col + k * rows + r);
+      w[k] = __ldg(w2 + k * rows + r);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) df_acc(s, w[k], __ldg(u2 + c[k]));
+  } else {
 #pragma unroll 4
-  for (int k = 0; k < K; ++k) {
-    int at = k * rows + r;
-    df_acc(s, __ldg(w2 + at), __ldg(u2 + __ldg(col + at)));
+    for (int k = 0; k < K; ++k) {
+      int at = k * rows + r;
+      df_acc(s, __ldg(w2 + at), __ldg(u2 + __ldg(col + at)));
+    }
   }
   U[r] = df_value(s);
 }
@@ -238,7 +254,7 @@ __device__ __forceinline__ int face_index(const GridDev &g, int axis, const int 
 __global__ void divergence_kernel(GridDev g, const double *U0, const double *U1,
                                   const double *U2, double inv_bdt, double *s, DevStats *stats,
                                   double *partials, unsigned int *counter, int want_sums,
-                                  double inv_ncells) {
+                                  double inv_ncells, float *s32) {
   int i[3];
   double v = 0.0;
   if (cell_of_thread(g, i)) {
@@ -253,6 +269,7 @@ __global__ void divergence_kernel(GridDev g, const double *U0, const double *U1,
     }
     v = acc * inv_bdt;
     s[c] = v;
+    if (s32) s32[c] = d2f_rz_bits(v);   // FP32 copy read by the first FP32 transform pass
   }
   if (want_sums) {
     if (grid_sum(v, partials, counter, &stats->sum_s)) stats->mean_s = stats->sum_s * inv_ncells;
@@ -377,14 +394,19 @@ __global__ void gradient_mixed_kernel(int N, int K, const int32_t *__restrict__ 
                                       VT *__restrict__ fo) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  constexpr int KB = (DIM == 2) ? 9 : 27;   // the 3^d gradient block
+  (void)K;
   DF g[DIM];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) g[a] = DF{0.f, 0.f};
-#pragma unroll 3
-  for (int k = 0; k < K; ++k) {
-    const float2 pv = __ldg(p2 + __ldg(col + k * N + i));
+  int c[KB];
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) df_acc(g[a], __ldg(D2 + (a * K + k) * N + i), pv);
+  for (int k = 0; k < KB; ++k) c[k] = __ldg(col + k * N + i);
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    const float2 pv = __ldg(p2 + c[k]);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) df_acc(g[a], __ldg(D2 + (a * KB + k) * N + i), pv);
   }
   const bool ib = type[i] != PC_NODE_FLUID;
 #pragma unroll
@@ -496,7 +518,7 @@ static void launch_residual(bool singular, bool write_r, bool norm, dim3 cg, dim
 }
 
 static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_final_residual,
-                            cudaStream_t st) {
+                            cudaStream_t st, const float *s32 = nullptr) {
   const long long nc = p->ncells;
   const int T = 256;
   GridDev g = grid_dev(p);
@@ -507,7 +529,8 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
     prof_mark(p, st, 3);
   } else {
     int sweeps = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
-    PC_TRY(solve_fp32_grid(p, SRC_F64_, s64, DST_F64_SET_, pout, st));
+    if (s32) PC_TRY(solve_fp32_grid(p, SRC_F32_, s32, DST_F64_SET_, pout, st));
+    else PC_TRY(solve_fp32_grid(p, SRC_F64_, s64, DST_F64_SET_, pout, st));
     prof_mark(p, st, 3);
     for (int it = 0; it < sweeps; ++it) {
       float *r32 = reinterpret_cast<float *>(p->work64);   // work64 is free in mixed mode
@@ -597,9 +620,17 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   prof_mark(p, st, 0);
   for (int a = 0; a < d; ++a) {
     long long rows = p->nface_total[a];
-    if (mixed)
-      transfer_mixed_kernel<<<grid_for(rows, T), T, 0, st>>>((int)rows, p->K, p->fcol[a], p->fw2[a],
-                                                             p->u2 + (long long)a * N, p->U64[a]);
+    if (mixed) {
+      if (p->K == 12)
+        transfer_mixed_kernel<12><<<grid_for(rows, T), T, 0, st>>>((int)rows, p->K, p->fcol[a], p->fw2[a],
+                                                                   p->u2 + (long long)a * N, p->U64[a]);
+      else if (p->K == 27)
+        transfer_mixed_kernel<27><<<grid_for(rows, T), T, 0, st>>>((int)rows, p->K, p->fcol[a], p->fw2[a],
+                                                                   p->u2 + (long long)a * N, p->U64[a]);
+      else
+        transfer_mixed_kernel<0><<<grid_for(rows, T), T, 0, st>>>((int)rows, p->K, p->fcol[a], p->fw2[a],
+                                                                  p->u2 + (long long)a * N, p->U64[a]);
+    }
     else
       transfer64_kernel<<<grid_for(rows, T), T, 0, st>>>((int)rows, p->K, p->fcol[a], p->fw64[a],
                                                          p->ut64 + (long long)a * N, p->U64[a]);
@@ -611,11 +642,13 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   cell_launch(p, cg, cb);
   divergence_kernel<<<cg, cb, 0, st>>>(g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt),
                                        p->s64, p->dstats, p->partials, p->counters,
-                                       (p->singular || stats) ? 1 : 0, 1.0 / (double)nc);
+                                       (p->singular || stats) ? 1 : 0, 1.0 / (double)nc,
+                                       mixed ? reinterpret_cast<float *>(p->work64) : nullptr);
   count_launch(p);
   prof_mark(p, st, 2);
   PC_CUDA_TRY(cudaGetLastError());
-  PC_TRY(solve_grid(p, p->s64, dp, stats != nullptr, st));
+  PC_TRY(solve_grid(p, p->s64, dp, stats != nullptr, st,
+                    mixed ? reinterpret_cast<const float *>(p->work64) : nullptr));
   const void *ug = du;
   if (p->vdtype == PC_DTYPE_F64) {
     if (mixed) {
