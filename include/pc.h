@@ -141,8 +141,13 @@ typedef struct {
   void *f_ib_out;
 } pc_project_args;
 
-/* count independent projections (each plan with its own arguments) on one stream; the
- * results equal those of count separate pc_project calls. Device pointers only. */
+/* count independent projections (each plan with its own arguments, each plan at most once) on
+ * one stream; the results are bitwise those of count separate pc_project calls. Device pointers
+ * only. Plans in MIXED or FP32 precision are grouped (by dimension, velocity type, neighbour
+ * count and refinement sweeps) and each stage of the pipeline runs as one kernel launch over all
+ * problems of a group; the launch sequence is captured into a CUDA graph when a batch
+ * composition (plans and argument pointers) is first seen, which also allocates its small work
+ * tables, and replayed afterwards (8 compositions are cached). FP64 plans run one by one. */
 pc_status pc_project_batch(int count, pc_plan *const *plans, const pc_project_args *args,
                            void *cuda_stream);
 

@@ -75,6 +75,7 @@ void prof_mark(Plan *p, cudaStream_t st, int tag) {
 
 static void destroy_plan(Plan *p) {
   if (!p) return;
+  batch_forget_plan(p);
   int cur = -1;
   cudaGetDevice(&cur);
   cudaSetDevice(p->device);

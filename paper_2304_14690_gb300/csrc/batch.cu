@@ -1,0 +1,291 @@
+// pc_project_batch: many independent projections with one launch per pipeline stage.
+//
+// Problems of a batch are grouped by (dimension, velocity type, neighbour count, refinement
+// sweeps) among plans in mixed or FP32 precision. For each group every stage of the pipeline
+// (prep, transfer per axis, divergence, each transform pass of each solve, residuals, gauge,
+// split, gradient) is ONE kernel launch over all problems of the group: a segment table maps
+// each block to its problem and problem-local block, and each transform pass reads per-problem
+// pass arguments and (problem, tile) work items. The whole sequence is captured once per batch
+// composition into a CUDA graph and replayed. Each problem keeps the block decomposition of its
+// single-problem launches, so batch results are bitwise those of separate pc_project calls.
+// Plans in FP64 precision run one by one through pc_project.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "passes.cuh"
+#include "pc_internal.cuh"
+
+namespace pc {
+
+namespace {
+
+constexpr int kBatchThreads = 256;   // CTA size of the batched transform passes
+
+struct PassBatch {
+  int args_off = 0;      // index of the first PassArgs of this pass
+  int items_off = 0;
+  int nitems = 0;
+  int threads = 0;
+  size_t smem = 0;
+};
+
+struct Group {
+  std::vector<int> members;
+  int dim = 2, vdtype = 0, K = 12, sweeps = 0;
+  int total[BATCH_STAGES] = {0};
+  BatchProblem *dP = nullptr;
+  int *dseg = nullptr;                  // BATCH_STAGES x (n + 1)
+  PassArgs<float> *dargs = nullptr;
+  int2 *ditems = nullptr;
+  std::vector<std::vector<PassBatch>> solves;   // [solve][pass]
+  bool any_singular = false;
+};
+
+struct Exec {
+  std::vector<Plan *> plans;
+  std::vector<pc_project_args> args;
+  std::vector<Group> groups;
+  std::vector<int> singles;             // problems run through pc_project
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<void *> allocs;
+  unsigned long long stamp = 0;
+  int device = 0;
+};
+
+std::mutex g_mutex;
+std::vector<Exec *> g_cache;
+unsigned long long g_clock = 0;
+constexpr size_t kMaxExecs = 8;
+
+void free_exec(Exec *e) {
+  if (!e) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  cudaSetDevice(e->device);
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  if (e->graph) cudaGraphDestroy(e->graph);
+  if (e->cap) cudaStreamDestroy(e->cap);
+  for (void *a : e->allocs) cudaFree(a);
+  if (cur >= 0) cudaSetDevice(cur);
+  delete e;
+}
+
+bool same_args(const pc_project_args &a, const pc_project_args &b) {
+  return a.dt == b.dt && a.u_star == b.u_star && a.f_ib_in == b.f_ib_in && a.p_out == b.p_out &&
+         a.u_out == b.u_out && a.f_ib_out == b.f_ib_out;
+}
+
+template <typename T>
+pc_status upload(Exec *e, T **dptr, const std::vector<T> &host) {
+  size_t bytes = std::max<size_t>(host.size() * sizeof(T), 16);
+  if (cudaMalloc(reinterpret_cast<void **>(dptr), bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PC_ERR_OUT_OF_MEMORY, "batch table allocation of %zu bytes failed", bytes);
+  }
+  e->allocs.push_back(*dptr);
+  if (!host.empty()) PC_CUDA_TRY(cudaMemcpy(*dptr, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return PC_OK;
+}
+
+bool batchable(const Plan *p) { return p->precision == PC_PREC_MIXED || p->precision == PC_PREC_FP32; }
+
+pc_status build_group(Exec *e, Group &g) {
+  const int n = (int)g.members.size();
+  std::vector<BatchProblem> hp(n);
+  std::vector<int> seg((size_t)BATCH_STAGES * (n + 1), 0);
+  for (int i = 0; i < n; ++i) {
+    const Plan *p = e->plans[g.members[i]];
+    batch_problem_fill(p, e->args[g.members[i]], hp[i]);
+    g.any_singular = g.any_singular || p->singular;
+    int nb[BATCH_STAGES];
+    batch_block_counts(p, nb);
+    for (int s = 0; s < BATCH_STAGES; ++s) seg[(size_t)s * (n + 1) + i + 1] = seg[(size_t)s * (n + 1) + i] + nb[s];
+  }
+  for (int s = 0; s < BATCH_STAGES; ++s) g.total[s] = seg[(size_t)s * (n + 1) + n];
+  PC_TRY(upload(e, &g.dP, hp));
+  PC_TRY(upload(e, &g.dseg, seg));
+  // transform passes of every solve: first solve from the FP32 source copy, then the sweeps
+  std::vector<PassArgs<float>> args;
+  std::vector<int2> items;
+  for (int j = 0; j <= g.sweeps; ++j) {
+    std::vector<PassBatch> passes;
+    std::vector<std::vector<PassSpec>> specs(n);
+    for (int i = 0; i < n; ++i) {
+      Plan *p = e->plans[g.members[i]];
+      const void *src = reinterpret_cast<const float *>(p->work64);
+      specs[i] = solve_pass_specs(p, true, SRC_F32, src, j == 0 ? DST_F64_SET : DST_F64_ADD,
+                                  e->args[g.members[i]].p_out);
+    }
+    const size_t npass = specs[0].size();
+    for (size_t k = 0; k < npass; ++k) {
+      PassBatch pb;
+      pb.args_off = (int)args.size();
+      pb.items_off = (int)items.size();
+      for (int i = 0; i < n; ++i) {
+        PassArgs<float> A;
+        long long tiles;
+        int threads;
+        size_t smem;
+        PC_TRY(build_pass<float>(e->plans[g.members[i]], specs[i][k], A, tiles, threads, smem, kBatchThreads));
+        const int ai = (int)args.size();
+        args.push_back(A);
+        for (long long t = 0; t < tiles; ++t) items.push_back(make_int2(ai, (int)t));
+        pb.threads = std::max(pb.threads, threads);
+        pb.smem = std::max(pb.smem, smem);
+      }
+      pb.nitems = (int)items.size() - pb.items_off;
+      passes.push_back(pb);
+    }
+    g.solves.push_back(passes);
+  }
+  PC_TRY(upload(e, &g.dargs, args));
+  PC_TRY(upload(e, &g.ditems, items));
+  return PC_OK;
+}
+
+pc_status record_group(Exec *e, const Group &g, cudaStream_t st) {
+  const int n = (int)g.members.size();
+  auto seg = [&](int s) { return g.dseg + (size_t)s * (n + 1); };
+  batch_launch(BATCH_ZERO, 0, g.dP, nullptr, n, n, 0, st);
+  batch_launch(BATCH_PREP, g.vdtype, g.dP, seg(BATCH_PREP), n, g.total[BATCH_PREP], 0, st);
+  for (int a = 0; a < g.dim; ++a)
+    batch_launch(BATCH_TRANSFER, g.K, g.dP, seg(BATCH_TRANSFER + a), n, g.total[BATCH_TRANSFER + a], a, st);
+  batch_launch(BATCH_DIVERGENCE, 0, g.dP, seg(BATCH_DIVERGENCE), n, g.total[BATCH_DIVERGENCE], 0, st);
+  for (int j = 0; j <= g.sweeps; ++j) {
+    if (j > 0) batch_launch(BATCH_RESIDUAL, 0, g.dP, seg(BATCH_RESIDUAL), n, g.total[BATCH_RESIDUAL], 0, st);
+    for (const PassBatch &pb : g.solves[j])
+      PC_TRY(launch_batched_pass<float>(g.dargs, g.ditems + pb.items_off, pb.nitems, pb.threads, pb.smem, st));
+  }
+  if (g.any_singular)
+    batch_launch(BATCH_GAUGE_SUM, 0, g.dP, seg(BATCH_GAUGE_SUM), n, g.total[BATCH_GAUGE_SUM], 0, st);
+  batch_launch(BATCH_FINALIZE, 0, g.dP, seg(BATCH_FINALIZE), n, g.total[BATCH_FINALIZE], 0, st);
+  batch_launch(BATCH_GRADIENT, g.dim * 10 + g.vdtype, g.dP, seg(BATCH_GRADIENT), n, g.total[BATCH_GRADIENT], 0, st);
+  PC_CUDA_TRY(cudaGetLastError());
+  return PC_OK;
+}
+
+pc_status build_exec(Exec *e) {
+  const int count = (int)e->plans.size();
+  for (int i = 0; i < count; ++i) {
+    Plan *p = e->plans[i];
+    if (!batchable(p)) { e->singles.push_back(i); continue; }
+    const int sweeps = p->precision == PC_PREC_MIXED ? p->refine_iters : 0;
+    const int K = (p->K == 12 || p->K == 27) ? p->K : 0;
+    Group *g = nullptr;
+    for (Group &c : e->groups)
+      if (c.dim == p->dim && c.vdtype == p->vdtype && c.K == K && c.sweeps == sweeps) g = &c;
+    if (!g) {
+      e->groups.emplace_back();
+      g = &e->groups.back();
+      g->dim = p->dim; g->vdtype = p->vdtype; g->K = K; g->sweeps = sweeps;
+    }
+    g->members.push_back(i);
+  }
+  for (Group &g : e->groups) PC_TRY(build_group(e, g));
+  PC_CUDA_TRY(cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking));
+  if (!e->groups.empty()) {
+    PC_CUDA_TRY(cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal));
+    pc_status s = PC_OK;
+    for (const Group &g : e->groups)
+      if (s == PC_OK) s = record_group(e, g, e->cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(e->cap, &graph);
+    if (s != PC_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return s != PC_OK ? s : fail(PC_ERR_CUDA, "batch capture failed: %s", cudaGetErrorString(ce));
+    }
+    e->graph = graph;
+    PC_CUDA_TRY(cudaGraphInstantiate(&e->exec, graph, 0ULL));
+  }
+  return PC_OK;
+}
+
+}  // namespace
+
+void batch_forget_plan(const Plan *p) {
+  std::lock_guard<std::mutex> lock(g_mutex);
+  for (size_t i = 0; i < g_cache.size();) {
+    Exec *e = g_cache[i];
+    if (std::find(e->plans.begin(), e->plans.end(), p) != e->plans.end()) {
+      free_exec(e);
+      g_cache.erase(g_cache.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+}  // namespace pc
+
+extern "C" pc_status pc_project_batch(int count, pc_plan *const *plans, const pc_project_args *args,
+                                      void *cuda_stream) {
+  using namespace pc;
+  if (count < 0 || (count > 0 && (!plans || !args))) return fail(PC_ERR_INVALID_ARG, "bad batch arguments");
+  if (count == 0) return PC_OK;
+  int device = -1;
+  for (int i = 0; i < count; ++i) {
+    const Plan *p = reinterpret_cast<const Plan *>(plans[i]);
+    if (!p) return fail(PC_ERR_INVALID_ARG, "plan %d is NULL", i);
+    if (!args[i].u_star || !args[i].p_out || !args[i].u_out || !(args[i].dt > 0.0))
+      return fail(PC_ERR_INVALID_ARG, "batch entry %d: u_star, p_out, u_out and dt > 0 are required", i);
+    if (device < 0) device = p->device;
+    if (p->device != device) return fail(PC_ERR_INVALID_ARG, "all plans of a batch must be on one device");
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return fail(PC_ERR_INVALID_ARG, "a plan appears twice in one batch");
+    for (const void *ptr : {args[i].u_star, args[i].f_ib_in, (const void *)args[i].p_out, (const void *)args[i].u_out,
+                            (const void *)args[i].f_ib_out}) {
+      if (!ptr) continue;
+      cudaPointerAttributes at;
+      if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess ||
+          !(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return fail(PC_ERR_INVALID_ARG, "batch entry %d: pc_project_batch takes device pointers only", i);
+      }
+    }
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return fail(PC_ERR_CUDA, "cannot select device %d", device);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Exec *e = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    for (Exec *c : g_cache) {
+      if ((int)c->plans.size() != count) continue;
+      bool same = true;
+      for (int i = 0; i < count && same; ++i)
+        same = c->plans[i] == reinterpret_cast<Plan *>(plans[i]) && same_args(c->args[i], args[i]);
+      if (same) { e = c; break; }
+    }
+    if (!e) {
+      e = new Exec();
+      e->device = device;
+      for (int i = 0; i < count; ++i) {
+        e->plans.push_back(reinterpret_cast<Plan *>(plans[i]));
+        e->args.push_back(args[i]);
+      }
+      pc_status s = build_exec(e);
+      if (s != PC_OK) {
+        free_exec(e);
+        return s;
+      }
+      if (g_cache.size() >= kMaxExecs) {
+        auto old = std::min_element(g_cache.begin(), g_cache.end(),
+                                    [](const Exec *a, const Exec *b) { return a->stamp < b->stamp; });
+        free_exec(*old);
+        g_cache.erase(old);
+      }
+      g_cache.push_back(e);
+    }
+    e->stamp = ++g_clock;
+  }
+  if (e->exec) PC_CUDA_TRY(cudaGraphLaunch(e->exec, st));
+  for (int i : e->singles) {
+    pc_status s = pc_project(plans[i], args[i].dt, args[i].u_star, args[i].f_ib_in, args[i].p_out, args[i].u_out,
+                             args[i].f_ib_out, nullptr, cuda_stream);
+    if (s != PC_OK) return s;
+  }
+  return PC_OK;
+}

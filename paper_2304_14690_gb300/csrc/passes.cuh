@@ -1,0 +1,64 @@
+// Descriptors of one transform pass (see poisson.cu) shared with the batched executor.
+#pragma once
+
+#include <vector>
+
+#include "fft.cuh"
+#include "pc_internal.cuh"
+
+namespace pc {
+
+enum SrcMode { SRC_F32 = 0, SRC_F64 = 1, SRC_WORK = 2 };
+enum DstMode { DST_WORK = 0, DST_F64_SET = 1, DST_F64_ADD = 2 };
+
+template <typename Real>
+struct PassArgs {
+  using T = typename Cplx<Real>::T;
+  int axis, kind, n, M, nst;
+  StageInfo st[kMaxRadices];
+  const T *tw;
+  int dim;
+  int shape[3];
+  int stride;           // element stride along the axis
+  int inner;            // column tiles: number of line positions f (= stride)
+  int lines;            // row tiles: number of lines
+  int L;                // lines per tile (power of two)
+  int lbits;            // log2(L)
+  int tpl_bits;         // log2(threads per line)
+  int col;              // 1: column tile
+  int tiles_per_outer;  // column tiles: ceil(inner / L)
+  int do_fwd, do_div, do_inv;
+  const Real *lam[3];
+  int singular;
+  int src_mode;
+  const void *src;
+  int dst_mode;
+  void *dst;
+  Real out_scale;       // normalisation of the inverse (2/n)
+};
+
+// One pass of a solve: axis, phases, source and destination.
+struct PassSpec {
+  int axis;
+  bool fwd, div, inv;
+  int src_mode;
+  const void *src;
+  int dst_mode;
+  void *dst;
+};
+
+// The passes of one solve of plan p from src to dst, in launch order.
+std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, const void *src,
+                                       int dst_mode, void *dst);
+// Fill the kernel arguments and launch shape of one pass (no launch). batch_threads > 0 sizes
+// the tile to fill a CTA of that many threads (batched launches); 0 sizes it so that the
+// problem alone fills the GPU.
+template <typename Real>
+pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long long &tiles, int &threads,
+                     size_t &smem, int batch_threads);
+// One launch of the batched pass kernel over items (args index, tile).
+template <typename Real>
+pc_status launch_batched_pass(const PassArgs<Real> *dargs, const int2 *ditems, int nitems, int threads,
+                              size_t smem, cudaStream_t st);
+
+}  // namespace pc

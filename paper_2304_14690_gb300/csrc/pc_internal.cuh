@@ -184,6 +184,56 @@ pc_status solve_fp64(Plan *p, const double *s_dev, double *p_dev, bool from_face
                      cudaStream_t st);
 pc_status solve_mixed(Plan *p, const double *s_dev, double *p_dev, bool from_faces,
                       int sweeps, cudaStream_t st);
+// ----------------------------------------------------------------------------- batches
+// Stages of the batched pipeline (one launch per stage for all problems of a batch).
+enum BatchStage {
+  BATCH_ZERO = 0, BATCH_PREP = 1, BATCH_TRANSFER = 2 /* +axis */, BATCH_DIVERGENCE = 5, BATCH_RESIDUAL = 6,
+  BATCH_GAUGE_SUM = 7, BATCH_FINALIZE = 8, BATCH_GRADIENT = 9, BATCH_STAGES = 10
+};
+
+// Cell-grid geometry and strides shared by the per-cell kernels (project.cu).
+struct GridDev {
+  int dim;
+  int n[3];           // cells per axis, padded: n3[0..2] with the last axis fastest
+  int nf[3];          // faces along each axis (n or n+1)
+  int cs[3];          // cell strides
+  int fs[3][3];       // fs[a][b]: stride of axis b in the face array of axis a
+  int periodic[3];
+  int lo_kind[3], hi_kind[3];   // 0 Neumann, 1 Dirichlet (ghost sign), ignored when periodic
+  double inv_h[3], inv_h2[3];
+};
+
+// Per-problem parameters of a batched launch (device array, one entry per problem).
+struct BatchProblem {
+  GridDev g;
+  int dim, N, ncells, K, Kg, singular, gmode;
+  unsigned cgx, cgy, cgz;         // cell-grid launch shape of the problem
+  const void *u, *f;
+  void *uo, *fo;
+  double *p;
+  double dt, inv_dt, beta, inv_bdt, inv_ncells;
+  float2 *u2;
+  const int32_t *fcol[3];
+  const float2 *fw2[3];
+  double *U64[3];
+  int frows[3];
+  double *s64;
+  float *s32, *r32;
+  float2 *p2;
+  const int32_t *ncol;
+  const float2 *nD2;
+  const uint8_t *ntype;
+  DevStats *ds;
+  double *partials;
+  unsigned int *counters;
+};
+
+void batch_launch(int stage, int variant, const BatchProblem *P, const int *seg, int count, int total_blocks,
+                  int extra, cudaStream_t st);
+void batch_block_counts(const Plan *p, int *nb);
+void batch_problem_fill(const Plan *p, const pc_project_args &a, BatchProblem &q);
+void batch_forget_plan(const Plan *p);
+
 // Solve of device arrays for a plan description built by the caller (project.cu).
 pc_status solve_grid_device(Plan *p, const double *s, double *pout, cudaStream_t st);
 pc_status prepare_kernels();

@@ -17,38 +17,10 @@
 
 #include "fft.cuh"
 #include "numeric.cuh"
+#include "passes.cuh"
 #include "pc_internal.cuh"
 
 namespace pc {
-
-enum SrcMode { SRC_F32 = 0, SRC_F64 = 1, SRC_WORK = 2 };
-enum DstMode { DST_WORK = 0, DST_F64_SET = 1, DST_F64_ADD = 2 };
-
-template <typename Real>
-struct PassArgs {
-  using T = typename Cplx<Real>::T;
-  int axis, kind, n, M, nst;
-  StageInfo st[kMaxRadices];
-  const T *tw;
-  int dim;
-  int shape[3];
-  int stride;           // element stride along the axis
-  int inner;            // column tiles: number of line positions f (= stride)
-  int lines;            // row tiles: number of lines
-  int L;                // lines per tile (power of two)
-  int lbits;            // log2(L)
-  int tpl_bits;         // log2(threads per line)
-  int col;              // 1: column tile
-  int tiles_per_outer;  // column tiles: ceil(inner / L)
-  int do_fwd, do_div, do_inv;
-  const Real *lam[3];
-  int singular;
-  int src_mode;
-  const void *src;
-  int dst_mode;
-  void *dst;
-  Real out_scale;       // normalisation of the inverse (2/n)
-};
 
 // Source element gi in the pass precision (FP64 sources enter FP32 passes truncated to 24 bits,
 // by integer operations; the refinement corrects what that drops).
@@ -69,22 +41,24 @@ constexpr int kLoadsPerThread = 2 * kSlotsPerThread;   // n / tpl <= 8
 // One axis pass over a tile of lines: [forward transform] [eigenvalue division] [inverse].
 // Dynamic shared memory: L*M complex slots, then per line the eigenvalue sum of the other
 // axes, the line's base cell index (-1 for lines past a ragged end) and its zero-mode flag.
+// Threads beyond L * tpl (a batched launch sized for a larger tile) take part in the barriers
+// only.
 template <typename Real>
-__global__ void __launch_bounds__(1024) axis_pass(PassArgs<Real> A) {
+__device__ __forceinline__ void axis_pass_body(const PassArgs<Real> &A, const int tile, unsigned char *smem_raw) {
   using T = typename Cplx<Real>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T *buf = reinterpret_cast<T *>(smem_raw);
   Real *lamo = reinterpret_cast<Real *>(buf + A.L * A.M);
   int *lbase = reinterpret_cast<int *>(lamo + A.L);
   int *lzero = lbase + A.L;
   const int t = threadIdx.x;
+  const bool active = t < (A.L << A.tpl_bits);
   TileGeom g;
   g.L = A.L;
   g.M = A.M;
   g.tpl = 1 << A.tpl_bits;
   if (A.col) { g.es = A.L; g.ls = 1; g.line = t & (A.L - 1); g.lane = t >> A.lbits; }
   else { g.es = 1; g.ls = A.M; g.line = t >> A.tpl_bits; g.lane = t & (g.tpl - 1); }
-  const int tile = blockIdx.x;
+  if (!active) { g.line = 0; g.lane = 1 << 24; }   // every position loop is empty
   const int n = A.n;
 
   if (t < A.L) {
@@ -117,7 +91,7 @@ __global__ void __launch_bounds__(1024) axis_pass(PassArgs<Real> A) {
   __syncthreads();
   const int line = g.line;
   const int base = lbase[line];
-  const bool valid = base >= 0;
+  const bool valid = active && base >= 0;
   const int stride = A.stride;
   const bool fft_inv_dir = !(A.kind == KIND_ND || A.kind == KIND_DN);
 
@@ -203,6 +177,29 @@ __global__ void __launch_bounds__(1024) axis_pass(PassArgs<Real> A) {
   }
 }
 
+template <typename Real>
+__global__ void __launch_bounds__(1024) axis_pass(PassArgs<Real> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  axis_pass_body<Real>(A, blockIdx.x, smem_raw);
+}
+
+// Batched pass: CTA b processes tile items[b].y of the pass described by args[items[b].x] (one
+// launch for every problem of a batch; each problem keeps its own tile shape).
+template <typename Real>
+__global__ void __launch_bounds__(1024) axis_pass_batched(const PassArgs<Real> *__restrict__ args,
+                                                          const int2 *__restrict__ items) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) PassArgs<Real> A;
+  const int2 it = items[blockIdx.x];
+  {
+    const unsigned *src = reinterpret_cast<const unsigned *>(args + it.x);
+    unsigned *dst = reinterpret_cast<unsigned *>(&A);
+    for (int w = threadIdx.x; w < (int)(sizeof(PassArgs<Real>) / 4); w += blockDim.x) dst[w] = __ldg(src + w);
+  }
+  __syncthreads();
+  axis_pass_body<Real>(A, it.y, smem_raw);
+}
+
 // ----------------------------------------------------------------------------- host side
 
 static void radix_plan(int M, int *radix, int &nr) {
@@ -276,11 +273,15 @@ pc_status build_axis_tables(Plan *p) {
 }
 
 template <typename Real>
-static pc_status launch_pass(Plan *p, int axis, bool fwd, bool div, bool inv, int src_mode,
-                             const void *src, int dst_mode, void *dst, cudaStream_t st) {
+pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long long &tiles, int &threads,
+                     size_t &smem, int batch_threads) {
   using T = typename Cplx<Real>::T;
+  const int axis = ps.axis;
+  const bool fwd = ps.fwd, div = ps.div, inv = ps.inv;
+  const int src_mode = ps.src_mode, dst_mode = ps.dst_mode;
+  const void *src = ps.src;
+  void *dst = ps.dst;
   const AxisInfo &ax = p->ax[axis];
-  PassArgs<Real> A;
   memset(&A, 0, sizeof(A));
   A.axis = axis;
   A.kind = ax.kind;
@@ -313,14 +314,15 @@ static pc_status launch_pass(Plan *p, int axis, bool fwd, bool div, bool inv, in
   const int max_lines = 1024 / tpl;
   const int budget = 4096;          // complex slots per tile
   const int want_ctas = 152;        // at least one CTA per SM on both dies
-  long long tiles;
   int L;
   if (A.col) {
     // 32-byte row segments when the grid allows it, fewer lines when CTAs would be too few
     L = (sizeof(Real) == 8) ? 4 : 8;
     while (L * 2 <= 32 && L * 2 * M <= budget && L * 2 <= max_lines) L *= 2;
     long long outer = p->ncells / ((long long)stride * ax.n);
-    while (L > 1 && outer * ((stride + L - 1) / L) < want_ctas) L /= 2;
+    if (batch_threads > 0) L = 32;   // a batch fills its CTAs from many problems
+    while (L > 1 && batch_threads <= 0 && outer * ((stride + L - 1) / L) < want_ctas) L /= 2;
+    while (L > 1 && batch_threads > 0 && L * tpl > batch_threads) L /= 2;
     while (L > 1 && (L * M > budget || L > max_lines)) L /= 2;
     if (L > stride) L = 1 << (ilog2(stride + 1) - 1);
     A.inner = stride;
@@ -332,7 +334,8 @@ static pc_status launch_pass(Plan *p, int axis, bool fwd, bool div, bool inv, in
     if (L < 1) L = 1;
     L = 1 << (ilog2(L + 1) - 1);
     while (L > max_lines) L /= 2;
-    while (L > 1 && (lines + L - 1) / L < want_ctas) L /= 2;
+    while (L > 1 && batch_threads <= 0 && (lines + L - 1) / L < want_ctas) L /= 2;
+    while (L > 1 && batch_threads > 0 && L * tpl > batch_threads) L /= 2;
     A.lines = (int)lines;
     tiles = (lines + L - 1) / L;
   }
@@ -350,48 +353,77 @@ static pc_status launch_pass(Plan *p, int axis, bool fwd, bool div, bool inv, in
   A.dst_mode = dst_mode;
   A.dst = dst;
   A.out_scale = (Real)inv_scale(ax.kind, ax.n);
-  const int threads = L * tpl;
+  threads = L * tpl;
   if (threads > 1024 || L * M > 2 * budget)
     return fail(PC_ERR_UNSUPPORTED, "axis %d: tile of %d x %d too large", axis, L, M);
-  size_t smem = (size_t)L * M * sizeof(T) + (size_t)L * (sizeof(Real) + 2 * sizeof(int));
+  smem = (size_t)L * M * sizeof(T) + (size_t)L * (sizeof(Real) + 2 * sizeof(int));
+  return PC_OK;
+}
+
+template pc_status build_pass<float>(const Plan *, const PassSpec &, PassArgs<float> &, long long &, int &, size_t &, int);
+template pc_status build_pass<double>(const Plan *, const PassSpec &, PassArgs<double> &, long long &, int &, size_t &, int);
+
+template <typename Real>
+static pc_status launch_pass(Plan *p, const PassSpec &ps, cudaStream_t st) {
+  PassArgs<Real> A;
+  long long tiles;
+  int threads;
+  size_t smem;
+  PC_TRY(build_pass<Real>(p, ps, A, tiles, threads, smem, 0));
   axis_pass<Real><<<(unsigned)tiles, threads, smem, st>>>(A);
   count_launch(p);
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
 }
 
+template <typename Real>
+pc_status launch_batched_pass(const PassArgs<Real> *dargs, const int2 *ditems, int nitems, int threads,
+                              size_t smem, cudaStream_t st) {
+  if (nitems <= 0) return PC_OK;
+  axis_pass_batched<Real><<<(unsigned)nitems, threads, smem, st>>>(dargs, ditems);
+  PC_CUDA_TRY(cudaGetLastError());
+  return PC_OK;
+}
+template pc_status launch_batched_pass<float>(const PassArgs<float> *, const int2 *, int, int, size_t, cudaStream_t);
+template pc_status launch_batched_pass<double>(const PassArgs<double> *, const int2 *, int, int, size_t, cudaStream_t);
+
 // Kernel attributes set once per device, before any stream capture.
 pc_status prepare_kernels() {
   PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   return PC_OK;
+}
+
+std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, const void *src,
+                                       int dst_mode, void *dst) {
+  std::vector<PassSpec> v;
+  void *work = fp32 ? (void *)p->work32 : (void *)p->work64;
+  const int d = p->dim;
+  int cur_mode = src_mode;
+  const void *cur = src;
+  for (int a = d - 1; a >= 1; --a) {     // forward passes: last axis down to axis 1
+    v.push_back(PassSpec{a, true, false, false, cur_mode, cur, DST_WORK, work});
+    cur_mode = SRC_WORK;
+    cur = work;
+  }
+  v.push_back(PassSpec{0, true, true, true, cur_mode, cur, DST_WORK, work});   // axis 0 with the division
+  for (int a = 1; a < d; ++a) {         // inverse passes: axis 1 up to the last axis
+    const bool final_pass = (a == d - 1);
+    v.push_back(PassSpec{a, false, false, true, SRC_WORK, work, final_pass ? dst_mode : DST_WORK,
+                         final_pass ? dst : work});
+  }
+  return v;
 }
 
 // Full solve with Real precision: src (cells, src_mode) -> dst (dst_mode).
 template <typename Real>
 static pc_status solve_real(Plan *p, int src_mode, const void *src, int dst_mode, void *dst,
                             cudaStream_t st) {
-  Real *work = (Real *)(sizeof(Real) == 8 ? (void *)p->work64 : (void *)p->work32);
-  const int d = p->dim;
-  if (d == 1) return fail(PC_ERR_UNSUPPORTED, "dim 1");
-  // forward passes: last axis down to 1
-  int cur_mode = src_mode;
-  const void *cur = src;
-  for (int a = d - 1; a >= 1; --a) {
-    PC_TRY(launch_pass<Real>(p, a, true, false, false, cur_mode, cur, DST_WORK, work, st));
-    cur_mode = SRC_WORK;
-    cur = work;
-  }
-  // axis 0: forward, divide, inverse
-  bool last_pass = (d == 1);
-  (void)last_pass;
-  PC_TRY(launch_pass<Real>(p, 0, true, true, true, cur_mode, cur, DST_WORK, work, st));
-  // inverse passes: axis 1 .. last; the last one writes the destination
-  for (int a = 1; a < d; ++a) {
-    bool final_pass = (a == d - 1);
-    PC_TRY(launch_pass<Real>(p, a, false, false, true, SRC_WORK, work,
-                             final_pass ? dst_mode : DST_WORK, final_pass ? dst : (void *)work, st));
-  }
+  if (p->dim < 2) return fail(PC_ERR_UNSUPPORTED, "dim 1");
+  for (const PassSpec &ps : solve_pass_specs(p, sizeof(Real) == 4, src_mode, src, dst_mode, dst))
+    PC_TRY(launch_pass<Real>(p, ps, st));
   return PC_OK;
 }
 

@@ -29,6 +29,16 @@ pc_status solve_fp64_grid(Plan *p, const double *s, double *pout, cudaStream_t s
 enum { SRC_F32_ = 0, SRC_F64_ = 1 };
 enum { DST_F64_SET_ = 1, DST_F64_ADD_ = 2 };
 
+// ----------------------------------------------------------------------------- block context
+// Kernels address their block through a VBlock: the hardware block in a single-problem launch,
+// or the problem-local block of a batched launch (one launch for many problems, batch.cu).
+struct VBlock {
+  unsigned x, y, z, nx, ny, nz;
+};
+__device__ __forceinline__ VBlock hw_block() {
+  return VBlock{blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z};
+}
+
 // ----------------------------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -55,11 +65,11 @@ __device__ void block_sum_add(double v, double *dst) {
 // Deterministic grid-wide sum: every block writes its partial (fixed shuffle tree), the last
 // block to finish sums all partials in block order and writes *dst, then resets the counter.
 // Results are bitwise reproducible, unlike concurrent floating-point atomics.
-__device__ bool grid_sum(double v, double *partials, unsigned int *counter, double *dst) {
+__device__ bool grid_sum(double v, double *partials, unsigned int *counter, double *dst, const VBlock &vb) {
   __shared__ double sh[32];
   __shared__ bool last;
-  const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
-  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const unsigned nblk = vb.nx * vb.ny * vb.nz;
+  const unsigned bid = vb.x + vb.nx * (vb.y + vb.ny * vb.z);
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();
@@ -123,9 +133,9 @@ __device__ __forceinline__ float2 as_pair(float v) { return make_float2(v, 0.0f)
 // u~ = u* + dt f~; FP64 copy (FP64 path, SPLIT = false) or (hi, lo) FP32 pair (mixed). Compile-
 // time variants keep the common case (no force, no statistics) free of FP64 arithmetic.
 template <typename VT, bool HAS_F, bool STATS, bool SPLIT>
-__global__ void prep_kernel(int count, const VT *__restrict__ u, const VT *__restrict__ f, double dt,
+__device__ __forceinline__ void prep_kernel_body(const VBlock &vb, int count, const VT *__restrict__ u, const VT *__restrict__ f, double dt,
                             double *__restrict__ ut64, float2 *__restrict__ u2, DevStats *stats) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = vb.x * blockDim.x + threadIdx.x;
   double m = 0.0;
   if (i < count) {
     const VT ui = u[i];
@@ -140,6 +150,11 @@ __global__ void prep_kernel(int count, const VT *__restrict__ u, const VT *__res
     }
   }
   if (STATS) block_max_update(m, &stats->max_u);
+}
+template <typename VT, bool HAS_F, bool STATS, bool SPLIT>
+__global__ void prep_kernel(int count, const VT *__restrict__ u, const VT *__restrict__ f, double dt,
+                            double *__restrict__ ut64, float2 *__restrict__ u2, DevStats *stats) {
+  prep_kernel_body<VT, HAS_F, STATS, SPLIT>(hw_block(), count, u, f, dt, ut64, u2, stats);
 }
 
 template <typename VT>
@@ -192,10 +207,10 @@ __device__ __forceinline__ double df_value(DF s) { return f2d_bits(s.hi) + f2d_b
 // KC > 0: the neighbour count is a compile-time constant and the loop is unrolled, so all
 // index and weight loads are in flight before the dependent gathers (memory-level parallelism).
 template <int KC>
-__global__ void transfer_mixed_kernel(int rows, int Kr, const int32_t *__restrict__ col,
+__device__ __forceinline__ void transfer_mixed_kernel_body(const VBlock &vb, int rows, int Kr, const int32_t *__restrict__ col,
                                       const float2 *__restrict__ w2, const float2 *__restrict__ u2,
                                       double *__restrict__ U) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = vb.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   const int K = KC > 0 ? KC : Kr;
   DF s{0.f, 0.f};
@@ -218,26 +233,23 @@ __global__ void transfer_mixed_kernel(int rows, int Kr, const int32_t *__restric
   }
   U[r] = df_value(s);
 }
+template <int KC>
+__global__ void transfer_mixed_kernel(int rows, int Kr, const int32_t *__restrict__ col,
+                                      const float2 *__restrict__ w2, const float2 *__restrict__ u2,
+                                      double *__restrict__ U) {
+  transfer_mixed_kernel_body<KC>(hw_block(), rows, Kr, col, w2, u2, U);
+}
 
 // ----------------------------------------------------------------------------- grid geometry
 // Cells are addressed by a 3D launch (x: last axis, y: middle axis, z: first axis of a 3D grid;
-// 2D grids use x and y), so no kernel divides an index. Axes are padded to three with extent 1.
-struct GridDev {
-  int dim;
-  int n[3];           // cells per axis, padded: n3[0..2] with the last axis fastest
-  int nf[3];          // faces along each axis (n or n+1)
-  int cs[3];          // cell strides
-  int fs[3][3];       // fs[a][b]: stride of axis b in the face array of axis a
-  int periodic[3];
-  int lo_kind[3], hi_kind[3];   // 0 Neumann, 1 Dirichlet (ghost sign), ignored when periodic
-  double inv_h[3], inv_h2[3];
-};
+// 2D grids use x and y), so no kernel divides an index. Axes are padded to three with extent 1
+// (GridDev, pc_internal.cuh).
 
 // Cell multi-index of this thread (false when outside the grid).
-__device__ __forceinline__ bool cell_of_thread(const GridDev &g, int *i) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g.dim == 2) { i[0] = blockIdx.y; i[1] = x; i[2] = 0; return x < g.n[1]; }
-  i[0] = blockIdx.z; i[1] = blockIdx.y; i[2] = x;
+__device__ __forceinline__ bool cell_of_thread(const GridDev &g, int *i, const VBlock &vb) {
+  const int x = vb.x * blockDim.x + threadIdx.x;
+  if (g.dim == 2) { i[0] = vb.y; i[1] = x; i[2] = 0; return x < g.n[1]; }
+  i[0] = vb.z; i[1] = vb.y; i[2] = x;
   return x < g.n[2];
 }
 __device__ __forceinline__ int cell_index(const GridDev &g, const int *i) {
@@ -251,13 +263,13 @@ __device__ __forceinline__ int face_index(const GridDev &g, int axis, const int 
 }
 
 // s = D_h U / (beta dt), plus sum(s), sum(s^2).
-__global__ void divergence_kernel(GridDev g, const double *U0, const double *U1,
+__device__ __forceinline__ void divergence_kernel_body(const VBlock &vb, GridDev g, const double *U0, const double *U1,
                                   const double *U2, double inv_bdt, double *s, DevStats *stats,
                                   double *partials, unsigned int *counter, int want_sums,
                                   double inv_ncells, float *s32) {
   int i[3];
   double v = 0.0;
-  if (cell_of_thread(g, i)) {
+  if (cell_of_thread(g, i, vb)) {
     const int c = cell_index(g, i);
     const double *U[3] = {U0, U1, U2};
     double acc = 0.0;
@@ -272,18 +284,30 @@ __global__ void divergence_kernel(GridDev g, const double *U0, const double *U1,
     if (s32) s32[c] = d2f_rz_bits(v);   // FP32 copy read by the first FP32 transform pass
   }
   if (want_sums) {
-    if (grid_sum(v, partials, counter, &stats->sum_s)) stats->mean_s = stats->sum_s * inv_ncells;
-    grid_sum(v * v, partials + (gridDim.x * gridDim.y * gridDim.z), counter + 1, &stats->sum_s2);
+    if (grid_sum(v, partials, counter, &stats->sum_s, vb)) stats->mean_s = stats->sum_s * inv_ncells;
+    grid_sum(v * v, partials + (vb.nx * vb.ny * vb.nz), counter + 1, &stats->sum_s2, vb);
   }
 }
 
+__global__ void divergence_kernel(GridDev g, const double *U0, const double *U1,
+                                  const double *U2, double inv_bdt, double *s, DevStats *stats,
+                                  double *partials, unsigned int *counter, int want_sums,
+                                  double inv_ncells, float *s32) {
+  divergence_kernel_body(hw_block(), g, U0, U1, U2, inv_bdt, s, stats, partials, counter, want_sums, inv_ncells, s32);
+}
+
 // Sum and sum of squares of a cell array (the source of pc_solve_poisson), and its mean.
+__device__ __forceinline__ void sum_kernel_body(const VBlock &vb, long long count, const double *x, DevStats *stats, double *partials,
+                           unsigned int *counter) {
+  long long c = (long long)vb.x * blockDim.x + threadIdx.x;
+  double v = (c < count) ? x[c] : 0.0;
+  if (grid_sum(v, partials, counter, &stats->sum_s, vb)) stats->mean_s = stats->sum_s / (double)count;
+  grid_sum(v * v, partials + vb.nx, counter + 1, &stats->sum_s2, vb);
+}
+
 __global__ void sum_kernel(long long count, const double *x, DevStats *stats, double *partials,
                            unsigned int *counter) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double v = (c < count) ? x[c] : 0.0;
-  if (grid_sum(v, partials, counter, &stats->sum_s)) stats->mean_s = stats->sum_s / (double)count;
-  grid_sum(v * v, partials + gridDim.x, counter + 1, &stats->sum_s2);
+  sum_kernel_body(hw_block(), count, x, stats, partials, counter);
 }
 
 // L_h p at cell i (ghost rules: Neumann p_ghost = p_edge, Dirichlet -p_edge, periodic wrap).
@@ -312,36 +336,47 @@ __device__ __forceinline__ double lap_at(const GridDev &g, const double *p, cons
 // r = s - mean(s) - L_h p in FP64, stored as FP32 (truncated by integer operations) for the
 // next FP32 solve; optionally ||r||^2.
 template <bool SINGULAR, bool WRITE_R, bool NORM>
-__global__ void residual_kernel(GridDev g, const double *__restrict__ s, const double *__restrict__ p,
+__device__ __forceinline__ void residual_kernel_body(const VBlock &vb, GridDev g, const double *__restrict__ s, const double *__restrict__ p,
                                 float *__restrict__ r, const DevStats *stats, double *res2,
                                 double *partials, unsigned int *counter) {
   int i[3];
   double v = 0.0;
-  if (cell_of_thread(g, i)) {
+  if (cell_of_thread(g, i, vb)) {
     const int c = cell_index(g, i);
     const double pc = p[c];
     const double sc = SINGULAR ? s[c] - stats->mean_s : s[c];
     v = sc - lap_at(g, p, i, c, pc);
     if (WRITE_R) r[c] = d2f_rz_bits(v);
   }
-  if (NORM) grid_sum(v * v, partials, counter, res2);
+  if (NORM) grid_sum(v * v, partials, counter, res2, vb);
+}
+template <bool SINGULAR, bool WRITE_R, bool NORM>
+__global__ void residual_kernel(GridDev g, const double *__restrict__ s, const double *__restrict__ p,
+                                float *__restrict__ r, const DevStats *stats, double *res2,
+                                double *partials, unsigned int *counter) {
+  residual_kernel_body<SINGULAR, WRITE_R, NORM>(hw_block(), g, s, p, r, stats, res2, partials, counter);
 }
 
 // Sum of p (and the corner value); the reducing block stores the gauge constant.
-__global__ void gauge_sum_kernel(long long ncells, const double *p, DevStats *stats, double *partials,
+__device__ __forceinline__ void gauge_sum_kernel_body(const VBlock &vb, long long ncells, const double *p, DevStats *stats, double *partials,
                                  unsigned int *counter, int gauge_mode) {
-  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long c = (long long)vb.x * blockDim.x + threadIdx.x;
   double v = (c < ncells) ? p[c] : 0.0;
   if (c == 0) stats->corner_p = v;
-  if (grid_sum(v, partials, counter, &stats->sum_p))
+  if (grid_sum(v, partials, counter, &stats->sum_p, vb))
     stats->shift = (gauge_mode == 1) ? stats->sum_p / (double)ncells : p[0];
+}
+
+__global__ void gauge_sum_kernel(long long ncells, const double *p, DevStats *stats, double *partials,
+                                 unsigned int *counter, int gauge_mode) {
+  gauge_sum_kernel_body(hw_block(), ncells, p, stats, partials, counter, gauge_mode);
 }
 
 // p -= shift (gauge), and the (hi, lo) FP32 split of p for the compensated gradient.
 template <bool GAUGE, bool SPLIT>
-__global__ void finalize_p_kernel(int ncells, double *__restrict__ p, const DevStats *stats,
+__device__ __forceinline__ void finalize_p_kernel_body(const VBlock &vb, int ncells, double *__restrict__ p, const DevStats *stats,
                                   float2 *__restrict__ p2) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  int c = vb.x * blockDim.x + threadIdx.x;
   if (c >= ncells) return;
   double v = p[c];
   if (GAUGE) {
@@ -349,6 +384,11 @@ __global__ void finalize_p_kernel(int ncells, double *__restrict__ p, const DevS
     p[c] = v;
   }
   if (SPLIT) p2[c] = as_pair(v);
+}
+template <bool GAUGE, bool SPLIT>
+__global__ void finalize_p_kernel(int ncells, double *__restrict__ p, const DevStats *stats,
+                                  float2 *__restrict__ p2) {
+  finalize_p_kernel_body<GAUGE, SPLIT>(hw_block(), ncells, p, stats, p2);
 }
 
 // ----------------------------------------------------------------------------- gradient
@@ -387,12 +427,12 @@ __global__ void gradient64_kernel(int N, int K, const int32_t *__restrict__ col,
 }
 
 template <typename VT, int DIM>
-__global__ void gradient_mixed_kernel(int N, int K, const int32_t *__restrict__ col,
+__device__ __forceinline__ void gradient_mixed_kernel_body(const VBlock &vb, int N, int K, const int32_t *__restrict__ col,
                                       const float2 *__restrict__ D2, const float2 *__restrict__ p2,
                                       const uint8_t *__restrict__ type, const VT *__restrict__ u,
                                       double inv_dt, double dt, double beta, VT *__restrict__ uo,
                                       VT *__restrict__ fo) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = vb.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   constexpr int KB = (DIM == 2) ? 9 : 27;   // the 3^d gradient block
   (void)K;
@@ -422,6 +462,14 @@ __global__ void gradient_mixed_kernel(int N, int K, const int32_t *__restrict__ 
     }
   }
 }
+template <typename VT, int DIM>
+__global__ void gradient_mixed_kernel(int N, int K, const int32_t *__restrict__ col,
+                                      const float2 *__restrict__ D2, const float2 *__restrict__ p2,
+                                      const uint8_t *__restrict__ type, const VT *__restrict__ u,
+                                      double inv_dt, double dt, double beta, VT *__restrict__ uo,
+                                      VT *__restrict__ fo) {
+  gradient_mixed_kernel_body<VT, DIM>(hw_block(), N, K, col, D2, p2, type, u, inv_dt, dt, beta, uo, fo);
+}
 
 // ----------------------------------------------------------------------------- check
 // max over cells of |D_h (U - beta dt G_h p)|; wall faces carry no flux and no gradient.
@@ -429,7 +477,7 @@ __global__ void div_check_kernel(GridDev g, const double *U0, const double *U1,
                                  const double *U2, const double *p, double bdt, DevStats *stats) {
   int i[3];
   double v = 0.0;
-  if (cell_of_thread(g, i)) {
+  if (cell_of_thread(g, i, hw_block())) {
     const int c = cell_index(g, i);
     const double *U[3] = {U0, U1, U2};
     double pc = p[c];
@@ -447,6 +495,162 @@ __global__ void div_check_kernel(GridDev g, const double *U0, const double *U1,
     v = fabs(acc);
   }
   block_max_update(v, &stats->max_div);
+}
+
+static GridDev grid_dev(const Plan *p);
+static void cell_launch(const Plan *p, dim3 &grid, dim3 &block);
+
+// ----------------------------------------------------------------------------- batched kernels
+// One launch per pipeline stage for a whole batch of problems. seg[p] is the first block of
+// problem p in the launch (seg[count] = total blocks); each problem keeps exactly the block
+// decomposition of its single-problem launch, so sums and results are bitwise the same.
+__device__ __forceinline__ int batch_problem_of(const int *seg, int count, int b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(seg + mid) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ VBlock flat_block(int local, int nblocks) {
+  return VBlock{(unsigned)local, 0u, 0u, (unsigned)nblocks, 1u, 1u};
+}
+__device__ __forceinline__ VBlock cell_block(const BatchProblem &q, int local) {
+  const unsigned x = local % q.cgx, yz = local / q.cgx;
+  return VBlock{x, yz % q.cgy, yz / q.cgy, q.cgx, q.cgy, q.cgz};
+}
+
+__global__ void batch_zero_stats(const BatchProblem *__restrict__ P) {
+  unsigned *w = reinterpret_cast<unsigned *>(P[blockIdx.x].ds);
+  for (int k = threadIdx.x; k < (int)(sizeof(DevStats) / 4); k += blockDim.x) w[k] = 0u;
+}
+
+template <typename VT>
+__global__ void batch_prep(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
+  const int pi = batch_problem_of(seg, count, blockIdx.x);
+  const BatchProblem &q = P[pi];
+  const int nb = seg[pi + 1] - seg[pi];
+  const VBlock vb = flat_block(blockIdx.x - seg[pi], nb);
+  const int cnt = q.dim * q.N;
+  if (q.f) prep_kernel_body<VT, true, false, true>(vb, cnt, (const VT *)q.u, (const VT *)q.f, q.dt, nullptr, q.u2, nullptr);
+  else prep_kernel_body<VT, false, false, true>(vb, cnt, (const VT *)q.u, nullptr, q.dt, nullptr, q.u2, nullptr);
+}
+
+template <int KC>
+__global__ void batch_transfer(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count, int a) {
+  const int pi = batch_problem_of(seg, count, blockIdx.x);
+  const BatchProblem &q = P[pi];
+  const VBlock vb = flat_block(blockIdx.x - seg[pi], seg[pi + 1] - seg[pi]);
+  transfer_mixed_kernel_body<KC>(vb, q.frows[a], q.K, q.fcol[a], q.fw2[a], q.u2 + (long long)a * q.N, q.U64[a]);
+}
+
+__global__ void batch_divergence(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
+  const int pi = batch_problem_of(seg, count, blockIdx.x);
+  const BatchProblem &q = P[pi];
+  const VBlock vb = cell_block(q, blockIdx.x - seg[pi]);
+  divergence_kernel_body(vb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, q.s64, q.ds, q.partials, q.counters,
+                         q.singular, q.inv_ncells, q.s32);
+}
+
+__global__ void batch_residual(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
+  const int pi = batch_problem_of(seg, count, blockIdx.x);
+  const BatchProblem &q = P[pi];
+  const VBlock vb = cell_block(q, blockIdx.x - seg[pi]);
+  if (q.singular) residual_kernel_body<true, true, false>(vb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
+  else residual_kernel_body<false, true, false>(vb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
+}
+
+__global__ void batch_gauge_sum(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
+  const int pi = batch_problem_of(seg, count, blockIdx.x);
+  const BatchProblem &q = P[pi];
+  const VBlock vb = flat_block(blockIdx.x - seg[pi], seg[pi + 1] - seg[pi]);
+  gauge_sum_kernel_body(vb, q.ncells, q.p, q.ds, q.partials, q.counters, q.gmode);
+}
+
+__global__ void batch_finalize(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
+  const int pi = batch_problem_of(seg, count, blockIdx.x);
+  const BatchProblem &q = P[pi];
+  const VBlock vb = flat_block(blockIdx.x - seg[pi], seg[pi + 1] - seg[pi]);
+  if (q.gmode) finalize_p_kernel_body<true, true>(vb, q.ncells, q.p, q.ds, q.p2);
+  else finalize_p_kernel_body<false, true>(vb, q.ncells, q.p, q.ds, q.p2);
+}
+
+template <typename VT, int DIM>
+__global__ void batch_gradient(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
+  const int pi = batch_problem_of(seg, count, blockIdx.x);
+  const BatchProblem &q = P[pi];
+  const VBlock vb = flat_block(blockIdx.x - seg[pi], seg[pi + 1] - seg[pi]);
+  gradient_mixed_kernel_body<VT, DIM>(vb, q.N, q.Kg, q.ncol, q.nD2, q.p2, q.ntype, (const VT *)q.u, q.inv_dt,
+                                      q.dt, q.beta, (VT *)q.uo, (VT *)q.fo);
+}
+
+// Launchers used by the batch executor (batch.cu).
+void batch_launch(int stage, int variant, const BatchProblem *P, const int *seg, int count, int total_blocks,
+                  int extra, cudaStream_t st) {
+  if (total_blocks <= 0) return;
+  const int T = 256;
+  switch (stage) {
+    case BATCH_ZERO: batch_zero_stats<<<count, 64, 0, st>>>(P); break;
+    case BATCH_PREP:
+      if (variant == PC_DTYPE_F64) batch_prep<double><<<total_blocks, T, 0, st>>>(P, seg, count);
+      else batch_prep<float><<<total_blocks, T, 0, st>>>(P, seg, count);
+      break;
+    case BATCH_TRANSFER:
+      if (variant == 12) batch_transfer<12><<<total_blocks, T, 0, st>>>(P, seg, count, extra);
+      else if (variant == 27) batch_transfer<27><<<total_blocks, T, 0, st>>>(P, seg, count, extra);
+      else batch_transfer<0><<<total_blocks, T, 0, st>>>(P, seg, count, extra);
+      break;
+    case BATCH_DIVERGENCE: batch_divergence<<<total_blocks, T, 0, st>>>(P, seg, count); break;
+    case BATCH_RESIDUAL: batch_residual<<<total_blocks, T, 0, st>>>(P, seg, count); break;
+    case BATCH_GAUGE_SUM: batch_gauge_sum<<<total_blocks, T, 0, st>>>(P, seg, count); break;
+    case BATCH_FINALIZE: batch_finalize<<<total_blocks, T, 0, st>>>(P, seg, count); break;
+    case BATCH_GRADIENT:
+      if (variant == 2 * 10 + PC_DTYPE_F64) batch_gradient<double, 2><<<total_blocks, T, 0, st>>>(P, seg, count);
+      else if (variant == 3 * 10 + PC_DTYPE_F64) batch_gradient<double, 3><<<total_blocks, T, 0, st>>>(P, seg, count);
+      else if (variant == 2 * 10 + PC_DTYPE_F32) batch_gradient<float, 2><<<total_blocks, T, 0, st>>>(P, seg, count);
+      else batch_gradient<float, 3><<<total_blocks, T, 0, st>>>(P, seg, count);
+      break;
+  }
+}
+
+// Block counts of each stage for one problem (identical to the single-problem launches).
+void batch_block_counts(const Plan *p, int *nb) {
+  const long long N = p->N, nc = p->ncells;
+  dim3 cg, cb;
+  cell_launch(p, cg, cb);
+  nb[BATCH_ZERO] = 1;
+  nb[BATCH_PREP] = grid_for((long long)p->dim * N, 256);
+  for (int a = 0; a < 3; ++a) nb[BATCH_TRANSFER + a] = a < p->dim ? grid_for(p->nface_total[a], 256) : 0;
+  nb[BATCH_DIVERGENCE] = (int)(cg.x * cg.y * cg.z);
+  nb[BATCH_RESIDUAL] = (int)(cg.x * cg.y * cg.z);
+  nb[BATCH_GAUGE_SUM] = p->singular ? grid_for(nc, 256) : 0;
+  nb[BATCH_FINALIZE] = grid_for(nc, 256);
+  nb[BATCH_GRADIENT] = grid_for(N, 256);
+}
+
+void batch_problem_fill(const Plan *p, const pc_project_args &a, BatchProblem &q) {
+  memset(&q, 0, sizeof(q));
+  q.g = grid_dev(p);
+  dim3 cg, cb;
+  cell_launch(p, cg, cb);
+  q.cgx = cg.x; q.cgy = cg.y; q.cgz = cg.z;
+  q.dim = p->dim; q.N = (int)p->N; q.ncells = (int)p->ncells; q.K = p->K; q.Kg = p->Kg;
+  q.singular = p->singular;
+  q.gmode = p->singular ? (p->gauge == 1 ? 2 : 1) : 0;
+  q.u = a.u_star; q.f = a.f_ib_in; q.uo = a.u_out; q.fo = a.f_ib_out; q.p = a.p_out;
+  q.dt = a.dt; q.inv_dt = 1.0 / a.dt; q.beta = p->beta; q.inv_bdt = 1.0 / (p->beta * a.dt);
+  q.inv_ncells = 1.0 / (double)p->ncells;
+  q.u2 = p->u2;
+  for (int k = 0; k < 3; ++k) {
+    q.fcol[k] = p->fcol[k]; q.fw2[k] = p->fw2[k]; q.U64[k] = p->U64[k];
+    q.frows[k] = (int)p->nface_total[k];
+  }
+  q.s64 = p->s64;
+  q.s32 = reinterpret_cast<float *>(p->work64);
+  q.r32 = reinterpret_cast<float *>(p->work64);
+  q.p2 = p->p2; q.ncol = p->ncol; q.nD2 = p->nD2; q.ntype = p->ntype;
+  q.ds = p->dstats; q.partials = p->partials; q.counters = p->counters;
 }
 
 // ----------------------------------------------------------------------------- host
@@ -826,13 +1030,3 @@ extern "C" pc_status pc_solve_poisson(pc_plan *plan, const double *s, double *p_
   return pc::solve_impl(p, s, p_out, stats, (cudaStream_t)cuda_stream);
 }
 
-extern "C" pc_status pc_project_batch(int count, pc_plan *const *plans, const pc_project_args *args,
-                                      void *cuda_stream) {
-  if (count < 0 || (count > 0 && (!plans || !args))) return pc::fail(PC_ERR_INVALID_ARG, "bad batch arguments");
-  for (int i = 0; i < count; ++i) {
-    pc_status s = pc_project(plans[i], args[i].dt, args[i].u_star, args[i].f_ib_in, args[i].p_out,
-                             args[i].u_out, args[i].f_ib_out, nullptr, cuda_stream);
-    if (s != PC_OK) return s;
-  }
-  return PC_OK;
-}

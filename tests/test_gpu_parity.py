@@ -206,19 +206,32 @@ def test_graph_equals_direct(env, problems):
 
 
 def test_batch_equals_single(env, problems):
+    """pc_project_batch runs one launch per stage for all problems; every result is bitwise the
+    result of a separate pc_project call (mixed and FP32 plans batched, 2D and 3D groups, with and
+    without IB force, singular and non-singular; an FP64 plan runs on its own)."""
     pc, torch, dev = env
     plans, args, singles = [], [], []
-    for prob, _, _ in problems[:4]:
-        plan = pc.Plan(prob, precision="mixed")
+    extra = [wl.generic(dim=2, n=(64, 96), bc_lo=("P", "P"), bc_hi=("P", "P"), seed=41),
+             wl.generic(dim=2, n=(32, 48), bc_lo=("W", "W"), bc_hi=("W", "W"), seed=42,
+                        obstacles=[("circle", (1.0, 1.5), 0.3)], with_force=True)]
+    probs = [pr for pr, _, _ in problems] + extra
+    precisions = ["mixed"] * (len(probs) - 2) + ["fp32", "fp64"]
+    for prob, prec in zip(probs, precisions):
+        plan = pc.Plan(prob, precision=prec)
         u = torch.as_tensor(prob.u_star, device=dev)
+        f = torch.as_tensor(prob.f_ib, device=dev) if prob.f_ib is not None else None
         p, uo, fo = plan.alloc_outputs()
         plans.append(plan)
-        args.append(dict(dt=prob.dt, u_star=u, p=p, u=uo, f=fo))
-        singles.append(plan.project(u)[:3])
-    pc.project_batch(plans, args)
-    torch.cuda.synchronize()
-    for a, s in zip(args, singles):
-        assert torch.equal(a["p"], s[0]) and torch.equal(a["u"], s[1]) and torch.equal(a["f"], s[2])
+        args.append(dict(dt=prob.dt, u_star=u, f_ib=f, p=p, u=uo, f=fo))
+        plan.graphs(False)
+        singles.append(plan.project(u, f)[:3])
+    for rep in range(2):               # second call replays the cached batch graph
+        for a in args:
+            a["p"].zero_(); a["u"].zero_(); a["f"].zero_()
+        pc.project_batch(plans, args)
+        torch.cuda.synchronize()
+        for a, s in zip(args, singles):
+            assert torch.equal(a["p"], s[0]) and torch.equal(a["u"], s[1]) and torch.equal(a["f"], s[2])
     for pl in plans:
         pl.close()
 
