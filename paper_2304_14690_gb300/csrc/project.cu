@@ -64,22 +64,47 @@ __device__ void block_sum_add(double v, double *dst) {
 }
 // Deterministic grid-wide sum: every block writes its partial (fixed shuffle tree), the last
 // block to finish sums all partials in block order and writes *dst, then resets the counter.
-// Results are bitwise reproducible, unlike concurrent floating-point atomics.
+// Results are bitwise reproducible, unlike concurrent floating-point atomics. Inside a block the
+// sum runs in double-float FP32 arithmetic (TwoSum; Knuth) on the exact FP32 split of each
+// value, so the FP64 pipe sees one add per block instead of a shuffle tree per thread; the
+// relative error stays below about 2^-44 of the sum of magnitudes.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+__device__ __forceinline__ void df_add(float &hi, float &lo, float bhi, float blo) {
+  float s, e;
+  two_sum(hi, bhi, s, e);
+  e += lo + blo;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+__device__ __forceinline__ void warp_sum_df(float &hi, float &lo) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_down_sync(0xffffffffu, hi, o), l2 = __shfl_down_sync(0xffffffffu, lo, o);
+    df_add(hi, lo, h2, l2);
+  }
+}
 __device__ bool grid_sum(double v, double *partials, unsigned int *counter, double *dst, const VBlock &vb) {
-  __shared__ double sh[32];
+  __shared__ float2 sh[32];
   __shared__ bool last;
   const unsigned nblk = vb.nx * vb.ny * vb.nz;
   const unsigned bid = vb.x + vb.nx * (vb.y + vb.ny * vb.z);
-  v = warp_sum(v);
+  float hi, lo;
+  split_f64(v, hi, lo);
+  warp_sum_df(hi, lo);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   __syncthreads();
-  if (lane == 0) sh[wid] = v;
+  if (lane == 0) sh[wid] = make_float2(hi, lo);
   __syncthreads();
   if (wid == 0) {
-    v = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
-    v = warp_sum(v);
+    const float2 w = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : make_float2(0.f, 0.f);
+    hi = w.x;
+    lo = w.y;
+    warp_sum_df(hi, lo);
     if (lane == 0) {
-      partials[bid] = v;
+      partials[bid] = f2d_bits(hi) + f2d_bits(lo);
       __threadfence();
       last = atomicAdd(counter, 1u) == nblk - 1;
     }
@@ -87,15 +112,9 @@ __device__ bool grid_sum(double v, double *partials, unsigned int *counter, doub
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  double acc = 0.0;
-  for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x) acc += ((volatile double *)partials)[b];
-  acc = warp_sum(acc);
-  __syncthreads();
-  if (lane == 0) sh[wid] = acc;
-  __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    for (unsigned b = 0; b < nblk; ++b) t += ((volatile double *)partials)[b];
     *dst = t;
     *counter = 0u;
     return true;
@@ -245,10 +264,13 @@ __global__ void transfer_mixed_kernel(int rows, int Kr, const int32_t *__restric
 // 2D grids use x and y), so no kernel divides an index. Axes are padded to three with extent 1
 // (GridDev, pc_internal.cuh).
 
-// Cell multi-index of this thread (false when outside the grid).
+// Cell multi-index of this thread (false when outside the grid). The cell kernels are templated
+// on the dimension and unroll their axis loops, so the index arrays stay in registers (a
+// runtime-indexed array would be placed in local memory).
+template <int DIM>
 __device__ __forceinline__ bool cell_of_thread(const GridDev &g, int *i, const VBlock &vb) {
   const int x = vb.x * blockDim.x + threadIdx.x;
-  if (g.dim == 2) { i[0] = vb.y; i[1] = x; i[2] = 0; return x < g.n[1]; }
+  if (DIM == 2) { i[0] = vb.y; i[1] = x; i[2] = 0; return x < g.n[1]; }
   i[0] = vb.z; i[1] = vb.y; i[2] = x;
   return x < g.n[2];
 }
@@ -258,22 +280,25 @@ __device__ __forceinline__ int cell_index(const GridDev &g, const int *i) {
 // Linear index of face fi along `axis` with the other coordinates of cell i.
 __device__ __forceinline__ int face_index(const GridDev &g, int axis, const int *i, int fi) {
   int f = 0;
+#pragma unroll
   for (int b = 0; b < 3; ++b) f += ((b == axis) ? fi : i[b]) * g.fs[axis][b];
   return f;
 }
 
 // s = D_h U / (beta dt), plus sum(s), sum(s^2).
+template <int DIM>
 __device__ __forceinline__ void divergence_kernel_body(const VBlock &vb, GridDev g, const double *U0, const double *U1,
                                   const double *U2, double inv_bdt, double *s, DevStats *stats,
                                   double *partials, unsigned int *counter, int want_sums,
                                   double inv_ncells, float *s32) {
   int i[3];
   double v = 0.0;
-  if (cell_of_thread(g, i, vb)) {
+  if (cell_of_thread<DIM>(g, i, vb)) {
     const int c = cell_index(g, i);
     const double *U[3] = {U0, U1, U2};
     double acc = 0.0;
-    for (int a = 0; a < g.dim; ++a) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
       int hi = i[a] + 1;
       if (g.periodic[a] && hi == g.n[a]) hi = 0;
       double d = U[a][face_index(g, a, i, hi)] - U[a][face_index(g, a, i, i[a])];
@@ -289,11 +314,12 @@ __device__ __forceinline__ void divergence_kernel_body(const VBlock &vb, GridDev
   }
 }
 
+template <int DIM>
 __global__ void divergence_kernel(GridDev g, const double *U0, const double *U1,
                                   const double *U2, double inv_bdt, double *s, DevStats *stats,
                                   double *partials, unsigned int *counter, int want_sums,
                                   double inv_ncells, float *s32) {
-  divergence_kernel_body(hw_block(), g, U0, U1, U2, inv_bdt, s, stats, partials, counter, want_sums, inv_ncells, s32);
+  divergence_kernel_body<DIM>(hw_block(), g, U0, U1, U2, inv_bdt, s, stats, partials, counter, want_sums, inv_ncells, s32);
 }
 
 // Sum and sum of squares of a cell array (the source of pc_solve_poisson), and its mean.
@@ -323,9 +349,11 @@ __device__ __forceinline__ void neighbours(const GridDev &g, const double *p, co
   else pr = g.hi_kind[a] ? -pc : pc;
 }
 
+template <int DIM>
 __device__ __forceinline__ double lap_at(const GridDev &g, const double *p, const int *i, int c, double pc) {
   double acc = 0.0;
-  for (int a = 0; a < g.dim; ++a) {
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
     double pl, pr;
     neighbours(g, p, i, c, a, pc, pl, pr);
     acc = fma((pl + pr) - 2.0 * pc, g.inv_h2[a], acc);
@@ -335,26 +363,26 @@ __device__ __forceinline__ double lap_at(const GridDev &g, const double *p, cons
 
 // r = s - mean(s) - L_h p in FP64, stored as FP32 (truncated by integer operations) for the
 // next FP32 solve; optionally ||r||^2.
-template <bool SINGULAR, bool WRITE_R, bool NORM>
+template <int DIM, bool SINGULAR, bool WRITE_R, bool NORM>
 __device__ __forceinline__ void residual_kernel_body(const VBlock &vb, GridDev g, const double *__restrict__ s, const double *__restrict__ p,
                                 float *__restrict__ r, const DevStats *stats, double *res2,
                                 double *partials, unsigned int *counter) {
   int i[3];
   double v = 0.0;
-  if (cell_of_thread(g, i, vb)) {
+  if (cell_of_thread<DIM>(g, i, vb)) {
     const int c = cell_index(g, i);
     const double pc = p[c];
     const double sc = SINGULAR ? s[c] - stats->mean_s : s[c];
-    v = sc - lap_at(g, p, i, c, pc);
+    v = sc - lap_at<DIM>(g, p, i, c, pc);
     if (WRITE_R) r[c] = d2f_rz_bits(v);
   }
   if (NORM) grid_sum(v * v, partials, counter, res2, vb);
 }
-template <bool SINGULAR, bool WRITE_R, bool NORM>
+template <int DIM, bool SINGULAR, bool WRITE_R, bool NORM>
 __global__ void residual_kernel(GridDev g, const double *__restrict__ s, const double *__restrict__ p,
                                 float *__restrict__ r, const DevStats *stats, double *res2,
                                 double *partials, unsigned int *counter) {
-  residual_kernel_body<SINGULAR, WRITE_R, NORM>(hw_block(), g, s, p, r, stats, res2, partials, counter);
+  residual_kernel_body<DIM, SINGULAR, WRITE_R, NORM>(hw_block(), g, s, p, r, stats, res2, partials, counter);
 }
 
 // Sum of p (and the corner value); the reducing block stores the gauge constant.
@@ -473,16 +501,18 @@ __global__ void gradient_mixed_kernel(int N, int K, const int32_t *__restrict__ 
 
 // ----------------------------------------------------------------------------- check
 // max over cells of |D_h (U - beta dt G_h p)|; wall faces carry no flux and no gradient.
+template <int DIM>
 __global__ void div_check_kernel(GridDev g, const double *U0, const double *U1,
                                  const double *U2, const double *p, double bdt, DevStats *stats) {
   int i[3];
   double v = 0.0;
-  if (cell_of_thread(g, i, hw_block())) {
+  if (cell_of_thread<DIM>(g, i, hw_block())) {
     const int c = cell_index(g, i);
     const double *U[3] = {U0, U1, U2};
     double pc = p[c];
     double acc = 0.0;
-    for (int a = 0; a < g.dim; ++a) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
       // gradient on the low and high faces of the cell
       double pl, pr;
       neighbours(g, p, i, c, a, pc, pl, pr);
@@ -549,16 +579,25 @@ __global__ void batch_divergence(const BatchProblem *__restrict__ P, const int *
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
   const VBlock vb = cell_block(q, blockIdx.x - seg[pi]);
-  divergence_kernel_body(vb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, q.s64, q.ds, q.partials, q.counters,
-                         q.singular, q.inv_ncells, q.s32);
+  if (q.g.dim == 2)
+    divergence_kernel_body<2>(vb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, q.s64, q.ds, q.partials, q.counters,
+                              q.singular, q.inv_ncells, q.s32);
+  else
+    divergence_kernel_body<3>(vb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, q.s64, q.ds, q.partials, q.counters,
+                              q.singular, q.inv_ncells, q.s32);
 }
 
 __global__ void batch_residual(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
   const VBlock vb = cell_block(q, blockIdx.x - seg[pi]);
-  if (q.singular) residual_kernel_body<true, true, false>(vb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
-  else residual_kernel_body<false, true, false>(vb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
+  if (q.g.dim == 2) {
+    if (q.singular) residual_kernel_body<2, true, true, false>(vb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
+    else residual_kernel_body<2, false, true, false>(vb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
+  } else {
+    if (q.singular) residual_kernel_body<3, true, true, false>(vb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
+    else residual_kernel_body<3, false, true, false>(vb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
+  }
 }
 
 __global__ void batch_gauge_sum(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
@@ -710,7 +749,11 @@ static bool is_device_ptr(const void *ptr) {
 static void launch_residual(bool singular, bool write_r, bool norm, dim3 cg, dim3 cb, cudaStream_t st,
                             const GridDev &g, const double *s, const double *p, float *r, DevStats *ds,
                             double *res2, double *partials, unsigned int *counters) {
-#define PC_RES(S, W, N) residual_kernel<S, W, N><<<cg, cb, 0, st>>>(g, s, p, r, ds, res2, partials, counters)
+#define PC_RES(S, W, N)                                                                      \
+  do {                                                                                       \
+    if (g.dim == 2) residual_kernel<2, S, W, N><<<cg, cb, 0, st>>>(g, s, p, r, ds, res2, partials, counters); \
+    else residual_kernel<3, S, W, N><<<cg, cb, 0, st>>>(g, s, p, r, ds, res2, partials, counters); \
+  } while (0)
   if (singular) {
     if (write_r) { if (norm) PC_RES(true, true, true); else PC_RES(true, true, false); }
     else PC_RES(true, false, true);
@@ -844,10 +887,12 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   GridDev g = grid_dev(p);
   dim3 cg, cb;
   cell_launch(p, cg, cb);
-  divergence_kernel<<<cg, cb, 0, st>>>(g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt),
-                                       p->s64, p->dstats, p->partials, p->counters,
-                                       (p->singular || stats) ? 1 : 0, 1.0 / (double)nc,
-                                       mixed ? reinterpret_cast<float *>(p->work64) : nullptr);
+  {
+    auto divk = (d == 2) ? divergence_kernel<2> : divergence_kernel<3>;
+    divk<<<cg, cb, 0, st>>>(g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt), p->s64, p->dstats,
+                            p->partials, p->counters, (p->singular || stats) ? 1 : 0, 1.0 / (double)nc,
+                            mixed ? reinterpret_cast<float *>(p->work64) : nullptr);
+  }
   count_launch(p);
   prof_mark(p, st, 2);
   PC_CUDA_TRY(cudaGetLastError());
@@ -874,7 +919,8 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   count_launch(p);
   prof_mark(p, st, 6);
   if (stats) {
-    div_check_kernel<<<cg, cb, 0, st>>>(g, p->U64[0], p->U64[1], p->U64[2], dp, p->beta * dt, p->dstats);
+    auto chk = (d == 2) ? div_check_kernel<2> : div_check_kernel<3>;
+    chk<<<cg, cb, 0, st>>>(g, p->U64[0], p->U64[1], p->U64[2], dp, p->beta * dt, p->dstats);
     count_launch(p);
     prof_mark(p, st, 7);
   }
