@@ -207,6 +207,25 @@ pc_status pc_profile_read(pc_plan *plan, pc_profile *out);
  * plan). Results are identical with graphs on or off. */
 pc_status pc_set_graphs(pc_plan *plan, int on);
 
+/* Schedule of the transform passes (§2.3 three-step solve). Every pass along `axis` gives each
+ * thread at most `slots` complex slots of a line (2, 4, 8 or 16): this fixes the threads per
+ * line and the radix schedule of the FFT (largest power-of-two radices up to min(slots, 16),
+ * then 3 and 5). `precision` selects the FP64 passes (PC_PREC_FP64) or the FP32 passes (the
+ * other two). A schedule is part of the plan: single and batched calls use it alike, and changing
+ * it drops the plan's captured CUDA graphs. Results change only by rounding between schedules.
+ * Errors: PC_ERR_INVALID_ARG for a bad axis or slot count; a schedule whose tile does not fit the
+ * kernels fails at the next call with PC_ERR_UNSUPPORTED. Defaults: 4 (FP32), 2 (FP64). */
+pc_status pc_plan_set_transform_slots(pc_plan *plan, int axis, pc_precision precision, int slots);
+pc_status pc_plan_get_transform_slots(const pc_plan *plan, int axis, pc_precision precision,
+                                      int *slots_out);
+
+/* Autotuner: times the plan's own transform solve (FP64 for FP64 plans, FP32 otherwise) on
+ * `cuda_stream` for every slot count of every axis in turn (coordinate descent, two rounds),
+ * keeps the fastest schedule and returns its milliseconds per solve in *best_ms_out
+ * (nullable). It synchronises the stream, overwrites the plan's workspace, and must not run
+ * during a stream capture or while a call of the plan is in flight. */
+pc_status pc_plan_autotune(pc_plan *plan, void *cuda_stream, double *best_ms_out);
+
 /* Device bytes held by the plan. */
 pc_status pc_plan_bytes(const pc_plan *plan, size_t *bytes_out);
 

@@ -73,6 +73,15 @@ void prof_mark(Plan *p, cudaStream_t st, int tag) {
   s->n++;
 }
 
+void plan_drop_graphs(Plan *p) {
+  batch_forget_plan(p);
+  for (int i = 0; i < kGraphCache; ++i) {
+    if (p->graphs[i].exec) cudaGraphExecDestroy(p->graphs[i].exec);
+    if (p->graphs[i].graph) cudaGraphDestroy(p->graphs[i].graph);
+    p->graphs[i] = GraphEntry{};
+  }
+}
+
 static void destroy_plan(Plan *p) {
   if (!p) return;
   batch_forget_plan(p);
@@ -84,10 +93,7 @@ static void destroy_plan(Plan *p) {
       for (int e = 0; e < kProfEvents; ++e) cudaEventDestroy(p->slots[i].ev[e]);
     delete[] p->slots;
   }
-  for (int i = 0; i < kGraphCache; ++i) {
-    if (p->graphs[i].exec) cudaGraphExecDestroy(p->graphs[i].exec);
-    if (p->graphs[i].graph) cudaGraphDestroy(p->graphs[i].graph);
-  }
+  plan_drop_graphs(p);
   if (p->cap_ev_made)
     for (int e = 0; e < kProfEvents; ++e) cudaEventDestroy(p->cap_ev[e]);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);

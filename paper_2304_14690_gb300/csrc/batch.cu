@@ -29,6 +29,7 @@ struct PassBatch {
   int nitems = 0;
   int threads = 0;
   size_t smem = 0;
+  int emax = 1;          // largest slots per thread among the problems' passes
 };
 
 struct Group {
@@ -136,6 +137,7 @@ pc_status build_group(Exec *e, Group &g) {
         for (long long t = 0; t < tiles; ++t) items.push_back(make_int2(ai, (int)t));
         pb.threads = std::max(pb.threads, threads);
         pb.smem = std::max(pb.smem, smem);
+        pb.emax = std::max(pb.emax, A.emax);
       }
       pb.nitems = (int)items.size() - pb.items_off;
       passes.push_back(pb);
@@ -158,7 +160,7 @@ pc_status record_group(Exec *e, const Group &g, cudaStream_t st) {
   for (int j = 0; j <= g.sweeps; ++j) {
     if (j > 0) batch_launch(BATCH_RESIDUAL, 0, g.dP, seg(BATCH_RESIDUAL), n, g.total[BATCH_RESIDUAL], 0, st);
     for (const PassBatch &pb : g.solves[j])
-      PC_TRY(launch_batched_pass<float>(g.dargs, g.ditems + pb.items_off, pb.nitems, pb.threads, pb.smem, st));
+      PC_TRY(launch_batched_pass<float>(g.dargs, g.ditems + pb.items_off, pb.nitems, pb.threads, pb.smem, pb.emax, st));
   }
   if (g.any_singular)
     batch_launch(BATCH_GAUGE_SUM, 0, g.dP, seg(BATCH_GAUGE_SUM), n, g.total[BATCH_GAUGE_SUM], 0, st);

@@ -2,11 +2,11 @@
 //
 // A CTA holds a tile of L lines of one axis in shared memory as complex slots: line l,
 // slot q at buf[l*ls + q*es] (row tiles: es = 1, ls = M; column tiles: es = L, ls = 1).
-// Every thread works on one line of the tile: column tiles map consecutive threads to
-// consecutive lines (coalesced global access across adjacent lines), row tiles map them to
-// consecutive positions of one line. A thread covers the positions lane, lane + tpl, ... of its
-// line, tpl = threads per line (a power of two, >= M/2), so all index arithmetic is shifts,
-// masks and one multiply-high per FFT stage.
+// Column tiles map consecutive threads to consecutive lines (coalesced global access across
+// adjacent lines), row tiles map them to consecutive positions of one line. A thread covers the
+// positions lane, lane + tpl, ... of its line, tpl = threads per line (a power of two) with at
+// most EMAX slots per thread, so all index arithmetic is shifts, masks and one multiply-high
+// per FFT stage.
 //
 // Every real-to-real transform of length n (n even) runs through one complex FFT of length
 // M = n/2:
@@ -15,8 +15,10 @@
 //   Dir-Dir     DST-II / DST-III (DCT-II of the sign-alternated line, reversed)
 //   Neu-Dir     DCT-IV (self-inverse up to 2/n), half-length complex FFT with pre/post twiddles
 //   Dir-Neu     DST-IV (DCT-IV of the reversed line with alternating output signs)
-// The FFT is a mixed-radix (2,3,4,5) Stockham autosort done in place: every stage reads its
-// butterfly inputs into registers, synchronises, and writes the outputs.
+// The FFT is a mixed-radix Stockham autosort (radices 16, 8, 4, 2, 3, 5) between two shared
+// buffers: every stage reads its butterflies' inputs from one buffer into registers and writes
+// the outputs to the other, one barrier per stage. The radix-8 and radix-16 butterflies run in
+// registers (2 x 4 and 4 x 4 decompositions).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -58,10 +60,6 @@ struct TileGeom {
   int tpl;   // threads per line (position stride)
 };
 
-// Work items a thread keeps in registers across a barrier are bounded by tpl >= M/2: every
-// FFT stage is one butterfly per thread.
-constexpr int kSlotsPerThread = 2;
-
 // One FFT stage: radix R, current span Ns, twiddle stride M/(Ns R). j / Ns is a shift when Ns
 // is a power of two, else a multiply-high by magic = ceil(2^32/Ns) (exact for j < 2^16).
 struct StageInfo {
@@ -86,22 +84,92 @@ __device__ __forceinline__ decltype(T::x) &realref(T *buf, const TileGeom &g, in
   return reinterpret_cast<R *>(buf)[2 * (line * g.ls + (j >> 1) * g.es) + (j & 1)];
 }
 
-// Small DFT of radix R on v[0..R-1] (forward sign -1, inverse +1). Radix 3 and 5 take their
-// roots of unity from the length-M FFT table (M divisible by R).
-template <typename T, int R>
-__device__ __forceinline__ void small_dft(T *v, const T *tw, int M, bool inv) {
+// ----------------------------------------------------------------------------- butterflies
+// Forward transforms use the kernel e^{-2 pi i/R}, inverse ones its conjugate.
+template <typename T, bool INV> __device__ __forceinline__ T rot4(T a) { return INV ? cmul_pi(a) : cmul_mi(a); }
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft4(T &a0, T &a1, T &a2, T &a3) {
+  const T s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  const T s13 = cadd(a1, a3), d13 = rot4<T, INV>(csub(a1, a3));
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, d13);
+  a3 = csub(d02, d13);
+}
+
+// e^{-+2 pi i e/16} for the exponents the radix-8 and radix-16 butterflies use (cosines and
+// sines of multiples of pi/8).
+template <typename T, bool INV>
+__device__ __forceinline__ T w16(int e) {
+  using R = decltype(T::x);
+  const R c1 = (R)0.92387953251128675613, s1 = (R)0.38268343236508977173, r2 = (R)0.70710678118654752440;
+  R re, im;
+  switch (e) {
+    case 1: re = c1; im = -s1; break;
+    case 2: re = r2; im = -r2; break;
+    case 3: re = s1; im = -c1; break;
+    case 4: re = 0; im = -1; break;
+    case 6: re = -r2; im = -r2; break;
+    case 9: re = -c1; im = s1; break;
+    default: re = 1; im = 0; break;
+  }
+  return cmk<T>(re, INV ? -im : im);
+}
+
+// Small DFT of radix R on v[0..R-1], outputs in natural order. Radix 3 and 5 take their roots of
+// unity from the length-M FFT table (M divisible by R).
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void small_dft(T *v, const T *tw, int M) {
   if (R == 2) {
-    T a = v[0], b = v[1];
-    v[0] = cadd(a, b); v[1] = csub(a, b);
+    const T a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
   } else if (R == 4) {
-    T a0 = v[0], a1 = v[1], a2 = v[2], a3 = v[3];
-    T s02 = cadd(a0, a2), d02 = csub(a0, a2);
-    T s13 = cadd(a1, a3), d13 = csub(a1, a3);
-    T rot = inv ? cmul_pi(d13) : cmul_mi(d13);
-    v[0] = cadd(s02, s13);
-    v[2] = csub(s02, s13);
-    v[1] = cadd(d02, rot);
-    v[3] = csub(d02, rot);
+    dft4<T, INV>(v[0], v[1], v[2], v[3]);
+  } else if (R == 8) {
+    // X_{2m} = DFT4(x_k + x_{k+4}), X_{2m+1} = DFT4((x_k - x_{k+4}) w8^k)
+    T u[4], d[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      u[k] = cadd(v[k], v[k + 4]);
+      d[k] = csub(v[k], v[k + 4]);
+    }
+    d[1] = cmul(d[1], w16<T, INV>(2));
+    d[2] = rot4<T, INV>(d[2]);
+    d[3] = cmul(d[3], w16<T, INV>(6));
+    dft4<T, INV>(u[0], u[1], u[2], u[3]);
+    dft4<T, INV>(d[0], d[1], d[2], d[3]);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      v[2 * m] = u[m];
+      v[2 * m + 1] = d[m];
+    }
+  } else if (R == 16) {
+    // input k = k1 + 4 k2, output j = j2 + 4 j1: DFT4 over k2, twiddle w16^(j2 k1), DFT4 over k1
+    T y[4][4];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      y[k1][0] = v[k1];
+      y[k1][1] = v[k1 + 4];
+      y[k1][2] = v[k1 + 8];
+      y[k1][3] = v[k1 + 12];
+      dft4<T, INV>(y[k1][0], y[k1][1], y[k1][2], y[k1][3]);
+    }
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1) {
+#pragma unroll
+      for (int j2 = 1; j2 < 4; ++j2) {
+        if (j2 * k1 == 4) y[k1][j2] = rot4<T, INV>(y[k1][j2]);
+        else y[k1][j2] = cmul(y[k1][j2], w16<T, INV>(j2 * k1));
+      }
+    }
+#pragma unroll
+    for (int j2 = 0; j2 < 4; ++j2) {
+      dft4<T, INV>(y[0][j2], y[1][j2], y[2][j2], y[3][j2]);
+#pragma unroll
+      for (int j1 = 0; j1 < 4; ++j1) v[j2 + 4 * j1] = y[j1][j2];
+    }
   } else {
     T in[R];
 #pragma unroll
@@ -112,59 +180,80 @@ __device__ __forceinline__ void small_dft(T *v, const T *tw, int M, bool inv) {
       T acc = in[0];
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        T w = ldg(&tw[((q * r) % R) * step]);
-        acc = cadd(acc, inv ? cmulc(in[r], w) : cmul(in[r], w));
+        const T w = ldg(&tw[((q * r) % R) * step]);
+        acc = cadd(acc, INV ? cmulc(in[r], w) : cmul(in[r], w));
       }
       v[q] = acc;
     }
   }
 }
 
-// One Stockham stage of radix R over every line of the tile (all threads of the CTA).
-template <typename T, int R, int MAXB>
-__device__ void fft_stage(T *buf, const TileGeom &g, const StageInfo &s, const T *tw, bool inv) {
+// One Stockham stage of radix R from src to dst over every line of the tile. A thread does up to
+// MAXB butterflies (j = lane, lane + tpl, ...). pre (nullable): a slot-wise factor applied to the
+// inputs (the DCT-IV pre-twiddle, folded into the first stage).
+template <typename T, int R, int MAXB, bool INV>
+__device__ __forceinline__ void fft_stage(const T *src, T *dst, const TileGeom &g, const StageInfo &s,
+                                          const T *tw, const T *pre) {
   const int NBl = g.M / R;
-  T v[MAXB][R];
+  const int base = g.line * g.ls;
 #pragma unroll
   for (int b = 0; b < MAXB; ++b) {
-    int j = g.lane + b * g.tpl;
+    const int j = g.lane + b * g.tpl;
     if (j < NBl) {
+      T v[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b][r] = slot(buf, g, g.line, j + r * NBl);
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int b = 0; b < MAXB; ++b) {
-    int j = g.lane + b * g.tpl;
-    if (j < NBl) {
-      int q = s.shift >= 0 ? (j >> s.shift) : (int)__umulhi((unsigned)j, s.magic);
-      int k = j - q * s.Ns;
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        T w = ldg(&tw[r * k * s.stride_m]);
-        v[b][r] = inv ? cmulc(v[b][r], w) : cmul(v[b][r], w);
+      for (int r = 0; r < R; ++r) {
+        const int q = j + r * NBl;
+        v[r] = src[base + q * g.es];
+        if (pre) v[r] = cmul(v[r], ldg(&pre[q]));
       }
-      small_dft<T, R>(v[b], tw, g.M, inv);
-      int base = q * s.Ns * R + k;
+      const int qd = s.shift >= 0 ? (j >> s.shift) : (int)__umulhi((unsigned)j, s.magic);
+      const int k = j - qd * s.Ns;
+      if (s.Ns > 1) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) slot(buf, g, g.line, base + r * s.Ns) = v[b][r];
+        for (int r = 1; r < R; ++r) {
+          const T w = ldg(&tw[r * k * s.stride_m]);
+          v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+        }
+      }
+      small_dft<T, R, INV>(v, tw, g.M);
+      const int ob = qd * s.Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[base + (ob + r * s.Ns) * g.es] = v[r];
     }
   }
   __syncthreads();
 }
 
-// Complex FFT of length g.M on every line (unnormalised).
-template <typename T>
-__device__ void fft_lines(T *buf, const TileGeom &g, const StageInfo *st, int nst, const T *tw,
-                          bool inv) {
+constexpr int cdiv_c(int a, int b) { return (a + b - 1) / b; }
+
+// Complex FFT of length g.M on every line (unnormalised), ping-ponging between a and b; returns
+// the buffer that holds the result. Every thread of the CTA calls it (barriers).
+template <typename T, int EMAX, bool INV>
+__device__ T *fft_run(T *a, T *b, const TileGeom &g, const StageInfo *st, int nst, const T *tw, const T *pre) {
   for (int s = 0; s < nst; ++s) {
     const StageInfo si = st[s];
-    if (si.R == 4) fft_stage<T, 4, 1>(buf, g, si, tw, inv);
-    else if (si.R == 2) fft_stage<T, 2, 1>(buf, g, si, tw, inv);
-    else if (si.R == 3) fft_stage<T, 3, 1>(buf, g, si, tw, inv);
-    else fft_stage<T, 5, 1>(buf, g, si, tw, inv);
+    const T *p0 = (s == 0) ? pre : nullptr;
+    // power-of-two radices above EMAX never occur (radix schedule), so they are not compiled
+    switch (si.R) {
+      case 16:
+        if constexpr (EMAX >= 16) fft_stage<T, 16, cdiv_c(EMAX, 16), INV>(a, b, g, si, tw, p0);
+        break;
+      case 8:
+        if constexpr (EMAX >= 8) fft_stage<T, 8, cdiv_c(EMAX, 8), INV>(a, b, g, si, tw, p0);
+        break;
+      case 4:
+        if constexpr (EMAX >= 4) fft_stage<T, 4, cdiv_c(EMAX, 4), INV>(a, b, g, si, tw, p0);
+        break;
+      case 2: fft_stage<T, 2, cdiv_c(EMAX, 2), INV>(a, b, g, si, tw, p0); break;
+      case 3: fft_stage<T, 3, cdiv_c(EMAX, 3), INV>(a, b, g, si, tw, p0); break;
+      default: fft_stage<T, 5, cdiv_c(EMAX, 5), INV>(a, b, g, si, tw, p0); break;
+    }
+    T *t = a;
+    a = b;
+    b = t;
   }
+  return a;
 }
 
 // ----------------------------------------------------------------------------- forward
@@ -186,249 +275,159 @@ __device__ __forceinline__ void fwd_slot_of(int kind, int n, int j, int &q, int 
   if (kind == KIND_DN) comp ^= 1;
 }
 
-// F2: slot-local pre-twiddle (DCT-IV / DST-IV only).
-template <typename T>
-__device__ void pretwiddle(T *buf, const TileGeom &g, int kind, const T *tw) {
-  if (kind != KIND_ND && kind != KIND_DN) return;
-  const T *t4 = tw + tw_dct4pre(g.M);
-  for (int q = g.lane; q < g.M; q += g.tpl) {
-    T &z = slot(buf, g, g.line, q);
-    z = cmul(z, ldg(&t4[q]));
-  }
-  __syncthreads();
-}
-
-// F4: FFT output -> real spectral coefficients in natural order (in place, via registers).
-template <typename T>
-__device__ void fwd_post(T *buf, const TileGeom &g, int kind, int n, const T *tw) {
+// F4: FFT output (slots of buf) -> real spectral coefficients in natural order, handed to
+// emit(position, value). A thread reads only the slots of its own outputs.
+template <typename T, typename Emit>
+__device__ __forceinline__ void fwd_post(const T *buf, const TileGeom &g, int kind, int n, const T *tw, Emit emit) {
   using R = decltype(T::x);
   const int M = g.M;
-  const int line = g.line;
+  const int base = g.line * g.ls;
+  auto at = [&](int q) { return buf[base + q * g.es]; };
   if (kind == KIND_ND || kind == KIND_DN) {
     // y_q = e^{-i pi q/n} Z_q; X_2q = Re y_q; X_{n-1-2q} = -Im y_q (DCT-IV), +Im y_q (DST-IV)
     const T *tp = tw + tw_dct4post(M);
-    constexpr int MAXI = kSlotsPerThread;
-    T y[MAXI];
-#pragma unroll
-    for (int b = 0; b < MAXI; ++b) {
-      int q = g.lane + b * g.tpl;
-      if (q < M) y[b] = cmul(slot(buf, g, line, q), ldg(&tp[q]));
+    for (int q = g.lane; q < M; q += g.tpl) {
+      const T y = cmul(at(q), ldg(&tp[q]));
+      emit(2 * q, y.x);
+      emit(n - 1 - 2 * q, (kind == KIND_ND) ? -y.y : y.y);
     }
-    __syncthreads();
-#pragma unroll
-    for (int b = 0; b < MAXI; ++b) {
-      int q = g.lane + b * g.tpl;
-      if (q < M) {
-        realref(buf, g, line, 2 * q) = y[b].x;
-        realref(buf, g, line, n - 1 - 2 * q) = (kind == KIND_ND) ? -y[b].y : y[b].y;
-      }
-    }
-    __syncthreads();
     return;
   }
   // Real DFT of the (reordered) line from the half-length FFT: pairs (k, M-k), k <= M/2.
   const int P = M / 2 + 1;
   const T *w1 = tw + tw_rdft(M);
-  if (kind == KIND_PP) {
-    for (int k = g.lane; k < P; k += g.tpl) {
-      if (k == 0) {
-        T z = slot(buf, g, line, 0);
-        slot(buf, g, line, 0) = cmk<T>(z.x + z.y, z.x - z.y);
-        continue;
-      }
-      int km = M - k;
-      T zk = slot(buf, g, line, k), zm = slot(buf, g, line, km);
-      // X_k = E + w^k O,  E = (Zk + conj Zm)/2,  O = -i (Zk - conj Zm)/2
-      T E = cscale(cadd(zk, cconj(zm)), (R)0.5), O = cscale(cmul_mi(csub(zk, cconj(zm))), (R)0.5);
-      T Xk = cadd(E, cmul(O, ldg(&w1[k])));
-      if (km != k) {
-        T E2 = cscale(cadd(zm, cconj(zk)), (R)0.5), O2 = cscale(cmul_mi(csub(zm, cconj(zk))), (R)0.5);
-        slot(buf, g, line, km) = cadd(E2, cmul(O2, ldg(&w1[km])));
-      }
-      slot(buf, g, line, k) = Xk;
-    }
-    __syncthreads();
-    return;
-  }
-  // DCT-II (and DST-II by reversal): V = real DFT of v; t_k = e^{-i pi k/(2n)} V_k;
-  // X_k = Re t_k, X_{n-k} = -Im t_k.
   const T *wq = tw + tw_quarter(M);
-  constexpr int MAXP = kSlotsPerThread / 2 + 1;
-  R out[MAXP][4];
-  int pos[MAXP][4];
-#pragma unroll
-  for (int b = 0; b < MAXP; ++b) {
-    int k = g.lane + b * g.tpl;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) pos[b][c] = -1;
-    if (k < P) {
-      if (k == 0) {
-        T z = slot(buf, g, line, 0);
-        R V0 = z.x + z.y, VM = z.x - z.y;
-        T tM = cscale(ldg(&wq[M]), VM);
-        out[b][0] = V0; pos[b][0] = 0;
-        out[b][1] = tM.x; pos[b][1] = M;
+  const bool dd = kind == KIND_DD;
+  for (int k = g.lane; k < P; k += g.tpl) {
+    if (k == 0) {
+      const T z = at(0);
+      const R V0 = z.x + z.y, VM = z.x - z.y;
+      if (kind == KIND_PP) {
+        emit(0, V0);
+        emit(1, VM);
       } else {
-        int km = M - k;
-        T zk = slot(buf, g, line, k), zm = slot(buf, g, line, km);
-        T E = cscale(cadd(zk, cconj(zm)), (R)0.5), O = cscale(cmul_mi(csub(zk, cconj(zm))), (R)0.5);
-        T Vk = cadd(E, cmul(O, ldg(&w1[k])));
-        T tk = cmul(Vk, ldg(&wq[k]));
-        out[b][0] = tk.x; pos[b][0] = k;
-        out[b][1] = -tk.y; pos[b][1] = n - k;
-        if (km != k) {
-          T E2 = cscale(cadd(zm, cconj(zk)), (R)0.5), O2 = cscale(cmul_mi(csub(zm, cconj(zk))), (R)0.5);
-          T Vm = cadd(E2, cmul(O2, ldg(&w1[km])));
-          T tm = cmul(Vm, ldg(&wq[km]));
-          out[b][2] = tm.x; pos[b][2] = km;
-          out[b][3] = -tm.y; pos[b][3] = n - km;
-        }
+        const T tM = cscale(ldg(&wq[M]), VM);
+        emit(dd ? n - 1 : 0, V0);
+        emit(dd ? n - 1 - M : M, tM.x);
+      }
+      continue;
+    }
+    const int km = M - k;
+    const T zk = at(k), zm = at(km);
+    // V_k = E + w^k O,  E = (Zk + conj Zm)/2,  O = -i (Zk - conj Zm)/2
+    const T E = cscale(cadd(zk, cconj(zm)), (R)0.5), O = cscale(cmul_mi(csub(zk, cconj(zm))), (R)0.5);
+    const T Vk = cadd(E, cmul(O, ldg(&w1[k])));
+    T Vm = Vk;
+    if (km != k) {
+      const T E2 = cscale(cadd(zm, cconj(zk)), (R)0.5), O2 = cscale(cmul_mi(csub(zm, cconj(zk))), (R)0.5);
+      Vm = cadd(E2, cmul(O2, ldg(&w1[km])));
+    }
+    if (kind == KIND_PP) {
+      emit(2 * k, Vk.x);
+      emit(2 * k + 1, Vk.y);
+      if (km != k) {
+        emit(2 * km, Vm.x);
+        emit(2 * km + 1, Vm.y);
+      }
+    } else {
+      // DCT-II (DST-II by reversal): t_k = e^{-i pi k/(2n)} V_k; X_k = Re t_k, X_{n-k} = -Im t_k
+      const T tk = cmul(Vk, ldg(&wq[k]));
+      emit(dd ? n - 1 - k : k, tk.x);
+      emit(dd ? k - 1 : n - k, -tk.y);
+      if (km != k) {
+        const T tm = cmul(Vm, ldg(&wq[km]));
+        emit(dd ? n - 1 - km : km, tm.x);
+        emit(dd ? km - 1 : n - km, -tm.y);
       }
     }
   }
-  __syncthreads();
-#pragma unroll
-  for (int b = 0; b < MAXP; ++b) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      if (pos[b][c] >= 0) {
-        int i = pos[b][c];
-        if (kind == KIND_DD) i = n - 1 - i;
-        realref(buf, g, line, i) = out[b][c];
-      }
-    }
-  }
-  __syncthreads();
 }
 
 // ----------------------------------------------------------------------------- inverse
-// I1: real spectral coefficients (natural order, in place) -> complex slots for the inverse FFT.
-template <typename T>
-__device__ void inv_pre(T *buf, const TileGeom &g, int kind, int n, const T *tw) {
+// I1: real spectral coefficients (natural order, read through fetch(i)) -> complex slots of
+// buf for the inverse FFT. A thread writes the slots of its own pairs; the caller puts a barrier
+// after it.
+template <typename T, typename Fetch>
+__device__ __forceinline__ void inv_pre(T *buf, const TileGeom &g, int kind, int n, const T *tw, Fetch fetch) {
   using R = decltype(T::x);
   const int M = g.M;
-  const int line = g.line;
+  const int base = g.line * g.ls;
+  auto put = [&](int q, T v) { buf[base + q * g.es] = v; };
   if (kind == KIND_ND || kind == KIND_DN) {
     // The inverse of DCT-IV/DST-IV is the same transform times 2/n: same pre-processing.
-    constexpr int MAXI = kSlotsPerThread;
-    R a[MAXI], bb[MAXI];
-#pragma unroll
-    for (int b = 0; b < MAXI; ++b) {
-      int q = g.lane + b * g.tpl;
-      if (q < M) {
-        R x0 = realref(buf, g, line, 2 * q), x1 = realref(buf, g, line, n - 1 - 2 * q);
-        a[b] = (kind == KIND_ND) ? x0 : x1;
-        bb[b] = (kind == KIND_ND) ? x1 : x0;
-      }
-    }
-    __syncthreads();
     const T *t4 = tw + tw_dct4pre(M);
-#pragma unroll
-    for (int b = 0; b < MAXI; ++b) {
-      int q = g.lane + b * g.tpl;
-      if (q < M) slot(buf, g, line, q) = cmul(cmk<T>(a[b], bb[b]), ldg(&t4[q]));
+    for (int q = g.lane; q < M; q += g.tpl) {
+      const R x0 = fetch(2 * q), x1 = fetch(n - 1 - 2 * q);
+      const T z = (kind == KIND_ND) ? cmk<T>(x0, x1) : cmk<T>(x1, x0);
+      put(q, cmul(z, ldg(&t4[q])));
     }
-    __syncthreads();
     return;
   }
   const int P = M / 2 + 1;
   const T *w1 = tw + tw_rdft(M);
-  if (kind == KIND_PP) {
-    for (int k = g.lane; k < P; k += g.tpl) {
-      if (k == 0) {
-        T z = slot(buf, g, line, 0);   // (X_0, X_M), both real
-        R E = (R)0.5 * (z.x + z.y), O = (R)0.5 * (z.x - z.y);
-        slot(buf, g, line, 0) = cmk<T>(E, O);   // Z_0 = E + i O
-        continue;
-      }
-      int km = M - k;
-      T xk = slot(buf, g, line, k), xm = slot(buf, g, line, km);
-      // Z_k = E + i O, E = (X_k + conj X_{M-k})/2, O = (X_k - conj X_{M-k}) conj(w^k)/2
-      T E = cscale(cadd(xk, cconj(xm)), (R)0.5);
-      T O = cscale(cmulc(csub(xk, cconj(xm)), ldg(&w1[k])), (R)0.5);
-      T Zk = cadd(E, cmul_pi(O));
-      if (km != k) {
-        T E2 = cscale(cadd(xm, cconj(xk)), (R)0.5);
-        T O2 = cscale(cmulc(csub(xm, cconj(xk)), ldg(&w1[km])), (R)0.5);
-        slot(buf, g, line, km) = cadd(E2, cmul_pi(O2));
-      }
-      slot(buf, g, line, k) = Zk;
-    }
-    __syncthreads();
-    return;
-  }
-  // DCT-III (DST-III through the reversal Y_i = X_{n-1-i}):
-  // V_k = e^{+i pi k/(2n)} (X_k - i X_{n-k}) with X_n = 0, then the inverse real DFT wrapper.
   const T *wq = tw + tw_quarter(M);
-  constexpr int MAXP = kSlotsPerThread / 2 + 1;
-  T zo[MAXP][2];
-#pragma unroll
-  for (int b = 0; b < MAXP; ++b) {
-    int k = g.lane + b * g.tpl;
-    if (k < P) {
-      auto X = [&](int i) -> R {
-        if (i >= n) return (R)0;
-        return realref(buf, g, line, kind == KIND_DD ? n - 1 - i : i);
-      };
-      auto V = [&](int i) -> T { return cmulc(cmk<T>(X(i), -X(n - i)), ldg(&wq[i])); };
-      if (k == 0) {
-        R V0 = X(0);
-        R VM = V(M).x;   // real: sqrt(2) X_M
-        zo[b][0] = cmk<T>((R)0.5 * (V0 + VM), (R)0.5 * (V0 - VM));
+  const bool dd = kind == KIND_DD;
+  // coefficient i of the line (reversed for DST-III); X_n = 0
+  auto X = [&](int i) -> R {
+    if (i >= n) return (R)0;
+    return fetch(dd ? n - 1 - i : i);
+  };
+  // DCT-III: V_k = e^{+i pi k/(2n)} (X_k - i X_{n-k})
+  auto V = [&](int i) -> T { return cmulc(cmk<T>(X(i), -X(n - i)), ldg(&wq[i])); };
+  for (int k = g.lane; k < P; k += g.tpl) {
+    if (k == 0) {
+      R a, b;
+      if (kind == KIND_PP) {
+        a = fetch(0);   // X_0
+        b = fetch(1);   // X_M
       } else {
-        int km = M - k;
-        T vk = V(k), vm = V(km);
-        T E = cscale(cadd(vk, cconj(vm)), (R)0.5);
-        T O = cscale(cmulc(csub(vk, cconj(vm)), ldg(&w1[k])), (R)0.5);
-        zo[b][0] = cadd(E, cmul_pi(O));
-        if (km != k) {
-          T E2 = cscale(cadd(vm, cconj(vk)), (R)0.5);
-          T O2 = cscale(cmulc(csub(vm, cconj(vk)), ldg(&w1[km])), (R)0.5);
-          zo[b][1] = cadd(E2, cmul_pi(O2));
-        }
+        a = X(0);
+        b = V(M).x;     // real: sqrt(2) X_M
       }
+      put(0, cmk<T>((R)0.5 * (a + b), (R)0.5 * (a - b)));
+      continue;
+    }
+    const int km = M - k;
+    T xk, xm;
+    if (kind == KIND_PP) {
+      xk = cmk<T>(fetch(2 * k), fetch(2 * k + 1));
+      xm = cmk<T>(fetch(2 * km), fetch(2 * km + 1));
+    } else {
+      xk = V(k);
+      xm = V(km);
+    }
+    // Z_k = E + i O, E = (X_k + conj X_{M-k})/2, O = (X_k - conj X_{M-k}) conj(w^k)/2
+    const T E = cscale(cadd(xk, cconj(xm)), (R)0.5);
+    const T O = cscale(cmulc(csub(xk, cconj(xm)), ldg(&w1[k])), (R)0.5);
+    put(k, cadd(E, cmul_pi(O)));
+    if (km != k) {
+      const T E2 = cscale(cadd(xm, cconj(xk)), (R)0.5);
+      const T O2 = cscale(cmulc(csub(xm, cconj(xk)), ldg(&w1[km])), (R)0.5);
+      put(km, cadd(E2, cmul_pi(O2)));
     }
   }
-  __syncthreads();
-#pragma unroll
-  for (int b = 0; b < MAXP; ++b) {
-    int k = g.lane + b * g.tpl;
-    if (k < P) {
-      slot(buf, g, line, k) = zo[b][0];
-      int km = M - k;
-      if (k != 0 && km != k) slot(buf, g, line, km) = zo[b][1];
-    }
-  }
-  __syncthreads();
 }
 
-// I3 (part 1): slot-local post twiddle for DCT-IV / DST-IV before the gather.
+// I3: output x_i (before the 2/n normalisation) from the inverse FFT result in buf.
 template <typename T>
-__device__ void inv_post_twiddle(T *buf, const TileGeom &g, int kind, const T *tw) {
-  if (kind != KIND_ND && kind != KIND_DN) return;
-  const T *tp = tw + tw_dct4post(g.M);
-  for (int q = g.lane; q < g.M; q += g.tpl) {
-    T &z = slot(buf, g, g.line, q);
-    z = cmul(z, ldg(&tp[q]));
+__device__ __forceinline__ decltype(T::x) inv_out(const T *buf, const TileGeom &g, int kind, int n, const T *tw,
+                                                  int i) {
+  const int base = g.line * g.ls;
+  if (kind == KIND_PP) {
+    const T z = buf[base + (i >> 1) * g.es];
+    return (i & 1) ? z.y : z.x;
   }
-  __syncthreads();
-}
-
-// I3 (part 2): where output x_i is read from after the inverse FFT, with sign; the caller
-// multiplies by inv_scale(kind, n).
-__device__ __forceinline__ void inv_src_of(int kind, int n, int i, int &j, bool &neg) {
-  neg = false;
-  if (kind == KIND_PP) { j = i; return; }
   if (kind == KIND_NN || kind == KIND_DD) {
-    j = (i & 1) ? (n - 1 - (i >> 1)) : (i >> 1);
-    neg = (kind == KIND_DD) && (i & 1);
-    return;
+    const int j = (i & 1) ? (n - 1 - (i >> 1)) : (i >> 1);
+    const T z = buf[base + (j >> 1) * g.es];
+    const auto v = (j & 1) ? z.y : z.x;
+    return (kind == KIND_DD && (i & 1)) ? -v : v;
   }
-  // DCT-IV / DST-IV: x_2q = Re y_q, x_{n-1-2q} = -+Im y_q  (real index 2q / 2q+1 of slot q)
-  if ((i & 1) == 0) { j = i; return; }
-  int q = (n - 1 - i) >> 1;
-  j = 2 * q + 1;
-  neg = (kind == KIND_ND);
+  // DCT-IV / DST-IV: y_q = e^{-i pi q/n} Z_q; x_2q = Re y_q, x_{n-1-2q} = -+Im y_q
+  const int q = (i & 1) ? ((n - 1 - i) >> 1) : (i >> 1);
+  const T y = cmul(buf[base + q * g.es], ldg(tw + tw_dct4post(g.M) + q));
+  if ((i & 1) == 0) return y.x;
+  return (kind == KIND_ND) ? -y.y : y.y;
 }
 
 // Normalisation of every inverse: 1/M of the half-length inverse FFT for the real DFT and

@@ -147,12 +147,6 @@ extern "C" pc_status pc_solve_poisson_static(int dim, const int64_t *n, const do
     const bool nlo = bc_lo[a] != PC_BC_DIRICHLET, nhi = bc_hi[a] != PC_BC_DIRICHLET;
     ax.kind = ax.periodic ? KIND_PP : (nlo && nhi) ? KIND_NN : (!nlo && !nhi) ? KIND_DD : (nlo ? KIND_ND : KIND_DN);
     if (!nlo || !nhi) pl.singular = false;
-    int m = ax.M;
-    ax.nradix = 0;
-    while (m % 4 == 0) { ax.radix[ax.nradix++] = 4; m /= 4; }
-    while (m % 2 == 0) { ax.radix[ax.nradix++] = 2; m /= 2; }
-    while (m % 3 == 0) { ax.radix[ax.nradix++] = 3; m /= 3; }
-    while (m % 5 == 0) { ax.radix[ax.nradix++] = 5; m /= 5; }
     ax.tw64 = reinterpret_cast<double2 *>(ws + off);
     off += 2LL * tw_total(ax.M);
     ax.lam64 = ws + off;

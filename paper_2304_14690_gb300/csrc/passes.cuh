@@ -9,6 +9,9 @@
 namespace pc {
 
 enum SrcMode { SRC_F32 = 0, SRC_F64 = 1, SRC_WORK = 2 };
+
+constexpr int kMaxPassThreads = 512;   // CTA size limit of the transform passes
+constexpr int kBatchPassEmax = 16;     // largest slots per thread of a batched pass kernel
 enum DstMode { DST_WORK = 0, DST_F64_SET = 1, DST_F64_ADD = 2 };
 
 template <typename Real>
@@ -23,6 +26,7 @@ struct PassArgs {
   int inner;            // column tiles: number of line positions f (= stride)
   int lines;            // row tiles: number of lines
   int L;                // lines per tile (power of two)
+  int emax;             // slots per thread (power of two): selects the kernel instance
   int lbits;            // log2(L)
   int tpl_bits;         // log2(threads per line)
   int col;              // 1: column tile
@@ -56,9 +60,10 @@ std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, c
 template <typename Real>
 pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long long &tiles, int &threads,
                      size_t &smem, int batch_threads);
-// One launch of the batched pass kernel over items (args index, tile).
+// One launch of the batched pass kernel over items (args index, tile); emax: the largest slots
+// per thread among the items' passes (selects the kernel instance).
 template <typename Real>
 pc_status launch_batched_pass(const PassArgs<Real> *dargs, const int2 *ditems, int nitems, int threads,
-                              size_t smem, cudaStream_t st);
+                              size_t smem, int emax, cudaStream_t st);
 
 }  // namespace pc

@@ -24,8 +24,10 @@ struct AxisInfo {
   int kind = 0;
   int n = 0;        // cells
   int M = 0;        // complex FFT length n/2
-  int nradix = 0;
-  int radix[kMaxRadices] = {0};
+  // Slots per thread of the transform passes along this axis, per precision (powers of two):
+  // they fix the threads per line and the radix schedule (see build_pass), chosen when the
+  // plan is built and shared by single and batched calls.
+  int slots32 = 4, slots64 = 2;
   double h = 0.0;
   double L = 0.0;   // n * h
   bool periodic = false;
@@ -179,11 +181,13 @@ inline int grid_for(int64_t work, int threads) {
   return (int)b;
 }
 
-// Solver entry points (poisson.cu).
-pc_status solve_fp64(Plan *p, const double *s_dev, double *p_dev, bool from_faces,
-                     cudaStream_t st);
-pc_status solve_mixed(Plan *p, const double *s_dev, double *p_dev, bool from_faces,
-                      int sweeps, cudaStream_t st);
+// Transform solves of a grid (poisson.cu): FP64 s -> p, and one FP32 solve whose source and
+// destination modes are those of passes.cuh (FP32 or FP64 source; FP64 set or accumulate).
+pc_status solve_fp64_grid(Plan *p, const double *s, double *pout, cudaStream_t st);
+pc_status solve_fp32_grid(Plan *p, int src_mode, const void *s, int dst_mode, double *pout,
+                          cudaStream_t st);
+// Drops the plan's captured CUDA graphs and batch executables (after a schedule change).
+void plan_drop_graphs(Plan *p);
 // ----------------------------------------------------------------------------- batches
 // Stages of the batched pipeline (one launch per stage for all problems of a batch).
 enum BatchStage {
@@ -201,13 +205,16 @@ struct GridDev {
   int periodic[3];
   int lo_kind[3], hi_kind[3];   // 0 Neumann, 1 Dirichlet (ghost sign), ignored when periodic
   double inv_h[3], inv_h2[3];
+  float ih2_hi[3], ih2_lo[3];   // inv_h2 as an FP32 pair (double-float residual)
+  // cell tiles of the cell kernels (project.cu): rows of the last axis, tile width 2^tw_bits,
+  // 2^th_bits thread rows of cr rows each, gx tiles along the last axis, nblk blocks
+  int rows, tw_bits, th_bits, cr, gx, nblk;
 };
 
 // Per-problem parameters of a batched launch (device array, one entry per problem).
 struct BatchProblem {
   GridDev g;
   int dim, N, ncells, K, Kg, singular, gmode;
-  unsigned cgx, cgy, cgz;         // cell-grid launch shape of the problem
   const void *u, *f;
   void *uo, *fo;
   double *p;
@@ -241,5 +248,34 @@ pc_status prepare_kernels();
 pc_status build_rows(Plan *p, const double *xyz_dev, cudaStream_t st);
 // Axis tables (poisson.cu).
 pc_status build_axis_tables(Plan *p);
+
+
+// ----------------------------------------------------------------------------- launches
+// Programmatic dependent launch: every kernel of the projection path first waits for the
+// kernel before it to complete (griddepcontrol.wait: its writes are visible after the wait),
+// then lets the next kernel of the stream be scheduled. The next kernel's CTAs can thus be
+// resident and waiting when this one ends, which hides the launch gap between dependent
+// kernels (also inside CUDA graphs, where the edges become programmatic). Without the launch
+// attribute the wait returns at once.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);   // errors surface through cudaGetLastError
+}
 
 }  // namespace pc

@@ -36,18 +36,21 @@ __device__ __forceinline__ Real load_src(const PassArgs<Real> &A, int gi) {
   return static_cast<const Real *>(A.src)[gi];
 }
 
-constexpr int kLoadsPerThread = 2 * kSlotsPerThread;   // n / tpl <= 8
-
 // One axis pass over a tile of lines: [forward transform] [eigenvalue division] [inverse].
-// Dynamic shared memory: L*M complex slots, then per line the eigenvalue sum of the other
-// axes, the line's base cell index (-1 for lines past a ragged end) and its zero-mode flag.
-// Threads beyond L * tpl (a batched launch sized for a larger tile) take part in the barriers
-// only.
-template <typename Real>
+// Dynamic shared memory: two buffers of L*M complex slots (the FFT ping-pongs between them),
+// then per line the eigenvalue sum of the other axes, the line's base cell index (-1 for lines
+// past a ragged end) and its zero-mode flag. Threads beyond L * tpl (a batched launch sized for
+// a larger tile) take part in the barriers only. Steps and barriers:
+//   forward:  load line -> scatter to slots | FFT stages | post-process -> global (forward-only)
+//             or -> real coefficients in the other buffer with the division fused |
+//   inverse:  (inverse-only: load coefficients -> other buffer |) pre-process -> slots |
+//             FFT stages | normalise and store.
+template <typename Real, int EMAX>
 __device__ __forceinline__ void axis_pass_body(const PassArgs<Real> &A, const int tile, unsigned char *smem_raw) {
   using T = typename Cplx<Real>::T;
-  T *buf = reinterpret_cast<T *>(smem_raw);
-  Real *lamo = reinterpret_cast<Real *>(buf + A.L * A.M);
+  T *buf0 = reinterpret_cast<T *>(smem_raw);
+  T *buf1 = buf0 + A.L * A.M;
+  Real *lamo = reinterpret_cast<Real *>(buf1 + A.L * A.M);
   int *lbase = reinterpret_cast<int *>(lamo + A.L);
   int *lzero = lbase + A.L;
   const int t = threadIdx.x;
@@ -93,101 +96,110 @@ __device__ __forceinline__ void axis_pass_body(const PassArgs<Real> &A, const in
   const int base = lbase[line];
   const bool valid = active && base >= 0;
   const int stride = A.stride;
-  const bool fft_inv_dir = !(A.kind == KIND_ND || A.kind == KIND_DN);
+  const bool dct4 = A.kind == KIND_ND || A.kind == KIND_DN;
 
   // All global loads of a thread are issued before any is used (memory-level parallelism).
-  Real xin[kLoadsPerThread];
+  Real xin[2 * EMAX];
 #pragma unroll
-  for (int b = 0; b < kLoadsPerThread; ++b) {
+  for (int b = 0; b < 2 * EMAX; ++b) {
     const int j = g.lane + b * g.tpl;
     xin[b] = (valid && j < n) ? load_src(A, base + j * stride) : (Real)0;
   }
+  T *res;        // buffer with the latest slots
+  T *coef;       // buffer with the real coefficients for the inverse
   if (A.do_fwd) {
     // F1: scatter the real line into the complex slots (Makhoul / DCT-IV ordering).
 #pragma unroll
-    for (int b = 0; b < kLoadsPerThread; ++b) {
+    for (int b = 0; b < 2 * EMAX; ++b) {
       const int j = g.lane + b * g.tpl;
       if (j < n) {
         int q, comp;
         bool neg;
         fwd_slot_of(A.kind, n, j, q, comp, neg);
-        reinterpret_cast<Real *>(&slot(buf, g, line, q))[comp] = neg ? -xin[b] : xin[b];
+        reinterpret_cast<Real *>(&slot(buf0, g, line, q))[comp] = neg ? -xin[b] : xin[b];
       }
     }
     __syncthreads();
-    pretwiddle(buf, g, A.kind, A.tw);
-    fft_lines(buf, g, A.st, A.nst, A.tw, false);
-    fwd_post(buf, g, A.kind, n, A.tw);
-  } else {
-#pragma unroll
-    for (int b = 0; b < kLoadsPerThread; ++b) {
-      const int j = g.lane + b * g.tpl;
-      if (j < n) realref(buf, g, line, j) = xin[b];
+    res = fft_run<T, EMAX, false>(buf0, buf1, g, A.st, A.nst, A.tw, dct4 ? A.tw + tw_dct4pre(A.M) : nullptr);
+    if (!A.do_inv) {
+      // forward-only pass: the coefficients go straight to global memory (DST_WORK)
+      if (valid) {
+        Real *dst = static_cast<Real *>(A.dst);
+        fwd_post(res, g, A.kind, n, A.tw, [&](int pos, Real X) { dst[base + pos * stride] = X; });
+      }
+      return;
     }
-    __syncthreads();
-  }
-
-  if (A.do_div) {
-    // p^ = s^ / (lambda_axis(j) + sum of the other axes' eigenvalues); zero mode -> 0.
+    coef = (res == buf0) ? buf1 : buf0;
     if (valid) {
+      // p^ = s^ / (lambda_axis(j) + sum of the other axes' eigenvalues); zero mode -> 0
       const Real lo = lamo[line];
       const bool z = A.singular && lzero[line];
       const Real *la = A.lam[A.axis];
-      for (int j = g.lane; j < n; j += g.tpl) {
-        Real &v = realref(buf, g, line, j);
-        v = (z && j == 0) ? (Real)0 : v / (__ldg(la + j) + lo);
-      }
+      const bool dv = A.do_div;
+      fwd_post(res, g, A.kind, n, A.tw, [&](int pos, Real X) {
+        if (dv) X = (z && pos == 0) ? (Real)0 : X / (__ldg(la + pos) + lo);
+        realref(coef, g, line, pos) = X;
+      });
+    }
+    __syncthreads();
+  } else {
+    // inverse-only pass: the coefficients are staged in shared memory first
+    coef = buf1;
+    res = buf0;
+#pragma unroll
+    for (int b = 0; b < 2 * EMAX; ++b) {
+      const int j = g.lane + b * g.tpl;
+      if (j < n) realref(coef, g, line, j) = xin[b];
     }
     __syncthreads();
   }
-
-  if (A.do_inv) {
-    inv_pre(buf, g, A.kind, n, A.tw);
-    fft_lines(buf, g, A.st, A.nst, A.tw, fft_inv_dir);
-    inv_post_twiddle(buf, g, A.kind, A.tw);
-    if (!valid) return;
-    double old[kLoadsPerThread];
-    if (A.dst_mode == DST_F64_ADD) {
+  if (!A.do_inv) return;
+  // I1: coefficients -> slots (into the buffer the forward FFT result came from)
+  T *slots = (coef == buf0) ? buf1 : buf0;
+  if (valid) inv_pre(slots, g, A.kind, n, A.tw, [&](int i) -> Real { return realref(coef, g, line, i); });
+  __syncthreads();
+  if (dct4) res = fft_run<T, EMAX, false>(slots, coef, g, A.st, A.nst, A.tw, nullptr);
+  else res = fft_run<T, EMAX, true>(slots, coef, g, A.st, A.nst, A.tw, nullptr);
+  if (!valid) return;
+  // I3: normalise and store, in chunks of 8 outputs (the old values of an accumulating store
+  // are loaded together)
+  const Real scale = A.out_scale;
+  constexpr int kChunk = 8;
 #pragma unroll
-      for (int b = 0; b < kLoadsPerThread; ++b) {
-        const int i = g.lane + b * g.tpl;
-        old[b] = (i < n) ? static_cast<const double *>(A.dst)[base + i * stride] : 0.0;
-      }
+  for (int c0 = 0; c0 < 2 * EMAX; c0 += kChunk) {
+    Real x[kChunk];
+    double old[kChunk];
+#pragma unroll
+    for (int b = 0; b < kChunk; ++b) {
+      const int i = g.lane + (c0 + b) * g.tpl;
+      x[b] = (i < n) ? inv_out(res, g, A.kind, n, A.tw, i) * scale : (Real)0;
+      old[b] = (A.dst_mode == DST_F64_ADD && i < n) ? static_cast<const double *>(A.dst)[base + i * stride] : 0.0;
     }
 #pragma unroll
-    for (int b = 0; b < kLoadsPerThread; ++b) {
-      const int i = g.lane + b * g.tpl;
+    for (int b = 0; b < kChunk; ++b) {
+      const int i = g.lane + (c0 + b) * g.tpl;
       if (i >= n) continue;
-      int j;
-      bool neg;
-      inv_src_of(A.kind, n, i, j, neg);
-      Real x = realref(buf, g, line, j) * (neg ? -A.out_scale : A.out_scale);
-      int gi = base + i * stride;
-      if (A.dst_mode == DST_WORK) static_cast<Real *>(A.dst)[gi] = x;
-      else if (A.dst_mode == DST_F64_SET) static_cast<double *>(A.dst)[gi] = to_f64(x);
-      else static_cast<double *>(A.dst)[gi] = old[b] + to_f64(x);
-    }
-  } else {
-    if (!valid) return;
-#pragma unroll
-    for (int b = 0; b < kLoadsPerThread; ++b) {
-      const int j = g.lane + b * g.tpl;
-      if (j < n) static_cast<Real *>(A.dst)[base + j * stride] = realref(buf, g, line, j);
+      const int gi = base + i * stride;
+      if (A.dst_mode == DST_WORK) static_cast<Real *>(A.dst)[gi] = x[b];
+      else if (A.dst_mode == DST_F64_SET) static_cast<double *>(A.dst)[gi] = to_f64(x[b]);
+      else static_cast<double *>(A.dst)[gi] = old[b] + to_f64(x[b]);
     }
   }
 }
 
-template <typename Real>
-__global__ void __launch_bounds__(1024) axis_pass(PassArgs<Real> A) {
+template <typename Real, int EMAX>
+__global__ void __launch_bounds__(kMaxPassThreads) axis_pass(PassArgs<Real> A) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  axis_pass_body<Real>(A, blockIdx.x, smem_raw);
+  axis_pass_body<Real, EMAX>(A, blockIdx.x, smem_raw);
 }
 
 // Batched pass: CTA b processes tile items[b].y of the pass described by args[items[b].x] (one
 // launch for every problem of a batch; each problem keeps its own tile shape).
-template <typename Real>
-__global__ void __launch_bounds__(1024) axis_pass_batched(const PassArgs<Real> *__restrict__ args,
-                                                          const int2 *__restrict__ items) {
+template <typename Real, int EMAX>
+__global__ void __launch_bounds__(kMaxPassThreads) axis_pass_batched(const PassArgs<Real> *__restrict__ args,
+                                                                     const int2 *__restrict__ items) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) PassArgs<Real> A;
   const int2 it = items[blockIdx.x];
@@ -197,16 +209,20 @@ __global__ void __launch_bounds__(1024) axis_pass_batched(const PassArgs<Real> *
     for (int w = threadIdx.x; w < (int)(sizeof(PassArgs<Real>) / 4); w += blockDim.x) dst[w] = __ldg(src + w);
   }
   __syncthreads();
-  axis_pass_body<Real>(A, it.y, smem_raw);
+  axis_pass_body<Real, EMAX>(A, it.y, smem_raw);
 }
 
 // ----------------------------------------------------------------------------- host side
 
-static void radix_plan(int M, int *radix, int &nr) {
+// Radix schedule of a length-M FFT with at most E slots per thread: the largest power-of-two
+// radices up to min(E, 16) first, then the factors 3 and 5.
+static void radix_plan(int M, int E, int *radix, int &nr) {
   nr = 0;
   int m = M;
-  while (m % 4 == 0) { radix[nr++] = 4; m /= 4; }
-  while (m % 2 == 0) { radix[nr++] = 2; m /= 2; }
+  int rmax = E < 16 ? E : 16;
+  if (rmax < 2) rmax = 2;
+  for (int r = rmax; r >= 2; r >>= 1)
+    while (m % r == 0) { radix[nr++] = r; m /= r; }
   while (m % 3 == 0) { radix[nr++] = 3; m /= 3; }
   while (m % 5 == 0) { radix[nr++] = 5; m /= 5; }
 }
@@ -229,7 +245,6 @@ pc_status build_axis_tables(Plan *p) {
     AxisInfo &ax = p->ax[a];
     const int n = ax.n, M = n / 2;
     ax.M = M;
-    radix_plan(M, ax.radix, ax.nradix);
     std::vector<double2> tw(tw_total(M));
     auto put = [&](int off, int k, double ang) { tw[off + k] = make_double2(std::cos(ang), std::sin(ang)); };
     const double pi = 3.14159265358979323846;
@@ -287,14 +302,23 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   A.kind = ax.kind;
   A.n = ax.n;
   A.M = ax.M;
-  A.nst = ax.nradix;
+  const int M = ax.M;
+  // threads per line: a power of two with at most E slots per thread; the kernel instance is
+  // the smallest power of two >= M / tpl
+  const int E = (sizeof(Real) == 8) ? ax.slots64 : ax.slots32;
+  const int tpl = 1 << ilog2((M + E - 1) / E);
+  const int emax = 1 << ilog2((M + tpl - 1) / tpl);
+  A.emax = emax;
   {
+    int radix[kMaxRadices], nr;
+    radix_plan(M, emax, radix, nr);
+    A.nst = nr;
     int Ns = 1;
-    for (int i = 0; i < ax.nradix; ++i) {
+    for (int i = 0; i < nr; ++i) {
       StageInfo &si = A.st[i];
-      si.R = ax.radix[i];
+      si.R = radix[i];
       si.Ns = Ns;
-      si.stride_m = ax.M / (Ns * si.R);
+      si.stride_m = M / (Ns * si.R);
       si.shift = ((Ns & (Ns - 1)) == 0) ? ilog2(Ns) : -1;
       si.magic = (unsigned)(((1ULL << 32) + Ns - 1) / Ns);
       Ns *= si.R;
@@ -308,22 +332,18 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   A.stride = stride;
   const int last = p->dim - 1;
   A.col = axis != last;
-  const int M = ax.M;
-  // threads per line: a power of two >= M/4 (bounds the registers held across barriers)
-  const int tpl = 1 << ilog2((M + kSlotsPerThread - 1) / kSlotsPerThread);
-  const int max_lines = 1024 / tpl;
-  const int budget = 4096;          // complex slots per tile
-  const int want_ctas = 152;        // at least one CTA per SM on both dies
+  const int max_threads = batch_threads > 0 ? batch_threads : 256;
+  const int max_lines = max_threads / tpl > 0 ? max_threads / tpl : 1;
+  const int budget = 8192;          // complex slots per tile (two buffers: 2 x 64 KB in FP32)
+  const int want_ctas = 2 * 152;    // two CTAs per SM on both dies
   int L;
   if (A.col) {
     // 32-byte row segments when the grid allows it, fewer lines when CTAs would be too few
-    L = (sizeof(Real) == 8) ? 4 : 8;
-    while (L * 2 <= 32 && L * 2 * M <= budget && L * 2 <= max_lines) L *= 2;
-    long long outer = p->ncells / ((long long)stride * ax.n);
-    if (batch_threads > 0) L = 32;   // a batch fills its CTAs from many problems
-    while (L > 1 && batch_threads <= 0 && outer * ((stride + L - 1) / L) < want_ctas) L /= 2;
-    while (L > 1 && batch_threads > 0 && L * tpl > batch_threads) L /= 2;
+    L = 32;
     while (L > 1 && (L * M > budget || L > max_lines)) L /= 2;
+    long long outer = p->ncells / ((long long)stride * ax.n);
+    const int Lmin = (sizeof(Real) == 8) ? 4 : 8;
+    while (L > Lmin && batch_threads <= 0 && outer * ((stride + L - 1) / L) < want_ctas) L /= 2;
     if (L > stride) L = 1 << (ilog2(stride + 1) - 1);
     A.inner = stride;
     A.tiles_per_outer = (stride + L - 1) / L;
@@ -335,7 +355,6 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
     L = 1 << (ilog2(L + 1) - 1);
     while (L > max_lines) L /= 2;
     while (L > 1 && batch_threads <= 0 && (lines + L - 1) / L < want_ctas) L /= 2;
-    while (L > 1 && batch_threads > 0 && L * tpl > batch_threads) L /= 2;
     A.lines = (int)lines;
     tiles = (lines + L - 1) / L;
   }
@@ -354,9 +373,11 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   A.dst = dst;
   A.out_scale = (Real)inv_scale(ax.kind, ax.n);
   threads = L * tpl;
-  if (threads > 1024 || L * M > 2 * budget)
+  if (threads > kMaxPassThreads || L * M > budget)
     return fail(PC_ERR_UNSUPPORTED, "axis %d: tile of %d x %d too large", axis, L, M);
-  smem = (size_t)L * M * sizeof(T) + (size_t)L * (sizeof(Real) + 2 * sizeof(int));
+  if (batch_threads > 0 && emax > kBatchPassEmax)
+    return fail(PC_ERR_UNSUPPORTED, "axis %d: %d slots per thread exceed the batched kernel", axis, emax);
+  smem = 2 * (size_t)L * M * sizeof(T) + (size_t)L * (sizeof(Real) + 2 * sizeof(int));
   return PC_OK;
 }
 
@@ -370,7 +391,13 @@ static pc_status launch_pass(Plan *p, const PassSpec &ps, cudaStream_t st) {
   int threads;
   size_t smem;
   PC_TRY(build_pass<Real>(p, ps, A, tiles, threads, smem, 0));
-  axis_pass<Real><<<(unsigned)tiles, threads, smem, st>>>(A);
+  switch (A.emax) {
+    case 1: case 2: launch_pdl(axis_pass<Real, 2>, (unsigned)tiles, threads, smem, st, A); break;
+    case 4: launch_pdl(axis_pass<Real, 4>, (unsigned)tiles, threads, smem, st, A); break;
+    case 8: launch_pdl(axis_pass<Real, 8>, (unsigned)tiles, threads, smem, st, A); break;
+    case 16: launch_pdl(axis_pass<Real, 16>, (unsigned)tiles, threads, smem, st, A); break;
+    default: return fail(PC_ERR_UNSUPPORTED, "no transform kernel for %d slots per thread", A.emax);
+  }
   count_launch(p);
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
@@ -378,21 +405,36 @@ static pc_status launch_pass(Plan *p, const PassSpec &ps, cudaStream_t st) {
 
 template <typename Real>
 pc_status launch_batched_pass(const PassArgs<Real> *dargs, const int2 *ditems, int nitems, int threads,
-                              size_t smem, cudaStream_t st) {
+                              size_t smem, int emax, cudaStream_t st) {
   if (nitems <= 0) return PC_OK;
-  axis_pass_batched<Real><<<(unsigned)nitems, threads, smem, st>>>(dargs, ditems);
+  switch (emax) {
+    case 1: case 2: launch_pdl(axis_pass_batched<Real, 2>, (unsigned)nitems, threads, smem, st, dargs, ditems); break;
+    case 4: launch_pdl(axis_pass_batched<Real, 4>, (unsigned)nitems, threads, smem, st, dargs, ditems); break;
+    case 8: launch_pdl(axis_pass_batched<Real, 8>, (unsigned)nitems, threads, smem, st, dargs, ditems); break;
+    case 16: launch_pdl(axis_pass_batched<Real, 16>, (unsigned)nitems, threads, smem, st, dargs, ditems); break;
+    default: return fail(PC_ERR_UNSUPPORTED, "no batched transform kernel for %d slots per thread", emax);
+  }
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
 }
-template pc_status launch_batched_pass<float>(const PassArgs<float> *, const int2 *, int, int, size_t, cudaStream_t);
-template pc_status launch_batched_pass<double>(const PassArgs<double> *, const int2 *, int, int, size_t, cudaStream_t);
+template pc_status launch_batched_pass<float>(const PassArgs<float> *, const int2 *, int, int, size_t, int, cudaStream_t);
+template pc_status launch_batched_pass<double>(const PassArgs<double> *, const int2 *, int, int, size_t, int, cudaStream_t);
 
 // Kernel attributes set once per device, before any stream capture.
 pc_status prepare_kernels() {
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  const int lim = 200 * 1024;
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   return PC_OK;
 }
 

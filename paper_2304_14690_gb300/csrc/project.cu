@@ -22,10 +22,6 @@
 
 namespace pc {
 
-pc_status solve_fp32_grid(Plan *p, int src_mode, const void *s, int dst_mode, double *pout,
-                          cudaStream_t st);
-pc_status solve_fp64_grid(Plan *p, const double *s, double *pout, cudaStream_t st);
-
 enum { SRC_F32_ = 0, SRC_F64_ = 1 };
 enum { DST_F64_SET_ = 1, DST_F64_ADD_ = 2 };
 
@@ -112,10 +108,18 @@ __device__ bool grid_sum(double v, double *partials, unsigned int *counter, doub
   __syncthreads();
   if (!last) return false;
   __threadfence();
+  // The whole last block sums the partials: thread t takes partials t, t + blockDim, ... in
+  // order, then a fixed shuffle tree and the warp totals in warp order (deterministic).
+  __shared__ double shw[32];
+  double t = 0.0;
+  for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x) t += __ldcg(partials + b);
+  t = warp_sum(t);
+  if (lane == 0) shw[wid] = t;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (unsigned b = 0; b < nblk; ++b) t += ((volatile double *)partials)[b];
-    *dst = t;
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += shw[w];
+    *dst = tot;
     *counter = 0u;
     return true;
   }
@@ -151,21 +155,29 @@ __device__ __forceinline__ float2 as_pair(float v) { return make_float2(v, 0.0f)
 
 // u~ = u* + dt f~; FP64 copy (FP64 path, SPLIT = false) or (hi, lo) FP32 pair (mixed). Compile-
 // time variants keep the common case (no force, no statistics) free of FP64 arithmetic.
+// Element kernels over a flat array: each thread takes kFlatPerThread elements, 256 apart.
+constexpr int kFlatThreads = 256;
+constexpr int kFlatPerThread = 4;
+constexpr int kFlatPerBlock = kFlatThreads * kFlatPerThread;
+
 template <typename VT, bool HAS_F, bool STATS, bool SPLIT>
-__device__ __forceinline__ void prep_kernel_body(const VBlock &vb, int count, const VT *__restrict__ u, const VT *__restrict__ f, double dt,
+__device__ __forceinline__ void prep_kernel_body(unsigned b, int count, const VT *__restrict__ u, const VT *__restrict__ f, double dt,
                             double *__restrict__ ut64, float2 *__restrict__ u2, DevStats *stats) {
-  int i = vb.x * blockDim.x + threadIdx.x;
   double m = 0.0;
-  if (i < count) {
-    const VT ui = u[i];
-    if (STATS) m = fabs(as_f64(ui));
-    if (HAS_F) {
-      double v = fma(dt, as_f64(f[i]), as_f64(ui));
-      if (SPLIT) u2[i] = as_pair(v);
-      else ut64[i] = v;
-    } else {
-      if (SPLIT) u2[i] = as_pair(ui);
-      else ut64[i] = as_f64(ui);
+#pragma unroll
+  for (int k = 0; k < kFlatPerThread; ++k) {
+    const int i = (int)b * kFlatPerBlock + k * kFlatThreads + threadIdx.x;
+    if (i < count) {
+      const VT ui = u[i];
+      if (STATS) m = fmax(m, fabs(as_f64(ui)));
+      if (HAS_F) {
+        double v = fma(dt, as_f64(f[i]), as_f64(ui));
+        if (SPLIT) u2[i] = as_pair(v);
+        else ut64[i] = v;
+      } else {
+        if (SPLIT) u2[i] = as_pair(ui);
+        else ut64[i] = as_f64(ui);
+      }
     }
   }
   if (STATS) block_max_update(m, &stats->max_u);
@@ -173,15 +185,16 @@ __device__ __forceinline__ void prep_kernel_body(const VBlock &vb, int count, co
 template <typename VT, bool HAS_F, bool STATS, bool SPLIT>
 __global__ void prep_kernel(int count, const VT *__restrict__ u, const VT *__restrict__ f, double dt,
                             double *__restrict__ ut64, float2 *__restrict__ u2, DevStats *stats) {
-  prep_kernel_body<VT, HAS_F, STATS, SPLIT>(hw_block(), count, u, f, dt, ut64, u2, stats);
+  pdl_enter();
+  prep_kernel_body<VT, HAS_F, STATS, SPLIT>(blockIdx.x, count, u, f, dt, ut64, u2, stats);
 }
 
 template <typename VT>
 static void launch_prep(bool has_f, bool stats, bool split, int cnt, const VT *u, const VT *f, double dt,
                         double *ut64, float2 *u2, DevStats *ds, cudaStream_t st) {
-  const int T = 256;
-  const int G = grid_for(cnt, T);
-#define PC_PREP(F, S, P) prep_kernel<VT, F, S, P><<<G, T, 0, st>>>(cnt, u, f, dt, ut64, u2, ds)
+  const int T = kFlatThreads;
+  const int G = grid_for(cnt, kFlatPerBlock);
+#define PC_PREP(F, S, P) launch_pdl(prep_kernel<VT, F, S, P>, G, T, 0, st, cnt, u, f, dt, ut64, u2, ds)
   if (has_f) {
     if (stats) { if (split) PC_PREP(true, true, true); else PC_PREP(true, true, false); }
     else { if (split) PC_PREP(true, false, true); else PC_PREP(true, false, false); }
@@ -196,6 +209,7 @@ static void launch_prep(bool has_f, bool stats, bool split, int cnt, const VT *u
 __global__ void transfer64_kernel(int rows, int K, const int32_t *__restrict__ col,
                                   const double *__restrict__ w, const double *__restrict__ u,
                                   double *__restrict__ U) {
+  pdl_enter();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   double acc = 0.0;
@@ -256,23 +270,32 @@ template <int KC>
 __global__ void transfer_mixed_kernel(int rows, int Kr, const int32_t *__restrict__ col,
                                       const float2 *__restrict__ w2, const float2 *__restrict__ u2,
                                       double *__restrict__ U) {
+  pdl_enter();
   transfer_mixed_kernel_body<KC>(hw_block(), rows, Kr, col, w2, u2, U);
 }
 
 // ----------------------------------------------------------------------------- grid geometry
-// Cells are addressed by a 3D launch (x: last axis, y: middle axis, z: first axis of a 3D grid;
-// 2D grids use x and y), so no kernel divides an index. Axes are padded to three with extent 1
-// (GridDev, pc_internal.cuh).
+// Cell kernels view the grid as g.rows rows of the last axis. A block of 256 threads covers
+// 2^tw_bits positions of the last axis times 2^th_bits thread rows, and every thread walks
+// g.cr consecutive rows, so the fixed cost of a block (problem lookup, reductions) is spread
+// over 256 * cr cells. The launch is one-dimensional: block b is tile (b % gx, b / gx). The
+// kernels are templated on the dimension and unroll their axis loops, so the small index
+// arrays stay in registers.
 
-// Cell multi-index of this thread (false when outside the grid). The cell kernels are templated
-// on the dimension and unroll their axis loops, so the index arrays stay in registers (a
-// runtime-indexed array would be placed in local memory).
+// Column of this thread and its first row in block b.
+__device__ __forceinline__ void tile_pos(const GridDev &g, unsigned b, int &x, int &row0) {
+  const int t = threadIdx.x;
+  const int by = (int)(b / (unsigned)g.gx);
+  const int bx = (int)b - by * g.gx;
+  x = (bx << g.tw_bits) + (t & ((1 << g.tw_bits) - 1));
+  row0 = ((by << g.th_bits) + (t >> g.tw_bits)) * g.cr;
+}
+// Multi-index of cell (row, x).
 template <int DIM>
-__device__ __forceinline__ bool cell_of_thread(const GridDev &g, int *i, const VBlock &vb) {
-  const int x = vb.x * blockDim.x + threadIdx.x;
-  if (DIM == 2) { i[0] = vb.y; i[1] = x; i[2] = 0; return x < g.n[1]; }
-  i[0] = vb.z; i[1] = vb.y; i[2] = x;
-  return x < g.n[2];
+__device__ __forceinline__ void cell_at(const GridDev &g, int row, int x, int *i) {
+  if (DIM == 2) { i[0] = row; i[1] = x; i[2] = 0; return; }
+  const int i0 = row / g.n[1];
+  i[0] = i0; i[1] = row - i0 * g.n[1]; i[2] = x;
 }
 __device__ __forceinline__ int cell_index(const GridDev &g, const int *i) {
   return i[0] * g.cs[0] + i[1] * g.cs[1] + i[2] * g.cs[2];
@@ -284,60 +307,117 @@ __device__ __forceinline__ int face_index(const GridDev &g, int axis, const int 
   for (int b = 0; b < 3; ++b) f += ((b == axis) ? fi : i[b]) * g.fs[axis][b];
   return f;
 }
+__device__ __forceinline__ VBlock tile_block(const GridDev &g, unsigned b) {
+  return VBlock{b, 0u, 0u, (unsigned)g.nblk, 1u, 1u};
+}
 
-// s = D_h U / (beta dt), plus sum(s), sum(s^2).
+// ----------------------------------------------------------------------------- double-float
+// Unevaluated FP32 pairs (hi + lo, struct DF above) with error-free transformations (Knuth's TwoSum, Dekker's
+// product through fma); the _rn intrinsics keep the compiler from contracting them.
+__device__ __forceinline__ DF df_of(double v) {
+  DF r;
+  split_f64(v, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float z = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, z)), __fsub_rn(b.hi, z));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s, e);
+  return DF{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float h = __fadd_rn(p, e);
+  return DF{h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+
+// ----------------------------------------------------------------------------- divergence
+// s = D_h U / (beta dt) (FP64), its FP32 copy, and optionally sum(s), sum(s^2).
 template <int DIM>
-__device__ __forceinline__ void divergence_kernel_body(const VBlock &vb, GridDev g, const double *U0, const double *U1,
-                                  const double *U2, double inv_bdt, double *s, DevStats *stats,
-                                  double *partials, unsigned int *counter, int want_sums,
-                                  double inv_ncells, float *s32) {
-  int i[3];
-  double v = 0.0;
-  if (cell_of_thread<DIM>(g, i, vb)) {
-    const int c = cell_index(g, i);
-    const double *U[3] = {U0, U1, U2};
-    double acc = 0.0;
+__device__ __forceinline__ void divergence_body(unsigned b, const GridDev &g, const double *U0, const double *U1,
+                                                const double *U2, double inv_bdt, double *s, float *s32,
+                                                DevStats *stats, double *partials, unsigned int *counter,
+                                                int want_sums, double inv_ncells) {
+  int x, row0;
+  tile_pos(g, b, x, row0);
+  const double *U[3] = {U0, U1, U2};
+  double c[DIM];
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      int hi = i[a] + 1;
-      if (g.periodic[a] && hi == g.n[a]) hi = 0;
-      double d = U[a][face_index(g, a, i, hi)] - U[a][face_index(g, a, i, i[a])];
-      acc += d * g.inv_h[a];
+  for (int a = 0; a < DIM; ++a) c[a] = g.inv_h[a] * inv_bdt;
+  double sum = 0.0, sum2 = 0.0;
+  if (x < g.n[DIM - 1]) {
+    const int rend = min(row0 + g.cr, g.rows);
+    for (int row = row0; row < rend; ++row) {
+      int i[3];
+      cell_at<DIM>(g, row, x, i);
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        int hi = i[a] + 1;
+        if (g.periodic[a] && hi == g.n[a]) hi = 0;
+        const double d = U[a][face_index(g, a, i, hi)] - U[a][face_index(g, a, i, i[a])];
+        v = (a == 0) ? d * c[0] : fma(d, c[a], v);
+      }
+      const int ci = cell_index(g, i);
+      s[ci] = v;
+      if (s32) s32[ci] = d2f_rz_bits(v);   // FP32 copy read by the first FP32 transform pass
+      if (want_sums) {
+        sum += v;
+        sum2 = fma(v, v, sum2);
+      }
     }
-    v = acc * inv_bdt;
-    s[c] = v;
-    if (s32) s32[c] = d2f_rz_bits(v);   // FP32 copy read by the first FP32 transform pass
   }
   if (want_sums) {
-    if (grid_sum(v, partials, counter, &stats->sum_s, vb)) stats->mean_s = stats->sum_s * inv_ncells;
-    grid_sum(v * v, partials + (vb.nx * vb.ny * vb.nz), counter + 1, &stats->sum_s2, vb);
+    const VBlock vb = tile_block(g, b);
+    if (grid_sum(sum, partials, counter, &stats->sum_s, vb)) stats->mean_s = stats->sum_s * inv_ncells;
+    grid_sum(sum2, partials + g.nblk, counter + 1, &stats->sum_s2, vb);
   }
 }
 
 template <int DIM>
-__global__ void divergence_kernel(GridDev g, const double *U0, const double *U1,
-                                  const double *U2, double inv_bdt, double *s, DevStats *stats,
-                                  double *partials, unsigned int *counter, int want_sums,
-                                  double inv_ncells, float *s32) {
-  divergence_kernel_body<DIM>(hw_block(), g, U0, U1, U2, inv_bdt, s, stats, partials, counter, want_sums, inv_ncells, s32);
+__global__ void divergence_kernel(GridDev g, const double *U0, const double *U1, const double *U2,
+                                  double inv_bdt, double *s, float *s32, DevStats *stats, double *partials,
+                                  unsigned int *counter, int want_sums, double inv_ncells) {
+  pdl_enter();
+  divergence_body<DIM>(blockIdx.x, g, U0, U1, U2, inv_bdt, s, s32, stats, partials, counter, want_sums,
+                       inv_ncells);
 }
 
+// ----------------------------------------------------------------------------- flat kernels
 // Sum and sum of squares of a cell array (the source of pc_solve_poisson), and its mean.
-__device__ __forceinline__ void sum_kernel_body(const VBlock &vb, long long count, const double *x, DevStats *stats, double *partials,
-                           unsigned int *counter) {
-  long long c = (long long)vb.x * blockDim.x + threadIdx.x;
-  double v = (c < count) ? x[c] : 0.0;
-  if (grid_sum(v, partials, counter, &stats->sum_s, vb)) stats->mean_s = stats->sum_s / (double)count;
-  grid_sum(v * v, partials + vb.nx, counter + 1, &stats->sum_s2, vb);
+__device__ __forceinline__ void sum_kernel_body(unsigned b, unsigned nblk, long long count, const double *x,
+                                                DevStats *stats, double *partials, unsigned int *counter) {
+  double v1 = 0.0, v2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < kFlatPerThread; ++k) {
+    const long long c = (long long)b * kFlatPerBlock + k * kFlatThreads + threadIdx.x;
+    if (c < count) {
+      const double v = x[c];
+      v1 += v;
+      v2 = fma(v, v, v2);
+    }
+  }
+  const VBlock vb{b, 0u, 0u, nblk, 1u, 1u};
+  if (grid_sum(v1, partials, counter, &stats->sum_s, vb)) stats->mean_s = stats->sum_s / (double)count;
+  grid_sum(v2, partials + nblk, counter + 1, &stats->sum_s2, vb);
 }
 
 __global__ void sum_kernel(long long count, const double *x, DevStats *stats, double *partials,
                            unsigned int *counter) {
-  sum_kernel_body(hw_block(), count, x, stats, partials, counter);
+  pdl_enter();
+  sum_kernel_body(blockIdx.x, gridDim.x, count, x, stats, partials, counter);
 }
 
-// L_h p at cell i (ghost rules: Neumann p_ghost = p_edge, Dirichlet -p_edge, periodic wrap).
-// The two neighbours of cell c along axis a (ghost rules at the domain boundary).
+// ----------------------------------------------------------------------------- residual
+// The two neighbours of cell c along axis a (ghost rules at the domain boundary: Neumann
+// p_ghost = p_edge, Dirichlet -p_edge, periodic wrap).
 __device__ __forceinline__ void neighbours(const GridDev &g, const double *p, const int *i, int c,
                                            int a, double pc, double &pl, double &pr) {
   const int st = g.cs[a];
@@ -349,74 +429,105 @@ __device__ __forceinline__ void neighbours(const GridDev &g, const double *p, co
   else pr = g.hi_kind[a] ? -pc : pc;
 }
 
-template <int DIM>
-__device__ __forceinline__ double lap_at(const GridDev &g, const double *p, const int *i, int c, double pc) {
-  double acc = 0.0;
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    double pl, pr;
-    neighbours(g, p, i, c, a, pc, pl, pr);
-    acc = fma((pl + pr) - 2.0 * pc, g.inv_h2[a], acc);
-  }
-  return acc;
-}
-
-// r = s - mean(s) - L_h p in FP64, stored as FP32 (truncated by integer operations) for the
-// next FP32 solve; optionally ||r||^2.
+// r = s - mean(s) - L_h p, evaluated in double-float arithmetic (about 48 significant bits:
+// the FP64 pipe of this GPU runs at 1/64 of the FP32 rate) and stored as FP32 for the next
+// FP32 solve; optionally ||r||^2. The refinement converges to the solution of this residual,
+// so its ~2^-44 relative rounding bounds the attainable accuracy far below the 1e-10 target.
 template <int DIM, bool SINGULAR, bool WRITE_R, bool NORM>
-__device__ __forceinline__ void residual_kernel_body(const VBlock &vb, GridDev g, const double *__restrict__ s, const double *__restrict__ p,
-                                float *__restrict__ r, const DevStats *stats, double *res2,
-                                double *partials, unsigned int *counter) {
-  int i[3];
-  double v = 0.0;
-  if (cell_of_thread<DIM>(g, i, vb)) {
-    const int c = cell_index(g, i);
-    const double pc = p[c];
-    const double sc = SINGULAR ? s[c] - stats->mean_s : s[c];
-    v = sc - lap_at<DIM>(g, p, i, c, pc);
-    if (WRITE_R) r[c] = d2f_rz_bits(v);
+__device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, const double *__restrict__ s,
+                                              const double *__restrict__ p, float *__restrict__ r,
+                                              const DevStats *stats, double *res2, double *partials,
+                                              unsigned int *counter) {
+  int x, row0;
+  tile_pos(g, b, x, row0);
+  double nrm = 0.0;
+  if (x < g.n[DIM - 1]) {
+    DF mean{0.0f, 0.0f};
+    if (SINGULAR) mean = df_of(stats->mean_s);
+    const int rend = min(row0 + g.cr, g.rows);
+    for (int row = row0; row < rend; ++row) {
+      int i[3];
+      cell_at<DIM>(g, row, x, i);
+      const int c = cell_index(g, i);
+      const double pc = p[c];
+      const DF dc = df_of(pc);
+      DF acc{0.0f, 0.0f};
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        double pl, pr;
+        neighbours(g, p, i, c, a, pc, pl, pr);
+        const DF t = df_add(df_sub(df_of(pl), dc), df_sub(df_of(pr), dc));
+        acc = df_add(acc, df_mul(t, DF{g.ih2_hi[a], g.ih2_lo[a]}));
+      }
+      DF sc = df_of(s[c]);
+      if (SINGULAR) sc = df_sub(sc, mean);
+      const DF v = df_sub(sc, acc);
+      if (WRITE_R) r[c] = v.hi;
+      if (NORM) {
+        const double vd = f2d_bits(v.hi) + f2d_bits(v.lo);
+        nrm = fma(vd, vd, nrm);
+      }
+    }
   }
-  if (NORM) grid_sum(v * v, partials, counter, res2, vb);
+  if (NORM) grid_sum(nrm, partials, counter, res2, tile_block(g, b));
 }
 template <int DIM, bool SINGULAR, bool WRITE_R, bool NORM>
 __global__ void residual_kernel(GridDev g, const double *__restrict__ s, const double *__restrict__ p,
                                 float *__restrict__ r, const DevStats *stats, double *res2,
                                 double *partials, unsigned int *counter) {
-  residual_kernel_body<DIM, SINGULAR, WRITE_R, NORM>(hw_block(), g, s, p, r, stats, res2, partials, counter);
+  pdl_enter();
+  residual_body<DIM, SINGULAR, WRITE_R, NORM>(blockIdx.x, g, s, p, r, stats, res2, partials, counter);
 }
 
+// ----------------------------------------------------------------------------- gauge
 // Sum of p (and the corner value); the reducing block stores the gauge constant.
-__device__ __forceinline__ void gauge_sum_kernel_body(const VBlock &vb, long long ncells, const double *p, DevStats *stats, double *partials,
-                                 unsigned int *counter, int gauge_mode) {
-  long long c = (long long)vb.x * blockDim.x + threadIdx.x;
-  double v = (c < ncells) ? p[c] : 0.0;
-  if (c == 0) stats->corner_p = v;
-  if (grid_sum(v, partials, counter, &stats->sum_p, vb))
+__device__ __forceinline__ void gauge_sum_body(unsigned b, unsigned nblk, long long ncells, const double *p,
+                                               DevStats *stats, double *partials, unsigned int *counter,
+                                               int gauge_mode) {
+  DF acc{0.0f, 0.0f};
+#pragma unroll
+  for (int k = 0; k < kFlatPerThread; ++k) {
+    const long long c = (long long)b * kFlatPerBlock + k * kFlatThreads + threadIdx.x;
+    if (c < ncells) {
+      const double v = p[c];
+      if (c == 0) stats->corner_p = v;
+      acc = df_add(acc, df_of(v));
+    }
+  }
+  if (grid_sum(f2d_bits(acc.hi) + f2d_bits(acc.lo), partials, counter, &stats->sum_p, VBlock{b, 0u, 0u, nblk, 1u, 1u}))
     stats->shift = (gauge_mode == 1) ? stats->sum_p / (double)ncells : p[0];
 }
 
 __global__ void gauge_sum_kernel(long long ncells, const double *p, DevStats *stats, double *partials,
                                  unsigned int *counter, int gauge_mode) {
-  gauge_sum_kernel_body(hw_block(), ncells, p, stats, partials, counter, gauge_mode);
+  pdl_enter();
+  gauge_sum_body(blockIdx.x, gridDim.x, ncells, p, stats, partials, counter, gauge_mode);
 }
 
 // p -= shift (gauge), and the (hi, lo) FP32 split of p for the compensated gradient.
 template <bool GAUGE, bool SPLIT>
-__device__ __forceinline__ void finalize_p_kernel_body(const VBlock &vb, int ncells, double *__restrict__ p, const DevStats *stats,
-                                  float2 *__restrict__ p2) {
-  int c = vb.x * blockDim.x + threadIdx.x;
-  if (c >= ncells) return;
-  double v = p[c];
-  if (GAUGE) {
-    v -= stats->shift;
-    p[c] = v;
+__device__ __forceinline__ void finalize_p_body(unsigned b, int ncells, double *__restrict__ p,
+                                                const DevStats *stats, float2 *__restrict__ p2) {
+  double shift = 0.0;
+  if (GAUGE) shift = stats->shift;
+#pragma unroll
+  for (int k = 0; k < kFlatPerThread; ++k) {
+    const int c = (int)b * kFlatPerBlock + k * kFlatThreads + threadIdx.x;
+    if (c < ncells) {
+      double v = p[c];
+      if (GAUGE) {
+        v -= shift;
+        p[c] = v;
+      }
+      if (SPLIT) p2[c] = as_pair(v);
+    }
   }
-  if (SPLIT) p2[c] = as_pair(v);
 }
 template <bool GAUGE, bool SPLIT>
 __global__ void finalize_p_kernel(int ncells, double *__restrict__ p, const DevStats *stats,
                                   float2 *__restrict__ p2) {
-  finalize_p_kernel_body<GAUGE, SPLIT>(hw_block(), ncells, p, stats, p2);
+  pdl_enter();
+  finalize_p_body<GAUGE, SPLIT>(blockIdx.x, ncells, p, stats, p2);
 }
 
 // ----------------------------------------------------------------------------- gradient
@@ -429,6 +540,7 @@ __global__ void gradient64_kernel(int N, int K, const int32_t *__restrict__ col,
                                   const uint8_t *__restrict__ type, const VT *__restrict__ u,
                                   double inv_dt, double dt, double beta, VT *__restrict__ uo,
                                   VT *__restrict__ fo) {
+  pdl_enter();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double g[DIM];
@@ -496,6 +608,7 @@ __global__ void gradient_mixed_kernel(int N, int K, const int32_t *__restrict__ 
                                       const uint8_t *__restrict__ type, const VT *__restrict__ u,
                                       double inv_dt, double dt, double beta, VT *__restrict__ uo,
                                       VT *__restrict__ fo) {
+  pdl_enter();
   gradient_mixed_kernel_body<VT, DIM>(hw_block(), N, K, col, D2, p2, type, u, inv_dt, dt, beta, uo, fo);
 }
 
@@ -504,31 +617,37 @@ __global__ void gradient_mixed_kernel(int N, int K, const int32_t *__restrict__ 
 template <int DIM>
 __global__ void div_check_kernel(GridDev g, const double *U0, const double *U1,
                                  const double *U2, const double *p, double bdt, DevStats *stats) {
-  int i[3];
+  pdl_enter();
+  int x, row0;
+  tile_pos(g, blockIdx.x, x, row0);
+  const double *U[3] = {U0, U1, U2};
   double v = 0.0;
-  if (cell_of_thread<DIM>(g, i, hw_block())) {
-    const int c = cell_index(g, i);
-    const double *U[3] = {U0, U1, U2};
-    double pc = p[c];
-    double acc = 0.0;
+  if (x < g.n[DIM - 1]) {
+    const int rend = min(row0 + g.cr, g.rows);
+    for (int row = row0; row < rend; ++row) {
+      int i[3];
+      cell_at<DIM>(g, row, x, i);
+      const int c = cell_index(g, i);
+      const double pc = p[c];
+      double acc = 0.0;
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      // gradient on the low and high faces of the cell
-      double pl, pr;
-      neighbours(g, p, i, c, a, pc, pl, pr);
-      int hi = i[a] + 1;
-      if (g.periodic[a] && hi == g.n[a]) hi = 0;
-      double Ulo = U[a][face_index(g, a, i, i[a])] - bdt * (pc - pl) * g.inv_h[a];
-      double Uhi = U[a][face_index(g, a, i, hi)] - bdt * (pr - pc) * g.inv_h[a];
-      acc += (Uhi - Ulo) * g.inv_h[a];
+      for (int a = 0; a < DIM; ++a) {
+        // gradient on the low and high faces of the cell
+        double pl, pr;
+        neighbours(g, p, i, c, a, pc, pl, pr);
+        int hi = i[a] + 1;
+        if (g.periodic[a] && hi == g.n[a]) hi = 0;
+        const double Ulo = U[a][face_index(g, a, i, i[a])] - bdt * (pc - pl) * g.inv_h[a];
+        const double Uhi = U[a][face_index(g, a, i, hi)] - bdt * (pr - pc) * g.inv_h[a];
+        acc += (Uhi - Ulo) * g.inv_h[a];
+      }
+      v = fmax(v, fabs(acc));
     }
-    v = fabs(acc);
   }
   block_max_update(v, &stats->max_div);
 }
 
 static GridDev grid_dev(const Plan *p);
-static void cell_launch(const Plan *p, dim3 &grid, dim3 &block);
 
 // ----------------------------------------------------------------------------- batched kernels
 // One launch per pipeline stage for a whole batch of problems. seg[p] is the first block of
@@ -546,29 +665,27 @@ __device__ __forceinline__ int batch_problem_of(const int *seg, int count, int b
 __device__ __forceinline__ VBlock flat_block(int local, int nblocks) {
   return VBlock{(unsigned)local, 0u, 0u, (unsigned)nblocks, 1u, 1u};
 }
-__device__ __forceinline__ VBlock cell_block(const BatchProblem &q, int local) {
-  const unsigned x = local % q.cgx, yz = local / q.cgx;
-  return VBlock{x, yz % q.cgy, yz / q.cgy, q.cgx, q.cgy, q.cgz};
-}
 
 __global__ void batch_zero_stats(const BatchProblem *__restrict__ P) {
+  pdl_enter();
   unsigned *w = reinterpret_cast<unsigned *>(P[blockIdx.x].ds);
   for (int k = threadIdx.x; k < (int)(sizeof(DevStats) / 4); k += blockDim.x) w[k] = 0u;
 }
 
 template <typename VT>
 __global__ void batch_prep(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
+  pdl_enter();
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
-  const int nb = seg[pi + 1] - seg[pi];
-  const VBlock vb = flat_block(blockIdx.x - seg[pi], nb);
+  const unsigned lb = blockIdx.x - seg[pi];
   const int cnt = q.dim * q.N;
-  if (q.f) prep_kernel_body<VT, true, false, true>(vb, cnt, (const VT *)q.u, (const VT *)q.f, q.dt, nullptr, q.u2, nullptr);
-  else prep_kernel_body<VT, false, false, true>(vb, cnt, (const VT *)q.u, nullptr, q.dt, nullptr, q.u2, nullptr);
+  if (q.f) prep_kernel_body<VT, true, false, true>(lb, cnt, (const VT *)q.u, (const VT *)q.f, q.dt, nullptr, q.u2, nullptr);
+  else prep_kernel_body<VT, false, false, true>(lb, cnt, (const VT *)q.u, nullptr, q.dt, nullptr, q.u2, nullptr);
 }
 
 template <int KC>
 __global__ void batch_transfer(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count, int a) {
+  pdl_enter();
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
   const VBlock vb = flat_block(blockIdx.x - seg[pi], seg[pi + 1] - seg[pi]);
@@ -576,47 +693,51 @@ __global__ void batch_transfer(const BatchProblem *__restrict__ P, const int *__
 }
 
 __global__ void batch_divergence(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
+  pdl_enter();
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
-  const VBlock vb = cell_block(q, blockIdx.x - seg[pi]);
+  const unsigned lb = blockIdx.x - seg[pi];
   if (q.g.dim == 2)
-    divergence_kernel_body<2>(vb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, q.s64, q.ds, q.partials, q.counters,
-                              q.singular, q.inv_ncells, q.s32);
+    divergence_body<2>(lb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, q.s64, q.s32, q.ds, q.partials, q.counters,
+                       q.singular, q.inv_ncells);
   else
-    divergence_kernel_body<3>(vb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, q.s64, q.ds, q.partials, q.counters,
-                              q.singular, q.inv_ncells, q.s32);
+    divergence_body<3>(lb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, q.s64, q.s32, q.ds, q.partials, q.counters,
+                       q.singular, q.inv_ncells);
 }
 
 __global__ void batch_residual(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
+  pdl_enter();
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
-  const VBlock vb = cell_block(q, blockIdx.x - seg[pi]);
+  const unsigned lb = blockIdx.x - seg[pi];
   if (q.g.dim == 2) {
-    if (q.singular) residual_kernel_body<2, true, true, false>(vb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
-    else residual_kernel_body<2, false, true, false>(vb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
+    if (q.singular) residual_body<2, true, true, false>(lb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
+    else residual_body<2, false, true, false>(lb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
   } else {
-    if (q.singular) residual_kernel_body<3, true, true, false>(vb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
-    else residual_kernel_body<3, false, true, false>(vb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
+    if (q.singular) residual_body<3, true, true, false>(lb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
+    else residual_body<3, false, true, false>(lb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
   }
 }
 
 __global__ void batch_gauge_sum(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
+  pdl_enter();
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
-  const VBlock vb = flat_block(blockIdx.x - seg[pi], seg[pi + 1] - seg[pi]);
-  gauge_sum_kernel_body(vb, q.ncells, q.p, q.ds, q.partials, q.counters, q.gmode);
+  gauge_sum_body(blockIdx.x - seg[pi], seg[pi + 1] - seg[pi], q.ncells, q.p, q.ds, q.partials, q.counters, q.gmode);
 }
 
 __global__ void batch_finalize(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
+  pdl_enter();
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
-  const VBlock vb = flat_block(blockIdx.x - seg[pi], seg[pi + 1] - seg[pi]);
-  if (q.gmode) finalize_p_kernel_body<true, true>(vb, q.ncells, q.p, q.ds, q.p2);
-  else finalize_p_kernel_body<false, true>(vb, q.ncells, q.p, q.ds, q.p2);
+  const unsigned lb = blockIdx.x - seg[pi];
+  if (q.gmode) finalize_p_body<true, true>(lb, q.ncells, q.p, q.ds, q.p2);
+  else finalize_p_body<false, true>(lb, q.ncells, q.p, q.ds, q.p2);
 }
 
 template <typename VT, int DIM>
 __global__ void batch_gradient(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
+  pdl_enter();
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
   const VBlock vb = flat_block(blockIdx.x - seg[pi], seg[pi + 1] - seg[pi]);
@@ -630,25 +751,25 @@ void batch_launch(int stage, int variant, const BatchProblem *P, const int *seg,
   if (total_blocks <= 0) return;
   const int T = 256;
   switch (stage) {
-    case BATCH_ZERO: batch_zero_stats<<<count, 64, 0, st>>>(P); break;
+    case BATCH_ZERO: launch_pdl(batch_zero_stats, count, 64, 0, st, P); break;
     case BATCH_PREP:
-      if (variant == PC_DTYPE_F64) batch_prep<double><<<total_blocks, T, 0, st>>>(P, seg, count);
-      else batch_prep<float><<<total_blocks, T, 0, st>>>(P, seg, count);
+      if (variant == PC_DTYPE_F64) launch_pdl(batch_prep<double>, total_blocks, T, 0, st, P, seg, count);
+      else launch_pdl(batch_prep<float>, total_blocks, T, 0, st, P, seg, count);
       break;
     case BATCH_TRANSFER:
-      if (variant == 12) batch_transfer<12><<<total_blocks, T, 0, st>>>(P, seg, count, extra);
-      else if (variant == 27) batch_transfer<27><<<total_blocks, T, 0, st>>>(P, seg, count, extra);
-      else batch_transfer<0><<<total_blocks, T, 0, st>>>(P, seg, count, extra);
+      if (variant == 12) launch_pdl(batch_transfer<12>, total_blocks, T, 0, st, P, seg, count, extra);
+      else if (variant == 27) launch_pdl(batch_transfer<27>, total_blocks, T, 0, st, P, seg, count, extra);
+      else launch_pdl(batch_transfer<0>, total_blocks, T, 0, st, P, seg, count, extra);
       break;
-    case BATCH_DIVERGENCE: batch_divergence<<<total_blocks, T, 0, st>>>(P, seg, count); break;
-    case BATCH_RESIDUAL: batch_residual<<<total_blocks, T, 0, st>>>(P, seg, count); break;
-    case BATCH_GAUGE_SUM: batch_gauge_sum<<<total_blocks, T, 0, st>>>(P, seg, count); break;
-    case BATCH_FINALIZE: batch_finalize<<<total_blocks, T, 0, st>>>(P, seg, count); break;
+    case BATCH_DIVERGENCE: launch_pdl(batch_divergence, total_blocks, T, 0, st, P, seg, count); break;
+    case BATCH_RESIDUAL: launch_pdl(batch_residual, total_blocks, T, 0, st, P, seg, count); break;
+    case BATCH_GAUGE_SUM: launch_pdl(batch_gauge_sum, total_blocks, T, 0, st, P, seg, count); break;
+    case BATCH_FINALIZE: launch_pdl(batch_finalize, total_blocks, T, 0, st, P, seg, count); break;
     case BATCH_GRADIENT:
-      if (variant == 2 * 10 + PC_DTYPE_F64) batch_gradient<double, 2><<<total_blocks, T, 0, st>>>(P, seg, count);
-      else if (variant == 3 * 10 + PC_DTYPE_F64) batch_gradient<double, 3><<<total_blocks, T, 0, st>>>(P, seg, count);
-      else if (variant == 2 * 10 + PC_DTYPE_F32) batch_gradient<float, 2><<<total_blocks, T, 0, st>>>(P, seg, count);
-      else batch_gradient<float, 3><<<total_blocks, T, 0, st>>>(P, seg, count);
+      if (variant == 2 * 10 + PC_DTYPE_F64) launch_pdl(batch_gradient<double, 2>, total_blocks, T, 0, st, P, seg, count);
+      else if (variant == 3 * 10 + PC_DTYPE_F64) launch_pdl(batch_gradient<double, 3>, total_blocks, T, 0, st, P, seg, count);
+      else if (variant == 2 * 10 + PC_DTYPE_F32) launch_pdl(batch_gradient<float, 2>, total_blocks, T, 0, st, P, seg, count);
+      else launch_pdl(batch_gradient<float, 3>, total_blocks, T, 0, st, P, seg, count);
       break;
   }
 }
@@ -656,24 +777,20 @@ void batch_launch(int stage, int variant, const BatchProblem *P, const int *seg,
 // Block counts of each stage for one problem (identical to the single-problem launches).
 void batch_block_counts(const Plan *p, int *nb) {
   const long long N = p->N, nc = p->ncells;
-  dim3 cg, cb;
-  cell_launch(p, cg, cb);
+  const GridDev g = grid_dev(p);
   nb[BATCH_ZERO] = 1;
-  nb[BATCH_PREP] = grid_for((long long)p->dim * N, 256);
+  nb[BATCH_PREP] = grid_for((long long)p->dim * N, kFlatPerBlock);
   for (int a = 0; a < 3; ++a) nb[BATCH_TRANSFER + a] = a < p->dim ? grid_for(p->nface_total[a], 256) : 0;
-  nb[BATCH_DIVERGENCE] = (int)(cg.x * cg.y * cg.z);
-  nb[BATCH_RESIDUAL] = (int)(cg.x * cg.y * cg.z);
-  nb[BATCH_GAUGE_SUM] = p->singular ? grid_for(nc, 256) : 0;
-  nb[BATCH_FINALIZE] = grid_for(nc, 256);
+  nb[BATCH_DIVERGENCE] = g.nblk;
+  nb[BATCH_RESIDUAL] = g.nblk;
+  nb[BATCH_GAUGE_SUM] = p->singular ? grid_for(nc, kFlatPerBlock) : 0;
+  nb[BATCH_FINALIZE] = grid_for(nc, kFlatPerBlock);
   nb[BATCH_GRADIENT] = grid_for(N, 256);
 }
 
 void batch_problem_fill(const Plan *p, const pc_project_args &a, BatchProblem &q) {
   memset(&q, 0, sizeof(q));
   q.g = grid_dev(p);
-  dim3 cg, cb;
-  cell_launch(p, cg, cb);
-  q.cgx = cg.x; q.cgy = cg.y; q.cgz = cg.z;
   q.dim = p->dim; q.N = (int)p->N; q.ncells = (int)p->ncells; q.K = p->K; q.Kg = p->Kg;
   q.singular = p->singular;
   q.gmode = p->singular ? (p->gauge == 1 ? 2 : 1) : 0;
@@ -706,6 +823,8 @@ static GridDev grid_dev(const Plan *p) {
       g.hi_kind[a] = ax.bc_hi == PC_BC_DIRICHLET;
       g.inv_h[a] = 1.0 / ax.h;
       g.inv_h2[a] = 1.0 / (ax.h * ax.h);
+      g.ih2_hi[a] = (float)g.inv_h2[a];
+      g.ih2_lo[a] = (float)(g.inv_h2[a] - (double)g.ih2_hi[a]);
     } else {
       g.n[a] = 1;
       g.nf[a] = 1;
@@ -723,17 +842,26 @@ static GridDev grid_dev(const Plan *p) {
     }
     for (int b = p->dim; b < 3; ++b) g.fs[ax][b] = 0;
   }
+  // cell tiles: 2^tw_bits positions of the last axis (32..256) x 2^th_bits thread rows, cr rows
+  // per thread; cr shrinks while the grid would not give two blocks per SM
+  const int nl = g.n[p->dim - 1];
+  g.rows = (int)(p->ncells / nl);
+  g.tw_bits = 5;
+  while ((1 << g.tw_bits) < nl && g.tw_bits < 8) ++g.tw_bits;
+  g.th_bits = 8 - g.tw_bits;
+  g.gx = (nl + (1 << g.tw_bits) - 1) >> g.tw_bits;
+  auto nblk_for = [&](int cr) {
+    const long long rpb = (long long)cr << g.th_bits;
+    return (long long)g.gx * ((g.rows + rpb - 1) / rpb);
+  };
+  g.cr = 4;
+  while (g.cr > 1 && nblk_for(g.cr) < 2 * 152) g.cr >>= 1;
+  g.nblk = (int)nblk_for(g.cr);
   return g;
 }
 
 // Launch shape covering every cell: x over the last axis, y/z over the others.
-static void cell_launch(const Plan *p, dim3 &grid, dim3 &block) {
-  const int last = p->dim - 1;
-  block = dim3(256);
-  unsigned gx = (unsigned)((p->n[last] + 255) / 256);
-  if (p->dim == 2) grid = dim3(gx, (unsigned)p->n[0], 1);
-  else grid = dim3(gx, (unsigned)p->n[1], (unsigned)p->n[0]);
-}
+
 
 static bool is_device_ptr(const void *ptr) {
   if (!ptr) return true;
@@ -746,13 +874,13 @@ static bool is_device_ptr(const void *ptr) {
 }
 
 // Grid-level solve: s64 (device) -> p (device, FP64), gauge applied; fills dstats fields.
-static void launch_residual(bool singular, bool write_r, bool norm, dim3 cg, dim3 cb, cudaStream_t st,
+static void launch_residual(bool singular, bool write_r, bool norm, cudaStream_t st,
                             const GridDev &g, const double *s, const double *p, float *r, DevStats *ds,
                             double *res2, double *partials, unsigned int *counters) {
 #define PC_RES(S, W, N)                                                                      \
   do {                                                                                       \
-    if (g.dim == 2) residual_kernel<2, S, W, N><<<cg, cb, 0, st>>>(g, s, p, r, ds, res2, partials, counters); \
-    else residual_kernel<3, S, W, N><<<cg, cb, 0, st>>>(g, s, p, r, ds, res2, partials, counters); \
+    if (g.dim == 2) launch_pdl(residual_kernel<2, S, W, N>, g.nblk, 256, 0, st, g, s, p, r, ds, res2, partials, counters); \
+    else launch_pdl(residual_kernel<3, S, W, N>, g.nblk, 256, 0, st, g, s, p, r, ds, res2, partials, counters); \
   } while (0)
   if (singular) {
     if (write_r) { if (norm) PC_RES(true, true, true); else PC_RES(true, true, false); }
@@ -767,10 +895,8 @@ static void launch_residual(bool singular, bool write_r, bool norm, dim3 cg, dim
 static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_final_residual,
                             cudaStream_t st, const float *s32 = nullptr) {
   const long long nc = p->ncells;
-  const int T = 256;
+  const int T = kFlatThreads;
   GridDev g = grid_dev(p);
-  dim3 cg, cb;
-  cell_launch(p, cg, cb);
   if (p->precision == PC_PREC_FP64) {
     PC_TRY(solve_fp64_grid(p, s64, pout, st));
     prof_mark(p, st, 3);
@@ -781,7 +907,7 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
     prof_mark(p, st, 3);
     for (int it = 0; it < sweeps; ++it) {
       float *r32 = reinterpret_cast<float *>(p->work64);   // work64 is free in mixed mode
-      launch_residual(p->singular, true, want_final_residual, cg, cb, st, g, s64, pout, r32, p->dstats,
+      launch_residual(p->singular, true, want_final_residual, st, g, s64, pout, r32, p->dstats,
                       &p->dstats->res2[it], p->partials, p->counters);
       count_launch(p);
       prof_mark(p, st, 4);
@@ -791,7 +917,7 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
   }
   if (want_final_residual) {
     int it = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
-    launch_residual(p->singular, false, true, cg, cb, st, g, s64, pout, nullptr, p->dstats,
+    launch_residual(p->singular, false, true, st, g, s64, pout, nullptr, p->dstats,
                     &p->dstats->res2[it], p->partials, p->counters);
     count_launch(p);
     prof_mark(p, st, 7);
@@ -799,14 +925,15 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
   // gauge (singular problems), then the FP32 split of p for the mixed gradient
   int gmode = p->singular ? (p->gauge == 1 ? 2 : 1) : 0;
   if (gmode) {
-    gauge_sum_kernel<<<grid_for(nc, T), T, 0, st>>>(nc, pout, p->dstats, p->partials, p->counters, gmode);
+    launch_pdl(gauge_sum_kernel, grid_for(nc, kFlatPerBlock), T, 0, st, nc, pout, p->dstats, p->partials, p->counters, gmode);
     count_launch(p);
   }
   bool mixed = p->precision != PC_PREC_FP64;
   if (gmode || mixed) {
-    if (gmode && mixed) finalize_p_kernel<true, true><<<grid_for(nc, T), T, 0, st>>>((int)nc, pout, p->dstats, p->p2);
-    else if (gmode) finalize_p_kernel<true, false><<<grid_for(nc, T), T, 0, st>>>((int)nc, pout, p->dstats, nullptr);
-    else finalize_p_kernel<false, true><<<grid_for(nc, T), T, 0, st>>>((int)nc, pout, p->dstats, p->p2);
+    const int G = grid_for(nc, kFlatPerBlock);
+    if (gmode && mixed) launch_pdl(finalize_p_kernel<true, true>, G, T, 0, st, (int)nc, pout, p->dstats, p->p2);
+    else if (gmode) launch_pdl(finalize_p_kernel<true, false>, G, T, 0, st, (int)nc, pout, p->dstats, nullptr);
+    else launch_pdl(finalize_p_kernel<false, true>, G, T, 0, st, (int)nc, pout, p->dstats, p->p2);
     count_launch(p);
   }
   prof_mark(p, st, 5);
@@ -869,29 +996,27 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
     long long rows = p->nface_total[a];
     if (mixed) {
       if (p->K == 12)
-        transfer_mixed_kernel<12><<<grid_for(rows, T), T, 0, st>>>((int)rows, p->K, p->fcol[a], p->fw2[a],
+        launch_pdl(transfer_mixed_kernel<12>, grid_for(rows, T), T, 0, st, (int)rows, p->K, p->fcol[a], p->fw2[a],
                                                                    p->u2 + (long long)a * N, p->U64[a]);
       else if (p->K == 27)
-        transfer_mixed_kernel<27><<<grid_for(rows, T), T, 0, st>>>((int)rows, p->K, p->fcol[a], p->fw2[a],
+        launch_pdl(transfer_mixed_kernel<27>, grid_for(rows, T), T, 0, st, (int)rows, p->K, p->fcol[a], p->fw2[a],
                                                                    p->u2 + (long long)a * N, p->U64[a]);
       else
-        transfer_mixed_kernel<0><<<grid_for(rows, T), T, 0, st>>>((int)rows, p->K, p->fcol[a], p->fw2[a],
+        launch_pdl(transfer_mixed_kernel<0>, grid_for(rows, T), T, 0, st, (int)rows, p->K, p->fcol[a], p->fw2[a],
                                                                   p->u2 + (long long)a * N, p->U64[a]);
     }
     else
-      transfer64_kernel<<<grid_for(rows, T), T, 0, st>>>((int)rows, p->K, p->fcol[a], p->fw64[a],
+      launch_pdl(transfer64_kernel, grid_for(rows, T), T, 0, st, (int)rows, p->K, p->fcol[a], p->fw64[a],
                                                          p->ut64 + (long long)a * N, p->U64[a]);
     count_launch(p);
   }
   prof_mark(p, st, 1);
   GridDev g = grid_dev(p);
-  dim3 cg, cb;
-  cell_launch(p, cg, cb);
   {
     auto divk = (d == 2) ? divergence_kernel<2> : divergence_kernel<3>;
-    divk<<<cg, cb, 0, st>>>(g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt), p->s64, p->dstats,
-                            p->partials, p->counters, (p->singular || stats) ? 1 : 0, 1.0 / (double)nc,
-                            mixed ? reinterpret_cast<float *>(p->work64) : nullptr);
+    launch_pdl(divk, g.nblk, 256, 0, st, g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt), p->s64,
+               mixed ? reinterpret_cast<float *>(p->work64) : nullptr, p->dstats, p->partials, p->counters,
+               (p->singular || stats) ? 1 : 0, 1.0 / (double)nc);
   }
   count_launch(p);
   prof_mark(p, st, 2);
@@ -901,26 +1026,26 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   const void *ug = du;
   if (p->vdtype == PC_DTYPE_F64) {
     if (mixed) {
-      if (d == 2) gradient_mixed_kernel<double, 2><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
-      else gradient_mixed_kernel<double, 3><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
+      if (d == 2) launch_pdl(gradient_mixed_kernel<double, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
+      else launch_pdl(gradient_mixed_kernel<double, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
     } else {
-      if (d == 2) gradient64_kernel<double, 2><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
-      else gradient64_kernel<double, 3><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
+      if (d == 2) launch_pdl(gradient64_kernel<double, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
+      else launch_pdl(gradient64_kernel<double, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
     }
   } else {
     if (mixed) {
-      if (d == 2) gradient_mixed_kernel<float, 2><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
-      else gradient_mixed_kernel<float, 3><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
+      if (d == 2) launch_pdl(gradient_mixed_kernel<float, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
+      else launch_pdl(gradient_mixed_kernel<float, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
     } else {
-      if (d == 2) gradient64_kernel<float, 2><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
-      else gradient64_kernel<float, 3><<<grid_for(N, T), T, 0, st>>>((int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
+      if (d == 2) launch_pdl(gradient64_kernel<float, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
+      else launch_pdl(gradient64_kernel<float, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
     }
   }
   count_launch(p);
   prof_mark(p, st, 6);
   if (stats) {
     auto chk = (d == 2) ? div_check_kernel<2> : div_check_kernel<3>;
-    chk<<<cg, cb, 0, st>>>(g, p->U64[0], p->U64[1], p->U64[2], dp, p->beta * dt, p->dstats);
+    launch_pdl(chk, g.nblk, 256, 0, st, g, p->U64[0], p->U64[1], p->U64[2], dp, p->beta * dt, p->dstats);
     count_launch(p);
     prof_mark(p, st, 7);
   }
@@ -937,7 +1062,7 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
 // statistics): source sums, transform solve, gauge. Used by the allocation-free entry point.
 pc_status solve_grid_device(Plan *p, const double *s, double *pout, cudaStream_t st) {
   const long long nc = p->ncells;
-  sum_kernel<<<grid_for(nc, 256), 256, 0, st>>>(nc, s, p->dstats, p->partials, p->counters);
+  launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, s, p->dstats, p->partials, p->counters);
   count_launch(p);
   PC_CUDA_TRY(cudaGetLastError());
   return solve_grid(p, s, pout, false, st);
@@ -952,7 +1077,7 @@ static pc_status solve_impl(Plan *p, const double *s, double *p_out, pc_stats *s
   if (hp) dp = p->stage_p;
   prof_begin(p, st);
   PC_CUDA_TRY(cudaMemsetAsync(p->dstats, 0, sizeof(DevStats), st));
-  sum_kernel<<<grid_for(nc, 256), 256, 0, st>>>(nc, ds, p->dstats, p->partials, p->counters);
+  launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, ds, p->dstats, p->partials, p->counters);
   count_launch(p);
   prof_mark(p, st, 2);
   PC_TRY(solve_grid(p, ds, dp, stats != nullptr, st));

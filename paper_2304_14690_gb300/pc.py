@@ -107,6 +107,10 @@ FUNCTIONS = {
                                                ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p]),
     "pc_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Profile)]),
+    "pc_plan_set_transform_slots": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "pc_plan_get_transform_slots": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.POINTER(ctypes.c_int)]),
+    "pc_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "pc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pc_last_error_message": (ctypes.c_char_p, []),
 }
@@ -229,6 +233,29 @@ class Plan:
 
     def graphs(self, on=True):
         _check(load().pc_set_graphs(self.handle, 1 if on else 0))
+
+    def _prec_code(self, precision):
+        return PRECISION[precision if precision is not None else self.precision]
+
+    def set_slots(self, axis, slots, precision=None):
+        """Slots per thread of the transform passes along axis (2, 4, 8 or 16)."""
+        _check(load().pc_plan_set_transform_slots(self.handle, axis, self._prec_code(precision), slots))
+
+    def slots(self, precision=None):
+        """Current slots per thread of every axis for the given (default: the plan's) precision."""
+        out = []
+        for a in range(self.dim):
+            v = ctypes.c_int()
+            _check(load().pc_plan_get_transform_slots(self.handle, a, self._prec_code(precision), ctypes.byref(v)))
+            out.append(v.value)
+        return out
+
+    def autotune(self, stream=None):
+        """Time the plan's transform solve for every slot count of every axis and keep the
+        fastest schedule; returns its milliseconds per solve."""
+        ms = ctypes.c_double()
+        _check(load().pc_plan_autotune(self.handle, _stream_handle(stream), ctypes.byref(ms)))
+        return ms.value
 
     def profile(self, on=True):
         _check(load().pc_profile_enable(self.handle, 1 if on else 0))
