@@ -122,6 +122,66 @@ def laplacian(p, g):
     return out
 
 
+# Error-free transformations for a compensated residual (Knuth's TwoSum; Dekker's splitting
+# and product, 1971). numpy evaluates each elementwise operation separately (no fused
+# multiply-add), as these algorithms require.
+def _two_sum(a, b):
+    s = a + b
+    z = s - a
+    return s, (a - (s - z)) + (b - z)
+
+
+_DEKKER = 134217729.0          # 2^27 + 1
+
+
+def _split(x):
+    t = _DEKKER * x
+    hi = t - (t - x)
+    return hi, x - hi
+
+
+def _two_prod(a, b):
+    p = a * b
+    ah, al = _split(a)
+    bh, bl = _split(b)
+    return p, ((ah * bh - p) + ah * bl + al * bh) + al * bl
+
+
+def _dd_add(ah, al, bh, bl):
+    s, e = _two_sum(ah, bh)
+    e = e + (al + bl)
+    h = s + e
+    return h, e - (h - s)
+
+
+def _dd_div(ah, al, b):
+    q = ah / b
+    p, e = _two_prod(q, b)
+    r = ((ah - p) - e + al) / b
+    h = q + r
+    return h, r - (h - q)
+
+
+def residual_compensated(s, p, g):
+    """s - L_h p in double-double arithmetic (about 106 significant bits), rounded to FP64.
+
+    Same operator as laplacian(): (p_{j-1} - 2 p_j + p_{j+1}) / (h_a h_a) per axis with the
+    ghost rules; only the arithmetic differs."""
+    rh = np.array(s, dtype=np.float64, copy=True)
+    rl = np.zeros_like(rh)
+    for a in range(g.dim):
+        q = _ghost_pad(p, g, a)
+        n = p.shape[a]
+        left = np.take(q, range(0, n), axis=a)
+        mid = np.take(q, range(1, n + 1), axis=a)
+        right = np.take(q, range(2, n + 2), axis=a)
+        th, tl = _two_sum(left, right)
+        th, tl = _dd_add(th, tl, -2.0 * mid, np.zeros_like(mid))
+        th, tl = _dd_div(th, tl, g.h[a] * g.h[a])
+        rh, rl = _dd_add(rh, rl, -th, -tl)
+    return rh + rl
+
+
 def face_gradient(p, g, a):
     """G_h p on the faces normal to axis a: (p_right - p_left)/h_a using the ghost rules.
 

@@ -189,3 +189,40 @@ def test_corner_gauge():
     assert p[0, 0] == 0.0
     pm, _ = P.solve(s, g)
     assert np.abs((p - p.mean()) - pm).max() < 1e-13
+
+
+@pytest.mark.parametrize("bc", [("P", "P"), ("W", "W"), ("I", "D"), ("D", "W")])
+def test_compensated_residual_is_exact(bc, rng):
+    """grid.residual_compensated against exact rational arithmetic (fractions.Fraction), on a
+    source that nearly cancels L_h p (residual ~1e-9 of terms ~1e4): the double-double
+    evaluation gives the exact residual to a few ulps of the residual itself, where an FP64
+    evaluation would be wrong in every digit."""
+    from fractions import Fraction
+    n = (6, 5)
+    g = G.Grid(2, n, (0.0, 0.0), (0.3, 0.7), (bc[0], "W"), (bc[1], "W"))
+    p = rng.normal(size=n) * 1e3
+    s = G.laplacian(p, g) + rng.normal(size=n) * 1e-9
+    got = G.residual_compensated(s, p, g)
+    pad = [G._ghost_pad(p, g, a) for a in range(2)]
+    for i in range(n[0]):
+        for j in range(n[1]):
+            acc = Fraction(s[i, j])
+            for a, (di, dj) in enumerate(((1, 0), (0, 1))):
+                q = pad[a]
+                ci, cj = i + di, j + dj              # centre in the padded array
+                t = Fraction(q[ci - di, cj - dj]) - 2 * Fraction(q[ci, cj]) + Fraction(q[ci + di, cj + dj])
+                acc -= t / Fraction(g.h[a] * g.h[a])
+            exact = float(acc)
+            assert abs(got[i, j] - exact) <= 4 * np.finfo(float).eps * abs(exact)
+
+
+def test_refined_solve_is_a_fixed_point(rng):
+    """On a 1024 x 512 grid with the channel's boundary pairs, the oracle's solve (dense
+    expansion + one compensated refinement sweep) is at the fixed point of refinement: a
+    further sweep changes it by less than 1e-15 (relative L2)."""
+    g = G.Grid(2, (1024, 512), (0.0, 0.0), (20.0 / 1024, 10.0 / 512), ("I", "W"), ("D", "W"))
+    s = rng.normal(size=g.shape)
+    p, _ = P.solve(s, g)
+    bases = [P.eigenbasis(P.axis_kind(g, a), g.n[a], g.h[a]) for a in range(2)]
+    d = P._expand_solve(G.residual_compensated(s, p, g), g, bases, False)
+    assert np.linalg.norm(d) <= 1e-15 * np.linalg.norm(p)
