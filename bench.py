@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-problem batch measurement")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--no-3d", action="store_true", help="skip the 256x128x128 box-with-sphere measurement")
+    ap.add_argument("--steps-3d", type=int, default=20)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the accuracy, plain-FP64 and end-to-end measurements that follow the "
                          "timed region (shorter profiler launch lists); the timed step is unchanged")
@@ -229,6 +231,26 @@ def ncu_traffic(phase):
         return None
 
 
+# ----------------------------------------------------------------------------- ranks
+
+def max_over_ranks(x, world, device=None):
+    """The maximum of x over all ranks (x itself with one rank). Under NCCL the tensor lives on
+    the rank's GPU; under gloo on the host."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, steps, total_ms, world):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank * steps / (total_ms * 1e-3)
+
+
 # ----------------------------------------------------------------------------- our arm
 
 def run_ours(args, rank, world, local_rank):
@@ -274,13 +296,9 @@ def run_ours(args, rank, world, local_rank):
     prof = plan.profile_read()
     plan.profile(False)
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     cells = prob.num_cells
-    value = world * cells * steps / (total_ms * 1e-3)
+    value = job_value(cells, steps, total_ms, world)
     srt = sorted(step_ms)
     p50 = srt[len(srt) // 2]
     p99 = srt[min(len(srt) - 1, int(0.99 * len(srt)))]
@@ -347,6 +365,9 @@ def run_ours(args, rank, world, local_rank):
     batch = None
     if not args.no_batch:
         batch = run_batch(args, dev, stream, flush, world)
+    box3d = None
+    if not args.no_3d:
+        box3d = run_3d(args, dev, stream, flush, world, rank)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -369,6 +390,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(prof["kernel_launches"] * steps / calls),
         "clocks": clocks, "cpu_baseline": cpu, "wall_s": round(wall, 3),
         "batch_2d_512": batch,
+        "box_sphere_3d": box3d,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -393,16 +415,75 @@ def run_e2e(plan, prob, stream, dev, steps, world):
         plan.project(hu, out=ho)          # H2D of u*, kernels, D2H of p, u, f inside the call
         ee[k][1].record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = sum(a.elapsed_time(b) for a, b in ee) / ne
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": world * prob.num_cells / (e2e_ms * 1e-3), "unit": UNIT,
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ee) / ne, world, dev)
+    e2e = {"value": job_value(prob.num_cells, 1, e2e_ms, world), "unit": UNIT,
            "h2d_bytes_per_step": int(hu.numel() * hu.element_size()),
            "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in ho)),
            "ms_per_step": round(e2e_ms, 5)}
     return e2e
+
+
+def run_3d(args, dev, stream, flush, world, rank):
+    """The 3D box with a sphere, 256x128x128 cells, ~4.3e6 nodes, K = 27, FP32 u*: mixed
+    precision (autotuned schedule) against the plain FP64 path, both timed per projection."""
+    import torch
+    from paper_2304_14690_gb300 import pc, workloads as wl
+    t0 = time.perf_counter()
+    prob = wl.box_sphere()
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    plan = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, device=dev.index)
+    tune_ms = plan.autotune()
+    setup_s = time.perf_counter() - t0
+    u = torch.as_tensor(prob.u_star, device=dev)
+    outs = plan.alloc_outputs()
+
+    def timed(pl, out, k):
+        for _ in range(3):
+            pl.project(u, out=out)
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for i in range(k):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            pl.project(u, out=out)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        t = sorted(a.elapsed_time(b) for a, b in ev)
+        return sum(t) / k, t[len(t) // 2], t[min(k - 1, int(0.99 * k))]
+
+    k = args.steps_3d
+    plan.profile(True)
+    ms, p50, p99 = timed(plan, outs, k)
+    ms = max_over_ranks(ms, world, dev)
+    prof = plan.profile_read()
+    plan.profile(False)
+    calls = max(prof["calls"], 1)
+    out = {"workload": "box_sphere 256x128x128 cells, walls on all faces (DCT-II x3, zero mode), sphere D=1, "
+                       "K=27, FP32 u*", "cells": prob.num_cells, "nodes": prob.num_nodes,
+           "steps": k, "ms_per_step": round(ms, 4), "value": round(job_value(prob.num_cells, 1, ms, world), 1),
+           "unit": UNIT, "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4)},
+           "phase_ms": {kk: round(v / calls, 5) for kk, v in prof["phase_ms"].items() if v > 0},
+           "transform_slots": plan.slots(), "tuned_solve_ms": round(tune_ms, 4),
+           "generate_s": round(gen_s, 1), "plan_and_tune_s": round(setup_s, 1)}
+    if rank == 0 and not args.no_extras:
+        ref = pc.Plan(prob, precision="fp64", device=dev.index)
+        ro = ref.alloc_outputs()
+        ms64, _, _ = timed(ref, ro, max(5, k // 2))
+        plan.project(u, out=outs)
+        _, _, _, st = plan.project(u, out=outs, stats=True)
+        torch.cuda.synchronize(dev)
+
+        def rel(a, b):
+            return float(torch.linalg.vector_norm(a.double() - b.double()) / torch.linalg.vector_norm(b.double()))
+
+        out["accuracy"] = {"rel_l2_p_vs_fp64_gpu": rel(outs[0], ro[0]), "rel_l2_u_vs_fp64_gpu": rel(outs[1], ro[1]),
+                           "max_div_after_rel": st["max_div_after"] * min(prob.h) / st["max_abs_u_star"],
+                           "residual_norms": st["residual_norm"]}
+        out["fp64_path"] = {"ms_per_step": round(ms64, 4), "speedup_of_this_path": round(ms64 / ms, 3)}
+        ref.close()
+    plan.close()
+    return out
 
 
 def run_batch(args, dev, stream, flush, world):
@@ -431,10 +512,10 @@ def run_batch(args, dev, stream, flush, world):
         pc.project_batch(plans, bargs)
         evs[i][1].record(stream)
     torch.cuda.synchronize(dev)
-    ms = sum(a.elapsed_time(b) for a, b in evs) / k
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / k, world, dev)
     cells = sum(pr.num_cells for pr in probs)
     out = {"problems": len(probs), "cells": cells, "nodes": sum(pr.num_nodes for pr in probs),
-           "ms_per_batch": round(ms, 4), "value": round(world * cells / (ms * 1e-3), 1), "unit": UNIT,
+           "ms_per_batch": round(ms, 4), "value": round(job_value(cells, 1, ms, world), 1), "unit": UNIT,
            "steps": k, "setup_s": round(setup_s, 1),
            "workload": "512 2D problems, n0,n1 in {64..512}, h=1/64, P-P / P-wall / wall-wall, 0-2 circles"}
     for pl in plans:

@@ -353,7 +353,8 @@ def _random_field(pts, lo, L, n, kmax, rng):
     dim = len(n)
     ks = [np.fft.fftfreq(n[a]) * n[a] for a in range(dim)]
     K = np.sqrt(sum(np.meshgrid(*[k * k for k in ks], indexing="ij")))
-    amp = np.where((K >= 1) & (K <= kmax), K ** (-5.0 / 6.0 - (dim - 1) / 2.0), 0.0)
+    Ks = np.where(K >= 1, K, 1.0)
+    amp = np.where((K >= 1) & (K <= kmax), Ks ** (-5.0 / 6.0 - (dim - 1) / 2.0), 0.0)
     out = []
     for _ in range(dim):
         noise = rng.normal(size=tuple(n)) + 1j * rng.normal(size=tuple(n))
