@@ -42,6 +42,16 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--no-3d", action="store_true", help="skip the 256x128x128 box-with-sphere measurement")
     ap.add_argument("--steps-3d", type=int, default=20)
+    ap.add_argument("--serve", action="store_true",
+                    help="serving measurement: Poisson-arrival request stream with continuous batching")
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-pool", type=int, default=64)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-cold", action="store_true",
+                    help="start with no resident plans (default: build every pool plan before the trace)")
+    ap.add_argument("--serve-fp64-requests", type=int, default=2000,
+                    help="prefix of the trace also served one at a time by plain FP64 projections")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the accuracy, plain-FP64 and end-to-end measurements that follow the "
                          "timed region (shorter profiler launch lists); the timed step is unchanged")
@@ -546,6 +556,54 @@ def run_reference(args, rank):
     print(json.dumps(out), flush=True)
 
 
+def run_serve(args, rank):
+    """Config 5: a seeded Poisson-arrival stream of projection requests over a pool of 2D and 3D
+    geometries, served with continuous batching under an HBM budget (mixed precision), and a
+    prefix of the same trace served one request at a time by plain FP64 projections."""
+    import torch
+    from paper_2304_14690_gb300 import serving, workloads as wl
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    pool = wl.serving_pool(count=args.serve_pool)
+    gen_s = time.perf_counter() - t0
+    trace = wl.serving_trace(count=args.serve_requests, rate=args.serve_rate, pool_size=len(pool))
+    budget = int(args.serve_budget_gb * (1 << 30))
+
+    def serve(tr, **kw):
+        srv = serving.Server(pool, budget_bytes=budget, **kw)
+        t = time.perf_counter()
+        warm = srv.warm(range(len(pool))) if not args.serve_cold else 0
+        warm_s = time.perf_counter() - t
+        builds0 = srv.cache.builds
+        reqs = srv.run(tr)
+        out = serving.summarize(reqs, pool)
+        out.update(batches=srv.batches, mean_batch=round(len(reqs) / max(srv.batches, 1), 2),
+                   plan_builds=srv.cache.builds - builds0, evictions=srv.cache.evictions,
+                   warm_plans=warm, warm_s=round(warm_s, 1), host_launch_s=round(srv.host_s, 3),
+                   gpu_batch_s=round(srv.gpu_s, 3))
+        srv.close()
+        torch.cuda.synchronize()
+        return out
+
+    main = serve(trace, precision=args.precision, refine=args.refine)
+    k = min(args.serve_fp64_requests, len(trace))
+    prefix_mixed = serve(trace[:k], precision=args.precision, refine=args.refine)
+    prefix_fp64 = serve(trace[:k], precision="fp64", batched=False, max_inflight=1)
+    n2 = sum(1 for p in pool if p.dim == 2)
+    out = {"metric": "served grid-points/s and p50/p99 latency (continuous batching)",
+           "value": round(main["value"], 1), "unit": UNIT, "n_gpus": 1, "mode": "serve",
+           "higher_is_better": True, "dtype": "f32" if args.precision != "fp64" else "f64",
+           "data": "synthetic",
+           "config": {"workload": f"Poisson arrivals {args.serve_rate:g}/s, {len(trace)} requests, pool of "
+                                  f"{len(pool)} geometries ({n2} 2D n^2, n in 128..1024; {len(pool) - n2} 3D n^3, "
+                                  f"n in 64..192), one obstacle each", "budget_gb": args.serve_budget_gb,
+                      "precision": args.precision, "refine_iters": args.refine, "pool_generate_s": round(gen_s, 1)},
+           "served": main, "prefix": {"requests": k, "mixed_batched": prefix_mixed,
+                                      "fp64_one_at_a_time": prefix_fp64}}
+    print(json.dumps(out), flush=True)
+
+
 def _blas_threads():
     for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
         if os.environ.get(k):
@@ -570,6 +628,11 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.serve:
+        import __graft_entry__
+        __graft_entry__.build()
+        run_serve(args, rank)
         return
     if world > 1:
         import torch

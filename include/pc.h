@@ -55,7 +55,9 @@ typedef enum {
 
 typedef enum {
   PC_PREC_FP64 = 0,   /* every step in FP64 */
-  PC_PREC_MIXED = 1,  /* compensated FP32 gathers, FP32 transforms, FP64 residual refinement */
+  PC_PREC_MIXED = 1,  /* compensated FP32 gathers, FP32 transforms, refinement with a residual
+                         in double-float arithmetic (~48 significant bits) against the FP64
+                         iterate */
   PC_PREC_FP32 = 2    /* as MIXED with no refinement (reports the unrefined FP32 error) */
 } pc_precision;
 
@@ -89,7 +91,7 @@ typedef struct {
   double support_factor;    /* support radius / local spacing (paper: 3, §2.2) */
   double beta;              /* AB2 pressure factor 3/2 of Eq. 4 */
   int precision;            /* pc_precision */
-  int refine_iters;         /* MIXED: number of FP64-residual refinement sweeps (fixed, >= 0) */
+  int refine_iters;         /* MIXED: number of refinement sweeps (fixed, >= 0; 2 reaches 1e-10) */
   int gauge;                /* 0: mean(p) = 0; 1: p at the corner cell = 0 (§3.1). Applies only
                                when no face is Dirichlet (the solution is then defined up to
                                a constant) */
@@ -110,8 +112,9 @@ typedef struct {
 typedef struct pc_plan pc_plan;
 
 /* Build a plan: neighbour search (§2.2 linked-list search), the WLS rows C^-1 A (§2.2
- * Eqs. 13-17, f-unknown basis of Eq. 16) for every flux-carrying face (value row) and every
- * node (derivative rows over the K nearest cell centres), eigenvalue and twiddle tables, and
+ * Eqs. 13-17, f-unknown basis of Eq. 16) for every flux-carrying face (value row over the K
+ * nearest nodes) and every node (derivative rows over the 3^dim block of cell centres around
+ * it, shifted inward at walls, wrapped on periodic axes), eigenvalue and twiddle tables, and
  * the whole workspace of pc_project. The coefficients depend only on positions and are
  * computed once (§2.2, last paragraph). Runs on `device` on `cuda_stream` and returns when
  * done. hbm_budget_bytes = 0 means no budget. */
@@ -151,6 +154,22 @@ typedef struct {
 pc_status pc_project_batch(int count, pc_plan *const *plans, const pc_project_args *args,
                            void *cuda_stream);
 
+/* Batch executor for batches that change from call to call (continuous batching in a request
+ * loop): the same grouping and one-launch-per-stage kernels as pc_project_batch, with the same
+ * bitwise results, but nothing is captured, cached or allocated per call. The executor owns
+ * `slots` table slots of `table_bytes` each (0 = 16 MiB), each a pinned host buffer with a
+ * device copy: a launch fills the next slot on the host, copies it with one asynchronous
+ * transfer on `cuda_stream` and launches the stage kernels behind it; it waits on the host only
+ * when the slot it reuses still belongs to a batch that has not finished. A plan must not be in
+ * two batches that may run at the same time (they share the plan's workspace). Errors:
+ * PC_ERR_BUDGET when a batch's tables exceed table_bytes; as pc_project_batch otherwise.
+ * Launches on one executor are serialised by a lock; destroy waits for its pending batches. */
+typedef struct pc_batcher pc_batcher;
+pc_status pc_batcher_create(int device, size_t table_bytes, int slots, pc_batcher **out);
+pc_status pc_batcher_launch(pc_batcher *batcher, int count, pc_plan *const *plans,
+                            const pc_project_args *args, void *cuda_stream);
+pc_status pc_batcher_destroy(pc_batcher *batcher);
+
 /* The grid-level Poisson solve alone (§2.3 three-step algorithm): L_h p = s, cells in FP64,
  * with the plan's precision, refinement and gauge. */
 pc_status pc_solve_poisson(pc_plan *plan, const double *s, double *p_out, pc_stats *stats,
@@ -181,7 +200,9 @@ pc_status pc_solve_poisson_static(int dim, const int64_t *n, const double *h, co
  * normal to that axis (rows = faces in C order of that face array); which = dim: derivative
  * rows of the nodes (rows = nodes, weights [dim][rows][K]). col_out: [rows][K] int32 (node
  * index for faces, cell linear index for nodes), w_out: FP64 host buffers. rows_out gets the
- * row count; pass NULL buffers to query it. */
+ * row count; pass NULL buffers to query it. FP64 plans return the FP64 weights; MIXED and FP32
+ * plans keep only the FP32 (hi, lo) pairs after setup (the FP64 weights are setup temporaries)
+ * and return hi + lo, within 2^-46 of the FP64 weight. */
 pc_status pc_plan_rows(const pc_plan *plan, int which, int64_t *rows_out, int32_t *col_out,
                        double *w_out);
 
@@ -228,6 +249,16 @@ pc_status pc_plan_autotune(pc_plan *plan, void *cuda_stream, double *best_ms_out
 
 /* Device bytes held by the plan. */
 pc_status pc_plan_bytes(const pc_plan *plan, size_t *bytes_out);
+
+/* A second workspace for a plan: the clone shares the plan's WLS rows, node types and transform
+ * tables (read-only) and owns its own workspace (face fluxes, cell arrays, node copies,
+ * statistics, CUDA graphs), so the plan and its clones can run projections at the same time
+ * (on different streams, or in one batch) with identical results. Cloning a clone clones its
+ * root. A clone costs the workspace only (about 60 bytes per cell plus 8 * dim bytes per node in
+ * mixed precision, against the rows' 12 K bytes per face and (4 + 8 dim) 3^dim per node). The
+ * transform schedule is copied at cloning time. The root must outlive its clones: pc_destroy of
+ * a plan with live clones fails with PC_ERR_INVALID_ARG. */
+pc_status pc_plan_clone(pc_plan *plan, void *cuda_stream, pc_plan **out_plan);
 
 pc_status pc_destroy(pc_plan *plan);
 

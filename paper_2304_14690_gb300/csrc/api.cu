@@ -42,6 +42,25 @@ pc_status plan_alloc(Plan *p, void **ptr, size_t bytes) {
   return PC_OK;
 }
 
+// Frees one plan allocation before the plan's end (setup temporaries).
+pc_status plan_node_staging(Plan *p) {
+  const size_t vb = (size_t)p->dim * p->N * (p->vdtype == PC_DTYPE_F64 ? 8 : 4);
+  if (plan_alloc(p, &p->stage_u, vb) != PC_OK || plan_alloc(p, &p->stage_f, vb) != PC_OK ||
+      plan_alloc(p, &p->stage_uo, vb) != PC_OK || plan_alloc(p, &p->stage_fo, vb) != PC_OK)
+    return PC_ERR_OUT_OF_MEMORY;
+  return PC_OK;
+}
+
+static void plan_free(Plan *p, void *ptr, size_t bytes) {
+  for (int i = 0; i < p->nallocs; ++i)
+    if (p->allocs[i] == ptr) {
+      cudaFree(ptr);
+      p->allocs[i] = p->allocs[--p->nallocs];
+      p->bytes -= bytes;
+      return;
+    }
+}
+
 bool axis_length_supported(int n);
 pc_status prepare_kernels();
 
@@ -142,6 +161,38 @@ static size_t partial_slots(const Plan *p) {
   return (size_t)(2 * (cells_launch > flat_launch ? cells_launch : flat_launch) + 64);
 }
 
+// Per-call workspace of a plan (one projection at a time per workspace): face fluxes, cell
+// arrays, node copies, statistics and reduction scratch, and the capture stream and events of
+// its CUDA graphs.
+static pc_status alloc_workspace(Plan *p, cudaStream_t st) {
+  const bool mixed = p->precision != PC_PREC_FP64;
+  const long long N = p->N, nc = p->ncells;
+  const int dd = p->dim;
+  for (int a = 0; a < dd; ++a)
+    if (plan_alloc(p, (void **)&p->U64[a], p->nface_total[a] * 8) != PC_OK) return PC_ERR_OUT_OF_MEMORY;
+  if (plan_alloc(p, (void **)&p->s64, nc * 8) != PC_OK || plan_alloc(p, (void **)&p->work64, nc * 8) != PC_OK ||
+      plan_alloc(p, (void **)&p->work32, nc * 4) != PC_OK ||
+      plan_alloc(p, (void **)&p->dstats, sizeof(DevStats)) != PC_OK ||
+      plan_alloc(p, (void **)&p->partials, partial_slots(p) * sizeof(double)) != PC_OK ||
+      plan_alloc(p, (void **)&p->counters, 16 * sizeof(unsigned int)) != PC_OK ||
+      plan_alloc(p, (void **)&p->stage_p, nc * 8) != PC_OK || plan_alloc(p, (void **)&p->stage_s, nc * 8) != PC_OK)
+    return PC_ERR_OUT_OF_MEMORY;
+  if (mixed) {
+    if (plan_alloc(p, (void **)&p->p2, nc * 8) != PC_OK || plan_alloc(p, (void **)&p->u2, dd * N * 8) != PC_OK)
+      return PC_ERR_OUT_OF_MEMORY;
+  } else {
+    if (plan_alloc(p, (void **)&p->ut64, dd * N * 8) != PC_OK) return PC_ERR_OUT_OF_MEMORY;
+  }
+  if (cudaMemsetAsync(p->counters, 0, 16 * sizeof(unsigned int), st) != cudaSuccess)
+    return fail(PC_ERR_CUDA, "counter reset failed");
+  if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(PC_ERR_CUDA, "stream creation failed");
+  for (int e = 0; e < kProfEvents; ++e)
+    if (cudaEventCreate(&p->cap_ev[e]) != cudaSuccess) return fail(PC_ERR_CUDA, "event creation failed");
+  p->cap_ev_made = true;
+  return PC_OK;
+}
+
 static pc_status create(const pc_problem_desc *d, int device, size_t budget, cudaStream_t st, Plan **out) {
   if (!d || !out) return fail(PC_ERR_INVALID_ARG, "desc and out_plan are required");
   *out = nullptr;
@@ -226,40 +277,32 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
   const long long N = p->N, K = p->K, nc = ncells;
   const int dd = p->dim;
   size_t need = 0;
-  for (int a = 0; a < dd; ++a) need += (size_t)p->nface_total[a] * (K * (4 + 8 + (mixed ? 8 : 0)) + 8);
+  // weights: FP64 in FP64 plans, FP32 (hi, lo) pairs in mixed and FP32 plans (8 bytes either way)
+  for (int a = 0; a < dd; ++a) need += (size_t)p->nface_total[a] * (K * (4 + 8) + 8);
   const long long Kg = p->Kg;
-  need += (size_t)N * Kg * (4 + dd * (8 + (mixed ? 8 : 0))) + N;
+  need += (size_t)N * Kg * (4 + dd * 8) + N;
   need += (size_t)nc * (8 + 8 + 4 + (mixed ? 8 : 0) + 8 + 8);
-  need += (size_t)dd * N * (mixed ? 8 : 8);
-  const size_t vsz = p->vdtype == PC_DTYPE_F64 ? 8 : 4;
-  need += (size_t)dd * N * vsz * 4 + (size_t)dd * N * 8;   // staging + node copy
+  need += (size_t)dd * N * 8;
+  need += (size_t)dd * N * 8;                             // node coordinates (setup only)
   if (budget && need > budget)
     return bail(fail(PC_ERR_BUDGET, "plan needs %zu bytes, budget is %zu", need, budget));
 
+  // read-only rows (shared with clones)
   for (int a = 0; a < dd; ++a) {
     long long rows = p->nface_total[a];
     if (plan_alloc(p, (void **)&p->fcol[a], rows * K * 4) != PC_OK ||
-        plan_alloc(p, (void **)&p->fw64[a], rows * K * 8) != PC_OK)
+        (!mixed && plan_alloc(p, (void **)&p->fw64[a], rows * K * 8) != PC_OK))
       return bail(PC_ERR_OUT_OF_MEMORY);
     if (mixed && plan_alloc(p, (void **)&p->fw2[a], rows * K * 8) != PC_OK) return bail(PC_ERR_OUT_OF_MEMORY);
-    if (plan_alloc(p, (void **)&p->U64[a], rows * 8) != PC_OK) return bail(PC_ERR_OUT_OF_MEMORY);
   }
-  if (plan_alloc(p, (void **)&p->ncol, N * Kg * 4) != PC_OK || plan_alloc(p, (void **)&p->nD64, dd * N * Kg * 8) != PC_OK ||
-      plan_alloc(p, (void **)&p->ntype, N) != PC_OK || plan_alloc(p, (void **)&p->s64, nc * 8) != PC_OK ||
-      plan_alloc(p, (void **)&p->work64, nc * 8) != PC_OK || plan_alloc(p, (void **)&p->work32, nc * 4) != PC_OK ||
-      plan_alloc(p, (void **)&p->dstats, sizeof(DevStats)) != PC_OK ||
-      plan_alloc(p, (void **)&p->partials, partial_slots(p) * sizeof(double)) != PC_OK ||
-      plan_alloc(p, (void **)&p->counters, 16 * sizeof(unsigned int)) != PC_OK ||
-      plan_alloc(p, (void **)&p->stage_p, nc * 8) != PC_OK || plan_alloc(p, (void **)&p->stage_s, nc * 8) != PC_OK ||
-      plan_alloc(p, &p->stage_u, dd * N * vsz) != PC_OK || plan_alloc(p, &p->stage_f, dd * N * vsz) != PC_OK ||
-      plan_alloc(p, &p->stage_uo, dd * N * vsz) != PC_OK || plan_alloc(p, &p->stage_fo, dd * N * vsz) != PC_OK)
+  if (plan_alloc(p, (void **)&p->ncol, N * Kg * 4) != PC_OK ||
+      (!mixed && plan_alloc(p, (void **)&p->nD64, dd * N * Kg * 8) != PC_OK) ||
+      (mixed && plan_alloc(p, (void **)&p->nD2, dd * N * Kg * 8) != PC_OK) ||
+      plan_alloc(p, (void **)&p->ntype, N) != PC_OK)
     return bail(PC_ERR_OUT_OF_MEMORY);
-  if (mixed) {
-    if (plan_alloc(p, (void **)&p->nD2, dd * N * Kg * 8) != PC_OK || plan_alloc(p, (void **)&p->p2, nc * 8) != PC_OK ||
-        plan_alloc(p, (void **)&p->u2, dd * N * 8) != PC_OK)
-      return bail(PC_ERR_OUT_OF_MEMORY);
-  } else {
-    if (plan_alloc(p, (void **)&p->ut64, dd * N * 8) != PC_OK) return bail(PC_ERR_OUT_OF_MEMORY);
+  {
+    pc_status ws = alloc_workspace(p, st);
+    if (ws != PC_OK) return bail(ws);
   }
   // node coordinates and types on the device
   double *xyz_dev = nullptr;
@@ -283,18 +326,13 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
     if (hb & 1u) return bail(fail(PC_ERR_INVALID_ARG, "a node lies outside the domain or is not finite"));
     if (hb & 2u) return bail(fail(PC_ERR_INVALID_ARG, "node_type values must be 0, 1 or 2"));
   }
-  if (cudaMemsetAsync(p->counters, 0, 16 * sizeof(unsigned int), st) != cudaSuccess)
-    return bail(fail(PC_ERR_CUDA, "counter reset failed"));
-  if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
-    return bail(fail(PC_ERR_CUDA, "stream creation failed"));
-  for (int e = 0; e < kProfEvents; ++e)
-    if (cudaEventCreate(&p->cap_ev[e]) != cudaSuccess) return bail(fail(PC_ERR_CUDA, "event creation failed"));
-  p->cap_ev_made = true;
   if (prepare_kernels() != PC_OK) return bail(PC_ERR_CUDA);
   pc_status s = build_axis_tables(p);
   if (s != PC_OK) return bail(s);
   s = build_rows(p, xyz_dev, st);
   if (s != PC_OK) return bail(s);
+  cudaStreamSynchronize(st);
+  plan_free(p, xyz_dev, (size_t)dd * N * 8);
   *out = p;
   return PC_OK;
 }
@@ -310,7 +348,51 @@ extern "C" pc_status pc_plan_create(const pc_problem_desc *desc, int device, siz
 }
 
 extern "C" pc_status pc_destroy(pc_plan *plan) {
-  pc::destroy_plan(reinterpret_cast<pc::Plan *>(plan));
+  pc::Plan *p = reinterpret_cast<pc::Plan *>(plan);
+  if (!p) return PC_OK;
+  if (p->clones > 0) return pc::fail(PC_ERR_INVALID_ARG, "the plan has %d live clones: destroy them first", p->clones);
+  if (p->root) p->root->clones--;
+  pc::destroy_plan(p);
+  return PC_OK;
+}
+
+extern "C" pc_status pc_plan_clone(pc_plan *plan, void *cuda_stream, pc_plan **out_plan) {
+  using namespace pc;
+  Plan *src = reinterpret_cast<Plan *>(plan);
+  if (!src || !out_plan) return fail(PC_ERR_INVALID_ARG, "plan and out_plan are required");
+  *out_plan = nullptr;
+  Plan *root = src->root ? src->root : src;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cudaSetDevice(root->device) != cudaSuccess) return fail(PC_ERR_CUDA, "cannot select device %d", root->device);
+  Plan *p = new Plan();
+  p->device = root->device;
+  p->dim = root->dim;
+  for (int a = 0; a < 3; ++a) {
+    p->n[a] = root->n[a]; p->lo[a] = root->lo[a]; p->h[a] = root->h[a];
+    p->bc_lo[a] = root->bc_lo[a]; p->bc_hi[a] = root->bc_hi[a];
+    p->ax[a] = root->ax[a];                       // tables borrowed; schedule copied
+    p->nface_total[a] = root->nface_total[a];
+    p->fcol[a] = root->fcol[a]; p->fw64[a] = root->fw64[a]; p->fw2[a] = root->fw2[a];
+  }
+  p->N = root->N; p->K = root->K; p->Kg = root->Kg;
+  p->eps = root->eps; p->support_factor = root->support_factor; p->beta = root->beta;
+  p->precision = root->precision; p->refine_iters = root->refine_iters; p->gauge = root->gauge;
+  p->vdtype = root->vdtype; p->singular = root->singular; p->ncells = root->ncells;
+  p->ncol = root->ncol; p->nD64 = root->nD64; p->nD2 = root->nD2; p->ntype = root->ntype;
+  p->graphs_on = root->graphs_on;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  pc_status s = alloc_workspace(p, st);
+  if (s == PC_OK && cudaStreamSynchronize(st) != cudaSuccess) s = fail(PC_ERR_CUDA, "clone setup failed");
+  if (s != PC_OK) {
+    destroy_plan(p);
+    if (cur >= 0) cudaSetDevice(cur);
+    return s;
+  }
+  p->root = root;
+  root->clones++;
+  if (cur >= 0) cudaSetDevice(cur);
+  *out_plan = reinterpret_cast<pc_plan *>(p);
   return PC_OK;
 }
 
@@ -384,7 +466,15 @@ extern "C" pc_status pc_plan_rows(const pc_plan *plan, int which, int64_t *rows_
   const int32_t *dc = which < p->dim ? p->fcol[which] : p->ncol;
   const double *dw = which < p->dim ? p->fw64[which] : p->nD64;
   PC_CUDA_TRY(cudaMemcpy(c.data(), dc, c.size() * 4, cudaMemcpyDeviceToHost));
-  PC_CUDA_TRY(cudaMemcpy(w.data(), dw, w.size() * 8, cudaMemcpyDeviceToHost));
+  if (dw) {
+    PC_CUDA_TRY(cudaMemcpy(w.data(), dw, w.size() * 8, cudaMemcpyDeviceToHost));
+  } else {
+    // MIXED / FP32 plans keep the weights as FP32 (hi, lo) pairs only
+    const float2 *d2 = which < p->dim ? p->fw2[which] : p->nD2;
+    std::vector<float2> w2(w.size());
+    PC_CUDA_TRY(cudaMemcpy(w2.data(), d2, w2.size() * sizeof(float2), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < w.size(); ++i) w[i] = (double)w2[i].x + (double)w2[i].y;
+  }
   const long long nw = which < p->dim ? 1 : p->dim;
   for (long long r = 0; r < rows; ++r)
     for (long long k = 0; k < K; ++k) {

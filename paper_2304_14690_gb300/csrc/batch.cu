@@ -44,7 +44,16 @@ struct Group {
   bool any_singular = false;
 };
 
+// Table space of one batch in a pinned host buffer and its device copy (the batch executor):
+// tables are appended at 256-byte boundaries and copied with one asynchronous transfer.
+struct Arena {
+  char *host = nullptr;
+  char *dev = nullptr;
+  size_t cap = 0, used = 0;
+};
+
 struct Exec {
+  Arena *arena = nullptr;               // set: tables go to the arena, no allocation
   std::vector<Plan *> plans;
   std::vector<pc_project_args> args;
   std::vector<Group> groups;
@@ -83,6 +92,16 @@ bool same_args(const pc_project_args &a, const pc_project_args &b) {
 template <typename T>
 pc_status upload(Exec *e, T **dptr, const std::vector<T> &host) {
   size_t bytes = std::max<size_t>(host.size() * sizeof(T), 16);
+  if (e->arena) {
+    Arena &a = *e->arena;
+    const size_t off = (a.used + 255) & ~(size_t)255;
+    if (off + bytes > a.cap)
+      return fail(PC_ERR_BUDGET, "batch tables need more than the executor's %zu bytes per batch", a.cap);
+    if (!host.empty()) memcpy(a.host + off, host.data(), host.size() * sizeof(T));
+    *dptr = reinterpret_cast<T *>(a.dev + off);
+    a.used = off + bytes;
+    return PC_OK;
+  }
   if (cudaMalloc(reinterpret_cast<void **>(dptr), bytes) != cudaSuccess) {
     cudaGetLastError();
     return fail(PC_ERR_OUT_OF_MEMORY, "batch table allocation of %zu bytes failed", bytes);
@@ -170,7 +189,8 @@ pc_status record_group(Exec *e, const Group &g, cudaStream_t st) {
   return PC_OK;
 }
 
-pc_status build_exec(Exec *e) {
+// Groups of the batch and their device tables (no capture).
+pc_status build_groups(Exec *e) {
   const int count = (int)e->plans.size();
   for (int i = 0; i < count; ++i) {
     Plan *p = e->plans[i];
@@ -188,6 +208,11 @@ pc_status build_exec(Exec *e) {
     g->members.push_back(i);
   }
   for (Group &g : e->groups) PC_TRY(build_group(e, g));
+  return PC_OK;
+}
+
+pc_status build_exec(Exec *e) {
+  PC_TRY(build_groups(e));
   PC_CUDA_TRY(cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking));
   if (!e->groups.empty()) {
     PC_CUDA_TRY(cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal));
@@ -223,12 +248,13 @@ void batch_forget_plan(const Plan *p) {
 
 }  // namespace pc
 
-extern "C" pc_status pc_project_batch(int count, pc_plan *const *plans, const pc_project_args *args,
-                                      void *cuda_stream) {
-  using namespace pc;
+namespace pc {
+namespace {
+
+// Checks shared by pc_project_batch and pc_batcher_launch; returns the batch's device.
+pc_status validate_batch(int count, pc_plan *const *plans, const pc_project_args *args, int &device) {
   if (count < 0 || (count > 0 && (!plans || !args))) return fail(PC_ERR_INVALID_ARG, "bad batch arguments");
-  if (count == 0) return PC_OK;
-  int device = -1;
+  device = -1;
   for (int i = 0; i < count; ++i) {
     const Plan *p = reinterpret_cast<const Plan *>(plans[i]);
     if (!p) return fail(PC_ERR_INVALID_ARG, "plan %d is NULL", i);
@@ -245,10 +271,47 @@ extern "C" pc_status pc_project_batch(int count, pc_plan *const *plans, const pc
       if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess ||
           !(at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
         cudaGetLastError();
-        return fail(PC_ERR_INVALID_ARG, "batch entry %d: pc_project_batch takes device pointers only", i);
+        return fail(PC_ERR_INVALID_ARG, "batch entry %d: batched projections take device pointers only", i);
       }
     }
   }
+  return PC_OK;
+}
+
+pc_status run_singles(const Exec &e, pc_plan *const *plans, const pc_project_args *args, void *stream) {
+  for (int i : e.singles) {
+    pc_status s = pc_project(plans[i], args[i].dt, args[i].u_star, args[i].f_ib_in, args[i].p_out, args[i].u_out,
+                             args[i].f_ib_out, nullptr, stream);
+    if (s != PC_OK) return s;
+  }
+  return PC_OK;
+}
+
+// One table slot of the batch executor: pinned host staging, its device copy, and the event
+// recorded after the last batch that used it.
+struct Slot {
+  Arena arena;
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+};
+
+}  // namespace
+
+struct Batcher {
+  int device = 0;
+  std::vector<Slot> slots;
+  size_t next = 0;
+  std::mutex m;
+};
+
+}  // namespace pc
+
+extern "C" pc_status pc_project_batch(int count, pc_plan *const *plans, const pc_project_args *args,
+                                      void *cuda_stream) {
+  using namespace pc;
+  int device = -1;
+  PC_TRY(validate_batch(count, plans, args, device));
+  if (count == 0) return PC_OK;
   if (cudaSetDevice(device) != cudaSuccess) return fail(PC_ERR_CUDA, "cannot select device %d", device);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   Exec *e = nullptr;
@@ -284,10 +347,87 @@ extern "C" pc_status pc_project_batch(int count, pc_plan *const *plans, const pc
     e->stamp = ++g_clock;
   }
   if (e->exec) PC_CUDA_TRY(cudaGraphLaunch(e->exec, st));
-  for (int i : e->singles) {
-    pc_status s = pc_project(plans[i], args[i].dt, args[i].u_star, args[i].f_ib_in, args[i].p_out, args[i].u_out,
-                             args[i].f_ib_out, nullptr, cuda_stream);
-    if (s != PC_OK) return s;
+  return run_singles(*e, plans, args, cuda_stream);
+}
+
+extern "C" pc_status pc_batcher_create(int device, size_t table_bytes, int slots, pc_batcher **out) {
+  using namespace pc;
+  if (!out || slots < 1 || slots > 64) return fail(PC_ERR_INVALID_ARG, "out is required and slots must be in [1, 64]");
+  *out = nullptr;
+  if (table_bytes == 0) table_bytes = (size_t)16 << 20;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cudaSetDevice(device) != cudaSuccess) return fail(PC_ERR_CUDA, "cannot select device %d", device);
+  Batcher *b = new Batcher();
+  b->device = device;
+  b->slots.resize(slots);
+  pc_status s = PC_OK;
+  for (Slot &sl : b->slots) {
+    sl.arena.cap = table_bytes;
+    if (cudaMallocHost(reinterpret_cast<void **>(&sl.arena.host), table_bytes) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void **>(&sl.arena.dev), table_bytes) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      s = fail(PC_ERR_OUT_OF_MEMORY, "batch executor: %d slots of %zu bytes", slots, table_bytes);
+      break;
+    }
   }
+  if (cur >= 0) cudaSetDevice(cur);
+  if (s != PC_OK) {
+    pc_batcher_destroy(reinterpret_cast<pc_batcher *>(b));
+    return s;
+  }
+  *out = reinterpret_cast<pc_batcher *>(b);
+  return PC_OK;
+}
+
+extern "C" pc_status pc_batcher_launch(pc_batcher *batcher, int count, pc_plan *const *plans,
+                                       const pc_project_args *args, void *cuda_stream) {
+  using namespace pc;
+  Batcher *b = reinterpret_cast<Batcher *>(batcher);
+  if (!b) return fail(PC_ERR_INVALID_ARG, "batcher is NULL");
+  int device = -1;
+  PC_TRY(validate_batch(count, plans, args, device));
+  if (count == 0) return PC_OK;
+  if (device != b->device) return fail(PC_ERR_INVALID_ARG, "plans are on device %d, the executor on %d", device, b->device);
+  std::lock_guard<std::mutex> lock(b->m);
+  if (cudaSetDevice(device) != cudaSuccess) return fail(PC_ERR_CUDA, "cannot select device %d", device);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Slot &sl = b->slots[b->next % b->slots.size()];
+  b->next++;
+  if (sl.pending) PC_CUDA_TRY(cudaEventSynchronize(sl.done));   // its previous batch still reads it
+  sl.pending = false;
+  Exec e;
+  e.arena = &sl.arena;
+  e.arena->used = 0;
+  e.device = device;
+  for (int i = 0; i < count; ++i) {
+    e.plans.push_back(reinterpret_cast<Plan *>(plans[i]));
+    e.args.push_back(args[i]);
+  }
+  PC_TRY(build_groups(&e));
+  if (e.arena->used > 0)
+    PC_CUDA_TRY(cudaMemcpyAsync(sl.arena.dev, sl.arena.host, e.arena->used, cudaMemcpyHostToDevice, st));
+  for (const Group &g : e.groups) PC_TRY(record_group(&e, g, st));
+  PC_CUDA_TRY(cudaEventRecord(sl.done, st));
+  sl.pending = true;
+  return run_singles(e, plans, args, cuda_stream);
+}
+
+extern "C" pc_status pc_batcher_destroy(pc_batcher *batcher) {
+  using namespace pc;
+  Batcher *b = reinterpret_cast<Batcher *>(batcher);
+  if (!b) return PC_OK;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  cudaSetDevice(b->device);
+  for (Slot &sl : b->slots) {
+    if (sl.pending) cudaEventSynchronize(sl.done);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.arena.dev) cudaFree(sl.arena.dev);
+    if (sl.arena.host) cudaFreeHost(sl.arena.host);
+  }
+  if (cur >= 0) cudaSetDevice(cur);
+  delete b;
   return PC_OK;
 }

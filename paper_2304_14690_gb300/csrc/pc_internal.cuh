@@ -129,6 +129,10 @@ struct Plan {
   size_t bytes = 0;
   void *allocs[64];
   int nallocs = 0;
+  // Clones (pc_plan_clone): a clone borrows the rows, node types and axis tables of its root
+  // and owns its workspace; a root with live clones is not destroyed.
+  struct Plan *root = nullptr;
+  int clones = 0;
   // CUDA graphs of pc_project (on by default for device pointers without statistics)
   bool graphs_on = true;
   cudaStream_t cap_stream = nullptr;
@@ -172,6 +176,9 @@ pc_status fail(pc_status st, const char *fmt, ...);
   } while (0)
 
 pc_status plan_alloc(Plan *p, void **ptr, size_t bytes);
+// Staging buffers of the node arrays for calls with host pointers, allocated on the first such
+// call (device-pointer callers never pay for them).
+pc_status plan_node_staging(Plan *p);
 
 // ----------------------------------------------------------------------------- launches
 inline int grid_for(int64_t work, int threads) {

@@ -973,6 +973,7 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   const void *du = u_star, *df = f_in;
   double *dp = p_out;
   void *duo = u_out, *dfo = f_out;
+  if ((hu || (f_in && hf) || huo || (f_out && hfo)) && !p->stage_u) PC_TRY(plan_node_staging(p));
   if (hu) { PC_CUDA_TRY(cudaMemcpyAsync(p->stage_u, u_star, vbytes, cudaMemcpyHostToDevice, st)); du = p->stage_u; }
   if (f_in && hf) { PC_CUDA_TRY(cudaMemcpyAsync(p->stage_f, f_in, vbytes, cudaMemcpyHostToDevice, st)); df = p->stage_f; }
   if (hp) dp = p->stage_p;

@@ -238,8 +238,9 @@ __device__ __forceinline__ void record_failure(unsigned int *flags, unsigned int
   atomicMin(reinterpret_cast<unsigned long long *>(flags + 2), key);
 }
 
+// FP64 weight (FP64 plans) and/or its FP32 (hi, lo) pair (mixed and FP32 plans).
 __device__ __forceinline__ void split_store(double v, double *w64, float2 *w2, long long at) {
-  w64[at] = v;
+  if (w64) w64[at] = v;
   if (w2) {
     float hi = (float)v;
     w2[at] = make_float2(hi, (float)(v - (double)hi));

@@ -20,6 +20,10 @@ STATUS = ["ok", "invalid argument", "unsupported", "singular WLS system", "out o
           "device-memory budget exceeded", "CUDA error", "refinement not converged", "timeout"]
 
 
+PC_OK, PC_ERR_INVALID_ARG, PC_ERR_UNSUPPORTED, PC_ERR_WLS_SINGULAR = 0, 1, 2, 3
+PC_ERR_OUT_OF_MEMORY, PC_ERR_BUDGET, PC_ERR_CUDA = 4, 5, 6
+
+
 class PcError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"libpc status {status} ({STATUS[status] if status < len(STATUS) else '?'}): {message}")
@@ -100,6 +104,7 @@ FUNCTIONS = {
                                     ctypes.c_void_p, ctypes.c_void_p]),
     "pc_plan_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "pc_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "pc_plan_clone": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "pc_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "pc_set_graphs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "pc_solve_poisson_static": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
@@ -111,6 +116,10 @@ FUNCTIONS = {
     "pc_plan_get_transform_slots": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                    ctypes.POINTER(ctypes.c_int)]),
     "pc_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "pc_batcher_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "pc_batcher_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.POINTER(ProjectArgs), ctypes.c_void_p]),
+    "pc_batcher_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "pc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pc_last_error_message": (ctypes.c_char_p, []),
 }
@@ -217,7 +226,7 @@ class Plan:
 
     def close(self):
         if getattr(self, "handle", None):
-            load().pc_destroy(self.handle)
+            _check(load().pc_destroy(self.handle))
             self.handle = None
 
     def __del__(self):
@@ -225,6 +234,17 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def clone(self, stream=None):
+        """pc_plan_clone: another workspace on the same rows and tables (the clone keeps its
+        root alive)."""
+        h = ctypes.c_void_p()
+        _check(load().pc_plan_clone(self.handle, _stream_handle(stream), ctypes.byref(h)))
+        c = Plan.__new__(Plan)
+        c.__dict__.update({k: v for k, v in self.__dict__.items() if k != "handle"})
+        c._root = getattr(self, "_root", None) or self
+        c.handle = h
+        return c
 
     def nbytes(self):
         b = ctypes.c_size_t()
@@ -329,9 +349,7 @@ def solve_poisson_static(dim, n, h, bc_lo, bc_hi, s, p_out, gauge=0, stream=None
     return p_out
 
 
-def project_batch(plans, args, stream=None):
-    """pc_project_batch over (plan, dict(dt, u_star, f_ib, p, u, f)) pairs (device tensors)."""
-    lib = load()
+def _batch_arrays(plans, args):
     n = len(plans)
     hs = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
     arr = (ProjectArgs * n)()
@@ -342,4 +360,35 @@ def project_batch(plans, args, stream=None):
         arr[i].p_out = _ptr(a["p"])
         arr[i].u_out = _ptr(a["u"])
         arr[i].f_ib_out = _ptr(a.get("f"))
-    _check(lib.pc_project_batch(n, hs, arr, _stream_handle(stream)))
+    return n, hs, arr
+
+
+def project_batch(plans, args, stream=None):
+    """pc_project_batch over (plan, dict(dt, u_star, f_ib, p, u, f)) pairs (device tensors)."""
+    n, hs, arr = _batch_arrays(plans, args)
+    _check(load().pc_project_batch(n, hs, arr, _stream_handle(stream)))
+
+
+class Batcher:
+    """pc_batcher: launches batches that change from call to call, without capture or
+    allocation per call (see include/pc.h)."""
+
+    def __init__(self, device=0, table_bytes=0, slots=4):
+        h = ctypes.c_void_p()
+        _check(load().pc_batcher_create(device, table_bytes, slots, ctypes.byref(h)))
+        self.handle = h
+
+    def launch(self, plans, args, stream=None):
+        n, hs, arr = _batch_arrays(plans, args)
+        _check(load().pc_batcher_launch(self.handle, n, hs, arr, _stream_handle(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pc_batcher_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -418,3 +418,43 @@ def batch_2d(count=512, seed=14693, sizes=BATCH_SIZES):
         p.name = f"batch_{i}"
         probs.append(p)
     return probs
+
+
+SERVE_SIZES_2D = (128, 192, 256, 384, 512, 768, 1024)
+SERVE_SIZES_3D = (64, 96, 128, 192)
+
+
+def serving_pool(count=64, seed=14695, frac_2d=0.7, sizes_2d=SERVE_SIZES_2D, sizes_3d=SERVE_SIZES_3D):
+    """Geometries of the request stream: 2D n x n (h = 1/n, inflow/outflow along x, walls
+    along y, one cylinder) or 3D n^3 (h = 1/n, walls, one sphere) with n drawn uniformly from
+    the size lists; obstacle diameter 10-30% of the box, centre inside it; nodes on a jittered
+    lattice at h; u* vortices plus a gradient perturbation."""
+    rng = np.random.default_rng(seed)
+    pool = []
+    for i in range(count):
+        two = rng.uniform() < frac_2d
+        dim = 2 if two else 3
+        n = int(rng.choice(sizes_2d if two else sizes_3d))
+        h = 1.0 / n
+        D = rng.uniform(0.1, 0.3)
+        c = tuple(float(rng.uniform(0.5 * D + 4 * h, 1.0 - 0.5 * D - 4 * h)) for _ in range(dim))
+        obs = [("circle" if two else "sphere", c, 0.5 * D)]
+        if two:
+            bl, bh = ("I", "W"), ("D", "W")
+        else:
+            bl, bh = ("W", "W", "W"), ("W", "W", "W")
+        p = generic(dim=dim, n=(n,) * dim, h=(h,) * dim, bc_lo=bl, bc_hi=bh, obstacles=obs,
+                    seed=int(rng.integers(0, 2**31)))
+        p.name = f"serve_{i}_{dim}d_{n}"
+        pool.append(p)
+    return pool
+
+
+def serving_trace(count=20000, rate=2000.0, pool_size=64, seed=14696):
+    """Poisson arrivals: (arrival seconds, geometry index, u* scale) per request, exponential
+    gaps of mean 1/rate, geometry uniform over the pool, scale uniform in [0.5, 1.5]."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    g = rng.integers(0, pool_size, size=count)
+    s = rng.uniform(0.5, 1.5, size=count)
+    return [(float(t[i]), int(g[i]), float(s[i])) for i in range(count)]
