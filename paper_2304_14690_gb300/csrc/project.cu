@@ -339,7 +339,8 @@ __device__ __forceinline__ DF df_mul(DF a, DF b) {
 }
 
 // ----------------------------------------------------------------------------- divergence
-// s = D_h U / (beta dt) (FP64), its FP32 copy, and optionally sum(s), sum(s^2).
+// s = D_h U / (beta dt) (FP64), its FP32 copy; want_sums 1: sum(s) and the mean, 2: also
+// sum(s^2) (statistics).
 template <int DIM>
 __device__ __forceinline__ void divergence_body(unsigned b, const GridDev &g, const double *U0, const double *U1,
                                                 const double *U2, double inv_bdt, double *s, float *s32,
@@ -368,16 +369,14 @@ __device__ __forceinline__ void divergence_body(unsigned b, const GridDev &g, co
       const int ci = cell_index(g, i);
       s[ci] = v;
       if (s32) s32[ci] = d2f_rz_bits(v);   // FP32 copy read by the first FP32 transform pass
-      if (want_sums) {
-        sum += v;
-        sum2 = fma(v, v, sum2);
-      }
+      if (want_sums) sum += v;
+      if (want_sums > 1) sum2 = fma(v, v, sum2);
     }
   }
   if (want_sums) {
     const VBlock vb = tile_block(g, b);
     if (grid_sum(sum, partials, counter, &stats->sum_s, vb)) stats->mean_s = stats->sum_s * inv_ncells;
-    grid_sum(sum2, partials + g.nblk, counter + 1, &stats->sum_s2, vb);
+    if (want_sums > 1) grid_sum(sum2, partials + g.nblk, counter + 1, &stats->sum_s2, vb);
   }
 }
 
@@ -842,8 +841,9 @@ static GridDev grid_dev(const Plan *p) {
     }
     for (int b = p->dim; b < 3; ++b) g.fs[ax][b] = 0;
   }
-  // cell tiles: 2^tw_bits positions of the last axis (32..256) x 2^th_bits thread rows, cr rows
-  // per thread; cr shrinks while the grid would not give two blocks per SM
+  // cell tiles: 2^tw_bits positions of the last axis (32..256) x 2^th_bits thread rows, cr = 4
+  // rows per thread. The tiling depends on the grid only (not on how full the GPU is), so a
+  // problem has the same blocks, and the same reduction order, alone and in a batch.
   const int nl = g.n[p->dim - 1];
   g.rows = (int)(p->ncells / nl);
   g.tw_bits = 5;
@@ -855,7 +855,6 @@ static GridDev grid_dev(const Plan *p) {
     return (long long)g.gx * ((g.rows + rpb - 1) / rpb);
   };
   g.cr = 4;
-  while (g.cr > 1 && nblk_for(g.cr) < 2 * 152) g.cr >>= 1;
   g.nblk = (int)nblk_for(g.cr);
   return g;
 }
@@ -1017,7 +1016,7 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
     auto divk = (d == 2) ? divergence_kernel<2> : divergence_kernel<3>;
     launch_pdl(divk, g.nblk, 256, 0, st, g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt), p->s64,
                mixed ? reinterpret_cast<float *>(p->work64) : nullptr, p->dstats, p->partials, p->counters,
-               (p->singular || stats) ? 1 : 0, 1.0 / (double)nc);
+               stats ? 2 : (p->singular ? 1 : 0), 1.0 / (double)nc);
   }
   count_launch(p);
   prof_mark(p, st, 2);
