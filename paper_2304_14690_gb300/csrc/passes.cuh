@@ -39,6 +39,7 @@ struct PassArgs {
   int dst_mode;
   void *dst;
   Real out_scale;       // normalisation of the inverse (2/n)
+  float2 *split;        // nullable: the FP32 (hi, lo) split of every FP64 value stored
 };
 
 // One pass of a solve: axis, phases, source and destination.
@@ -49,11 +50,13 @@ struct PassSpec {
   const void *src;
   int dst_mode;
   void *dst;
+  float2 *split;        // nullable: also store the (hi, lo) split of the FP64 result
 };
 
-// The passes of one solve of plan p from src to dst, in launch order.
+// The passes of one solve of plan p from src to dst, in launch order; split (nullable) goes to
+// the final pass.
 std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, const void *src,
-                                       int dst_mode, void *dst);
+                                       int dst_mode, void *dst, float2 *split = nullptr);
 // Fill the kernel arguments and launch shape of one pass (no launch). batch_threads > 0 sizes
 // the tile to fill a CTA of that many threads (batched launches); 0 sizes it so that the
 // problem alone fills the GPU.

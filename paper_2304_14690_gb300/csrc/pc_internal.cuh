@@ -192,7 +192,7 @@ inline int grid_for(int64_t work, int threads) {
 // destination modes are those of passes.cuh (FP32 or FP64 source; FP64 set or accumulate).
 pc_status solve_fp64_grid(Plan *p, const double *s, double *pout, cudaStream_t st);
 pc_status solve_fp32_grid(Plan *p, int src_mode, const void *s, int dst_mode, double *pout,
-                          cudaStream_t st);
+                          cudaStream_t st, float2 *split = nullptr);
 // Drops the plan's captured CUDA graphs and batch executables (after a schedule change).
 void plan_drop_graphs(Plan *p);
 // ----------------------------------------------------------------------------- batches
@@ -221,7 +221,7 @@ struct GridDev {
 // Per-problem parameters of a batched launch (device array, one entry per problem).
 struct BatchProblem {
   GridDev g;
-  int dim, N, ncells, K, Kg, singular, gmode;
+  int dim, vdtype, N, ncells, K, Kg, singular, gmode;
   const void *u, *f;
   void *uo, *fo;
   double *p;

@@ -180,9 +180,17 @@ __device__ __forceinline__ void axis_pass_body(const PassArgs<Real> &A, const in
       const int i = g.lane + (c0 + b) * g.tpl;
       if (i >= n) continue;
       const int gi = base + i * stride;
-      if (A.dst_mode == DST_WORK) static_cast<Real *>(A.dst)[gi] = x[b];
-      else if (A.dst_mode == DST_F64_SET) static_cast<double *>(A.dst)[gi] = to_f64(x[b]);
-      else static_cast<double *>(A.dst)[gi] = old[b] + to_f64(x[b]);
+      if (A.dst_mode == DST_WORK) {
+        static_cast<Real *>(A.dst)[gi] = x[b];
+      } else {
+        const double v = (A.dst_mode == DST_F64_SET) ? to_f64(x[b]) : old[b] + to_f64(x[b]);
+        static_cast<double *>(A.dst)[gi] = v;
+        if (A.split) {
+          float hi, lo;
+          split_f64(v, hi, lo);
+          A.split[gi] = make_float2(hi, lo);
+        }
+      }
     }
   }
 }
@@ -372,6 +380,7 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   A.dst_mode = dst_mode;
   A.dst = dst;
   A.out_scale = (Real)inv_scale(ax.kind, ax.n);
+  A.split = ps.split;
   threads = L * tpl;
   if (threads > kMaxPassThreads || L * M > budget)
     return fail(PC_ERR_UNSUPPORTED, "axis %d: tile of %d x %d too large", axis, L, M);
@@ -439,22 +448,22 @@ pc_status prepare_kernels() {
 }
 
 std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, const void *src,
-                                       int dst_mode, void *dst) {
+                                       int dst_mode, void *dst, float2 *split) {
   std::vector<PassSpec> v;
   void *work = fp32 ? (void *)p->work32 : (void *)p->work64;
   const int d = p->dim;
   int cur_mode = src_mode;
   const void *cur = src;
   for (int a = d - 1; a >= 1; --a) {     // forward passes: last axis down to axis 1
-    v.push_back(PassSpec{a, true, false, false, cur_mode, cur, DST_WORK, work});
+    v.push_back(PassSpec{a, true, false, false, cur_mode, cur, DST_WORK, work, nullptr});
     cur_mode = SRC_WORK;
     cur = work;
   }
-  v.push_back(PassSpec{0, true, true, true, cur_mode, cur, DST_WORK, work});   // axis 0 with the division
+  v.push_back(PassSpec{0, true, true, true, cur_mode, cur, DST_WORK, work, nullptr});   // axis 0, division
   for (int a = 1; a < d; ++a) {         // inverse passes: axis 1 up to the last axis
     const bool final_pass = (a == d - 1);
     v.push_back(PassSpec{a, false, false, true, SRC_WORK, work, final_pass ? dst_mode : DST_WORK,
-                         final_pass ? dst : work});
+                         final_pass ? dst : work, final_pass ? split : nullptr});
   }
   return v;
 }
@@ -462,9 +471,9 @@ std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, c
 // Full solve with Real precision: src (cells, src_mode) -> dst (dst_mode).
 template <typename Real>
 static pc_status solve_real(Plan *p, int src_mode, const void *src, int dst_mode, void *dst,
-                            cudaStream_t st) {
+                            cudaStream_t st, float2 *split = nullptr) {
   if (p->dim < 2) return fail(PC_ERR_UNSUPPORTED, "dim 1");
-  for (const PassSpec &ps : solve_pass_specs(p, sizeof(Real) == 4, src_mode, src, dst_mode, dst))
+  for (const PassSpec &ps : solve_pass_specs(p, sizeof(Real) == 4, src_mode, src, dst_mode, dst, split))
     PC_TRY(launch_pass<Real>(p, ps, st));
   return PC_OK;
 }
@@ -474,8 +483,8 @@ pc_status solve_fp64_grid(Plan *p, const double *s, double *pout, cudaStream_t s
 }
 
 pc_status solve_fp32_grid(Plan *p, int src_mode, const void *s, int dst_mode, double *pout,
-                          cudaStream_t st) {
-  return solve_real<float>(p, src_mode, s, dst_mode, pout, st);
+                          cudaStream_t st, float2 *split) {
+  return solve_real<float>(p, src_mode, s, dst_mode, pout, st, split);
 }
 
 }  // namespace pc

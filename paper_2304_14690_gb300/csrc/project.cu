@@ -239,9 +239,15 @@ __device__ __forceinline__ double df_value(DF s) { return f2d_bits(s.hi) + f2d_b
 
 // KC > 0: the neighbour count is a compile-time constant and the loop is unrolled, so all
 // index and weight loads are in flight before the dependent gathers (memory-level parallelism).
-template <int KC>
+// The gathered node value as an FP32 (hi, lo) pair, here the pairs of u~ that prep wrote.
+struct PairSrc {
+  const float2 *p;
+  __device__ __forceinline__ float2 operator()(int c) const { return __ldg(p + c); }
+};
+
+template <int KC, typename Src>
 __device__ __forceinline__ void transfer_mixed_kernel_body(const VBlock &vb, int rows, int Kr, const int32_t *__restrict__ col,
-                                      const float2 *__restrict__ w2, const float2 *__restrict__ u2,
+                                      const float2 *__restrict__ w2, Src src,
                                       double *__restrict__ U) {
   int r = vb.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
@@ -256,22 +262,21 @@ __device__ __forceinline__ void transfer_mixed_kernel_body(const VBlock &vb, int
       w[k] = __ldg(w2 + k * rows + r);
     }
 #pragma unroll
-    for (int k = 0; k < K; ++k) df_acc(s, w[k], __ldg(u2 + c[k]));
+    for (int k = 0; k < K; ++k) df_acc(s, w[k], src(c[k]));
   } else {
 #pragma unroll 4
     for (int k = 0; k < K; ++k) {
       int at = k * rows + r;
-      df_acc(s, __ldg(w2 + at), __ldg(u2 + __ldg(col + at)));
+      df_acc(s, __ldg(w2 + at), src(__ldg(col + at)));
     }
   }
   U[r] = df_value(s);
 }
-template <int KC>
+template <int KC, typename Src>
 __global__ void transfer_mixed_kernel(int rows, int Kr, const int32_t *__restrict__ col,
-                                      const float2 *__restrict__ w2, const float2 *__restrict__ u2,
-                                      double *__restrict__ U) {
+                                      const float2 *__restrict__ w2, Src src, double *__restrict__ U) {
   pdl_enter();
-  transfer_mixed_kernel_body<KC>(hw_block(), rows, Kr, col, w2, u2, U);
+  transfer_mixed_kernel_body<KC>(hw_block(), rows, Kr, col, w2, src, U);
 }
 
 // ----------------------------------------------------------------------------- grid geometry
@@ -688,7 +693,8 @@ __global__ void batch_transfer(const BatchProblem *__restrict__ P, const int *__
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
   const VBlock vb = flat_block(blockIdx.x - seg[pi], seg[pi + 1] - seg[pi]);
-  transfer_mixed_kernel_body<KC>(vb, q.frows[a], q.K, q.fcol[a], q.fw2[a], q.u2 + (long long)a * q.N, q.U64[a]);
+  transfer_mixed_kernel_body<KC>(vb, q.frows[a], q.K, q.fcol[a], q.fw2[a], PairSrc{q.u2 + (long long)a * q.N},
+                                 q.U64[a]);
 }
 
 __global__ void batch_divergence(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
@@ -731,7 +737,6 @@ __global__ void batch_finalize(const BatchProblem *__restrict__ P, const int *__
   const BatchProblem &q = P[pi];
   const unsigned lb = blockIdx.x - seg[pi];
   if (q.gmode) finalize_p_body<true, true>(lb, q.ncells, q.p, q.ds, q.p2);
-  else finalize_p_body<false, true>(lb, q.ncells, q.p, q.ds, q.p2);
 }
 
 template <typename VT, int DIM>
@@ -783,14 +788,14 @@ void batch_block_counts(const Plan *p, int *nb) {
   nb[BATCH_DIVERGENCE] = g.nblk;
   nb[BATCH_RESIDUAL] = g.nblk;
   nb[BATCH_GAUGE_SUM] = p->singular ? grid_for(nc, kFlatPerBlock) : 0;
-  nb[BATCH_FINALIZE] = grid_for(nc, kFlatPerBlock);
+  nb[BATCH_FINALIZE] = p->singular ? grid_for(nc, kFlatPerBlock) : 0;   // else split by the last pass
   nb[BATCH_GRADIENT] = grid_for(N, 256);
 }
 
 void batch_problem_fill(const Plan *p, const pc_project_args &a, BatchProblem &q) {
   memset(&q, 0, sizeof(q));
   q.g = grid_dev(p);
-  q.dim = p->dim; q.N = (int)p->N; q.ncells = (int)p->ncells; q.K = p->K; q.Kg = p->Kg;
+  q.dim = p->dim; q.vdtype = p->vdtype; q.N = (int)p->N; q.ncells = (int)p->ncells; q.K = p->K; q.Kg = p->Kg;
   q.singular = p->singular;
   q.gmode = p->singular ? (p->gauge == 1 ? 2 : 1) : 0;
   q.u = a.u_star; q.f = a.f_ib_in; q.uo = a.u_out; q.fo = a.f_ib_out; q.p = a.p_out;
@@ -900,9 +905,12 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
     PC_TRY(solve_fp64_grid(p, s64, pout, st));
     prof_mark(p, st, 3);
   } else {
+    // the final pass of the last solve stores the (hi, lo) split of p for the gradient itself
+    // when no gauge shift follows
     int sweeps = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
-    if (s32) PC_TRY(solve_fp32_grid(p, SRC_F32_, s32, DST_F64_SET_, pout, st));
-    else PC_TRY(solve_fp32_grid(p, SRC_F64_, s64, DST_F64_SET_, pout, st));
+    float2 *split_last = p->singular ? nullptr : p->p2;
+    if (s32) PC_TRY(solve_fp32_grid(p, SRC_F32_, s32, DST_F64_SET_, pout, st, sweeps ? nullptr : split_last));
+    else PC_TRY(solve_fp32_grid(p, SRC_F64_, s64, DST_F64_SET_, pout, st, sweeps ? nullptr : split_last));
     prof_mark(p, st, 3);
     for (int it = 0; it < sweeps; ++it) {
       float *r32 = reinterpret_cast<float *>(p->work64);   // work64 is free in mixed mode
@@ -910,7 +918,7 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
                       &p->dstats->res2[it], p->partials, p->counters);
       count_launch(p);
       prof_mark(p, st, 4);
-      PC_TRY(solve_fp32_grid(p, SRC_F32_, r32, DST_F64_ADD_, pout, st));
+      PC_TRY(solve_fp32_grid(p, SRC_F32_, r32, DST_F64_ADD_, pout, st, it == sweeps - 1 ? split_last : nullptr));
       prof_mark(p, st, 3);
     }
   }
@@ -928,11 +936,10 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
     count_launch(p);
   }
   bool mixed = p->precision != PC_PREC_FP64;
-  if (gmode || mixed) {
+  if (gmode) {
     const int G = grid_for(nc, kFlatPerBlock);
     if (gmode && mixed) launch_pdl(finalize_p_kernel<true, true>, G, T, 0, st, (int)nc, pout, p->dstats, p->p2);
-    else if (gmode) launch_pdl(finalize_p_kernel<true, false>, G, T, 0, st, (int)nc, pout, p->dstats, nullptr);
-    else launch_pdl(finalize_p_kernel<false, true>, G, T, 0, st, (int)nc, pout, p->dstats, p->p2);
+    else launch_pdl(finalize_p_kernel<true, false>, G, T, 0, st, (int)nc, pout, p->dstats, nullptr);
     count_launch(p);
   }
   prof_mark(p, st, 5);
@@ -993,21 +1000,17 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   count_launch(p);
   prof_mark(p, st, 0);
   for (int a = 0; a < d; ++a) {
-    long long rows = p->nface_total[a];
+    const long long rows = p->nface_total[a];
+    const int G = grid_for(rows, T);
     if (mixed) {
-      if (p->K == 12)
-        launch_pdl(transfer_mixed_kernel<12>, grid_for(rows, T), T, 0, st, (int)rows, p->K, p->fcol[a], p->fw2[a],
-                                                                   p->u2 + (long long)a * N, p->U64[a]);
-      else if (p->K == 27)
-        launch_pdl(transfer_mixed_kernel<27>, grid_for(rows, T), T, 0, st, (int)rows, p->K, p->fcol[a], p->fw2[a],
-                                                                   p->u2 + (long long)a * N, p->U64[a]);
-      else
-        launch_pdl(transfer_mixed_kernel<0>, grid_for(rows, T), T, 0, st, (int)rows, p->K, p->fcol[a], p->fw2[a],
-                                                                  p->u2 + (long long)a * N, p->U64[a]);
+      const PairSrc src{p->u2 + (long long)a * N};
+      if (p->K == 12) launch_pdl(transfer_mixed_kernel<12, PairSrc>, G, T, 0, st, (int)rows, p->K, p->fcol[a], p->fw2[a], src, p->U64[a]);
+      else if (p->K == 27) launch_pdl(transfer_mixed_kernel<27, PairSrc>, G, T, 0, st, (int)rows, p->K, p->fcol[a], p->fw2[a], src, p->U64[a]);
+      else launch_pdl(transfer_mixed_kernel<0, PairSrc>, G, T, 0, st, (int)rows, p->K, p->fcol[a], p->fw2[a], src, p->U64[a]);
+    } else {
+      launch_pdl(transfer64_kernel, G, T, 0, st, (int)rows, p->K, p->fcol[a], p->fw64[a],
+                 p->ut64 + (long long)a * N, p->U64[a]);
     }
-    else
-      launch_pdl(transfer64_kernel, grid_for(rows, T), T, 0, st, (int)rows, p->K, p->fcol[a], p->fw64[a],
-                                                         p->ut64 + (long long)a * N, p->U64[a]);
     count_launch(p);
   }
   prof_mark(p, st, 1);
