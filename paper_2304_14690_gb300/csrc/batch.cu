@@ -137,10 +137,10 @@ pc_status build_group(Exec *e, Group &g) {
     for (int i = 0; i < n; ++i) {
       Plan *p = e->plans[g.members[i]];
       const void *src = reinterpret_cast<const float *>(p->work64);
-      // the last solve of a problem without a gauge shift stores the split of p (as single calls do)
-      float2 *split = (j == g.sweeps && !p->singular) ? p->p2 : nullptr;
-      specs[i] = solve_pass_specs(p, true, SRC_F32, src, j == 0 ? DST_F64_SET : DST_F64_ADD,
-                                  e->args[g.members[i]].p_out, split);
+      // the iterate is kept in p2 as (hi, lo) pairs; the last solve also writes p in FP64 (as
+      // single calls do)
+      double *f64 = (j == g.sweeps) ? e->args[g.members[i]].p_out : nullptr;
+      specs[i] = solve_pass_specs(p, true, SRC_F32, src, j == 0 ? DST_PAIR_SET : DST_PAIR_ADD, p->p2, f64);
     }
     const size_t npass = specs[0].size();
     for (size_t k = 0; k < npass; ++k) {

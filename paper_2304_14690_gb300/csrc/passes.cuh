@@ -12,7 +12,9 @@ enum SrcMode { SRC_F32 = 0, SRC_F64 = 1, SRC_WORK = 2 };
 
 constexpr int kMaxPassThreads = 512;   // CTA size limit of the transform passes
 constexpr int kBatchPassEmax = 16;     // largest slots per thread of a batched pass kernel
-enum DstMode { DST_WORK = 0, DST_F64_SET = 1, DST_F64_ADD = 2 };
+// DST_PAIR_*: the refinement iterate of the FP32 solves, kept as FP32 (hi, lo) pairs
+// (double-float): SET stores the pass result, ADD adds it to the stored pair.
+enum DstMode { DST_WORK = 0, DST_F64_SET = 1, DST_F64_ADD = 2, DST_PAIR_SET = 3, DST_PAIR_ADD = 4 };
 
 template <typename Real>
 struct PassArgs {
@@ -39,7 +41,7 @@ struct PassArgs {
   int dst_mode;
   void *dst;
   Real out_scale;       // normalisation of the inverse (2/n)
-  float2 *split;        // nullable: the FP32 (hi, lo) split of every FP64 value stored
+  double *f64;          // nullable (pair modes): also store the pair's value in FP64
 };
 
 // One pass of a solve: axis, phases, source and destination.
@@ -50,13 +52,13 @@ struct PassSpec {
   const void *src;
   int dst_mode;
   void *dst;
-  float2 *split;        // nullable: also store the (hi, lo) split of the FP64 result
+  double *f64;          // nullable (pair modes): also store the result in FP64
 };
 
-// The passes of one solve of plan p from src to dst, in launch order; split (nullable) goes to
+// The passes of one solve of plan p from src to dst, in launch order; f64 (nullable) goes to
 // the final pass.
 std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, const void *src,
-                                       int dst_mode, void *dst, float2 *split = nullptr);
+                                       int dst_mode, void *dst, double *f64 = nullptr);
 // Fill the kernel arguments and launch shape of one pass (no launch). batch_threads > 0 sizes
 // the tile to fill a CTA of that many threads (batched launches); 0 sizes it so that the
 // problem alone fills the GPU.

@@ -191,8 +191,8 @@ inline int grid_for(int64_t work, int threads) {
 // Transform solves of a grid (poisson.cu): FP64 s -> p, and one FP32 solve whose source and
 // destination modes are those of passes.cuh (FP32 or FP64 source; FP64 set or accumulate).
 pc_status solve_fp64_grid(Plan *p, const double *s, double *pout, cudaStream_t st);
-pc_status solve_fp32_grid(Plan *p, int src_mode, const void *s, int dst_mode, double *pout,
-                          cudaStream_t st, float2 *split = nullptr);
+pc_status solve_fp32_grid(Plan *p, int src_mode, const void *s, int dst_mode, void *dst,
+                          cudaStream_t st, double *f64 = nullptr);
 // Drops the plan's captured CUDA graphs and batch executables (after a schedule change).
 void plan_drop_graphs(Plan *p);
 // ----------------------------------------------------------------------------- batches

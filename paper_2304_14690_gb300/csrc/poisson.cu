@@ -168,12 +168,14 @@ __device__ __forceinline__ void axis_pass_body(const PassArgs<Real> &A, const in
 #pragma unroll
   for (int c0 = 0; c0 < 2 * EMAX; c0 += kChunk) {
     Real x[kChunk];
-    double old[kChunk];
+    // previous value of an accumulating store: an FP64 value or a (hi, lo) pair, 8 bytes either way
+    unsigned long long old[kChunk];
+    const bool acc = A.dst_mode == DST_F64_ADD || A.dst_mode == DST_PAIR_ADD;
 #pragma unroll
     for (int b = 0; b < kChunk; ++b) {
       const int i = g.lane + (c0 + b) * g.tpl;
       x[b] = (i < n) ? inv_out(res, g, A.kind, n, A.tw, i) * scale : (Real)0;
-      old[b] = (A.dst_mode == DST_F64_ADD && i < n) ? static_cast<const double *>(A.dst)[base + i * stride] : 0.0;
+      old[b] = (acc && i < n) ? static_cast<const unsigned long long *>(A.dst)[base + i * stride] : 0ULL;
     }
 #pragma unroll
     for (int b = 0; b < kChunk; ++b) {
@@ -182,14 +184,22 @@ __device__ __forceinline__ void axis_pass_body(const PassArgs<Real> &A, const in
       const int gi = base + i * stride;
       if (A.dst_mode == DST_WORK) {
         static_cast<Real *>(A.dst)[gi] = x[b];
-      } else {
-        const double v = (A.dst_mode == DST_F64_SET) ? to_f64(x[b]) : old[b] + to_f64(x[b]);
-        static_cast<double *>(A.dst)[gi] = v;
-        if (A.split) {
-          float hi, lo;
-          split_f64(v, hi, lo);
-          A.split[gi] = make_float2(hi, lo);
+      } else if (A.dst_mode == DST_PAIR_SET || A.dst_mode == DST_PAIR_ADD) {
+        // FP32 passes only: the pair (hi, lo) += x with Knuth's TwoSum, renormalised
+        float hi = (float)x[b], lo = 0.0f;
+        if (A.dst_mode == DST_PAIR_ADD) {
+          const float a = __uint_as_float((unsigned)old[b]), alo = __uint_as_float((unsigned)(old[b] >> 32));
+          const float bb = hi;
+          const float s1 = __fadd_rn(a, bb), z = __fsub_rn(s1, a);
+          const float e = __fadd_rn(__fadd_rn(__fsub_rn(a, __fsub_rn(s1, z)), __fsub_rn(bb, z)), alo);
+          hi = __fadd_rn(s1, e);
+          lo = __fsub_rn(e, __fsub_rn(hi, s1));
         }
+        static_cast<float2 *>(A.dst)[gi] = make_float2(hi, lo);
+        if (A.f64) A.f64[gi] = f2d_bits(hi) + f2d_bits(lo);
+      } else {
+        static_cast<double *>(A.dst)[gi] =
+            (A.dst_mode == DST_F64_SET) ? to_f64(x[b]) : __longlong_as_double((long long)old[b]) + to_f64(x[b]);
       }
     }
   }
@@ -380,7 +390,7 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   A.dst_mode = dst_mode;
   A.dst = dst;
   A.out_scale = (Real)inv_scale(ax.kind, ax.n);
-  A.split = ps.split;
+  A.f64 = ps.f64;
   threads = L * tpl;
   if (threads > kMaxPassThreads || L * M > budget)
     return fail(PC_ERR_UNSUPPORTED, "axis %d: tile of %d x %d too large", axis, L, M);
@@ -448,7 +458,7 @@ pc_status prepare_kernels() {
 }
 
 std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, const void *src,
-                                       int dst_mode, void *dst, float2 *split) {
+                                       int dst_mode, void *dst, double *f64) {
   std::vector<PassSpec> v;
   void *work = fp32 ? (void *)p->work32 : (void *)p->work64;
   const int d = p->dim;
@@ -463,7 +473,7 @@ std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, c
   for (int a = 1; a < d; ++a) {         // inverse passes: axis 1 up to the last axis
     const bool final_pass = (a == d - 1);
     v.push_back(PassSpec{a, false, false, true, SRC_WORK, work, final_pass ? dst_mode : DST_WORK,
-                         final_pass ? dst : work, final_pass ? split : nullptr});
+                         final_pass ? dst : work, final_pass ? f64 : nullptr});
   }
   return v;
 }
@@ -471,9 +481,9 @@ std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, c
 // Full solve with Real precision: src (cells, src_mode) -> dst (dst_mode).
 template <typename Real>
 static pc_status solve_real(Plan *p, int src_mode, const void *src, int dst_mode, void *dst,
-                            cudaStream_t st, float2 *split = nullptr) {
+                            cudaStream_t st, double *f64 = nullptr) {
   if (p->dim < 2) return fail(PC_ERR_UNSUPPORTED, "dim 1");
-  for (const PassSpec &ps : solve_pass_specs(p, sizeof(Real) == 4, src_mode, src, dst_mode, dst, split))
+  for (const PassSpec &ps : solve_pass_specs(p, sizeof(Real) == 4, src_mode, src, dst_mode, dst, f64))
     PC_TRY(launch_pass<Real>(p, ps, st));
   return PC_OK;
 }
@@ -482,9 +492,9 @@ pc_status solve_fp64_grid(Plan *p, const double *s, double *pout, cudaStream_t s
   return solve_real<double>(p, SRC_F64, s, DST_F64_SET, pout, st);
 }
 
-pc_status solve_fp32_grid(Plan *p, int src_mode, const void *s, int dst_mode, double *pout,
-                          cudaStream_t st, float2 *split) {
-  return solve_real<float>(p, src_mode, s, dst_mode, pout, st, split);
+pc_status solve_fp32_grid(Plan *p, int src_mode, const void *s, int dst_mode, void *dst,
+                          cudaStream_t st, double *f64) {
+  return solve_real<float>(p, src_mode, s, dst_mode, dst, st, f64);
 }
 
 }  // namespace pc

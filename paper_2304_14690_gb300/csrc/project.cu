@@ -23,7 +23,7 @@
 namespace pc {
 
 enum { SRC_F32_ = 0, SRC_F64_ = 1 };
-enum { DST_F64_SET_ = 1, DST_F64_ADD_ = 2 };
+enum { DST_F64_SET_ = 1, DST_F64_ADD_ = 2, DST_PAIR_SET_ = 3, DST_PAIR_ADD_ = 4 };
 
 // ----------------------------------------------------------------------------- block context
 // Kernels address their block through a VBlock: the hardware block in a single-problem launch,
@@ -348,7 +348,7 @@ __device__ __forceinline__ DF df_mul(DF a, DF b) {
 // sum(s^2) (statistics).
 template <int DIM>
 __device__ __forceinline__ void divergence_body(unsigned b, const GridDev &g, const double *U0, const double *U1,
-                                                const double *U2, double inv_bdt, double *s, float *s32,
+                                                const double *U2, double inv_bdt, double *s, float2 *s2, float *s32,
                                                 DevStats *stats, double *partials, unsigned int *counter,
                                                 int want_sums, double inv_ncells) {
   int x, row0;
@@ -372,7 +372,8 @@ __device__ __forceinline__ void divergence_body(unsigned b, const GridDev &g, co
         v = (a == 0) ? d * c[0] : fma(d, c[a], v);
       }
       const int ci = cell_index(g, i);
-      s[ci] = v;
+      if (s2) s2[ci] = as_pair(v);     // the refinement keeps s as a (hi, lo) pair
+      else s[ci] = v;
       if (s32) s32[ci] = d2f_rz_bits(v);   // FP32 copy read by the first FP32 transform pass
       if (want_sums) sum += v;
       if (want_sums > 1) sum2 = fma(v, v, sum2);
@@ -387,10 +388,10 @@ __device__ __forceinline__ void divergence_body(unsigned b, const GridDev &g, co
 
 template <int DIM>
 __global__ void divergence_kernel(GridDev g, const double *U0, const double *U1, const double *U2,
-                                  double inv_bdt, double *s, float *s32, DevStats *stats, double *partials,
-                                  unsigned int *counter, int want_sums, double inv_ncells) {
+                                  double inv_bdt, double *s, float2 *s2, float *s32, DevStats *stats,
+                                  double *partials, unsigned int *counter, int want_sums, double inv_ncells) {
   pdl_enter();
-  divergence_body<DIM>(blockIdx.x, g, U0, U1, U2, inv_bdt, s, s32, stats, partials, counter, want_sums,
+  divergence_body<DIM>(blockIdx.x, g, U0, U1, U2, inv_bdt, s, s2, s32, stats, partials, counter, want_sums,
                        inv_ncells);
 }
 
@@ -433,13 +434,21 @@ __device__ __forceinline__ void neighbours(const GridDev &g, const double *p, co
   else pr = g.hi_kind[a] ? -pc : pc;
 }
 
+// A stored value as a double-float pair: FP64 values are split exactly as split_f64 does,
+// pairs are taken as they are.
+__device__ __forceinline__ DF to_df(double v) { return df_of(v); }
+__device__ __forceinline__ DF to_df(float2 v) { return DF{v.x, v.y}; }
+__device__ __forceinline__ DF df_neg_(DF a) { return DF{-a.hi, -a.lo}; }
+
 // r = s - mean(s) - L_h p, evaluated in double-float arithmetic (about 48 significant bits:
 // the FP64 pipe of this GPU runs at 1/64 of the FP32 rate) and stored as FP32 for the next
 // FP32 solve; optionally ||r||^2. The refinement converges to the solution of this residual,
 // so its ~2^-44 relative rounding bounds the attainable accuracy far below the 1e-10 target.
-template <int DIM, bool SINGULAR, bool WRITE_R, bool NORM>
-__device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, const double *__restrict__ s,
-                                              const double *__restrict__ p, float *__restrict__ r,
+// SV, PV: storage of s and p, double or a float2 (hi, lo) pair (the refinement keeps both as
+// pairs; FP64 arrays come from pc_solve_poisson and from the statistics of FP64 plans).
+template <int DIM, bool SINGULAR, bool WRITE_R, bool NORM, typename SV, typename PV>
+__device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, const SV *__restrict__ s,
+                                              const PV *__restrict__ p, float *__restrict__ r,
                                               const DevStats *stats, double *res2, double *partials,
                                               unsigned int *counter) {
   int x, row0;
@@ -453,17 +462,23 @@ __device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, cons
       int i[3];
       cell_at<DIM>(g, row, x, i);
       const int c = cell_index(g, i);
-      const double pc = p[c];
-      const DF dc = df_of(pc);
+      const DF dc = to_df(p[c]);
       DF acc{0.0f, 0.0f};
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
-        double pl, pr;
-        neighbours(g, p, i, c, a, pc, pl, pr);
-        const DF t = df_add(df_sub(df_of(pl), dc), df_sub(df_of(pr), dc));
+        // neighbours with the ghost rules: Neumann p_ghost = p_edge, Dirichlet -p_edge, periodic wrap
+        const int st = g.cs[a];
+        DF pl, pr;
+        if (i[a] > 0) pl = to_df(p[c - st]);
+        else if (g.periodic[a]) pl = to_df(p[c + (g.n[a] - 1) * st]);
+        else pl = g.lo_kind[a] ? df_neg_(dc) : dc;
+        if (i[a] < g.n[a] - 1) pr = to_df(p[c + st]);
+        else if (g.periodic[a]) pr = to_df(p[c - (g.n[a] - 1) * st]);
+        else pr = g.hi_kind[a] ? df_neg_(dc) : dc;
+        const DF t = df_add(df_sub(pl, dc), df_sub(pr, dc));
         acc = df_add(acc, df_mul(t, DF{g.ih2_hi[a], g.ih2_lo[a]}));
       }
-      DF sc = df_of(s[c]);
+      DF sc = to_df(s[c]);
       if (SINGULAR) sc = df_sub(sc, mean);
       const DF v = df_sub(sc, acc);
       if (WRITE_R) r[c] = v.hi;
@@ -475,12 +490,12 @@ __device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, cons
   }
   if (NORM) grid_sum(nrm, partials, counter, res2, tile_block(g, b));
 }
-template <int DIM, bool SINGULAR, bool WRITE_R, bool NORM>
-__global__ void residual_kernel(GridDev g, const double *__restrict__ s, const double *__restrict__ p,
+template <int DIM, bool SINGULAR, bool WRITE_R, bool NORM, typename SV, typename PV>
+__global__ void residual_kernel(GridDev g, const SV *__restrict__ s, const PV *__restrict__ p,
                                 float *__restrict__ r, const DevStats *stats, double *res2,
                                 double *partials, unsigned int *counter) {
   pdl_enter();
-  residual_body<DIM, SINGULAR, WRITE_R, NORM>(blockIdx.x, g, s, p, r, stats, res2, partials, counter);
+  residual_body<DIM, SINGULAR, WRITE_R, NORM, SV, PV>(blockIdx.x, g, s, p, r, stats, res2, partials, counter);
 }
 
 // ----------------------------------------------------------------------------- gauge
@@ -703,10 +718,12 @@ __global__ void batch_divergence(const BatchProblem *__restrict__ P, const int *
   const BatchProblem &q = P[pi];
   const unsigned lb = blockIdx.x - seg[pi];
   if (q.g.dim == 2)
-    divergence_body<2>(lb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, q.s64, q.s32, q.ds, q.partials, q.counters,
+    divergence_body<2>(lb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, nullptr, reinterpret_cast<float2 *>(q.s64),
+                       q.s32, q.ds, q.partials, q.counters,
                        q.singular, q.inv_ncells);
   else
-    divergence_body<3>(lb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, q.s64, q.s32, q.ds, q.partials, q.counters,
+    divergence_body<3>(lb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, nullptr, reinterpret_cast<float2 *>(q.s64),
+                       q.s32, q.ds, q.partials, q.counters,
                        q.singular, q.inv_ncells);
 }
 
@@ -715,12 +732,13 @@ __global__ void batch_residual(const BatchProblem *__restrict__ P, const int *__
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
   const unsigned lb = blockIdx.x - seg[pi];
+  const float2 *s2 = reinterpret_cast<const float2 *>(q.s64);
   if (q.g.dim == 2) {
-    if (q.singular) residual_body<2, true, true, false>(lb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
-    else residual_body<2, false, true, false>(lb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
+    if (q.singular) residual_body<2, true, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters);
+    else residual_body<2, false, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters);
   } else {
-    if (q.singular) residual_body<3, true, true, false>(lb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
-    else residual_body<3, false, true, false>(lb, q.g, q.s64, q.p, q.r32, q.ds, nullptr, q.partials, q.counters);
+    if (q.singular) residual_body<3, true, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters);
+    else residual_body<3, false, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters);
   }
 }
 
@@ -878,13 +896,16 @@ static bool is_device_ptr(const void *ptr) {
 }
 
 // Grid-level solve: s64 (device) -> p (device, FP64), gauge applied; fills dstats fields.
-static void launch_residual(bool singular, bool write_r, bool norm, cudaStream_t st,
-                            const GridDev &g, const double *s, const double *p, float *r, DevStats *ds,
-                            double *res2, double *partials, unsigned int *counters) {
-#define PC_RES(S, W, N)                                                                      \
-  do {                                                                                       \
-    if (g.dim == 2) launch_pdl(residual_kernel<2, S, W, N>, g.nblk, 256, 0, st, g, s, p, r, ds, res2, partials, counters); \
-    else launch_pdl(residual_kernel<3, S, W, N>, g.nblk, 256, 0, st, g, s, p, r, ds, res2, partials, counters); \
+template <typename SV, typename PV>
+static void launch_residual(bool singular, bool write_r, bool norm, cudaStream_t st, const GridDev &g,
+                            const SV *s, const PV *p, float *r, DevStats *ds, double *res2, double *partials,
+                            unsigned int *counters) {
+#define PC_RES(S, W, N)                                                                                       \
+  do {                                                                                                        \
+    if (g.dim == 2)                                                                                           \
+      launch_pdl(residual_kernel<2, S, W, N, SV, PV>, g.nblk, 256, 0, st, g, s, p, r, ds, res2, partials, counters); \
+    else                                                                                                      \
+      launch_pdl(residual_kernel<3, S, W, N, SV, PV>, g.nblk, 256, 0, st, g, s, p, r, ds, res2, partials, counters); \
   } while (0)
   if (singular) {
     if (write_r) { if (norm) PC_RES(true, true, true); else PC_RES(true, true, false); }
@@ -896,8 +917,11 @@ static void launch_residual(bool singular, bool write_r, bool norm, cudaStream_t
 #undef PC_RES
 }
 
+// s2 (nullable): the source as (hi, lo) pairs (projections); otherwise s64 in FP64
+// (pc_solve_poisson). FP32 solves keep the refinement iterate in p->p2 as (hi, lo) pairs, read
+// by the residual and the gradient; the last solve also writes p in FP64 to pout.
 static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_final_residual,
-                            cudaStream_t st, const float *s32 = nullptr) {
+                            cudaStream_t st, const float *s32 = nullptr, const float2 *s2 = nullptr) {
   const long long nc = p->ncells;
   const int T = kFlatThreads;
   GridDev g = grid_dev(p);
@@ -905,27 +929,35 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
     PC_TRY(solve_fp64_grid(p, s64, pout, st));
     prof_mark(p, st, 3);
   } else {
-    // the final pass of the last solve stores the (hi, lo) split of p for the gradient itself
-    // when no gauge shift follows
     int sweeps = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
-    float2 *split_last = p->singular ? nullptr : p->p2;
-    if (s32) PC_TRY(solve_fp32_grid(p, SRC_F32_, s32, DST_F64_SET_, pout, st, sweeps ? nullptr : split_last));
-    else PC_TRY(solve_fp32_grid(p, SRC_F64_, s64, DST_F64_SET_, pout, st, sweeps ? nullptr : split_last));
+    if (s32) PC_TRY(solve_fp32_grid(p, SRC_F32_, s32, DST_PAIR_SET_, p->p2, st, sweeps ? nullptr : pout));
+    else PC_TRY(solve_fp32_grid(p, SRC_F64_, s64, DST_PAIR_SET_, p->p2, st, sweeps ? nullptr : pout));
     prof_mark(p, st, 3);
     for (int it = 0; it < sweeps; ++it) {
       float *r32 = reinterpret_cast<float *>(p->work64);   // work64 is free in mixed mode
-      launch_residual(p->singular, true, want_final_residual, st, g, s64, pout, r32, p->dstats,
-                      &p->dstats->res2[it], p->partials, p->counters);
+      if (s2)
+        launch_residual(p->singular, true, want_final_residual, st, g, s2, (const float2 *)p->p2, r32, p->dstats,
+                        &p->dstats->res2[it], p->partials, p->counters);
+      else
+        launch_residual(p->singular, true, want_final_residual, st, g, s64, (const float2 *)p->p2, r32, p->dstats,
+                        &p->dstats->res2[it], p->partials, p->counters);
       count_launch(p);
       prof_mark(p, st, 4);
-      PC_TRY(solve_fp32_grid(p, SRC_F32_, r32, DST_F64_ADD_, pout, st, it == sweeps - 1 ? split_last : nullptr));
+      PC_TRY(solve_fp32_grid(p, SRC_F32_, r32, DST_PAIR_ADD_, p->p2, st, it == sweeps - 1 ? pout : nullptr));
       prof_mark(p, st, 3);
     }
   }
   if (want_final_residual) {
     int it = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
-    launch_residual(p->singular, false, true, st, g, s64, pout, nullptr, p->dstats,
-                    &p->dstats->res2[it], p->partials, p->counters);
+    if (p->precision == PC_PREC_FP64)
+      launch_residual(p->singular, false, true, st, g, s64, (const double *)pout, (float *)nullptr, p->dstats,
+                      &p->dstats->res2[it], p->partials, p->counters);
+    else if (s2)
+      launch_residual(p->singular, false, true, st, g, s2, (const float2 *)p->p2, (float *)nullptr, p->dstats,
+                      &p->dstats->res2[it], p->partials, p->counters);
+    else
+      launch_residual(p->singular, false, true, st, g, s64, (const float2 *)p->p2, (float *)nullptr, p->dstats,
+                      &p->dstats->res2[it], p->partials, p->counters);
     count_launch(p);
     prof_mark(p, st, 7);
   }
@@ -1017,7 +1049,8 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   GridDev g = grid_dev(p);
   {
     auto divk = (d == 2) ? divergence_kernel<2> : divergence_kernel<3>;
-    launch_pdl(divk, g.nblk, 256, 0, st, g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt), p->s64,
+    launch_pdl(divk, g.nblk, 256, 0, st, g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt),
+               mixed ? nullptr : p->s64, mixed ? reinterpret_cast<float2 *>(p->s64) : nullptr,
                mixed ? reinterpret_cast<float *>(p->work64) : nullptr, p->dstats, p->partials, p->counters,
                stats ? 2 : (p->singular ? 1 : 0), 1.0 / (double)nc);
   }
@@ -1025,7 +1058,8 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   prof_mark(p, st, 2);
   PC_CUDA_TRY(cudaGetLastError());
   PC_TRY(solve_grid(p, p->s64, dp, stats != nullptr, st,
-                    mixed ? reinterpret_cast<const float *>(p->work64) : nullptr));
+                    mixed ? reinterpret_cast<const float *>(p->work64) : nullptr,
+                    mixed ? reinterpret_cast<const float2 *>(p->s64) : nullptr));
   const void *ug = du;
   if (p->vdtype == PC_DTYPE_F64) {
     if (mixed) {
