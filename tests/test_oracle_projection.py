@@ -181,3 +181,49 @@ def test_ib_relations(problems):
         fl = ~ib
         corr = p.u_star[:, fl] - p.beta * p.dt * r["grad"][:, fl]
         assert np.abs(r["u"][:, fl] - corr).max() == 0.0
+
+
+def test_ib_iteration_reaches_the_affine_fixed_point():
+    """§2.3 IB iteration: one pass maps the force f to F(f) = M f + c (affine: the whole pass is
+    linear in u~ = u* + dt f). Its fixed point, found by a direct dense solve of (I - M) f = c
+    with M built column by column on the boundary/virtual components, is where the iteration
+    ends when run to a tight tolerance; u vanishes at those nodes on every pass."""
+    from paper_2304_14690_gb300 import workloads as wl
+    prob = wl.generic(dim=2, n=(24, 20), bc_lo=("W", "W"), bc_hi=("W", "W"),
+                      obstacles=[("circle", (0.7, 0.6), 0.2)], seed=11)
+    g = G.Grid(prob.dim, prob.n, prob.lo, prob.h, prob.bc_lo, prob.bc_hi)
+    pl = PR.build_plan(g, prob.nodes, prob.node_type, K=12)
+    ib = np.flatnonzero(prob.node_type != PR.FLUID)
+    F = lambda f: PR.project(pl, prob.dt, prob.u_star, f)["f"]
+    f0 = np.zeros_like(prob.u_star)
+    c = F(f0)
+    cols = []
+    for a in range(prob.dim):
+        for k in ib:
+            e = np.zeros_like(f0)
+            e[a, k] = 1.0
+            cols.append((F(e) - c)[:, ib].ravel())
+    M = np.array(cols).T
+    x = np.linalg.solve(np.eye(M.shape[0]) - M, c[:, ib].ravel())
+    fstar = np.zeros_like(f0)
+    fstar[:, ib] = x.reshape(prob.dim, len(ib))
+    out = PR.project_ib(pl, prob.dt, prob.u_star, tol=1e-26, max_iters=400)
+    assert out["iterations"] < 400
+    assert np.linalg.norm(out["f"] - fstar) <= 1e-11 * np.linalg.norm(fstar)
+    assert np.all(out["u"][:, ib] == 0.0)
+    assert np.all(out["f"][:, prob.node_type == PR.FLUID] == 0.0)
+    # the paper's tolerance stops early, after the force change has fallen below it
+    short = PR.project_ib(pl, prob.dt, prob.u_star, tol=1e-3)
+    d, p = short["history"][-1]
+    assert 1 < short["iterations"] < out["iterations"] and d <= 1e-3 * p
+
+
+def test_ib_stopping_rule():
+    assert PR.ib_converged(0.0, 0.0, 1e-3)          # no force and no change: converged
+    assert not PR.ib_converged(1e-30, 0.0, 1e-3)    # first pass from zero force never stops
+    assert PR.ib_converged(1e-4, 1.0, 1e-3) and not PR.ib_converged(2e-3, 1.0, 1e-3)
+    t = np.array([0, 1, 2, 0], dtype=np.uint8)
+    fn = np.array([[0.0, 3.0, 0.0, 0.0], [0.0, 4.0, 1.0, 0.0]])
+    fo = np.array([[0.0, 0.0, 0.0, 0.0], [0.0, 4.0, 0.0, 0.0]])
+    d, p = PR.ib_change(fn, fo, t)
+    assert d == pytest.approx((9.0 + 1.0) / 2) and p == pytest.approx(16.0 / 2)
