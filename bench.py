@@ -371,6 +371,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None if args.no_extras else run_e2e(plan, prob, stream, dev, steps, world)
+    ib = None if args.no_extras else run_ib(plan, prob, u_dev, stream, dev, flush)
 
     batch = None
     if not args.no_batch:
@@ -399,6 +400,7 @@ def run_ours(args, rank, world, local_rank):
         "accuracy": acc, "fp64_path": fp64, "e2e": e2e,
         "gpu_launches": int(prof["kernel_launches"] * steps / calls),
         "clocks": clocks, "cpu_baseline": cpu, "wall_s": round(wall, 3),
+        "ib_iteration": ib,
         "batch_2d_512": batch,
         "box_sphere_3d": box3d,
     }
@@ -431,6 +433,60 @@ def run_e2e(plan, prob, stream, dev, steps, world):
            "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in ho)),
            "ms_per_step": round(e2e_ms, 5)}
     return e2e
+
+
+def run_ib(plan, prob, u_dev, stream, dev, flush, tol=1e-3, max_iters=50, reps=10):
+    """One time step of the IB-force iteration (§2.3) at the paper's tolerance 1e-3, from zero
+    force, through pc_project_ib: as one CUDA graph (while node, device-side stopping rule; the
+    default) and driven from the host (graphs off; per-pass phases from the profiler), against
+    the same number of full pc_project passes fed with the previous force."""
+    import torch
+    outs = plan.alloc_outputs()
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for k in range(reps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            fn()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        return sum(a.elapsed_time(b) for a, b in ev) / reps
+
+    info = {}
+
+    def step():
+        info.update(plan.project_ib(u_dev, tol=tol, max_iters=max_iters, out=outs)[3])
+
+    ms_graph = timed(step)
+    its = info["iterations"]
+    plan.graphs(False)
+    plan.profile(True)
+    ms_host = timed(step)
+    prof = plan.profile_read()
+    plan.profile(False)
+    plan.graphs(True)
+    fb = [plan.alloc_outputs() for _ in range(2)]
+
+    def full():
+        f = None
+        for i in range(its):
+            plan.project(u_dev, f, out=fb[i & 1])
+            f = fb[i & 1][2]
+
+    ms_full = timed(full)
+    passes = max(prof["calls"], 1)
+    return {"tol": tol, "iterations": its, "converged": info["converged"],
+            "ib_nodes": int((prob.node_type != 0).sum()),
+            "ms_per_time_step": round(ms_graph, 4), "ms_per_pass": round(ms_graph / its, 5),
+            "host_loop_ms_per_time_step": round(ms_host, 4),
+            "host_loop_pass_phase_ms": {k: round(v / passes, 5) for k, v in prof["phase_ms"].items() if v > 0},
+            "full_passes_ms": round(ms_full, 4), "speedup_vs_full_passes": round(ms_full / ms_graph, 3),
+            "cells_per_s_per_time_step": round(prob.num_cells / (ms_graph * 1e-3), 1),
+            "history_last": info["history"][-1]}
 
 
 def run_3d(args, dev, stream, flush, world, rank):

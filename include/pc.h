@@ -135,6 +135,40 @@ pc_status pc_project(pc_plan *plan, double dt, const void *u_star, const void *f
                      double *p_out, void *u_out, void *f_ib_out, pc_stats *stats,
                      void *cuda_stream);
 
+/* The IB-force iteration of §2.3: the modified PPE (Eq. 20) and the force update (Eq. 19) are
+ * repeated, each pass with the force of the previous one, until the mean over boundary/virtual
+ * nodes of |f_new - f_old|^2 is <= tol times the mean of |f_old|^2 (a zero previous force stops
+ * only with zero change), or max_iters passes (>= 1). The paper's tolerance is 1e-3.
+ *   f_ib_init  force of the first pass ([dim][N] of velocity_dtype, nullable = zero: the first
+ *              iteration of a time step); only its boundary/virtual entries are used, the force
+ *              lives at those points
+ *   p_out, u_out, f_ib_out   as pc_project, from the last pass (f_ib_out nullable)
+ *   history    nullable HOST buffer of 2*max_iters doubles: (mean |df|^2, mean |f_old|^2) per pass
+ *   result     nullable: passes run, whether the rule was met, and the last pair
+ * Each pass after the first updates u~ only at the boundary/virtual nodes, recomputes only the
+ * fluxes of the faces whose WLS value row reaches one of them, solves, and evaluates the gradient
+ * at those nodes alone (§2.3); the gradient at the fluid nodes and Eq. 4 follow the last pass.
+ * The iterates are bitwise those of repeated pc_project calls fed with the previous force.
+ * The stopping rule is evaluated on the device. With CUDA graphs on (pc_set_graphs, the default)
+ * the whole time step is one graph launch: a while-conditional node repeats the later passes
+ * until the device-side rule stops it (captured once per argument set, dt, tol and max_iters);
+ * with graphs off the host reads the decision after every pass. Either way the call returns when
+ * the step is done (one stream synchronisation per call, reading the pass count and history).
+ * Device pointers only, max_iters in [1, 1000] (PC_ERR_INVALID_ARG otherwise); not capturable
+ * (PC_ERR_INVALID_ARG on a capturing stream). The first call on a plan builds the node and face
+ * lists (one allocation: about 4 bytes per listed node or face, two force iterates, 16 KB of
+ * loop state). */
+typedef struct {
+  int iterations;
+  int converged;
+  double diff;   /* last pass: mean over boundary/virtual nodes of |f_new - f_old|^2 */
+  double prev;   /* and of |f_old|^2 */
+} pc_ib_result;
+
+pc_status pc_project_ib(pc_plan *plan, double dt, const void *u_star, const void *f_ib_init,
+                        double tol, int max_iters, double *p_out, void *u_out, void *f_ib_out,
+                        double *history, pc_ib_result *result, void *cuda_stream);
+
 typedef struct {
   double dt;
   const void *u_star;

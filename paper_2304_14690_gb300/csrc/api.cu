@@ -94,6 +94,7 @@ void prof_mark(Plan *p, cudaStream_t st, int tag) {
 
 void plan_drop_graphs(Plan *p) {
   batch_forget_plan(p);
+  ib_drop_graph(p);
   for (int i = 0; i < kGraphCache; ++i) {
     if (p->graphs[i].exec) cudaGraphExecDestroy(p->graphs[i].exec);
     if (p->graphs[i].graph) cudaGraphDestroy(p->graphs[i].graph);
@@ -116,6 +117,7 @@ static void destroy_plan(Plan *p) {
   if (p->cap_ev_made)
     for (int e = 0; e < kProfEvents; ++e) cudaEventDestroy(p->cap_ev[e]);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->ib_body_stream) cudaStreamDestroy(p->ib_body_stream);
   for (int i = 0; i < p->nallocs; ++i) cudaFree(p->allocs[i]);
   if (cur >= 0) cudaSetDevice(cur);
   delete p;

@@ -52,6 +52,8 @@ struct DevStats {
   double max_u;
   double mean_s;           // sum_s / ncells, written by the reducing block
   double shift;            // gauge constant, written by the reducing block
+  double ib_diff;          // IB-force iteration: sum over IB nodes of |f_new - f_old|^2
+  double ib_prev;          //   and of |f_old|^2
   unsigned int flags;
   unsigned int pad;
 };
@@ -80,6 +82,28 @@ struct GraphEntry {
   int tag[kProfEvents];
   long long launches = 0;
   unsigned long long stamp = 0;
+};
+
+// IB-force iteration (pc_project_ib): the device-side state of one time step's loop, written by
+// the last block of each pass's stopping-rule reduction, and the instantiated CUDA graph that
+// runs the whole loop (a while-conditional node around the later passes).
+constexpr int kIbMaxIters = 1000;
+struct IbCtl {
+  int it;                      // passes done
+  int conv;                    // stopping rule met by the last pass
+  int body;                    // executions of the loop graph's body (safety bound)
+  int pad;
+  double diff, prev;           // last pass: mean |f_new - f_old|^2 and mean |f_old|^2 (IB nodes)
+  double hist[2 * kIbMaxIters];
+};
+struct IbGraph {
+  const void *u = nullptr, *f = nullptr;
+  void *p = nullptr, *uo = nullptr, *fo = nullptr;
+  double dt = 0.0, tol = 0.0;
+  int max_iters = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long l_first = 0, l_body = 0, l_final = 0;   // kernels per segment (launch counts)
 };
 
 struct Plan {
@@ -126,6 +150,17 @@ struct Plan {
   // Staging for host pointers passed to pc_project.
   void *stage_u = nullptr, *stage_f = nullptr, *stage_uo = nullptr, *stage_fo = nullptr;
   double *stage_p = nullptr, *stage_s = nullptr;
+  // IB-force iteration (pc_project_ib), built on its first call: the boundary/virtual nodes,
+  // per axis the faces whose value row reaches one of them (the only fluxes that change after
+  // the first pass), and two compact force iterates [dim][nib] of velocity_dtype.
+  int64_t nib = -1;
+  int32_t *ib_idx = nullptr;
+  int32_t *ib_face[3] = {nullptr, nullptr, nullptr};
+  int64_t nib_face[3] = {0, 0, 0};
+  void *ib_f[2] = {nullptr, nullptr};   // [0] previous iterate, [1] current/new iterate
+  IbCtl *ib_ctl = nullptr;
+  cudaStream_t ib_body_stream = nullptr;
+  IbGraph ib_graph;
   size_t bytes = 0;
   void *allocs[64];
   int nallocs = 0;
@@ -154,6 +189,7 @@ struct Plan {
 // Profiler hooks (no-ops unless enabled): begin a call record, close the running segment as
 // phase `tag`, count kernel launches.
 void prof_begin(Plan *p, cudaStream_t st);
+void ib_drop_graph(Plan *p);   // the IB loop graph of a plan (project.cu)
 void prof_mark(Plan *p, cudaStream_t st, int tag);
 inline void count_launch(Plan *p, int n = 1) { p->launches += n; }
 
@@ -269,6 +305,10 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Set while a graph whose edges must stay plain is captured (the bodies of conditional nodes):
+// launch_pdl then launches without the programmatic attribute.
+inline thread_local bool tl_plain_launch = false;
+
 template <typename... KArgs, typename... Args>
 inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                        Args... args) {
@@ -281,7 +321,7 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = tl_plain_launch ? 0 : 1;
   cudaLaunchKernelEx(&cfg, kernel, args...);   // errors surface through cudaGetLastError
 }
 

@@ -206,19 +206,24 @@ static void launch_prep(bool has_f, bool stats, bool split, int cnt, const VT *u
 }
 
 // ----------------------------------------------------------------------------- transfer
-__global__ void transfer64_kernel(int rows, int K, const int32_t *__restrict__ col,
-                                  const double *__restrict__ w, const double *__restrict__ u,
-                                  double *__restrict__ U) {
-  pdl_enter();
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= rows) return;
+// Value row r of the face array (rows faces, neighbour-rank-major weights) applied to u~.
+__device__ __forceinline__ double transfer64_row(int r, int rows, int K, const int32_t *__restrict__ col,
+                                                 const double *__restrict__ w, const double *__restrict__ u) {
   double acc = 0.0;
 #pragma unroll 4
   for (int k = 0; k < K; ++k) {
     int at = k * rows + r;
     acc = fma(__ldg(w + at), __ldg(u + __ldg(col + at)), acc);
   }
-  U[r] = acc;
+  return acc;
+}
+__global__ void transfer64_kernel(int rows, int K, const int32_t *__restrict__ col,
+                                  const double *__restrict__ w, const double *__restrict__ u,
+                                  double *__restrict__ U) {
+  pdl_enter();
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  U[r] = transfer64_row(r, rows, K, col, w, u);
 }
 
 // Compensated dot product in FP32 arithmetic: (w.x + w.y) . (u.x + u.y) accumulated as an
@@ -246,11 +251,8 @@ struct PairSrc {
 };
 
 template <int KC, typename Src>
-__device__ __forceinline__ void transfer_mixed_kernel_body(const VBlock &vb, int rows, int Kr, const int32_t *__restrict__ col,
-                                      const float2 *__restrict__ w2, Src src,
-                                      double *__restrict__ U) {
-  int r = vb.x * blockDim.x + threadIdx.x;
-  if (r >= rows) return;
+__device__ __forceinline__ double transfer_mixed_row(int r, int rows, int Kr, const int32_t *__restrict__ col,
+                                                     const float2 *__restrict__ w2, Src src) {
   const int K = KC > 0 ? KC : Kr;
   DF s{0.f, 0.f};
   if (KC > 0) {
@@ -270,7 +272,15 @@ __device__ __forceinline__ void transfer_mixed_kernel_body(const VBlock &vb, int
       df_acc(s, __ldg(w2 + at), src(__ldg(col + at)));
     }
   }
-  U[r] = df_value(s);
+  return df_value(s);
+}
+template <int KC, typename Src>
+__device__ __forceinline__ void transfer_mixed_kernel_body(const VBlock &vb, int rows, int Kr, const int32_t *__restrict__ col,
+                                      const float2 *__restrict__ w2, Src src,
+                                      double *__restrict__ U) {
+  int r = vb.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  U[r] = transfer_mixed_row<KC>(r, rows, Kr, col, w2, src);
 }
 template <int KC, typename Src>
 __global__ void transfer_mixed_kernel(int rows, int Kr, const int32_t *__restrict__ col,
@@ -553,6 +563,20 @@ __global__ void finalize_p_kernel(int ncells, double *__restrict__ p, const DevS
 template <typename VT>
 __device__ __forceinline__ void store_v(VT *p, long long i, double v) { p[i] = (VT)v; }
 
+// WLS gradient of p at node i (derivative rows over the 3^d cell block).
+template <int DIM>
+__device__ __forceinline__ void grad64_at(int i, int N, int K, const int32_t *__restrict__ col,
+                                          const double *__restrict__ D, const double *__restrict__ p, double *g) {
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) g[a] = 0.0;
+#pragma unroll 3
+  for (int k = 0; k < K; ++k) {
+    double pv = __ldg(p + __ldg(col + k * N + i));
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) g[a] = fma(__ldg(D + (a * K + k) * N + i), pv, g[a]);
+  }
+}
+
 template <typename VT, int DIM>
 __global__ void gradient64_kernel(int N, int K, const int32_t *__restrict__ col,
                                   const double *__restrict__ D, const double *__restrict__ p,
@@ -563,14 +587,7 @@ __global__ void gradient64_kernel(int N, int K, const int32_t *__restrict__ col,
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double g[DIM];
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) g[a] = 0.0;
-#pragma unroll 3
-  for (int k = 0; k < K; ++k) {
-    double pv = __ldg(p + __ldg(col + k * N + i));
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) g[a] = fma(__ldg(D + (a * K + k) * N + i), pv, g[a]);
-  }
+  grad64_at<DIM>(i, N, K, col, D, p, g);
   const bool ib = type[i] != PC_NODE_FLUID;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
@@ -585,16 +602,11 @@ __global__ void gradient64_kernel(int N, int K, const int32_t *__restrict__ col,
   }
 }
 
-template <typename VT, int DIM>
-__device__ __forceinline__ void gradient_mixed_kernel_body(const VBlock &vb, int N, int K, const int32_t *__restrict__ col,
-                                      const float2 *__restrict__ D2, const float2 *__restrict__ p2,
-                                      const uint8_t *__restrict__ type, const VT *__restrict__ u,
-                                      double inv_dt, double dt, double beta, VT *__restrict__ uo,
-                                      VT *__restrict__ fo) {
-  int i = vb.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+// Compensated WLS gradient of the split pressure at node i.
+template <int DIM>
+__device__ __forceinline__ void grad_mixed_at(int i, int N, const int32_t *__restrict__ col,
+                                              const float2 *__restrict__ D2, const float2 *__restrict__ p2, double *gout) {
   constexpr int KB = (DIM == 2) ? 9 : 27;   // the 3^d gradient block
-  (void)K;
   DF g[DIM];
 #pragma unroll
   for (int a = 0; a < DIM; ++a) g[a] = DF{0.f, 0.f};
@@ -607,10 +619,25 @@ __device__ __forceinline__ void gradient_mixed_kernel_body(const VBlock &vb, int
 #pragma unroll
     for (int a = 0; a < DIM; ++a) df_acc(g[a], __ldg(D2 + (a * KB + k) * N + i), pv);
   }
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) gout[a] = df_value(g[a]);
+}
+
+template <typename VT, int DIM>
+__device__ __forceinline__ void gradient_mixed_kernel_body(const VBlock &vb, int N, int K, const int32_t *__restrict__ col,
+                                      const float2 *__restrict__ D2, const float2 *__restrict__ p2,
+                                      const uint8_t *__restrict__ type, const VT *__restrict__ u,
+                                      double inv_dt, double dt, double beta, VT *__restrict__ uo,
+                                      VT *__restrict__ fo) {
+  int i = vb.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  (void)K;
+  double g[DIM];
+  grad_mixed_at<DIM>(i, N, col, D2, p2, g);
   const bool ib = type[i] != PC_NODE_FLUID;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
-    double ga = df_value(g[a]);
+    double ga = g[a];
     double us = (double)u[a * N + i];
     if (ib) {
       store_v(uo, a * N + i, 0.0);
@@ -664,6 +691,146 @@ __global__ void div_check_kernel(GridDev g, const double *U0, const double *U1,
     }
   }
   block_max_update(v, &stats->max_div);
+}
+
+// ----------------------------------------------------------------------------- IB-force iteration
+// Kernels of pc_project_ib (§2.3). After the first pass only the force at the boundary and
+// virtual nodes changes, so a pass updates u~ at those nodes, recomputes the fluxes of the
+// faces whose value row reaches one of them (idx lists built once per plan), and evaluates the
+// gradient and the new force (Eq. 19) at those nodes alone; the gradient at the fluid nodes is
+// taken once, after the last pass. Every value is computed by the same per-row and per-node
+// arithmetic as the full pass, so the iterates equal those of repeated pc_project calls.
+//
+// Face flags: flag[r] = 1 when row r of this face array gathers a boundary/virtual node.
+__global__ void ib_face_flags_kernel(int rows, int K, const int32_t *__restrict__ col,
+                                     const uint8_t *__restrict__ type, uint8_t *__restrict__ flag) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  uint8_t f = 0;
+  for (int k = 0; k < K; ++k) f |= (uint8_t)(__ldg(type + __ldg(col + k * rows + r)) != PC_NODE_FLUID);
+  flag[r] = f;
+}
+
+// Compact force [dim][nib] from a full [dim][N] array (nullptr: zero).
+template <typename VT>
+__global__ void ib_gather_kernel(int nib, int N, int dim, const int32_t *__restrict__ idx,
+                                 const VT *__restrict__ f, VT *__restrict__ fc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nib) return;
+  const int i = __ldg(idx + j);
+  for (int a = 0; a < dim; ++a) fc[(long long)a * nib + j] = f ? f[(long long)a * N + i] : (VT)0;
+}
+
+// u~ = u* + dt f~ at the boundary/virtual nodes from the current iterate fc (the arithmetic of
+// the full prep with a force), which is also saved as the previous iterate fo for the stopping
+// rule before the pass overwrites fc with the new force.
+template <typename VT, bool SPLIT>
+__global__ void ib_prep_kernel(int nib, int N, int dim, const int32_t *__restrict__ idx,
+                               const VT *__restrict__ u, const VT *__restrict__ fc, VT *__restrict__ fo,
+                               double dt, double *__restrict__ ut64, float2 *__restrict__ u2) {
+  pdl_enter();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nib) return;
+  const int i = __ldg(idx + j);
+  for (int a = 0; a < dim; ++a) {
+    const long long at = (long long)a * N + i;
+    const VT f = fc[(long long)a * nib + j];
+    fo[(long long)a * nib + j] = f;
+    const double v = fma(dt, as_f64(f), as_f64(u[at]));
+    if (SPLIT) u2[at] = as_pair(v);
+    else ut64[at] = v;
+  }
+}
+
+// Fluxes of the listed faces only.
+__global__ void ib_transfer64_kernel(int nl, const int32_t *__restrict__ list, int rows, int K,
+                                     const int32_t *__restrict__ col, const double *__restrict__ w,
+                                     const double *__restrict__ u, double *__restrict__ U) {
+  pdl_enter();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nl) return;
+  const int r = __ldg(list + t);
+  U[r] = transfer64_row(r, rows, K, col, w, u);
+}
+template <int KC>
+__global__ void ib_transfer_mixed_kernel(int nl, const int32_t *__restrict__ list, int rows, int Kr,
+                                         const int32_t *__restrict__ col, const float2 *__restrict__ w2,
+                                         PairSrc src, double *__restrict__ U) {
+  pdl_enter();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nl) return;
+  const int r = __ldg(list + t);
+  U[r] = transfer_mixed_row<KC>(r, rows, Kr, col, w2, src);
+}
+
+// New force at the boundary/virtual nodes (Eq. 19), compact [dim][nib].
+template <typename VT, int DIM, bool MIXED>
+__global__ void ib_force_kernel(int nib, const int32_t *__restrict__ idx, int N, int K,
+                                const int32_t *__restrict__ col, const double *__restrict__ D,
+                                const float2 *__restrict__ D2, const double *__restrict__ p,
+                                const float2 *__restrict__ p2, const VT *__restrict__ u, double inv_dt,
+                                double beta, VT *__restrict__ fc) {
+  pdl_enter();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nib) return;
+  const int i = __ldg(idx + j);
+  double g[DIM];
+  if (MIXED) grad_mixed_at<DIM>(i, N, col, D2, p2, g);
+  else grad64_at<DIM>(i, N, K, col, D, p, g);
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    const double us = (double)u[(long long)a * N + i];
+    store_v(fc, (long long)a * nib + j, -us * inv_dt + beta * g[a]);
+  }
+}
+
+// Sums over the boundary/virtual nodes of |f_new - f_old|^2 and |f_old|^2 (deterministic: a
+// fixed grid of kIbBlocks blocks, grid-stride, then the last-block reduction). The thread that
+// completes the second sum applies the stopping rule of §2.3 to the means, records the pass in
+// ctl and, inside the loop graph (COND), sets the condition of the while node: another pass
+// unless converged or max_iters passes are done.
+constexpr int kIbBlocks = 32;
+template <typename VT, bool COND>
+__global__ void ib_change_kernel(int nib, int dim, const VT *__restrict__ fn, const VT *__restrict__ fo,
+                                 DevStats *stats, double *partials, unsigned int *counter, IbCtl *ctl,
+                                 double tol, int max_iters, cudaGraphConditionalHandle cond) {
+  pdl_enter();
+  double d = 0.0, o = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nib; j += gridDim.x * blockDim.x)
+    for (int a = 0; a < dim; ++a) {
+      const double n = as_f64(fn[(long long)a * nib + j]), f = as_f64(fo[(long long)a * nib + j]);
+      d = fma(n - f, n - f, d);
+      o = fma(f, f, o);
+    }
+  const VBlock vb = hw_block();
+  grid_sum(d, partials, counter, &stats->ib_diff, vb);
+  if (grid_sum(o, partials + gridDim.x, counter + 1, &stats->ib_prev, vb)) {
+    // every block has passed the first sum, whose total was stored before its last block
+    // entered the second one (store, fence, counter) and is read past L1 here
+    const double diff = __ldcg(&stats->ib_diff) / (double)nib;
+    const double prev = stats->ib_prev / (double)nib;
+    const int it = ctl->it;
+    if (it < kIbMaxIters) {
+      ctl->hist[2 * it] = diff;
+      ctl->hist[2 * it + 1] = prev;
+    }
+    const bool conv = prev == 0.0 ? diff == 0.0 : diff <= tol * prev;
+    ctl->it = it + 1;
+    ctl->conv = conv ? 1 : 0;
+    ctl->diff = diff;
+    ctl->prev = prev;
+    if (COND) cudaGraphSetConditional(cond, (!conv && it + 1 < max_iters) ? 1u : 0u);
+  }
+}
+
+// Safety bound of the loop graph, independent of the stopping rule: it runs after the rule in
+// every execution of the while body and clears the condition once 1 + (body executions) passes
+// are done, so the loop ends after max_iters passes even if the rule's reduction never decided.
+__global__ void ib_guard_kernel(IbCtl *ctl, int max_iters, cudaGraphConditionalHandle cond) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int n = ++ctl->body;
+    if (n + 1 >= max_iters) cudaGraphSetConditional(cond, 0u);
+  }
 }
 
 static GridDev grid_dev(const Plan *p);
@@ -997,6 +1164,33 @@ static pc_status fill_stats(Plan *p, pc_stats *stats, cudaStream_t st) {
   return PC_OK;
 }
 
+// Gradient and correction at every node (Eq. 4 at fluid nodes, Eqs. 18-19 at boundary/virtual
+// nodes) from the solved pressure: p2 pairs (mixed) or the FP64 p in dp.
+static void launch_gradient(Plan *p, cudaStream_t st, const double *dp, const void *ug, double dt, void *duo,
+                            void *dfo) {
+  const int T = 256;
+  const long long N = p->N;
+  const int d = p->dim;
+  const bool mixed = p->precision != PC_PREC_FP64;
+  if (p->vdtype == PC_DTYPE_F64) {
+    if (mixed) {
+      if (d == 2) launch_pdl(gradient_mixed_kernel<double, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
+      else launch_pdl(gradient_mixed_kernel<double, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
+    } else {
+      if (d == 2) launch_pdl(gradient64_kernel<double, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
+      else launch_pdl(gradient64_kernel<double, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
+    }
+  } else {
+    if (mixed) {
+      if (d == 2) launch_pdl(gradient_mixed_kernel<float, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
+      else launch_pdl(gradient_mixed_kernel<float, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
+    } else {
+      if (d == 2) launch_pdl(gradient64_kernel<float, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
+      else launch_pdl(gradient64_kernel<float, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
+    }
+  }
+}
+
 static pc_status project_impl(Plan *p, double dt, const void *u_star, const void *f_in, double *p_out,
                               void *u_out, void *f_out, pc_stats *stats, cudaStream_t st,
                               bool all_device = false) {
@@ -1060,24 +1254,7 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   PC_TRY(solve_grid(p, p->s64, dp, stats != nullptr, st,
                     mixed ? reinterpret_cast<const float *>(p->work64) : nullptr,
                     mixed ? reinterpret_cast<const float2 *>(p->s64) : nullptr));
-  const void *ug = du;
-  if (p->vdtype == PC_DTYPE_F64) {
-    if (mixed) {
-      if (d == 2) launch_pdl(gradient_mixed_kernel<double, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
-      else launch_pdl(gradient_mixed_kernel<double, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
-    } else {
-      if (d == 2) launch_pdl(gradient64_kernel<double, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
-      else launch_pdl(gradient64_kernel<double, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
-    }
-  } else {
-    if (mixed) {
-      if (d == 2) launch_pdl(gradient_mixed_kernel<float, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
-      else launch_pdl(gradient_mixed_kernel<float, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
-    } else {
-      if (d == 2) launch_pdl(gradient64_kernel<float, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
-      else launch_pdl(gradient64_kernel<float, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
-    }
-  }
+  launch_gradient(p, st, dp, du, dt, duo, dfo);
   count_launch(p);
   prof_mark(p, st, 6);
   if (stats) {
@@ -1209,6 +1386,323 @@ static pc_status project_graph(Plan *p, double dt, const void *u_star, const voi
   return PC_OK;
 }
 
+// ----------------------------------------------------------------------------- IB-force iteration
+// Tables of the iteration, built on the first pc_project_ib call of a plan instance (one setup
+// synchronisation): the boundary/virtual node list, the faces each axis must refresh after the
+// first pass (ascending face order), and the two compact force iterates.
+static pc_status ib_tables(Plan *p, cudaStream_t st) {
+  if (p->nib >= 0) return PC_OK;
+  const long long N = p->N;
+  const int d = p->dim;
+  std::vector<uint8_t> type((size_t)N);
+  PC_CUDA_TRY(cudaMemcpyAsync(type.data(), p->ntype, (size_t)N, cudaMemcpyDeviceToHost, st));
+  PC_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<int32_t> idx;
+  for (long long i = 0; i < N; ++i)
+    if (type[(size_t)i] != PC_NODE_FLUID) idx.push_back((int32_t)i);
+  std::vector<int32_t> faces[3];
+  if (!idx.empty()) {
+    long long maxrows = 0;
+    for (int a = 0; a < d; ++a) maxrows = p->nface_total[a] > maxrows ? p->nface_total[a] : maxrows;
+    uint8_t *flag = nullptr;
+    PC_CUDA_TRY(cudaMalloc(&flag, (size_t)maxrows));
+    std::vector<uint8_t> hf((size_t)maxrows);
+    cudaError_t e = cudaSuccess;
+    for (int a = 0; a < d && e == cudaSuccess; ++a) {
+      const long long rows = p->nface_total[a];
+      ib_face_flags_kernel<<<grid_for(rows, 256), 256, 0, st>>>((int)rows, p->K, p->fcol[a], p->ntype, flag);
+      e = cudaMemcpyAsync(hf.data(), flag, (size_t)rows, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      for (long long r = 0; r < rows && e == cudaSuccess; ++r)
+        if (hf[(size_t)r]) faces[a].push_back((int32_t)r);
+    }
+    cudaFree(flag);
+    if (e != cudaSuccess) return fail(PC_ERR_CUDA, "IB face tables: %s", cudaGetErrorString(e));
+  }
+  const long long nib = (long long)idx.size();
+  const size_t vsz = p->vdtype == PC_DTYPE_F64 ? 8 : 4;
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  size_t ints = (size_t)nib;
+  for (int a = 0; a < d; ++a) ints += faces[a].size();
+  const size_t fbytes = up((size_t)d * nib * vsz);
+  const size_t total = up(ints * 4) + 2 * fbytes + up(sizeof(IbCtl)) + 256;
+  char *base = nullptr;
+  PC_TRY(plan_alloc(p, (void **)&base, total));
+  p->ib_ctl = reinterpret_cast<IbCtl *>(base + up(ints * 4) + 2 * fbytes);
+  int32_t *ip = reinterpret_cast<int32_t *>(base);
+  p->ib_idx = ip;
+  if (nib) PC_CUDA_TRY(cudaMemcpyAsync(ip, idx.data(), (size_t)nib * 4, cudaMemcpyHostToDevice, st));
+  ip += nib;
+  for (int a = 0; a < d; ++a) {
+    p->ib_face[a] = ip;
+    p->nib_face[a] = (int64_t)faces[a].size();
+    if (!faces[a].empty())
+      PC_CUDA_TRY(cudaMemcpyAsync(ip, faces[a].data(), faces[a].size() * 4, cudaMemcpyHostToDevice, st));
+    ip += faces[a].size();
+  }
+  p->ib_f[0] = base + up(ints * 4);
+  p->ib_f[1] = base + up(ints * 4) + fbytes;
+  PC_CUDA_TRY(cudaStreamSynchronize(st));   // the host vectors die here
+  p->nib = nib;
+  return PC_OK;
+}
+
+template <typename VT>
+static void ib_launch_force(Plan *p, cudaStream_t st, const double *dp, const VT *u, double dt, VT *fc) {
+  const int T = 256;
+  const int G = grid_for(p->nib, T);
+  const bool mixed = p->precision != PC_PREC_FP64;
+  const int nib = (int)p->nib, N = (int)p->N;
+  if (p->dim == 2) {
+    if (mixed) launch_pdl(ib_force_kernel<VT, 2, true>, G, T, 0, st, nib, p->ib_idx, N, p->Kg, p->ncol, p->nD64, p->nD2, dp, p->p2, u, 1.0 / dt, p->beta, fc);
+    else launch_pdl(ib_force_kernel<VT, 2, false>, G, T, 0, st, nib, p->ib_idx, N, p->Kg, p->ncol, p->nD64, p->nD2, dp, p->p2, u, 1.0 / dt, p->beta, fc);
+  } else {
+    if (mixed) launch_pdl(ib_force_kernel<VT, 3, true>, G, T, 0, st, nib, p->ib_idx, N, p->Kg, p->ncol, p->nD64, p->nD2, dp, p->p2, u, 1.0 / dt, p->beta, fc);
+    else launch_pdl(ib_force_kernel<VT, 3, false>, G, T, 0, st, nib, p->ib_idx, N, p->Kg, p->ncol, p->nD64, p->nD2, dp, p->p2, u, 1.0 / dt, p->beta, fc);
+  }
+}
+
+// One pass of the iteration: u~ (all nodes on the first pass, then the IB nodes), fluxes (all
+// faces on the first pass, then the listed faces), source, solve, the new force at the IB nodes
+// (ib_f[1], after the current one has been saved in ib_f[0]) and the stopping rule. With cond
+// != 0 the rule also sets the while condition of the loop graph.
+template <typename VT>
+static pc_status ib_pass(Plan *p, bool first, double dt, const VT *du, double *dp, double tol, int max_iters,
+                         bool use_cond, cudaGraphConditionalHandle cond, cudaStream_t st) {
+  const int d = p->dim;
+  const long long N = p->N, nc = p->ncells;
+  const bool mixed = p->precision != PC_PREC_FP64;
+  const int T = 256;
+  const int nib = (int)p->nib;
+  VT *fo = static_cast<VT *>(p->ib_f[0]), *fc = static_cast<VT *>(p->ib_f[1]);
+  prof_begin(p, st);
+  PC_CUDA_TRY(cudaMemsetAsync(p->dstats, 0, sizeof(DevStats), st));
+  if (first) {
+    launch_prep<VT>(false, false, mixed, (int)(d * N), du, nullptr, dt, p->ut64, p->u2, p->dstats, st);
+    count_launch(p);
+  }
+  if (nib) {
+    if (mixed) launch_pdl(ib_prep_kernel<VT, true>, grid_for(nib, T), T, 0, st, nib, (int)N, d, p->ib_idx, du, (const VT *)fc, fo, dt, p->ut64, p->u2);
+    else launch_pdl(ib_prep_kernel<VT, false>, grid_for(nib, T), T, 0, st, nib, (int)N, d, p->ib_idx, du, (const VT *)fc, fo, dt, p->ut64, p->u2);
+    count_launch(p);
+  }
+  prof_mark(p, st, 0);
+  for (int a = 0; a < d; ++a) {
+    const long long rows = p->nface_total[a];
+    const long long nl = first ? rows : p->nib_face[a];
+    if (nl == 0) continue;
+    const int G = grid_for(nl, T);
+    if (mixed) {
+      const PairSrc src{p->u2 + (long long)a * N};
+      if (first) {
+        if (p->K == 12) launch_pdl(transfer_mixed_kernel<12, PairSrc>, G, T, 0, st, (int)rows, p->K, p->fcol[a], p->fw2[a], src, p->U64[a]);
+        else if (p->K == 27) launch_pdl(transfer_mixed_kernel<27, PairSrc>, G, T, 0, st, (int)rows, p->K, p->fcol[a], p->fw2[a], src, p->U64[a]);
+        else launch_pdl(transfer_mixed_kernel<0, PairSrc>, G, T, 0, st, (int)rows, p->K, p->fcol[a], p->fw2[a], src, p->U64[a]);
+      } else {
+        if (p->K == 12) launch_pdl(ib_transfer_mixed_kernel<12>, G, T, 0, st, (int)nl, p->ib_face[a], (int)rows, p->K, p->fcol[a], p->fw2[a], src, p->U64[a]);
+        else if (p->K == 27) launch_pdl(ib_transfer_mixed_kernel<27>, G, T, 0, st, (int)nl, p->ib_face[a], (int)rows, p->K, p->fcol[a], p->fw2[a], src, p->U64[a]);
+        else launch_pdl(ib_transfer_mixed_kernel<0>, G, T, 0, st, (int)nl, p->ib_face[a], (int)rows, p->K, p->fcol[a], p->fw2[a], src, p->U64[a]);
+      }
+    } else {
+      if (first) launch_pdl(transfer64_kernel, G, T, 0, st, (int)rows, p->K, p->fcol[a], p->fw64[a], p->ut64 + (long long)a * N, p->U64[a]);
+      else launch_pdl(ib_transfer64_kernel, G, T, 0, st, (int)nl, p->ib_face[a], (int)rows, p->K, p->fcol[a], p->fw64[a], p->ut64 + (long long)a * N, p->U64[a]);
+    }
+    count_launch(p);
+  }
+  prof_mark(p, st, 1);
+  GridDev g = grid_dev(p);
+  {
+    auto divk = (d == 2) ? divergence_kernel<2> : divergence_kernel<3>;
+    launch_pdl(divk, g.nblk, 256, 0, st, g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt),
+               mixed ? nullptr : p->s64, mixed ? reinterpret_cast<float2 *>(p->s64) : nullptr,
+               mixed ? reinterpret_cast<float *>(p->work64) : nullptr, p->dstats, p->partials, p->counters,
+               p->singular ? 1 : 0, 1.0 / (double)nc);
+  }
+  count_launch(p);
+  prof_mark(p, st, 2);
+  PC_CUDA_TRY(cudaGetLastError());
+  PC_TRY(solve_grid(p, p->s64, dp, false, st, mixed ? reinterpret_cast<const float *>(p->work64) : nullptr,
+                    mixed ? reinterpret_cast<const float2 *>(p->s64) : nullptr));
+  if (nib) {
+    ib_launch_force<VT>(p, st, dp, du, dt, fc);
+    count_launch(p);
+    prof_mark(p, st, 6);
+    const int G = grid_for(nib, T) < kIbBlocks ? grid_for(nib, T) : kIbBlocks;
+    if (use_cond)
+      launch_pdl(ib_change_kernel<VT, true>, G, T, 0, st, nib, d, (const VT *)fc, (const VT *)fo, p->dstats, p->partials, p->counters, p->ib_ctl, tol, max_iters, cond);
+    else
+      launch_pdl(ib_change_kernel<VT, false>, G, T, 0, st, nib, d, (const VT *)fc, (const VT *)fo, p->dstats, p->partials, p->counters, p->ib_ctl, tol, max_iters, cond);
+    count_launch(p);
+    prof_mark(p, st, 7);
+  }
+  PC_CUDA_TRY(cudaGetLastError());
+  return PC_OK;
+}
+
+// Start of a time step: pass counter cleared, the initial force (IB entries of f_init, or zero)
+// as the current iterate.
+template <typename VT>
+static pc_status ib_start(Plan *p, const VT *f_init, cudaStream_t st) {
+  PC_CUDA_TRY(cudaMemsetAsync(p->ib_ctl, 0, offsetof(IbCtl, hist), st));
+  ib_gather_kernel<VT><<<grid_for(p->nib, 256), 256, 0, st>>>((int)p->nib, (int)p->N, p->dim, p->ib_idx, f_init,
+                                                              static_cast<VT *>(p->ib_f[1]));
+  count_launch(p);
+  return PC_OK;
+}
+
+void ib_drop_graph(Plan *p) {
+  if (p->ib_graph.exec) cudaGraphExecDestroy(p->ib_graph.exec);
+  if (p->ib_graph.graph) cudaGraphDestroy(p->ib_graph.graph);
+  p->ib_graph = IbGraph{};
+}
+
+// The whole time step as one CUDA graph: start, first pass, a while node whose body is one later
+// pass (its condition set on the device by the stopping rule), then the gradient and Eq. 4 at
+// every node. Captured once per argument set on the plan's private streams with plain launches
+// (no programmatic edges in the conditional body) and no profiler events.
+template <typename VT>
+static pc_status ib_capture(Plan *p, double dt, const VT *du, const VT *f_init, double tol, int max_iters,
+                            double *dp, VT *duo, VT *dfo) {
+  ib_drop_graph(p);
+  if (!p->ib_body_stream) PC_CUDA_TRY(cudaStreamCreateWithFlags(&p->ib_body_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = p->cap_stream, bs = p->ib_body_stream;
+  const bool prof = p->prof;
+  p->prof = false;
+  p->cur = nullptr;
+  tl_plain_launch = true;
+  const long long l0 = p->launches;
+  long long l1 = 0, l2 = 0, l3 = 0;
+  pc_status s = PC_OK;
+  cudaGraph_t g = nullptr, body_done = nullptr;
+  cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (ce == cudaSuccess) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edges = nullptr;
+    size_t ndeps = 0;
+    cudaGraphConditionalHandle h = 0;
+    cudaGraphNode_t node = nullptr;
+    cudaGraphNodeParams cp = {};
+    if (s == PC_OK) {
+      ce = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, nullptr, nullptr, nullptr);
+      if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&h, cg, 0u, cudaGraphCondAssignDefault);
+      if (ce != cudaSuccess) s = fail(PC_ERR_CUDA, "IB loop graph: %s", cudaGetErrorString(ce));
+    }
+    if (s == PC_OK) s = ib_start<VT>(p, f_init, cs);
+    if (s == PC_OK) s = ib_pass<VT>(p, true, dt, du, dp, tol, max_iters, true, h, cs);
+    l1 = p->launches;
+    if (s == PC_OK) {
+      ce = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, &edges, &ndeps);
+      if (ce == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ce = cudaGraphAddNode(&node, cg, deps, edges, ndeps, &cp);
+      }
+      if (ce == cudaSuccess) ce = cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+      if (ce == cudaSuccess)
+        ce = cudaStreamBeginCaptureToGraph(bs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal);
+      if (ce != cudaSuccess) s = fail(PC_ERR_CUDA, "IB loop graph: %s", cudaGetErrorString(ce));
+      else {
+        s = ib_pass<VT>(p, false, dt, du, dp, tol, max_iters, true, h, bs);
+        if (s == PC_OK) {
+          ib_guard_kernel<<<1, 32, 0, bs>>>(p->ib_ctl, max_iters, h);
+          count_launch(p);
+          if (cudaGetLastError() != cudaSuccess) s = fail(PC_ERR_CUDA, "IB loop guard launch failed");
+        }
+        ce = cudaStreamEndCapture(bs, &body_done);
+        if (s == PC_OK && ce != cudaSuccess) s = fail(PC_ERR_CUDA, "IB loop body capture: %s", cudaGetErrorString(ce));
+      }
+    }
+    l2 = p->launches;
+    if (s == PC_OK) {
+      launch_gradient(p, cs, dp, du, dt, duo, dfo);
+      count_launch(p);
+      if (cudaGetLastError() != cudaSuccess) s = fail(PC_ERR_CUDA, "IB loop graph: gradient launch failed");
+    }
+    l3 = p->launches;
+    ce = cudaStreamEndCapture(cs, &g);
+    if (s == PC_OK && ce != cudaSuccess) s = fail(PC_ERR_CUDA, "IB loop capture: %s", cudaGetErrorString(ce));
+  } else {
+    s = fail(PC_ERR_CUDA, "IB loop capture: %s", cudaGetErrorString(ce));
+  }
+  tl_plain_launch = false;
+  p->prof = prof;
+  p->launches = l0;
+  if (s != PC_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  cudaGraphExec_t ex = nullptr;
+  ce = cudaGraphInstantiate(&ex, g, 0ULL);
+  if (ce != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(PC_ERR_CUDA, "IB loop graph instantiation: %s", cudaGetErrorString(ce));
+  }
+  IbGraph &e = p->ib_graph;
+  e.graph = g; e.exec = ex;
+  e.u = du; e.f = f_init; e.p = dp; e.uo = duo; e.fo = dfo; e.dt = dt; e.tol = tol; e.max_iters = max_iters;
+  e.l_first = l1 - l0; e.l_body = l2 - l1; e.l_final = l3 - l2;
+  return PC_OK;
+}
+
+template <typename VT>
+static pc_status project_ib_impl(Plan *p, double dt, const VT *du, const VT *f_init, double tol, int max_iters,
+                                 double *dp, VT *duo, VT *dfo, double *history, pc_ib_result *res,
+                                 cudaStream_t st) {
+  PC_TRY(ib_tables(p, st));
+  IbCtl h;
+  memset(&h, 0, offsetof(IbCtl, hist));
+  if (p->nib == 0) {
+    // no boundary/virtual nodes: one pass with zero force, nothing to iterate
+    PC_TRY(ib_pass<VT>(p, true, dt, du, dp, tol, max_iters, false, 0, st));
+    h.it = 1;
+    h.conv = 1;
+    h.hist[0] = h.hist[1] = 0.0;
+    launch_gradient(p, st, dp, du, dt, duo, dfo);
+    count_launch(p);
+    PC_CUDA_TRY(cudaGetLastError());
+  } else if (p->graphs_on) {
+    IbGraph &e = p->ib_graph;
+    if (!(e.exec && e.u == du && e.f == f_init && e.p == dp && e.uo == duo && e.fo == dfo && e.dt == dt &&
+          e.tol == tol && e.max_iters == max_iters))
+      PC_TRY(ib_capture<VT>(p, dt, du, f_init, tol, max_iters, dp, duo, dfo));
+    PC_CUDA_TRY(cudaGraphLaunch(e.exec, st));
+    PC_CUDA_TRY(cudaMemcpyAsync(&h, p->ib_ctl, offsetof(IbCtl, hist) + 2 * sizeof(double) * max_iters,
+                                cudaMemcpyDeviceToHost, st));
+    PC_CUDA_TRY(cudaStreamSynchronize(st));
+    p->launches += e.l_first + (long long)(h.it - 1) * e.l_body + e.l_final;
+  } else {
+    // the same passes driven from the host: the pass counter and the decision are read back
+    // after every pass
+    PC_TRY(ib_start<VT>(p, f_init, st));
+    for (int it = 0;; ++it) {
+      PC_TRY(ib_pass<VT>(p, it == 0, dt, du, dp, tol, max_iters, false, 0, st));
+      PC_CUDA_TRY(cudaMemcpyAsync(&h, p->ib_ctl, offsetof(IbCtl, hist), cudaMemcpyDeviceToHost, st));
+      PC_CUDA_TRY(cudaStreamSynchronize(st));
+      if (h.conv || h.it >= max_iters) break;
+    }
+    launch_gradient(p, st, dp, du, dt, duo, dfo);
+    count_launch(p);
+    PC_CUDA_TRY(cudaGetLastError());
+    PC_CUDA_TRY(cudaMemcpyAsync(&h, p->ib_ctl, offsetof(IbCtl, hist) + 2 * sizeof(double) * max_iters,
+                                cudaMemcpyDeviceToHost, st));
+    PC_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  if (history)
+    for (int k = 0; k < h.it; ++k) { history[2 * k] = h.hist[2 * k]; history[2 * k + 1] = h.hist[2 * k + 1]; }
+  if (res) {
+    res->iterations = h.it;
+    res->converged = h.conv;
+    res->diff = h.it ? h.hist[2 * (h.it - 1)] : 0.0;
+    res->prev = h.it ? h.hist[2 * (h.it - 1) + 1] : 0.0;
+  }
+  return PC_OK;
+}
+
 }  // namespace pc
 
 extern "C" pc_status pc_project(pc_plan *plan, double dt, const void *u_star, const void *f_ib_in,
@@ -1238,3 +1732,27 @@ extern "C" pc_status pc_solve_poisson(pc_plan *plan, const double *s, double *p_
   return pc::solve_impl(p, s, p_out, stats, (cudaStream_t)cuda_stream);
 }
 
+extern "C" pc_status pc_project_ib(pc_plan *plan, double dt, const void *u_star, const void *f_ib_init,
+                                   double tol, int max_iters, double *p_out, void *u_out, void *f_ib_out,
+                                   double *history, pc_ib_result *result, void *cuda_stream) {
+  pc::Plan *p = reinterpret_cast<pc::Plan *>(plan);
+  if (!p) return pc::fail(PC_ERR_INVALID_ARG, "plan is NULL");
+  if (!u_star || !p_out || !u_out) return pc::fail(PC_ERR_INVALID_ARG, "u_star, p_out and u_out are required");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return pc::fail(PC_ERR_INVALID_ARG, "dt must be positive and finite");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return pc::fail(PC_ERR_INVALID_ARG, "tol must be finite and >= 0");
+  if (max_iters < 1 || max_iters > pc::kIbMaxIters)
+    return pc::fail(PC_ERR_INVALID_ARG, "max_iters must be in [1, %d]", pc::kIbMaxIters);
+  if (cudaSetDevice(p->device) != cudaSuccess) return pc::fail(PC_ERR_CUDA, "cannot select device %d", p->device);
+  if (!pc::is_device_ptr(u_star) || (f_ib_init && !pc::is_device_ptr(f_ib_init)) || !pc::is_device_ptr(p_out) ||
+      !pc::is_device_ptr(u_out) || (f_ib_out && !pc::is_device_ptr(f_ib_out)))
+    return pc::fail(PC_ERR_INVALID_ARG, "pc_project_ib takes device pointers only");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return pc::fail(PC_ERR_INVALID_ARG, "pc_project_ib waits on the host between passes and cannot be captured");
+  if (p->vdtype == PC_DTYPE_F64)
+    return pc::project_ib_impl<double>(p, dt, (const double *)u_star, (const double *)f_ib_init, tol, max_iters,
+                                       p_out, (double *)u_out, (double *)f_ib_out, history, result, st);
+  return pc::project_ib_impl<float>(p, dt, (const float *)u_star, (const float *)f_ib_init, tol, max_iters, p_out,
+                                    (float *)u_out, (float *)f_ib_out, history, result, st);
+}

@@ -85,6 +85,11 @@ class Profile(ctypes.Structure):
 PHASES = ("prep", "transfer", "divergence", "transform", "residual", "gauge", "gradient", "stats")
 
 
+class IbResult(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("diff", ctypes.c_double), ("prev", ctypes.c_double)]
+
+
 class ProjectArgs(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("u_star", ctypes.c_void_p), ("f_ib_in", ctypes.c_void_p),
                 ("p_out", ctypes.c_void_p), ("u_out", ctypes.c_void_p), ("f_ib_out", ctypes.c_void_p)]
@@ -96,6 +101,10 @@ FUNCTIONS = {
     "pc_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.POINTER(Stats), ctypes.c_void_p]),
+    "pc_project_ib": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(IbResult), ctypes.c_void_p]),
     "pc_project_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(ProjectArgs), ctypes.c_void_p]),
     "pc_solve_poisson": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -321,6 +330,27 @@ class Plan:
                               _ptr(f, vshape, self.vdtype, "f_out"),
                               ctypes.byref(st) if st is not None else None, _stream_handle(stream)))
         return p, u, f, (st.as_dict() if st is not None else None)
+
+    def project_ib(self, u_star, f_init=None, tol=1e-3, max_iters=50, dt=None, out=None, stream=None):
+        """Run pc_project_ib (the IB-force iteration) on device tensors [dim, N].
+        Returns (p, u_out, f_out, info) with info = dict(iterations, converged, diff, prev,
+        history=[(diff, prev) per pass])."""
+        lib = load()
+        if dt is None:
+            dt = self.problem.dt
+        p, u, f = out if out is not None else self.alloc_outputs()
+        vshape = (self.dim, self.N)
+        hist = (ctypes.c_double * (2 * int(max_iters)))()
+        res = IbResult()
+        _check(lib.pc_project_ib(self.handle, float(dt), _ptr(u_star, vshape, self.vdtype, "u_star"),
+                                 _ptr(f_init, vshape, self.vdtype, "f_init"), float(tol), int(max_iters),
+                                 _ptr(p, self.shape, None, "p_out"), _ptr(u, vshape, self.vdtype, "u_out"),
+                                 _ptr(f, vshape, self.vdtype, "f_out"), hist, ctypes.byref(res),
+                                 _stream_handle(stream)))
+        n = res.iterations
+        info = dict(iterations=n, converged=bool(res.converged), diff=res.diff, prev=res.prev,
+                    history=[(hist[2 * k], hist[2 * k + 1]) for k in range(n)])
+        return p, u, f, info
 
     def solve_poisson(self, s, p_out=None, stats=False, stream=None):
         import torch

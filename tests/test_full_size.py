@@ -1,8 +1,8 @@
 """GPU parity at the full sizes of the measured workloads, through the C ABI.
 
 Channel with cylinder, 1024x512 cells, ~4.0e5 nodes (the benchmark workload): the oracle runs
-the whole projection, so p, u and f are compared element by element (FP64 1e-12, mixed 1e-10
-relative L2).
+the whole projection, and the IB-force iteration at tolerance 1e-3, so p, u and f are compared
+element by element (FP64 1e-12, mixed 1e-10 relative L2).
 
 Box with sphere, 256x128x128 cells, ~4.3e6 nodes, K = 27: the oracle's neighbour search and
 WLS setup for 1.3e7 face rows would take minutes, so the comparison is split:
@@ -49,10 +49,15 @@ def env():
     return pc, torch, torch.device("cuda", 0)
 
 
-def test_channel_full_projection(env):
-    pc, torch, dev = env
+@pytest.fixture(scope="module")
+def channel():
     prob = wl.channel_cylinder()
-    oplan = PR.build_plan(grid_of(prob), prob.nodes, prob.node_type, K=prob.knn)
+    return prob, PR.build_plan(grid_of(prob), prob.nodes, prob.node_type, K=prob.knn)
+
+
+def test_channel_full_projection(env, channel):
+    pc, torch, dev = env
+    prob, oplan = channel
     ref = PR.project(oplan, prob.dt, prob.u_star)
     u = torch.as_tensor(prob.u_star, device=dev)
     for precision, tol in (("fp64", 1e-12), ("mixed", 1e-10)):
@@ -64,6 +69,28 @@ def test_channel_full_projection(env):
         assert rel(uo.cpu().numpy(), ref["u"]) <= tol, precision
         assert rel(fo.cpu().numpy(), ref["f"]) <= tol, precision
         assert st["max_div_after"] * min(prob.h) / st["max_abs_u_star"] <= 1e-9
+        plan.close()
+
+
+def test_channel_ib_iteration(env, channel):
+    """The IB-force iteration at the paper's tolerance 1e-3 on the full channel (~2.4e4
+    boundary/virtual nodes), in the launch configuration the benchmark times: same number of
+    passes as the oracle (every pass ratio is far from the threshold), p, u, f element by element."""
+    pc, torch, dev = env
+    prob, oplan = channel
+    ref = PR.project_ib(oplan, prob.dt, prob.u_star, tol=1e-3, max_iters=50)
+    ratios = [d / p for d, p in ref["history"] if p > 0]
+    assert all(abs(r / 1e-3 - 1.0) > 0.05 for r in ratios)
+    u = torch.as_tensor(prob.u_star, device=dev)
+    for precision, tol in (("fp64", 1e-12), ("mixed", 1e-10)):
+        plan = pc.Plan(prob, precision=precision)
+        if precision == "mixed":
+            plan.autotune()
+        p, uo, fo, info = plan.project_ib(u, tol=1e-3, max_iters=50)
+        assert info["iterations"] == ref["iterations"] and info["converged"], precision
+        assert rel(p.cpu().numpy(), ref["p"]) <= tol, precision
+        assert rel(uo.cpu().numpy(), ref["u"]) <= tol, precision
+        assert rel(fo.cpu().numpy(), ref["f"]) <= tol, precision
         plan.close()
 
 

@@ -248,3 +248,123 @@ def test_taylor_green_config(env):
         assert rel(uo.cpu().numpy(), ref["u"]) <= tol
         assert st["max_div_after"] * min(prob.h) / st["max_abs_u_star"] <= 1e-9
         plan.close()
+
+
+IB_CASES = [1, 2, 7]     # the cases with obstacles (boundary and virtual nodes)
+
+
+def _masked(prob, f):
+    out = np.zeros_like(f)
+    ib = prob.node_type != 0
+    out[:, ib] = f[:, ib]
+    return out
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-10)])
+def test_project_ib_matches_oracle(env, problems, precision, tol):
+    """Fixed number of passes (tol 0): every pass's force feeds the next (§2.3). The force given
+    for the first pass is used only at boundary/virtual nodes, so the GPU gets the workload's
+    whole field and the oracle its IB entries. The per-pass sums of the stopping rule are
+    compared relative to their size (they are differences of nearly equal forces late in the
+    iteration, so they carry the forces' error over the relative change)."""
+    pc, torch, dev = env
+    for k in IB_CASES:
+        prob, oplan, _ = problems[k]
+        ref = PR.project_ib(oplan, prob.dt, prob.u_star, _masked(prob, prob.f_ib), tol=0.0, max_iters=4)
+        assert ref["iterations"] == 4
+        plan = pc.Plan(prob, precision=precision)
+        u = torch.as_tensor(prob.u_star, device=dev)
+        f = torch.as_tensor(prob.f_ib, device=dev)
+        p, uo, fo, info = plan.project_ib(u, f, tol=0.0, max_iters=4)
+        assert info["iterations"] == 4 and not info["converged"]
+        for name, got, want in (("p", p, ref["p"]), ("u", uo, ref["u"]), ("f", fo, ref["f"])):
+            e = rel(got.cpu().numpy(), want)
+            assert e <= tol, (precision, k, name, e)
+        for (gd, gp), (rd, rp) in zip(info["history"], ref["history"]):
+            assert abs(gd - rd) <= 1e-7 * rd and abs(gp - rp) <= 1e-7 * rp, (k, gd, rd, gp, rp)
+        plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_project_ib_stops_like_oracle(env, problems, precision):
+    """The paper's tolerance 1e-3: the GPU stops after the same pass as the oracle (the case is
+    checked to be far from the threshold at every pass, so rounding cannot flip a decision)."""
+    pc, torch, dev = env
+    for k in IB_CASES:
+        prob, oplan, _ = problems[k]
+        ref = PR.project_ib(oplan, prob.dt, prob.u_star, tol=1e-3, max_iters=60)
+        ratios = [d / p for d, p in ref["history"] if p > 0]
+        assert all(abs(r / 1e-3 - 1.0) > 0.01 for r in ratios)
+        plan = pc.Plan(prob, precision=precision)
+        u = torch.as_tensor(prob.u_star, device=dev)
+        p, uo, fo, info = plan.project_ib(u, tol=1e-3, max_iters=60)
+        assert info["iterations"] == ref["iterations"] and info["converged"]
+        assert info["history"][0][1] == 0.0             # the first pass starts from zero force
+        assert rel(fo.cpu().numpy(), ref["f"]) <= 1e-9
+        plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_project_ib_equals_repeated_project(env, problems, precision):
+    """The incremental passes (IB-node prep, listed faces, IB-node gradient) give bitwise the
+    iterates of full pc_project passes fed with the previous force."""
+    pc, torch, dev = env
+    for k in IB_CASES:
+        prob, _, _ = problems[k]
+        plan = pc.Plan(prob, precision=precision)
+        u = torch.as_tensor(prob.u_star, device=dev)
+        f = torch.as_tensor(_masked(prob, prob.f_ib), device=dev)
+        for _ in range(3):
+            p, uo, f, _ = plan.project(u, f)
+            p, uo, f = p.clone(), uo.clone(), f.clone()
+        pi, ui, fi, info = plan.project_ib(u, f_init=torch.as_tensor(_masked(prob, prob.f_ib), device=dev),
+                                           tol=0.0, max_iters=3)
+        assert info["iterations"] == 3
+        assert torch.equal(pi, p) and torch.equal(ui, uo) and torch.equal(fi, f), (precision, k)
+        plan.close()
+
+
+def test_project_ib_without_ib_nodes(env, problems):
+    """No boundary/virtual nodes: one pass, converged (no force and no change), equal to
+    pc_project."""
+    pc, torch, dev = env
+    prob, _, _ = problems[0]
+    assert not np.any(prob.node_type != 0)
+    plan = pc.Plan(prob, precision="mixed")
+    u = torch.as_tensor(prob.u_star, device=dev)
+    p, uo, fo, _ = plan.project(u)
+    p, uo, fo = p.clone(), uo.clone(), fo.clone()
+    pi, ui, fi, info = plan.project_ib(u, tol=1e-3)
+    assert info["iterations"] == 1 and info["converged"] and info["history"] == [(0.0, 0.0)]
+    assert torch.equal(pi, p) and torch.equal(ui, uo) and torch.equal(fi, fo)
+    with pytest.raises(pc.PcError):
+        plan.project_ib(u.cpu(), tol=1e-3)              # device pointers only
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_project_ib_graph_equals_host_loop(env, problems, precision):
+    """The loop graph (while node, device-side stopping rule) and the host-driven loop run the
+    same passes: same pass count and history, bitwise outputs; a replay of the cached graph with
+    new input values gives the host loop's result too; max_iters bounds the graph's loop."""
+    pc, torch, dev = env
+    for k in IB_CASES:
+        prob, _, _ = problems[k]
+        plan = pc.Plan(prob, precision=precision)
+        u = torch.as_tensor(prob.u_star, device=dev)
+        outs = plan.alloc_outputs()
+        res = {}
+        for mode in (False, True):
+            plan.graphs(mode)
+            for scale in (1.0, 0.5):
+                u.copy_(torch.as_tensor(prob.u_star, device=dev) * scale)
+                p, uo, fo, info = plan.project_ib(u, tol=1e-3, max_iters=60, out=outs)
+                res[mode, scale] = ([t.clone() for t in (p, uo, fo)], info)
+        for scale in (1.0, 0.5):
+            (a, ia), (b, ib_) = res[False, scale], res[True, scale]
+            assert ia["iterations"] == ib_["iterations"] and ia["history"] == ib_["history"], (k, scale)
+            assert all(torch.equal(x, y) for x, y in zip(a, b)), (precision, k, scale)
+        for m in (1, 2):
+            _, _, _, info = plan.project_ib(u, tol=0.0, max_iters=m, out=outs)
+            assert info["iterations"] == m and not info["converged"]
+        plan.close()
