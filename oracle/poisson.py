@@ -19,6 +19,15 @@ The last two pairs put different homogeneous conditions at the two ends of one a
 §2.3 does not list (it asks for the same type on both ends); they are still diagonalised
 exactly by these bases and are used for an inflow/outflow channel.
 
+§2.3 allows two sets of eigenvalues with the same transforms: the central finite-difference
+ones above (the exact inverse of L_h), and the pseudo-spectral ones. Writing each FD eigenvalue
+as -(2/h)^2 sin^2(theta/2), theta = 2 pi k/n (periodic, k the wavenumber), pi k/n (N-N),
+pi (k+1)/n (D-D) or pi (k+1/2)/n (N-D, D-N), the pseudo-spectral eigenvalue of the same basis
+vector is -(theta/h)^2: the eigenvalue of the continuous second derivative for the continuous
+eigenfunction that the basis vector samples at the cell centres. The pseudo-spectral solve is
+defined by its expansion alone (its operator has no compact stencil), so it takes no
+refinement sweep; at the sizes where it is compared the expansion is at FP64 rounding.
+
 Zero mode: when every axis is periodic or Neumann-Neumann the summed eigenvalue of the
 constant mode is 0. Its source coefficient is the mean of s, which is dropped (the
 compatibility projection) and the solution gets no constant part (mean(p) = 0). An optional
@@ -43,8 +52,18 @@ def axis_kind(g, a):
     return lo + hi
 
 
-def eigenbasis(kind, n, h):
-    """(Phi, lam): Phi[:, k] is the k-th eigenvector of the 1D operator, lam[k] its eigenvalue."""
+def _lam(theta, h, eigenvalues):
+    """FD or pseudo-spectral eigenvalue of the basis vector with angle theta (§2.3)."""
+    if eigenvalues == "fd":
+        return -(4.0 / (h * h)) * np.sin(theta / 2.0) ** 2
+    if eigenvalues == "spectral":
+        return -(theta / h) ** 2
+    raise ValueError(eigenvalues)
+
+
+def eigenbasis(kind, n, h, eigenvalues="fd"):
+    """(Phi, lam): Phi[:, k] is the k-th eigenvector of the 1D operator, lam[k] its eigenvalue
+    (central finite-difference or pseudo-spectral, see the module header)."""
     j = np.arange(n, dtype=np.float64)[:, None]
     if kind == "PP":
         cols, wav = [np.ones(n)], [0]
@@ -56,24 +75,23 @@ def eigenbasis(kind, n, h):
             cols.append(np.cos(np.pi * j[:, 0]))
             wav.append(n // 2)
         Phi = np.stack(cols, axis=1)
-        lam = -(4.0 / (h * h)) * np.sin(np.pi * np.asarray(wav, dtype=np.float64) / n) ** 2
-        return Phi, lam
+        return Phi, _lam(2.0 * np.pi * np.asarray(wav, dtype=np.float64) / n, h, eigenvalues)
     k = np.arange(n, dtype=np.float64)[None, :]
     if kind == "NN":
         Phi = np.cos(np.pi * k * (j + 0.5) / n)
-        lam = -(4.0 / (h * h)) * np.sin(np.pi * k[0] / (2.0 * n)) ** 2
+        theta = np.pi * k[0] / n
     elif kind == "DD":
         Phi = np.sin(np.pi * (k + 1.0) * (j + 0.5) / n)
-        lam = -(4.0 / (h * h)) * np.sin(np.pi * (k[0] + 1.0) / (2.0 * n)) ** 2
+        theta = np.pi * (k[0] + 1.0) / n
     elif kind == "ND":
         Phi = np.cos(np.pi * (k + 0.5) * (j + 0.5) / n)
-        lam = -(4.0 / (h * h)) * np.sin(np.pi * (2.0 * k[0] + 1.0) / (4.0 * n)) ** 2
+        theta = np.pi * (k[0] + 0.5) / n
     elif kind == "DN":
         Phi = np.sin(np.pi * (k + 0.5) * (j + 0.5) / n)
-        lam = -(4.0 / (h * h)) * np.sin(np.pi * (2.0 * k[0] + 1.0) / (4.0 * n)) ** 2
+        theta = np.pi * (k[0] + 0.5) / n
     else:
         raise ValueError(kind)
-    return Phi, lam
+    return Phi, _lam(theta, h, eigenvalues)
 
 
 def _apply(M, x, a):
@@ -112,8 +130,9 @@ def _expand_solve(s, g, bases, singular):
     return p
 
 
-def solve(s, g, gauge="mean"):
-    """Return (p, removed_mean) with L_h p = s (s minus its mean when the problem is singular).
+def solve(s, g, gauge="mean", eigenvalues="fd"):
+    """Return (p, removed_mean) with L_h p = s (s minus its mean when the problem is singular);
+    with eigenvalues="spectral" the pseudo-spectral solve of the same source instead.
 
     removed_mean is the mean of s dropped by the compatibility projection (0 otherwise).
 
@@ -123,12 +142,13 @@ def solve(s, g, gauge="mean"):
     residual in double-double arithmetic (grid.residual_compensated), brings it to FP64
     rounding of the exact solution that the three-step algorithm defines."""
     s = np.asarray(s, dtype=np.float64).reshape(g.shape)
-    bases = [eigenbasis(axis_kind(g, a), g.n[a], g.h[a]) for a in range(g.dim)]
+    bases = [eigenbasis(axis_kind(g, a), g.n[a], g.h[a], eigenvalues) for a in range(g.dim)]
     singular = g.singular()
     removed = float(np.mean(s)) if singular else 0.0
     p = _expand_solve(s, g, bases, singular)
-    r = residual_compensated(s - removed if singular else s, p, g)
-    p = p + _expand_solve(r, g, bases, singular)
+    if eigenvalues == "fd":
+        r = residual_compensated(s - removed if singular else s, p, g)
+        p = p + _expand_solve(r, g, bases, singular)
     if singular and gauge == "corner":
         p = p - p[tuple([0] * g.dim)]
     return p, removed

@@ -143,7 +143,7 @@ def node_gradient(plan, p):
     return np.sum(plan.node_D * vals[None, :, :], axis=2)          # (d, N)
 
 
-def project(plan, dt, u_star, f_ib=None, beta=1.5, gauge="mean"):
+def project(plan, dt, u_star, f_ib=None, beta=1.5, gauge="mean", eigenvalues="fd"):
     """One pressure-correction pass. Returns a dict with p, u, f, U (faces), s, div_after, removed."""
     g = plan.grid
     u_star = np.asarray(u_star, dtype=np.float64).reshape(g.dim, -1)
@@ -153,7 +153,7 @@ def project(plan, dt, u_star, f_ib=None, beta=1.5, gauge="mean"):
         u_tilde = u_star + dt * np.asarray(f_ib, dtype=np.float64).reshape(g.dim, -1)
     U = transfer(plan, u_tilde)
     s = G.divergence(U, g) / (beta * dt)
-    p, removed = P.solve(s, g, gauge=gauge)
+    p, removed = P.solve(s, g, gauge=gauge, eigenvalues=eigenvalues)
     grad = node_gradient(plan, p)
     ib = plan.node_type != FLUID
     u_new = u_star - beta * dt * grad

@@ -226,3 +226,66 @@ def test_refined_solve_is_a_fixed_point(rng):
     bases = [P.eigenbasis(P.axis_kind(g, a), g.n[a], g.h[a]) for a in range(2)]
     d = P._expand_solve(G.residual_compensated(s, p, g), g, bases, False)
     assert np.linalg.norm(d) <= 1e-15 * np.linalg.norm(p)
+
+
+# ----------------------------------------------------------------------------- pseudo-spectral
+def _continuous_mode(kind, m, n, h):
+    """The continuous eigenfunction of d2/dx2 with the axis's boundary conditions, sampled at the
+    cell centres x = (j + 1/2) h, and its eigenvalue (independent of the grid)."""
+    L = n * h
+    x = (np.arange(n) + 0.5) * h
+    if kind == "PP":
+        k = 2.0 * np.pi * m / L
+        return np.cos(k * x + 0.3), -k * k
+    if kind == "NN":
+        k = np.pi * m / L
+        return np.cos(k * x), -k * k
+    if kind == "DD":
+        k = np.pi * m / L
+        return np.sin(k * x), -k * k
+    k = np.pi * (m + 0.5) / L
+    return (np.cos(k * x) if kind == "ND" else np.sin(k * x)), -k * k
+
+
+@pytest.mark.parametrize("kinds,n", [(("PP", "NN"), (24, 16)), (("DD", "ND"), (20, 12)),
+                                     (("DN", "PP"), (16, 18)), (("NN", "DD", "DN"), (8, 10, 12))])
+def test_spectral_solve_is_exact_on_continuous_modes(kinds, n):
+    """§2.3 pseudo-spectral eigenvalues: a product of sampled continuous eigenfunctions (each
+    resolvable on its axis) is solved exactly, p = s / (sum of continuous eigenvalues), and the
+    FD eigenvalues are not (second-order error)."""
+    letters = {"PP": ("P", "P"), "NN": ("W", "W"), "DD": ("D", "D"), "ND": ("I", "D"), "DN": ("D", "I")}
+    h = [0.1, 0.07, 0.05][:len(n)]
+    g = G.Grid(len(n), n, [0.0] * len(n), h, [letters[k][0] for k in kinds], [letters[k][1] for k in kinds])
+    rng = np.random.default_rng(31)
+    for _ in range(3):
+        s = np.ones(n)
+        lam = 0.0
+        for a, kind in enumerate(kinds):
+            m = int(rng.integers(1, n[a] // 2 - 1))
+            f, la = _continuous_mode(kind, m, n[a], h[a])
+            shape = [1] * len(n)
+            shape[a] = n[a]
+            s = s * f.reshape(shape)
+            lam += la
+        p, removed = P.solve(s, g, eigenvalues="spectral")
+        assert removed == pytest.approx(0.0, abs=1e-12)
+        np.testing.assert_allclose(p, s / lam, rtol=0, atol=1e-12 * np.abs(s / lam).max())
+        pfd, _ = P.solve(s, g)
+        assert np.abs(pfd - s / lam).max() > 1e-6 * np.abs(s / lam).max()
+
+
+def test_spectral_accuracy_on_smooth_periodic_function():
+    """p = exp(sin x) on [0, 2 pi): from s = p'' the pseudo-spectral solve recovers p - mean(p)
+    to rounding at n = 64, while the FD solve keeps its O(h^2) error."""
+    n = 64
+    h = 2.0 * np.pi / n
+    g = G.Grid(2, (n, 4), (0.0, 0.0), (h, 1.0), ("P", "P"), ("P", "P"))
+    x = (np.arange(n) + 0.5) * h
+    pe = np.exp(np.sin(x))
+    se = (np.cos(x) ** 2 - np.sin(x)) * pe
+    s = np.repeat(se[:, None], 4, axis=1)
+    ref = np.repeat((pe - pe.mean())[:, None], 4, axis=1)
+    p, _ = P.solve(s, g, eigenvalues="spectral")
+    assert np.abs(p - ref).max() <= 1e-12
+    pfd, _ = P.solve(s, g)
+    assert np.abs(pfd - ref).max() > 1e-4
