@@ -17,7 +17,8 @@ Steps, in the paper's order (§2.3, one pass of the IB-force iteration with a gi
    (2/(3 dt)) div u* + (2/3) div f~ = (1/(beta dt)) div(u* + dt f~) with beta = 3/2.
    Wall faces carry no flux (§3.3 workaround); inflow and Dirichlet faces keep the
    transferred flux (Eq. 7: u^{n+1}.n = u*.n at an inflow).
-3. Source s = D_h U / (beta dt); discrete solve L_h p = s (oracle.poisson).
+3. Source s = D_h U / (beta dt), set to zero outside an optional RHS mask (§3.5); discrete
+   solve L_h p = s (oracle.poisson; or the pseudo-spectral solve of the same source).
 4. Gradient of p at the nodes with the gradient rows, then (Eqs. 18-19)
      fluid node:             u^{n+1} = u* - beta dt grad p,          f~ = 0
      boundary/virtual node:  f~ = -u*/dt + beta grad p,              u^{n+1} = 0
@@ -143,8 +144,10 @@ def node_gradient(plan, p):
     return np.sum(plan.node_D * vals[None, :, :], axis=2)          # (d, N)
 
 
-def project(plan, dt, u_star, f_ib=None, beta=1.5, gauge="mean", eigenvalues="fd"):
-    """One pressure-correction pass. Returns a dict with p, u, f, U (faces), s, div_after, removed."""
+def project(plan, dt, u_star, f_ib=None, beta=1.5, gauge="mean", eigenvalues="fd", rhs_mask=None):
+    """One pressure-correction pass. Returns a dict with p, u, f, U (faces), s, div_after, removed.
+    rhs_mask (cells, nonzero = flow domain): the source is set to zero outside it before the
+    solve (§3.5, the polar cavity's source/sink term outside the flow domain)."""
     g = plan.grid
     u_star = np.asarray(u_star, dtype=np.float64).reshape(g.dim, -1)
     if f_ib is None:
@@ -153,6 +156,8 @@ def project(plan, dt, u_star, f_ib=None, beta=1.5, gauge="mean", eigenvalues="fd
         u_tilde = u_star + dt * np.asarray(f_ib, dtype=np.float64).reshape(g.dim, -1)
     U = transfer(plan, u_tilde)
     s = G.divergence(U, g) / (beta * dt)
+    if rhs_mask is not None:
+        s = np.where(np.asarray(rhs_mask).reshape(g.shape) != 0, s, 0.0)
     p, removed = P.solve(s, g, gauge=gauge, eigenvalues=eigenvalues)
     grad = node_gradient(plan, p)
     ib = plan.node_type != FLUID
@@ -185,7 +190,8 @@ def ib_converged(diff, prev, tol):
     return diff == 0.0 if prev == 0.0 else diff <= tol * prev
 
 
-def project_ib(plan, dt, u_star, f_init=None, tol=1e-3, max_iters=50, beta=1.5, gauge="mean"):
+def project_ib(plan, dt, u_star, f_init=None, tol=1e-3, max_iters=50, beta=1.5, gauge="mean",
+               eigenvalues="fd", rhs_mask=None):
     """The IB-force iteration of §2.3 around the pressure correction: solve the modified PPE
     (Eq. 20) with the current force, update the force at the boundary and virtual points by
     Eq. 19 from the new pressure gradient, and repeat until ib_converged (or max_iters). The
@@ -197,7 +203,7 @@ def project_ib(plan, dt, u_star, f_init=None, tol=1e-3, max_iters=50, beta=1.5, 
     hist = []
     out = None
     for it in range(1, max_iters + 1):
-        out = project(plan, dt, u_star, f, beta=beta, gauge=gauge)
+        out = project(plan, dt, u_star, f, beta=beta, gauge=gauge, eigenvalues=eigenvalues, rhs_mask=rhs_mask)
         diff, prev = ib_change(out["f"], f, plan.node_type)
         hist.append((diff, prev))
         f = out["f"]

@@ -227,3 +227,26 @@ def test_ib_stopping_rule():
     fo = np.array([[0.0, 0.0, 0.0, 0.0], [0.0, 4.0, 0.0, 0.0]])
     d, p = PR.ib_change(fn, fo, t)
     assert d == pytest.approx((9.0 + 1.0) / 2) and p == pytest.approx(16.0 / 2)
+
+
+def test_rhs_mask_invariants():
+    """§3.5 RHS mask: with the source zeroed outside the flow domain, the corrected face flux has
+    D_h U_new = beta dt (s (1 - mask) + removed mean): zero divergence (minus the compatibility
+    constant) inside, the dropped source outside. An all-ones mask changes nothing."""
+    for case in (dict(dim=2, n=(24, 20), bc_lo=("W", "W"), bc_hi=("W", "W"), obstacles=[("circle", (0.7, 0.6), 0.2)]),
+                 dict(dim=2, n=(32, 16), bc_lo=("I", "W"), bc_hi=("D", "W"), obstacles=[("circle", (0.8, 0.5), 0.15)]),
+                 dict(dim=3, n=(8, 8, 10), bc_lo=("W", "W", "I"), bc_hi=("W", "W", "D"))):
+        prob = wl.generic(seed=41, with_force=True, **case)
+        g = G.Grid(prob.dim, prob.n, prob.lo, prob.h, prob.bc_lo, prob.bc_hi)
+        pl = PR.build_plan(g, prob.nodes, prob.node_type, K=prob.knn)
+        rng = np.random.default_rng(5)
+        mask = (rng.random(g.shape) > 0.3).astype(np.uint8)
+        full = PR.project(pl, prob.dt, prob.u_star, prob.f_ib)
+        out = PR.project(pl, prob.dt, prob.u_star, prob.f_ib, rhs_mask=mask)
+        bdt = prob.beta * prob.dt
+        expect = bdt * (full["s"] * (1 - mask) + out["removed"])
+        scale = bdt * np.abs(full["s"]).max()
+        assert np.abs(out["div_after"] - expect).max() <= 1e-11 * scale
+        assert np.abs(out["p"] - full["p"]).max() > 1e-6 * np.abs(full["p"]).max()
+        ones = PR.project(pl, prob.dt, prob.u_star, prob.f_ib, rhs_mask=np.ones(g.shape, np.uint8))
+        assert np.array_equal(ones["p"], full["p"]) and np.array_equal(ones["u"], full["u"])
