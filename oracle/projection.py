@@ -18,7 +18,9 @@ Steps, in the paper's order (§2.3, one pass of the IB-force iteration with a gi
    Wall faces carry no flux (§3.3 workaround); inflow and Dirichlet faces keep the
    transferred flux (Eq. 7: u^{n+1}.n = u*.n at an inflow).
 3. Source s = D_h U / (beta dt), set to zero outside an optional RHS mask (§3.5); discrete
-   solve L_h p = s (oracle.poisson; or the pseudo-spectral solve of the same source).
+   solve L_h p = s (oracle.poisson; or the pseudo-spectral solve of the same source). The
+   paper's own variant takes s from WLS derivative rows at the cell centres over the K nearest
+   nodes (div_mode "wls_direct"), without face fluxes.
 4. Gradient of p at the nodes with the gradient rows, then (Eqs. 18-19)
      fluid node:             u^{n+1} = u* - beta dt grad p,          f~ = 0
      boundary/virtual node:  f~ = -u*/dt + beta grad p,              u^{n+1} = 0
@@ -58,6 +60,8 @@ class Plan:
     face_w: list                # per axis: (num_faces, K) value-row weights (0 on wall faces)
     node_col: np.ndarray        # (N, 3^d) cell linear indices of the gradient block
     node_D: np.ndarray          # (d, N, 3^d) derivative-row weights
+    cell_col: np.ndarray = None  # (cells, K) node indices of the direct-divergence rows
+    cell_D: np.ndarray = None    # (d, cells, K) derivative-row weights at the cell centres
 
 
 def _box(g):
@@ -128,6 +132,35 @@ def gradient_block(g, pts):
     return idx
 
 
+def cell_rows(plan, chunk=200000):
+    """Derivative rows at every cell centre over its K nearest nodes (§2.2 rows at the pressure
+    points, for the paper's own divergence of u~ at the pressure points, §2.3). Built on first
+    use and kept on the plan."""
+    if plan.cell_col is None:
+        g = plan.grid
+        pts = plan.nodes.T.copy()
+        lo, lengths, periodic = _box(g)
+        cp = g.cell_points()
+        idx, _ = KNN.knn(pts, cp, plan.K, lo, lengths, periodic)
+        D = np.empty((g.dim,) + idx.shape)
+        for s0 in range(0, cp.shape[0], chunk):
+            s1 = min(s0 + chunk, cp.shape[0])
+            _, grad = _wls_block(pts, cp[s0:s1], idx[s0:s1], g, plan.eps, plan.support_factor)
+            D[:, s0:s1, :] = np.transpose(grad, (1, 0, 2))
+        plan.cell_col, plan.cell_D = idx, D
+    return plan.cell_col, plan.cell_D
+
+
+def direct_divergence(plan, u_tilde):
+    """div u~ at the cell centres from the WLS derivative rows: sum_a sum_k D_a,k u~_a,k."""
+    col, D = cell_rows(plan)
+    g = plan.grid
+    div = np.zeros(col.shape[0])
+    for a in range(g.dim):
+        div += np.sum(D[a] * u_tilde[a][col], axis=1)
+    return div.reshape(g.shape)
+
+
 def transfer(plan, u_tilde):
     """Face fluxes U_a = sum_k w_k u~_{a,k} (value rows), wall faces 0."""
     g = plan.grid
@@ -144,18 +177,27 @@ def node_gradient(plan, p):
     return np.sum(plan.node_D * vals[None, :, :], axis=2)          # (d, N)
 
 
-def project(plan, dt, u_star, f_ib=None, beta=1.5, gauge="mean", eigenvalues="fd", rhs_mask=None):
+def project(plan, dt, u_star, f_ib=None, beta=1.5, gauge="mean", eigenvalues="fd", rhs_mask=None,
+            div_mode="faces"):
     """One pressure-correction pass. Returns a dict with p, u, f, U (faces), s, div_after, removed.
     rhs_mask (cells, nonzero = flow domain): the source is set to zero outside it before the
-    solve (§3.5, the polar cavity's source/sink term outside the flow domain)."""
+    solve (§3.5, the polar cavity's source/sink term outside the flow domain).
+    div_mode "faces": s from the compact divergence of the WLS face fluxes; "wls_direct": s
+    from WLS derivative rows at the cell centres (§2.3 as printed), with U and div_after None."""
     g = plan.grid
     u_star = np.asarray(u_star, dtype=np.float64).reshape(g.dim, -1)
     if f_ib is None:
         u_tilde = u_star
     else:
         u_tilde = u_star + dt * np.asarray(f_ib, dtype=np.float64).reshape(g.dim, -1)
-    U = transfer(plan, u_tilde)
-    s = G.divergence(U, g) / (beta * dt)
+    if div_mode == "faces":
+        U = transfer(plan, u_tilde)
+        s = G.divergence(U, g) / (beta * dt)
+    elif div_mode == "wls_direct":
+        U = None
+        s = direct_divergence(plan, u_tilde) / (beta * dt)
+    else:
+        raise ValueError(div_mode)
     if rhs_mask is not None:
         s = np.where(np.asarray(rhs_mask).reshape(g.shape) != 0, s, 0.0)
     p, removed = P.solve(s, g, gauge=gauge, eigenvalues=eigenvalues)
@@ -165,10 +207,12 @@ def project(plan, dt, u_star, f_ib=None, beta=1.5, gauge="mean", eigenvalues="fd
     u_new[:, ib] = 0.0
     f_new = np.zeros_like(u_star)
     f_new[:, ib] = -u_star[:, ib] / dt + beta * grad[:, ib]
-    U_new = [U[a] - beta * dt * G.face_gradient(p, g, a) for a in range(g.dim)]
-    for a in range(g.dim):
-        U_new[a][g.face_is_wall(a)] = 0.0
-    div_after = G.divergence(U_new, g)
+    U_new, div_after = None, None
+    if U is not None:
+        U_new = [U[a] - beta * dt * G.face_gradient(p, g, a) for a in range(g.dim)]
+        for a in range(g.dim):
+            U_new[a][g.face_is_wall(a)] = 0.0
+        div_after = G.divergence(U_new, g)
     return dict(p=p, u=u_new, f=f_new, U=U, s=s, grad=grad, U_new=U_new,
                 div_after=div_after, removed=removed)
 
@@ -191,7 +235,7 @@ def ib_converged(diff, prev, tol):
 
 
 def project_ib(plan, dt, u_star, f_init=None, tol=1e-3, max_iters=50, beta=1.5, gauge="mean",
-               eigenvalues="fd", rhs_mask=None):
+               eigenvalues="fd", rhs_mask=None, div_mode="faces"):
     """The IB-force iteration of §2.3 around the pressure correction: solve the modified PPE
     (Eq. 20) with the current force, update the force at the boundary and virtual points by
     Eq. 19 from the new pressure gradient, and repeat until ib_converged (or max_iters). The
@@ -203,7 +247,8 @@ def project_ib(plan, dt, u_star, f_init=None, tol=1e-3, max_iters=50, beta=1.5, 
     hist = []
     out = None
     for it in range(1, max_iters + 1):
-        out = project(plan, dt, u_star, f, beta=beta, gauge=gauge, eigenvalues=eigenvalues, rhs_mask=rhs_mask)
+        out = project(plan, dt, u_star, f, beta=beta, gauge=gauge, eigenvalues=eigenvalues, rhs_mask=rhs_mask,
+                      div_mode=div_mode)
         diff, prev = ib_change(out["f"], f, plan.node_type)
         hist.append((diff, prev))
         f = out["f"]
