@@ -63,6 +63,23 @@ typedef enum {
 
 typedef enum { PC_DTYPE_F64 = 0, PC_DTYPE_F32 = 1 } pc_dtype;
 
+/* Eigenvalues of the transform solve (§2.3 allows both with the same transforms). With the
+ * angle theta of a basis vector (2 pi k/n periodic, pi k/n N-N, pi (k+1)/n D-D, pi (k+1/2)/n
+ * N-D and D-N): central finite differences -(2/h)^2 sin^2(theta/2), the exact inverse of the
+ * 2d+1-point Laplacian; pseudo-spectral -(theta/h)^2, the continuous eigenvalue of the function
+ * the basis vector samples. */
+typedef enum { PC_EIG_FD = 0, PC_EIG_SPECTRAL = 1 } pc_eigenvalues;
+
+/* Where the source of the PPE comes from. PC_DIV_FACES: WLS value rows transfer u~ to the MAC
+ * faces and s is their compact divergence D_h U / (beta dt), so the corrected face flux is
+ * divergence-free to rounding. PC_DIV_WLS_DIRECT: s = sum_a sum_k D_a,k u~_a,k / (beta dt) with
+ * WLS derivative rows at every cell centre over its K nearest nodes (the paper's evaluation of
+ * the right-hand side at the pressure points, §2.3); no face fluxes are formed, so max_div_after
+ * of pc_stats is not computed (0). The plan then holds K (index) + dim*K (weights) entries more
+ * per cell; pc_project_ib recomputes the whole source on every pass and pc_project_batch runs
+ * such plans one by one. */
+typedef enum { PC_DIV_FACES = 0, PC_DIV_WLS_DIRECT = 1 } pc_divergence;
+
 /* Node kinds of the double discretization (§2.3, Fig. 1). */
 typedef enum { PC_NODE_FLUID = 0, PC_NODE_BOUNDARY = 1, PC_NODE_VIRTUAL = 2 } pc_node_type;
 
@@ -96,6 +113,12 @@ typedef struct {
                                when no face is Dirichlet (the solution is then defined up to
                                a constant) */
   int velocity_dtype;       /* pc_dtype of u_star, f_ib_in, u_out, f_ib_out */
+  int eigenvalues;          /* pc_eigenvalues. PC_EIG_SPECTRAL needs precision FP64 or FP32
+                               (PC_ERR_UNSUPPORTED with MIXED: the refinement residual applies
+                               the compact L_h, which is the inverse of the FD eigenvalues only);
+                               its solve is not the inverse of L_h, so max_div_after and the
+                               residual norms of pc_stats do not apply (reported as 0 residuals) */
+  int divergence;           /* pc_divergence */
 } pc_problem_desc;
 
 /* Per-call diagnostics (optional). Filling it synchronizes the stream. */
@@ -204,6 +227,18 @@ pc_status pc_batcher_launch(pc_batcher *batcher, int count, pc_plan *const *plan
                             const pc_project_args *args, void *cuda_stream);
 pc_status pc_batcher_destroy(pc_batcher *batcher);
 
+/* RHS mask (§3.5, lid-driven polar cavity: the source is turned to zero at pressure points
+ * outside the flow domain, where part of the solid moves). mask: [cells] uint8 in C order
+ * (device or host), nonzero = inside the flow domain. Projections of this plan instance
+ * (pc_project, pc_project_ib, the batched calls) then set s = 0 at masked-out cells before the
+ * compatibility step and the solve; after the correction the face divergence vanishes inside
+ * the mask and equals beta dt times the dropped source outside it, so max_div_after of pc_stats
+ * is taken over the cells inside. The mask is copied into plan memory (1 byte per cell,
+ * allocated on the first call; the call waits for the copy). NULL clears it. Switching between
+ * masked and unmasked drops the plan's captured CUDA graphs; changing the mask's content does
+ * not need to. pc_solve_poisson takes its source as given (no mask). A clone starts unmasked. */
+pc_status pc_plan_set_rhs_mask(pc_plan *plan, const uint8_t *mask, void *cuda_stream);
+
 /* The grid-level Poisson solve alone (§2.3 three-step algorithm): L_h p = s, cells in FP64,
  * with the plan's precision, refinement and gauge. */
 pc_status pc_solve_poisson(pc_plan *plan, const double *s, double *p_out, pc_stats *stats,
@@ -232,7 +267,9 @@ pc_status pc_solve_poisson_static(int dim, const int64_t *n, const double *h, co
 
 /* WLS rows of a plan, for inspection and tests. which = 0..dim-1: value rows of the faces
  * normal to that axis (rows = faces in C order of that face array); which = dim: derivative
- * rows of the nodes (rows = nodes, weights [dim][rows][K]). col_out: [rows][K] int32 (node
+ * rows of the nodes (rows = nodes, weights [dim][rows][K]); which = dim+1 (PC_DIV_WLS_DIRECT
+ * plans only): derivative rows of the cell centres (rows = cells in C order, columns node
+ * indices, weights [dim][rows][K]). col_out: [rows][K] int32 (node
  * index for faces, cell linear index for nodes), w_out: FP64 host buffers. rows_out gets the
  * row count; pass NULL buffers to query it. FP64 plans return the FP64 weights; MIXED and FP32
  * plans keep only the FP32 (hi, lo) pairs after setup (the FP64 weights are setup temporaries)

@@ -211,6 +211,13 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
   if (d->gauge != 0 && d->gauge != 1) return fail(PC_ERR_INVALID_ARG, "gauge must be 0 or 1");
   if (d->velocity_dtype != PC_DTYPE_F64 && d->velocity_dtype != PC_DTYPE_F32)
     return fail(PC_ERR_INVALID_ARG, "bad velocity_dtype");
+  if (d->divergence != PC_DIV_FACES && d->divergence != PC_DIV_WLS_DIRECT)
+    return fail(PC_ERR_INVALID_ARG, "divergence must be PC_DIV_FACES or PC_DIV_WLS_DIRECT");
+  if (d->eigenvalues != PC_EIG_FD && d->eigenvalues != PC_EIG_SPECTRAL)
+    return fail(PC_ERR_INVALID_ARG, "eigenvalues must be PC_EIG_FD or PC_EIG_SPECTRAL");
+  if (d->eigenvalues == PC_EIG_SPECTRAL && d->precision == PC_PREC_MIXED)
+    return fail(PC_ERR_UNSUPPORTED, "pseudo-spectral eigenvalues need precision FP64 or FP32 (the mixed "
+                                    "refinement residual is that of the finite-difference operator)");
   long long ncells = 1;
   for (int a = 0; a < d->dim; ++a) {
     if (d->n[a] < 4 || d->n[a] > 4096) return fail(PC_ERR_INVALID_ARG, "n[%d] must be in [4, 4096]", a);
@@ -246,6 +253,8 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
   p->refine_iters = d->refine_iters;
   p->gauge = d->gauge;
   p->vdtype = d->velocity_dtype;
+  p->eigen = d->eigenvalues;
+  p->divmode = d->divergence;
   p->ncells = ncells;
   p->singular = true;
   for (int a = 0; a < 3; ++a) {
@@ -286,6 +295,7 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
   need += (size_t)nc * (8 + 8 + 4 + (mixed ? 8 : 0) + 8 + 8);
   need += (size_t)dd * N * 8;
   need += (size_t)dd * N * 8;                             // node coordinates (setup only)
+  if (p->divmode == PC_DIV_WLS_DIRECT) need += (size_t)nc * K * (4 + dd * 8);   // cell rows
   if (budget && need > budget)
     return bail(fail(PC_ERR_BUDGET, "plan needs %zu bytes, budget is %zu", need, budget));
 
@@ -301,6 +311,11 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
       (!mixed && plan_alloc(p, (void **)&p->nD64, dd * N * Kg * 8) != PC_OK) ||
       (mixed && plan_alloc(p, (void **)&p->nD2, dd * N * Kg * 8) != PC_OK) ||
       plan_alloc(p, (void **)&p->ntype, N) != PC_OK)
+    return bail(PC_ERR_OUT_OF_MEMORY);
+  if (p->divmode == PC_DIV_WLS_DIRECT &&
+      (plan_alloc(p, (void **)&p->ccol, nc * K * 4) != PC_OK ||
+       (!mixed && plan_alloc(p, (void **)&p->cD64, dd * nc * K * 8) != PC_OK) ||
+       (mixed && plan_alloc(p, (void **)&p->cD2, dd * nc * K * 8) != PC_OK)))
     return bail(PC_ERR_OUT_OF_MEMORY);
   {
     pc_status ws = alloc_workspace(p, st);
@@ -381,6 +396,8 @@ extern "C" pc_status pc_plan_clone(pc_plan *plan, void *cuda_stream, pc_plan **o
   p->eps = root->eps; p->support_factor = root->support_factor; p->beta = root->beta;
   p->precision = root->precision; p->refine_iters = root->refine_iters; p->gauge = root->gauge;
   p->vdtype = root->vdtype; p->singular = root->singular; p->ncells = root->ncells;
+  p->eigen = root->eigen;
+  p->divmode = root->divmode; p->ccol = root->ccol; p->cD64 = root->cD64; p->cD2 = root->cD2;
   p->ncol = root->ncol; p->nD64 = root->nD64; p->nD2 = root->nD2; p->ntype = root->ntype;
   p->graphs_on = root->graphs_on;
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -456,28 +473,31 @@ extern "C" pc_status pc_plan_rows(const pc_plan *plan, int which, int64_t *rows_
                                   double *w_out) {
   const pc::Plan *p = reinterpret_cast<const pc::Plan *>(plan);
   if (!p || !rows_out) return pc::fail(PC_ERR_INVALID_ARG, "plan and rows_out are required");
-  if (which < 0 || which > p->dim) return pc::fail(PC_ERR_INVALID_ARG, "which must be in [0, dim]");
+  if (which < 0 || which > p->dim + 1) return pc::fail(PC_ERR_INVALID_ARG, "which must be in [0, dim + 1]");
+  if (which == p->dim + 1 && p->divmode != PC_DIV_WLS_DIRECT)
+    return pc::fail(PC_ERR_INVALID_ARG, "cell rows exist only in PC_DIV_WLS_DIRECT plans");
   if (cudaSetDevice(p->device) != cudaSuccess) return pc::fail(PC_ERR_CUDA, "cannot select device");
-  const long long K = which < p->dim ? p->K : p->Kg;
-  long long rows = which < p->dim ? p->nface_total[which] : p->N;
+  const bool face = which < p->dim, cell = which == p->dim + 1;
+  const long long K = (face || cell) ? p->K : p->Kg;
+  long long rows = face ? p->nface_total[which] : (cell ? p->ncells : p->N);
   *rows_out = rows;
   if (!col_out && !w_out) return PC_OK;
   // stored neighbour-rank major on the device; returned row major
   std::vector<int32_t> c(rows * K);
-  std::vector<double> w((which < p->dim ? 1 : p->dim) * rows * K);
-  const int32_t *dc = which < p->dim ? p->fcol[which] : p->ncol;
-  const double *dw = which < p->dim ? p->fw64[which] : p->nD64;
+  std::vector<double> w((face ? 1 : p->dim) * rows * K);
+  const int32_t *dc = face ? p->fcol[which] : (cell ? p->ccol : p->ncol);
+  const double *dw = face ? p->fw64[which] : (cell ? p->cD64 : p->nD64);
   PC_CUDA_TRY(cudaMemcpy(c.data(), dc, c.size() * 4, cudaMemcpyDeviceToHost));
   if (dw) {
     PC_CUDA_TRY(cudaMemcpy(w.data(), dw, w.size() * 8, cudaMemcpyDeviceToHost));
   } else {
     // MIXED / FP32 plans keep the weights as FP32 (hi, lo) pairs only
-    const float2 *d2 = which < p->dim ? p->fw2[which] : p->nD2;
+    const float2 *d2 = face ? p->fw2[which] : (cell ? p->cD2 : p->nD2);
     std::vector<float2> w2(w.size());
     PC_CUDA_TRY(cudaMemcpy(w2.data(), d2, w2.size() * sizeof(float2), cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < w.size(); ++i) w[i] = (double)w2[i].x + (double)w2[i].y;
   }
-  const long long nw = which < p->dim ? 1 : p->dim;
+  const long long nw = face ? 1 : p->dim;
   for (long long r = 0; r < rows; ++r)
     for (long long k = 0; k < K; ++k) {
       if (col_out) col_out[r * K + k] = c[k * rows + r];

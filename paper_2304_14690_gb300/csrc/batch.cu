@@ -8,7 +8,8 @@
 // pass arguments and (problem, tile) work items. The whole sequence is captured once per batch
 // composition into a CUDA graph and replayed. Each problem keeps the block decomposition of its
 // single-problem launches, so batch results are bitwise those of separate pc_project calls.
-// Plans in FP64 precision run one by one through pc_project.
+// Plans in FP64 precision, and plans with the direct WLS divergence, run one by one through
+// pc_project.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -111,7 +112,9 @@ pc_status upload(Exec *e, T **dptr, const std::vector<T> &host) {
   return PC_OK;
 }
 
-bool batchable(const Plan *p) { return p->precision == PC_PREC_MIXED || p->precision == PC_PREC_FP32; }
+bool batchable(const Plan *p) {
+  return (p->precision == PC_PREC_MIXED || p->precision == PC_PREC_FP32) && p->divmode == PC_DIV_FACES;
+}
 
 pc_status build_group(Exec *e, Group &g) {
   const int n = (int)g.members.size();

@@ -170,6 +170,13 @@ struct Plan {
   int clones = 0;
   // CUDA graphs of pc_project (on by default for device pointers without statistics)
   bool graphs_on = true;
+  int eigen = PC_EIG_FD;       // pc_eigenvalues of the transform solve
+  uint8_t *rhs_mask = nullptr; // pc_plan_set_rhs_mask: plan copy of the mask (cells)
+  int divmode = PC_DIV_FACES;  // pc_divergence
+  int32_t *ccol = nullptr;     // direct divergence: [K][cells] node index
+  double *cD64 = nullptr;      //   [dim][K][cells] derivative-row weights (FP64 plans)
+  float2 *cD2 = nullptr;       //   (hi, lo) pairs (mixed and FP32 plans)
+  bool rhs_mask_on = false;
   cudaStream_t cap_stream = nullptr;
   GraphEntry graphs[kGraphCache];
   unsigned long long graph_clock = 0;
@@ -252,6 +259,7 @@ struct GridDev {
   // cell tiles of the cell kernels (project.cu): rows of the last axis, tile width 2^tw_bits,
   // 2^th_bits thread rows of cr rows each, gx tiles along the last axis, nblk blocks
   int rows, tw_bits, th_bits, cr, gx, nblk;
+  const uint8_t *mask;          // RHS mask per cell (nonzero = flow domain), nullptr = none
 };
 
 // Per-problem parameters of a batched launch (device array, one entry per problem).

@@ -273,7 +273,8 @@ pc_status build_axis_tables(Plan *p) {
     for (int k = 0; k < M; ++k) put(tw_dct4post(M), k, -pi * k / (double)n);
     std::vector<float2> tw32(tw.size());
     for (size_t i = 0; i < tw.size(); ++i) tw32[i] = make_float2((float)tw[i].x, (float)tw[i].y);
-    // eigenvalues per spectral index, -(4/h^2) sin^2(theta/2) with the angle of each basis
+    // eigenvalues per spectral index with the angle theta of each basis vector (th = theta/2):
+    // central finite differences -(4/h^2) sin^2(theta/2), pseudo-spectral -(theta/h)^2
     std::vector<double> lam(n);
     std::vector<float> lam32(n);
     const double c = -4.0 / (ax.h * ax.h);
@@ -290,7 +291,7 @@ pc_status build_axis_tables(Plan *p) {
         default: th = pi * (2.0 * m + 1.0) / (4.0 * n); break;
       }
       double s = std::sin(th);
-      lam[m] = c * s * s;
+      lam[m] = p->eigen == PC_EIG_SPECTRAL ? -(2.0 * th / ax.h) * (2.0 * th / ax.h) : c * s * s;
       lam32[m] = (float)lam[m];
     }
     PC_TRY(plan_alloc(p, (void **)&ax.tw64, tw.size() * sizeof(double2)));

@@ -382,6 +382,7 @@ __device__ __forceinline__ void divergence_body(unsigned b, const GridDev &g, co
         v = (a == 0) ? d * c[0] : fma(d, c[a], v);
       }
       const int ci = cell_index(g, i);
+      if (g.mask && !g.mask[ci]) v = 0.0;   // outside the flow domain (RHS mask)
       if (s2) s2[ci] = as_pair(v);     // the refinement keeps s as a (hi, lo) pair
       else s[ci] = v;
       if (s32) s32[ci] = d2f_rz_bits(v);   // FP32 copy read by the first FP32 transform pass
@@ -403,6 +404,51 @@ __global__ void divergence_kernel(GridDev g, const double *U0, const double *U1,
   pdl_enter();
   divergence_body<DIM>(blockIdx.x, g, U0, U1, U2, inv_bdt, s, s2, s32, stats, partials, counter, want_sums,
                        inv_ncells);
+}
+
+// Direct divergence (PC_DIV_WLS_DIRECT): s = (1/(beta dt)) sum_a sum_k D_a,k u~_a,k at every
+// cell centre from the cell derivative rows ([K][cells] columns, [dim][K][cells] weights), one
+// cell per thread, FP64 (u~ in ut64) or compensated FP32 (pairs of weights and u~). Zero outside
+// the RHS mask; the same outputs and sums as the face divergence.
+template <int DIM, bool MIXED>
+__global__ void direct_div_kernel(int nc, int K, const int32_t *__restrict__ col, const double *__restrict__ D,
+                                  const float2 *__restrict__ D2, const double *__restrict__ ut64,
+                                  const float2 *__restrict__ u2, int N, double inv_bdt, const uint8_t *__restrict__ mask,
+                                  double *s, float2 *s2, float *s32, DevStats *stats, double *partials,
+                                  unsigned int *counter, int want_sums, double inv_ncells) {
+  pdl_enter();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (c < nc) {
+    if (MIXED) {
+      DF acc{0.f, 0.f};
+      for (int k = 0; k < K; ++k) {
+        const int j = __ldg(col + (long long)k * nc + c);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+          df_acc(acc, __ldg(D2 + ((long long)a * K + k) * nc + c), __ldg(u2 + (long long)a * N + j));
+      }
+      v = df_value(acc) * inv_bdt;
+    } else {
+      double acc = 0.0;
+      for (int k = 0; k < K; ++k) {
+        const int j = __ldg(col + (long long)k * nc + c);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+          acc = fma(__ldg(D + ((long long)a * K + k) * nc + c), __ldg(ut64 + (long long)a * N + j), acc);
+      }
+      v = acc * inv_bdt;
+    }
+    if (mask && !mask[c]) v = 0.0;
+    if (s2) s2[c] = as_pair(v);
+    else s[c] = v;
+    if (s32) s32[c] = d2f_rz_bits(v);
+  }
+  if (want_sums) {
+    const VBlock vb = hw_block();
+    if (grid_sum(v, partials, counter, &stats->sum_s, vb)) stats->mean_s = stats->sum_s * inv_ncells;
+    if (want_sums > 1) grid_sum(v * v, partials + gridDim.x, counter + 1, &stats->sum_s2, vb);
+  }
 }
 
 // ----------------------------------------------------------------------------- flat kernels
@@ -659,7 +705,8 @@ __global__ void gradient_mixed_kernel(int N, int K, const int32_t *__restrict__ 
 }
 
 // ----------------------------------------------------------------------------- check
-// max over cells of |D_h (U - beta dt G_h p)|; wall faces carry no flux and no gradient.
+// max over cells of |D_h (U - beta dt G_h p)|; wall faces carry no flux and no gradient. Cells
+// outside the RHS mask are skipped.
 template <int DIM>
 __global__ void div_check_kernel(GridDev g, const double *U0, const double *U1,
                                  const double *U2, const double *p, double bdt, DevStats *stats) {
@@ -674,6 +721,7 @@ __global__ void div_check_kernel(GridDev g, const double *U0, const double *U1,
       int i[3];
       cell_at<DIM>(g, row, x, i);
       const int c = cell_index(g, i);
+      if (g.mask && !g.mask[c]) continue;   // the source was zeroed there on purpose
       const double pc = p[c];
       double acc = 0.0;
 #pragma unroll
@@ -1002,6 +1050,7 @@ void batch_problem_fill(const Plan *p, const pc_project_args &a, BatchProblem &q
 static GridDev grid_dev(const Plan *p) {
   GridDev g{};
   g.dim = p->dim;
+  g.mask = p->rhs_mask_on ? p->rhs_mask : nullptr;
   for (int a = 0; a < 3; ++a) {
     if (a < p->dim) {
       const AxisInfo &ax = p->ax[a];
@@ -1114,7 +1163,7 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
       prof_mark(p, st, 3);
     }
   }
-  if (want_final_residual) {
+  if (want_final_residual && p->eigen == PC_EIG_FD) {   // the residual of L_h: FD solves only
     int it = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
     if (p->precision == PC_PREC_FP64)
       launch_residual(p->singular, false, true, st, g, s64, (const double *)pout, (float *)nullptr, p->dstats,
@@ -1191,6 +1240,24 @@ static void launch_gradient(Plan *p, cudaStream_t st, const double *dp, const vo
   }
 }
 
+// Source of the direct-divergence mode into the same buffers as the face divergence.
+static void launch_direct_div(Plan *p, cudaStream_t st, double inv_bdt, int want_sums) {
+  const bool mixed = p->precision != PC_PREC_FP64;
+  const int nc = (int)p->ncells, T = 256, G = grid_for(nc, T);
+  const GridDev g = grid_dev(p);
+  double *s = mixed ? nullptr : p->s64;
+  float2 *s2 = mixed ? reinterpret_cast<float2 *>(p->s64) : nullptr;
+  float *s32 = mixed ? reinterpret_cast<float *>(p->work64) : nullptr;
+  const double inc = 1.0 / (double)nc;
+  if (p->dim == 2) {
+    if (mixed) launch_pdl(direct_div_kernel<2, true>, G, T, 0, st, nc, p->K, p->ccol, p->cD64, p->cD2, p->ut64, p->u2, (int)p->N, inv_bdt, g.mask, s, s2, s32, p->dstats, p->partials, p->counters, want_sums, inc);
+    else launch_pdl(direct_div_kernel<2, false>, G, T, 0, st, nc, p->K, p->ccol, p->cD64, p->cD2, p->ut64, p->u2, (int)p->N, inv_bdt, g.mask, s, s2, s32, p->dstats, p->partials, p->counters, want_sums, inc);
+  } else {
+    if (mixed) launch_pdl(direct_div_kernel<3, true>, G, T, 0, st, nc, p->K, p->ccol, p->cD64, p->cD2, p->ut64, p->u2, (int)p->N, inv_bdt, g.mask, s, s2, s32, p->dstats, p->partials, p->counters, want_sums, inc);
+    else launch_pdl(direct_div_kernel<3, false>, G, T, 0, st, nc, p->K, p->ccol, p->cD64, p->cD2, p->ut64, p->u2, (int)p->N, inv_bdt, g.mask, s, s2, s32, p->dstats, p->partials, p->counters, want_sums, inc);
+  }
+}
+
 static pc_status project_impl(Plan *p, double dt, const void *u_star, const void *f_in, double *p_out,
                               void *u_out, void *f_out, pc_stats *stats, cudaStream_t st,
                               bool all_device = false) {
@@ -1225,7 +1292,12 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
                        p->ut64, p->u2, p->dstats, st);
   count_launch(p);
   prof_mark(p, st, 0);
-  for (int a = 0; a < d; ++a) {
+  if (p->divmode == PC_DIV_WLS_DIRECT) {
+    launch_direct_div(p, st, 1.0 / (p->beta * dt), stats ? 2 : (p->singular ? 1 : 0));
+    count_launch(p);
+    prof_mark(p, st, 2);
+  }
+  for (int a = 0; a < d && p->divmode == PC_DIV_FACES; ++a) {
     const long long rows = p->nface_total[a];
     const int G = grid_for(rows, T);
     if (mixed) {
@@ -1239,17 +1311,17 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
     }
     count_launch(p);
   }
-  prof_mark(p, st, 1);
   GridDev g = grid_dev(p);
-  {
+  if (p->divmode == PC_DIV_FACES) {
+    prof_mark(p, st, 1);
     auto divk = (d == 2) ? divergence_kernel<2> : divergence_kernel<3>;
     launch_pdl(divk, g.nblk, 256, 0, st, g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt),
                mixed ? nullptr : p->s64, mixed ? reinterpret_cast<float2 *>(p->s64) : nullptr,
                mixed ? reinterpret_cast<float *>(p->work64) : nullptr, p->dstats, p->partials, p->counters,
                stats ? 2 : (p->singular ? 1 : 0), 1.0 / (double)nc);
+    count_launch(p);
+    prof_mark(p, st, 2);
   }
-  count_launch(p);
-  prof_mark(p, st, 2);
   PC_CUDA_TRY(cudaGetLastError());
   PC_TRY(solve_grid(p, p->s64, dp, stats != nullptr, st,
                     mixed ? reinterpret_cast<const float *>(p->work64) : nullptr,
@@ -1257,7 +1329,7 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   launch_gradient(p, st, dp, du, dt, duo, dfo);
   count_launch(p);
   prof_mark(p, st, 6);
-  if (stats) {
+  if (stats && p->divmode == PC_DIV_FACES) {   // no face fluxes in the direct mode
     auto chk = (d == 2) ? div_check_kernel<2> : div_check_kernel<3>;
     launch_pdl(chk, g.nblk, 256, 0, st, g, p->U64[0], p->U64[1], p->U64[2], dp, p->beta * dt, p->dstats);
     count_launch(p);
@@ -1401,7 +1473,7 @@ static pc_status ib_tables(Plan *p, cudaStream_t st) {
   for (long long i = 0; i < N; ++i)
     if (type[(size_t)i] != PC_NODE_FLUID) idx.push_back((int32_t)i);
   std::vector<int32_t> faces[3];
-  if (!idx.empty()) {
+  if (!idx.empty() && p->divmode == PC_DIV_FACES) {
     long long maxrows = 0;
     for (int a = 0; a < d; ++a) maxrows = p->nface_total[a] > maxrows ? p->nface_total[a] : maxrows;
     uint8_t *flag = nullptr;
@@ -1487,7 +1559,12 @@ static pc_status ib_pass(Plan *p, bool first, double dt, const VT *du, double *d
     count_launch(p);
   }
   prof_mark(p, st, 0);
-  for (int a = 0; a < d; ++a) {
+  if (p->divmode == PC_DIV_WLS_DIRECT) {   // the whole source again: no face lists in this mode
+    launch_direct_div(p, st, 1.0 / (p->beta * dt), p->singular ? 1 : 0);
+    count_launch(p);
+    prof_mark(p, st, 2);
+  }
+  for (int a = 0; a < d && p->divmode == PC_DIV_FACES; ++a) {
     const long long rows = p->nface_total[a];
     const long long nl = first ? rows : p->nib_face[a];
     if (nl == 0) continue;
@@ -1509,17 +1586,17 @@ static pc_status ib_pass(Plan *p, bool first, double dt, const VT *du, double *d
     }
     count_launch(p);
   }
-  prof_mark(p, st, 1);
-  GridDev g = grid_dev(p);
-  {
+  if (p->divmode == PC_DIV_FACES) {
+    prof_mark(p, st, 1);
+    GridDev g = grid_dev(p);
     auto divk = (d == 2) ? divergence_kernel<2> : divergence_kernel<3>;
     launch_pdl(divk, g.nblk, 256, 0, st, g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt),
                mixed ? nullptr : p->s64, mixed ? reinterpret_cast<float2 *>(p->s64) : nullptr,
                mixed ? reinterpret_cast<float *>(p->work64) : nullptr, p->dstats, p->partials, p->counters,
                p->singular ? 1 : 0, 1.0 / (double)nc);
+    count_launch(p);
+    prof_mark(p, st, 2);
   }
-  count_launch(p);
-  prof_mark(p, st, 2);
   PC_CUDA_TRY(cudaGetLastError());
   PC_TRY(solve_grid(p, p->s64, dp, false, st, mixed ? reinterpret_cast<const float *>(p->work64) : nullptr,
                     mixed ? reinterpret_cast<const float2 *>(p->s64) : nullptr));
@@ -1755,4 +1832,26 @@ extern "C" pc_status pc_project_ib(pc_plan *plan, double dt, const void *u_star,
                                        p_out, (double *)u_out, (double *)f_ib_out, history, result, st);
   return pc::project_ib_impl<float>(p, dt, (const float *)u_star, (const float *)f_ib_init, tol, max_iters, p_out,
                                     (float *)u_out, (float *)f_ib_out, history, result, st);
+}
+
+extern "C" pc_status pc_plan_set_rhs_mask(pc_plan *plan, const uint8_t *mask, void *cuda_stream) {
+  pc::Plan *p = reinterpret_cast<pc::Plan *>(plan);
+  if (!p) return pc::fail(PC_ERR_INVALID_ARG, "plan is NULL");
+  if (cudaSetDevice(p->device) != cudaSuccess) return pc::fail(PC_ERR_CUDA, "cannot select device %d", p->device);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (!mask) {
+    if (p->rhs_mask_on) {
+      p->rhs_mask_on = false;
+      pc::plan_drop_graphs(p);
+    }
+    return PC_OK;
+  }
+  if (!p->rhs_mask) PC_TRY(pc::plan_alloc(p, (void **)&p->rhs_mask, (size_t)p->ncells));
+  PC_CUDA_TRY(cudaMemcpyAsync(p->rhs_mask, mask, (size_t)p->ncells, cudaMemcpyDefault, st));
+  PC_CUDA_TRY(cudaStreamSynchronize(st));
+  if (!p->rhs_mask_on) {
+    p->rhs_mask_on = true;
+    pc::plan_drop_graphs(p);   // captured launches hold the grid description without the mask
+  }
+  return PC_OK;
 }

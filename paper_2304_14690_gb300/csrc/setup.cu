@@ -231,7 +231,7 @@ __device__ bool wls_rows(const KnnCtx &c, const double *q, const int *bi, const 
 }
 
 // Failure record: flags[0] ORs the kinds; flags[1..2] hold the smallest (query set, row) key
-// so the host can name the first query that failed (set 0..2: faces of that axis, 3: nodes).
+// so the host can name the first query that failed (set 0..2: faces of that axis, 3: nodes, 4: cells).
 __device__ __forceinline__ void record_failure(unsigned int *flags, unsigned int kind, int set, long long row) {
   atomicOr(flags, kind);
   unsigned long long key = ((unsigned long long)set << 48) | (unsigned long long)row;
@@ -289,6 +289,38 @@ __global__ void face_rows_kernel(KnnCtx c, WlsParams P, int axis, int nf_axis, i
   for (int k = 0; k < K; ++k) {
     col[(long long)k * rows + r] = bi[k];
     split_store(w[k], w64, w2, (long long)k * rows + r);
+  }
+}
+
+// Derivative rows of every cell centre over its K nearest nodes (the direct divergence of the
+// source at the pressure points, §2.3): weights [DIM][K][cells].
+template <int DIM>
+__global__ void cell_rows_kernel(KnnCtx c, WlsParams P, long long rows, const double *glo, const double *gh,
+                                 const int *gshape, int32_t *col, double *w64, float2 *w2, unsigned int *flags) {
+  long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  int idx[3];
+  long long rem = r;
+  for (int a = DIM - 1; a >= 0; --a) {
+    idx[a] = (int)(rem % gshape[a]);
+    rem /= gshape[a];
+  }
+  const int K = P.K;
+  double q[3];
+  for (int a = 0; a < DIM; ++a) q[a] = __dadd_rn(glo[a], __dmul_rn((double)idx[a] + 0.5, gh[a]));
+  double bd[kMaxK];
+  int bi[kMaxK];
+  double w[DIM * kMaxK];
+  bool ok = knn_query(c, q, K, bd, bi);
+  if (!ok) record_failure(flags, FLAG_KNN_SHORT, 4, r);
+  else if (!wls_rows<DIM>(c, q, bi, bd, P, w)) { ok = false; record_failure(flags, FLAG_WLS_SINGULAR, 4, r); }
+  if (!ok) {
+    for (int k = 0; k < K; ++k) bi[k] = 0;
+    for (int k = 0; k < DIM * K; ++k) w[k] = 0.0;
+  }
+  for (int k = 0; k < K; ++k) {
+    col[(long long)k * rows + r] = bi[k];
+    for (int a = 0; a < DIM; ++a) split_store(w[a * K + k], w64, w2, ((long long)a * K + k) * rows + r);
   }
 }
 
@@ -488,6 +520,17 @@ pc_status build_rows(Plan *p, const double *xyz, cudaStream_t st) {
       face_rows_kernel<3><<<grid_for(rows, 128), 128, 0, st>>>(nc, P, a, ax.nfaces, lo_wall, hi_wall, ax.n, rows, glo, gh,
                                                                gshape, p->fcol[a], p->fw64[a], mixed ? p->fw2[a] : nullptr, flags);
   }
+  if (p->divmode == PC_DIV_WLS_DIRECT) {
+    WlsParams Pc = P;
+    Pc.nrows_out = d;
+    Pc.first_row = 1;
+    if (d == 2)
+      cell_rows_kernel<2><<<grid_for(p->ncells, 128), 128, 0, st>>>(nc, Pc, p->ncells, glo, gh, gshape, p->ccol,
+                                                                    p->cD64, mixed ? p->cD2 : nullptr, flags);
+    else
+      cell_rows_kernel<3><<<grid_for(p->ncells, 128), 128, 0, st>>>(nc, Pc, p->ncells, glo, gh, gshape, p->ccol,
+                                                                    p->cD64, mixed ? p->cD2 : nullptr, flags);
+  }
   // cell centres as points: bucket == cell
   KnnCtx cc{};
   cc.dim = d;
@@ -524,7 +567,8 @@ pc_status build_rows(Plan *p, const double *xyz, cudaStream_t st) {
     return fail(PC_ERR_WLS_SINGULAR, "WLS setup failed (%s%s); first failing query: %s %lld",
                 (hf[0] & FLAG_KNN_SHORT) ? "fewer than K neighbours " : "",
                 (hf[0] & FLAG_WLS_SINGULAR) ? "normal matrix not positive definite" : "",
-                set < 3 ? (set == 0 ? "face row, axis 0," : (set == 1 ? "face row, axis 1," : "face row, axis 2,")) : "node",
+                set < 3 ? (set == 0 ? "face row, axis 0," : (set == 1 ? "face row, axis 1," : "face row, axis 2,"))
+                        : (set == 4 ? "cell row" : "node"),
                 row);
   }
   return PC_OK;

@@ -55,6 +55,8 @@ class ProblemDesc(ctypes.Structure):
         ("refine_iters", ctypes.c_int),
         ("gauge", ctypes.c_int),
         ("velocity_dtype", ctypes.c_int),
+        ("eigenvalues", ctypes.c_int),
+        ("divergence", ctypes.c_int),
     ]
 
 
@@ -101,6 +103,7 @@ FUNCTIONS = {
     "pc_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.POINTER(Stats), ctypes.c_void_p]),
+    "pc_plan_set_rhs_mask": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pc_project_ib": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
@@ -182,8 +185,12 @@ def _stream_handle(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
+EIGENVALUES = {"fd": 0, "spectral": 1}
+DIVERGENCE = {"faces": 0, "wls_direct": 1}
+
+
 def make_desc(problem, precision="fp64", refine_iters=2, gauge=0, velocity_dtype=None,
-              node_xyz=None, node_type=None):
+              node_xyz=None, node_type=None, eigenvalues="fd", div_mode="faces"):
     d = ProblemDesc()
     d.dim = problem.dim
     for a in range(3):
@@ -207,6 +214,8 @@ def make_desc(problem, precision="fp64", refine_iters=2, gauge=0, velocity_dtype
     if velocity_dtype is None:
         velocity_dtype = "f32" if problem.u_star.dtype == np.float32 else "f64"
     d.velocity_dtype = DTYPE[velocity_dtype]
+    d.eigenvalues = EIGENVALUES[eigenvalues]
+    d.divergence = DIVERGENCE[div_mode]
     return d
 
 
@@ -214,7 +223,7 @@ class Plan:
     """A libpc plan for one problem geometry (nodes, grid, boundaries)."""
 
     def __init__(self, problem, precision="fp64", refine_iters=2, gauge=0, device=0,
-                 budget_bytes=0, stream=None):
+                 budget_bytes=0, stream=None, eigenvalues="fd", div_mode="faces"):
         import torch
         lib = load()
         self.problem = problem
@@ -224,7 +233,7 @@ class Plan:
         xyz = torch.as_tensor(np.ascontiguousarray(problem.nodes, dtype=np.float64), device=self.device)
         typ = torch.as_tensor(np.ascontiguousarray(problem.node_type, dtype=np.uint8), device=self.device)
         self._desc = make_desc(problem, precision, refine_iters, gauge,
-                               "f32" if self.vdtype == torch.float32 else "f64", xyz, typ)
+                               "f32" if self.vdtype == torch.float32 else "f64", xyz, typ, eigenvalues, div_mode)
         h = ctypes.c_void_p()
         _check(lib.pc_plan_create(ctypes.byref(self._desc), device, budget_bytes,
                                   _stream_handle(stream), ctypes.byref(h)))
@@ -297,16 +306,18 @@ class Plan:
                     kernel_launches=pr.kernel_launches)
 
     def rows(self, which):
-        """(col [rows, K] int32, w) of face axis `which` (w [rows, K]) or of the nodes
-        (which == dim, w [dim, rows, K])."""
+        """(col [rows, K] int32, w) of face axis `which` (w [rows, K]), of the nodes
+        (which == dim, w [dim, rows, K]) or of the cell centres of a direct-divergence plan
+        (which == dim + 1, w [dim, rows, K])."""
         lib = load()
         n = ctypes.c_int64()
         _check(lib.pc_plan_rows(self.handle, which, ctypes.byref(n), None, None))
-        K = self.problem.knn if which < self.dim else 3 ** self.dim
+        K = 3 ** self.dim if which == self.dim else self.problem.knn
+        nw = 1 if which < self.dim else self.dim
         col = np.empty((n.value, K), dtype=np.int32)
-        w = np.empty(((self.dim if which == self.dim else 1), n.value, K), dtype=np.float64)
+        w = np.empty((nw, n.value, K), dtype=np.float64)
         _check(lib.pc_plan_rows(self.handle, which, ctypes.byref(n), col.ctypes.data, w.ctypes.data))
-        return col, (w if which == self.dim else w[0])
+        return col, (w if which >= self.dim else w[0])
 
     def alloc_outputs(self):
         import torch
@@ -330,6 +341,15 @@ class Plan:
                               _ptr(f, vshape, self.vdtype, "f_out"),
                               ctypes.byref(st) if st is not None else None, _stream_handle(stream)))
         return p, u, f, (st.as_dict() if st is not None else None)
+
+    def set_rhs_mask(self, mask, stream=None):
+        """pc_plan_set_rhs_mask: mask (cells, uint8, nonzero = flow domain; numpy array or
+        torch tensor) or None to clear."""
+        import torch
+        if mask is not None and not hasattr(mask, "data_ptr"):
+            mask = torch.as_tensor(np.ascontiguousarray(mask, dtype=np.uint8))
+        _check(load().pc_plan_set_rhs_mask(self.handle, _ptr(mask, self.shape, torch.uint8, "mask"),
+                                           _stream_handle(stream)))
 
     def project_ib(self, u_star, f_init=None, tol=1e-3, max_iters=50, dt=None, out=None, stream=None):
         """Run pc_project_ib (the IB-force iteration) on device tensors [dim, N].

@@ -368,3 +368,134 @@ def test_project_ib_graph_equals_host_loop(env, problems, precision):
             _, _, _, info = plan.project_ib(u, tol=0.0, max_iters=m, out=outs)
             assert info["iterations"] == m and not info["converged"]
         plan.close()
+
+
+@pytest.mark.parametrize("n", [(8, 8), (24, 20), (96, 64), (8, 12, 10)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_poisson_spectral_matches_oracle(env, n, precision, tol):
+    """Pseudo-spectral eigenvalues (§2.3): every boundary pairing against the oracle's
+    expansion with the same eigenvalues."""
+    pc, torch, dev = env
+    dim = len(n)
+    combos = list(itertools.product(list(KINDS), repeat=dim))
+    if dim == 3:
+        combos = combos[::7]
+    for i, kinds in enumerate(combos):
+        g, s = _poisson_case(kinds, n, 2000 + i)
+        ref, _ = P.solve(s, g, eigenvalues="spectral")
+        plan = pc.Plan(_GridProblem(g), precision=precision, eigenvalues="spectral")
+        p, _ = plan.solve_poisson(torch.as_tensor(s, device=dev))
+        e = rel(p.cpu().numpy(), ref)
+        assert e <= tol, (kinds, n, precision, e)
+        plan.close()
+
+
+def test_project_spectral_matches_oracle(env, problems):
+    """Whole projection with the pseudo-spectral solve (FP64 plans), and the mixed precision
+    refused (its refinement residual is that of the finite-difference operator)."""
+    pc, torch, dev = env
+    for prob, oplan, _ in problems:
+        ref = PR.project(oplan, prob.dt, prob.u_star, prob.f_ib, eigenvalues="spectral")
+        plan = pc.Plan(prob, precision="fp64", eigenvalues="spectral")
+        u = torch.as_tensor(prob.u_star, device=dev)
+        f = torch.as_tensor(prob.f_ib, device=dev)
+        p, uo, fo, st = plan.project(u, f, stats=True)
+        for name, got, want in (("p", p, ref["p"]), ("u", uo, ref["u"]), ("f", fo, ref["f"])):
+            e = rel(got.cpu().numpy(), want)
+            assert e <= 1e-12, (prob.bc_lo, prob.bc_hi, prob.n, name, e)
+        assert st["residual_norm"] == [0.0]
+        plan.close()
+    with pytest.raises(pc.PcError):
+        pc.Plan(problems[0][0], precision="mixed", eigenvalues="spectral")
+
+
+def _mask_for(prob, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.random(tuple(prob.n[:prob.dim])) > 0.3).astype(np.uint8)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-10)])
+def test_project_rhs_mask_matches_oracle(env, problems, precision, tol):
+    """§3.5 RHS mask: the source is zeroed outside the flow domain; single projections, the
+    IB iteration and a batch against the oracle (and the batch bitwise equal to single calls);
+    max_div_after is taken inside the mask; clearing the mask restores the unmasked result."""
+    pc, torch, dev = env
+    for k, (prob, oplan, ref0) in enumerate(problems):
+        mask = _mask_for(prob, 50 + k)
+        ref = PR.project(oplan, prob.dt, prob.u_star, prob.f_ib, rhs_mask=mask)
+        plan = pc.Plan(prob, precision=precision)
+        plan.set_rhs_mask(mask)
+        u = torch.as_tensor(prob.u_star, device=dev)
+        f = torch.as_tensor(prob.f_ib, device=dev)
+        p, uo, fo, st = plan.project(u, f, stats=True)
+        for name, got, want in (("p", p, ref["p"]), ("u", uo, ref["u"]), ("f", fo, ref["f"])):
+            e = rel(got.cpu().numpy(), want)
+            assert e <= tol, (precision, k, name, e)
+        expect = prob.beta * prob.dt * abs(ref["removed"])
+        scale = np.abs(ref["s"]).max() * prob.beta * prob.dt
+        assert st["max_div_after"] <= expect + 1e-9 * scale
+        # graph replay (no stats) and a batch of this plan with a clone give the same bits
+        p1, u1, f1, _ = plan.project(u, f)
+        p1, u1, f1 = p1.clone(), u1.clone(), f1.clone()
+        if precision == "mixed":
+            outs = plan.alloc_outputs()
+            pc.project_batch([plan], [dict(dt=prob.dt, u_star=u, f_ib=f, p=outs[0], u=outs[1], f=outs[2])])
+            torch.cuda.synchronize()
+            assert all(torch.equal(a, b) for a, b in zip(outs, (p1, u1, f1)))
+        assert rel(p1.cpu().numpy(), ref["p"]) <= tol
+        if np.any(prob.node_type != 0):
+            rib = PR.project_ib(oplan, prob.dt, prob.u_star, tol=0.0, max_iters=3, rhs_mask=mask)
+            pi, ui, fi, _ = plan.project_ib(u, tol=0.0, max_iters=3)
+            for name, got, want in (("p", pi, rib["p"]), ("u", ui, rib["u"]), ("f", fi, rib["f"])):
+                assert rel(got.cpu().numpy(), want) <= tol, (precision, k, "ib", name)
+        plan.set_rhs_mask(None)
+        p2, _, _, _ = plan.project(u, f)
+        assert rel(p2.cpu().numpy(), ref0["p"]) <= tol
+        plan.close()
+
+
+def test_direct_divergence_rows_match_oracle(env, problems):
+    """Cell-centre derivative rows of the direct divergence: KNN columns bit-exact, weights
+    within the kappa bound of the WLS normal matrix (as the face and node rows)."""
+    pc, torch, dev = env
+    ulp = np.finfo(np.float64).eps
+    for prob, oplan, _ in problems:
+        plan = pc.Plan(prob, precision="fp64", div_mode="wls_direct")
+        col, D = plan.rows(prob.dim + 1)
+        ccol, cD = PR.cell_rows(oplan)
+        assert np.array_equal(col, ccol), (prob.bc_lo, prob.n)
+        kap = _row_kappa(prob.nodes.T, oplan.grid.cell_points(), ccol, oplan.grid)
+        tol = 64 * ulp * kap[None, :, None] * np.abs(cD).max(axis=2, keepdims=True)
+        assert np.all(np.abs(D - cD) <= tol)
+        plan.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-10)])
+def test_project_direct_divergence_matches_oracle(env, problems, precision, tol):
+    """The paper's direct WLS divergence at the cell centres: single projections and the IB
+    iteration against the oracle, and a batch entry (run one by one) bitwise equal to a single
+    call."""
+    pc, torch, dev = env
+    for k, (prob, oplan, _) in enumerate(problems):
+        ref = PR.project(oplan, prob.dt, prob.u_star, prob.f_ib, div_mode="wls_direct")
+        plan = pc.Plan(prob, precision=precision, div_mode="wls_direct")
+        u = torch.as_tensor(prob.u_star, device=dev)
+        f = torch.as_tensor(prob.f_ib, device=dev)
+        p, uo, fo, st = plan.project(u, f, stats=True)
+        for name, got, want in (("p", p, ref["p"]), ("u", uo, ref["u"]), ("f", fo, ref["f"])):
+            e = rel(got.cpu().numpy(), want)
+            assert e <= tol, (precision, k, name, e)
+        assert abs(st["removed_mean"] - ref["removed"]) <= 1e-9 * max(1.0, np.abs(ref["s"]).max())
+        assert st["max_div_after"] == 0.0
+        p1 = plan.project(u, f)[0].clone()
+        outs = plan.alloc_outputs()
+        pc.project_batch([plan], [dict(dt=prob.dt, u_star=u, f_ib=f, p=outs[0], u=outs[1], f=outs[2])])
+        torch.cuda.synchronize()
+        assert torch.equal(outs[0], p1)
+        if np.any(prob.node_type != 0):
+            rib = PR.project_ib(oplan, prob.dt, prob.u_star, tol=0.0, max_iters=3, div_mode="wls_direct")
+            pi, ui, fi, info = plan.project_ib(u, tol=0.0, max_iters=3)
+            assert info["iterations"] == 3
+            for name, got, want in (("p", pi, rib["p"]), ("u", ui, rib["u"]), ("f", fi, rib["f"])):
+                assert rel(got.cpu().numpy(), want) <= tol, (precision, k, "ib", name)
+        plan.close()
