@@ -221,6 +221,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def transform_kernel_hash():
+    """Hash of the transform kernel's device code: fft.cuh and the device part of poisson.cu
+    (everything before its host-side section), so host-only edits keep a capture valid."""
+    csrc = os.path.join(ROOT, "paper_2304_14690_gb300", "csrc")
+    h = hashlib.sha1()
+    h.update(open(os.path.join(csrc, "fft.cuh"), "rb").read())
+    src = open(os.path.join(csrc, "poisson.cu"), "rb").read()
+    h.update(src.split(b"// ----------------------------------------------------------------------------- host side")[0])
+    return h.hexdigest()[:12]
+
+
 def ncu_traffic(phase):
     """DRAM bytes per call of a phase from the committed ncu summary, or None when the summary
     is absent or was taken on other kernel sources (the transform sources are hashed)."""
@@ -231,10 +242,7 @@ def ncu_traffic(phase):
         d = json.load(open(path)).get(phase)
         if not d:
             return None
-        h = hashlib.sha1()
-        for f in ("fft.cuh", "poisson.cu"):
-            h.update(open(os.path.join(ROOT, "paper_2304_14690_gb300", "csrc", f), "rb").read())
-        if h.hexdigest()[:12] != d.get("sources_sha1"):
+        if transform_kernel_hash() != d.get("sources_sha1"):
             return None
         return d["dram_bytes_per_call"]
     except Exception:
@@ -372,6 +380,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None if args.no_extras else run_e2e(plan, prob, stream, dev, steps, world)
     ib = None if args.no_extras else run_ib(plan, prob, u_dev, stream, dev, flush)
+    variants = None if args.no_extras else run_variants(args, prob, u_dev, stream, dev, flush, ms_step=total_ms / steps)
 
     batch = None
     if not args.no_batch:
@@ -401,6 +410,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(prof["kernel_launches"] * steps / calls),
         "clocks": clocks, "cpu_baseline": cpu, "wall_s": round(wall, 3),
         "ib_iteration": ib,
+        "variants": variants,
         "batch_2d_512": batch,
         "box_sphere_3d": box3d,
     }
@@ -487,6 +497,73 @@ def run_ib(plan, prob, u_dev, stream, dev, flush, tol=1e-3, max_iters=50, reps=1
             "full_passes_ms": round(ms_full, 4), "speedup_vs_full_passes": round(ms_full / ms_graph, 3),
             "cells_per_s_per_time_step": round(prob.num_cells / (ms_graph * 1e-3), 1),
             "history_last": info["history"][-1]}
+
+
+def run_variants(args, prob, u_dev, stream, dev, flush, ms_step, reps=50):
+    """The solve variants of the paper on the same workload, each timed per projection like the
+    main step: pseudo-spectral eigenvalues (FP64 plan, against the FD FP64 plan), the direct WLS
+    divergence at the cell centres (mixed; with the roofline of its gather kernel), and the RHS
+    mask (mixed; the cells inside the cylinder masked out)."""
+    import numpy as np
+    import torch
+    from paper_2304_14690_gb300 import pc
+
+    def timed(plan):
+        outs = plan.alloc_outputs()
+        for _ in range(3):
+            plan.project(u_dev, out=outs)
+        torch.cuda.synchronize(dev)
+        plan.profile(True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for k in range(reps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            plan.project(u_dev, out=outs)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        prof = plan.profile_read()
+        plan.profile(False)
+        calls = max(prof["calls"], 1)
+        return (sum(a.elapsed_time(b) for a, b in ev) / reps,
+                {k: v / calls for k, v in prof["phase_ms"].items() if v > 0})
+
+    out = {}
+    fd = pc.Plan(prob, precision="fp64", device=dev.index)
+    ms_fd, _ = timed(fd)
+    fd.close()
+    sp = pc.Plan(prob, precision="fp64", device=dev.index, eigenvalues="spectral")
+    ms_sp, _ = timed(sp)
+    sp.close()
+    out["spectral_fp64"] = {"ms_per_step": round(ms_sp, 5), "fd_fp64_ms_per_step": round(ms_fd, 5)}
+    di = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, device=dev.index, div_mode="wls_direct")
+    di.autotune()
+    ms_di, ph = timed(di)
+    di.close()
+    d, N, K, nc = prob.dim, prob.num_nodes, prob.knn, prob.num_cells
+    div_bytes = nc * K * (4 + d * 8) + d * N * 8 + nc * (8 + 4)
+    peak, peak_src = measured_peaks()
+    ach = div_bytes / (ph["divergence"] * 1e-3) / 1e9
+    out["wls_direct_divergence"] = {
+        "ms_per_step": round(ms_di, 5), "faces_ms_per_step": round(ms_step, 5),
+        "value": round(nc / (ms_di * 1e-3), 1), "unit": UNIT,
+        "phase_ms": {k: round(v, 5) for k, v in ph.items()},
+        "roofline_divergence": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                                "frac": round(ach / peak, 4), "algorithmic_bytes": div_bytes,
+                                "peak_source": peak_src}}
+    mk = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, device=dev.index)
+    mk.autotune()
+    g = prob.n
+    xc = prob.lo[0] + (np.arange(g[0]) + 0.5) * prob.h[0]
+    yc = prob.lo[1] + (np.arange(g[1]) + 0.5) * prob.h[1]
+    X, Y = np.meshgrid(xc, yc, indexing="ij")
+    inside = np.zeros(X.shape, dtype=bool)
+    for o in getattr(prob, "obstacles", None) or []:
+        inside |= (X - o[1][0]) ** 2 + (Y - o[1][1]) ** 2 < o[2] ** 2
+    mk.set_rhs_mask((~inside).astype(np.uint8))
+    ms_mk, _ = timed(mk)
+    mk.close()
+    out["rhs_mask"] = {"ms_per_step": round(ms_mk, 5), "masked_cells": int(inside.sum())}
+    return out
 
 
 def run_3d(args, dev, stream, flush, world, rank):
