@@ -222,13 +222,12 @@ def measured_peaks():
 
 
 def transform_kernel_hash():
-    """Hash of the transform kernel's device code: fft.cuh and the device part of poisson.cu
-    (everything before its host-side section), so host-only edits keep a capture valid."""
+    """Hash of the transform kernel's device code (fft.cuh and axis_pass.cuh), so host-only
+    edits keep a capture valid."""
     csrc = os.path.join(ROOT, "paper_2304_14690_gb300", "csrc")
     h = hashlib.sha1()
-    h.update(open(os.path.join(csrc, "fft.cuh"), "rb").read())
-    src = open(os.path.join(csrc, "poisson.cu"), "rb").read()
-    h.update(src.split(b"// ----------------------------------------------------------------------------- host side")[0])
+    for f in ("fft.cuh", "axis_pass.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:12]
 
 

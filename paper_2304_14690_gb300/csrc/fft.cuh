@@ -228,8 +228,9 @@ __device__ __forceinline__ void fft_stage(const T *src, T *dst, const TileGeom &
 constexpr int cdiv_c(int a, int b) { return (a + b - 1) / b; }
 
 // Complex FFT of length g.M on every line (unnormalised), ping-ponging between a and b; returns
-// the buffer that holds the result. Every thread of the CTA calls it (barriers).
-template <typename T, int EMAX, bool INV>
+// the buffer that holds the result. Every thread of the CTA calls it (barriers). POW2: M is a
+// power of two, so the radix-3 and radix-5 stages are not compiled into the caller.
+template <typename T, int EMAX, bool INV, bool POW2 = false>
 __device__ T *fft_run(T *a, T *b, const TileGeom &g, const StageInfo *st, int nst, const T *tw, const T *pre) {
   for (int s = 0; s < nst; ++s) {
     const StageInfo si = st[s];
@@ -246,8 +247,12 @@ __device__ T *fft_run(T *a, T *b, const TileGeom &g, const StageInfo *st, int ns
         if constexpr (EMAX >= 4) fft_stage<T, 4, cdiv_c(EMAX, 4), INV>(a, b, g, si, tw, p0);
         break;
       case 2: fft_stage<T, 2, cdiv_c(EMAX, 2), INV>(a, b, g, si, tw, p0); break;
-      case 3: fft_stage<T, 3, cdiv_c(EMAX, 3), INV>(a, b, g, si, tw, p0); break;
-      default: fft_stage<T, 5, cdiv_c(EMAX, 5), INV>(a, b, g, si, tw, p0); break;
+      case 3:
+        if constexpr (!POW2) fft_stage<T, 3, cdiv_c(EMAX, 3), INV>(a, b, g, si, tw, p0);
+        break;
+      default:
+        if constexpr (!POW2) fft_stage<T, 5, cdiv_c(EMAX, 5), INV>(a, b, g, si, tw, p0);
+        break;
     }
     T *t = a;
     a = b;

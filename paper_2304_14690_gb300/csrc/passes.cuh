@@ -65,6 +65,15 @@ std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, c
 template <typename Real>
 pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long long &tiles, int &threads,
                      size_t &smem, int batch_threads);
+// Single-problem FP32 pass of transform family 0 (real DFT), 1 (DCT-II/DST-II) or 2
+// (DCT-IV/DST-IV), each compiled in its own translation unit (pass_f32_family*.cu), and the
+// shared-memory attributes of their kernel instances.
+pc_status launch_pass_f32_family0(const PassArgs<float> &A, long long tiles, int threads, size_t smem, cudaStream_t st);
+pc_status launch_pass_f32_family1(const PassArgs<float> &A, long long tiles, int threads, size_t smem, cudaStream_t st);
+pc_status launch_pass_f32_family2(const PassArgs<float> &A, long long tiles, int threads, size_t smem, cudaStream_t st);
+pc_status prepare_pass_f32_family0(int lim);
+pc_status prepare_pass_f32_family1(int lim);
+pc_status prepare_pass_f32_family2(int lim);
 // One launch of the batched pass kernel over items (args index, tile); emax: the largest slots
 // per thread among the items' passes (selects the kernel instance).
 template <typename Real>

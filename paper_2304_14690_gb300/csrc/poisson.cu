@@ -15,220 +15,9 @@
 #include <cstring>
 #include <vector>
 
-#include "fft.cuh"
-#include "numeric.cuh"
-#include "passes.cuh"
-#include "pc_internal.cuh"
+#include "axis_pass.cuh"
 
 namespace pc {
-
-// Source element gi in the pass precision (FP64 sources enter FP32 passes truncated to 24 bits,
-// by integer operations; the refinement corrects what that drops).
-__device__ __forceinline__ float to_real(double v, float *) { return d2f_rz_bits(v); }
-__device__ __forceinline__ double to_real(double v, double *) { return v; }
-__device__ __forceinline__ double to_f64(float v) { return f2d_bits(v); }
-__device__ __forceinline__ double to_f64(double v) { return v; }
-
-template <typename Real>
-__device__ __forceinline__ Real load_src(const PassArgs<Real> &A, int gi) {
-  if (A.src_mode == SRC_F32) return (Real)__ldg(static_cast<const float *>(A.src) + gi);
-  if (A.src_mode == SRC_F64) return to_real(__ldg(static_cast<const double *>(A.src) + gi), (Real *)nullptr);
-  return static_cast<const Real *>(A.src)[gi];
-}
-
-// One axis pass over a tile of lines: [forward transform] [eigenvalue division] [inverse].
-// Dynamic shared memory: two buffers of L*M complex slots (the FFT ping-pongs between them),
-// then per line the eigenvalue sum of the other axes, the line's base cell index (-1 for lines
-// past a ragged end) and its zero-mode flag. Threads beyond L * tpl (a batched launch sized for
-// a larger tile) take part in the barriers only. Steps and barriers:
-//   forward:  load line -> scatter to slots | FFT stages | post-process -> global (forward-only)
-//             or -> real coefficients in the other buffer with the division fused |
-//   inverse:  (inverse-only: load coefficients -> other buffer |) pre-process -> slots |
-//             FFT stages | normalise and store.
-template <typename Real, int EMAX>
-__device__ __forceinline__ void axis_pass_body(const PassArgs<Real> &A, const int tile, unsigned char *smem_raw) {
-  using T = typename Cplx<Real>::T;
-  T *buf0 = reinterpret_cast<T *>(smem_raw);
-  T *buf1 = buf0 + A.L * A.M;
-  Real *lamo = reinterpret_cast<Real *>(buf1 + A.L * A.M);
-  int *lbase = reinterpret_cast<int *>(lamo + A.L);
-  int *lzero = lbase + A.L;
-  const int t = threadIdx.x;
-  const bool active = t < (A.L << A.tpl_bits);
-  TileGeom g;
-  g.L = A.L;
-  g.M = A.M;
-  g.tpl = 1 << A.tpl_bits;
-  if (A.col) { g.es = A.L; g.ls = 1; g.line = t & (A.L - 1); g.lane = t >> A.lbits; }
-  else { g.es = 1; g.ls = A.M; g.line = t >> A.tpl_bits; g.lane = t & (g.tpl - 1); }
-  if (!active) { g.line = 0; g.lane = 1 << 24; }   // every position loop is empty
-  const int n = A.n;
-
-  if (t < A.L) {
-    int base, valid;
-    if (A.col) {
-      int o = tile / A.tiles_per_outer;
-      int f = (tile - o * A.tiles_per_outer) * A.L + t;
-      valid = f < A.inner;
-      base = o * n * A.stride + f;
-    } else {
-      int line = tile * A.L + t;
-      valid = line < A.lines;
-      base = line * n;
-    }
-    lbase[t] = valid ? base : -1;
-    if (A.do_div && valid) {
-      int rem = base, idx[3] = {0, 0, 0};
-      for (int b = A.dim - 1; b >= 0; --b) { idx[b] = rem % A.shape[b]; rem /= A.shape[b]; }
-      Real lo = 0;
-      int zero = 1;
-      for (int b = 0; b < A.dim; ++b) {
-        if (b == A.axis) continue;
-        lo += A.lam[b][idx[b]];
-        zero &= idx[b] == 0;
-      }
-      lamo[t] = lo;
-      lzero[t] = zero;
-    }
-  }
-  __syncthreads();
-  const int line = g.line;
-  const int base = lbase[line];
-  const bool valid = active && base >= 0;
-  const int stride = A.stride;
-  const bool dct4 = A.kind == KIND_ND || A.kind == KIND_DN;
-
-  // All global loads of a thread are issued before any is used (memory-level parallelism).
-  Real xin[2 * EMAX];
-#pragma unroll
-  for (int b = 0; b < 2 * EMAX; ++b) {
-    const int j = g.lane + b * g.tpl;
-    xin[b] = (valid && j < n) ? load_src(A, base + j * stride) : (Real)0;
-  }
-  T *res;        // buffer with the latest slots
-  T *coef;       // buffer with the real coefficients for the inverse
-  if (A.do_fwd) {
-    // F1: scatter the real line into the complex slots (Makhoul / DCT-IV ordering).
-#pragma unroll
-    for (int b = 0; b < 2 * EMAX; ++b) {
-      const int j = g.lane + b * g.tpl;
-      if (j < n) {
-        int q, comp;
-        bool neg;
-        fwd_slot_of(A.kind, n, j, q, comp, neg);
-        reinterpret_cast<Real *>(&slot(buf0, g, line, q))[comp] = neg ? -xin[b] : xin[b];
-      }
-    }
-    __syncthreads();
-    res = fft_run<T, EMAX, false>(buf0, buf1, g, A.st, A.nst, A.tw, dct4 ? A.tw + tw_dct4pre(A.M) : nullptr);
-    if (!A.do_inv) {
-      // forward-only pass: the coefficients go straight to global memory (DST_WORK)
-      if (valid) {
-        Real *dst = static_cast<Real *>(A.dst);
-        fwd_post(res, g, A.kind, n, A.tw, [&](int pos, Real X) { dst[base + pos * stride] = X; });
-      }
-      return;
-    }
-    coef = (res == buf0) ? buf1 : buf0;
-    if (valid) {
-      // p^ = s^ / (lambda_axis(j) + sum of the other axes' eigenvalues); zero mode -> 0
-      const Real lo = lamo[line];
-      const bool z = A.singular && lzero[line];
-      const Real *la = A.lam[A.axis];
-      const bool dv = A.do_div;
-      fwd_post(res, g, A.kind, n, A.tw, [&](int pos, Real X) {
-        if (dv) X = (z && pos == 0) ? (Real)0 : X / (__ldg(la + pos) + lo);
-        realref(coef, g, line, pos) = X;
-      });
-    }
-    __syncthreads();
-  } else {
-    // inverse-only pass: the coefficients are staged in shared memory first
-    coef = buf1;
-    res = buf0;
-#pragma unroll
-    for (int b = 0; b < 2 * EMAX; ++b) {
-      const int j = g.lane + b * g.tpl;
-      if (j < n) realref(coef, g, line, j) = xin[b];
-    }
-    __syncthreads();
-  }
-  if (!A.do_inv) return;
-  // I1: coefficients -> slots (into the buffer the forward FFT result came from)
-  T *slots = (coef == buf0) ? buf1 : buf0;
-  if (valid) inv_pre(slots, g, A.kind, n, A.tw, [&](int i) -> Real { return realref(coef, g, line, i); });
-  __syncthreads();
-  if (dct4) res = fft_run<T, EMAX, false>(slots, coef, g, A.st, A.nst, A.tw, nullptr);
-  else res = fft_run<T, EMAX, true>(slots, coef, g, A.st, A.nst, A.tw, nullptr);
-  if (!valid) return;
-  // I3: normalise and store, in chunks of 8 outputs (the old values of an accumulating store
-  // are loaded together)
-  const Real scale = A.out_scale;
-  constexpr int kChunk = 8;
-#pragma unroll
-  for (int c0 = 0; c0 < 2 * EMAX; c0 += kChunk) {
-    Real x[kChunk];
-    // previous value of an accumulating store: an FP64 value or a (hi, lo) pair, 8 bytes either way
-    unsigned long long old[kChunk];
-    const bool acc = A.dst_mode == DST_F64_ADD || A.dst_mode == DST_PAIR_ADD;
-#pragma unroll
-    for (int b = 0; b < kChunk; ++b) {
-      const int i = g.lane + (c0 + b) * g.tpl;
-      x[b] = (i < n) ? inv_out(res, g, A.kind, n, A.tw, i) * scale : (Real)0;
-      old[b] = (acc && i < n) ? static_cast<const unsigned long long *>(A.dst)[base + i * stride] : 0ULL;
-    }
-#pragma unroll
-    for (int b = 0; b < kChunk; ++b) {
-      const int i = g.lane + (c0 + b) * g.tpl;
-      if (i >= n) continue;
-      const int gi = base + i * stride;
-      if (A.dst_mode == DST_WORK) {
-        static_cast<Real *>(A.dst)[gi] = x[b];
-      } else if (A.dst_mode == DST_PAIR_SET || A.dst_mode == DST_PAIR_ADD) {
-        // FP32 passes only: the pair (hi, lo) += x with Knuth's TwoSum, renormalised
-        float hi = (float)x[b], lo = 0.0f;
-        if (A.dst_mode == DST_PAIR_ADD) {
-          const float a = __uint_as_float((unsigned)old[b]), alo = __uint_as_float((unsigned)(old[b] >> 32));
-          const float bb = hi;
-          const float s1 = __fadd_rn(a, bb), z = __fsub_rn(s1, a);
-          const float e = __fadd_rn(__fadd_rn(__fsub_rn(a, __fsub_rn(s1, z)), __fsub_rn(bb, z)), alo);
-          hi = __fadd_rn(s1, e);
-          lo = __fsub_rn(e, __fsub_rn(hi, s1));
-        }
-        static_cast<float2 *>(A.dst)[gi] = make_float2(hi, lo);
-        if (A.f64) A.f64[gi] = f2d_bits(hi) + f2d_bits(lo);
-      } else {
-        static_cast<double *>(A.dst)[gi] =
-            (A.dst_mode == DST_F64_SET) ? to_f64(x[b]) : __longlong_as_double((long long)old[b]) + to_f64(x[b]);
-      }
-    }
-  }
-}
-
-template <typename Real, int EMAX>
-__global__ void __launch_bounds__(kMaxPassThreads) axis_pass(PassArgs<Real> A) {
-  pdl_enter();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  axis_pass_body<Real, EMAX>(A, blockIdx.x, smem_raw);
-}
-
-// Batched pass: CTA b processes tile items[b].y of the pass described by args[items[b].x] (one
-// launch for every problem of a batch; each problem keeps its own tile shape).
-template <typename Real, int EMAX>
-__global__ void __launch_bounds__(kMaxPassThreads) axis_pass_batched(const PassArgs<Real> *__restrict__ args,
-                                                                     const int2 *__restrict__ items) {
-  pdl_enter();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(16) PassArgs<Real> A;
-  const int2 it = items[blockIdx.x];
-  {
-    const unsigned *src = reinterpret_cast<const unsigned *>(args + it.x);
-    unsigned *dst = reinterpret_cast<unsigned *>(&A);
-    for (int w = threadIdx.x; w < (int)(sizeof(PassArgs<Real>) / 4); w += blockDim.x) dst[w] = __ldg(src + w);
-  }
-  __syncthreads();
-  axis_pass_body<Real, EMAX>(A, it.y, smem_raw);
-}
 
 // ----------------------------------------------------------------------------- host side
 
@@ -411,15 +200,17 @@ static pc_status launch_pass(Plan *p, const PassSpec &ps, cudaStream_t st) {
   int threads;
   size_t smem;
   PC_TRY(build_pass<Real>(p, ps, A, tiles, threads, smem, 0));
-  switch (A.emax) {
-    case 1: case 2: launch_pdl(axis_pass<Real, 2>, (unsigned)tiles, threads, smem, st, A); break;
-    case 4: launch_pdl(axis_pass<Real, 4>, (unsigned)tiles, threads, smem, st, A); break;
-    case 8: launch_pdl(axis_pass<Real, 8>, (unsigned)tiles, threads, smem, st, A); break;
-    case 16: launch_pdl(axis_pass<Real, 16>, (unsigned)tiles, threads, smem, st, A); break;
-    default: return fail(PC_ERR_UNSUPPORTED, "no transform kernel for %d slots per thread", A.emax);
+  if constexpr (sizeof(Real) == 4) {
+    // FP32 passes: the instance of the axis's transform family (one translation unit each)
+    switch (kind_family(A.kind)) {
+      case 0: PC_TRY(launch_pass_f32_family0(A, tiles, threads, smem, st)); break;
+      case 1: PC_TRY(launch_pass_f32_family1(A, tiles, threads, smem, st)); break;
+      default: PC_TRY(launch_pass_f32_family2(A, tiles, threads, smem, st)); break;
+    }
+  } else {
+    PC_TRY((launch_axis_pass_spec<Real, -1, false>(A, tiles, threads, smem, st)));
   }
   count_launch(p);
-  PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
 }
 
@@ -443,14 +234,10 @@ template pc_status launch_batched_pass<double>(const PassArgs<double> *, const i
 // Kernel attributes set once per device, before any stream capture.
 pc_status prepare_kernels() {
   const int lim = 200 * 1024;
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  PC_TRY(prepare_pass_f32_family0(lim));
+  PC_TRY(prepare_pass_f32_family1(lim));
+  PC_TRY(prepare_pass_f32_family2(lim));
+  PC_TRY((prepare_axis_pass_spec<double, -1, false>(lim)));
   PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
