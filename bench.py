@@ -380,6 +380,9 @@ def run_ours(args, rank, world, local_rank):
     e2e = None if args.no_extras else run_e2e(plan, prob, stream, dev, steps, world)
     ib = None if args.no_extras else run_ib(plan, prob, u_dev, stream, dev, flush)
     variants = None if args.no_extras else run_variants(args, prob, u_dev, stream, dev, flush, ms_step=total_ms / steps)
+    cufft = None if args.no_extras else {"shape": list(prob.n[:prob.dim]),
+                                         "rfft_irfft_ms": round(cufft_reference(prob.n[:prob.dim], stream, dev, flush), 5),
+                                         "this_fp32_solve_ms": round(tune_ms, 5)}
 
     batch = None
     if not args.no_batch:
@@ -410,6 +413,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks, "cpu_baseline": cpu, "wall_s": round(wall, 3),
         "ib_iteration": ib,
         "variants": variants,
+        "cufft_reference": cufft,
         "batch_2d_512": batch,
         "box_sphere_3d": box3d,
     }
@@ -496,6 +500,25 @@ def run_ib(plan, prob, u_dev, stream, dev, flush, tol=1e-3, max_iters=50, reps=1
             "full_passes_ms": round(ms_full, 4), "speedup_vs_full_passes": round(ms_full / ms_graph, 3),
             "cells_per_s_per_time_step": round(prob.num_cells / (ms_graph * 1e-3), 1),
             "history_last": info["history"][-1]}
+
+
+def cufft_reference(shape, stream, dev, flush, reps=50):
+    """cuFFT (through torch.fft) on the pressure grid's shape: one forward real-to-complex and one
+    inverse transform of an FP32 array, the transform work of one FP32 solve (reference point
+    only; the library does not use it)."""
+    import torch
+    x = torch.randn(tuple(int(v) for v in shape), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        torch.fft.irfftn(torch.fft.rfftn(x), s=x.shape)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for k in range(reps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        torch.fft.irfftn(torch.fft.rfftn(x), s=x.shape)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    return sum(a.elapsed_time(b) for a, b in ev) / reps
 
 
 def run_variants(args, prob, u_dev, stream, dev, flush, ms_step, reps=50):
@@ -607,7 +630,8 @@ def run_3d(args, dev, stream, flush, world, rank):
            "unit": UNIT, "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4)},
            "phase_ms": {kk: round(v / calls, 5) for kk, v in prof["phase_ms"].items() if v > 0},
            "transform_slots": plan.slots(), "tuned_solve_ms": round(tune_ms, 4),
-           "generate_s": round(gen_s, 1), "plan_and_tune_s": round(setup_s, 1)}
+           "generate_s": round(gen_s, 1), "plan_and_tune_s": round(setup_s, 1),
+           "cufft_rfft_irfft_ms": round(cufft_reference(prob.n[:3], stream, dev, flush), 4)}
     if rank == 0 and not args.no_extras:
         ref = pc.Plan(prob, precision="fp64", device=dev.index)
         ro = ref.alloc_outputs()

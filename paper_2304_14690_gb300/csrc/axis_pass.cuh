@@ -1,11 +1,11 @@
 // Device code of the transform passes (§2.3 three-step solve): one axis pass over a tile of
 // lines in shared memory, as a single-problem kernel and as the batched kernel of
-// pc_project_batch. The single-problem kernel is specialised on the transform family of the axis
-// (KC: 0 real DFT, 1 DCT-II/DST-II, 2 DCT-IV/DST-IV; -1 any, chosen at run time) and on a
-// power-of-two line length (no radix-3/5 stages), so an instance holds the code of one family
-// only; the batched kernel mixes passes of any kind in one launch and stays generic. The
-// arithmetic is the same in every instance (the specialisation only removes branches), so
-// single and batched results stay bitwise equal.
+// pc_project_batch. Both are specialised on the transform family of the axis (KC: 0 real DFT,
+// 1 DCT-II/DST-II, 2 DCT-IV/DST-IV; -1 any, chosen at run time) and on a power-of-two line
+// length (no radix-3/5 stages), so an instance holds the code of one family only; a batched
+// pass is launched once per family present among its problems. The arithmetic is the same in
+// every instance (the specialisation only removes branches), so single and batched results
+// stay bitwise equal.
 #pragma once
 
 #include "fft.cuh"
@@ -23,7 +23,6 @@ __device__ __forceinline__ int pass_kind(int k) {
   if (KC == 2) return k == KIND_DN ? KIND_DN : KIND_ND;
   return k;
 }
-inline int kind_family(int k) { return k == KIND_PP ? 0 : ((k == KIND_NN || k == KIND_DD) ? 1 : 2); }
 
 // Source element gi in the pass precision (FP64 sources enter FP32 passes truncated to 24 bits,
 // by integer operations; the refinement corrects what that drops).
@@ -218,7 +217,7 @@ __global__ void __launch_bounds__(kMaxPassThreads) axis_pass(PassArgs<Real> A) {
 
 // Batched pass: CTA b processes tile items[b].y of the pass described by args[items[b].x] (one
 // launch for every problem of a batch; each problem keeps its own tile shape).
-template <typename Real, int EMAX>
+template <typename Real, int EMAX, int KC, bool POW2>
 __global__ void __launch_bounds__(kMaxPassThreads) axis_pass_batched(const PassArgs<Real> *__restrict__ args,
                                                                      const int2 *__restrict__ items) {
   pdl_enter();
@@ -231,7 +230,7 @@ __global__ void __launch_bounds__(kMaxPassThreads) axis_pass_batched(const PassA
     for (int w = threadIdx.x; w < (int)(sizeof(PassArgs<Real>) / 4); w += blockDim.x) dst[w] = __ldg(src + w);
   }
   __syncthreads();
-  axis_pass_body<Real, EMAX>(A, it.y, smem_raw);
+  axis_pass_body<Real, EMAX, KC, POW2>(A, it.y, smem_raw);
 }
 
 
@@ -249,6 +248,31 @@ pc_status launch_axis_pass_spec(const PassArgs<Real> &A, long long tiles, int th
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
 }
+// Batched launch over items whose passes all belong to family KC (and have power-of-two lines
+// when POW2); emax: the largest slots per thread among them.
+template <typename Real, int KC, bool POW2>
+pc_status launch_batched_spec(const PassArgs<Real> *dargs, const int2 *ditems, int nitems, int threads, size_t smem,
+                              int emax, cudaStream_t st) {
+  if (nitems <= 0) return PC_OK;
+  switch (emax) {
+    case 1: case 2: launch_pdl(axis_pass_batched<Real, 2, KC, POW2>, (unsigned)nitems, threads, smem, st, dargs, ditems); break;
+    case 4: launch_pdl(axis_pass_batched<Real, 4, KC, POW2>, (unsigned)nitems, threads, smem, st, dargs, ditems); break;
+    case 8: launch_pdl(axis_pass_batched<Real, 8, KC, POW2>, (unsigned)nitems, threads, smem, st, dargs, ditems); break;
+    case 16: launch_pdl(axis_pass_batched<Real, 16, KC, POW2>, (unsigned)nitems, threads, smem, st, dargs, ditems); break;
+    default: return fail(PC_ERR_UNSUPPORTED, "no batched transform kernel for %d slots per thread", emax);
+  }
+  PC_CUDA_TRY(cudaGetLastError());
+  return PC_OK;
+}
+template <typename Real, int KC, bool POW2>
+pc_status prepare_batched_spec(int lim) {
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<Real, 2, KC, POW2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<Real, 4, KC, POW2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<Real, 8, KC, POW2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<Real, 16, KC, POW2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  return PC_OK;
+}
+
 template <typename Real, int KC, bool POW2>
 pc_status prepare_axis_pass_spec(int lim) {
   PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass<Real, 2, KC, POW2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));

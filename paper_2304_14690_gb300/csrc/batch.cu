@@ -24,13 +24,16 @@ namespace {
 
 constexpr int kBatchThreads = 256;   // CTA size of the batched transform passes
 
+// One launch of a batched pass: the items of the problems whose pass on this axis belongs to one
+// transform family (and whose lines are all powers of two, or not).
 struct PassBatch {
-  int args_off = 0;      // index of the first PassArgs of this pass
   int items_off = 0;
   int nitems = 0;
   int threads = 0;
   size_t smem = 0;
   int emax = 1;          // largest slots per thread among the problems' passes
+  int family = 0;
+  bool pow2 = false;
 };
 
 struct Group {
@@ -147,9 +150,9 @@ pc_status build_group(Exec *e, Group &g) {
     }
     const size_t npass = specs[0].size();
     for (size_t k = 0; k < npass; ++k) {
-      PassBatch pb;
-      pb.args_off = (int)args.size();
-      pb.items_off = (int)items.size();
+      // pass k of every problem, launched once per (family, power-of-two) key present
+      PassBatch key_pb[6];
+      std::vector<int2> key_items[6];
       for (int i = 0; i < n; ++i) {
         PassArgs<float> A;
         long long tiles;
@@ -158,13 +161,23 @@ pc_status build_group(Exec *e, Group &g) {
         PC_TRY(build_pass<float>(e->plans[g.members[i]], specs[i][k], A, tiles, threads, smem, kBatchThreads));
         const int ai = (int)args.size();
         args.push_back(A);
-        for (long long t = 0; t < tiles; ++t) items.push_back(make_int2(ai, (int)t));
+        const int key = pass_family(A.kind) * 2 + (((A.M & (A.M - 1)) == 0) ? 1 : 0);
+        PassBatch &pb = key_pb[key];
+        for (long long t = 0; t < tiles; ++t) key_items[key].push_back(make_int2(ai, (int)t));
         pb.threads = std::max(pb.threads, threads);
         pb.smem = std::max(pb.smem, smem);
         pb.emax = std::max(pb.emax, A.emax);
+        pb.family = key / 2;
+        pb.pow2 = key & 1;
       }
-      pb.nitems = (int)items.size() - pb.items_off;
-      passes.push_back(pb);
+      for (int key = 0; key < 6; ++key) {
+        if (key_items[key].empty()) continue;
+        PassBatch pb = key_pb[key];
+        pb.items_off = (int)items.size();
+        pb.nitems = (int)key_items[key].size();
+        items.insert(items.end(), key_items[key].begin(), key_items[key].end());
+        passes.push_back(pb);
+      }
     }
     g.solves.push_back(passes);
   }
@@ -184,7 +197,8 @@ pc_status record_group(Exec *e, const Group &g, cudaStream_t st) {
   for (int j = 0; j <= g.sweeps; ++j) {
     if (j > 0) batch_launch(BATCH_RESIDUAL, 0, g.dP, seg(BATCH_RESIDUAL), n, g.total[BATCH_RESIDUAL], 0, st);
     for (const PassBatch &pb : g.solves[j])
-      PC_TRY(launch_batched_pass<float>(g.dargs, g.ditems + pb.items_off, pb.nitems, pb.threads, pb.smem, pb.emax, st));
+      PC_TRY(launch_batched_pass_f32(pb.family, pb.pow2, g.dargs, g.ditems + pb.items_off, pb.nitems, pb.threads,
+                                     pb.smem, pb.emax, st));
   }
   if (g.any_singular)
     batch_launch(BATCH_GAUGE_SUM, 0, g.dP, seg(BATCH_GAUGE_SUM), n, g.total[BATCH_GAUGE_SUM], 0, st);

@@ -74,10 +74,17 @@ pc_status launch_pass_f32_family2(const PassArgs<float> &A, long long tiles, int
 pc_status prepare_pass_f32_family0(int lim);
 pc_status prepare_pass_f32_family1(int lim);
 pc_status prepare_pass_f32_family2(int lim);
-// One launch of the batched pass kernel over items (args index, tile); emax: the largest slots
-// per thread among the items' passes (selects the kernel instance).
-template <typename Real>
-pc_status launch_batched_pass(const PassArgs<Real> *dargs, const int2 *ditems, int nitems, int threads,
-                              size_t smem, int emax, cudaStream_t st);
+// Batched FP32 passes of one family (pow2: every line length of the items is a power of two).
+pc_status launch_batched_f32_family0(const PassArgs<float> *dargs, const int2 *ditems, int nitems, int threads,
+                                     size_t smem, int emax, bool pow2, cudaStream_t st);
+pc_status launch_batched_f32_family1(const PassArgs<float> *dargs, const int2 *ditems, int nitems, int threads,
+                                     size_t smem, int emax, bool pow2, cudaStream_t st);
+pc_status launch_batched_f32_family2(const PassArgs<float> *dargs, const int2 *ditems, int nitems, int threads,
+                                     size_t smem, int emax, bool pow2, cudaStream_t st);
+inline int pass_family(int kind) { return kind == KIND_PP ? 0 : ((kind == KIND_NN || kind == KIND_DD) ? 1 : 2); }
+// One launch of the batched FP32 pass kernel over items (args index, tile) of one family;
+// emax: the largest slots per thread among the items' passes (selects the kernel instance).
+pc_status launch_batched_pass_f32(int family, bool pow2, const PassArgs<float> *dargs, const int2 *ditems,
+                                  int nitems, int threads, size_t smem, int emax, cudaStream_t st);
 
 }  // namespace pc

@@ -202,7 +202,7 @@ static pc_status launch_pass(Plan *p, const PassSpec &ps, cudaStream_t st) {
   PC_TRY(build_pass<Real>(p, ps, A, tiles, threads, smem, 0));
   if constexpr (sizeof(Real) == 4) {
     // FP32 passes: the instance of the axis's transform family (one translation unit each)
-    switch (kind_family(A.kind)) {
+    switch (pass_family(A.kind)) {
       case 0: PC_TRY(launch_pass_f32_family0(A, tiles, threads, smem, st)); break;
       case 1: PC_TRY(launch_pass_f32_family1(A, tiles, threads, smem, st)); break;
       default: PC_TRY(launch_pass_f32_family2(A, tiles, threads, smem, st)); break;
@@ -214,22 +214,12 @@ static pc_status launch_pass(Plan *p, const PassSpec &ps, cudaStream_t st) {
   return PC_OK;
 }
 
-template <typename Real>
-pc_status launch_batched_pass(const PassArgs<Real> *dargs, const int2 *ditems, int nitems, int threads,
-                              size_t smem, int emax, cudaStream_t st) {
-  if (nitems <= 0) return PC_OK;
-  switch (emax) {
-    case 1: case 2: launch_pdl(axis_pass_batched<Real, 2>, (unsigned)nitems, threads, smem, st, dargs, ditems); break;
-    case 4: launch_pdl(axis_pass_batched<Real, 4>, (unsigned)nitems, threads, smem, st, dargs, ditems); break;
-    case 8: launch_pdl(axis_pass_batched<Real, 8>, (unsigned)nitems, threads, smem, st, dargs, ditems); break;
-    case 16: launch_pdl(axis_pass_batched<Real, 16>, (unsigned)nitems, threads, smem, st, dargs, ditems); break;
-    default: return fail(PC_ERR_UNSUPPORTED, "no batched transform kernel for %d slots per thread", emax);
-  }
-  PC_CUDA_TRY(cudaGetLastError());
-  return PC_OK;
+pc_status launch_batched_pass_f32(int family, bool pow2, const PassArgs<float> *dargs, const int2 *ditems,
+                                  int nitems, int threads, size_t smem, int emax, cudaStream_t st) {
+  if (family == 0) return launch_batched_f32_family0(dargs, ditems, nitems, threads, smem, emax, pow2, st);
+  if (family == 1) return launch_batched_f32_family1(dargs, ditems, nitems, threads, smem, emax, pow2, st);
+  return launch_batched_f32_family2(dargs, ditems, nitems, threads, smem, emax, pow2, st);
 }
-template pc_status launch_batched_pass<float>(const PassArgs<float> *, const int2 *, int, int, size_t, int, cudaStream_t);
-template pc_status launch_batched_pass<double>(const PassArgs<double> *, const int2 *, int, int, size_t, int, cudaStream_t);
 
 // Kernel attributes set once per device, before any stream capture.
 pc_status prepare_kernels() {
@@ -238,10 +228,6 @@ pc_status prepare_kernels() {
   PC_TRY(prepare_pass_f32_family1(lim));
   PC_TRY(prepare_pass_f32_family2(lim));
   PC_TRY((prepare_axis_pass_spec<double, -1, false>(lim)));
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  PC_CUDA_TRY(cudaFuncSetAttribute(axis_pass_batched<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   return PC_OK;
 }
 
