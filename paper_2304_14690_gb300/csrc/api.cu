@@ -65,7 +65,8 @@ bool axis_length_supported(int n);
 pc_status prepare_kernels();
 
 void prof_begin(Plan *p, cudaStream_t st) {
-  if (p->capturing) {   // phase boundaries become event-record nodes of the graph
+  if (p->capturing) {   // phase boundaries become event-record nodes of a profiled graph
+    if (!p->cap_events) return;
     p->cap_n = 1;
     cudaEventRecordWithFlags(p->cap_ev[0], st, cudaEventRecordExternal);
     return;
@@ -79,7 +80,7 @@ void prof_begin(Plan *p, cudaStream_t st) {
 
 void prof_mark(Plan *p, cudaStream_t st, int tag) {
   if (p->capturing) {
-    if (p->cap_n >= kProfEvents) return;
+    if (!p->cap_events || p->cap_n >= kProfEvents) return;
     p->cap_tag[p->cap_n - 1] = tag;
     cudaEventRecordWithFlags(p->cap_ev[p->cap_n], st, cudaEventRecordExternal);
     p->cap_n++;

@@ -82,6 +82,7 @@ struct GraphEntry {
   int tag[kProfEvents];
   long long launches = 0;
   unsigned long long stamp = 0;
+  bool prof = false;      // captured with the profiler's event-record nodes
 };
 
 // IB-force iteration (pc_project_ib): the device-side state of one time step's loop, written by
@@ -181,6 +182,7 @@ struct Plan {
   GraphEntry graphs[kGraphCache];
   unsigned long long graph_clock = 0;
   bool capturing = false;
+  bool cap_events = false;     // the capture records the phase boundaries as event nodes
   cudaEvent_t cap_ev[kProfEvents];
   int cap_tag[kProfEvents];
   int cap_n = 0;

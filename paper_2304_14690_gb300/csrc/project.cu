@@ -1377,7 +1377,8 @@ static bool graph_cached(const Plan *p, double dt, const void *u, const void *f,
                          const void *uo, const void *fo) {
   for (int i = 0; i < kGraphCache; ++i) {
     const GraphEntry &c = p->graphs[i];
-    if (c.exec && c.u == u && c.f == f && c.p == po && c.uo == uo && c.fo == fo && c.dt == dt) return true;
+    if (c.exec && c.u == u && c.f == f && c.p == po && c.uo == uo && c.fo == fo && c.dt == dt && c.prof == p->prof)
+      return true;
   }
   return false;
 }
@@ -1389,7 +1390,8 @@ static pc_status project_graph(Plan *p, double dt, const void *u_star, const voi
   GraphEntry *e = nullptr;
   for (int i = 0; i < kGraphCache; ++i) {
     GraphEntry &c = p->graphs[i];
-    if (c.exec && c.u == u_star && c.f == f_in && c.p == p_out && c.uo == u_out && c.fo == f_out && c.dt == dt) {
+    if (c.exec && c.u == u_star && c.f == f_in && c.p == p_out && c.uo == u_out && c.fo == f_out && c.dt == dt &&
+        c.prof == p->prof) {
       e = &c;
       break;
     }
@@ -1404,6 +1406,10 @@ static pc_status project_graph(Plan *p, double dt, const void *u_star, const voi
     e->graph = nullptr;
     PC_CUDA_TRY(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
     p->capturing = true;
+    // event-record nodes at the phase boundaries only in a profiled graph: they are full
+    // dependencies and would cut the programmatic overlap between the kernels around them
+    p->cap_events = p->prof;
+    p->cap_n = 0;
     const long long l0 = p->launches;
     pc_status s = project_impl(p, dt, u_star, f_in, p_out, u_out, f_out, nullptr, p->cap_stream, true);
     cudaGraph_t g = nullptr;
@@ -1440,6 +1446,7 @@ static pc_status project_graph(Plan *p, double dt, const void *u_star, const voi
     }
     for (int i = 0; i + 1 < e->nev; ++i) e->tag[i] = p->cap_tag[i];
     e->u = u_star; e->f = f_in; e->p = p_out; e->uo = u_out; e->fo = f_out; e->dt = dt;
+    e->prof = p->prof;
   }
   e->stamp = ++p->graph_clock;
   if (p->prof && p->slots && p->slots_used < kProfSlots) {

@@ -180,6 +180,36 @@ def test_host_pointers_match_device(env, problems):
     plan.close()
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("graphs", [True, False])
+def test_host_arrays_pinned_and_pageable(env, problems, precision, graphs):
+    """Host arrays, page-locked or pageable, are staged through the plan's device buffers: every
+    path gives the bits of the device-array call, the call returns with the results in the host
+    arrays, and a repeated call with new input values in the same host arrays is right too."""
+    pc, torch, dev = env
+    prob, _, _ = problems[2]
+    plan = pc.Plan(prob, precision=precision)
+    plan.graphs(graphs)
+    u = torch.as_tensor(prob.u_star, device=dev)
+    f = torch.as_tensor(prob.f_ib, device=dev)
+    ref = [t.cpu() for t in plan.project(u, f)[:3]]
+    ref2 = [t.cpu() for t in plan.project(u * 0.5, f)[:3]]
+    hu = torch.as_tensor(prob.u_star).pin_memory()
+    hf = torch.as_tensor(prob.f_ib).pin_memory()
+    outs = (torch.empty(prob.n[: prob.dim], dtype=torch.float64).pin_memory(),
+            torch.empty_like(hu).pin_memory(), torch.empty_like(hu).pin_memory())
+    got = plan.project(hu, hf, out=outs)[:3]
+    assert all(torch.equal(a, b) for a, b in zip(got, ref))
+    hu.mul_(0.5)
+    got = plan.project(hu, hf, out=outs)[:3]
+    assert all(torch.equal(a, b) for a, b in zip(got, ref2))
+    pu = torch.as_tensor(prob.u_star).clone()            # pageable: staged
+    pouts = (torch.empty(prob.n[: prob.dim], dtype=torch.float64), torch.empty_like(pu), torch.empty_like(pu))
+    got = plan.project(pu, torch.as_tensor(prob.f_ib).clone(), out=pouts)[:3]
+    assert all(torch.equal(a, b) for a, b in zip(got, ref))
+    plan.close()
+
+
 def test_graph_equals_direct(env, problems):
     """The cached CUDA-graph path gives bitwise the same results as direct launches, also after
     the arguments change (new capture) and when they come back (cache hit)."""
