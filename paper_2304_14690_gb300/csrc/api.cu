@@ -118,6 +118,9 @@ static void destroy_plan(Plan *p) {
   if (p->cap_ev_made)
     for (int e = 0; e < kProfEvents; ++e) cudaEventDestroy(p->cap_ev[e]);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->copy_st) cudaStreamDestroy(p->copy_st);
+  for (int e = 0; e < 3; ++e)
+    if (p->copy_ev[e]) cudaEventDestroy(p->copy_ev[e]);
   if (p->ib_body_stream) cudaStreamDestroy(p->ib_body_stream);
   for (int i = 0; i < p->nallocs; ++i) cudaFree(p->allocs[i]);
   if (cur >= 0) cudaSetDevice(cur);

@@ -150,6 +150,9 @@ struct Plan {
   unsigned int *counters = nullptr;  // completion counters of those reductions (kept at zero)
   // Staging for host pointers passed to pc_project.
   void *stage_u = nullptr, *stage_f = nullptr, *stage_uo = nullptr, *stage_fo = nullptr;
+  // copy stream and events of the host-array path (results copied back while kernels run)
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t copy_ev[3] = {nullptr, nullptr, nullptr};
   double *stage_p = nullptr, *stage_s = nullptr;
   // IB-force iteration (pc_project_ib), built on its first call: the boundary/virtual nodes,
   // per axis the faces whose value row reaches one of them (the only fluxes that change after

@@ -11,6 +11,7 @@
 //  gradient    g = sum_k D_k p_k at every node, then Eq. 4 at fluid nodes and Eqs. 18-19 at
 //              boundary/virtual nodes
 //  check       max |D_h (U - beta dt G_h p)| (only when statistics are requested)
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstddef>
@@ -628,9 +629,9 @@ __global__ void gradient64_kernel(int N, int K, const int32_t *__restrict__ col,
                                   const double *__restrict__ D, const double *__restrict__ p,
                                   const uint8_t *__restrict__ type, const VT *__restrict__ u,
                                   double inv_dt, double dt, double beta, VT *__restrict__ uo,
-                                  VT *__restrict__ fo) {
+                                  VT *__restrict__ fo, int b0) {
   pdl_enter();
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = (blockIdx.x + b0) * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double g[DIM];
   grad64_at<DIM>(i, N, K, col, D, p, g);
@@ -699,9 +700,11 @@ __global__ void gradient_mixed_kernel(int N, int K, const int32_t *__restrict__ 
                                       const float2 *__restrict__ D2, const float2 *__restrict__ p2,
                                       const uint8_t *__restrict__ type, const VT *__restrict__ u,
                                       double inv_dt, double dt, double beta, VT *__restrict__ uo,
-                                      VT *__restrict__ fo) {
+                                      VT *__restrict__ fo, int b0) {
   pdl_enter();
-  gradient_mixed_kernel_body<VT, DIM>(hw_block(), N, K, col, D2, p2, type, u, inv_dt, dt, beta, uo, fo);
+  VBlock vb = hw_block();
+  vb.x += (unsigned)b0;
+  gradient_mixed_kernel_body<VT, DIM>(vb, N, K, col, D2, p2, type, u, inv_dt, dt, beta, uo, fo);
 }
 
 // ----------------------------------------------------------------------------- check
@@ -1215,27 +1218,30 @@ static pc_status fill_stats(Plan *p, pc_stats *stats, cudaStream_t st) {
 
 // Gradient and correction at every node (Eq. 4 at fluid nodes, Eqs. 18-19 at boundary/virtual
 // nodes) from the solved pressure: p2 pairs (mixed) or the FP64 p in dp.
+// Blocks [b0, b0 + nb) of the node grid (nb < 0: all from b0).
 static void launch_gradient(Plan *p, cudaStream_t st, const double *dp, const void *ug, double dt, void *duo,
-                            void *dfo) {
+                            void *dfo, int b0 = 0, int nb = -1) {
   const int T = 256;
   const long long N = p->N;
   const int d = p->dim;
   const bool mixed = p->precision != PC_PREC_FP64;
+  const int G = nb < 0 ? grid_for(N, T) - b0 : nb;
+  if (G <= 0) return;
   if (p->vdtype == PC_DTYPE_F64) {
     if (mixed) {
-      if (d == 2) launch_pdl(gradient_mixed_kernel<double, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
-      else launch_pdl(gradient_mixed_kernel<double, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
+      if (d == 2) launch_pdl(gradient_mixed_kernel<double, 2>, G, T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo, b0);
+      else launch_pdl(gradient_mixed_kernel<double, 3>, G, T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo, b0);
     } else {
-      if (d == 2) launch_pdl(gradient64_kernel<double, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
-      else launch_pdl(gradient64_kernel<double, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo);
+      if (d == 2) launch_pdl(gradient64_kernel<double, 2>, G, T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo, b0);
+      else launch_pdl(gradient64_kernel<double, 3>, G, T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const double *)ug, 1.0 / dt, dt, p->beta, (double *)duo, (double *)dfo, b0);
     }
   } else {
     if (mixed) {
-      if (d == 2) launch_pdl(gradient_mixed_kernel<float, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
-      else launch_pdl(gradient_mixed_kernel<float, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
+      if (d == 2) launch_pdl(gradient_mixed_kernel<float, 2>, G, T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo, b0);
+      else launch_pdl(gradient_mixed_kernel<float, 3>, G, T, 0, st, (int)N, p->Kg, p->ncol, p->nD2, p->p2, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo, b0);
     } else {
-      if (d == 2) launch_pdl(gradient64_kernel<float, 2>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
-      else launch_pdl(gradient64_kernel<float, 3>, grid_for(N, T), T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo);
+      if (d == 2) launch_pdl(gradient64_kernel<float, 2>, G, T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo, b0);
+      else launch_pdl(gradient64_kernel<float, 3>, G, T, 0, st, (int)N, p->Kg, p->ncol, p->nD64, dp, p->ntype, (const float *)ug, 1.0 / dt, dt, p->beta, (float *)duo, (float *)dfo, b0);
     }
   }
 }
@@ -1326,7 +1332,43 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   PC_TRY(solve_grid(p, p->s64, dp, stats != nullptr, st,
                     mixed ? reinterpret_cast<const float *>(p->work64) : nullptr,
                     mixed ? reinterpret_cast<const float2 *>(p->s64) : nullptr));
-  launch_gradient(p, st, dp, du, dt, duo, dfo);
+  // Host results: the pressure is final here, so its copy runs on the plan's copy stream while
+  // the gradient computes; the gradient runs in two halves and the first half's u and f are
+  // copied while the second half computes (copy engines and kernels overlap).
+  const bool host_out = hp || huo || (f_out && hfo);
+  if (host_out && !p->copy_st) {
+    PC_CUDA_TRY(cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking));
+    for (int e = 0; e < 3; ++e) PC_CUDA_TRY(cudaEventCreateWithFlags(&p->copy_ev[e], cudaEventDisableTiming));
+  }
+  if (hp) {
+    PC_CUDA_TRY(cudaEventRecord(p->copy_ev[0], st));
+    PC_CUDA_TRY(cudaStreamWaitEvent(p->copy_st, p->copy_ev[0], 0));
+    PC_CUDA_TRY(cudaMemcpyAsync(p_out, dp, nc * sizeof(double), cudaMemcpyDeviceToHost, p->copy_st));
+  }
+  const int gblocks = grid_for(N, 256);
+  const bool split = (huo || (f_out && hfo)) && gblocks >= 2;
+  const int b1 = gblocks / 2;
+  const long long n1 = split ? std::min(N, (long long)b1 * 256) : 0;   // nodes of the first half
+  auto copy_nodes = [&](long long i0, long long i1, cudaStream_t cs) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    for (int a = 0; a < d && e == cudaSuccess && i1 > i0; ++a) {
+      const size_t off = ((size_t)a * N + i0) * vsz, len = (size_t)(i1 - i0) * vsz;
+      if (huo) e = cudaMemcpyAsync((char *)u_out + off, (const char *)duo + off, len, cudaMemcpyDeviceToHost, cs);
+      if (e == cudaSuccess && f_out && hfo)
+        e = cudaMemcpyAsync((char *)f_out + off, (const char *)dfo + off, len, cudaMemcpyDeviceToHost, cs);
+    }
+    return e;
+  };
+  if (split) {
+    launch_gradient(p, st, dp, du, dt, duo, dfo, 0, b1);
+    count_launch(p);
+    PC_CUDA_TRY(cudaEventRecord(p->copy_ev[1], st));
+    PC_CUDA_TRY(cudaStreamWaitEvent(p->copy_st, p->copy_ev[1], 0));
+    PC_CUDA_TRY(copy_nodes(0, n1, p->copy_st));
+    launch_gradient(p, st, dp, du, dt, duo, dfo, b1, -1);
+  } else {
+    launch_gradient(p, st, dp, du, dt, duo, dfo);
+  }
   count_launch(p);
   prof_mark(p, st, 6);
   if (stats && p->divmode == PC_DIV_FACES) {   // no face fluxes in the direct mode
@@ -1336,9 +1378,12 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
     prof_mark(p, st, 7);
   }
   PC_CUDA_TRY(cudaGetLastError());
-  if (hp) PC_CUDA_TRY(cudaMemcpyAsync(p_out, dp, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
-  if (huo) PC_CUDA_TRY(cudaMemcpyAsync(u_out, duo, vbytes, cudaMemcpyDeviceToHost, st));
-  if (f_out && hfo) PC_CUDA_TRY(cudaMemcpyAsync(f_out, dfo, vbytes, cudaMemcpyDeviceToHost, st));
+  if (split) PC_CUDA_TRY(copy_nodes(n1, N, st));
+  else PC_CUDA_TRY(copy_nodes(0, N, st));
+  if (host_out) {   // join the copy stream
+    PC_CUDA_TRY(cudaEventRecord(p->copy_ev[2], p->copy_st));
+    PC_CUDA_TRY(cudaStreamWaitEvent(st, p->copy_ev[2], 0));
+  }
   if (stats) PC_TRY(fill_stats(p, stats, st));
   if (hp || huo || (f_out && hfo)) PC_CUDA_TRY(cudaStreamSynchronize(st));
   return PC_OK;
