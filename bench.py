@@ -414,7 +414,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "grid": list(prob.n), "nodes": prob.num_nodes,
                    "precision": args.precision, "refine_iters": args.refine,
                    "knn": prob.knn, "l2": "256 MB buffer written between timed steps",
-                   "transform_slots": plan.slots(), "tuned_solve_ms": round(tune_ms, 5),
+                   "transform_slots": plan.slots(), "transform_ctas_per_sm": plan.ctas(),
+                   "tuned_solve_ms": round(tune_ms, 5),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "latency_ms": {"p50": round(p50, 5), "p99": round(p99, 5)},
         "roofline": roofline, "roofline_transform": roofline_transform,

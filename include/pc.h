@@ -311,8 +311,17 @@ pc_status pc_plan_set_transform_slots(pc_plan *plan, int axis, pc_precision prec
 pc_status pc_plan_get_transform_slots(const pc_plan *plan, int axis, pc_precision precision,
                                       int *slots_out);
 
+/* Tile size of the single-problem passes along `axis`: the number of lines per CTA is halved
+ * until the pass has at least ctas_per_sm x 152 CTAs (1, 2, 4 or 8; default 2). Part of the
+ * schedule like the slots: it drops the plan's graphs, leaves batched calls (whose tiles fill a
+ * fixed CTA) alone, and does not change results (each line is transformed the same way in any
+ * tile). Errors: PC_ERR_INVALID_ARG for a bad axis or count. */
+pc_status pc_plan_set_transform_ctas(pc_plan *plan, int axis, pc_precision precision, int ctas_per_sm);
+pc_status pc_plan_get_transform_ctas(const pc_plan *plan, int axis, pc_precision precision, int *ctas_out);
+
 /* Autotuner: times the plan's own transform solve (FP64 for FP64 plans, FP32 otherwise) on
- * `cuda_stream` for every slot count of every axis in turn (coordinate descent, two rounds),
+ * `cuda_stream` for every slot count and every CTA target of every axis in turn (coordinate
+ * descent, two rounds),
  * keeps the fastest schedule and returns its milliseconds per solve in *best_ms_out
  * (nullable). It synchronises the stream, overwrites the plan's workspace, and must not run
  * during a stream capture or while a call of the plan is in flight. */

@@ -28,6 +28,7 @@ struct AxisInfo {
   // they fix the threads per line and the radix schedule (see build_pass), chosen when the
   // plan is built and shared by single and batched calls.
   int slots32 = 4, slots64 = 2;
+  int ctas32 = 2, ctas64 = 2;    // CTAs per SM the single-problem passes aim for (tile lines)
   double h = 0.0;
   double L = 0.0;   // n * h
   bool periodic = false;

@@ -143,7 +143,8 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   const int max_threads = batch_threads > 0 ? batch_threads : 256;
   const int max_lines = max_threads / tpl > 0 ? max_threads / tpl : 1;
   const int budget = 8192;          // complex slots per tile (two buffers: 2 x 64 KB in FP32)
-  const int want_ctas = 2 * 152;    // two CTAs per SM on both dies
+  // CTAs per SM the tile size aims for (part of the plan's schedule; 152 SMs on both dies)
+  const int want_ctas = ((sizeof(Real) == 8) ? ax.ctas64 : ax.ctas32) * 152;
   int L;
   if (A.col) {
     // 32-byte row segments when the grid allows it, fewer lines when CTAs would be too few

@@ -15,6 +15,10 @@ static bool valid_slots(int s) { return s == 2 || s == 4 || s == 8 || s == 16; }
 static int &slots_ref(Plan *p, int axis, bool fp64) {
   return fp64 ? p->ax[axis].slots64 : p->ax[axis].slots32;
 }
+static int &ctas_ref(Plan *p, int axis, bool fp64) {
+  return fp64 ? p->ax[axis].ctas64 : p->ax[axis].ctas32;
+}
+static bool valid_ctas(int c) { return c == 1 || c == 2 || c == 4 || c == 8; }
 
 // One solve of the plan's transform precision from s64 into the staging buffer.
 static pc_status run_solve(Plan *p, bool fp64, cudaStream_t st) {
@@ -56,24 +60,27 @@ static pc_status autotune(Plan *p, cudaStream_t st, double *best_out) {
   for (int round = 0; round < 2 && status == PC_OK; ++round) {
     bool changed = false;
     for (int a = 0; a < p->dim && status == PC_OK; ++a) {
-      int &s = slots_ref(p, a, fp64);
-      for (int cand : {2, 4, 8, 16}) {
-        if (cand == s) continue;
-        const int keep = s;
-        s = cand;
-        float t = 0.0f;
-        const pc_status r = time_solve(p, fp64, st, e0, e1, reps, t);
-        if (r != PC_OK) {
-          // a schedule the kernels cannot run (a tile too large): not a candidate
-          cudaGetLastError();
-          s = keep;
-          continue;
-        }
-        if (t < 0.98f * best) {
-          best = t;
-          changed = true;
-        } else {
-          s = keep;
+      // the two knobs of the axis in turn: slots per thread, then CTAs per SM
+      for (int knob = 0; knob < 2; ++knob) {
+        int &s = knob == 0 ? slots_ref(p, a, fp64) : ctas_ref(p, a, fp64);
+        for (int cand : {1, 2, 4, 8, 16}) {
+          if (cand == s || (knob == 0 ? !valid_slots(cand) : !valid_ctas(cand))) continue;
+          const int keep = s;
+          s = cand;
+          float t = 0.0f;
+          const pc_status r = time_solve(p, fp64, st, e0, e1, reps, t);
+          if (r != PC_OK) {
+            // a schedule the kernels cannot run (a tile too large): not a candidate
+            cudaGetLastError();
+            s = keep;
+            continue;
+          }
+          if (t < 0.98f * best) {
+            best = t;
+            changed = true;
+          } else {
+            s = keep;
+          }
         }
       }
     }
@@ -104,6 +111,25 @@ extern "C" pc_status pc_plan_get_transform_slots(const pc_plan *plan, int axis, 
   if (!p || !slots_out) return pc::fail(PC_ERR_INVALID_ARG, "plan and slots_out are required");
   if (axis < 0 || axis >= p->dim) return pc::fail(PC_ERR_INVALID_ARG, "axis %d out of range", axis);
   *slots_out = pc::slots_ref(p, axis, precision == PC_PREC_FP64);
+  return PC_OK;
+}
+
+extern "C" pc_status pc_plan_set_transform_ctas(pc_plan *plan, int axis, pc_precision precision, int ctas_per_sm) {
+  pc::Plan *p = reinterpret_cast<pc::Plan *>(plan);
+  if (!p) return pc::fail(PC_ERR_INVALID_ARG, "plan is NULL");
+  if (axis < 0 || axis >= p->dim) return pc::fail(PC_ERR_INVALID_ARG, "axis %d out of range", axis);
+  if (!pc::valid_ctas(ctas_per_sm)) return pc::fail(PC_ERR_INVALID_ARG, "ctas_per_sm must be 1, 2, 4 or 8 (got %d)", ctas_per_sm);
+  pc::ctas_ref(p, axis, precision == PC_PREC_FP64) = ctas_per_sm;
+  pc::plan_drop_graphs(p);
+  return PC_OK;
+}
+
+extern "C" pc_status pc_plan_get_transform_ctas(const pc_plan *plan, int axis, pc_precision precision,
+                                                int *ctas_out) {
+  pc::Plan *p = const_cast<pc::Plan *>(reinterpret_cast<const pc::Plan *>(plan));
+  if (!p || !ctas_out) return pc::fail(PC_ERR_INVALID_ARG, "plan and ctas_out are required");
+  if (axis < 0 || axis >= p->dim) return pc::fail(PC_ERR_INVALID_ARG, "axis %d out of range", axis);
+  *ctas_out = pc::ctas_ref(p, axis, precision == PC_PREC_FP64);
   return PC_OK;
 }
 

@@ -127,6 +127,9 @@ FUNCTIONS = {
     "pc_plan_set_transform_slots": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "pc_plan_get_transform_slots": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                    ctypes.POINTER(ctypes.c_int)]),
+    "pc_plan_set_transform_ctas": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "pc_plan_get_transform_ctas": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.POINTER(ctypes.c_int)]),
     "pc_plan_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "pc_batcher_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "pc_batcher_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
@@ -288,9 +291,22 @@ class Plan:
             out.append(v.value)
         return out
 
+    def set_ctas(self, axis, ctas_per_sm, precision=None):
+        """CTAs per SM the single-problem passes along axis aim for (1, 2, 4 or 8)."""
+        _check(load().pc_plan_set_transform_ctas(self.handle, axis, self._prec_code(precision), ctas_per_sm))
+
+    def ctas(self, precision=None):
+        """Current CTA target of every axis for the given (default: the plan's) precision."""
+        out = []
+        for a in range(self.dim):
+            v = ctypes.c_int()
+            _check(load().pc_plan_get_transform_ctas(self.handle, a, self._prec_code(precision), ctypes.byref(v)))
+            out.append(v.value)
+        return out
+
     def autotune(self, stream=None):
-        """Time the plan's transform solve for every slot count of every axis and keep the
-        fastest schedule; returns its milliseconds per solve."""
+        """Time the plan's transform solve for every slot count and CTA target of every axis
+        and keep the fastest schedule; returns its milliseconds per solve."""
         ms = ctypes.c_double()
         _check(load().pc_plan_autotune(self.handle, _stream_handle(stream), ctypes.byref(ms)))
         return ms.value

@@ -529,3 +529,41 @@ def test_project_direct_divergence_matches_oracle(env, problems, precision, tol)
             for name, got, want in (("p", pi, rib["p"]), ("u", ui, rib["u"]), ("f", fi, rib["f"])):
                 assert rel(got.cpu().numpy(), want) <= tol, (precision, k, "ib", name)
         plan.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_schedule_knobs(env, problems, precision):
+    """The transform schedule: every slot count gives the oracle's result within tolerance
+    (results change only by rounding between schedules), the CTA target changes nothing at all
+    (each line is transformed the same way in any tile), a batch call agrees bitwise with the
+    single call under any schedule, and bad values are refused."""
+    pc, torch, dev = env
+    tol = 1e-12 if precision == "fp64" else 1e-10
+    for k in (1, 6):
+        prob, _, ref = problems[k]
+        plan = pc.Plan(prob, precision=precision)
+        u = torch.as_tensor(prob.u_star, device=dev)
+        f = torch.as_tensor(prob.f_ib, device=dev)
+        for slots in (2, 4, 8, 16):
+            for a in range(prob.dim):
+                plan.set_slots(a, slots)
+            base = None
+            for ctas in (1, 2, 4, 8):
+                for a in range(prob.dim):
+                    plan.set_ctas(a, ctas)
+                got = [t.clone() for t in plan.project(u, f)[:3]]
+                if base is None:
+                    base = got
+                    assert rel(got[0].cpu().numpy(), ref["p"]) <= tol, (k, slots)
+                else:
+                    assert all(torch.equal(x, y) for x, y in zip(got, base)), (k, slots, ctas)
+            if precision == "mixed":
+                outs = plan.alloc_outputs()
+                pc.project_batch([plan], [dict(dt=prob.dt, u_star=u, f_ib=f, p=outs[0], u=outs[1], f=outs[2])])
+                torch.cuda.synchronize()
+                assert all(torch.equal(x, y) for x, y in zip(outs, base)), (k, slots)
+        assert plan.ctas() == [8] * prob.dim
+        for bad in (0, 3, 16):
+            with pytest.raises(pc.PcError):
+                plan.set_ctas(0, bad)
+        plan.close()
