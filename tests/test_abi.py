@@ -73,6 +73,9 @@ def _desc(**over):
     (dict(refine_iters=99), 1),
     (dict(wls_eps=-1.0), 1),
     (dict(node_xyz=None), 1),
+    (dict(eigenvalues=2), 1),                        # neither FD nor pseudo-spectral
+    (dict(eigenvalues=1, precision=1), 2),           # pseudo-spectral with the mixed refinement
+    (dict(divergence=5), 1),                         # neither MAC faces nor direct WLS
 ])
 def test_descriptor_validation(lib, over, status):
     d, keep = _desc(**over)
