@@ -121,7 +121,9 @@ typedef struct {
   int divergence;           /* pc_divergence */
 } pc_problem_desc;
 
-/* Per-call diagnostics (optional). Filling it synchronizes the stream. */
+/* Per-call diagnostics (optional). Filling it synchronizes the stream, and a NaN or infinity that
+ * reached the source (through u_star, f_ib_in or dt) is then reported as PC_ERR_INVALID_ARG, with
+ * the statistics filled. Without stats nothing is checked. */
 typedef struct {
   double removed_mean;      /* mean of the source dropped by the compatibility projection */
   double source_norm;       /* ||s||_2 over cells */
@@ -181,6 +183,8 @@ pc_status pc_project(pc_plan *plan, double dt, const void *u_star, const void *f
  * (PC_ERR_INVALID_ARG on a capturing stream). The first call on a plan builds the node and face
  * lists (one allocation: about 4 bytes per listed node or face, two force iterates, 16 KB of
  * loop state). */
+/* A non-finite stopping sum in any pass (a diverging iteration, or a NaN or infinity in the
+ * input) returns PC_ERR_NOT_CONVERGED after result and history are filled. */
 typedef struct {
   int iterations;
   int converged;

@@ -1213,6 +1213,9 @@ static pc_status fill_stats(Plan *p, pc_stats *stats, cudaStream_t st) {
   stats->max_abs_u_star = ds.max_u;
   int gmode = p->singular ? (p->gauge == 1 ? 2 : 1) : 0;
   stats->gauge_shift = gmode == 1 ? ds.sum_p / nc : (gmode == 2 ? ds.corner_p : 0.0);
+  // a NaN or infinity anywhere in u~ reaches the source sums (the maxima above skip NaN)
+  if (!std::isfinite(ds.sum_s) || !std::isfinite(ds.sum_s2))
+    return fail(PC_ERR_INVALID_ARG, "non-finite source: u_star, f_ib_in or dt hold a NaN or infinity");
   return PC_OK;
 }
 
@@ -1829,6 +1832,10 @@ static pc_status project_ib_impl(Plan *p, double dt, const VT *du, const VT *f_i
     res->diff = h.it ? h.hist[2 * (h.it - 1)] : 0.0;
     res->prev = h.it ? h.hist[2 * (h.it - 1) + 1] : 0.0;
   }
+  for (int k = 0; k < 2 * h.it; ++k)
+    if (!std::isfinite(h.hist[k]))
+      return fail(PC_ERR_NOT_CONVERGED, "the IB force is not finite after pass %d (diverged, or non-finite input)",
+                  k / 2 + 1);
   return PC_OK;
 }
 

@@ -567,3 +567,25 @@ def test_schedule_knobs(env, problems, precision):
             with pytest.raises(pc.PcError):
                 plan.set_ctas(0, bad)
         plan.close()
+
+
+def test_non_finite_input_reported(env, problems):
+    """Device-detected non-finite data come back as a status, and the plan stays usable: a NaN in
+    u* makes a projection with statistics return PC_ERR_INVALID_ARG and the IB iteration
+    PC_ERR_NOT_CONVERGED; the next call with finite data is right."""
+    pc, torch, dev = env
+    prob, _, ref = problems[1]
+    plan = pc.Plan(prob, precision="mixed")
+    u = torch.as_tensor(prob.u_star, device=dev)
+    f = torch.as_tensor(prob.f_ib, device=dev)
+    bad = u.clone()
+    bad[0, 5] = float("nan")
+    with pytest.raises(pc.PcError) as e:
+        plan.project(bad, f, stats=True)
+    assert e.value.status == 1
+    with pytest.raises(pc.PcError) as e:
+        plan.project_ib(bad, tol=1e-3, max_iters=5)
+    assert e.value.status == 7
+    p, uo, fo, st = plan.project(u, f, stats=True)
+    assert rel(p.cpu().numpy(), ref["p"]) <= 1e-10
+    plan.close()
