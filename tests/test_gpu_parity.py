@@ -589,3 +589,35 @@ def test_non_finite_input_reported(env, problems):
     p, uo, fo, st = plan.project(u, f, stats=True)
     assert rel(p.cpu().numpy(), ref["p"]) <= 1e-10
     plan.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-10)])
+def test_fp32_velocity_storage(env, precision, tol):
+    """Velocity arrays stored in FP32 (as the 3D workload has them): projections, the IB
+    iteration and the direct divergence against the oracle run on the same FP32 values promoted
+    to FP64. p is computed in full precision from the FP32 input (tol); u and f are stored in
+    FP32, so they agree to FP32 rounding."""
+    pc, torch, dev = env
+    f32 = 2.0 ** -23
+    for k in IB_CASES:
+        c = CASES[k]
+        prob = wl.generic(seed=300 + k, with_force=True, dtype=np.float32, **c)
+        oplan = PR.build_plan(grid_of(prob), prob.nodes, prob.node_type, K=prob.knn)
+        u64 = prob.u_star.astype(np.float64)
+        fm = _masked(prob, prob.f_ib.astype(np.float64))
+        u = torch.as_tensor(prob.u_star, device=dev)
+        f = torch.as_tensor(_masked(prob, prob.f_ib), device=dev)
+        for div_mode in ("faces", "wls_direct"):
+            plan = pc.Plan(prob, precision=precision, div_mode=div_mode)
+            ref = PR.project(oplan, prob.dt, u64, fm, div_mode=div_mode)
+            p, uo, fo, _ = plan.project(u, f)
+            assert uo.dtype == torch.float32
+            assert rel(p.cpu().numpy(), ref["p"]) <= tol, (precision, k, div_mode)
+            assert rel(uo.cpu().numpy(), ref["u"]) <= f32 and rel(fo.cpu().numpy(), ref["f"]) <= f32
+            rib = PR.project_ib(oplan, prob.dt, u64, fm, tol=0.0, max_iters=3, div_mode=div_mode)
+            pi, ui, fi, info = plan.project_ib(u, f_init=f, tol=0.0, max_iters=3)
+            assert info["iterations"] == 3
+            # the force iterates are stored in FP32 between passes: FP32-level agreement
+            assert rel(pi.cpu().numpy(), rib["p"]) <= 1e-5, (precision, k, div_mode)
+            assert rel(fi.cpu().numpy(), rib["f"]) <= 1e-5 and rel(ui.cpu().numpy(), rib["u"]) <= 1e-5
+            plan.close()
