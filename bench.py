@@ -603,6 +603,41 @@ def run_variants(args, prob, u_dev, stream, dev, flush, ms_step, reps=50):
     ms_mk, _ = timed(mk)
     mk.close()
     out["rhs_mask"] = {"ms_per_step": round(ms_mk, 5), "masked_cells": int(inside.sum())}
+
+    def timed_solve(plan):
+        gen = torch.Generator(device=dev).manual_seed(5)
+        src = torch.randn(plan.shape, dtype=torch.float64, device=dev, generator=gen)
+        dst = torch.empty_like(src)
+        for _ in range(3):
+            plan.solve_poisson(src, dst)
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for k in range(reps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            plan.solve_poisson(src, dst, stream=stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        return sum(a.elapsed_time(b) for a, b in ev) / reps
+
+    # the regular (vertex) grid: the 400x400 periodic grid of the cylinder results, and an all-wall
+    # 512x512 vertex grid (513^2 unknowns, solved as its 1024^2 even extension), each against the
+    # cell-centred solve of the same cells
+    vert = {}
+    for tag, n, lo, hi in (("periodic_400x400", (400, 400), ("P", "P"), ("P", "P")),
+                           ("walls_512x512", (512, 512), ("W", "W"), ("W", "W"))):
+        hh = (1.0 / n[0], 1.0 / n[1])
+        row = {}
+        for gt in ("vertices", "cells"):
+            gp = pc.GridPlan(2, n, hh, lo, hi, grid_type=gt, precision=args.precision,
+                             refine_iters=args.refine, device=dev.index)
+            gp.autotune()
+            row[gt + "_ms"] = round(timed_solve(gp), 5)
+            if gt == "vertices":
+                row["unknowns"] = int(np.prod(gp.shape))
+            gp.close()
+        vert[tag] = row
+    out["vertex_grid_solve"] = vert
     return out
 
 

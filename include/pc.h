@@ -243,10 +243,48 @@ pc_status pc_batcher_destroy(pc_batcher *batcher);
  * not need to. pc_solve_poisson takes its source as given (no mask). A clone starts unmasked. */
 pc_status pc_plan_set_rhs_mask(pc_plan *plan, const uint8_t *mask, void *cuda_stream);
 
+/* Grid-only plans: the Poisson solve of §2.3 without nodes, on the cell centres of the grid
+ * (PC_GRID_CELLS, as in every pc_plan_create plan) or on its vertices (PC_GRID_VERTICES: the
+ * "regular" grid of §2.3, used for the results of §3.2). On a vertex grid with n cells per axis
+ * the unknowns of an axis are, per boundary pair (lo-hi): P-P vertices 0..n-1; N-N 0..n (mirror
+ * ghosts p_{-1} = p_1, p_{n+1} = p_{n-1}); D-D 1..n-1 (p_0 = p_n = 0); N-D 0..n-1 (p_n = 0);
+ * D-N 1..n (p_0 = 0). The eigenbases are DCT-I (N-N), DST-I (D-D) and the quarter-wave
+ * cosine/sine pairs (N-D, D-N); they are computed as the real DFT of the source extended evenly
+ * about Neumann ends and oddly about Dirichlet ends, i.e. the periodic cell-grid solve of 2n
+ * (N-N, D-D) or 4n (N-D, D-N) cells per axis, whose length must satisfy the transform limits
+ * (even, half of it 2^a 3^b 5^c <= 2048). When every axis is P-P or N-N the constant mode is
+ * dropped (on N-N axes it is the trapezoid-weighted mean) and reported in removed_mean; the
+ * corner gauge zeroes the first unknown. Only pc_solve_poisson, the schedule, profiling and
+ * pc_destroy apply to a grid-only plan; the node entry points and pc_plan_clone return
+ * PC_ERR_INVALID_ARG.
+ * pc_grid_plan_create reads desc during the call only; the plan belongs to the caller until
+ * pc_destroy. Errors: PC_ERR_INVALID_ARG for a malformed descriptor (dim, n[a] outside
+ * [4, 4096], h, boundary kinds, precision, refine_iters, gauge, eigenvalues, grid_type);
+ * PC_ERR_UNSUPPORTED for a solve length the transforms do not cover or pseudo-spectral
+ * eigenvalues with the MIXED refinement; PC_ERR_CUDA when the device is unavailable;
+ * PC_ERR_OUT_OF_MEMORY. cuda_stream orders the setup copies (NULL: the default stream). */
+typedef enum { PC_GRID_CELLS = 0, PC_GRID_VERTICES = 1 } pc_grid_type;
+typedef struct {
+  int dim;                  /* 2 or 3 */
+  int64_t n[3];             /* cells per axis */
+  double h[3];              /* spacing */
+  int bc_lo[3], bc_hi[3];   /* pc_bc per axis end */
+  int grid_type;            /* pc_grid_type */
+  int precision;            /* pc_precision */
+  int refine_iters;         /* MIXED: refinement sweeps */
+  int gauge;                /* 0 mean, 1 corner (used when the problem has a zero mode) */
+  int eigenvalues;          /* pc_eigenvalues */
+} pc_grid_desc;
+pc_status pc_grid_plan_create(const pc_grid_desc *desc, int device, void *cuda_stream, pc_plan **out_plan);
+
 /* The grid-level Poisson solve alone (§2.3 three-step algorithm): L_h p = s, cells in FP64,
  * with the plan's precision, refinement and gauge. */
 pc_status pc_solve_poisson(pc_plan *plan, const double *s, double *p_out, pc_stats *stats,
                            void *cuda_stream);
+/* (On a vertex-grid plan s and p_out have the unknowns' shape, C order. The statistics are those
+ * of the extended periodic solve; removed_mean is the dropped zero-mode coefficient of the vertex
+ * problem (0 when an axis has a Dirichlet end), gauge_shift the constant the gauge took from the
+ * extended solution: on problems without a zero mode only the mean that rounding left.) */
 
 /* Allocation-free grid-level Poisson solve (the paper has no counterpart: this is a service of
  * the library, not a step of the method). Solves L_h p = s in FP64 with the same transform

@@ -358,7 +358,116 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
   return PC_OK;
 }
 
+// Grid-only plan: the transform tables and the cell workspace, no nodes. A vertex grid becomes
+// the periodic cell grid of its symmetric extension: 2n cells on N-N and D-D axes, 4n on N-D
+// and D-N axes (n on P-P axes); the extension and the restriction to the vertex unknowns are
+// kernels of pc_solve_poisson.
+static pc_status create_grid(const pc_grid_desc *d, int device, cudaStream_t st, Plan **out) {
+  if (!d || !out) return fail(PC_ERR_INVALID_ARG, "desc and out_plan are required");
+  *out = nullptr;
+  if (d->dim != 2 && d->dim != 3) return fail(PC_ERR_INVALID_ARG, "dim must be 2 or 3");
+  if (d->grid_type != PC_GRID_CELLS && d->grid_type != PC_GRID_VERTICES) return fail(PC_ERR_INVALID_ARG, "bad grid_type");
+  if (d->precision < PC_PREC_FP64 || d->precision > PC_PREC_FP32) return fail(PC_ERR_INVALID_ARG, "bad precision");
+  if (d->refine_iters < 0 || d->refine_iters > kMaxRefine) return fail(PC_ERR_INVALID_ARG, "refine_iters in [0, %d]", kMaxRefine);
+  if (d->gauge != 0 && d->gauge != 1) return fail(PC_ERR_INVALID_ARG, "gauge must be 0 or 1");
+  if (d->eigenvalues != PC_EIG_FD && d->eigenvalues != PC_EIG_SPECTRAL)
+    return fail(PC_ERR_INVALID_ARG, "eigenvalues must be PC_EIG_FD or PC_EIG_SPECTRAL");
+  if (d->eigenvalues == PC_EIG_SPECTRAL && d->precision == PC_PREC_MIXED)
+    return fail(PC_ERR_UNSUPPORTED, "pseudo-spectral eigenvalues need precision FP64 or FP32");
+  const bool vert = d->grid_type == PC_GRID_VERTICES;
+  long long ncells = 1, nvtot = 1;
+  int nint[3] = {1, 1, 1}, nv[3] = {1, 1, 1}, vk[3] = {0, 0, 0};
+  bool psing = true;
+  for (int a = 0; a < d->dim; ++a) {
+    if (d->n[a] < 4 || d->n[a] > 4096) return fail(PC_ERR_INVALID_ARG, "n[%d] must be in [4, 4096]", a);
+    if (!(d->h[a] > 0) || !std::isfinite(d->h[a])) return fail(PC_ERR_INVALID_ARG, "h[%d] invalid", a);
+    if (d->bc_lo[a] < 0 || d->bc_lo[a] > 3 || d->bc_hi[a] < 0 || d->bc_hi[a] > 3)
+      return fail(PC_ERR_INVALID_ARG, "bad boundary kind on axis %d", a);
+    if ((d->bc_lo[a] == PC_BC_PERIODIC) != (d->bc_hi[a] == PC_BC_PERIODIC))
+      return fail(PC_ERR_INVALID_ARG, "periodic must pair with periodic (axis %d)", a);
+    if (d->bc_lo[a] == PC_BC_DIRICHLET || d->bc_hi[a] == PC_BC_DIRICHLET) psing = false;
+    const int n = (int)d->n[a];
+    vk[a] = axis_kind(d->bc_lo[a], d->bc_hi[a]);
+    if (vert) {
+      nint[a] = vk[a] == KIND_PP ? n : ((vk[a] == KIND_NN || vk[a] == KIND_DD) ? 2 * n : 4 * n);
+      nv[a] = vk[a] == KIND_NN ? n + 1 : (vk[a] == KIND_DD ? n - 1 : n);
+    } else {
+      nint[a] = nv[a] = n;
+    }
+    if (!axis_length_supported(nint[a]))
+      return fail(PC_ERR_UNSUPPORTED, "axis %d: the solve length %d must be even with half of it 2^a 3^b 5^c <= 2048",
+                  a, nint[a]);
+    ncells *= nint[a];
+    nvtot *= nv[a];
+  }
+  if (ncells > (1LL << 31) - 1) return fail(PC_ERR_UNSUPPORTED, "grid larger than 2^31 cells");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return fail(PC_ERR_CUDA, "device %d not available", device);
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return fail(PC_ERR_CUDA, "cannot select device %d", device);
+
+  Plan *p = new Plan();
+  p->device = device;
+  p->grid_only = true;
+  p->vertex = vert;
+  p->dim = d->dim;
+  p->N = 0;
+  p->Kg = d->dim == 2 ? 9 : 27;
+  p->precision = d->precision;
+  p->refine_iters = d->refine_iters;
+  p->gauge = d->gauge;
+  p->vdtype = PC_DTYPE_F64;
+  p->eigen = d->eigenvalues;
+  p->ncells = ncells;
+  p->problem_singular = psing;
+  p->singular = vert ? true : psing;   // the extension is periodic on every axis
+  p->nvtot = nvtot;
+  for (int a = 0; a < 3; ++a) {
+    const bool on = a < d->dim;
+    p->n[a] = on ? nint[a] : 1;
+    p->lo[a] = 0.0;
+    p->h[a] = on ? d->h[a] : 1.0;
+    p->bc_lo[a] = on ? (vert ? PC_BC_PERIODIC : d->bc_lo[a]) : 0;
+    p->bc_hi[a] = on ? (vert ? PC_BC_PERIODIC : d->bc_hi[a]) : 0;
+    p->vkind[a] = vk[a];
+    p->vn[a] = on ? (int)d->n[a] : 1;
+    p->nv[a] = nv[a];
+  }
+  for (int a = 0; a < d->dim; ++a) {
+    AxisInfo &ax = p->ax[a];
+    ax.n = nint[a];
+    ax.h = d->h[a];
+    ax.L = (double)nint[a] * d->h[a];
+    ax.bc_lo = p->bc_lo[a];
+    ax.bc_hi = p->bc_hi[a];
+    ax.periodic = ax.bc_lo == PC_BC_PERIODIC;
+    ax.nfaces = ax.periodic ? ax.n : ax.n + 1;
+    ax.kind = axis_kind(ax.bc_lo, ax.bc_hi);
+    p->nface_total[a] = 0;   // no faces: the plan has no transfer
+  }
+  auto bail = [&](pc_status s) { destroy_plan(p); return s; };
+  pc_status s = alloc_workspace(p, st);
+  if (s != PC_OK) return bail(s);
+  if (vert && plan_alloc(p, (void **)&p->vstage, (size_t)nvtot * 16) != PC_OK) return bail(PC_ERR_OUT_OF_MEMORY);
+  if (prepare_kernels() != PC_OK) return bail(PC_ERR_CUDA);
+  s = build_axis_tables(p);
+  if (s != PC_OK) return bail(s);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(PC_ERR_CUDA, "grid plan setup failed"));
+  *out = p;
+  return PC_OK;
+}
+
 }  // namespace pc
+
+extern "C" pc_status pc_grid_plan_create(const pc_grid_desc *desc, int device, void *cuda_stream, pc_plan **out_plan) {
+  if (!out_plan) return pc::fail(PC_ERR_INVALID_ARG, "out_plan is required");
+  pc::Plan *p = nullptr;
+  pc_status s = pc::create_grid(desc, device, (cudaStream_t)cuda_stream, &p);
+  if (s == PC_OK) *out_plan = reinterpret_cast<pc_plan *>(p);
+  return s;
+}
 
 extern "C" pc_status pc_plan_create(const pc_problem_desc *desc, int device, size_t hbm_budget_bytes,
                                     void *cuda_stream, pc_plan **out_plan) {
@@ -381,6 +490,7 @@ extern "C" pc_status pc_plan_clone(pc_plan *plan, void *cuda_stream, pc_plan **o
   using namespace pc;
   Plan *src = reinterpret_cast<Plan *>(plan);
   if (!src || !out_plan) return fail(PC_ERR_INVALID_ARG, "plan and out_plan are required");
+  if (src->grid_only) return fail(PC_ERR_INVALID_ARG, "grid-only plans are not cloned");
   *out_plan = nullptr;
   Plan *root = src->root ? src->root : src;
   int cur = -1;
@@ -477,6 +587,7 @@ extern "C" pc_status pc_plan_rows(const pc_plan *plan, int which, int64_t *rows_
                                   double *w_out) {
   const pc::Plan *p = reinterpret_cast<const pc::Plan *>(plan);
   if (!p || !rows_out) return pc::fail(PC_ERR_INVALID_ARG, "plan and rows_out are required");
+  if (p->grid_only) return pc::fail(PC_ERR_INVALID_ARG, "a grid-only plan has no WLS rows");
   if (which < 0 || which > p->dim + 1) return pc::fail(PC_ERR_INVALID_ARG, "which must be in [0, dim + 1]");
   if (which == p->dim + 1 && p->divmode != PC_DIV_WLS_DIRECT)
     return pc::fail(PC_ERR_INVALID_ARG, "cell rows exist only in PC_DIV_WLS_DIRECT plans");

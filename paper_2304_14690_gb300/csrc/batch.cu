@@ -277,6 +277,7 @@ pc_status validate_batch(int count, pc_plan *const *plans, const pc_project_args
   for (int i = 0; i < count; ++i) {
     const Plan *p = reinterpret_cast<const Plan *>(plans[i]);
     if (!p) return fail(PC_ERR_INVALID_ARG, "plan %d is NULL", i);
+    if (p->grid_only) return fail(PC_ERR_INVALID_ARG, "plan %d is a grid-only plan: it has no nodes to project", i);
     if (!args[i].u_star || !args[i].p_out || !args[i].u_out || !(args[i].dt > 0.0))
       return fail(PC_ERR_INVALID_ARG, "batch entry %d: u_star, p_out, u_out and dt > 0 are required", i);
     if (device < 0) device = p->device;

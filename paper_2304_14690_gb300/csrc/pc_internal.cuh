@@ -178,6 +178,16 @@ struct Plan {
   int eigen = PC_EIG_FD;       // pc_eigenvalues of the transform solve
   uint8_t *rhs_mask = nullptr; // pc_plan_set_rhs_mask: plan copy of the mask (cells)
   int divmode = PC_DIV_FACES;  // pc_divergence
+  // grid-only plans (pc_grid_plan_create): no nodes, only the grid solve. A vertex grid is
+  // solved as the periodic cell grid of its symmetric extension, held by the plan's axes.
+  bool grid_only = false;
+  bool vertex = false;
+  bool problem_singular = true;  // the vertex problem (not its extension) has a zero mode
+  int vkind[3] = {0, 0, 0};      // per axis: 0 P-P, 1 N-N, 2 D-D, 3 N-D, 4 D-N
+  int vn[3] = {1, 1, 1};         // cells of the vertex grid per axis
+  int nv[3] = {1, 1, 1};         // unknowns per axis
+  long long nvtot = 0;
+  double *vstage = nullptr;      // host staging in the unknowns' layout
   int32_t *ccol = nullptr;     // direct divergence: [K][cells] node index
   double *cD64 = nullptr;      //   [dim][K][cells] derivative-row weights (FP64 plans)
   float2 *cD2 = nullptr;       //   (hi, lo) pairs (mixed and FP32 plans)

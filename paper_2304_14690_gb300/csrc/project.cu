@@ -884,6 +884,86 @@ __global__ void ib_guard_kernel(IbCtl *ctl, int max_iters, cudaGraphConditionalH
   }
 }
 
+// ----------------------------------------------------------------------------- vertex grids
+// A vertex grid is solved as the periodic cell grid of its symmetric extension (grid-only
+// plans): the source is extended evenly about Neumann ends and oddly about Dirichlet ends, the
+// extended solution is restricted to the vertex unknowns. The real DFT of such an extension is
+// the DCT-I, DST-I or quarter-wave transform of the vertex values.
+struct VertexGrid {
+  int dim;
+  int kind[3], n[3], m[3], nv[3];   // boundary pair, vertex-grid cells, extended length, unknowns
+};
+// The vertex unknown held by extended cell e of an axis, with its sign, or -1 where the
+// extension is zero (a Dirichlet end).
+__device__ __forceinline__ int vertex_fold(int kind, int n, int e, double &sign) {
+  sign = 1.0;
+  switch (kind) {
+    case KIND_PP: return e;
+    case KIND_NN: return e <= n ? e : 2 * n - e;
+    case KIND_DD:
+      if (e == 0 || e == n) return -1;
+      if (e < n) return e - 1;
+      sign = -1.0;
+      return 2 * n - e - 1;
+    case KIND_ND:   // even about 0, odd about n: period 4n
+      if (e < n) return e;
+      if (e == n || e == 3 * n) return -1;
+      sign = -1.0;
+      if (e <= 2 * n) return 2 * n - e;
+      if (e < 3 * n) return e - 2 * n;
+      sign = 1.0;
+      return 4 * n - e;
+    default:        // KIND_DN: odd about 0, even about n
+      if (e == 0 || e == 2 * n) return -1;
+      if (e <= n) return e - 1;
+      if (e < 2 * n) return 2 * n - e - 1;
+      sign = -1.0;
+      if (e <= 3 * n) return e - 2 * n - 1;
+      return 4 * n - e - 1;
+  }
+}
+__global__ void vertex_extend_kernel(VertexGrid V, const double *__restrict__ sv, double *__restrict__ se,
+                                     long long ne) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  int idx[3];
+  long long rem = e;
+  for (int a = V.dim - 1; a >= 0; --a) {
+    idx[a] = (int)(rem % V.m[a]);
+    rem /= V.m[a];
+  }
+  long long u = 0;
+  double sg = 1.0;
+  bool zero = false;
+  for (int a = 0; a < V.dim; ++a) {
+    double sa;
+    const int ua = vertex_fold(V.kind[a], V.n[a], idx[a], sa);
+    if (ua < 0) zero = true;
+    else {
+      u = u * V.nv[a] + ua;
+      sg *= sa;
+    }
+  }
+  se[e] = zero ? 0.0 : sg * sv[u];
+}
+__global__ void vertex_restrict_kernel(VertexGrid V, const double *__restrict__ pe, double *__restrict__ pv,
+                                       long long nvt) {
+  const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= nvt) return;
+  int idx[3];
+  long long rem = u;
+  for (int a = V.dim - 1; a >= 0; --a) {
+    idx[a] = (int)(rem % V.nv[a]);
+    rem /= V.nv[a];
+  }
+  long long e = 0;
+  for (int a = 0; a < V.dim; ++a) {
+    const int j0 = (V.kind[a] == KIND_DD || V.kind[a] == KIND_DN) ? 1 : 0;   // first unknown vertex
+    e = e * V.m[a] + idx[a] + j0;
+  }
+  pv[u] = pe[e];
+}
+
 static GridDev grid_dev(const Plan *p);
 
 // ----------------------------------------------------------------------------- batched kernels
@@ -1139,6 +1219,17 @@ static void launch_residual(bool singular, bool write_r, bool norm, cudaStream_t
 // s2 (nullable): the source as (hi, lo) pairs (projections); otherwise s64 in FP64
 // (pc_solve_poisson). FP32 solves keep the refinement iterate in p->p2 as (hi, lo) pairs, read
 // by the residual and the gradient; the last solve also writes p in FP64 to pout.
+// Gauge of the solved p: 0 none, 1 zero mean, 2 zero first cell. Problems with a zero mode take
+// the plan's gauge. The periodic extension of a vertex problem without one (an odd extension on
+// some axis) has an exactly mean-free solution; its mean is removed all the same, since the
+// refinement cannot correct the mean that FP32 rounding leaves (L_h of a constant is zero) and
+// that offset would break the odd symmetry the restriction relies on.
+static int gauge_mode(const Plan *p) {
+  if (!p->singular) return 0;
+  if (p->vertex && !p->problem_singular) return 1;
+  return p->gauge == 1 ? 2 : 1;
+}
+
 static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_final_residual,
                             cudaStream_t st, const float *s32 = nullptr, const float2 *s2 = nullptr) {
   const long long nc = p->ncells;
@@ -1180,8 +1271,8 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
     count_launch(p);
     prof_mark(p, st, 7);
   }
-  // gauge (singular problems), then the FP32 split of p for the mixed gradient
-  int gmode = p->singular ? (p->gauge == 1 ? 2 : 1) : 0;
+  // gauge, then the FP32 split of p for the mixed gradient
+  const int gmode = gauge_mode(p);
   if (gmode) {
     launch_pdl(gauge_sum_kernel, grid_for(nc, kFlatPerBlock), T, 0, st, nc, pout, p->dstats, p->partials, p->counters, gmode);
     count_launch(p);
@@ -1204,14 +1295,15 @@ static pc_status fill_stats(Plan *p, pc_stats *stats, cudaStream_t st) {
   PC_CUDA_TRY(cudaStreamSynchronize(st));
   memset(stats, 0, sizeof(*stats));
   const double nc = (double)p->ncells;
-  stats->removed_mean = p->singular ? ds.sum_s / nc : 0.0;
+  const bool zero_mode = p->vertex ? p->problem_singular : p->singular;
+  stats->removed_mean = zero_mode ? ds.sum_s / nc : 0.0;
   stats->source_norm = std::sqrt(fmax(ds.sum_s2, 0.0));
   int its = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
   for (int i = 0; i <= its && i < 9; ++i) stats->residual_norm[i] = std::sqrt(fmax(ds.res2[i], 0.0));
   stats->refine_iters_done = its;
   stats->max_div_after = ds.max_div;
   stats->max_abs_u_star = ds.max_u;
-  int gmode = p->singular ? (p->gauge == 1 ? 2 : 1) : 0;
+  const int gmode = gauge_mode(p);
   stats->gauge_shift = gmode == 1 ? ds.sum_p / nc : (gmode == 2 ? ds.corner_p : 0.0);
   // a NaN or infinity anywhere in u~ reaches the source sums (the maxima above skip NaN)
   if (!std::isfinite(ds.sum_s) || !std::isfinite(ds.sum_s2))
@@ -1400,6 +1492,44 @@ pc_status solve_grid_device(Plan *p, const double *s, double *pout, cudaStream_t
   count_launch(p);
   PC_CUDA_TRY(cudaGetLastError());
   return solve_grid(p, s, pout, false, st);
+}
+
+// pc_solve_poisson on a vertex-grid plan: extend the source, solve the periodic extension,
+// restrict the solution to the vertex unknowns.
+static pc_status vertex_solve(Plan *p, const double *s, double *p_out, pc_stats *stats, cudaStream_t st) {
+  const long long nc = p->ncells, nvt = p->nvtot;
+  const bool hs = !is_device_ptr(s), hp = !is_device_ptr(p_out);
+  const double *ds = s;
+  double *dp = p_out;
+  if (hs) {
+    PC_CUDA_TRY(cudaMemcpyAsync(p->vstage, s, nvt * sizeof(double), cudaMemcpyHostToDevice, st));
+    ds = p->vstage;
+  }
+  if (hp) dp = p->vstage + nvt;
+  VertexGrid V{};
+  V.dim = p->dim;
+  for (int a = 0; a < 3; ++a) {
+    V.kind[a] = p->vkind[a];
+    V.n[a] = p->vn[a];
+    V.m[a] = a < p->dim ? p->ax[a].n : 1;
+    V.nv[a] = p->nv[a];
+  }
+  prof_begin(p, st);
+  PC_CUDA_TRY(cudaMemsetAsync(p->dstats, 0, sizeof(DevStats), st));
+  vertex_extend_kernel<<<grid_for(nc, 256), 256, 0, st>>>(V, ds, p->stage_s, nc);
+  count_launch(p);
+  launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, (const double *)p->stage_s, p->dstats,
+             p->partials, p->counters);
+  count_launch(p);
+  prof_mark(p, st, 2);
+  PC_TRY(solve_grid(p, p->stage_s, p->stage_p, stats != nullptr, st));
+  vertex_restrict_kernel<<<grid_for(nvt, 256), 256, 0, st>>>(V, p->stage_p, dp, nvt);
+  count_launch(p);
+  PC_CUDA_TRY(cudaGetLastError());
+  if (hp) PC_CUDA_TRY(cudaMemcpyAsync(p_out, dp, nvt * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (stats) PC_TRY(fill_stats(p, stats, st));
+  if (hp) PC_CUDA_TRY(cudaStreamSynchronize(st));
+  return PC_OK;
 }
 
 static pc_status solve_impl(Plan *p, const double *s, double *p_out, pc_stats *stats, cudaStream_t st) {
@@ -1846,6 +1976,7 @@ extern "C" pc_status pc_project(pc_plan *plan, double dt, const void *u_star, co
                                 void *cuda_stream) {
   pc::Plan *p = reinterpret_cast<pc::Plan *>(plan);
   if (!p) return pc::fail(PC_ERR_INVALID_ARG, "plan is NULL");
+  if (p->grid_only) return pc::fail(PC_ERR_INVALID_ARG, "a grid-only plan has no nodes: use pc_solve_poisson");
   if (!u_star || !p_out || !u_out) return pc::fail(PC_ERR_INVALID_ARG, "u_star, p_out and u_out are required");
   if (!(dt > 0.0) || !std::isfinite(dt)) return pc::fail(PC_ERR_INVALID_ARG, "dt must be positive and finite");
   int dev = -1;
@@ -1865,6 +1996,7 @@ extern "C" pc_status pc_solve_poisson(pc_plan *plan, const double *s, double *p_
   pc::Plan *p = reinterpret_cast<pc::Plan *>(plan);
   if (!p || !s || !p_out) return pc::fail(PC_ERR_INVALID_ARG, "plan, s and p_out are required");
   if (cudaSetDevice(p->device) != cudaSuccess) return pc::fail(PC_ERR_CUDA, "cannot select device %d", p->device);
+  if (p->vertex) return pc::vertex_solve(p, s, p_out, stats, (cudaStream_t)cuda_stream);
   return pc::solve_impl(p, s, p_out, stats, (cudaStream_t)cuda_stream);
 }
 
@@ -1873,6 +2005,7 @@ extern "C" pc_status pc_project_ib(pc_plan *plan, double dt, const void *u_star,
                                    double *history, pc_ib_result *result, void *cuda_stream) {
   pc::Plan *p = reinterpret_cast<pc::Plan *>(plan);
   if (!p) return pc::fail(PC_ERR_INVALID_ARG, "plan is NULL");
+  if (p->grid_only) return pc::fail(PC_ERR_INVALID_ARG, "a grid-only plan has no nodes");
   if (!u_star || !p_out || !u_out) return pc::fail(PC_ERR_INVALID_ARG, "u_star, p_out and u_out are required");
   if (!(dt > 0.0) || !std::isfinite(dt)) return pc::fail(PC_ERR_INVALID_ARG, "dt must be positive and finite");
   if (!(tol >= 0.0) || !std::isfinite(tol)) return pc::fail(PC_ERR_INVALID_ARG, "tol must be finite and >= 0");
@@ -1896,6 +2029,7 @@ extern "C" pc_status pc_project_ib(pc_plan *plan, double dt, const void *u_star,
 extern "C" pc_status pc_plan_set_rhs_mask(pc_plan *plan, const uint8_t *mask, void *cuda_stream) {
   pc::Plan *p = reinterpret_cast<pc::Plan *>(plan);
   if (!p) return pc::fail(PC_ERR_INVALID_ARG, "plan is NULL");
+  if (p->grid_only) return pc::fail(PC_ERR_INVALID_ARG, "a grid-only plan has no projection to mask");
   if (cudaSetDevice(p->device) != cudaSuccess) return pc::fail(PC_ERR_CUDA, "cannot select device %d", p->device);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   if (!mask) {

@@ -97,7 +97,24 @@ class ProjectArgs(ctypes.Structure):
                 ("p_out", ctypes.c_void_p), ("u_out", ctypes.c_void_p), ("f_ib_out", ctypes.c_void_p)]
 
 
+class GridDesc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("n", ctypes.c_int64 * 3),
+        ("h", ctypes.c_double * 3),
+        ("bc_lo", ctypes.c_int * 3),
+        ("bc_hi", ctypes.c_int * 3),
+        ("grid_type", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("refine_iters", ctypes.c_int),
+        ("gauge", ctypes.c_int),
+        ("eigenvalues", ctypes.c_int),
+    ]
+
+
 FUNCTIONS = {
+    "pc_grid_plan_create": (ctypes.c_int, [ctypes.POINTER(GridDesc), ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
     "pc_plan_create": (ctypes.c_int, [ctypes.POINTER(ProblemDesc), ctypes.c_int, ctypes.c_size_t,
                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "pc_project": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
@@ -398,6 +415,56 @@ class Plan:
                                     _ptr(p_out, self.shape, torch.float64, "p_out"),
                                     ctypes.byref(st) if st is not None else None, _stream_handle(stream)))
         return p_out, (st.as_dict() if st is not None else None)
+
+
+GRID_TYPE = {"cells": 0, "vertices": 1}
+
+
+def vertex_unknowns(lo, hi, n):
+    """Pressure unknowns on a vertex-grid axis of n cells with boundary kinds lo, hi."""
+    if lo == "P":
+        return n
+    neu = lambda c: c in ("W", "I")
+    if neu(lo) and neu(hi):
+        return n + 1
+    if not neu(lo) and not neu(hi):
+        return n - 1
+    return n
+
+
+class GridPlan(Plan):
+    """A grid-only plan (pc_grid_plan_create): the Poisson solve alone, on the cell-centred or
+    the vertex pressure grid. solve_poisson, autotune and the schedule controls apply; the node
+    entry points do not."""
+
+    def __init__(self, dim, n, h, bc_lo, bc_hi, grid_type="cells", precision="fp64", refine_iters=2,
+                 gauge=0, eigenvalues="fd", device=0, stream=None):
+        import torch
+        lib = load()
+        d = GridDesc()
+        d.dim = dim
+        for a in range(3):
+            d.n[a] = int(n[a]) if a < dim else 1
+            d.h[a] = float(h[a]) if a < dim else 1.0
+            d.bc_lo[a] = BC[bc_lo[a]] if a < dim else 0
+            d.bc_hi[a] = BC[bc_hi[a]] if a < dim else 0
+        d.grid_type = GRID_TYPE[grid_type]
+        d.precision = PRECISION[precision]
+        d.refine_iters = int(refine_iters)
+        d.gauge = int(gauge)
+        d.eigenvalues = EIGENVALUES[eigenvalues]
+        self._gdesc = d
+        self.precision = precision
+        self.device = torch.device("cuda", device)
+        self.dim = dim
+        self.N = 0
+        h_ = ctypes.c_void_p()
+        _check(lib.pc_grid_plan_create(ctypes.byref(d), device, _stream_handle(stream), ctypes.byref(h_)))
+        self.handle = h_
+        if grid_type == "vertices":
+            self.shape = tuple(vertex_unknowns(bc_lo[a], bc_hi[a], int(n[a])) for a in range(dim))
+        else:
+            self.shape = tuple(int(n[a]) for a in range(dim))
 
 
 def solve_poisson_static(dim, n, h, bc_lo, bc_hi, s, p_out, gauge=0, stream=None):

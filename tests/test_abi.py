@@ -83,3 +83,44 @@ def test_descriptor_validation(lib, over, status):
     s = lib.pc_plan_create(ctypes.byref(d), 0, 0, None, ctypes.byref(h))
     assert s == status, lib.pc_last_error_message()
     assert lib.pc_last_error_message() != b""
+
+
+def _grid_desc(**over):
+    from paper_2304_14690_gb300 import pc
+    d = pc.GridDesc()
+    d.dim = 2
+    for a in range(3):
+        d.n[a] = 16 if a < 2 else 1
+        d.h[a] = 0.1
+        d.bc_lo[a] = d.bc_hi[a] = pc.BC["W"]
+    d.grid_type = 1
+    for k, v in over.items():
+        if k in ("n", "bc_lo", "bc_hi", "h"):
+            for i, x in enumerate(v):
+                getattr(d, k)[i] = x
+        else:
+            setattr(d, k, v)
+    return d
+
+
+@pytest.mark.parametrize("over,status", [
+    (dict(dim=1), 1),
+    (dict(grid_type=2), 1),
+    (dict(precision=7), 1),
+    (dict(gauge=3), 1),
+    (dict(eigenvalues=4), 1),
+    (dict(eigenvalues=1, precision=1), 2),           # pseudo-spectral with the mixed refinement
+    (dict(n=(3, 16)), 1),
+    (dict(h=(0.1, -1.0)), 1),
+    (dict(bc_lo=(0, 1)), 1),                          # periodic paired with a wall
+    (dict(bc_lo=(3, 1), n=(2048, 16)), 2),            # a D-N vertex axis extends to 4n = 8192
+    (dict(n=(14, 16)), 2),                            # a cell axis of 14 (half 7): no transform
+])
+def test_grid_descriptor_validation(lib, over, status):
+    d = _grid_desc(**over)
+    if "n" in over and over["n"] == (14, 16):
+        d.grid_type = 0
+    h = ctypes.c_void_p()
+    s = lib.pc_grid_plan_create(ctypes.byref(d), 0, None, ctypes.byref(h))
+    assert s == status, lib.pc_last_error_message()
+    assert lib.pc_last_error_message() != b""
