@@ -30,15 +30,29 @@ first unknown to zero.
 The solve expands the source in the eigenvectors with one dense basis per axis (numpy.linalg
 .solve finds the coefficients), divides by the summed eigenvalues and sums the expansion back.
 
+The pressure-correction pass on the vertex grid (build_plan, project, project_ib) takes the
+divergence of u~ at the pressure points from WLS derivative rows over their K nearest nodes
+(§2.3 as printed: there are no faces on this grid), solves on the unknowns, and takes the
+gradient at each node from the derivative rows over the 3^d block of lattice vertices around
+it (the nearest vertex and its neighbours, shifted inward at a non-periodic end, wrapped on a
+periodic axis). A Dirichlet boundary vertex is a point of that block with its known value 0.
+The node updates are those of the cell-grid pass (Eqs. 18-19).
+
 Parity: pinned by tests/test_oracle_vertex.py - the eigenvector relations against the operator
 applied by its ghost rules, a brute-force dense solve of the assembled operator on small 2D and
 3D grids, a manufactured solution converging at second order, continuous modes solved exactly
 with the pseudo-spectral eigenvalues, and the identity with the cell-grid periodic solve
-(oracle.poisson) of the symmetric extension of the source.
+(oracle.poisson) of the symmetric extension of the source. The pass: the derivative rows at the
+pressure points and at the nodes reproduce quadratics exactly; a gradient field is projected out
+with the pressure recovered at second order; the IB relations hold.
 """
+from dataclasses import dataclass
+
 import numpy as np
 
 from .grid import NEUMANN
+from . import knn as KNN
+from . import projection as PR
 
 
 def axis_kind(lo, hi):
@@ -160,3 +174,149 @@ def solve(s, n, h, bc_lo, bc_hi, gauge="mean", eigenvalues="fd"):
     if singular and gauge == "corner":
         p = p - p[zero]
     return p, removed
+
+
+# ----------------------------------------------------------------------------- the pass (§2.3)
+def lattice_shape(g):
+    """Vertices per axis of grid g: n on a periodic axis (vertex n is vertex 0), else n + 1."""
+    return tuple(int(g.n[a]) if g.periodic(a) else int(g.n[a]) + 1 for a in range(g.dim))
+
+
+def kinds_of(g):
+    return [axis_kind(g.bc_lo[a], g.bc_hi[a]) for a in range(g.dim)]
+
+
+def unknown_slices(g):
+    """Per axis, the slice of the lattice that holds the unknowns."""
+    out = []
+    for a, k in enumerate(kinds_of(g)):
+        m, j0 = unknowns(k, int(g.n[a]))
+        out.append(slice(j0, j0 + m))
+    return tuple(out)
+
+
+def _points(g, index_axes):
+    axes = [g.lo[a] + np.asarray(ix, dtype=np.float64) * g.h[a] for a, ix in enumerate(index_axes)]
+    mesh = np.meshgrid(*axes, indexing="ij")
+    return np.stack([m.ravel() for m in mesh], axis=1)
+
+
+def lattice_points(g):
+    return _points(g, [np.arange(m) for m in lattice_shape(g)])
+
+
+def pressure_points(g):
+    """Coordinates (unknowns, d) of the pressure unknowns, C order of the unknowns' shape."""
+    return _points(g, [np.arange(sl.start, sl.stop) for sl in unknown_slices(g)])
+
+
+def vertex_block(g, pts):
+    """Lattice linear indices (N, 3^d) of the 3 vertices per axis around each node: the nearest
+    vertex and its two neighbours, shifted inward at a non-periodic end, wrapped on a periodic
+    axis; C order of the block offsets."""
+    shape = lattice_shape(g)
+    N = pts.shape[0]
+    per_axis = []
+    for a in range(g.dim):
+        c = np.floor((pts[:, a] - g.lo[a]) / g.h[a] + 0.5).astype(np.int64)
+        if g.periodic(a):
+            c = np.mod(c, shape[a])
+            v = np.mod(c[:, None] - 1 + np.arange(3)[None, :], shape[a])
+        else:
+            c = np.clip(c, 0, shape[a] - 1)
+            start = np.clip(c - 1, 0, shape[a] - 3)
+            v = start[:, None] + np.arange(3)[None, :]
+        per_axis.append(v)
+    idx = np.zeros((N, 1), dtype=np.int64)
+    for a in range(g.dim):
+        idx = (idx[:, :, None] * shape[a] + per_axis[a][:, None, :]).reshape(N, -1)
+    return idx
+
+
+@dataclass
+class VertexPlan:
+    grid: object
+    nodes: np.ndarray           # (d, N)
+    node_type: np.ndarray       # (N,)
+    K: int
+    eps: float
+    support_factor: float
+    pt_col: np.ndarray          # (unknowns, K) node indices of the divergence rows
+    pt_D: np.ndarray            # (d, unknowns, K) derivative-row weights at the pressure points
+    node_col: np.ndarray        # (N, 3^d) lattice indices of the gradient block
+    node_D: np.ndarray          # (d, N, 3^d) derivative-row weights at the nodes
+
+
+def build_plan(g, nodes, node_type, K=12, eps=6.3, support_factor=3.0):
+    """Rows of the vertex-grid pass (§2.2: computed once from the positions)."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    pts = nodes.T.copy()
+    lo, lengths, periodic = PR._box(g)
+    qp = pressure_points(g)
+    idx, _ = KNN.knn(pts, qp, K, lo, lengths, periodic)
+    _, grad = PR._wls_block(pts, qp, idx, g, eps, support_factor)
+    pt_D = np.transpose(grad, (1, 0, 2))
+    lp = lattice_points(g)
+    nidx = vertex_block(g, pts)
+    _, ngrad = PR._wls_block(lp, pts, nidx, g, eps, support_factor)
+    return VertexPlan(g, nodes, np.asarray(node_type, dtype=np.uint8), K, eps, support_factor,
+                      idx, pt_D, nidx, np.transpose(ngrad, (1, 0, 2)))
+
+
+def direct_divergence(plan, u_tilde):
+    """div u~ at the pressure points: sum_a sum_k D_a,k u~_a,k, in the unknowns' shape."""
+    g = plan.grid
+    div = np.zeros(plan.pt_col.shape[0])
+    for a in range(g.dim):
+        div += np.sum(plan.pt_D[a] * u_tilde[a][plan.pt_col], axis=1)
+    return div.reshape(tuple(sl.stop - sl.start for sl in unknown_slices(g)))
+
+
+def embed(p, g):
+    """The unknowns p placed on the whole lattice, Dirichlet boundary vertices at 0."""
+    full = np.zeros(lattice_shape(g))
+    full[unknown_slices(g)] = p
+    return full
+
+
+def node_gradient(plan, p_full):
+    vals = np.asarray(p_full, dtype=np.float64).ravel()[plan.node_col]
+    return np.sum(plan.node_D * vals[None, :, :], axis=2)
+
+
+def project(plan, dt, u_star, f_ib=None, beta=1.5, gauge="mean", eigenvalues="fd"):
+    """One pressure-correction pass on the vertex grid: source from the direct divergence,
+    the vertex-grid solve, gradient and node updates (Eqs. 18-20). Returns p (unknowns),
+    p_full (lattice), u, f, s, grad, removed."""
+    g = plan.grid
+    u_star = np.asarray(u_star, dtype=np.float64).reshape(g.dim, -1)
+    u_tilde = u_star if f_ib is None else u_star + dt * np.asarray(f_ib, dtype=np.float64).reshape(g.dim, -1)
+    s = direct_divergence(plan, u_tilde) / (beta * dt)
+    p, removed = solve(s, g.n[: g.dim], g.h[: g.dim], g.bc_lo, g.bc_hi, gauge=gauge, eigenvalues=eigenvalues)
+    p_full = embed(p, g)
+    grad = node_gradient(plan, p_full)
+    ib = plan.node_type != PR.FLUID
+    u_new = u_star - beta * dt * grad
+    u_new[:, ib] = 0.0
+    f_new = np.zeros_like(u_star)
+    f_new[:, ib] = -u_star[:, ib] / dt + beta * grad[:, ib]
+    return dict(p=p, p_full=p_full, u=u_new, f=f_new, s=s, grad=grad, removed=removed)
+
+
+def project_ib(plan, dt, u_star, f_init=None, tol=1e-3, max_iters=50, beta=1.5, gauge="mean", eigenvalues="fd"):
+    """The IB-force iteration of §2.3 around the vertex-grid pass, with the stopping rule of
+    oracle.projection (ib_change, ib_converged)."""
+    u_star = np.asarray(u_star, dtype=np.float64)
+    f = np.zeros_like(u_star) if f_init is None else np.asarray(f_init, dtype=np.float64)
+    hist = []
+    out = None
+    for it in range(1, max_iters + 1):
+        out = project(plan, dt, u_star, f, beta=beta, gauge=gauge, eigenvalues=eigenvalues)
+        diff, prev = PR.ib_change(out["f"], f, plan.node_type)
+        hist.append((diff, prev))
+        f = out["f"]
+        if PR.ib_converged(diff, prev, tol):
+            break
+    out["iterations"] = it
+    out["history"] = hist
+    return out

@@ -183,3 +183,126 @@ def test_symmetric_extension_identity(kinds):
     back = pe[j0[0]:j0[0] + shape[0], j0[1]:j0[1] + shape[1]]
     assert np.abs(back - p).max() <= 1e-11 * np.abs(p).max()
     assert removed_e == pytest.approx(removed, abs=1e-12)
+
+
+# ----------------------------------------------------------------------------- the vertex-grid pass
+from paper_2304_14690_gb300 import workloads as wl   # noqa: E402
+
+
+def _grid(prob):
+    return G.Grid(prob.dim, prob.n, prob.lo, prob.h, prob.bc_lo, prob.bc_hi)
+
+
+def test_pressure_points_and_block():
+    """Unknown positions per boundary pair, and the gradient block: nearest vertex and its
+    neighbours, shifted inward at ends, wrapped on a periodic axis."""
+    g = G.Grid(2, (6, 4), (0.0, 0.0), (1.0, 1.0), ("D", "P"), ("W", "P"))
+    assert V.lattice_shape(g) == (7, 4)
+    pp = V.pressure_points(g)
+    assert sorted(set(pp[:, 0])) == [1.0, 2.0, 3.0, 4.0, 5.0, 6.0]     # D-N: vertices 1..n
+    assert sorted(set(pp[:, 1])) == [0.0, 1.0, 2.0, 3.0]               # P-P: 0..n-1
+    g2 = G.Grid(2, (6, 4), (0.0, 0.0), (1.0, 1.0), ("D", "I"), ("D", "D"))
+    assert sorted(set(V.pressure_points(g2)[:, 0])) == [1.0, 2.0, 3.0, 4.0, 5.0]   # D-D
+    assert sorted(set(V.pressure_points(g2)[:, 1])) == [0.0, 1.0, 2.0, 3.0]        # N-D
+    pts = np.array([[0.2, 0.2], [5.9, 3.7], [2.6, 1.4], [6.0, 3.45]])
+    idx = V.vertex_block(g, pts)
+    rows = [sorted({int(c) // 4 for c in r}) for r in idx]
+    cols = [sorted({int(c) % 4 for c in r}) for r in idx]
+    assert rows == [[0, 1, 2], [4, 5, 6], [2, 3, 4], [4, 5, 6]]
+    assert cols == [[0, 1, 3], [0, 1, 3], [0, 1, 2], [0, 2, 3]]
+
+
+@pytest.mark.parametrize("case", [
+    dict(dim=2, n=(20, 16), bc_lo=("W", "D"), bc_hi=("I", "W"), obstacles=[("circle", (0.6, 0.5), 0.15)]),
+    dict(dim=2, n=(16, 20), bc_lo=("D", "D"), bc_hi=("W", "D")),
+    dict(dim=3, n=(8, 10, 6), bc_lo=("W", "D", "I"), bc_hi=("W", "W", "D")),
+])
+def test_vertex_rows_reproduce_quadratics(case):
+    """Derivative rows at the pressure points (divergence of a quadratic velocity) and at the
+    nodes over the vertex block (gradient of a quadratic pressure) are exact, at boundary
+    vertices and next to obstacles."""
+    prob = wl.generic(seed=21, **case)
+    g = _grid(prob)
+    pl = V.build_plan(g, prob.nodes, prob.node_type, K=prob.knn)
+    d = prob.dim
+    rng = np.random.default_rng(4)
+    A, B, c0 = rng.normal(size=(d, d)), rng.normal(size=(d, d, d)), rng.normal(size=d)
+    x = prob.nodes
+    u = c0[:, None] + A @ x + np.einsum("aij,im,jm->am", B, x, x)
+    div = V.direct_divergence(pl, u).ravel()
+    q = V.pressure_points(g).T
+    expect = np.trace(A) + sum((B[a, a, :] + B[a, :, a]) @ q for a in range(d))
+    np.testing.assert_allclose(div, expect, rtol=0, atol=1e-9 * (1 + np.abs(expect).max()))
+    Q, b = rng.normal(size=(d, d)), rng.normal(size=d)
+    Q = Q + Q.T
+    lp = V.lattice_points(g).T
+    p_full = (b @ lp + 0.5 * np.einsum("im,ij,jm->m", lp, Q, lp)).reshape(V.lattice_shape(g))
+    gr = V.node_gradient(pl, p_full)
+    ex = b[:, None] + Q @ x
+    assert np.abs(gr - ex).max() < 1e-9 * (1 + np.abs(ex).max())
+
+
+def _phi(kinds, L):
+    """A smooth pressure meeting each axis's boundary pair, with its gradient."""
+    f, df = [], []
+    for k, l in zip(kinds, L):
+        if k == "PP":
+            f.append(lambda x, l=l: np.sin(2 * np.pi * x / l)); df.append(lambda x, l=l: 2 * np.pi / l * np.cos(2 * np.pi * x / l))
+        elif k == "NN":
+            f.append(lambda x, l=l: np.cos(np.pi * x / l)); df.append(lambda x, l=l: -np.pi / l * np.sin(np.pi * x / l))
+        elif k == "DD":
+            f.append(lambda x, l=l: np.sin(np.pi * x / l)); df.append(lambda x, l=l: np.pi / l * np.cos(np.pi * x / l))
+        elif k == "ND":
+            f.append(lambda x, l=l: np.cos(0.5 * np.pi * x / l)); df.append(lambda x, l=l: -0.5 * np.pi / l * np.sin(0.5 * np.pi * x / l))
+        else:
+            f.append(lambda x, l=l: np.sin(0.5 * np.pi * x / l)); df.append(lambda x, l=l: 0.5 * np.pi / l * np.cos(0.5 * np.pi * x / l))
+
+    def phi(x):
+        return np.prod([f[a](x[a]) for a in range(len(kinds))], axis=0)
+
+    def grad(x):
+        return np.stack([df[a](x[a]) * np.prod([f[b](x[b]) for b in range(len(kinds)) if b != a], axis=0)
+                         for a in range(len(kinds))])
+    return phi, grad
+
+
+@pytest.mark.parametrize("kinds", [("NN", "DD"), ("NN", "NN"), ("PP", "ND"), ("DN", "PP")])
+def test_vertex_projection_recovers_pressure(kinds):
+    """u* = beta dt grad(phi) with phi meeting the boundary conditions: the pass returns p -> phi
+    at the vertices and u -> 0 at the nodes, both at second order in h."""
+    ep, eu = [], []
+    for n in (32, 64, 128):
+        h = (1.0 / n, 1.0 / n)
+        prob = wl.generic(dim=2, n=(n, n), h=h, bc_lo=tuple(KINDS[k][0] for k in kinds),
+                          bc_hi=tuple(KINDS[k][1] for k in kinds), seed=13)
+        g = _grid(prob)
+        pl = V.build_plan(g, prob.nodes, prob.node_type, K=12)
+        phi, grad = _phi(kinds, (1.0, 1.0))
+        u_star = prob.beta * prob.dt * grad(prob.nodes)
+        r = V.project(pl, prob.dt, u_star)
+        ref = phi(V.pressure_points(g).T).reshape(r["p"].shape)
+        ep.append(np.abs(r["p"] - ref).max())
+        eu.append(np.abs(r["u"]).max())
+    assert ep[-1] < 1e-3 and eu[-1] < 1e-2, (ep, eu)
+    assert all(ep[i] / ep[i + 1] > 3.3 for i in range(2)), ep
+    assert all(eu[i] / eu[i + 1] > 3.3 for i in range(2)), eu
+
+
+def test_vertex_ib_relations_and_iteration():
+    """IB nodes: u = 0 and f = -u*/dt + beta grad p; the iteration stops by the §2.3 rule and its
+    last pass is the pass with the previous force."""
+    prob = wl.generic(dim=2, n=(24, 16), bc_lo=("I", "W"), bc_hi=("D", "W"),
+                      obstacles=[("circle", (0.7, 0.5), 0.2)], seed=2, with_force=True)
+    g = _grid(prob)
+    pl = V.build_plan(g, prob.nodes, prob.node_type, K=12)
+    r = V.project(pl, prob.dt, prob.u_star, prob.f_ib)
+    ib = prob.node_type != 0
+    assert ib.any()
+    assert np.all(r["u"][:, ib] == 0.0) and np.all(r["f"][:, ~ib] == 0.0)
+    np.testing.assert_allclose(r["f"][:, ib], -prob.u_star[:, ib] / prob.dt + prob.beta * r["grad"][:, ib],
+                               rtol=1e-12, atol=1e-12)
+    it = V.project_ib(pl, prob.dt, prob.u_star, tol=1e-3, max_iters=40)
+    assert 2 <= it["iterations"] < 40
+    diff, prev = it["history"][-1]
+    assert diff <= 1e-3 * prev
+    assert all(d > 1e-3 * p for d, p in it["history"][:-1])
