@@ -638,6 +638,15 @@ def run_variants(args, prob, u_dev, stream, dev, flush, ms_step, reps=50):
             gp.close()
         vert[tag] = row
     out["vertex_grid_solve"] = vert
+    # the whole pass on the vertex grid of the same workload (direct divergence at the vertex
+    # unknowns; the I-D axis extends to 4n, the wall pair to 2n: 8x the cells of the transforms)
+    vp = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, device=dev.index,
+                 div_mode="wls_direct", grid_type="vertices")
+    vp.autotune()
+    ms_vp, ph_vp = timed(vp)
+    out["vertex_grid_project"] = {"ms_per_step": round(ms_vp, 5), "unknowns": int(np.prod(vp.shape)),
+                                  "phase_ms": {k: round(v, 5) for k, v in ph_vp.items()}}
+    vp.close()
     return out
 
 

@@ -91,6 +91,10 @@ typedef struct {
   double radius;
 } pc_obstacle;
 
+/* Pressure points: the cell centres of the grid (the staggered grid of §2.3) or its vertices (the
+ * regular grid of §2.3 and §3.2; unknowns per axis and boundary pair at pc_grid_plan_create). */
+typedef enum { PC_GRID_CELLS = 0, PC_GRID_VERTICES = 1 } pc_grid_type;
+
 typedef struct {
   int dim;                  /* 2 or 3 */
   int64_t n[3];             /* cells per axis; n[a] even on every axis (transform length) */
@@ -119,6 +123,13 @@ typedef struct {
                                its solve is not the inverse of L_h, so max_div_after and the
                                residual norms of pc_stats do not apply (reported as 0 residuals) */
   int divergence;           /* pc_divergence */
+  int grid_type;            /* pc_grid_type. PC_GRID_VERTICES needs PC_DIV_WLS_DIRECT (a vertex grid
+                               has no faces; PC_ERR_UNSUPPORTED otherwise): the source is the WLS
+                               divergence at the vertex unknowns, the node gradient uses the 3^d
+                               block of lattice vertices around each node (Dirichlet boundary
+                               vertices with value 0), and p_out, the RHS mask and the rows of
+                               pc_plan_rows(dim + 1) are in the unknowns' layout. The solve length
+                               per axis is that of the vertex extension (pc_grid_plan_create) */
 } pc_problem_desc;
 
 /* Per-call diagnostics (optional). Filling it synchronizes the stream, and a NaN or infinity that
@@ -240,7 +251,8 @@ pc_status pc_batcher_destroy(pc_batcher *batcher);
  * is taken over the cells inside. The mask is copied into plan memory (1 byte per cell,
  * allocated on the first call; the call waits for the copy). NULL clears it. Switching between
  * masked and unmasked drops the plan's captured CUDA graphs; changing the mask's content does
- * not need to. pc_solve_poisson takes its source as given (no mask). A clone starts unmasked. */
+ * not need to. pc_solve_poisson takes its source as given (no mask). A clone starts unmasked.
+ * On a vertex-grid plan the mask has one byte per vertex unknown (C order of the unknowns). */
 pc_status pc_plan_set_rhs_mask(pc_plan *plan, const uint8_t *mask, void *cuda_stream);
 
 /* Grid-only plans: the Poisson solve of §2.3 without nodes, on the cell centres of the grid
@@ -263,7 +275,6 @@ pc_status pc_plan_set_rhs_mask(pc_plan *plan, const uint8_t *mask, void *cuda_st
  * PC_ERR_UNSUPPORTED for a solve length the transforms do not cover or pseudo-spectral
  * eigenvalues with the MIXED refinement; PC_ERR_CUDA when the device is unavailable;
  * PC_ERR_OUT_OF_MEMORY. cuda_stream orders the setup copies (NULL: the default stream). */
-typedef enum { PC_GRID_CELLS = 0, PC_GRID_VERTICES = 1 } pc_grid_type;
 typedef struct {
   int dim;                  /* 2 or 3 */
   int64_t n[3];             /* cells per axis */

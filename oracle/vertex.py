@@ -284,14 +284,17 @@ def node_gradient(plan, p_full):
     return np.sum(plan.node_D * vals[None, :, :], axis=2)
 
 
-def project(plan, dt, u_star, f_ib=None, beta=1.5, gauge="mean", eigenvalues="fd"):
+def project(plan, dt, u_star, f_ib=None, beta=1.5, gauge="mean", eigenvalues="fd", rhs_mask=None):
     """One pressure-correction pass on the vertex grid: source from the direct divergence,
-    the vertex-grid solve, gradient and node updates (Eqs. 18-20). Returns p (unknowns),
-    p_full (lattice), u, f, s, grad, removed."""
+    the vertex-grid solve, gradient and node updates (Eqs. 18-20). rhs_mask (unknowns' shape,
+    nonzero = flow domain) zeroes the source outside it before the solve (§3.5). Returns p
+    (unknowns), p_full (lattice), u, f, s, grad, removed."""
     g = plan.grid
     u_star = np.asarray(u_star, dtype=np.float64).reshape(g.dim, -1)
     u_tilde = u_star if f_ib is None else u_star + dt * np.asarray(f_ib, dtype=np.float64).reshape(g.dim, -1)
     s = direct_divergence(plan, u_tilde) / (beta * dt)
+    if rhs_mask is not None:
+        s = np.where(np.asarray(rhs_mask).reshape(s.shape) != 0, s, 0.0)
     p, removed = solve(s, g.n[: g.dim], g.h[: g.dim], g.bc_lo, g.bc_hi, gauge=gauge, eigenvalues=eigenvalues)
     p_full = embed(p, g)
     grad = node_gradient(plan, p_full)
@@ -303,7 +306,8 @@ def project(plan, dt, u_star, f_ib=None, beta=1.5, gauge="mean", eigenvalues="fd
     return dict(p=p, p_full=p_full, u=u_new, f=f_new, s=s, grad=grad, removed=removed)
 
 
-def project_ib(plan, dt, u_star, f_init=None, tol=1e-3, max_iters=50, beta=1.5, gauge="mean", eigenvalues="fd"):
+def project_ib(plan, dt, u_star, f_init=None, tol=1e-3, max_iters=50, beta=1.5, gauge="mean", eigenvalues="fd",
+               rhs_mask=None):
     """The IB-force iteration of §2.3 around the vertex-grid pass, with the stopping rule of
     oracle.projection (ib_change, ib_converged)."""
     u_star = np.asarray(u_star, dtype=np.float64)
@@ -311,7 +315,7 @@ def project_ib(plan, dt, u_star, f_init=None, tol=1e-3, max_iters=50, beta=1.5, 
     hist = []
     out = None
     for it in range(1, max_iters + 1):
-        out = project(plan, dt, u_star, f, beta=beta, gauge=gauge, eigenvalues=eigenvalues)
+        out = project(plan, dt, u_star, f, beta=beta, gauge=gauge, eigenvalues=eigenvalues, rhs_mask=rhs_mask)
         diff, prev = PR.ib_change(out["f"], f, plan.node_type)
         hist.append((diff, prev))
         f = out["f"]

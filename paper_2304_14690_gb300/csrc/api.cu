@@ -160,8 +160,23 @@ static bool host_ptr(const void *ptr) {
 }
 
 // Two partial sums per block of the largest reduction launch (cell grid or flat grid).
+// Sizes of a vertex-grid axis of n cells and boundary pair kind: the length of its periodic
+// symmetric extension (2n on N-N and D-D, 4n on N-D and D-N, n on P-P), the unknowns, the
+// lattice index of the first unknown and the lattice vertices.
+static void vertex_axis(int kind, int n, int &next, int &nunk, int &j0, int &nlat) {
+  next = kind == KIND_PP ? n : ((kind == KIND_NN || kind == KIND_DD) ? 2 * n : 4 * n);
+  nunk = kind == KIND_NN ? n + 1 : (kind == KIND_DD ? n - 1 : n);
+  j0 = (kind == KIND_DD || kind == KIND_DN) ? 1 : 0;
+  nlat = kind == KIND_PP ? n : n + 1;
+}
+
 static size_t partial_slots(const Plan *p) {
-  const long long last = p->n[p->dim - 1];
+  long long last = p->n[p->dim - 1];
+  if (p->vertex) {   // the transform grid is the extension: the longer last axis, fewer rows
+    int next, nunk, j0, nlat;
+    vertex_axis(p->vkind[p->dim - 1], p->vn[p->dim - 1], next, nunk, j0, nlat);
+    last = next;
+  }
   const long long cells_launch = ((last + 255) / 256) * (p->ncells / last);
   const long long flat_launch = (p->ncells + 255) / 256;
   return (size_t)(2 * (cells_launch > flat_launch ? cells_launch : flat_launch) + 64);
@@ -199,6 +214,25 @@ static pc_status alloc_workspace(Plan *p, cudaStream_t st) {
   return PC_OK;
 }
 
+// A vertex plan's axes become the periodic cell grid of the extension (after the node rows
+// have been built on the physical grid).
+static void vertex_switch_axes(Plan *p) {
+  for (int a = 0; a < p->dim; ++a) {
+    int next, nunk, j0, nlat;
+    vertex_axis(p->vkind[a], p->vn[a], next, nunk, j0, nlat);
+    AxisInfo &ax = p->ax[a];
+    ax.n = next;
+    ax.L = (double)next * ax.h;
+    ax.bc_lo = ax.bc_hi = PC_BC_PERIODIC;
+    ax.periodic = true;
+    ax.nfaces = ax.n;
+    ax.kind = axis_kind(PC_BC_PERIODIC, PC_BC_PERIODIC);
+    p->n[a] = next;
+    p->bc_lo[a] = p->bc_hi[a] = PC_BC_PERIODIC;
+    p->nface_total[a] = 0;
+  }
+}
+
 static pc_status create(const pc_problem_desc *d, int device, size_t budget, cudaStream_t st, Plan **out) {
   if (!d || !out) return fail(PC_ERR_INVALID_ARG, "desc and out_plan are required");
   *out = nullptr;
@@ -222,7 +256,13 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
   if (d->eigenvalues == PC_EIG_SPECTRAL && d->precision == PC_PREC_MIXED)
     return fail(PC_ERR_UNSUPPORTED, "pseudo-spectral eigenvalues need precision FP64 or FP32 (the mixed "
                                     "refinement residual is that of the finite-difference operator)");
-  long long ncells = 1;
+  if (d->grid_type != PC_GRID_CELLS && d->grid_type != PC_GRID_VERTICES)
+    return fail(PC_ERR_INVALID_ARG, "grid_type must be PC_GRID_CELLS or PC_GRID_VERTICES");
+  const bool vert = d->grid_type == PC_GRID_VERTICES;
+  if (vert && d->divergence != PC_DIV_WLS_DIRECT)
+    return fail(PC_ERR_UNSUPPORTED, "a vertex pressure grid has no faces: it needs PC_DIV_WLS_DIRECT");
+  long long ncells = 1, nvtot = 1, nftot = 1;
+  int vk[3] = {0, 0, 0}, nint[3] = {1, 1, 1}, nv[3] = {1, 1, 1}, vj0[3] = {0, 0, 0}, nf[3] = {1, 1, 1};
   for (int a = 0; a < d->dim; ++a) {
     if (d->n[a] < 4 || d->n[a] > 4096) return fail(PC_ERR_INVALID_ARG, "n[%d] must be in [4, 4096]", a);
     if (!(d->h[a] > 0) || !std::isfinite(d->h[a]) || !std::isfinite(d->lo[a]))
@@ -231,10 +271,15 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
       return fail(PC_ERR_INVALID_ARG, "bad boundary kind on axis %d", a);
     if ((d->bc_lo[a] == PC_BC_PERIODIC) != (d->bc_hi[a] == PC_BC_PERIODIC))
       return fail(PC_ERR_INVALID_ARG, "periodic must pair with periodic (axis %d)", a);
-    if (!axis_length_supported((int)d->n[a]))
-      return fail(PC_ERR_UNSUPPORTED, "n[%d] = %lld: cells per axis must be even with n/2 = 2^a 3^b 5^c <= 2048",
-                  a, (long long)d->n[a]);
-    ncells *= d->n[a];
+    vk[a] = axis_kind(d->bc_lo[a], d->bc_hi[a]);
+    if (vert) vertex_axis(vk[a], (int)d->n[a], nint[a], nv[a], vj0[a], nf[a]);
+    else nint[a] = nv[a] = nf[a] = (int)d->n[a];
+    if (!axis_length_supported(nint[a]))
+      return fail(PC_ERR_UNSUPPORTED, "axis %d: the solve length %d must be even with half of it 2^a 3^b 5^c <= 2048",
+                  a, nint[a]);
+    ncells *= nint[a];
+    nvtot *= nv[a];
+    nftot *= nf[a];
   }
   if (ncells > (1LL << 31) - 1) return fail(PC_ERR_UNSUPPORTED, "grid larger than 2^31 cells");
   int ndev = 0;
@@ -261,6 +306,17 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
   p->divmode = d->divergence;
   p->ncells = ncells;
   p->singular = true;
+  p->vertex = vert;
+  p->nvtot = nvtot;
+  p->nftot = nftot;
+  p->npts = vert ? nvtot : ncells;
+  for (int a = 0; a < 3; ++a) {
+    p->vkind[a] = vk[a];
+    p->vn[a] = a < d->dim ? (int)d->n[a] : 1;
+    p->nv[a] = nv[a];
+    p->vj0[a] = vj0[a];
+    p->nf[a] = nf[a];
+  }
   for (int a = 0; a < 3; ++a) {
     p->n[a] = a < d->dim ? d->n[a] : 1;
     p->lo[a] = a < d->dim ? d->lo[a] : 0.0;
@@ -280,10 +336,12 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
     ax.kind = axis_kind(d->bc_lo[a], d->bc_hi[a]);
     if (d->bc_lo[a] == PC_BC_DIRICHLET || d->bc_hi[a] == PC_BC_DIRICHLET) p->singular = false;
   }
+  p->problem_singular = p->singular;
+  if (vert) p->singular = true;   // the extension is periodic on every axis
   for (int a = 0; a < d->dim; ++a) {
     long long rows = 1;
     for (int b = 0; b < d->dim; ++b) rows *= (b == a) ? p->ax[b].nfaces : p->ax[b].n;
-    p->nface_total[a] = rows;
+    p->nface_total[a] = vert ? 0 : rows;   // a vertex grid has no faces
   }
   auto bail = [&](pc_status s) { destroy_plan(p); return s; };
 
@@ -299,7 +357,8 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
   need += (size_t)nc * (8 + 8 + 4 + (mixed ? 8 : 0) + 8 + 8);
   need += (size_t)dd * N * 8;
   need += (size_t)dd * N * 8;                             // node coordinates (setup only)
-  if (p->divmode == PC_DIV_WLS_DIRECT) need += (size_t)nc * K * (4 + dd * 8);   // cell rows
+  if (p->divmode == PC_DIV_WLS_DIRECT) need += (size_t)p->npts * K * (4 + dd * 8);   // point rows
+  if (vert) need += (size_t)nvtot * 16;
   if (budget && need > budget)
     return bail(fail(PC_ERR_BUDGET, "plan needs %zu bytes, budget is %zu", need, budget));
 
@@ -316,11 +375,13 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
       (mixed && plan_alloc(p, (void **)&p->nD2, dd * N * Kg * 8) != PC_OK) ||
       plan_alloc(p, (void **)&p->ntype, N) != PC_OK)
     return bail(PC_ERR_OUT_OF_MEMORY);
+  const long long np = p->npts;
   if (p->divmode == PC_DIV_WLS_DIRECT &&
-      (plan_alloc(p, (void **)&p->ccol, nc * K * 4) != PC_OK ||
-       (!mixed && plan_alloc(p, (void **)&p->cD64, dd * nc * K * 8) != PC_OK) ||
-       (mixed && plan_alloc(p, (void **)&p->cD2, dd * nc * K * 8) != PC_OK)))
+      (plan_alloc(p, (void **)&p->ccol, np * K * 4) != PC_OK ||
+       (!mixed && plan_alloc(p, (void **)&p->cD64, dd * np * K * 8) != PC_OK) ||
+       (mixed && plan_alloc(p, (void **)&p->cD2, dd * np * K * 8) != PC_OK)))
     return bail(PC_ERR_OUT_OF_MEMORY);
+  if (vert && plan_alloc(p, (void **)&p->vstage, (size_t)nvtot * 16) != PC_OK) return bail(PC_ERR_OUT_OF_MEMORY);
   {
     pc_status ws = alloc_workspace(p, st);
     if (ws != PC_OK) return bail(ws);
@@ -348,15 +409,18 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
     if (hb & 2u) return bail(fail(PC_ERR_INVALID_ARG, "node_type values must be 0, 1 or 2"));
   }
   if (prepare_kernels() != PC_OK) return bail(PC_ERR_CUDA);
-  pc_status s = build_axis_tables(p);
+  // rows on the physical grid, then (vertex plans) the transform axes of the extension
+  pc_status s = build_rows(p, xyz_dev, st);
   if (s != PC_OK) return bail(s);
-  s = build_rows(p, xyz_dev, st);
+  if (vert) vertex_switch_axes(p);
+  s = build_axis_tables(p);
   if (s != PC_OK) return bail(s);
   cudaStreamSynchronize(st);
   plan_free(p, xyz_dev, (size_t)dd * N * 8);
   *out = p;
   return PC_OK;
 }
+
 
 // Grid-only plan: the transform tables and the cell workspace, no nodes. A vertex grid becomes
 // the periodic cell grid of its symmetric extension: 2n cells on N-N and D-D axes, 4n on N-D
@@ -389,8 +453,8 @@ static pc_status create_grid(const pc_grid_desc *d, int device, cudaStream_t st,
     const int n = (int)d->n[a];
     vk[a] = axis_kind(d->bc_lo[a], d->bc_hi[a]);
     if (vert) {
-      nint[a] = vk[a] == KIND_PP ? n : ((vk[a] == KIND_NN || vk[a] == KIND_DD) ? 2 * n : 4 * n);
-      nv[a] = vk[a] == KIND_NN ? n + 1 : (vk[a] == KIND_DD ? n - 1 : n);
+      int j0, nlat;
+      vertex_axis(vk[a], n, nint[a], nv[a], j0, nlat);
     } else {
       nint[a] = nv[a] = n;
     }
@@ -434,7 +498,13 @@ static pc_status create_grid(const pc_grid_desc *d, int device, cudaStream_t st,
     p->vkind[a] = vk[a];
     p->vn[a] = on ? (int)d->n[a] : 1;
     p->nv[a] = nv[a];
+    if (on && vert) {
+      int next, nunk;
+      vertex_axis(vk[a], (int)d->n[a], next, nunk, p->vj0[a], p->nf[a]);
+    }
   }
+  p->nftot = 1;
+  for (int a = 0; a < d->dim; ++a) p->nftot *= p->nf[a];
   for (int a = 0; a < d->dim; ++a) {
     AxisInfo &ax = p->ax[a];
     ax.n = nint[a];
@@ -514,8 +584,16 @@ extern "C" pc_status pc_plan_clone(pc_plan *plan, void *cuda_stream, pc_plan **o
   p->divmode = root->divmode; p->ccol = root->ccol; p->cD64 = root->cD64; p->cD2 = root->cD2;
   p->ncol = root->ncol; p->nD64 = root->nD64; p->nD2 = root->nD2; p->ntype = root->ntype;
   p->graphs_on = root->graphs_on;
+  p->vertex = root->vertex; p->problem_singular = root->problem_singular;
+  p->nvtot = root->nvtot; p->nftot = root->nftot; p->npts = root->npts;
+  for (int a = 0; a < 3; ++a) {
+    p->vkind[a] = root->vkind[a]; p->vn[a] = root->vn[a]; p->nv[a] = root->nv[a];
+    p->vj0[a] = root->vj0[a]; p->nf[a] = root->nf[a];
+  }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   pc_status s = alloc_workspace(p, st);
+  if (s == PC_OK && p->vertex && plan_alloc(p, (void **)&p->vstage, (size_t)p->nvtot * 16) != PC_OK)
+    s = PC_ERR_OUT_OF_MEMORY;
   if (s == PC_OK && cudaStreamSynchronize(st) != cudaSuccess) s = fail(PC_ERR_CUDA, "clone setup failed");
   if (s != PC_OK) {
     destroy_plan(p);
@@ -594,7 +672,7 @@ extern "C" pc_status pc_plan_rows(const pc_plan *plan, int which, int64_t *rows_
   if (cudaSetDevice(p->device) != cudaSuccess) return pc::fail(PC_ERR_CUDA, "cannot select device");
   const bool face = which < p->dim, cell = which == p->dim + 1;
   const long long K = (face || cell) ? p->K : p->Kg;
-  long long rows = face ? p->nface_total[which] : (cell ? p->ncells : p->N);
+  long long rows = face ? p->nface_total[which] : (cell ? p->npts : p->N);
   *rows_out = rows;
   if (!col_out && !w_out) return PC_OK;
   // stored neighbour-rank major on the device; returned row major

@@ -187,7 +187,11 @@ struct Plan {
   int vn[3] = {1, 1, 1};         // cells of the vertex grid per axis
   int nv[3] = {1, 1, 1};         // unknowns per axis
   long long nvtot = 0;
-  double *vstage = nullptr;      // host staging in the unknowns' layout
+  int vj0[3] = {0, 0, 0};        // lattice index of the first unknown per axis
+  int nf[3] = {1, 1, 1};         // lattice vertices per axis (n periodic, else n + 1)
+  long long nftot = 0;
+  long long npts = 0;            // pressure points with direct-divergence rows (cells or unknowns)
+  double *vstage = nullptr;      // vertex plans: [2][unknowns], source and host staging of p
   int32_t *ccol = nullptr;     // direct divergence: [K][cells] node index
   double *cD64 = nullptr;      //   [dim][K][cells] derivative-row weights (FP64 plans)
   float2 *cD2 = nullptr;       //   (hi, lo) pairs (mixed and FP32 plans)

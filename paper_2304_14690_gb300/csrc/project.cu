@@ -892,6 +892,7 @@ __global__ void ib_guard_kernel(IbCtl *ctl, int max_iters, cudaGraphConditionalH
 struct VertexGrid {
   int dim;
   int kind[3], n[3], m[3], nv[3];   // boundary pair, vertex-grid cells, extended length, unknowns
+  int j0[3], nf[3];                 // lattice index of the first unknown, lattice vertices
 };
 // The vertex unknown held by extended cell e of an axis, with its sign, or -1 where the
 // extension is zero (a Dirichlet end).
@@ -924,6 +925,7 @@ __device__ __forceinline__ int vertex_fold(int kind, int n, int e, double &sign)
 }
 __global__ void vertex_extend_kernel(VertexGrid V, const double *__restrict__ sv, double *__restrict__ se,
                                      long long ne) {
+  pdl_enter();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
   int idx[3];
@@ -946,25 +948,50 @@ __global__ void vertex_extend_kernel(VertexGrid V, const double *__restrict__ sv
   }
   se[e] = zero ? 0.0 : sg * sv[u];
 }
+// The extended solution on the vertex lattice (vertex j of an axis is extended cell j). Writes
+// any of: the unknowns (pv), the whole lattice in FP64 (pl, Dirichlet boundary vertices exactly
+// 0) and as FP32 (hi, lo) pairs (pl2) for the compensated gradient.
 __global__ void vertex_restrict_kernel(VertexGrid V, const double *__restrict__ pe, double *__restrict__ pv,
-                                       long long nvt) {
-  const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= nvt) return;
+                                       double *__restrict__ pl, float2 *__restrict__ pl2, long long nlat) {
+  pdl_enter();
+  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nlat) return;
   int idx[3];
-  long long rem = u;
+  long long rem = l;
   for (int a = V.dim - 1; a >= 0; --a) {
-    idx[a] = (int)(rem % V.nv[a]);
-    rem /= V.nv[a];
+    idx[a] = (int)(rem % V.nf[a]);
+    rem /= V.nf[a];
   }
-  long long e = 0;
+  long long e = 0, u = 0;
+  bool unknown = true;
   for (int a = 0; a < V.dim; ++a) {
-    const int j0 = (V.kind[a] == KIND_DD || V.kind[a] == KIND_DN) ? 1 : 0;   // first unknown vertex
-    e = e * V.m[a] + idx[a] + j0;
+    e = e * V.m[a] + idx[a];
+    const int ua = idx[a] - V.j0[a];
+    if (ua < 0 || ua >= V.nv[a]) unknown = false;   // a Dirichlet boundary vertex
+    u = u * V.nv[a] + (ua < 0 ? 0 : ua);
   }
-  pv[u] = pe[e];
+  const double v = unknown ? pe[e] : 0.0;
+  if (pv && unknown) pv[u] = v;
+  if (pl) pl[l] = v;
+  if (pl2) pl2[l] = as_pair(v);
 }
 
 static GridDev grid_dev(const Plan *p);
+
+static VertexGrid vertex_grid(const Plan *p) {
+  VertexGrid V{};
+  V.dim = p->dim;
+  for (int a = 0; a < 3; ++a) {
+    V.kind[a] = p->vkind[a];
+    V.n[a] = p->vn[a];
+    V.m[a] = a < p->dim ? p->ax[a].n : 1;
+    V.nv[a] = p->nv[a];
+    V.j0[a] = p->vj0[a];
+    V.nf[a] = p->nf[a];
+  }
+  return V;
+}
+
 
 // ----------------------------------------------------------------------------- batched kernels
 // One launch per pipeline stage for a whole batch of problems. seg[p] is the first block of
@@ -1133,7 +1160,7 @@ void batch_problem_fill(const Plan *p, const pc_project_args &a, BatchProblem &q
 static GridDev grid_dev(const Plan *p) {
   GridDev g{};
   g.dim = p->dim;
-  g.mask = p->rhs_mask_on ? p->rhs_mask : nullptr;
+  g.mask = (p->rhs_mask_on && !p->vertex) ? p->rhs_mask : nullptr;   // vertex plans mask their unknowns
   for (int a = 0; a < 3; ++a) {
     if (a < p->dim) {
       const AxisInfo &ax = p->ax[a];
@@ -1359,6 +1386,39 @@ static void launch_direct_div(Plan *p, cudaStream_t st, double inv_bdt, int want
   }
 }
 
+// The source and solve of a pass on a vertex-grid plan: the direct divergence at the vertex
+// unknowns (FP64, into the first half of vstage), its symmetric extension (s64), the solve of
+// the periodic extension (stage_p), and the restriction to the unknowns (dp) and to the whole
+// lattice (work64 in FP64, p2 as pairs in mixed and FP32 plans), which the gradient reads.
+static pc_status vertex_pass_solve(Plan *p, cudaStream_t st, double inv_bdt, double *dp, bool want_stats) {
+  const long long nc = p->ncells, npt = p->npts;
+  const bool mixed = p->precision != PC_PREC_FP64;
+  const int T = 256, G = grid_for(npt, T);
+  const uint8_t *mask = p->rhs_mask_on ? p->rhs_mask : nullptr;
+  double *sv = p->vstage;
+  if (p->dim == 2) {
+    if (mixed) launch_pdl(direct_div_kernel<2, true>, G, T, 0, st, (int)npt, p->K, p->ccol, p->cD64, p->cD2, p->ut64, p->u2, (int)p->N, inv_bdt, mask, sv, (float2 *)nullptr, (float *)nullptr, p->dstats, p->partials, p->counters, 0, 0.0);
+    else launch_pdl(direct_div_kernel<2, false>, G, T, 0, st, (int)npt, p->K, p->ccol, p->cD64, p->cD2, p->ut64, p->u2, (int)p->N, inv_bdt, mask, sv, (float2 *)nullptr, (float *)nullptr, p->dstats, p->partials, p->counters, 0, 0.0);
+  } else {
+    if (mixed) launch_pdl(direct_div_kernel<3, true>, G, T, 0, st, (int)npt, p->K, p->ccol, p->cD64, p->cD2, p->ut64, p->u2, (int)p->N, inv_bdt, mask, sv, (float2 *)nullptr, (float *)nullptr, p->dstats, p->partials, p->counters, 0, 0.0);
+    else launch_pdl(direct_div_kernel<3, false>, G, T, 0, st, (int)npt, p->K, p->ccol, p->cD64, p->cD2, p->ut64, p->u2, (int)p->N, inv_bdt, mask, sv, (float2 *)nullptr, (float *)nullptr, p->dstats, p->partials, p->counters, 0, 0.0);
+  }
+  count_launch(p);
+  const VertexGrid V = vertex_grid(p);
+  launch_pdl(vertex_extend_kernel, grid_for(nc, T), T, 0, st, V, (const double *)sv, p->s64, nc);
+  count_launch(p);
+  launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, (const double *)p->s64, p->dstats,
+             p->partials, p->counters);
+  count_launch(p);
+  prof_mark(p, st, 2);
+  PC_TRY(solve_grid(p, p->s64, p->stage_p, want_stats, st));
+  launch_pdl(vertex_restrict_kernel, grid_for(p->nftot, T), T, 0, st, V, (const double *)p->stage_p, dp,
+             p->work64, mixed ? reinterpret_cast<float2 *>(p->p2) : (float2 *)nullptr, p->nftot);
+  count_launch(p);
+  PC_CUDA_TRY(cudaGetLastError());
+  return PC_OK;
+}
+
 static pc_status project_impl(Plan *p, double dt, const void *u_star, const void *f_in, double *p_out,
                               void *u_out, void *f_out, pc_stats *stats, cudaStream_t st,
                               bool all_device = false) {
@@ -1376,7 +1436,8 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   if ((hu || (f_in && hf) || huo || (f_out && hfo)) && !p->stage_u) PC_TRY(plan_node_staging(p));
   if (hu) { PC_CUDA_TRY(cudaMemcpyAsync(p->stage_u, u_star, vbytes, cudaMemcpyHostToDevice, st)); du = p->stage_u; }
   if (f_in && hf) { PC_CUDA_TRY(cudaMemcpyAsync(p->stage_f, f_in, vbytes, cudaMemcpyHostToDevice, st)); df = p->stage_f; }
-  if (hp) dp = p->stage_p;
+  if (hp) dp = p->vertex ? p->vstage + p->nvtot : p->stage_p;
+  const long long np_out = p->vertex ? p->nvtot : nc;   // pressure values returned
   if (huo) duo = p->stage_uo;
   if (f_out && hfo) dfo = p->stage_fo;
 
@@ -1393,7 +1454,9 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
                        p->ut64, p->u2, p->dstats, st);
   count_launch(p);
   prof_mark(p, st, 0);
-  if (p->divmode == PC_DIV_WLS_DIRECT) {
+  if (p->vertex) {
+    PC_TRY(vertex_pass_solve(p, st, 1.0 / (p->beta * dt), dp, stats != nullptr));
+  } else if (p->divmode == PC_DIV_WLS_DIRECT) {
     launch_direct_div(p, st, 1.0 / (p->beta * dt), stats ? 2 : (p->singular ? 1 : 0));
     count_launch(p);
     prof_mark(p, st, 2);
@@ -1424,9 +1487,11 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
     prof_mark(p, st, 2);
   }
   PC_CUDA_TRY(cudaGetLastError());
-  PC_TRY(solve_grid(p, p->s64, dp, stats != nullptr, st,
-                    mixed ? reinterpret_cast<const float *>(p->work64) : nullptr,
-                    mixed ? reinterpret_cast<const float2 *>(p->s64) : nullptr));
+  if (!p->vertex)
+    PC_TRY(solve_grid(p, p->s64, dp, stats != nullptr, st,
+                      mixed ? reinterpret_cast<const float *>(p->work64) : nullptr,
+                      mixed ? reinterpret_cast<const float2 *>(p->s64) : nullptr));
+  const double *gp = p->vertex ? p->work64 : dp;   // the pressure the gradient reads (FP64 plans)
   // Host results: the pressure is final here, so its copy runs on the plan's copy stream while
   // the gradient computes; the gradient runs in two halves and the first half's u and f are
   // copied while the second half computes (copy engines and kernels overlap).
@@ -1438,7 +1503,7 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   if (hp) {
     PC_CUDA_TRY(cudaEventRecord(p->copy_ev[0], st));
     PC_CUDA_TRY(cudaStreamWaitEvent(p->copy_st, p->copy_ev[0], 0));
-    PC_CUDA_TRY(cudaMemcpyAsync(p_out, dp, nc * sizeof(double), cudaMemcpyDeviceToHost, p->copy_st));
+    PC_CUDA_TRY(cudaMemcpyAsync(p_out, dp, np_out * sizeof(double), cudaMemcpyDeviceToHost, p->copy_st));
   }
   const int gblocks = grid_for(N, 256);
   const bool split = (huo || (f_out && hfo)) && gblocks >= 2;
@@ -1455,14 +1520,14 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
     return e;
   };
   if (split) {
-    launch_gradient(p, st, dp, du, dt, duo, dfo, 0, b1);
+    launch_gradient(p, st, gp, du, dt, duo, dfo, 0, b1);
     count_launch(p);
     PC_CUDA_TRY(cudaEventRecord(p->copy_ev[1], st));
     PC_CUDA_TRY(cudaStreamWaitEvent(p->copy_st, p->copy_ev[1], 0));
     PC_CUDA_TRY(copy_nodes(0, n1, p->copy_st));
-    launch_gradient(p, st, dp, du, dt, duo, dfo, b1, -1);
+    launch_gradient(p, st, gp, du, dt, duo, dfo, b1, -1);
   } else {
-    launch_gradient(p, st, dp, du, dt, duo, dfo);
+    launch_gradient(p, st, gp, du, dt, duo, dfo);
   }
   count_launch(p);
   prof_mark(p, st, 6);
@@ -1506,14 +1571,7 @@ static pc_status vertex_solve(Plan *p, const double *s, double *p_out, pc_stats 
     ds = p->vstage;
   }
   if (hp) dp = p->vstage + nvt;
-  VertexGrid V{};
-  V.dim = p->dim;
-  for (int a = 0; a < 3; ++a) {
-    V.kind[a] = p->vkind[a];
-    V.n[a] = p->vn[a];
-    V.m[a] = a < p->dim ? p->ax[a].n : 1;
-    V.nv[a] = p->nv[a];
-  }
+  const VertexGrid V = vertex_grid(p);
   prof_begin(p, st);
   PC_CUDA_TRY(cudaMemsetAsync(p->dstats, 0, sizeof(DevStats), st));
   vertex_extend_kernel<<<grid_for(nc, 256), 256, 0, st>>>(V, ds, p->stage_s, nc);
@@ -1523,7 +1581,7 @@ static pc_status vertex_solve(Plan *p, const double *s, double *p_out, pc_stats 
   count_launch(p);
   prof_mark(p, st, 2);
   PC_TRY(solve_grid(p, p->stage_s, p->stage_p, stats != nullptr, st));
-  vertex_restrict_kernel<<<grid_for(nvt, 256), 256, 0, st>>>(V, p->stage_p, dp, nvt);
+  vertex_restrict_kernel<<<grid_for(p->nftot, 256), 256, 0, st>>>(V, p->stage_p, dp, nullptr, nullptr, p->nftot);
   count_launch(p);
   PC_CUDA_TRY(cudaGetLastError());
   if (hp) PC_CUDA_TRY(cudaMemcpyAsync(p_out, dp, nvt * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1744,7 +1802,9 @@ static pc_status ib_pass(Plan *p, bool first, double dt, const VT *du, double *d
     count_launch(p);
   }
   prof_mark(p, st, 0);
-  if (p->divmode == PC_DIV_WLS_DIRECT) {   // the whole source again: no face lists in this mode
+  if (p->vertex) {                           // the whole source again, solve and restriction
+    PC_TRY(vertex_pass_solve(p, st, 1.0 / (p->beta * dt), dp, false));
+  } else if (p->divmode == PC_DIV_WLS_DIRECT) {   // the whole source again: no face lists in this mode
     launch_direct_div(p, st, 1.0 / (p->beta * dt), p->singular ? 1 : 0);
     count_launch(p);
     prof_mark(p, st, 2);
@@ -1783,10 +1843,11 @@ static pc_status ib_pass(Plan *p, bool first, double dt, const VT *du, double *d
     prof_mark(p, st, 2);
   }
   PC_CUDA_TRY(cudaGetLastError());
-  PC_TRY(solve_grid(p, p->s64, dp, false, st, mixed ? reinterpret_cast<const float *>(p->work64) : nullptr,
-                    mixed ? reinterpret_cast<const float2 *>(p->s64) : nullptr));
+  if (!p->vertex)
+    PC_TRY(solve_grid(p, p->s64, dp, false, st, mixed ? reinterpret_cast<const float *>(p->work64) : nullptr,
+                      mixed ? reinterpret_cast<const float2 *>(p->s64) : nullptr));
   if (nib) {
-    ib_launch_force<VT>(p, st, dp, du, dt, fc);
+    ib_launch_force<VT>(p, st, p->vertex ? p->work64 : dp, du, dt, fc);
     count_launch(p);
     prof_mark(p, st, 6);
     const int G = grid_for(nib, T) < kIbBlocks ? grid_for(nib, T) : kIbBlocks;
@@ -1881,7 +1942,7 @@ static pc_status ib_capture(Plan *p, double dt, const VT *du, const VT *f_init, 
     }
     l2 = p->launches;
     if (s == PC_OK) {
-      launch_gradient(p, cs, dp, du, dt, duo, dfo);
+      launch_gradient(p, cs, p->vertex ? p->work64 : dp, du, dt, duo, dfo);
       count_launch(p);
       if (cudaGetLastError() != cudaSuccess) s = fail(PC_ERR_CUDA, "IB loop graph: gradient launch failed");
     }
@@ -1924,7 +1985,7 @@ static pc_status project_ib_impl(Plan *p, double dt, const VT *du, const VT *f_i
     h.it = 1;
     h.conv = 1;
     h.hist[0] = h.hist[1] = 0.0;
-    launch_gradient(p, st, dp, du, dt, duo, dfo);
+    launch_gradient(p, st, p->vertex ? p->work64 : dp, du, dt, duo, dfo);
     count_launch(p);
     PC_CUDA_TRY(cudaGetLastError());
   } else if (p->graphs_on) {
@@ -1947,7 +2008,7 @@ static pc_status project_ib_impl(Plan *p, double dt, const VT *du, const VT *f_i
       PC_CUDA_TRY(cudaStreamSynchronize(st));
       if (h.conv || h.it >= max_iters) break;
     }
-    launch_gradient(p, st, dp, du, dt, duo, dfo);
+    launch_gradient(p, st, p->vertex ? p->work64 : dp, du, dt, duo, dfo);
     count_launch(p);
     PC_CUDA_TRY(cudaGetLastError());
     PC_CUDA_TRY(cudaMemcpyAsync(&h, p->ib_ctl, offsetof(IbCtl, hist) + 2 * sizeof(double) * max_iters,
@@ -2039,8 +2100,10 @@ extern "C" pc_status pc_plan_set_rhs_mask(pc_plan *plan, const uint8_t *mask, vo
     }
     return PC_OK;
   }
-  if (!p->rhs_mask) PC_TRY(pc::plan_alloc(p, (void **)&p->rhs_mask, (size_t)p->ncells));
-  PC_CUDA_TRY(cudaMemcpyAsync(p->rhs_mask, mask, (size_t)p->ncells, cudaMemcpyDefault, st));
+  // one byte per pressure point: the cells, or the unknowns of a vertex grid
+  const size_t nm = (size_t)(p->npts > 0 ? p->npts : p->ncells);
+  if (!p->rhs_mask) PC_TRY(pc::plan_alloc(p, (void **)&p->rhs_mask, nm));
+  PC_CUDA_TRY(cudaMemcpyAsync(p->rhs_mask, mask, nm, cudaMemcpyDefault, st));
   PC_CUDA_TRY(cudaStreamSynchronize(st));
   if (!p->rhs_mask_on) {
     p->rhs_mask_on = true;

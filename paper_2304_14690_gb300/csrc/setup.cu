@@ -31,8 +31,9 @@ struct KnnCtx {
   const int *sorted;   // node indices, grouped by bucket
   const double *xyz;   // [dim][N]
   long long N;
-  int cells;           // 1: the points are the cell centres of the grid (bucket == cell)
+  int cells;           // 1: the points are grid points (bucket == point): lo + (i + off) h
   double h[3];
+  double off[3];       // 0.5 for cell centres, 0 for vertices
 };
 
 __device__ __forceinline__ double min_image(double d, int periodic, double L, double halfL) {
@@ -44,7 +45,7 @@ __device__ __forceinline__ double min_image(double d, int periodic, double L, do
 }
 
 __device__ __forceinline__ double cell_centre(const KnnCtx &c, int a, int i) {
-  return __dadd_rn(c.lo[a], __dmul_rn((double)i + 0.5, c.h[a]));
+  return __dadd_rn(c.lo[a], __dmul_rn((double)i + c.off[a], c.h[a]));
 }
 
 __device__ __forceinline__ double point_coord(const KnnCtx &c, int a, long long id) {
@@ -292,11 +293,14 @@ __global__ void face_rows_kernel(KnnCtx c, WlsParams P, int axis, int nf_axis, i
   }
 }
 
-// Derivative rows of every cell centre over its K nearest nodes (the direct divergence of the
-// source at the pressure points, §2.3): weights [DIM][K][cells].
+// Derivative rows of every pressure point over its K nearest nodes (the direct divergence of
+// the source at the pressure points, §2.3): weights [DIM][K][points]. The points are
+// lo + (i + off) h over the index box gshape: the cell centres (off = 1/2) or the vertex
+// unknowns (off = index of the first unknown).
 template <int DIM>
 __global__ void cell_rows_kernel(KnnCtx c, WlsParams P, long long rows, const double *glo, const double *gh,
-                                 const int *gshape, int32_t *col, double *w64, float2 *w2, unsigned int *flags) {
+                                 const int *gshape, const double *goff, int32_t *col, double *w64, float2 *w2,
+                                 unsigned int *flags) {
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   int idx[3];
@@ -307,7 +311,7 @@ __global__ void cell_rows_kernel(KnnCtx c, WlsParams P, long long rows, const do
   }
   const int K = P.K;
   double q[3];
-  for (int a = 0; a < DIM; ++a) q[a] = __dadd_rn(glo[a], __dmul_rn((double)idx[a] + 0.5, gh[a]));
+  for (int a = 0; a < DIM; ++a) q[a] = __dadd_rn(glo[a], __dmul_rn((double)idx[a] + goff[a], gh[a]));
   double bd[kMaxK];
   int bi[kMaxK];
   double w[DIM * kMaxK];
@@ -324,11 +328,11 @@ __global__ void cell_rows_kernel(KnnCtx c, WlsParams P, long long rows, const do
   }
 }
 
-// Derivative rows of every node over the 3^DIM block of cell centres around it: along each
-// axis the cell holding the node and its two neighbours, shifted inward at a non-periodic
-// wall, wrapped on a periodic axis; listed in C order of the block offsets. Three distinct
-// cell centres per axis determine a quadratic exactly, which a K-nearest choice next to a 3D
-// wall does not guarantee.
+// Derivative rows of every node over the 3^DIM block of pressure points around it: along each
+// axis the cell holding the node (on a vertex lattice: the nearest vertex) and its two
+// neighbours, shifted inward at a non-periodic wall, wrapped on a periodic axis; listed in C
+// order of the block offsets. Three distinct points per axis determine a quadratic exactly,
+// which a K-nearest choice next to a 3D wall does not guarantee.
 template <int DIM>
 __global__ void node_rows_kernel(KnnCtx c, WlsParams P, const double *xyz, long long N,
                                  int32_t *col, double *D64, float2 *D2, unsigned int *flags) {
@@ -339,8 +343,15 @@ __global__ void node_rows_kernel(KnnCtx c, WlsParams P, const double *xyz, long 
   for (int a = 0; a < DIM; ++a) q[a] = xyz[(long long)a * N + i];
   int cells[3][3];
   for (int a = 0; a < DIM; ++a) {
-    double t = floor((q[a] - c.lo[a]) / c.h[a]);
-    int ci = (int)fmax(0.0, fmin(t, (double)(c.nb[a] - 1)));
+    const double x = (q[a] - c.lo[a]) / c.h[a];
+    const double t = c.off[a] == 0.0 ? floor(x + 0.5) : floor(x);
+    int ci;
+    if (c.periodic[a]) {
+      ci = (int)t % c.nb[a];
+      if (ci < 0) ci += c.nb[a];
+    } else {
+      ci = (int)fmax(0.0, fmin(t, (double)(c.nb[a] - 1)));
+    }
     int st = ci - 1;
     if (!c.periodic[a]) st = max(0, min(st, c.nb[a] - 3));
     for (int o = 0; o < 3; ++o) {
@@ -494,16 +505,26 @@ pc_status build_rows(Plan *p, const double *xyz, cudaStream_t st) {
   P.c_dim = (d == 2) ? std::sqrt(pi / p->K) : std::pow(4.0 * pi / (3.0 * p->K), 1.0 / 3.0);
   const bool mixed = p->precision != PC_PREC_FP64;
 
-  double *glo = nullptr, *gh = nullptr;
+  double *glo = nullptr, *gh = nullptr, *goff = nullptr;
   int *gshape = nullptr;
   if (cudaMalloc(&glo, 3 * sizeof(double)) != cudaSuccess || cudaMalloc(&gh, 3 * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&gshape, 3 * sizeof(int)) != cudaSuccess) {
+      cudaMalloc(&goff, 3 * sizeof(double)) != cudaSuccess || cudaMalloc(&gshape, 3 * sizeof(int)) != cudaSuccess) {
+    cudaFree(glo); cudaFree(gh); cudaFree(goff);
     cleanup();
     return fail(PC_ERR_OUT_OF_MEMORY, "setup scratch allocation failed");
   }
+  // the index box of the pressure points: cells, or the unknowns of a vertex grid (which has no
+  // face rows, so the face kernels never see the vertex box)
   int hshape[3] = {(int)p->n[0], (int)p->n[1], (int)p->n[2]};
+  double hoff[3] = {0.5, 0.5, 0.5};
+  if (p->vertex)
+    for (int a = 0; a < 3; ++a) {
+      hshape[a] = p->nv[a];
+      hoff[a] = (double)p->vj0[a];
+    }
   cudaMemcpyAsync(glo, p->lo, 3 * sizeof(double), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(gh, p->h, 3 * sizeof(double), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(goff, hoff, 3 * sizeof(double), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(gshape, hshape, 3 * sizeof(int), cudaMemcpyHostToDevice, st);
 
   P.nrows_out = 1;
@@ -511,6 +532,7 @@ pc_status build_rows(Plan *p, const double *xyz, cudaStream_t st) {
   for (int a = 0; a < d; ++a) {
     const AxisInfo &ax = p->ax[a];
     long long rows = p->nface_total[a];
+    if (rows == 0) continue;   // a vertex grid has no faces
     int lo_wall = (!ax.periodic && ax.bc_lo == PC_BC_NEUMANN_WALL);
     int hi_wall = (!ax.periodic && ax.bc_hi == PC_BC_NEUMANN_WALL);
     if (d == 2)
@@ -525,20 +547,22 @@ pc_status build_rows(Plan *p, const double *xyz, cudaStream_t st) {
     Pc.nrows_out = d;
     Pc.first_row = 1;
     if (d == 2)
-      cell_rows_kernel<2><<<grid_for(p->ncells, 128), 128, 0, st>>>(nc, Pc, p->ncells, glo, gh, gshape, p->ccol,
-                                                                    p->cD64, mixed ? p->cD2 : nullptr, flags);
+      cell_rows_kernel<2><<<grid_for(p->npts, 128), 128, 0, st>>>(nc, Pc, p->npts, glo, gh, gshape, goff, p->ccol,
+                                                                  p->cD64, mixed ? p->cD2 : nullptr, flags);
     else
-      cell_rows_kernel<3><<<grid_for(p->ncells, 128), 128, 0, st>>>(nc, Pc, p->ncells, glo, gh, gshape, p->ccol,
-                                                                    p->cD64, mixed ? p->cD2 : nullptr, flags);
+      cell_rows_kernel<3><<<grid_for(p->npts, 128), 128, 0, st>>>(nc, Pc, p->npts, glo, gh, gshape, goff, p->ccol,
+                                                                  p->cD64, mixed ? p->cD2 : nullptr, flags);
   }
-  // cell centres as points: bucket == cell
+  // pressure points (cell centres, or the vertex lattice with its Dirichlet boundary vertices)
+  // as points: bucket == point
   KnnCtx cc{};
   cc.dim = d;
   for (int a = 0; a < 3; ++a) {
-    cc.nb[a] = (a < d) ? (int)p->n[a] : 1;
+    cc.nb[a] = (a < d) ? (p->vertex ? p->nf[a] : (int)p->n[a]) : 1;
     cc.cs[a] = (a < d) ? p->h[a] : 1.0;
     cc.lo[a] = p->lo[a];
     cc.h[a] = p->h[a];
+    cc.off[a] = p->vertex ? 0.0 : 0.5;
     cc.L[a] = (double)p->n[a] * p->h[a];
     cc.halfL[a] = 0.5 * cc.L[a];
     cc.periodic[a] = (a < d) ? p->ax[a].periodic : 0;
@@ -558,6 +582,7 @@ pc_status build_rows(Plan *p, const double *xyz, cudaStream_t st) {
   cleanup();
   cudaFree(glo);
   cudaFree(gh);
+  cudaFree(goff);
   cudaFree(gshape);
   if (e != cudaSuccess) return fail(PC_ERR_CUDA, "setup kernels failed: %s", cudaGetErrorString(e));
   if (hf[0] & (FLAG_WLS_SINGULAR | FLAG_KNN_SHORT)) {

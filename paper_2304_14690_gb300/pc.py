@@ -57,6 +57,7 @@ class ProblemDesc(ctypes.Structure):
         ("velocity_dtype", ctypes.c_int),
         ("eigenvalues", ctypes.c_int),
         ("divergence", ctypes.c_int),
+        ("grid_type", ctypes.c_int),
     ]
 
 
@@ -205,12 +206,27 @@ def _stream_handle(stream):
     return getattr(stream, "cuda_stream", stream)
 
 
+GRID_TYPE = {"cells": 0, "vertices": 1}
+
+
+def vertex_unknowns(lo, hi, n):
+    """Pressure unknowns on a vertex-grid axis of n cells with boundary kinds lo, hi."""
+    if lo == "P":
+        return n
+    neu = lambda c: c in ("W", "I")
+    if neu(lo) and neu(hi):
+        return n + 1
+    if not neu(lo) and not neu(hi):
+        return n - 1
+    return n
+
+
 EIGENVALUES = {"fd": 0, "spectral": 1}
 DIVERGENCE = {"faces": 0, "wls_direct": 1}
 
 
 def make_desc(problem, precision="fp64", refine_iters=2, gauge=0, velocity_dtype=None,
-              node_xyz=None, node_type=None, eigenvalues="fd", div_mode="faces"):
+              node_xyz=None, node_type=None, eigenvalues="fd", div_mode="faces", grid_type="cells"):
     d = ProblemDesc()
     d.dim = problem.dim
     for a in range(3):
@@ -236,6 +252,7 @@ def make_desc(problem, precision="fp64", refine_iters=2, gauge=0, velocity_dtype
     d.velocity_dtype = DTYPE[velocity_dtype]
     d.eigenvalues = EIGENVALUES[eigenvalues]
     d.divergence = DIVERGENCE[div_mode]
+    d.grid_type = GRID_TYPE[grid_type]
     return d
 
 
@@ -243,7 +260,7 @@ class Plan:
     """A libpc plan for one problem geometry (nodes, grid, boundaries)."""
 
     def __init__(self, problem, precision="fp64", refine_iters=2, gauge=0, device=0,
-                 budget_bytes=0, stream=None, eigenvalues="fd", div_mode="faces"):
+                 budget_bytes=0, stream=None, eigenvalues="fd", div_mode="faces", grid_type="cells"):
         import torch
         lib = load()
         self.problem = problem
@@ -253,14 +270,20 @@ class Plan:
         xyz = torch.as_tensor(np.ascontiguousarray(problem.nodes, dtype=np.float64), device=self.device)
         typ = torch.as_tensor(np.ascontiguousarray(problem.node_type, dtype=np.uint8), device=self.device)
         self._desc = make_desc(problem, precision, refine_iters, gauge,
-                               "f32" if self.vdtype == torch.float32 else "f64", xyz, typ, eigenvalues, div_mode)
+                               "f32" if self.vdtype == torch.float32 else "f64", xyz, typ, eigenvalues, div_mode,
+                               grid_type)
         h = ctypes.c_void_p()
         _check(lib.pc_plan_create(ctypes.byref(self._desc), device, budget_bytes,
                                   _stream_handle(stream), ctypes.byref(h)))
         self.handle = h
         self.dim = problem.dim
         self.N = problem.num_nodes
-        self.shape = tuple(int(v) for v in problem.n[: problem.dim])
+        if grid_type == "vertices":
+            # the pressure unknowns of the vertex grid (p_out, the RHS mask)
+            self.shape = tuple(vertex_unknowns(problem.bc_lo[a], problem.bc_hi[a], int(problem.n[a]))
+                               for a in range(problem.dim))
+        else:
+            self.shape = tuple(int(v) for v in problem.n[: problem.dim])
 
     def close(self):
         if getattr(self, "handle", None):
@@ -415,21 +438,6 @@ class Plan:
                                     _ptr(p_out, self.shape, torch.float64, "p_out"),
                                     ctypes.byref(st) if st is not None else None, _stream_handle(stream)))
         return p_out, (st.as_dict() if st is not None else None)
-
-
-GRID_TYPE = {"cells": 0, "vertices": 1}
-
-
-def vertex_unknowns(lo, hi, n):
-    """Pressure unknowns on a vertex-grid axis of n cells with boundary kinds lo, hi."""
-    if lo == "P":
-        return n
-    neu = lambda c: c in ("W", "I")
-    if neu(lo) and neu(hi):
-        return n + 1
-    if not neu(lo) and not neu(hi):
-        return n - 1
-    return n
 
 
 class GridPlan(Plan):

@@ -76,6 +76,8 @@ def _desc(**over):
     (dict(eigenvalues=2), 1),                        # neither FD nor pseudo-spectral
     (dict(eigenvalues=1, precision=1), 2),           # pseudo-spectral with the mixed refinement
     (dict(divergence=5), 1),                         # neither MAC faces nor direct WLS
+    (dict(grid_type=2), 1),                          # neither cells nor vertices
+    (dict(grid_type=1), 2),                          # vertices with MAC-face divergence
 ])
 def test_descriptor_validation(lib, over, status):
     d, keep = _desc(**over)

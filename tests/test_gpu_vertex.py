@@ -1,7 +1,11 @@
-"""Grid-only plans against the oracle: the Poisson solve on the vertex ("regular") pressure grid
-of §2.3 (the grid of the §3.2 results) for every boundary pairing, and on the cell-centred grid
-without nodes. The vertex solve goes through the symmetric extension to a periodic cell grid on
-the device; the oracle expands in the DCT-I / DST-I / quarter-wave eigenvectors directly."""
+"""The vertex ("regular") pressure grid of §2.3 (the grid of the §3.2 results) against the oracle.
+
+Grid-only plans: the Poisson solve for every boundary pairing, and the cell-centred solve without
+nodes. The vertex solve goes through the symmetric extension to a periodic cell grid on the device;
+the oracle expands in the DCT-I / DST-I / quarter-wave eigenvectors directly.
+
+Vertex-grid projection plans: the WLS rows at the vertex unknowns and at the nodes, one pass, the
+IB-force iteration, host arrays, clones and the RHS mask."""
 import itertools
 
 import numpy as np
@@ -186,3 +190,153 @@ def test_grid_plan_autotune_keeps_results(env):
     assert rel(p1.cpu().numpy(), ref) <= 1e-10
     assert rel(p0, ref) <= 1e-10
     plan.close()
+
+
+# ----------------------------------------------------------------------------- the vertex-grid pass
+from paper_2304_14690_gb300 import workloads as wl   # noqa: E402
+
+VCASES = [
+    dict(dim=2, n=(32, 24), bc_lo=("I", "W"), bc_hi=("D", "W"), obstacles=[("circle", (1.0, 0.75), 0.25)]),
+    dict(dim=2, n=(40, 40), bc_lo=("P", "P"), bc_hi=("P", "P"), obstacles=[("circle", (1.25, 1.25), 0.3)]),
+    dict(dim=2, n=(24, 32), bc_lo=("D", "W"), bc_hi=("W", "D")),
+    dict(dim=3, n=(12, 10, 8), bc_lo=("W", "D", "P"), bc_hi=("W", "W", "P"), obstacles=[("sphere", (0.4, 0.3, 0.25), 0.12)]),
+]
+
+
+@pytest.fixture(scope="module")
+def vproblems():
+    out = []
+    for i, c in enumerate(VCASES):
+        p = wl.generic(seed=500 + i, with_force=True, **c)
+        g = G.Grid(p.dim, p.n, p.lo, p.h, p.bc_lo, p.bc_hi)
+        pl = V.build_plan(g, p.nodes, p.node_type, K=p.knn)
+        out.append((p, pl, V.project(pl, p.dt, p.u_star, p.f_ib)))
+    return out
+
+
+def _vplan(pc, prob, precision, **kw):
+    return pc.Plan(prob, precision=precision, div_mode="wls_direct", grid_type="vertices", **kw)
+
+
+def _row_kappa(points, queries, idx, g, support_factor=3.0, eps=6.3):
+    """Condition number of the WLS normal matrix of every row (for the weight tolerance)."""
+    from oracle import knn as KNN, wls as W
+    delta = points[idx] - queries[:, None, :]
+    for a in range(g.dim):
+        if g.periodic(a):
+            L = g.length(a)
+            da = delta[..., a]
+            delta[..., a] = np.where(da > L / 2, da - L, np.where(da < -L / 2, da + L, da))
+    d2 = KNN.squared_distance(delta)
+    hs = W.support_radius(d2.max(axis=1), idx.shape[1], g.dim, support_factor)
+    w = W.gaussian_weight(d2, hs[:, None], eps)
+    q = W.basis(delta / hs[:, None, None])
+    C = np.einsum("qk,qki,qkj->qij", w, q, q)
+    return np.linalg.cond(C)
+
+
+def test_vertex_rows_match_oracle(env, vproblems):
+    """Rows at the vertex unknowns (K nearest nodes, bit-exact columns) and at the nodes (the
+    vertex block, bit-exact lattice columns); weights within the kappa bound."""
+    pc, torch, dev = env
+    ulp = np.finfo(np.float64).eps
+    for prob, opl, _ in vproblems:
+        plan = _vplan(pc, prob, "fp64")
+        g = opl.grid
+        col, D = plan.rows(prob.dim + 1)
+        assert np.array_equal(col, opl.pt_col), (prob.bc_lo, prob.n)
+        kap = _row_kappa(prob.nodes.T, V.pressure_points(g), opl.pt_col, g)
+        assert np.all(np.abs(D - opl.pt_D) <= 64 * ulp * kap[None, :, None] * np.abs(opl.pt_D).max(axis=2, keepdims=True))
+        col, D = plan.rows(prob.dim)
+        assert np.array_equal(col, opl.node_col), (prob.bc_lo, prob.n)
+        kap = _row_kappa(V.lattice_points(g), prob.nodes.T, opl.node_col, g)
+        assert np.all(np.abs(D - opl.node_D) <= 64 * ulp * kap[None, :, None] * np.abs(opl.node_D).max(axis=2, keepdims=True))
+        plan.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-10)])
+def test_vertex_project_matches_oracle(env, vproblems, precision, tol):
+    """One pass on the vertex grid against the oracle: p at the unknowns, u and f at the nodes;
+    the statistics' removed mean; the CUDA-graph replay (no statistics) bitwise equal."""
+    pc, torch, dev = env
+    for prob, _, ref in vproblems:
+        plan = _vplan(pc, prob, precision)
+        u = torch.as_tensor(prob.u_star, device=dev)
+        f = torch.as_tensor(prob.f_ib, device=dev)
+        p, uo, fo, st = plan.project(u, f, stats=True)
+        for name, got, want in (("p", p, ref["p"]), ("u", uo, ref["u"]), ("f", fo, ref["f"])):
+            e = rel(got.cpu().numpy(), want)
+            assert e <= tol, (prob.bc_lo, prob.n, precision, name, e)
+        assert abs(st["removed_mean"] - ref["removed"]) <= 1e-10 * (1 + abs(ref["removed"]))
+        p2, u2, f2, _ = plan.project(u, f)
+        p3, u3, f3, _ = plan.project(u, f)
+        assert torch.equal(p2, p3) and torch.equal(u2, u3) and torch.equal(f2, f3)
+        assert rel(p2.cpu().numpy(), ref["p"]) <= tol
+        plan.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-10)])
+def test_vertex_project_ib_matches_oracle(env, vproblems, precision, tol):
+    """The IB-force iteration on the vertex grid (device loop graph): a fixed number of passes
+    and the 1e-3 rule of §2.3, against the oracle's iteration."""
+    pc, torch, dev = env
+    for prob, opl, _ in vproblems[:2] + vproblems[3:]:
+        plan = _vplan(pc, prob, precision)
+        u = torch.as_tensor(prob.u_star, device=dev)
+        ref = V.project_ib(opl, prob.dt, prob.u_star, tol=0.0, max_iters=3)
+        p, uo, fo, info = plan.project_ib(u, tol=0.0, max_iters=3)
+        assert info["iterations"] == 3
+        for name, got, want in (("p", p, ref["p"]), ("u", uo, ref["u"]), ("f", fo, ref["f"])):
+            e = rel(got.cpu().numpy(), want)
+            assert e <= tol, (prob.bc_lo, precision, name, e)
+        ref = V.project_ib(opl, prob.dt, prob.u_star, tol=1e-3, max_iters=50)
+        p, uo, fo, info = plan.project_ib(u, tol=1e-3, max_iters=50)
+        assert info["iterations"] == ref["iterations"], (info["iterations"], ref["iterations"])
+        assert rel(fo.cpu().numpy(), ref["f"]) <= 10 * tol
+        plan.close()
+
+
+def test_vertex_project_host_arrays_and_clone(env, vproblems):
+    """Host (pinned) arrays through the staged path, and a clone's workspace, give the device
+    result bit for bit."""
+    pc, torch, dev = env
+    prob, _, ref = vproblems[0]
+    plan = _vplan(pc, prob, "mixed")
+    u = torch.as_tensor(prob.u_star, device=dev)
+    f = torch.as_tensor(prob.f_ib, device=dev)
+    p1, u1, f1, _ = plan.project(u, f)
+    hu = torch.as_tensor(prob.u_star).pin_memory()
+    hf = torch.as_tensor(prob.f_ib).pin_memory()
+    outs = (torch.empty(plan.shape, dtype=torch.float64).pin_memory(),
+            torch.empty(prob.u_star.shape, dtype=torch.float64).pin_memory(),
+            torch.empty(prob.u_star.shape, dtype=torch.float64).pin_memory())
+    p2, u2, f2, _ = plan.project(hu, hf, out=outs)
+    torch.cuda.synchronize()
+    assert np.array_equal(p2.numpy(), p1.cpu().numpy())
+    assert np.array_equal(u2.numpy(), u1.cpu().numpy()) and np.array_equal(f2.numpy(), f1.cpu().numpy())
+    c = plan.clone()
+    p3, u3, f3, _ = c.project(u, f)
+    assert torch.equal(p3, p1) and torch.equal(u3, u1) and torch.equal(f3, f1)
+    c.close()
+    plan.close()
+
+
+def test_vertex_project_rhs_mask_matches_oracle(env, vproblems):
+    pc, torch, dev = env
+    prob, opl, _ = vproblems[2]
+    plan = _vplan(pc, prob, "mixed")
+    mask = (np.random.default_rng(3).random(plan.shape) > 0.25).astype(np.uint8)
+    plan.set_rhs_mask(mask)
+    ref = V.project(opl, prob.dt, prob.u_star, prob.f_ib, rhs_mask=mask)
+    p, uo, fo, _ = plan.project(torch.as_tensor(prob.u_star, device=dev), torch.as_tensor(prob.f_ib, device=dev))
+    for name, got, want in (("p", p, ref["p"]), ("u", uo, ref["u"]), ("f", fo, ref["f"])):
+        assert rel(got.cpu().numpy(), want) <= 1e-10, name
+    plan.close()
+
+
+def test_vertex_plan_refuses_faces(env):
+    pc, torch, dev = env
+    prob = wl.generic(dim=2, n=(16, 16), seed=1)
+    with pytest.raises(pc.PcError) as e:
+        pc.Plan(prob, div_mode="faces", grid_type="vertices")
+    assert e.value.status == 2

@@ -306,3 +306,17 @@ def test_vertex_ib_relations_and_iteration():
     diff, prev = it["history"][-1]
     assert diff <= 1e-3 * prev
     assert all(d > 1e-3 * p for d, p in it["history"][:-1])
+
+
+def test_vertex_rhs_mask_zeroes_source():
+    """The masked source is zero outside the mask and unchanged inside; an all-ones mask changes
+    nothing."""
+    prob = wl.generic(dim=2, n=(16, 12), bc_lo=("W", "W"), bc_hi=("D", "W"), seed=6)
+    g = _grid(prob)
+    pl = V.build_plan(g, prob.nodes, prob.node_type, K=12)
+    r0 = V.project(pl, prob.dt, prob.u_star)
+    mask = np.random.default_rng(1).random(r0["s"].shape) > 0.3
+    r1 = V.project(pl, prob.dt, prob.u_star, rhs_mask=mask)
+    assert np.array_equal(r1["s"][mask], r0["s"][mask]) and np.all(r1["s"][~mask] == 0.0)
+    r2 = V.project(pl, prob.dt, prob.u_star, rhs_mask=np.ones_like(mask))
+    assert np.array_equal(r2["p"], r0["p"])
