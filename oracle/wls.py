@@ -57,12 +57,19 @@ def gaussian_weight(r2, hs, eps):
     return np.where(r2 <= hs * hs, w, 0.0)
 
 
-def rows(delta, d2, eps, support_factor):
+def pure_second_terms(dim):
+    """Basis indices of f_11, f_22 (, f_33): with the 1/2 factors of Eq. 16 their rows of C^-1 A
+    are the second derivatives themselves."""
+    return (3, 5) if dim == 2 else (4, 7, 9)
+
+
+def rows(delta, d2, eps, support_factor, laplacian=False):
     """WLS coefficient rows for a batch of queries.
 
     delta (Q, K, d): stencil offsets x_k - x (minimum image); d2 (Q, K): squared distances.
     The local spacing comes from the farthest stencil point (the K-th neighbour of a K-nearest
-    stencil). Returns (value_row (Q, K), grad_rows (Q, d, K)).
+    stencil). Returns (value_row (Q, K), grad_rows (Q, d, K)), and with laplacian=True also the
+    Laplacian row (Q, K): the sum of the pure second-derivative rows (scaled by 1/hs^2).
     """
     Q, K, d = delta.shape
     hs = support_radius(d2.max(axis=1), K, d, support_factor)     # (Q,)
@@ -77,4 +84,7 @@ def rows(delta, d2, eps, support_factor):
     R = np.linalg.solve(C, A)                                       # (Q, m, K) = C^-1 A
     value = R[:, 0, :]
     grad = R[:, 1:1 + d, :] / hs[:, None, None]
-    return value, grad
+    if not laplacian:
+        return value, grad
+    lap = R[:, list(pure_second_terms(d)), :].sum(axis=1) / (hs * hs)[:, None]
+    return value, grad, lap

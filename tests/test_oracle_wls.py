@@ -122,3 +122,24 @@ def test_support_radius_reading():
     assert abs(hs - 3.0 * 2.0 * math.sqrt(math.pi / 12)) < 1e-15
     hs3 = W.support_radius(np.array(4.0), 27, 3, 3.0)
     assert abs(hs3 - 3.0 * 2.0 * (4 * math.pi / 81) ** (1 / 3)) < 1e-15
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_laplacian_row_reproduces_quadratics(dim, rng):
+    """The Laplacian row (sum of the pure second-derivative rows of C^-1 A) returns 2 tr(A) for
+    f = c + b.x + x^T A x at every query, sums to 0, and misses the x^3 term's Laplacian."""
+    K = 12 if dim == 2 else 27
+    pts = _cloud(dim, rng)
+    queries = rng.uniform(-0.05, 0.05, size=(40, dim))
+    idx, d2 = KNN.knn(pts, queries, K, [-1.0] * dim, [2.0] * dim, [False] * dim)
+    delta = pts[idx] - queries[:, None, :]
+    val, grad, lap = W.rows(delta, d2, 6.3, 3.0, laplacian=True)
+    val0, grad0 = W.rows(delta, d2, 6.3, 3.0)
+    assert np.array_equal(val, val0) and np.array_equal(grad, grad0)
+    c, b, A = rng.normal(), rng.normal(size=dim), rng.normal(size=(dim, dim))
+    A = A + A.T
+    fk = c + pts[idx] @ b + np.einsum("qki,ij,qkj->qk", pts[idx], A, pts[idx])
+    assert np.abs(np.sum(lap * fk, axis=1) - 2.0 * np.trace(A)).max() < 1e-7 * (1 + abs(np.trace(A)))
+    assert np.abs(lap.sum(axis=1)).max() < 1e-6 * np.abs(lap).max()
+    cub = pts[idx][..., 0] ** 3
+    assert np.abs(np.sum(lap * cub, axis=1) - 6.0 * queries[:, 0]).max() > 1e-9
