@@ -647,7 +647,53 @@ def run_variants(args, prob, u_dev, stream, dev, flush, ms_step, reps=50):
     out["vertex_grid_project"] = {"ms_per_step": round(ms_vp, 5), "unknowns": int(np.prod(vp.shape)),
                                   "phase_ms": {k: round(v, 5) for k, v in ph_vp.items()}}
     vp.close()
+    out["time_step"] = run_time_step(args, prob, u_dev, stream, dev, flush, reps)
     return out
+
+
+def run_time_step(args, prob, u_dev, stream, dev, flush, reps):
+    """Full time steps on the same workload: the AB2 predictor of Eq. 3 on the nodes (nu = 0.01,
+    K = 12) followed by one pressure correction, both on the device; the predictor alone with
+    its roofline (algorithmic bytes per node 4K + 8(d+1)K + 48d: columns, weights, own velocity,
+    the stored R and u* read and written, u* written)."""
+    import torch
+    from paper_2304_14690_gb300 import pc
+    plan = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, device=dev.index)
+    plan.autotune()
+    mom = pc.Momentum(plan, nu=0.01)
+    outs = [plan.alloc_outputs() for _ in range(2)]
+    us = torch.empty_like(u_dev)
+    dt = prob.dt
+    u = u_dev.clone()
+    for k in range(3):
+        mom.predict(u, dt, out=us)
+        plan.project(us, dt=dt, out=outs[k % 2])
+        u = outs[k % 2][1]
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for k in range(reps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        mom.predict(u, dt, out=us, stream=stream)
+        ev[k][1].record(stream)
+        plan.project(us, dt=dt, out=outs[k % 2], stream=stream)
+        ev[k][2].record(stream)
+        u = outs[k % 2][1]
+    torch.cuda.synchronize(dev)
+    ms_pred = sum(a.elapsed_time(b) for a, b, _ in ev) / reps
+    ms_step = sum(a.elapsed_time(c) for a, _, c in ev) / reps
+    d, N, K = prob.dim, prob.num_nodes, 12
+    nbytes = N * (4 * K + 8 * (d + 1) * K + 48 * d)
+    peak, peak_src = measured_peaks()
+    ach = nbytes / (ms_pred * 1e-3) / 1e9
+    finite = bool(torch.isfinite(u).all())
+    mom.close()
+    plan.close()
+    return {"ms_per_step": round(ms_step, 5), "predictor_ms": round(ms_pred, 5), "nu": 0.01, "finite": finite,
+            "roofline_predictor": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                                   "frac": round(ach / peak, 4), "algorithmic_bytes": nbytes,
+                                   "peak_source": peak_src}}
 
 
 def run_3d(args, dev, stream, flush, world, rank):

@@ -395,6 +395,32 @@ pc_status pc_plan_clone(pc_plan *plan, void *cuda_stream, pc_plan **out_plan);
 
 pc_status pc_destroy(pc_plan *plan);
 
+/* The first fractional step around the correction: the second-order Adams-Bashforth predictor
+ * of Eq. 3 (§2.1) on the plan's nodes,
+ *   u* = u^n + (3/2) dt R^n - (1/2) dt R^{n-1},   R = -u . grad u + nu lap u + F,
+ * with R^{n-1} carrying -grad p^{n-1}. Gradient and Laplacian at a node are WLS rows (§2.2)
+ * over its knn nearest nodes (itself included), with the plan's weight constant and support
+ * factor. grad p^{n-1} at a fluid node is recovered from the last correction, u^n = u*^{n-1} -
+ * beta dt grad p^{n-1} (Eq. 18), so a run alternates pc_momentum_predict and a correction of its
+ * u* (pc_project or pc_project_ib with the same dt) whose u_out is the next u_n. The first step
+ * after create or reset is forward Euler. Boundary points get the prescribed velocity
+ * (u_boundary, NULL: zero), virtual points zero.
+ * pc_momentum_create: node_xyz [dim][N] (device or host, the coordinates the plan was built
+ * from), knn in [6, 32] (2D) or [10, 32] (3D) and <= N, nu >= 0, body_force [dim] host or NULL
+ * (zero). The plan must outlive the object. Errors: PC_ERR_INVALID_ARG, PC_ERR_WLS_SINGULAR
+ * (a node's normal matrix), PC_ERR_OUT_OF_MEMORY, PC_ERR_CUDA.
+ * pc_momentum_predict: u_n, u_boundary and u_star [dim][N] in the plan's velocity dtype, device
+ * pointers only (PC_ERR_INVALID_ARG otherwise); dt must not change between resets
+ * (PC_ERR_INVALID_ARG). Asynchronous on cuda_stream. FP64 arithmetic in FP64 plans,
+ * compensated FP32 pairs otherwise. */
+typedef struct pc_momentum pc_momentum;
+pc_status pc_momentum_create(pc_plan *plan, const double *node_xyz, int knn, double nu, const double *body_force,
+                             void *cuda_stream, pc_momentum **out);
+pc_status pc_momentum_predict(pc_momentum *m, double dt, const void *u_n, const void *u_boundary, void *u_star,
+                              void *cuda_stream);
+pc_status pc_momentum_reset(pc_momentum *m);
+pc_status pc_momentum_destroy(pc_momentum *m);
+
 const char *pc_status_string(pc_status status);
 const char *pc_last_error_message(void); /* thread-local; "" when none */
 

@@ -339,6 +339,10 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
   p->problem_singular = p->singular;
   if (vert) p->singular = true;   // the extension is periodic on every axis
   for (int a = 0; a < d->dim; ++a) {
+    p->phys_L[a] = p->ax[a].L;
+    p->phys_periodic[a] = p->ax[a].periodic;
+  }
+  for (int a = 0; a < d->dim; ++a) {
     long long rows = 1;
     for (int b = 0; b < d->dim; ++b) rows *= (b == a) ? p->ax[b].nfaces : p->ax[b].n;
     p->nface_total[a] = vert ? 0 : rows;   // a vertex grid has no faces
@@ -586,6 +590,7 @@ extern "C" pc_status pc_plan_clone(pc_plan *plan, void *cuda_stream, pc_plan **o
   p->graphs_on = root->graphs_on;
   p->vertex = root->vertex; p->problem_singular = root->problem_singular;
   p->nvtot = root->nvtot; p->nftot = root->nftot; p->npts = root->npts;
+  for (int a = 0; a < 3; ++a) { p->phys_L[a] = root->phys_L[a]; p->phys_periodic[a] = root->phys_periodic[a]; }
   for (int a = 0; a < 3; ++a) {
     p->vkind[a] = root->vkind[a]; p->vn[a] = root->vn[a]; p->nv[a] = root->nv[a];
     p->vj0[a] = root->vj0[a]; p->nf[a] = root->nf[a];

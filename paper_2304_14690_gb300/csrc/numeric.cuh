@@ -64,4 +64,28 @@ __device__ __forceinline__ float d2f_rz_bits(double v) {
                          (unsigned)((b & 0xfffffffffffffULL) >> 29));
 }
 
+// An FP64 value as an unevaluated FP32 pair (hi, lo).
+__device__ __forceinline__ float2 as_pair(double v) {
+  float hi, lo;
+  split_f64(v, hi, lo);
+  return make_float2(hi, lo);
+}
+__device__ __forceinline__ float2 as_pair(float v) { return make_float2(v, 0.0f); }
+
+// Compensated dot product in FP32 arithmetic: (w.x + w.y) . (u.x + u.y) accumulated as an
+// unevaluated pair; products by TwoProduct (fma), sums by TwoSum.
+struct DF { float hi, lo; };
+__device__ __forceinline__ void df_acc(DF &s, float2 w, float2 u) {
+  float p = w.x * u.x;
+  float e = fmaf(w.x, u.x, -p);
+  e = fmaf(w.x, u.y, e);
+  e = fmaf(w.y, u.x, e);
+  float t = s.hi + p;
+  float z = t - s.hi;
+  float err = (s.hi - (t - z)) + (p - z);
+  s.hi = t;
+  s.lo += err + e;
+}
+__device__ __forceinline__ double df_value(DF s) { return f2d_bits(s.hi) + f2d_bits(s.lo); }
+
 }  // namespace pc

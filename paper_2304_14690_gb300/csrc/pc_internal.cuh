@@ -191,6 +191,8 @@ struct Plan {
   int nf[3] = {1, 1, 1};         // lattice vertices per axis (n periodic, else n + 1)
   long long nftot = 0;
   long long npts = 0;            // pressure points with direct-divergence rows (cells or unknowns)
+  double phys_L[3] = {1.0, 1.0, 1.0};   // the physical box (a vertex plan's axes hold the extension)
+  int phys_periodic[3] = {0, 0, 0};
   double *vstage = nullptr;      // vertex plans: [2][unknowns], source and host staging of p
   int32_t *ccol = nullptr;     // direct divergence: [K][cells] node index
   double *cD64 = nullptr;      //   [dim][K][cells] derivative-row weights (FP64 plans)
@@ -317,6 +319,10 @@ pc_status solve_grid_device(Plan *p, const double *s, double *pout, cudaStream_t
 pc_status prepare_kernels();
 // Setup (setup.cu).
 pc_status build_rows(Plan *p, const double *xyz_dev, cudaStream_t st);
+// Momentum rows at every node over its K nearest nodes: columns [K][N]; first-derivative rows
+// and the Laplacian row [dim + 1][K][N], FP64 (w64) and/or FP32 pairs (w2).
+pc_status build_momentum_rows(const Plan *p, const double *xyz_dev, int K, int32_t *col, double *w64, float2 *w2,
+                              cudaStream_t st);
 // Axis tables (poisson.cu).
 pc_status build_axis_tables(Plan *p);
 

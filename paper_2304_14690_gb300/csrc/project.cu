@@ -147,12 +147,6 @@ __device__ __forceinline__ double ld(const VT *p, long long i) { return (double)
 
 __device__ __forceinline__ double as_f64(double v) { return v; }
 __device__ __forceinline__ double as_f64(float v) { return f2d_bits(v); }
-__device__ __forceinline__ float2 as_pair(double v) {
-  float hi, lo;
-  split_f64(v, hi, lo);
-  return make_float2(hi, lo);
-}
-__device__ __forceinline__ float2 as_pair(float v) { return make_float2(v, 0.0f); }
 
 // u~ = u* + dt f~; FP64 copy (FP64 path, SPLIT = false) or (hi, lo) FP32 pair (mixed). Compile-
 // time variants keep the common case (no force, no statistics) free of FP64 arithmetic.
@@ -227,21 +221,6 @@ __global__ void transfer64_kernel(int rows, int K, const int32_t *__restrict__ c
   U[r] = transfer64_row(r, rows, K, col, w, u);
 }
 
-// Compensated dot product in FP32 arithmetic: (w.x + w.y) . (u.x + u.y) accumulated as an
-// unevaluated pair; products by TwoProduct (fma), sums by TwoSum.
-struct DF { float hi, lo; };
-__device__ __forceinline__ void df_acc(DF &s, float2 w, float2 u) {
-  float p = w.x * u.x;
-  float e = fmaf(w.x, u.x, -p);
-  e = fmaf(w.x, u.y, e);
-  e = fmaf(w.y, u.x, e);
-  float t = s.hi + p;
-  float z = t - s.hi;
-  float err = (s.hi - (t - z)) + (p - z);
-  s.hi = t;
-  s.lo += err + e;
-}
-__device__ __forceinline__ double df_value(DF s) { return f2d_bits(s.hi) + f2d_bits(s.lo); }
 
 // KC > 0: the neighbour count is a compile-time constant and the loop is unrolled, so all
 // index and weight loads are in flight before the dependent gathers (memory-level parallelism).

@@ -159,6 +159,7 @@ struct WlsParams {
   double eps, support_factor, c_dim;
   int nrows_out;      // 1 (value row) or DIM (derivative rows)
   int first_row;      // 0 or 1
+  int lap_row;        // 1: one more row after them, the Laplacian (sum of the pure second-derivative rows)
 };
 
 // Given the neighbours of query q, write nrows_out rows (weights per neighbour) into w_out
@@ -205,12 +206,16 @@ __device__ bool wls_rows(const KnnCtx &c, const double *q, const int *bi, const 
       C[i][j] = t / d;
     }
   }
-  for (int r = 0; r < P.nrows_out; ++r) {
-    const int e = P.first_row + r;
+  // basis indices of the pure second derivatives (the 1/2 factors of the basis make their rows
+  // the derivatives themselves)
+  const int p0 = (DIM == 2) ? 3 : 4, p1 = (DIM == 2) ? 5 : 7, p2 = (DIM == 2) ? -1 : 9;
+  for (int r = 0; r < P.nrows_out + (P.lap_row ? 1 : 0); ++r) {
+    const bool lap = r == P.nrows_out;
+    const int e = lap ? -1 : P.first_row + r;
     double y[m];
-    // L z = e_e ; L^T y = z
+    // L z = rhs ; L^T y = z  (rhs: the unit vector e, or the sum of the pure second-derivative ones)
     for (int i = 0; i < m; ++i) {
-      double t = (i == e) ? 1.0 : 0.0;
+      double t = lap ? ((i == p0 || i == p1 || i == p2) ? 1.0 : 0.0) : ((i == e) ? 1.0 : 0.0);
       for (int k = 0; k < i; ++k) t -= C[i][k] * y[k];
       y[i] = t / C[i][i];
     }
@@ -219,7 +224,7 @@ __device__ bool wls_rows(const KnnCtx &c, const double *q, const int *bi, const 
       for (int k = i + 1; k < m; ++k) t -= C[k][i] * y[k];
       y[i] = t / C[i][i];
     }
-    const double scale = (e == 0) ? 1.0 : 1.0 / hs;
+    const double scale = lap ? 1.0 / (hs * hs) : ((e == 0) ? 1.0 : 1.0 / hs);
     for (int k = 0; k < K; ++k) {
       double qv[m];
       wls_basis<DIM>(xi_all[k], qv);
@@ -441,28 +446,36 @@ __global__ void scatter_kernel(const int *bid, long long N, const int *start, in
   sorted[start[b] + pos] = (int)i;
 }
 
-pc_status build_rows(Plan *p, const double *xyz, cudaStream_t st) {
-  const int d = p->dim;
-  const long long N = p->N;
-  // bucket grid for the nodes: about 4 nodes per bucket on average
-  KnnCtx nc{};
+// Nodes sorted into a bucket grid over the box (about 4 nodes per bucket on average), for the
+// K-nearest queries: fills nc (with the box and the bucket arrays) and owns the scratch.
+struct NodeBuckets {
+  int *bid = nullptr, *count = nullptr, *start = nullptr, *sums = nullptr, *sorted = nullptr;
+  void release() {
+    cudaFree(bid); cudaFree(count); cudaFree(start); cudaFree(sums); cudaFree(sorted);
+    bid = count = start = sums = sorted = nullptr;
+  }
+};
+
+static pc_status bucket_nodes(int d, const double *lo, const double *L, const int *periodic, const double *h,
+                              const double *xyz, long long N, cudaStream_t st, KnnCtx &nc, NodeBuckets &b) {
+  nc = KnnCtx{};
   nc.dim = d;
   double vol = 1.0;
-  for (int a = 0; a < d; ++a) vol *= p->ax[a].L;
+  for (int a = 0; a < d; ++a) vol *= L[a];
   double cs = std::pow(4.0 * vol / (double)N, 1.0 / d);
   long long nbt = 1;
   for (int a = 0; a < 3; ++a) {
     if (a < d) {
-      int nb = (int)std::floor(p->ax[a].L / cs);
+      int nb = (int)std::floor(L[a] / cs);
       if (nb < 1) nb = 1;
       if (nb > 4096) nb = 4096;
       nc.nb[a] = nb;
-      nc.cs[a] = p->ax[a].L / nb;
-      nc.lo[a] = p->lo[a];
-      nc.L[a] = (double)p->n[a] * p->h[a];
+      nc.cs[a] = L[a] / nb;
+      nc.lo[a] = lo[a];
+      nc.L[a] = L[a];
       nc.halfL[a] = 0.5 * nc.L[a];
-      nc.periodic[a] = p->ax[a].periodic;
-      nc.h[a] = p->h[a];
+      nc.periodic[a] = periodic[a];
+      nc.h[a] = h[a];
       nbt *= nb;
     } else {
       nc.nb[a] = 1;
@@ -472,30 +485,53 @@ pc_status build_rows(Plan *p, const double *xyz, cudaStream_t st) {
   nc.xyz = xyz;
   nc.N = N;
   nc.cells = 0;
-  int *bid = nullptr, *count = nullptr, *start = nullptr, *sums = nullptr, *sorted = nullptr;
-  unsigned int *flags = nullptr;
   long long nblk = (nbt + 1 + 1023) / 1024;   // scan covers nbt + 1 entries
+  if (cudaMalloc(&b.bid, N * sizeof(int)) != cudaSuccess || cudaMalloc(&b.count, (nbt + 1) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&b.start, (nbt + 1) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&b.sums, (nblk + 1) * sizeof(int)) != cudaSuccess || cudaMalloc(&b.sorted, N * sizeof(int)) != cudaSuccess) {
+    b.release();
+    return fail(PC_ERR_OUT_OF_MEMORY, "setup scratch allocation failed");
+  }
+  cudaMemsetAsync(b.count, 0, (nbt + 1) * sizeof(int), st);
+  bucket_count_kernel<<<grid_for(N, 256), 256, 0, st>>>(xyz, N, nc, b.bid, b.count);
+  scan_block_kernel<<<(unsigned)nblk, 1024, 0, st>>>(b.count, b.start, b.sums, nbt + 1);
+  scan_sums_kernel<<<1, 32, 0, st>>>(b.sums, (int)nblk);
+  scan_add_kernel<<<(unsigned)nblk, 1024, 0, st>>>(b.start, b.sums, nbt + 1);
+  cudaMemsetAsync(b.count, 0, (nbt + 1) * sizeof(int), st);
+  scatter_kernel<<<grid_for(N, 256), 256, 0, st>>>(b.bid, N, b.start, b.count, b.sorted);
+  nc.start = b.start;
+  nc.sorted = b.sorted;
+  return PC_OK;
+}
+
+pc_status build_rows(Plan *p, const double *xyz, cudaStream_t st) {
+  const int d = p->dim;
+  const long long N = p->N;
+  KnnCtx nc{};
+  NodeBuckets nb{};
+  unsigned int *flags = nullptr;
   auto cleanup = [&]() {
-    cudaFree(bid); cudaFree(count); cudaFree(start); cudaFree(sums); cudaFree(sorted); cudaFree(flags);
+    nb.release();
+    cudaFree(flags);
   };
-  if (cudaMalloc(&bid, N * sizeof(int)) != cudaSuccess || cudaMalloc(&count, (nbt + 1) * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&start, (nbt + 1) * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&sums, (nblk + 1) * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&sorted, N * sizeof(int)) != cudaSuccess || cudaMalloc(&flags, 4 * sizeof(unsigned)) != cudaSuccess) {
+  {
+    double L[3], lo[3], h[3];
+    int per[3];
+    for (int a = 0; a < 3; ++a) {
+      L[a] = a < d ? p->ax[a].L : 1.0;
+      lo[a] = p->lo[a];
+      h[a] = p->h[a];
+      per[a] = a < d ? (int)p->ax[a].periodic : 0;
+    }
+    pc_status bs = bucket_nodes(d, lo, L, per, h, xyz, N, st, nc, nb);
+    if (bs != PC_OK) return bs;
+  }
+  if (cudaMalloc(&flags, 4 * sizeof(unsigned)) != cudaSuccess) {
     cleanup();
     return fail(PC_ERR_OUT_OF_MEMORY, "setup scratch allocation failed");
   }
-  cudaMemsetAsync(count, 0, (nbt + 1) * sizeof(int), st);
   cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned), st);
   cudaMemsetAsync(flags + 2, 0xff, 2 * sizeof(unsigned), st);
-  bucket_count_kernel<<<grid_for(N, 256), 256, 0, st>>>(xyz, N, nc, bid, count);
-  scan_block_kernel<<<(unsigned)nblk, 1024, 0, st>>>(count, start, sums, nbt + 1);
-  scan_sums_kernel<<<1, 32, 0, st>>>(sums, (int)nblk);
-  scan_add_kernel<<<(unsigned)nblk, 1024, 0, st>>>(start, sums, nbt + 1);
-  cudaMemsetAsync(count, 0, (nbt + 1) * sizeof(int), st);
-  scatter_kernel<<<grid_for(N, 256), 256, 0, st>>>(bid, N, start, count, sorted);
-  nc.start = start;
-  nc.sorted = sorted;
 
   WlsParams P{};
   P.K = p->K;
@@ -595,6 +631,78 @@ pc_status build_rows(Plan *p, const double *xyz, cudaStream_t st) {
                 set < 3 ? (set == 0 ? "face row, axis 0," : (set == 1 ? "face row, axis 1," : "face row, axis 2,"))
                         : (set == 4 ? "cell row" : "node"),
                 row);
+  }
+  return PC_OK;
+}
+
+
+// Rows of the meshless momentum operators (§2.2 at the nodes): for every node, its K nearest
+// nodes (itself included, at distance 0), the first-derivative rows and the Laplacian row.
+template <int DIM>
+__global__ void momentum_rows_kernel(KnnCtx c, WlsParams P, const double *xyz, long long N, int32_t *col,
+                                     double *w64, float2 *w2, unsigned int *flags) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int K = P.K;
+  double q[3];
+  for (int a = 0; a < DIM; ++a) q[a] = xyz[(long long)a * N + i];
+  double bd[kMaxK];
+  int bi[kMaxK];
+  double w[(DIM + 1) * kMaxK];
+  bool ok = knn_query(c, q, K, bd, bi);
+  if (!ok) record_failure(flags, FLAG_KNN_SHORT, 5, i);
+  else if (!wls_rows<DIM>(c, q, bi, bd, P, w)) { ok = false; record_failure(flags, FLAG_WLS_SINGULAR, 5, i); }
+  if (!ok) {
+    for (int k = 0; k < K; ++k) bi[k] = (int)i;
+    for (int k = 0; k < (DIM + 1) * K; ++k) w[k] = 0.0;
+  }
+  for (int k = 0; k < K; ++k) {
+    col[(long long)k * N + i] = bi[k];
+    for (int r = 0; r <= DIM; ++r) split_store(w[r * K + k], w64, w2, ((long long)r * K + k) * N + i);
+  }
+}
+
+pc_status build_momentum_rows(const Plan *p, const double *xyz, int K, int32_t *col, double *w64, float2 *w2,
+                              cudaStream_t st) {
+  const int d = p->dim;
+  const long long N = p->N;
+  KnnCtx nc{};
+  NodeBuckets nb{};
+  unsigned int *flags = nullptr;
+  {
+    double lo[3], h[3];
+    for (int a = 0; a < 3; ++a) { lo[a] = p->lo[a]; h[a] = p->h[a]; }
+    pc_status bs = bucket_nodes(d, lo, p->phys_L, p->phys_periodic, h, xyz, N, st, nc, nb);
+    if (bs != PC_OK) return bs;
+  }
+  if (cudaMalloc(&flags, 4 * sizeof(unsigned)) != cudaSuccess) {
+    nb.release();
+    return fail(PC_ERR_OUT_OF_MEMORY, "setup scratch allocation failed");
+  }
+  cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned), st);
+  cudaMemsetAsync(flags + 2, 0xff, 2 * sizeof(unsigned), st);
+  WlsParams P{};
+  P.K = K;
+  P.eps = p->eps;
+  P.support_factor = p->support_factor;
+  const double pi = 3.14159265358979323846;
+  P.c_dim = (d == 2) ? std::sqrt(pi / K) : std::pow(4.0 * pi / (3.0 * K), 1.0 / 3.0);
+  P.first_row = 1;
+  P.nrows_out = d;
+  P.lap_row = 1;
+  if (d == 2) momentum_rows_kernel<2><<<grid_for(N, 128), 128, 0, st>>>(nc, P, xyz, N, col, w64, w2, flags);
+  else momentum_rows_kernel<3><<<grid_for(N, 128), 128, 0, st>>>(nc, P, xyz, N, col, w64, w2, flags);
+  cudaError_t e = cudaGetLastError();
+  unsigned int hf[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hf, flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  nb.release();
+  cudaFree(flags);
+  if (e != cudaSuccess) return fail(PC_ERR_CUDA, "momentum row setup failed: %s", cudaGetErrorString(e));
+  if (hf[0] & (FLAG_WLS_SINGULAR | FLAG_KNN_SHORT)) {
+    unsigned long long key = ((unsigned long long)hf[3] << 32) | hf[2];
+    return fail(PC_ERR_WLS_SINGULAR, "momentum rows: WLS setup failed at node %lld",
+                (long long)(key & ((1ULL << 48) - 1)));
   }
   return PC_OK;
 }

@@ -153,6 +153,13 @@ FUNCTIONS = {
     "pc_batcher_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
                                          ctypes.POINTER(ProjectArgs), ctypes.c_void_p]),
     "pc_batcher_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "pc_momentum_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                          ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "pc_momentum_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
+    "pc_momentum_reset": (ctypes.c_int, [ctypes.c_void_p]),
+    "pc_momentum_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "pc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pc_last_error_message": (ctypes.c_char_p, []),
 }
@@ -473,6 +480,51 @@ class GridPlan(Plan):
             self.shape = tuple(vertex_unknowns(bc_lo[a], bc_hi[a], int(n[a])) for a in range(dim))
         else:
             self.shape = tuple(int(n[a]) for a in range(dim))
+
+
+class Momentum:
+    """pc_momentum: the AB2 predictor of Eq. 3 on a plan's nodes. predict(u_n, dt) returns u*;
+    correct it with the plan (project / project_ib, same dt) and feed the corrected velocity to
+    the next predict."""
+
+    def __init__(self, plan, nu=0.0, force=None, knn=None, stream=None):
+        lib = load()
+        self.plan = plan
+        prob = plan.problem
+        xyz = np.ascontiguousarray(prob.nodes, dtype=np.float64)
+        f = None
+        if force is not None:
+            f = (ctypes.c_double * 3)(*[float(force[a]) if a < plan.dim else 0.0 for a in range(3)])
+        h = ctypes.c_void_p()
+        _check(lib.pc_momentum_create(plan.handle, xyz.ctypes.data, int(knn or prob.knn), float(nu), f,
+                                      _stream_handle(stream), ctypes.byref(h)))
+        self.handle = h
+        self._shape = (plan.dim, plan.N)
+        self._dtype = plan.vdtype
+        self._device = plan.device
+
+    def predict(self, u_n, dt, u_boundary=None, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self._shape, dtype=self._dtype, device=self._device)
+        _check(load().pc_momentum_predict(self.handle, float(dt), _ptr(u_n, self._shape, self._dtype, "u_n"),
+                                          _ptr(u_boundary, self._shape, self._dtype, "u_boundary"),
+                                          _ptr(out, self._shape, self._dtype, "u_star"), _stream_handle(stream)))
+        return out
+
+    def reset(self):
+        _check(load().pc_momentum_reset(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(load().pc_momentum_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solve_poisson_static(dim, n, h, bc_lo, bc_hi, s, p_out, gauge=0, stream=None):
