@@ -48,12 +48,15 @@ bool device_ptr(const void *ptr) {
 template <typename VT>
 __device__ __forceinline__ double vload(const VT *p, long long i) { return (double)p[i]; }
 
-template <typename VT, int DIM, bool MIXED>
-__global__ void ab2_predict_kernel(int N, int K, const int32_t *__restrict__ col, const double *__restrict__ W,
+// KC > 0: the neighbour count is a compile-time constant, the loop is unrolled and every column
+// and weight load is issued before the dependent gathers (as in the transfer kernels).
+template <typename VT, int DIM, bool MIXED, int KC>
+__global__ void ab2_predict_kernel(int N, int Kr, const int32_t *__restrict__ col, const double *__restrict__ W,
                                    const float2 *__restrict__ W2, const uint8_t *__restrict__ type,
                                    const VT *__restrict__ u, const VT *__restrict__ ub, double dt, double inv_bdt,
                                    double nu, double F0, double F1, double F2, int first, double *R_prev,
                                    double *us_prev, VT *__restrict__ us) {
+  const int K = KC > 0 ? KC : Kr;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const uint8_t t = type[i];
@@ -76,7 +79,7 @@ __global__ void ab2_predict_kernel(int N, int K, const int32_t *__restrict__ col
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
       for (int r = 0; r <= DIM; ++r) acc[a][r] = DF{0.f, 0.f};
-#pragma unroll 4
+#pragma unroll (KC > 0 ? KC : 4)
     for (int k = 0; k < K; ++k) {
       const int j = __ldg(col + (long long)k * N + i);
       float2 w[DIM + 1];
@@ -98,7 +101,7 @@ __global__ void ab2_predict_kernel(int N, int K, const int32_t *__restrict__ col
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
       for (int r = 0; r <= DIM; ++r) g[a][r] = 0.0;
-#pragma unroll 4
+#pragma unroll (KC > 0 ? KC : 4)
     for (int k = 0; k < K; ++k) {
       const int j = __ldg(col + (long long)k * N + i);
       double w[DIM + 1];
@@ -143,15 +146,25 @@ void launch_predict(pc_momentum *m, double dt, const void *u, const void *ub, vo
   const int first = m->steps == 0;
   const VT *uu = static_cast<const VT *>(u), *bb = static_cast<const VT *>(ub);
   VT *oo = static_cast<VT *>(us);
-#define PC_PREDICT(D, MX)                                                                                     \
-  ab2_predict_kernel<VT, D, MX><<<G, T, 0, st>>>(N, m->K, m->col, m->w64, m->w2, p->ntype, uu, bb, dt, inv_bdt, \
-                                                 m->nu, m->F[0], m->F[1], m->F[2], first, m->R_prev, m->us_prev, oo)
+#define PC_PREDICT(D, MX, KC)                                                                                   \
+  ab2_predict_kernel<VT, D, MX, KC><<<G, T, 0, st>>>(N, m->K, m->col, m->w64, m->w2, p->ntype, uu, bb, dt, inv_bdt, \
+                                                     m->nu, m->F[0], m->F[1], m->F[2], first, m->R_prev, m->us_prev, oo)
   if (p->dim == 2) {
-    if (m->mixed) PC_PREDICT(2, true);
-    else PC_PREDICT(2, false);
+    if (m->K == 12) {
+      if (m->mixed) PC_PREDICT(2, true, 12);
+      else PC_PREDICT(2, false, 12);
+    } else {
+      if (m->mixed) PC_PREDICT(2, true, 0);
+      else PC_PREDICT(2, false, 0);
+    }
   } else {
-    if (m->mixed) PC_PREDICT(3, true);
-    else PC_PREDICT(3, false);
+    if (m->K == 27) {
+      if (m->mixed) PC_PREDICT(3, true, 27);
+      else PC_PREDICT(3, false, 27);
+    } else {
+      if (m->mixed) PC_PREDICT(3, true, 0);
+      else PC_PREDICT(3, false, 0);
+    }
   }
 #undef PC_PREDICT
 }
