@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-problem batch measurement")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--batch-problems", type=int, default=512,
+                    help="problems in the batch measurement (fewer: the same mix, for profiling)")
     ap.add_argument("--no-3d", action="store_true", help="skip the 256x128x128 box-with-sphere measurement")
     ap.add_argument("--steps-3d", type=int, default=20)
     ap.add_argument("--serve", action="store_true",
@@ -776,7 +778,7 @@ def run_batch(args, dev, stream, flush, world):
     import torch
     from paper_2304_14690_gb300 import pc, workloads as wl
     t0 = time.perf_counter()
-    probs = wl.batch_2d()
+    probs = wl.batch_2d(count=args.batch_problems)
     plans, bargs = [], []
     for pr in probs:
         plan = pc.Plan(pr, precision=args.precision, refine_iters=args.refine, device=dev.index)
