@@ -113,7 +113,9 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   const int M = ax.M;
   // threads per line: a power of two with at most E slots per thread; the kernel instance is
   // the smallest power of two >= M / tpl
-  const int E = (sizeof(Real) == 8) ? ax.slots64 : ax.slots32;
+  int E = (sizeof(Real) == 8) ? ax.slots64 : ax.slots32;
+  // a line must fit one CTA: longer lines take more slots per thread (up to 16)
+  while (E < 16 && (M + E - 1) / E > kMaxPassThreads) E *= 2;
   const int tpl = 1 << ilog2((M + E - 1) / E);
   const int emax = 1 << ilog2((M + tpl - 1) / tpl);
   A.emax = emax;

@@ -902,49 +902,47 @@ __device__ __forceinline__ int vertex_fold(int kind, int n, int e, double &sign)
       return 4 * n - e - 1;
   }
 }
-__global__ void vertex_extend_kernel(VertexGrid V, const double *__restrict__ sv, double *__restrict__ se,
-                                     long long ne) {
+// Both kernels run on a grid whose x covers the last axis and whose y (and z) are the indices of
+// the other axes, so no thread divides to find its position.
+__device__ __forceinline__ void grid_position(int dim, int *idx) {
+  idx[dim - 1] = blockIdx.x * blockDim.x + threadIdx.x;
+  idx[dim - 2] = blockIdx.y;
+  if (dim == 3) idx[0] = blockIdx.z;
+}
+__global__ void vertex_extend_kernel(VertexGrid V, const double *__restrict__ sv, double *__restrict__ se) {
   pdl_enter();
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= ne) return;
   int idx[3];
-  long long rem = e;
-  for (int a = V.dim - 1; a >= 0; --a) {
-    idx[a] = (int)(rem % V.m[a]);
-    rem /= V.m[a];
-  }
-  long long u = 0;
-  double sg = 1.0;
-  bool zero = false;
+  grid_position(V.dim, idx);
+  if (idx[V.dim - 1] >= V.m[V.dim - 1]) return;
+  int e = 0, u = 0;
+  bool zero = false, neg = false;
   for (int a = 0; a < V.dim; ++a) {
     double sa;
     const int ua = vertex_fold(V.kind[a], V.n[a], idx[a], sa);
+    e = e * V.m[a] + idx[a];
     if (ua < 0) zero = true;
     else {
       u = u * V.nv[a] + ua;
-      sg *= sa;
+      neg ^= sa < 0.0;
     }
   }
-  se[e] = zero ? 0.0 : sg * sv[u];
+  double v = zero ? 0.0 : sv[u];
+  se[e] = neg ? -v : v;
 }
 // The extended solution on the vertex lattice (vertex j of an axis is extended cell j). Writes
 // any of: the unknowns (pv), the whole lattice in FP64 (pl, Dirichlet boundary vertices exactly
 // 0) and as FP32 (hi, lo) pairs (pl2) for the compensated gradient.
 __global__ void vertex_restrict_kernel(VertexGrid V, const double *__restrict__ pe, double *__restrict__ pv,
-                                       double *__restrict__ pl, float2 *__restrict__ pl2, long long nlat) {
+                                       double *__restrict__ pl, float2 *__restrict__ pl2) {
   pdl_enter();
-  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= nlat) return;
   int idx[3];
-  long long rem = l;
-  for (int a = V.dim - 1; a >= 0; --a) {
-    idx[a] = (int)(rem % V.nf[a]);
-    rem /= V.nf[a];
-  }
-  long long e = 0, u = 0;
+  grid_position(V.dim, idx);
+  if (idx[V.dim - 1] >= V.nf[V.dim - 1]) return;
+  int e = 0, u = 0, l = 0;
   bool unknown = true;
   for (int a = 0; a < V.dim; ++a) {
     e = e * V.m[a] + idx[a];
+    l = l * V.nf[a] + idx[a];
     const int ua = idx[a] - V.j0[a];
     if (ua < 0 || ua >= V.nv[a]) unknown = false;   // a Dirichlet boundary vertex
     u = u * V.nv[a] + (ua < 0 ? 0 : ua);
@@ -953,6 +951,11 @@ __global__ void vertex_restrict_kernel(VertexGrid V, const double *__restrict__ 
   if (pv && unknown) pv[u] = v;
   if (pl) pl[l] = v;
   if (pl2) pl2[l] = as_pair(v);
+}
+// Launch shapes of the two kernels: x over the last axis, y and z over the others.
+static dim3 vertex_grid_dims(int dim, const int *shape, int threads) {
+  return dim3((unsigned)((shape[dim - 1] + threads - 1) / threads), (unsigned)shape[dim - 2],
+              dim == 3 ? (unsigned)shape[0] : 1u);
 }
 
 static GridDev grid_dev(const Plan *p);
@@ -1384,15 +1387,15 @@ static pc_status vertex_pass_solve(Plan *p, cudaStream_t st, double inv_bdt, dou
   }
   count_launch(p);
   const VertexGrid V = vertex_grid(p);
-  launch_pdl(vertex_extend_kernel, grid_for(nc, T), T, 0, st, V, (const double *)sv, p->s64, nc);
+  launch_pdl(vertex_extend_kernel, vertex_grid_dims(p->dim, V.m, T), T, 0, st, V, (const double *)sv, p->s64);
   count_launch(p);
   launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, (const double *)p->s64, p->dstats,
              p->partials, p->counters);
   count_launch(p);
   prof_mark(p, st, 2);
   PC_TRY(solve_grid(p, p->s64, p->stage_p, want_stats, st));
-  launch_pdl(vertex_restrict_kernel, grid_for(p->nftot, T), T, 0, st, V, (const double *)p->stage_p, dp,
-             p->work64, mixed ? reinterpret_cast<float2 *>(p->p2) : (float2 *)nullptr, p->nftot);
+  launch_pdl(vertex_restrict_kernel, vertex_grid_dims(p->dim, V.nf, T), T, 0, st, V, (const double *)p->stage_p, dp,
+             p->work64, mixed ? reinterpret_cast<float2 *>(p->p2) : (float2 *)nullptr);
   count_launch(p);
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
@@ -1553,14 +1556,14 @@ static pc_status vertex_solve(Plan *p, const double *s, double *p_out, pc_stats 
   const VertexGrid V = vertex_grid(p);
   prof_begin(p, st);
   PC_CUDA_TRY(cudaMemsetAsync(p->dstats, 0, sizeof(DevStats), st));
-  vertex_extend_kernel<<<grid_for(nc, 256), 256, 0, st>>>(V, ds, p->stage_s, nc);
+  vertex_extend_kernel<<<vertex_grid_dims(p->dim, V.m, 256), 256, 0, st>>>(V, ds, p->stage_s);
   count_launch(p);
   launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, (const double *)p->stage_s, p->dstats,
              p->partials, p->counters);
   count_launch(p);
   prof_mark(p, st, 2);
   PC_TRY(solve_grid(p, p->stage_s, p->stage_p, stats != nullptr, st));
-  vertex_restrict_kernel<<<grid_for(p->nftot, 256), 256, 0, st>>>(V, p->stage_p, dp, nullptr, nullptr, p->nftot);
+  vertex_restrict_kernel<<<vertex_grid_dims(p->dim, V.nf, 256), 256, 0, st>>>(V, p->stage_p, dp, nullptr, nullptr);
   count_launch(p);
   PC_CUDA_TRY(cudaGetLastError());
   if (hp) PC_CUDA_TRY(cudaMemcpyAsync(p_out, dp, nvt * sizeof(double), cudaMemcpyDeviceToHost, st));

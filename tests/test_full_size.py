@@ -94,6 +94,49 @@ def test_channel_ib_iteration(env, channel):
         plan.close()
 
 
+def test_channel_vertex_projection(env, channel):
+    """The channel workload on the regular (vertex) pressure grid (1024 x 513 unknowns, N-D by
+    N-N; transforms on the 4096 x 1024 extension), in the benchmark's launch configuration:
+    one pass against the oracle's vertex pass, p, u, f element by element."""
+    from oracle import vertex as V
+    pc, torch, dev = env
+    prob, _ = channel
+    vpl = V.build_plan(grid_of(prob), prob.nodes, prob.node_type, K=prob.knn)
+    ref = V.project(vpl, prob.dt, prob.u_star)
+    u = torch.as_tensor(prob.u_star, device=dev)
+    for precision, tol in (("fp64", 1e-12), ("mixed", 1e-10)):
+        plan = pc.Plan(prob, precision=precision, div_mode="wls_direct", grid_type="vertices")
+        if precision == "mixed":
+            plan.autotune()
+        p, uo, fo, _ = plan.project(u)
+        assert p.shape == ref["p"].shape
+        assert rel(p.cpu().numpy(), ref["p"]) <= tol, precision
+        assert rel(uo.cpu().numpy(), ref["u"]) <= tol, precision
+        assert rel(fo.cpu().numpy(), ref["f"]) <= tol, precision
+        plan.close()
+
+
+@pytest.mark.parametrize("kinds", [(("I", "D"), ("W", "W")), (("D", "W"), ("P", "P"))])
+def test_vertex_solve_maximum_extension(env, kinds):
+    """Vertex-grid solves at the largest extension the transforms take (4096 per axis): a
+    1024-cell N-D or D-N axis (4n) with a 2048-cell N-N or P-P axis, against the oracle's
+    DCT-I / quarter-wave expansion."""
+    from oracle import vertex as V
+    pc, torch, dev = env
+    (lo0, hi0), (lo1, hi1) = kinds
+    n = (1024, 2048) if lo1 != "P" else (1024, 4096)
+    h = (1.0 / n[0], 1.0 / n[1])
+    lo, hi = (lo0, lo1), (hi0, hi1)
+    shape = tuple(V.unknowns(V.axis_kind(lo[a], hi[a]), n[a])[0] for a in range(2))
+    s = np.random.default_rng(17).normal(size=shape)
+    ref, _ = V.solve(s, n, h, lo, hi)
+    for precision, tol in (("fp64", 1e-12), ("mixed", 1e-10)):
+        plan = pc.GridPlan(2, n, h, lo, hi, grid_type="vertices", precision=precision)
+        p, _ = plan.solve_poisson(torch.as_tensor(s, device=dev))
+        assert rel(p.cpu().numpy(), ref) <= tol, (kinds, precision)
+        plan.close()
+
+
 @pytest.fixture(scope="module")
 def box(env):
     pc, torch, dev = env
