@@ -1,5 +1,9 @@
 """GPU parity at the full sizes of the measured workloads, through the C ABI.
 
+The channel workload also runs on the vertex grid (one pass and the IB iteration against the
+oracle's vertex pass) and through the AB2 predictor (two steps against the oracle); vertex
+solves run at the largest extension the transforms take.
+
 Channel with cylinder, 1024x512 cells, ~4.0e5 nodes (the benchmark workload): the oracle runs
 the whole projection, and the IB-force iteration at tolerance 1e-3, so p, u and f are compared
 element by element (FP64 1e-12, mixed 1e-10 relative L2).
@@ -113,6 +117,49 @@ def test_channel_vertex_projection(env, channel):
         assert rel(p.cpu().numpy(), ref["p"]) <= tol, precision
         assert rel(uo.cpu().numpy(), ref["u"]) <= tol, precision
         assert rel(fo.cpu().numpy(), ref["f"]) <= tol, precision
+        plan.close()
+
+
+def test_channel_vertex_ib_iteration(env, channel):
+    """The IB-force iteration at tolerance 1e-3 on the channel's vertex grid: same number of
+    passes as the oracle, p, u, f element by element."""
+    from oracle import vertex as V
+    pc, torch, dev = env
+    prob, _ = channel
+    vpl = V.build_plan(grid_of(prob), prob.nodes, prob.node_type, K=prob.knn)
+    ref = V.project_ib(vpl, prob.dt, prob.u_star, tol=1e-3, max_iters=50)
+    ratios = [d / p for d, p in ref["history"] if p > 0]
+    assert all(abs(r / 1e-3 - 1.0) > 0.05 for r in ratios)
+    u = torch.as_tensor(prob.u_star, device=dev)
+    plan = pc.Plan(prob, precision="mixed", div_mode="wls_direct", grid_type="vertices")
+    plan.autotune()
+    p, uo, fo, info = plan.project_ib(u, tol=1e-3, max_iters=50)
+    assert info["iterations"] == ref["iterations"] and info["converged"]
+    for got, want in ((p, ref["p"]), (uo, ref["u"]), (fo, ref["f"])):
+        assert rel(got.cpu().numpy(), want) <= 1e-10
+    plan.close()
+
+
+def test_channel_predictor_full_size(env, channel):
+    """The AB2 predictor on the channel's 398,401 nodes (K = 12) in the launch configuration of
+    the bench's time step: two steps (Euler start, then AB2 with the recovered pressure
+    gradient) against the oracle, the correction between them taken from the oracle."""
+    from oracle import momentum as M
+    pc, torch, dev = env
+    prob, oplan = channel
+    m_ref = M.build(grid_of(prob), prob.nodes, prob.node_type, K=12, nu=0.01)
+    dt = 1e-4
+    for precision, tol in (("fp64", 1e-12), ("mixed", 1e-10)):
+        M.reset(m_ref)
+        plan = pc.Plan(prob, precision=precision)
+        mom = pc.Momentum(plan, nu=0.01)
+        u = prob.u_star.copy()
+        for step in range(2):
+            want = M.predict(m_ref, dt, u)
+            got = mom.predict(torch.as_tensor(u, device=dev), dt)
+            assert rel(got.cpu().numpy(), want) <= tol, (precision, step)
+            u = PR.project(oplan, dt, want)["u"]
+        mom.close()
         plan.close()
 
 
