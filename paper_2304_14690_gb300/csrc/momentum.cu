@@ -81,10 +81,10 @@ __global__ void ab2_predict_kernel(int N, int Kr, const int32_t *__restrict__ co
       for (int r = 0; r <= DIM; ++r) acc[a][r] = DF{0.f, 0.f};
 #pragma unroll (KC > 0 ? KC : 4)
     for (int k = 0; k < K; ++k) {
-      const int j = __ldg(col + (long long)k * N + i);
+      const int j = __ldcs(col + (long long)k * N + i);
       float2 w[DIM + 1];
 #pragma unroll
-      for (int r = 0; r <= DIM; ++r) w[r] = __ldg(W2 + ((long long)r * K + k) * N + i);
+      for (int r = 0; r <= DIM; ++r) w[r] = __ldcs(W2 + ((long long)r * K + k) * N + i);
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         const float2 ua = as_pair(u[(long long)a * N + j]);
@@ -103,10 +103,10 @@ __global__ void ab2_predict_kernel(int N, int Kr, const int32_t *__restrict__ co
       for (int r = 0; r <= DIM; ++r) g[a][r] = 0.0;
 #pragma unroll (KC > 0 ? KC : 4)
     for (int k = 0; k < K; ++k) {
-      const int j = __ldg(col + (long long)k * N + i);
+      const int j = __ldcs(col + (long long)k * N + i);
       double w[DIM + 1];
 #pragma unroll
-      for (int r = 0; r <= DIM; ++r) w[r] = __ldg(W + ((long long)r * K + k) * N + i);
+      for (int r = 0; r <= DIM; ++r) w[r] = __ldcs(W + ((long long)r * K + k) * N + i);
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
         const double ua = vload(u, (long long)a * N + j);

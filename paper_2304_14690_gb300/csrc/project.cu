@@ -208,7 +208,7 @@ __device__ __forceinline__ double transfer64_row(int r, int rows, int K, const i
 #pragma unroll 4
   for (int k = 0; k < K; ++k) {
     int at = k * rows + r;
-    acc = fma(__ldg(w + at), __ldg(u + __ldg(col + at)), acc);
+    acc = fma(__ldcs(w + at), __ldg(u + __ldcs(col + at)), acc);
   }
   return acc;
 }
@@ -239,9 +239,9 @@ __device__ __forceinline__ double transfer_mixed_row(int r, int rows, int Kr, co
     int c[KC > 0 ? KC : 1];
     float2 w[KC > 0 ? KC : 1];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      c[k] = __ldg(col + k * rows + r);
-      w[k] = __ldg(w2 + k * rows + r);
+    for (int k = 0; k < K; ++k) {   // read once: streamed past the caches that hold the gathered values
+      c[k] = __ldcs(col + k * rows + r);
+      w[k] = __ldcs(w2 + k * rows + r);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) df_acc(s, w[k], src(c[k]));
@@ -249,7 +249,7 @@ __device__ __forceinline__ double transfer_mixed_row(int r, int rows, int Kr, co
 #pragma unroll 4
     for (int k = 0; k < K; ++k) {
       int at = k * rows + r;
-      df_acc(s, __ldg(w2 + at), src(__ldg(col + at)));
+      df_acc(s, __ldcs(w2 + at), src(__ldcs(col + at)));
     }
   }
   return df_value(s);
@@ -403,19 +403,19 @@ __global__ void direct_div_kernel(int nc, int K, const int32_t *__restrict__ col
     if (MIXED) {
       DF acc{0.f, 0.f};
       for (int k = 0; k < K; ++k) {
-        const int j = __ldg(col + (long long)k * nc + c);
+        const int j = __ldcs(col + (long long)k * nc + c);
 #pragma unroll
         for (int a = 0; a < DIM; ++a)
-          df_acc(acc, __ldg(D2 + ((long long)a * K + k) * nc + c), __ldg(u2 + (long long)a * N + j));
+          df_acc(acc, __ldcs(D2 + ((long long)a * K + k) * nc + c), __ldg(u2 + (long long)a * N + j));
       }
       v = df_value(acc) * inv_bdt;
     } else {
       double acc = 0.0;
       for (int k = 0; k < K; ++k) {
-        const int j = __ldg(col + (long long)k * nc + c);
+        const int j = __ldcs(col + (long long)k * nc + c);
 #pragma unroll
         for (int a = 0; a < DIM; ++a)
-          acc = fma(__ldg(D + ((long long)a * K + k) * nc + c), __ldg(ut64 + (long long)a * N + j), acc);
+          acc = fma(__ldcs(D + ((long long)a * K + k) * nc + c), __ldg(ut64 + (long long)a * N + j), acc);
       }
       v = acc * inv_bdt;
     }
@@ -597,9 +597,9 @@ __device__ __forceinline__ void grad64_at(int i, int N, int K, const int32_t *__
   for (int a = 0; a < DIM; ++a) g[a] = 0.0;
 #pragma unroll 3
   for (int k = 0; k < K; ++k) {
-    double pv = __ldg(p + __ldg(col + k * N + i));
+    double pv = __ldg(p + __ldcs(col + k * N + i));
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) g[a] = fma(__ldg(D + (a * K + k) * N + i), pv, g[a]);
+    for (int a = 0; a < DIM; ++a) g[a] = fma(__ldcs(D + (a * K + k) * N + i), pv, g[a]);
   }
 }
 
@@ -638,12 +638,12 @@ __device__ __forceinline__ void grad_mixed_at(int i, int N, const int32_t *__res
   for (int a = 0; a < DIM; ++a) g[a] = DF{0.f, 0.f};
   int c[KB];
 #pragma unroll
-  for (int k = 0; k < KB; ++k) c[k] = __ldg(col + k * N + i);
+  for (int k = 0; k < KB; ++k) c[k] = __ldcs(col + k * N + i);   // rows: read once, streamed
 #pragma unroll
   for (int k = 0; k < KB; ++k) {
     const float2 pv = __ldg(p2 + c[k]);
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) df_acc(g[a], __ldg(D2 + (a * KB + k) * N + i), pv);
+    for (int a = 0; a < DIM; ++a) df_acc(g[a], __ldcs(D2 + (a * KB + k) * N + i), pv);
   }
 #pragma unroll
   for (int a = 0; a < DIM; ++a) gout[a] = df_value(g[a]);
