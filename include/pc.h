@@ -322,7 +322,10 @@ pc_status pc_solve_poisson_static(int dim, const int64_t *n, const double *h, co
  * normal to that axis (rows = faces in C order of that face array); which = dim: derivative
  * rows of the nodes (rows = nodes, weights [dim][rows][K]); which = dim+1 (PC_DIV_WLS_DIRECT
  * plans only): derivative rows of the cell centres (rows = cells in C order, columns node
- * indices, weights [dim][rows][K]). col_out: [rows][K] int32 (node
+ * indices, weights [dim][rows][K]). On a vertex-grid plan there are no face rows, the rows of
+ * dim+1 are those of the vertex unknowns (C order of the unknowns), and the node rows' columns
+ * are linear indices of the vertex lattice (n per periodic axis, n + 1 otherwise, Dirichlet
+ * boundary vertices included). col_out: [rows][K] int32 (node
  * index for faces, cell linear index for nodes), w_out: FP64 host buffers. rows_out gets the
  * row count; pass NULL buffers to query it. FP64 plans return the FP64 weights; MIXED and FP32
  * plans keep only the FP32 (hi, lo) pairs after setup (the FP64 weights are setup temporaries)
