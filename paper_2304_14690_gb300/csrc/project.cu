@@ -929,11 +929,12 @@ __global__ void vertex_extend_kernel(VertexGrid V, const double *__restrict__ sv
   double v = zero ? 0.0 : sv[u];
   se[e] = neg ? -v : v;
 }
-// The extended solution on the vertex lattice (vertex j of an axis is extended cell j). Writes
+// The extended solution on the vertex lattice (vertex j of an axis is extended cell j), less the
+// gauge constant of the extension (stats->shift, zeroed with the statistics of every call). Writes
 // any of: the unknowns (pv), the whole lattice in FP64 (pl, Dirichlet boundary vertices exactly
 // 0) and as FP32 (hi, lo) pairs (pl2) for the compensated gradient.
-__global__ void vertex_restrict_kernel(VertexGrid V, const double *__restrict__ pe, double *__restrict__ pv,
-                                       double *__restrict__ pl, float2 *__restrict__ pl2) {
+__global__ void vertex_restrict_kernel(VertexGrid V, const double *__restrict__ pe, const DevStats *stats,
+                                       double *__restrict__ pv, double *__restrict__ pl, float2 *__restrict__ pl2) {
   pdl_enter();
   int idx[3];
   grid_position(V.dim, idx);
@@ -947,7 +948,7 @@ __global__ void vertex_restrict_kernel(VertexGrid V, const double *__restrict__ 
     if (ua < 0 || ua >= V.nv[a]) unknown = false;   // a Dirichlet boundary vertex
     u = u * V.nv[a] + (ua < 0 ? 0 : ua);
   }
-  const double v = unknown ? pe[e] : 0.0;
+  const double v = unknown ? pe[e] - stats->shift : 0.0;   // the gauge of the extension (0 without one)
   if (pv && unknown) pv[u] = v;
   if (pl) pl[l] = v;
   if (pl2) pl2[l] = as_pair(v);
@@ -1287,7 +1288,7 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
     count_launch(p);
   }
   bool mixed = p->precision != PC_PREC_FP64;
-  if (gmode) {
+  if (gmode && !p->vertex) {   // a vertex plan's restriction subtracts the shift itself
     const int G = grid_for(nc, kFlatPerBlock);
     if (gmode && mixed) launch_pdl(finalize_p_kernel<true, true>, G, T, 0, st, (int)nc, pout, p->dstats, p->p2);
     else launch_pdl(finalize_p_kernel<true, false>, G, T, 0, st, (int)nc, pout, p->dstats, nullptr);
@@ -1394,8 +1395,8 @@ static pc_status vertex_pass_solve(Plan *p, cudaStream_t st, double inv_bdt, dou
   count_launch(p);
   prof_mark(p, st, 2);
   PC_TRY(solve_grid(p, p->s64, p->stage_p, want_stats, st));
-  launch_pdl(vertex_restrict_kernel, vertex_grid_dims(p->dim, V.nf, T), T, 0, st, V, (const double *)p->stage_p, dp,
-             p->work64, mixed ? reinterpret_cast<float2 *>(p->p2) : (float2 *)nullptr);
+  launch_pdl(vertex_restrict_kernel, vertex_grid_dims(p->dim, V.nf, T), T, 0, st, V, (const double *)p->stage_p,
+             (const DevStats *)p->dstats, dp, p->work64, mixed ? reinterpret_cast<float2 *>(p->p2) : (float2 *)nullptr);
   count_launch(p);
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
@@ -1563,7 +1564,8 @@ static pc_status vertex_solve(Plan *p, const double *s, double *p_out, pc_stats 
   count_launch(p);
   prof_mark(p, st, 2);
   PC_TRY(solve_grid(p, p->stage_s, p->stage_p, stats != nullptr, st));
-  vertex_restrict_kernel<<<vertex_grid_dims(p->dim, V.nf, 256), 256, 0, st>>>(V, p->stage_p, dp, nullptr, nullptr);
+  vertex_restrict_kernel<<<vertex_grid_dims(p->dim, V.nf, 256), 256, 0, st>>>(V, p->stage_p, p->dstats, dp, nullptr,
+                                                                               nullptr);
   count_launch(p);
   PC_CUDA_TRY(cudaGetLastError());
   if (hp) PC_CUDA_TRY(cudaMemcpyAsync(p_out, dp, nvt * sizeof(double), cudaMemcpyDeviceToHost, st));
