@@ -1390,9 +1390,13 @@ static pc_status vertex_pass_solve(Plan *p, cudaStream_t st, double inv_bdt, dou
   const VertexGrid V = vertex_grid(p);
   launch_pdl(vertex_extend_kernel, vertex_grid_dims(p->dim, V.m, T), T, 0, st, V, (const double *)sv, p->s64);
   count_launch(p);
-  launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, (const double *)p->s64, p->dstats,
-             p->partials, p->counters);
-  count_launch(p);
+  // the source sums: the mean the residual removes (zero-mode problems; an odd extension has
+  // mean zero) and the statistics
+  if (want_stats || p->problem_singular) {
+    launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, (const double *)p->s64, p->dstats,
+               p->partials, p->counters);
+    count_launch(p);
+  }
   prof_mark(p, st, 2);
   PC_TRY(solve_grid(p, p->s64, p->stage_p, want_stats, st));
   launch_pdl(vertex_restrict_kernel, vertex_grid_dims(p->dim, V.nf, T), T, 0, st, V, (const double *)p->stage_p,
