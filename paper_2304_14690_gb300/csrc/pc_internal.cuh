@@ -84,6 +84,7 @@ struct GraphEntry {
   long long launches = 0;
   unsigned long long stamp = 0;
   bool prof = false;      // captured with the profiler's event-record nodes
+  int kind = 0;           // 0: pc_project (all the keys above); 1: pc_solve_poisson (u = s, p)
 };
 
 // IB-force iteration (pc_project_ib): the device-side state of one time step's loop, written by

@@ -1548,9 +1548,10 @@ pc_status solve_grid_device(Plan *p, const double *s, double *pout, cudaStream_t
 
 // pc_solve_poisson on a vertex-grid plan: extend the source, solve the periodic extension,
 // restrict the solution to the vertex unknowns.
-static pc_status vertex_solve(Plan *p, const double *s, double *p_out, pc_stats *stats, cudaStream_t st) {
+static pc_status vertex_solve(Plan *p, const double *s, double *p_out, pc_stats *stats, cudaStream_t st,
+                              bool all_device = false) {
   const long long nc = p->ncells, nvt = p->nvtot;
-  const bool hs = !is_device_ptr(s), hp = !is_device_ptr(p_out);
+  const bool hs = !all_device && !is_device_ptr(s), hp = !all_device && !is_device_ptr(p_out);
   const double *ds = s;
   double *dp = p_out;
   if (hs) {
@@ -1578,9 +1579,10 @@ static pc_status vertex_solve(Plan *p, const double *s, double *p_out, pc_stats 
   return PC_OK;
 }
 
-static pc_status solve_impl(Plan *p, const double *s, double *p_out, pc_stats *stats, cudaStream_t st) {
+static pc_status solve_impl(Plan *p, const double *s, double *p_out, pc_stats *stats, cudaStream_t st,
+                            bool all_device = false) {
   const long long nc = p->ncells;
-  const bool hs = !is_device_ptr(s), hp = !is_device_ptr(p_out);
+  const bool hs = !all_device && !is_device_ptr(s), hp = !all_device && !is_device_ptr(p_out);
   const double *ds = s;
   double *dp = p_out;
   if (hs) { PC_CUDA_TRY(cudaMemcpyAsync(p->stage_s, s, nc * sizeof(double), cudaMemcpyHostToDevice, st)); ds = p->stage_s; }
@@ -1601,25 +1603,24 @@ static bool graph_cached(const Plan *p, double dt, const void *u, const void *f,
                          const void *uo, const void *fo) {
   for (int i = 0; i < kGraphCache; ++i) {
     const GraphEntry &c = p->graphs[i];
-    if (c.exec && c.u == u && c.f == f && c.p == po && c.uo == uo && c.fo == fo && c.dt == dt && c.prof == p->prof)
+    if (c.exec && c.kind == 0 && c.u == u && c.f == f && c.p == po && c.uo == uo && c.fo == fo && c.dt == dt &&
+        c.prof == p->prof)
       return true;
   }
   return false;
 }
 
-// pc_project through a cached CUDA graph: captured once per argument set on the plan's
-// private stream, then replayed with one launch on the caller's stream.
-static pc_status project_graph(Plan *p, double dt, const void *u_star, const void *f_in, double *p_out,
-                               void *u_out, void *f_out, cudaStream_t st) {
+// A cached CUDA graph of one call: looked up by `match`, else captured once on the plan's private
+// stream by `capture` (which records the argument set in the entry), then replayed with one
+// launch on the caller's stream. pc_project and pc_solve_poisson with device arrays use it.
+template <typename Match, typename Capture>
+static pc_status run_graph(Plan *p, cudaStream_t st, Match match, Capture capture) {
   GraphEntry *e = nullptr;
-  for (int i = 0; i < kGraphCache; ++i) {
-    GraphEntry &c = p->graphs[i];
-    if (c.exec && c.u == u_star && c.f == f_in && c.p == p_out && c.uo == u_out && c.fo == f_out && c.dt == dt &&
-        c.prof == p->prof) {
-      e = &c;
+  for (int i = 0; i < kGraphCache; ++i)
+    if (p->graphs[i].exec && p->graphs[i].prof == p->prof && match(p->graphs[i])) {
+      e = &p->graphs[i];
       break;
     }
-  }
   if (!e) {
     e = &p->graphs[0];
     for (int i = 1; i < kGraphCache; ++i)
@@ -1635,7 +1636,7 @@ static pc_status project_graph(Plan *p, double dt, const void *u_star, const voi
     p->cap_events = p->prof;
     p->cap_n = 0;
     const long long l0 = p->launches;
-    pc_status s = project_impl(p, dt, u_star, f_in, p_out, u_out, f_out, nullptr, p->cap_stream, true);
+    pc_status s = capture(*e, p->cap_stream);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
     p->capturing = false;
@@ -1669,7 +1670,6 @@ static pc_status project_graph(Plan *p, double dt, const void *u_star, const voi
         if (p->cap_ev[i] == ev) e->evnode[i] = nodes[k];
     }
     for (int i = 0; i + 1 < e->nev; ++i) e->tag[i] = p->cap_tag[i];
-    e->u = u_star; e->f = f_in; e->p = p_out; e->uo = u_out; e->fo = f_out; e->dt = dt;
     e->prof = p->prof;
   }
   e->stamp = ++p->graph_clock;
@@ -1687,6 +1687,33 @@ static pc_status project_graph(Plan *p, double dt, const void *u_star, const voi
   PC_CUDA_TRY(cudaGraphLaunch(e->exec, st));
   p->launches += e->launches;
   return PC_OK;
+}
+
+// pc_project through a cached CUDA graph, one per argument set (pointers and dt).
+static pc_status project_graph(Plan *p, double dt, const void *u_star, const void *f_in, double *p_out,
+                               void *u_out, void *f_out, cudaStream_t st) {
+  return run_graph(
+      p, st,
+      [&](const GraphEntry &c) {
+        return c.kind == 0 && c.u == u_star && c.f == f_in && c.p == p_out && c.uo == u_out && c.fo == f_out &&
+               c.dt == dt;
+      },
+      [&](GraphEntry &e, cudaStream_t cs) {
+        pc_status s = project_impl(p, dt, u_star, f_in, p_out, u_out, f_out, nullptr, cs, true);
+        e.kind = 0; e.u = u_star; e.f = f_in; e.p = p_out; e.uo = u_out; e.fo = f_out; e.dt = dt;
+        return s;
+      });
+}
+
+// pc_solve_poisson with device arrays through a cached CUDA graph, one per (s, p_out).
+static pc_status solve_graph(Plan *p, const double *s, double *p_out, cudaStream_t st) {
+  return run_graph(
+      p, st, [&](const GraphEntry &c) { return c.kind == 1 && c.u == s && c.p == p_out; },
+      [&](GraphEntry &e, cudaStream_t cs) {
+        pc_status r = p->vertex ? vertex_solve(p, s, p_out, nullptr, cs, true) : solve_impl(p, s, p_out, nullptr, cs, true);
+        e.kind = 1; e.u = s; e.f = nullptr; e.p = p_out; e.uo = nullptr; e.fo = nullptr; e.dt = 0.0;
+        return r;
+      });
 }
 
 // ----------------------------------------------------------------------------- IB-force iteration
@@ -2045,6 +2072,9 @@ extern "C" pc_status pc_solve_poisson(pc_plan *plan, const double *s, double *p_
   pc::Plan *p = reinterpret_cast<pc::Plan *>(plan);
   if (!p || !s || !p_out) return pc::fail(PC_ERR_INVALID_ARG, "plan, s and p_out are required");
   if (cudaSetDevice(p->device) != cudaSuccess) return pc::fail(PC_ERR_CUDA, "cannot select device %d", p->device);
+  // device arrays without statistics: one launch of a graph cached per (s, p_out)
+  if (p->graphs_on && !stats && pc::is_device_ptr(s) && pc::is_device_ptr(p_out))
+    return pc::solve_graph(p, s, p_out, (cudaStream_t)cuda_stream);
   if (p->vertex) return pc::vertex_solve(p, s, p_out, stats, (cudaStream_t)cuda_stream);
   return pc::solve_impl(p, s, p_out, stats, (cudaStream_t)cuda_stream);
 }
