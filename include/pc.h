@@ -352,7 +352,8 @@ pc_status pc_profile_read(pc_plan *plan, pc_profile *out);
 /* CUDA graphs (on by default): a pc_project call with device pointers and no stats is
  * captured once per distinct (pointers, dt) into a CUDA graph on a plan-private stream and then
  * replayed with a single launch on the caller's stream (up to 4 argument sets are cached per
- * plan). Results are identical with graphs on or off. */
+ * plan). A pc_solve_poisson call with device arrays and no stats is captured the same way per
+ * (s, p_out). Results are identical with graphs on or off. */
 pc_status pc_set_graphs(pc_plan *plan, int on);
 
 /* Schedule of the transform passes (§2.3 three-step solve). Every pass along `axis` gives each
