@@ -340,3 +340,26 @@ def test_vertex_plan_refuses_faces(env):
     with pytest.raises(pc.PcError) as e:
         pc.Plan(prob, div_mode="faces", grid_type="vertices")
     assert e.value.status == 2
+
+
+def test_solve_graph_equals_direct(env):
+    """pc_solve_poisson with device arrays replays a cached graph; with graphs off it launches
+    directly. Both give the same bits, on vertex and cell grid-only plans, and a second call
+    with other arrays captures its own graph."""
+    pc, torch, dev = env
+    lib = pc.load()
+    for grid_type, n, lo, hi in (("vertices", (24, 20), ("I", "W"), ("D", "W")), ("cells", (32, 16), ("P", "W"), ("P", "D"))):
+        h = (0.05, 0.07)
+        plan = pc.GridPlan(2, n, h, lo, hi, grid_type=grid_type, precision="mixed")
+        rng = np.random.default_rng(11)
+        s1 = torch.as_tensor(rng.normal(size=plan.shape), device=dev)
+        s2 = torch.as_tensor(rng.normal(size=plan.shape), device=dev)
+        g1, _ = plan.solve_poisson(s1)
+        g1b, _ = plan.solve_poisson(s1)          # replay
+        g2, _ = plan.solve_poisson(s2)           # another argument set
+        assert lib.pc_set_graphs(plan.handle, 0) == 0
+        d1, _ = plan.solve_poisson(s1)
+        d2, _ = plan.solve_poisson(s2)
+        torch.cuda.synchronize()
+        assert torch.equal(g1, d1) and torch.equal(g1b, d1) and torch.equal(g2, d2), grid_type
+        plan.close()
