@@ -126,3 +126,13 @@ def test_grid_descriptor_validation(lib, over, status):
     s = lib.pc_grid_plan_create(ctypes.byref(d), 0, None, ctypes.byref(h))
     assert s == status, lib.pc_last_error_message()
     assert lib.pc_last_error_message() != b""
+
+
+def test_momentum_entry_points_reject_null(lib):
+    """The predictor's entry points check their arguments before touching a device."""
+    h = ctypes.c_void_p()
+    assert lib.pc_momentum_create(None, None, 12, 0.0, None, None, ctypes.byref(h)) == 1
+    assert lib.pc_last_error_message() != b""
+    assert lib.pc_momentum_predict(None, 0.1, None, None, None, None) == 1
+    assert lib.pc_momentum_reset(None) == 1
+    assert lib.pc_momentum_destroy(None) == 0
