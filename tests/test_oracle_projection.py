@@ -166,6 +166,49 @@ def test_transfer_exact_for_quadratic_velocity():
     assert np.all(U[1].ravel()[wall] == 0.0)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_boundary_face_rule(dim):
+    """§2.1 Eq. 7 and the §3.3 workaround: a wall face carries no flux (its value is replaced by
+    exactly 0), while an inflow face (u^{n+1}.n = u*.n) and a Dirichlet face keep the value row's
+    transferred flux. The value rows reproduce quadratics, so with a quadratic u~ the flux at
+    every inflow, Dirichlet and interior face is the quadratic's value at the face centre; a
+    rule that also zeroed inflow or Dirichlet faces, or kept wall fluxes, fails here."""
+    if dim == 2:
+        prob = wl.generic(dim=2, n=(12, 10), bc_lo=("I", "W"), bc_hi=("D", "W"), seed=21)
+    else:
+        prob = wl.generic(dim=3, n=(8, 6, 6), bc_lo=("I", "W", "D"), bc_hi=("D", "I", "W"), seed=22)
+    g = grid_of(prob)
+    plan = PR.build_plan(g, prob.nodes, prob.node_type, K=prob.knn)
+    X = prob.nodes
+    coef = np.random.default_rng(7).normal(size=(dim, dim, dim))
+
+    def quad(a, pts):   # component a: 1 + sum_b x_b + sum_{b<=c} coef x_b x_c, pts (dim, m)
+        v = 1.0 + (a + 1) * pts.sum(axis=0)
+        for b in range(dim):
+            for c in range(b, dim):
+                v = v + coef[a, b, c] * pts[b] * pts[c]
+        return v
+
+    u = np.stack([quad(a, X) for a in range(dim)])
+    U = PR.transfer(plan, u)
+    seen = {"I": 0, "D": 0, "W": 0}
+    for a in range(dim):
+        fp = g.face_points(a)
+        exact = quad(a, fp.T).reshape(g.face_shape(a))
+        Ua = U[a]
+        along = np.indices(g.face_shape(a))[a]
+        inner = (along > 0) & (along < g.n[a])
+        assert np.abs(Ua[inner] - exact[inner]).max() < 1e-11 * np.abs(exact).max()
+        for kind, sel in ((g.bc_lo[a], along == 0), (g.bc_hi[a], along == g.n[a])):
+            seen[kind] += int(sel.sum())
+            if kind == "W":
+                assert np.all(Ua[sel] == 0.0)
+            else:
+                assert np.abs(exact[sel]).min() > 0.1          # a zeroed face would show
+                assert np.abs(Ua[sel] - exact[sel]).max() < 1e-11 * np.abs(exact).max()
+    assert all(v > 0 for v in seen.values())
+
+
 def test_ib_relations(problems):
     for p, plan in problems:
         if not np.any(p.node_type != 0):
