@@ -153,7 +153,9 @@ typedef struct pc_plan pc_plan;
  * it, shifted inward at walls, wrapped on periodic axes), eigenvalue and twiddle tables, and
  * the whole workspace of pc_project. The coefficients depend only on positions and are
  * computed once (§2.2, last paragraph). Runs on `device` on `cuda_stream` and returns when
- * done. hbm_budget_bytes = 0 means no budget. */
+ * done. hbm_budget_bytes = 0 means no budget. Limits: at most 2^31 - 2^16 cells, faces normal to
+ * any axis, and nodes (the kernels number rows in 32 bits and offset into the row arrays in 64
+ * bits); larger problems return PC_ERR_UNSUPPORTED before any device call. */
 pc_status pc_plan_create(const pc_problem_desc *desc, int device, size_t hbm_budget_bytes,
                          void *cuda_stream, pc_plan **out_plan);
 

@@ -240,7 +240,6 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
   const int m = d->dim == 2 ? 6 : 10;
   if (d->knn < m || d->knn > kMaxK) return fail(PC_ERR_INVALID_ARG, "knn must be in [%d, %d]", m, kMaxK);
   if (d->num_nodes < d->knn) return fail(PC_ERR_INVALID_ARG, "fewer nodes than knn");
-  if (d->num_nodes > 2000000000LL) return fail(PC_ERR_UNSUPPORTED, "more than 2e9 nodes");
   if (!d->node_xyz || !d->node_type) return fail(PC_ERR_INVALID_ARG, "node_xyz and node_type are required");
   if (!(d->wls_eps > 0) || !(d->support_factor > 0) || !(d->beta > 0))
     return fail(PC_ERR_INVALID_ARG, "wls_eps, support_factor and beta must be positive");
@@ -281,7 +280,18 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
     nvtot *= nv[a];
     nftot *= nf[a];
   }
-  if (ncells > (1LL << 31) - 1) return fail(PC_ERR_UNSUPPORTED, "grid larger than 2^31 cells");
+  // The kernels number rows (cells, faces, nodes, pressure points) with 32-bit indices and form
+  // every offset into the row arrays ([K][rows], [dim][3^dim][N]) in 64 bits; a thread index
+  // runs at most one block past the last row, so each row count stays below kMaxRows.
+  if (ncells > kMaxRows) return fail(PC_ERR_UNSUPPORTED, "grid of %lld cells: at most %lld", ncells, kMaxRows);
+  if (d->num_nodes > kMaxRows)
+    return fail(PC_ERR_UNSUPPORTED, "%lld nodes: at most %lld", (long long)d->num_nodes, kMaxRows);
+  for (int a = 0; a < d->dim && !vert; ++a) {
+    const long long faces = ncells / nint[a] * (nint[a] + 1);
+    if (faces > kMaxRows) return fail(PC_ERR_UNSUPPORTED, "%lld faces normal to axis %d: at most %lld", faces, a, kMaxRows);
+  }
+  if (vert && (nftot > kMaxRows || nvtot > kMaxRows))
+    return fail(PC_ERR_UNSUPPORTED, "vertex lattice of %lld points: at most %lld", nftot, kMaxRows);
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     cudaGetLastError();
@@ -468,7 +478,7 @@ static pc_status create_grid(const pc_grid_desc *d, int device, cudaStream_t st,
     ncells *= nint[a];
     nvtot *= nv[a];
   }
-  if (ncells > (1LL << 31) - 1) return fail(PC_ERR_UNSUPPORTED, "grid larger than 2^31 cells");
+  if (ncells > kMaxRows) return fail(PC_ERR_UNSUPPORTED, "grid of %lld cells: at most %lld", ncells, kMaxRows);
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     cudaGetLastError();

@@ -15,6 +15,8 @@ enum AxisKind { KIND_PP = 0, KIND_NN = 1, KIND_DD = 2, KIND_ND = 3, KIND_DN = 4 
 
 constexpr int kMaxRadices = 24;
 constexpr int kMaxK = 32;
+// Largest row count (cells, faces per axis, nodes) the kernels index with 32-bit row numbers.
+constexpr long long kMaxRows = (1LL << 31) - (1LL << 16);
 constexpr int kMaxRefine = 8;
 
 // Device-side status word values (written by kernels, read at the next sync point).

@@ -156,12 +156,12 @@ constexpr int kFlatPerThread = 4;
 constexpr int kFlatPerBlock = kFlatThreads * kFlatPerThread;
 
 template <typename VT, bool HAS_F, bool STATS, bool SPLIT>
-__device__ __forceinline__ void prep_kernel_body(unsigned b, int count, const VT *__restrict__ u, const VT *__restrict__ f, double dt,
+__device__ __forceinline__ void prep_kernel_body(unsigned b, long long count, const VT *__restrict__ u, const VT *__restrict__ f, double dt,
                             double *__restrict__ ut64, float2 *__restrict__ u2, DevStats *stats) {
   double m = 0.0;
 #pragma unroll
   for (int k = 0; k < kFlatPerThread; ++k) {
-    const int i = (int)b * kFlatPerBlock + k * kFlatThreads + threadIdx.x;
+    const long long i = (long long)b * kFlatPerBlock + k * kFlatThreads + threadIdx.x;
     if (i < count) {
       const VT ui = u[i];
       if (STATS) m = fmax(m, fabs(as_f64(ui)));
@@ -178,14 +178,14 @@ __device__ __forceinline__ void prep_kernel_body(unsigned b, int count, const VT
   if (STATS) block_max_update(m, &stats->max_u);
 }
 template <typename VT, bool HAS_F, bool STATS, bool SPLIT>
-__global__ void prep_kernel(int count, const VT *__restrict__ u, const VT *__restrict__ f, double dt,
+__global__ void prep_kernel(long long count, const VT *__restrict__ u, const VT *__restrict__ f, double dt,
                             double *__restrict__ ut64, float2 *__restrict__ u2, DevStats *stats) {
   pdl_enter();
   prep_kernel_body<VT, HAS_F, STATS, SPLIT>(blockIdx.x, count, u, f, dt, ut64, u2, stats);
 }
 
 template <typename VT>
-static void launch_prep(bool has_f, bool stats, bool split, int cnt, const VT *u, const VT *f, double dt,
+static void launch_prep(bool has_f, bool stats, bool split, long long cnt, const VT *u, const VT *f, double dt,
                         double *ut64, float2 *u2, DevStats *ds, cudaStream_t st) {
   const int T = kFlatThreads;
   const int G = grid_for(cnt, kFlatPerBlock);
@@ -207,7 +207,7 @@ __device__ __forceinline__ double transfer64_row(int r, int rows, int K, const i
   double acc = 0.0;
 #pragma unroll 4
   for (int k = 0; k < K; ++k) {
-    int at = k * rows + r;
+    const long long at = (long long)k * rows + r;
     acc = fma(__ldcs(w + at), __ldg(u + __ldcs(col + at)), acc);
   }
   return acc;
@@ -240,15 +240,15 @@ __device__ __forceinline__ double transfer_mixed_row(int r, int rows, int Kr, co
     float2 w[KC > 0 ? KC : 1];
 #pragma unroll
     for (int k = 0; k < K; ++k) {   // read once: streamed past the caches that hold the gathered values
-      c[k] = __ldcs(col + k * rows + r);
-      w[k] = __ldcs(w2 + k * rows + r);
+      c[k] = __ldcs(col + (long long)k * rows + r);
+      w[k] = __ldcs(w2 + (long long)k * rows + r);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) df_acc(s, w[k], src(c[k]));
   } else {
 #pragma unroll 4
     for (int k = 0; k < K; ++k) {
-      int at = k * rows + r;
+      const long long at = (long long)k * rows + r;
       df_acc(s, __ldcs(w2 + at), src(__ldcs(col + at)));
     }
   }
@@ -567,7 +567,7 @@ __device__ __forceinline__ void finalize_p_body(unsigned b, int ncells, double *
   if (GAUGE) shift = stats->shift;
 #pragma unroll
   for (int k = 0; k < kFlatPerThread; ++k) {
-    const int c = (int)b * kFlatPerBlock + k * kFlatThreads + threadIdx.x;
+    const long long c = (long long)b * kFlatPerBlock + k * kFlatThreads + threadIdx.x;
     if (c < ncells) {
       double v = p[c];
       if (GAUGE) {
@@ -597,9 +597,9 @@ __device__ __forceinline__ void grad64_at(int i, int N, int K, const int32_t *__
   for (int a = 0; a < DIM; ++a) g[a] = 0.0;
 #pragma unroll 3
   for (int k = 0; k < K; ++k) {
-    double pv = __ldg(p + __ldcs(col + k * N + i));
+    double pv = __ldg(p + __ldcs(col + (long long)k * N + i));
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) g[a] = fma(__ldcs(D + (a * K + k) * N + i), pv, g[a]);
+    for (int a = 0; a < DIM; ++a) g[a] = fma(__ldcs(D + ((long long)a * K + k) * N + i), pv, g[a]);
   }
 }
 
@@ -617,13 +617,13 @@ __global__ void gradient64_kernel(int N, int K, const int32_t *__restrict__ col,
   const bool ib = type[i] != PC_NODE_FLUID;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
-    double us = (double)u[a * N + i];
+    double us = (double)u[(long long)a * N + i];
     if (ib) {
-      store_v(uo, a * N + i, 0.0);
-      if (fo) store_v(fo, a * N + i, -us * inv_dt + beta * g[a]);
+      store_v(uo, (long long)a * N + i, 0.0);
+      if (fo) store_v(fo, (long long)a * N + i, -us * inv_dt + beta * g[a]);
     } else {
-      store_v(uo, a * N + i, us - beta * dt * g[a]);
-      if (fo) store_v(fo, a * N + i, 0.0);
+      store_v(uo, (long long)a * N + i, us - beta * dt * g[a]);
+      if (fo) store_v(fo, (long long)a * N + i, 0.0);
     }
   }
 }
@@ -638,12 +638,12 @@ __device__ __forceinline__ void grad_mixed_at(int i, int N, const int32_t *__res
   for (int a = 0; a < DIM; ++a) g[a] = DF{0.f, 0.f};
   int c[KB];
 #pragma unroll
-  for (int k = 0; k < KB; ++k) c[k] = __ldcs(col + k * N + i);   // rows: read once, streamed
+  for (int k = 0; k < KB; ++k) c[k] = __ldcs(col + (long long)k * N + i);   // rows: read once, streamed
 #pragma unroll
   for (int k = 0; k < KB; ++k) {
     const float2 pv = __ldg(p2 + c[k]);
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) df_acc(g[a], __ldcs(D2 + (a * KB + k) * N + i), pv);
+    for (int a = 0; a < DIM; ++a) df_acc(g[a], __ldcs(D2 + ((long long)a * KB + k) * N + i), pv);
   }
 #pragma unroll
   for (int a = 0; a < DIM; ++a) gout[a] = df_value(g[a]);
@@ -664,13 +664,13 @@ __device__ __forceinline__ void gradient_mixed_kernel_body(const VBlock &vb, int
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
     double ga = g[a];
-    double us = (double)u[a * N + i];
+    double us = (double)u[(long long)a * N + i];
     if (ib) {
-      store_v(uo, a * N + i, 0.0);
-      if (fo) store_v(fo, a * N + i, -us * inv_dt + beta * ga);
+      store_v(uo, (long long)a * N + i, 0.0);
+      if (fo) store_v(fo, (long long)a * N + i, -us * inv_dt + beta * ga);
     } else {
-      store_v(uo, a * N + i, us - beta * dt * ga);
-      if (fo) store_v(fo, a * N + i, 0.0);
+      store_v(uo, (long long)a * N + i, us - beta * dt * ga);
+      if (fo) store_v(fo, (long long)a * N + i, 0.0);
     }
   }
 }
@@ -737,7 +737,7 @@ __global__ void ib_face_flags_kernel(int rows, int K, const int32_t *__restrict_
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   uint8_t f = 0;
-  for (int k = 0; k < K; ++k) f |= (uint8_t)(__ldg(type + __ldg(col + k * rows + r)) != PC_NODE_FLUID);
+  for (int k = 0; k < K; ++k) f |= (uint8_t)(__ldg(type + __ldg(col + (long long)k * rows + r)) != PC_NODE_FLUID);
   flag[r] = f;
 }
 
@@ -1005,7 +1005,7 @@ __global__ void batch_prep(const BatchProblem *__restrict__ P, const int *__rest
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
   const unsigned lb = blockIdx.x - seg[pi];
-  const int cnt = q.dim * q.N;
+  const long long cnt = (long long)q.dim * q.N;
   if (q.f) prep_kernel_body<VT, true, false, true>(lb, cnt, (const VT *)q.u, (const VT *)q.f, q.dt, nullptr, q.u2, nullptr);
   else prep_kernel_body<VT, false, false, true>(lb, cnt, (const VT *)q.u, nullptr, q.dt, nullptr, q.u2, nullptr);
 }
@@ -1434,10 +1434,10 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   const bool mixed = p->precision != PC_PREC_FP64;
   const long long cnt = (long long)d * N;
   if (p->vdtype == PC_DTYPE_F64)
-    launch_prep<double>(df != nullptr, stats != nullptr, mixed, (int)cnt, (const double *)du, (const double *)df, dt,
+    launch_prep<double>(df != nullptr, stats != nullptr, mixed, cnt, (const double *)du, (const double *)df, dt,
                         p->ut64, p->u2, p->dstats, st);
   else
-    launch_prep<float>(df != nullptr, stats != nullptr, mixed, (int)cnt, (const float *)du, (const float *)df, dt,
+    launch_prep<float>(df != nullptr, stats != nullptr, mixed, cnt, (const float *)du, (const float *)df, dt,
                        p->ut64, p->u2, p->dstats, st);
   count_launch(p);
   prof_mark(p, st, 0);
@@ -1808,7 +1808,7 @@ static pc_status ib_pass(Plan *p, bool first, double dt, const VT *du, double *d
   prof_begin(p, st);
   PC_CUDA_TRY(cudaMemsetAsync(p->dstats, 0, sizeof(DevStats), st));
   if (first) {
-    launch_prep<VT>(false, false, mixed, (int)(d * N), du, nullptr, dt, p->ut64, p->u2, p->dstats, st);
+    launch_prep<VT>(false, false, mixed, (long long)d * N, du, nullptr, dt, p->ut64, p->u2, p->dstats, st);
     count_launch(p);
   }
   if (nib) {

@@ -87,6 +87,23 @@ def test_descriptor_validation(lib, over, status):
     assert lib.pc_last_error_message() != b""
 
 
+@pytest.mark.parametrize("over", [
+    dict(dim=3, n=(4096, 4096, 128)),   # 2^31 cells: beyond the kernels' 32-bit row numbers
+    dict(num_nodes=1 << 31),            # 2^31 nodes
+    dict(num_nodes=(1 << 31) - (1 << 16) + 1),
+])
+def test_plan_beyond_row_limits_is_refused_before_the_device(lib, over):
+    """Row arrays are indexed with 64-bit offsets and 32-bit row numbers, so a plan whose cells,
+    faces or nodes exceed 2^31 - 2^16 is refused (PC_ERR_UNSUPPORTED) by validation, before any
+    device call; the node arrays are never read."""
+    d, keep = _desc(**over)
+    h = ctypes.c_void_p()
+    s = lib.pc_plan_create(ctypes.byref(d), 0, 0, None, ctypes.byref(h))
+    assert s == 2, lib.pc_last_error_message()
+    assert b"at most" in lib.pc_last_error_message()
+    assert not h.value
+
+
 def _grid_desc(**over):
     from paper_2304_14690_gb300 import pc
     d = pc.GridDesc()
