@@ -312,8 +312,12 @@ pc_status pc_solve_poisson(pc_plan *plan, const double *s, double *p_out, pc_sta
  *  - Limit: at most 524288 cells (e.g. 1024 x 512); larger grids return PC_ERR_BUDGET.
  *  - s and p_out are device pointers (C order, one FP64 value per cell); host pointers are
  *    rejected with PC_ERR_INVALID_ARG.
+ *  - s and p_out must be device memory of the current device (or managed memory);
+ *    PC_ERR_INVALID_ARG otherwise.
  *  - The first call on a device looks up the array's device address, zeroes it and sets kernel
- *    attributes; make that first call before any stream capture.
+ *    attributes; make that first call before any stream capture. The address is cached per
+ *    device: after cudaDeviceReset the cache is stale, so do not use this entry point again in
+ *    that process.
  *  - All calls share the one array and it keeps the last call's contents: calls that overlap on
  *    the GPU (different streams, or different host threads) race and corrupt each other. */
 pc_status pc_solve_poisson_static(int dim, const int64_t *n, const double *h, const int *bc_lo,

@@ -106,6 +106,8 @@ extern "C" pc_status pc_solve_poisson_static(int dim, const int64_t *n, const do
   if (ncells > kStaticMaxCells)
     return fail(PC_ERR_BUDGET, "grid of %lld cells exceeds the static workspace limit of %lld cells",
                 ncells, kStaticMaxCells);
+  int cur = -1;
+  PC_CUDA_TRY(cudaGetDevice(&cur));
   for (const void *ptr : {(const void *)s, (const void *)p_out}) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess ||
@@ -113,6 +115,9 @@ extern "C" pc_status pc_solve_poisson_static(int dim, const int64_t *n, const do
       cudaGetLastError();
       return fail(PC_ERR_INVALID_ARG, "s and p_out must be device pointers");
     }
+    // the kernels run on the current device with its copy of the workspace
+    if (at.type == cudaMemoryTypeDevice && at.device != cur)
+      return fail(PC_ERR_INVALID_ARG, "s and p_out live on device %d, the current device is %d", at.device, cur);
   }
   double *ws = nullptr;
   PC_TRY(static_scratch(&ws));
@@ -171,8 +176,10 @@ extern "C" pc_status pc_solve_poisson_static(int dim, const int64_t *n, const do
     const int total = tw_total(ax.M) + ax.n;
     static_axis_tables<<<(total + 255) / 256, 256, 0, st>>>(ax.n, ax.M, ax.kind, ax.h, ax.tw64, ax.lam64);
   }
-  // Statistics start at zero; the reduction counters are left at zero by every reduction.
+  // Statistics and the reduction counters start at zero on every call: a completed reduction
+  // leaves its counter at zero, but a call cut short (a failed launch) may not have.
   PC_CUDA_TRY(cudaMemsetAsync(pl.dstats, 0, sizeof(DevStats), st));
+  PC_CUDA_TRY(cudaMemsetAsync(pl.counters, 0, 8 * sizeof(double), st));
   PC_CUDA_TRY(cudaGetLastError());
   return solve_grid_device(&pl, s, p_out, st);
 }

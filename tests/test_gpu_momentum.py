@@ -66,7 +66,7 @@ def test_predictor_matches_oracle(env, case, precision, tol):
     plan.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-9)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-10)])
 def test_time_steps_match_oracle(env, precision, tol):
     """Five full time steps (predictor, then the IB-force iteration of the correction) run on the
     device alone, against the same chain in the oracle."""

@@ -292,7 +292,7 @@ def test_vertex_project_ib_matches_oracle(env, vproblems, precision, tol):
         ref = V.project_ib(opl, prob.dt, prob.u_star, tol=1e-3, max_iters=50)
         p, uo, fo, info = plan.project_ib(u, tol=1e-3, max_iters=50)
         assert info["iterations"] == ref["iterations"], (info["iterations"], ref["iterations"])
-        assert rel(fo.cpu().numpy(), ref["f"]) <= 10 * tol
+        assert rel(fo.cpu().numpy(), ref["f"]) <= tol, rel(fo.cpu().numpy(), ref["f"])
         plan.close()
 
 
@@ -354,8 +354,10 @@ def test_solve_graph_equals_direct(env):
         rng = np.random.default_rng(11)
         s1 = torch.as_tensor(rng.normal(size=plan.shape), device=dev)
         s2 = torch.as_tensor(rng.normal(size=plan.shape), device=dev)
-        g1, _ = plan.solve_poisson(s1)
-        g1b, _ = plan.solve_poisson(s1)          # replay
+        out = torch.empty(plan.shape, dtype=torch.float64, device=dev)
+        g1 = plan.solve_poisson(s1, p_out=out)[0].clone()   # captured for (s1, out)
+        out.zero_()
+        g1b = plan.solve_poisson(s1, p_out=out)[0].clone()  # the same key: a replay
         g2, _ = plan.solve_poisson(s2)           # another argument set
         assert lib.pc_set_graphs(plan.handle, 0) == 0
         d1, _ = plan.solve_poisson(s1)
