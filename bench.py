@@ -36,7 +36,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
-    ap.add_argument("--refine", type=int, default=2)   # FP32 refinement contracts by ~eps32*kappa(L_h) per sweep
+    ap.add_argument("--refine", type=int, default=4,
+                    help="largest number of refinement sweeps (mixed precision)")
+    ap.add_argument("--refine-tol", type=float, default=1e-13,
+                    help="stopping rule ||r|| <= tol ||s|| (or the residual's rounding floor); <= 0: fixed sweeps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-problem batch measurement")
     ap.add_argument("--batch-steps", type=int, default=20)
@@ -52,6 +55,14 @@ def parse():
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-cold", action="store_true",
                     help="start with no resident plans (default: build every pool plan before the trace)")
+    ap.add_argument("--serve-max-queue", type=int, default=512,
+                    help="waiting requests beyond which arrivals are refused (backpressure)")
+    ap.add_argument("--serve-deadline", type=float, default=0.5,
+                    help="seconds a request may wait before it is dropped (load shedding)")
+    ap.add_argument("--no-serve-leg", action="store_true",
+                    help="skip the bounded serving leg of the default run")
+    ap.add_argument("--serve-leg-pool", type=int, default=16)
+    ap.add_argument("--serve-leg-requests", type=int, default=2000)
     ap.add_argument("--serve-fp64-requests", type=int, default=2000,
                     help="prefix of the trace also served one at a time by plain FP64 projections")
     ap.add_argument("--no-extras", action="store_true",
@@ -182,9 +193,12 @@ def _smi_id(dev, local_rank):
 
 # ----------------------------------------------------------------------------- roofline
 
-def phase_bytes(prob, precision, refine):
-    """Algorithmic (compulsory) DRAM bytes per call of each phase, from the data each kernel must
-    read and write once: WLS rows (index + weights), gathered node/cell values, outputs."""
+def phase_bytes(prob, precision, refine, sweeps_done=None, adaptive=False):
+    """Algorithmic DRAM bytes per call of each phase, from the data each kernel must read and
+    write once: WLS rows (index + weights), gathered node/cell values, outputs. The transform
+    phase takes the scope table's figure for a multi-pass solve: (2 dim - 1) axis passes, each
+    reading and writing 4 B per cell (24 B per cell per solve in 2D, 40 B in 3D), times the
+    solves run (the first and one per refinement sweep)."""
     d, N, K, Kg = prob.dim, prob.num_nodes, prob.knn, 3 ** prob.dim
     nc = prob.num_cells
     faces = 0
@@ -198,21 +212,29 @@ def phase_bytes(prob, precision, refine):
     tr = faces * (K * (4 + wbytes) + 8) + d * N * 8
     prep = d * N * (vb + 8)
     div = faces * 8 + nc * (8 + (4 if mixed else 0))
-    sweeps = refine if precision == "mixed" else 0
+    sweeps = (refine if sweeps_done is None else sweeps_done) if precision == "mixed" else 0
     npass = 2 * d - 1
-    if mixed:
-        # FP32 passes read and write 4 B per cell; the last pass of a solve writes p in FP64
-        # (8 B, or 16 B when it accumulates in a refinement sweep)
-        first = 4 * (npass * 2 - 1) + 8
-        xf = nc * (first + sweeps * (first + 8))
-        res = sweeps * nc * (8 + 8 + 4)
-    else:
-        xf = nc * (8 * (npass * 2 - 1) + 8)
-        res = 0
+    xf = nc * npass * 8 * (1 + sweeps) * (1 if mixed else 2)
+    # residuals: one per sweep, and with the stopping rule one more (the deciding one)
+    res = (sweeps + (1 if adaptive and sweeps_done is not None else 0)) * nc * (8 + 8 + 4) if mixed else 0
     gauge = nc * ((8 + 16 + 8) if singular else 16) if mixed else (nc * 24 if singular else 0)
     grad = N * (Kg * (4 + d * wbytes) + d * vb * 3 + 1) + nc * 8
     return {"prep": prep, "transfer": tr, "divergence": div, "transform": xf, "residual": res,
             "gauge": gauge, "gradient": grad}
+
+
+def transform_design_bytes(prob, precision, refine):
+    """Bytes the transform passes of this design move per projection: FP32 passes read and write
+    4 B per cell, the first reads the FP32 source, and the last pass of each solve writes the
+    iterate as an FP32 pair (8 B; read and written, 16 B, when it accumulates in a sweep) and,
+    in the last solve, p in FP64 (8 B). Reported beside the roofline, not used for it."""
+    d, nc = prob.dim, prob.num_cells
+    npass = 2 * d - 1
+    if precision != "mixed" and precision != "fp32":
+        return nc * (8 * (npass * 2 - 1) + 8)
+    sweeps = refine if precision == "mixed" else 0
+    first = 4 * (npass * 2 - 1) + 8
+    return nc * (first + sweeps * (first + 8) + 8)
 
 
 def measured_peaks():
@@ -283,7 +305,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     prob = workload()
-    plan = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, device=local_rank)
+    plan = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, refine_tol=args.refine_tol, device=local_rank)
     tune_ms = plan.autotune()          # transform schedule, chosen once per plan (untimed)
     u_dev = torch.as_tensor(prob.u_star, device=dev)
     outs = plan.alloc_outputs()
@@ -335,7 +357,10 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- roofline of the dominant phase (live CUDA events on the launching stream)
     calls = max(prof["calls"], 1)
-    pb = phase_bytes(prob, args.precision, args.refine)
+    _, _, _, st0 = plan.project(u_dev, out=outs, stats=True)   # sweeps the stopping rule ran
+    sweeps_done = st0["refine_iters_done"]
+    adaptive = args.precision == "mixed" and args.refine_tol > 0 and args.refine > 0
+    pb = phase_bytes(prob, args.precision, args.refine, sweeps_done, adaptive)
     phases = {k: v / calls for k, v in prof["phase_ms"].items() if v > 0}
     dom = max((k for k in phases if k in pb), key=lambda k: phases[k])
     peak, peak_src = measured_peaks()
@@ -343,9 +368,14 @@ def run_ours(args, rank, world, local_rank):
     def roof(name):
         ms = phases[name]
         ach = pb[name] / (ms * 1e-3) / 1e9
-        return {"bound": "hbm", "phase": name, "achieved": round(ach, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": ncu_traffic(name),
-                "algorithmic_bytes": pb[name], "ms": round(ms, 5), "peak_source": peak_src}
+        r = {"bound": "hbm", "phase": name, "achieved": round(ach, 1), "peak": peak,
+             "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": ncu_traffic(name),
+             "algorithmic_bytes": pb[name], "ms": round(ms, 5), "peak_source": peak_src}
+        if name == "transform":
+            r["bytes_rule"] = "(2 dim - 1) passes x 8 B per cell per solve, solves = 1 + sweeps"
+            r["design_bytes"] = transform_design_bytes(prob, args.precision, sweeps_done)
+            r["solves"] = 1 + (sweeps_done if args.precision == "mixed" else 0)
+        return r
 
     roofline = roof(dom)
     roofline_transform = roof("transform") if "transform" in phases else None
@@ -367,6 +397,8 @@ def run_ours(args, rank, world, local_rank):
         _, _, _, st = plan.project(u_dev, out=outs, stats=True)
         acc["max_div_after_rel"] = st["max_div_after"] * min(prob.h) / st["max_abs_u_star"]
         acc["residual_norms"] = st["residual_norm"]
+        acc["refine_iters_done"] = st["refine_iters_done"]
+        acc["refine_converged"] = st["refine_converged"]
         if args.precision == "mixed":
             p32 = pc.Plan(prob, precision="fp32", device=local_rank)
             o32 = p32.alloc_outputs()
@@ -403,6 +435,9 @@ def run_ours(args, rank, world, local_rank):
     box3d = None
     if not args.no_3d:
         box3d = run_3d(args, dev, stream, flush, world, rank)
+    serve = None
+    if rank == 0 and world == 1 and not args.no_serve_leg:
+        serve = serving_leg(args, dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -414,8 +449,11 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": list(prob.n), "nodes": prob.num_nodes,
-                   "precision": args.precision, "refine_iters": args.refine,
+                   "precision": args.precision, "refine_iters": args.refine, "refine_tol": args.refine_tol,
                    "knn": prob.knn, "l2": "256 MB buffer written between timed steps",
+                   "headline": "the 1024x512 channel (the workload the metric is quoted on); the 512-problem "
+                               "batch, where the scope table puts the transform-pass HBM target, is reported "
+                               "with its own rooflines in batch_2d_512",
                    "transform_slots": plan.slots(), "transform_ctas_per_sm": plan.ctas(),
                    "tuned_solve_ms": round(tune_ms, 5),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -432,6 +470,7 @@ def run_ours(args, rank, world, local_rank):
         "cufft_reference": cufft,
         "batch_2d_512": batch,
         "box_sphere_3d": box3d,
+        "serving": serve,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -577,7 +616,7 @@ def run_variants(args, prob, u_dev, stream, dev, flush, ms_step, reps=50):
     ms_sp, _ = timed(sp)
     sp.close()
     out["spectral_fp64"] = {"ms_per_step": round(ms_sp, 5), "fd_fp64_ms_per_step": round(ms_fd, 5)}
-    di = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, device=dev.index, div_mode="wls_direct")
+    di = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, refine_tol=args.refine_tol, device=dev.index, div_mode="wls_direct")
     di.autotune()
     ms_di, ph = timed(di)
     di.close()
@@ -592,7 +631,7 @@ def run_variants(args, prob, u_dev, stream, dev, flush, ms_step, reps=50):
         "roofline_divergence": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                                 "frac": round(ach / peak, 4), "algorithmic_bytes": div_bytes,
                                 "peak_source": peak_src}}
-    mk = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, device=dev.index)
+    mk = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, refine_tol=args.refine_tol, device=dev.index)
     mk.autotune()
     g = prob.n
     xc = prob.lo[0] + (np.arange(g[0]) + 0.5) * prob.h[0]
@@ -632,7 +671,7 @@ def run_variants(args, prob, u_dev, stream, dev, flush, ms_step, reps=50):
         row = {}
         for gt in ("vertices", "cells"):
             gp = pc.GridPlan(2, n, hh, lo, hi, grid_type=gt, precision=args.precision,
-                             refine_iters=args.refine, device=dev.index)
+                             refine_iters=args.refine, refine_tol=args.refine_tol, device=dev.index)
             gp.autotune()
             row[gt + "_ms"] = round(timed_solve(gp), 5)
             if gt == "vertices":
@@ -642,7 +681,7 @@ def run_variants(args, prob, u_dev, stream, dev, flush, ms_step, reps=50):
     out["vertex_grid_solve"] = vert
     # the whole pass on the vertex grid of the same workload (direct divergence at the vertex
     # unknowns; the I-D axis extends to 4n, the wall pair to 2n: 8x the cells of the transforms)
-    vp = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, device=dev.index,
+    vp = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, refine_tol=args.refine_tol, device=dev.index,
                  div_mode="wls_direct", grid_type="vertices")
     vp.autotune()
     ms_vp, ph_vp = timed(vp)
@@ -660,7 +699,7 @@ def run_time_step(args, prob, u_dev, stream, dev, flush, reps):
     the stored R and u* read and written, u* written)."""
     import torch
     from paper_2304_14690_gb300 import pc
-    plan = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, device=dev.index)
+    plan = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, refine_tol=args.refine_tol, device=dev.index)
     plan.autotune()
     mom = pc.Momentum(plan, nu=0.01)
     outs = [plan.alloc_outputs() for _ in range(2)]
@@ -716,7 +755,7 @@ def run_3d(args, dev, stream, flush, world, rank):
     prob = wl.box_sphere()
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    plan = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, device=dev.index)
+    plan = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, refine_tol=args.refine_tol, device=dev.index)
     tune_ms = plan.autotune()
     setup_s = time.perf_counter() - t0
     u = torch.as_tensor(prob.u_star, device=dev)
@@ -752,6 +791,20 @@ def run_3d(args, dev, stream, flush, world, rank):
            "transform_slots": plan.slots(), "tuned_solve_ms": round(tune_ms, 4),
            "generate_s": round(gen_s, 1), "plan_and_tune_s": round(setup_s, 1),
            "cufft_rfft_irfft_ms": round(cufft_reference(prob.n[:3], stream, dev, flush), 4)}
+    # roofline of the transform phase by the scope table's bytes (40 B per cell per solve in 3D)
+    _, _, _, st0 = plan.project(u, out=outs, stats=True)
+    sweeps_done = st0["refine_iters_done"]
+    adaptive = args.precision == "mixed" and args.refine_tol > 0 and args.refine > 0
+    pb = phase_bytes(prob, args.precision, args.refine, sweeps_done, adaptive)
+    peak, peak_src = measured_peaks()
+    xf_ms = out["phase_ms"].get("transform", 0.0)
+    if xf_ms > 0:
+        ach = pb["transform"] / (xf_ms * 1e-3) / 1e9
+        out["roofline_transform"] = {
+            "bound": "hbm", "phase": "transform", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(ach / peak, 4), "algorithmic_bytes": pb["transform"], "ms": xf_ms,
+            "solves": 1 + sweeps_done, "bytes_rule": "(2 dim - 1) passes x 8 B per cell per solve, solves = 1 + sweeps",
+            "peak_source": peak_src}
     if rank == 0 and not args.no_extras:
         ref = pc.Plan(prob, precision="fp64", device=dev.index)
         ro = ref.alloc_outputs()
@@ -765,7 +818,8 @@ def run_3d(args, dev, stream, flush, world, rank):
 
         out["accuracy"] = {"rel_l2_p_vs_fp64_gpu": rel(outs[0], ro[0]), "rel_l2_u_vs_fp64_gpu": rel(outs[1], ro[1]),
                            "max_div_after_rel": st["max_div_after"] * min(prob.h) / st["max_abs_u_star"],
-                           "residual_norms": st["residual_norm"]}
+                           "residual_norms": st["residual_norm"], "refine_iters_done": st["refine_iters_done"],
+                           "refine_converged": st["refine_converged"]}
         out["fp64_path"] = {"ms_per_step": round(ms64, 4), "speedup_of_this_path": round(ms64 / ms, 3)}
         ref.close()
     plan.close()
@@ -781,7 +835,7 @@ def run_batch(args, dev, stream, flush, world):
     probs = wl.batch_2d(count=args.batch_problems)
     plans, bargs = [], []
     for pr in probs:
-        plan = pc.Plan(pr, precision=args.precision, refine_iters=args.refine, device=dev.index)
+        plan = pc.Plan(pr, precision=args.precision, refine_iters=args.refine, refine_tol=args.refine_tol, device=dev.index)
         u = torch.as_tensor(pr.u_star, device=dev)
         p, uo, fo = plan.alloc_outputs()
         plans.append(plan)
@@ -804,6 +858,45 @@ def run_batch(args, dev, stream, flush, world):
            "ms_per_batch": round(ms, 4), "value": round(job_value(cells, 1, ms, world), 1), "unit": UNIT,
            "steps": k, "setup_s": round(setup_s, 1),
            "workload": "512 2D problems, n0,n1 in {64..512}, h=1/64, P-P / P-wall / wall-wall, 0-2 circles"}
+    # phases of the batch: a second timed region whose stages record their boundaries into the
+    # first plan's profiler (direct launches, same kernels); roofline of the transform passes by
+    # the scope table's bytes, and of the whole batch by every phase's algorithmic bytes
+    plans[0].profile(True)
+    pc.project_batch(plans, bargs)
+    plans[0].profile_read()
+    for i in range(k):
+        flush.fill_(i & 0xFF)
+        pc.project_batch(plans, bargs)
+    torch.cuda.synchronize(dev)
+    prof = plans[0].profile_read()
+    plans[0].profile(False)
+    calls = max(prof["calls"], 1)
+    phases = {kk: v / calls for kk, v in prof["phase_ms"].items() if v > 0}
+    adaptive = args.precision == "mixed" and args.refine_tol > 0 and args.refine > 0
+    done = []
+    for pl, pr in zip(plans, probs):   # sweeps each problem's stopping rule ran (one stats call each)
+        _, _, _, st = pl.project(torch.as_tensor(pr.u_star, device=dev), stats=True)
+        done.append(st["refine_iters_done"])
+    out["sweeps_done"] = {str(k): done.count(k) for k in sorted(set(done))}
+    pbs = [phase_bytes(pr, args.precision, args.refine, d, adaptive) for pr, d in zip(probs, done)]
+    tot = {kk: sum(b[kk] for b in pbs) for kk in pbs[0]}
+    peak, peak_src = measured_peaks()
+    xf_ms = phases.get("transform", 0.0)
+    if xf_ms > 0:
+        ach = tot["transform"] / (xf_ms * 1e-3) / 1e9
+        out["roofline_transform"] = {
+            "bound": "hbm", "phase": "transform", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(ach / peak, 4), "algorithmic_bytes": tot["transform"], "ms": round(xf_ms, 4),
+            "bytes_rule": "(2 dim - 1) passes x 8 B per cell per solve, solves = 1 + sweeps",
+            "design_bytes": sum(transform_design_bytes(pr, args.precision, d) for pr, d in zip(probs, done)),
+            "peak_source": peak_src}
+    step_bytes = sum(tot.values())
+    ach = step_bytes / (ms * 1e-3) / 1e9
+    out["roofline_step"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                            "frac": round(ach / peak, 4), "algorithmic_bytes": step_bytes, "ms": round(ms, 4),
+                            "peak_source": peak_src}
+    out["phase_ms"] = {kk: round(v, 4) for kk, v in phases.items()}
+    out["profiled_ms_per_batch"] = round(sum(phases.values()), 4)
     for pl in plans:
         pl.close()
     return out
@@ -830,6 +923,62 @@ def run_reference(args, rank):
         "e2e": {"value": round(val, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
+
+
+def serving_leg(args, dev):
+    """A bounded serving run inside the default bench: the first serve_leg_pool geometries of
+    the config-5 pool, serve_leg_requests Poisson arrivals at the configured 2000/s and at two
+    lower rates, continuous batching with backpressure (bounded queue) and a deadline. Reports
+    p50/p99 per rate, the highest rate served without shedding, and the accuracy of a sample of
+    served results against plain FP64 projections of the same requests."""
+    import torch
+    from paper_2304_14690_gb300 import pc, serving, workloads as wl
+    t0 = time.perf_counter()
+    pool = wl.serving_pool(count=args.serve_pool)[: args.serve_leg_pool]
+    gen_s = time.perf_counter() - t0
+    budget = int(args.serve_budget_gb * (1 << 30))
+    rates = [args.serve_rate, 0.75 * args.serve_rate, 0.5 * args.serve_rate]
+    k = args.serve_leg_requests
+    sample = set(range(0, k, max(1, k // 8)))
+    srv = serving.Server(pool, budget_bytes=budget, precision=args.precision, refine=args.refine,
+                         refine_tol=args.refine_tol, max_queue=args.serve_max_queue, deadline_s=args.serve_deadline,
+                         keep_outputs=sample, device=dev.index)
+    t1 = time.perf_counter()
+    srv.warm(range(len(pool)))
+    warm_s = time.perf_counter() - t1
+    legs = []
+    acc = None
+    for ri, rate in enumerate(rates):
+        trace = wl.serving_trace(count=k, rate=rate, pool_size=len(pool), seed=14696 + ri)
+        srv.outputs = {}
+        reqs = srv.run(trace)
+        summ = serving.summarize(reqs, pool)
+        summ.update(rate=rate, batches=srv.batches, mean_batch=round(summ["served"] / max(srv.batches, 1), 2))
+        legs.append(summ)
+        if acc is None:
+            # sampled served requests against the plain FP64 projection of the same u*
+            errs_p, errs_u = [], []
+            for r in reqs:
+                if r.shed or r.rid not in srv.outputs:
+                    continue
+                prob = pool[r.geometry]
+                ref = pc.Plan(prob, precision="fp64", device=dev.index)
+                u = torch.mul(torch.as_tensor(prob.u_star, device=dev), r.scale)
+                p64, u64, _, _ = ref.project(u)
+                got = srv.outputs[r.rid]
+                errs_p.append(float(torch.linalg.vector_norm(got[0].to(dev) - p64) / torch.linalg.vector_norm(p64)))
+                errs_u.append(float(torch.linalg.vector_norm(got[1].to(dev) - u64) / torch.linalg.vector_norm(u64)))
+                ref.close()
+            acc = {"sampled": len(errs_p), "max_rel_l2_p_vs_fp64_gpu": max(errs_p) if errs_p else None,
+                   "max_rel_l2_u_vs_fp64_gpu": max(errs_u) if errs_u else None}
+    srv.close()
+    unshed = [lg["rate"] for lg in legs if lg["shed"]["queue"] + lg["shed"]["deadline"] == 0]
+    n2 = sum(1 for p in pool if p.dim == 2)
+    return {"workload": f"Poisson arrivals, {k} requests per rate, pool of the first {len(pool)} config-5 "
+                        f"geometries ({n2} 2D, {len(pool) - n2} 3D), continuous batching, queue bound "
+                        f"{args.serve_max_queue}, deadline {args.serve_deadline} s",
+            "legs": legs, "highest_rate_without_shedding": max(unshed) if unshed else None,
+            "accuracy": acc, "pool_generate_s": round(gen_s, 1), "warm_s": round(warm_s, 1)}
 
 
 def run_serve(args, rank):
@@ -862,9 +1011,9 @@ def run_serve(args, rank):
         torch.cuda.synchronize()
         return out
 
-    main = serve(trace, precision=args.precision, refine=args.refine)
+    main = serve(trace, precision=args.precision, refine=args.refine, refine_tol=args.refine_tol)
     k = min(args.serve_fp64_requests, len(trace))
-    prefix_mixed = serve(trace[:k], precision=args.precision, refine=args.refine)
+    prefix_mixed = serve(trace[:k], precision=args.precision, refine=args.refine, refine_tol=args.refine_tol)
     prefix_fp64 = serve(trace[:k], precision="fp64", batched=False, max_inflight=1)
     n2 = sum(1 for p in pool if p.dim == 2)
     out = {"metric": "served grid-points/s and p50/p99 latency (continuous batching)",

@@ -112,7 +112,7 @@ typedef struct {
   double support_factor;    /* support radius / local spacing (paper: 3, §2.2) */
   double beta;              /* AB2 pressure factor 3/2 of Eq. 4 */
   int precision;            /* pc_precision */
-  int refine_iters;         /* MIXED: number of refinement sweeps (fixed, >= 0; 2 reaches 1e-10) */
+  int refine_iters;         /* MIXED: largest number of refinement sweeps (0..8; see refine_tol) */
   int gauge;                /* 0: mean(p) = 0; 1: p at the corner cell = 0 (§3.1). Applies only
                                when no face is Dirichlet (the solution is then defined up to
                                a constant) */
@@ -130,6 +130,17 @@ typedef struct {
                                vertices with value 0), and p_out, the RHS mask and the rows of
                                pc_plan_rows(dim + 1) are in the unknowns' layout. The solve length
                                per axis is that of the vertex extension (pc_grid_plan_create) */
+  double refine_tol;        /* MIXED: stopping rule of the refinement (§8 S6 reading), decided on the
+                               device after each residual r_k = s - mean - L_h p_k (k sweeps done):
+                               stop when ||r_k|| <= refine_tol ||s|| (converged); or when k >= 2 and
+                               ||r_k|| > 16 (||r_1|| / ||r_0||) ||r_{k-1}||: the residual no longer
+                               falls at the rate of a sweep, it has reached the rounding floor of
+                               its own evaluation (about 1e-12 to 1e-10 of ||s|| on 256^2 to
+                               4096 x 1024 grids), and the iterate's error is then below the
+                               previous one's by about that rate (converged at the floor); or after
+                               refine_iters sweeps (not converged). Sweeps past the stop are still
+                               launched and exit at once, so graphs and batches keep one shape.
+                               refine_tol <= 0: exactly refine_iters sweeps, no rule */
 } pc_problem_desc;
 
 /* Per-call diagnostics (optional). Filling it synchronizes the stream, and a NaN or infinity that
@@ -143,6 +154,9 @@ typedef struct {
   double max_div_after;     /* max |D_h (U - beta dt G_h p)| over cells (faces corrected) */
   double max_abs_u_star;    /* velocity scale */
   double gauge_shift;       /* constant subtracted from p by the gauge */
+  int refine_converged;     /* MIXED with refine_tol > 0: the stopping rule was met (1) or the
+                               sweeps ran out (0; the call then returns PC_ERR_NOT_CONVERGED with
+                               every output and statistic written) */
 } pc_stats;
 
 typedef struct pc_plan pc_plan;
@@ -284,9 +298,10 @@ typedef struct {
   int bc_lo[3], bc_hi[3];   /* pc_bc per axis end */
   int grid_type;            /* pc_grid_type */
   int precision;            /* pc_precision */
-  int refine_iters;         /* MIXED: refinement sweeps */
+  int refine_iters;         /* MIXED: largest number of refinement sweeps */
   int gauge;                /* 0 mean, 1 corner (used when the problem has a zero mode) */
   int eigenvalues;          /* pc_eigenvalues */
+  double refine_tol;        /* MIXED: stopping rule, as pc_problem_desc.refine_tol */
 } pc_grid_desc;
 pc_status pc_grid_plan_create(const pc_grid_desc *desc, int device, void *cuda_stream, pc_plan **out_plan);
 

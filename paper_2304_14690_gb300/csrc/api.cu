@@ -310,6 +310,7 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
   p->beta = d->beta;
   p->precision = d->precision;
   p->refine_iters = d->refine_iters;
+  p->refine_tol = std::isfinite(d->refine_tol) ? d->refine_tol : 0.0;
   p->gauge = d->gauge;
   p->vdtype = d->velocity_dtype;
   p->eigen = d->eigenvalues;
@@ -495,6 +496,7 @@ static pc_status create_grid(const pc_grid_desc *d, int device, cudaStream_t st,
   p->Kg = d->dim == 2 ? 9 : 27;
   p->precision = d->precision;
   p->refine_iters = d->refine_iters;
+  p->refine_tol = std::isfinite(d->refine_tol) ? d->refine_tol : 0.0;
   p->gauge = d->gauge;
   p->vdtype = PC_DTYPE_F64;
   p->eigen = d->eigenvalues;
@@ -592,7 +594,8 @@ extern "C" pc_status pc_plan_clone(pc_plan *plan, void *cuda_stream, pc_plan **o
   }
   p->N = root->N; p->K = root->K; p->Kg = root->Kg;
   p->eps = root->eps; p->support_factor = root->support_factor; p->beta = root->beta;
-  p->precision = root->precision; p->refine_iters = root->refine_iters; p->gauge = root->gauge;
+  p->precision = root->precision; p->refine_iters = root->refine_iters; p->refine_tol = root->refine_tol;
+  p->gauge = root->gauge;
   p->vdtype = root->vdtype; p->singular = root->singular; p->ncells = root->ncells;
   p->eigen = root->eigen;
   p->divmode = root->divmode; p->ccol = root->ccol; p->cD64 = root->cD64; p->cD2 = root->cD2;

@@ -1,15 +1,16 @@
 // pc_project_batch: many independent projections with one launch per pipeline stage.
 //
 // Problems of a batch are grouped by (dimension, velocity type, neighbour count, refinement
-// sweeps) among plans in mixed or FP32 precision. For each group every stage of the pipeline
-// (prep, transfer per axis, divergence, each transform pass of each solve, residuals, gauge,
-// split, gradient) is ONE kernel launch over all problems of the group: a segment table maps
-// each block to its problem and problem-local block, and each transform pass reads per-problem
-// pass arguments and (problem, tile) work items. The whole sequence is captured once per batch
-// composition into a CUDA graph and replayed. Each problem keeps the block decomposition of its
-// single-problem launches, so batch results are bitwise those of separate pc_project calls.
-// Plans in FP64 precision, and plans with the direct WLS divergence, run one by one through
-// pc_project.
+// settings) among plans in mixed or FP32 precision. For each group every per-cell and per-node
+// stage of the pipeline (prep, transfer per axis, divergence, residuals, gauge, split, gradient)
+// is ONE kernel launch over all problems of the group: a segment table maps each block to its
+// problem and problem-local block. Each transform pass is ONE persistent launch over the
+// problems of every group, 2D and 3D, all transform families and line lengths together: its
+// CTAs walk a work list of (pass arguments, tile) items. The whole sequence is captured once per
+// batch composition into a CUDA graph and replayed. Each problem keeps the block decomposition
+// of its single-problem launches and each line is transformed as in a single call, so batch
+// results are bitwise those of separate pc_project calls. Plans in FP64 precision, and plans
+// with the direct WLS divergence, run one by one through pc_project.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -24,27 +25,26 @@ namespace {
 
 constexpr int kBatchThreads = 256;   // CTA size of the batched transform passes
 
-// One launch of a batched pass: the items of the problems whose pass on this axis belongs to one
-// transform family (and whose lines are all powers of two, or not).
-struct PassBatch {
+// One persistent launch of a batched transform pass: its items in the work list, over every
+// problem of the batch that has this pass (any family, line length and dimension).
+struct PassLaunch {
   int items_off = 0;
   int nitems = 0;
-  int threads = 0;
-  size_t smem = 0;
-  int emax = 1;          // largest slots per thread among the problems' passes
-  int family = 0;
-  bool pow2 = false;
+  int emax = 1;          // largest slots per thread among the items' passes (kernel instance)
+  int grid = 1;          // CTAs: the resident ones, or fewer items
+  size_t smem = 0;       // the pass body's shared memory
+  int stage = 0;         // bytes of the tile staging buffer (the largest tile's input)
 };
 
+// Problems that share the templated per-stage kernels (dimension, velocity type, neighbour
+// count) and the refinement settings.
 struct Group {
   std::vector<int> members;
   int dim = 2, vdtype = 0, K = 12, sweeps = 0;
+  bool adaptive = false;   // refinement with the device-side stopping rule (refine_tol > 0)
   int total[BATCH_STAGES] = {0};
   BatchProblem *dP = nullptr;
   int *dseg = nullptr;                  // BATCH_STAGES x (n + 1)
-  PassArgs<float> *dargs = nullptr;
-  int2 *ditems = nullptr;
-  std::vector<std::vector<PassBatch>> solves;   // [solve][pass]
   bool any_singular = false;
 };
 
@@ -62,6 +62,9 @@ struct Exec {
   std::vector<pc_project_args> args;
   std::vector<Group> groups;
   std::vector<int> singles;             // problems run through pc_project
+  PassArgs<float> *dargs = nullptr;     // transform passes of every problem and solve
+  int2 *ditems = nullptr;               // work list: (args index, tile)
+  std::vector<std::vector<PassLaunch>> passes;   // [solve][pass]
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -119,6 +122,7 @@ bool batchable(const Plan *p) {
   return (p->precision == PC_PREC_MIXED || p->precision == PC_PREC_FP32) && p->divmode == PC_DIV_FACES;
 }
 
+// Per-problem tables of one group: problem descriptions and the block segments of each stage.
 pc_status build_group(Exec *e, Group &g) {
   const int n = (int)g.members.size();
   std::vector<BatchProblem> hp(n);
@@ -134,76 +138,151 @@ pc_status build_group(Exec *e, Group &g) {
   for (int s = 0; s < BATCH_STAGES; ++s) g.total[s] = seg[(size_t)s * (n + 1) + n];
   PC_TRY(upload(e, &g.dP, hp));
   PC_TRY(upload(e, &g.dseg, seg));
-  // transform passes of every solve: first solve from the FP32 source copy, then the sweeps
+  return PC_OK;
+}
+
+// The transform passes of every problem of every group: pass k of solve j of all problems that
+// have it is one persistent launch, its items sorted by transform family, power-of-two length
+// and line length so the CTAs resident together run the same code.
+pc_status build_passes(Exec *e) {
+  int nsm = 152;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, e->device) != cudaSuccess) {
+    cudaGetLastError();
+    nsm = 152;
+  }
+  int jmax = -1;
+  for (const Group &g : e->groups) jmax = std::max(jmax, g.sweeps);
   std::vector<PassArgs<float>> args;
   std::vector<int2> items;
-  for (int j = 0; j <= g.sweeps; ++j) {
-    std::vector<PassBatch> passes;
-    std::vector<std::vector<PassSpec>> specs(n);
-    for (int i = 0; i < n; ++i) {
-      Plan *p = e->plans[g.members[i]];
-      const void *src = reinterpret_cast<const float *>(p->work64);
-      // the iterate is kept in p2 as (hi, lo) pairs; the last solve also writes p in FP64 (as
-      // single calls do)
-      double *f64 = (j == g.sweeps) ? e->args[g.members[i]].p_out : nullptr;
-      specs[i] = solve_pass_specs(p, true, SRC_F32, src, j == 0 ? DST_PAIR_SET : DST_PAIR_ADD, p->p2, f64);
+  for (int j = 0; j <= jmax; ++j) {
+    // pass specs of solve j of every problem that runs it
+    std::vector<std::pair<const Plan *, std::vector<PassSpec>>> specs;
+    size_t npass = 0;
+    for (const Group &g : e->groups) {
+      if (g.sweeps < j) continue;
+      for (int m : g.members) {
+        Plan *p = e->plans[m];
+        const void *src = reinterpret_cast<const float *>(p->work64);
+        // the iterate is kept in p2 as (hi, lo) pairs; the last solve also writes p in FP64 (as
+        // single calls do), and with the stopping rule every solve does (any may be the last)
+        // and the sweeps' passes skip once the rule stopped
+        double *f64 = (j == g.sweeps || g.adaptive) ? e->args[m].p_out : nullptr;
+        const unsigned *skip = g.adaptive ? &p->dstats->refine_stop : nullptr;
+        specs.emplace_back(p, solve_pass_specs(p, true, SRC_F32, src, j == 0 ? DST_PAIR_SET : DST_PAIR_ADD, p->p2,
+                                               f64, skip));
+        npass = std::max(npass, specs.back().second.size());
+      }
     }
-    const size_t npass = specs[0].size();
+    std::vector<PassLaunch> launches;
     for (size_t k = 0; k < npass; ++k) {
-      // pass k of every problem, launched once per (family, power-of-two) key present
-      PassBatch key_pb[6];
-      std::vector<int2> key_items[6];
-      for (int i = 0; i < n; ++i) {
+      struct Entry { long long key; int ai; long long tiles; };
+      std::vector<Entry> list;
+      PassLaunch pl;
+      pl.items_off = (int)items.size();
+      for (const auto &ps : specs) {
+        if (k >= ps.second.size()) continue;
         PassArgs<float> A;
         long long tiles;
         int threads;
         size_t smem;
-        PC_TRY(build_pass<float>(e->plans[g.members[i]], specs[i][k], A, tiles, threads, smem, kBatchThreads));
-        const int ai = (int)args.size();
+        PC_TRY(build_pass<float>(ps.first, ps.second[k], A, tiles, threads, smem, kBatchThreads));
+        const bool pow2 = (A.M & (A.M - 1)) == 0;
+        const long long key = ((long long)pass_family(A.kind) * 2 + (pow2 ? 0 : 1)) * 65536 + (65535 - A.M);
+        list.push_back(Entry{key, (int)args.size(), tiles});
         args.push_back(A);
-        const int key = pass_family(A.kind) * 2 + (((A.M & (A.M - 1)) == 0) ? 1 : 0);
-        PassBatch &pb = key_pb[key];
-        for (long long t = 0; t < tiles; ++t) key_items[key].push_back(make_int2(ai, (int)t));
-        pb.threads = std::max(pb.threads, threads);
-        pb.smem = std::max(pb.smem, smem);
-        pb.emax = std::max(pb.emax, A.emax);
-        pb.family = key / 2;
-        pb.pow2 = key & 1;
+        pl.smem = std::max(pl.smem, smem);
+        pl.emax = std::max(pl.emax, A.emax);
+        pl.stage = std::max(pl.stage, (A.L * A.n * (int)sizeof(float) + 127) & ~127);
       }
-      for (int key = 0; key < 6; ++key) {
-        if (key_items[key].empty()) continue;
-        PassBatch pb = key_pb[key];
-        pb.items_off = (int)items.size();
-        pb.nitems = (int)key_items[key].size();
-        items.insert(items.end(), key_items[key].begin(), key_items[key].end());
-        passes.push_back(pb);
-      }
+      if (list.empty()) continue;
+      std::stable_sort(list.begin(), list.end(), [](const Entry &a, const Entry &b) { return a.key < b.key; });
+      for (const Entry &en : list)
+        for (long long t = 0; t < en.tiles; ++t) items.push_back(make_int2(en.ai, (int)t));
+      pl.nitems = (int)items.size() - pl.items_off;
+      pl.smem = (pl.smem + 127) & ~(size_t)127;
+      const long long resident = (long long)persistent_f32_ctas_per_sm(pl.emax, kBatchThreads, pl.smem + pl.stage) * nsm;
+      pl.grid = (int)std::min<long long>(pl.nitems, resident);
+      launches.push_back(pl);
     }
-    g.solves.push_back(passes);
+    e->passes.push_back(launches);
   }
-  PC_TRY(upload(e, &g.dargs, args));
-  PC_TRY(upload(e, &g.ditems, items));
+  PC_TRY(upload(e, &e->dargs, args));
+  PC_TRY(upload(e, &e->ditems, items));
   return PC_OK;
 }
 
-pc_status record_group(Exec *e, const Group &g, cudaStream_t st) {
-  const int n = (int)g.members.size();
-  auto seg = [&](int s) { return g.dseg + (size_t)s * (n + 1); };
-  batch_launch(BATCH_ZERO, 0, g.dP, nullptr, n, n, 0, st);
-  batch_launch(BATCH_PREP, g.vdtype, g.dP, seg(BATCH_PREP), n, g.total[BATCH_PREP], 0, st);
-  for (int a = 0; a < g.dim; ++a)
-    batch_launch(BATCH_TRANSFER, g.K, g.dP, seg(BATCH_TRANSFER + a), n, g.total[BATCH_TRANSFER + a], a, st);
-  batch_launch(BATCH_DIVERGENCE, 0, g.dP, seg(BATCH_DIVERGENCE), n, g.total[BATCH_DIVERGENCE], 0, st);
-  for (int j = 0; j <= g.sweeps; ++j) {
-    if (j > 0) batch_launch(BATCH_RESIDUAL, 0, g.dP, seg(BATCH_RESIDUAL), n, g.total[BATCH_RESIDUAL], 0, st);
-    for (const PassBatch &pb : g.solves[j])
-      PC_TRY(launch_batched_pass_f32(pb.family, pb.pow2, g.dargs, g.ditems + pb.items_off, pb.nitems, pb.threads,
-                                     pb.smem, pb.emax, st));
+// The whole batch on one stream: the per-group stages, and one persistent launch per transform
+// pass for every group. prof (nullable): a plan whose profiler records the phase boundaries
+// (direct launches only, not under capture), with the phase tags of pc_profile_read.
+pc_status record_exec(Exec *e, cudaStream_t st, Plan *prof = nullptr) {
+  long long launches = 0;
+  auto mark = [&](int tag) { if (prof) prof_mark(prof, st, tag); };
+  auto segs = [](const Group &g, int s) { return g.dseg + (size_t)s * (g.members.size() + 1); };
+  if (prof) prof_begin(prof, st);
+  for (const Group &g : e->groups) {
+    const int n = (int)g.members.size();
+    batch_launch(BATCH_ZERO, 0, g.dP, nullptr, n, n, 0, st);
+    batch_launch(BATCH_PREP, g.vdtype, g.dP, segs(g, BATCH_PREP), n, g.total[BATCH_PREP], 0, st);
+    launches += 2;
   }
-  if (g.any_singular)
-    batch_launch(BATCH_GAUGE_SUM, 0, g.dP, seg(BATCH_GAUGE_SUM), n, g.total[BATCH_GAUGE_SUM], 0, st);
-  batch_launch(BATCH_FINALIZE, 0, g.dP, seg(BATCH_FINALIZE), n, g.total[BATCH_FINALIZE], 0, st);
-  batch_launch(BATCH_GRADIENT, g.dim * 10 + g.vdtype, g.dP, seg(BATCH_GRADIENT), n, g.total[BATCH_GRADIENT], 0, st);
+  mark(0);
+  for (const Group &g : e->groups)
+    for (int a = 0; a < g.dim; ++a) {
+      const int n = (int)g.members.size();
+      batch_launch(BATCH_TRANSFER, g.K, g.dP, segs(g, BATCH_TRANSFER + a), n, g.total[BATCH_TRANSFER + a], a, st);
+      ++launches;
+    }
+  mark(1);
+  for (const Group &g : e->groups) {
+    const int n = (int)g.members.size();
+    batch_launch(BATCH_DIVERGENCE, 0, g.dP, segs(g, BATCH_DIVERGENCE), n, g.total[BATCH_DIVERGENCE], 0, st);
+    ++launches;
+  }
+  mark(2);
+  for (size_t j = 0; j < e->passes.size(); ++j) {
+    if (j > 0) {
+      for (const Group &g : e->groups) {
+        if (g.sweeps < (int)j) continue;
+        const int n = (int)g.members.size();
+        batch_launch(BATCH_RESIDUAL, 0, g.dP, segs(g, BATCH_RESIDUAL), n, g.total[BATCH_RESIDUAL], (int)j - 1, st);
+        ++launches;
+      }
+      mark(4);
+    }
+    for (const PassLaunch &pl : e->passes[j]) {
+      PC_TRY(launch_persistent_f32(e->dargs, e->ditems + pl.items_off, pl.nitems, pl.grid, kBatchThreads, pl.smem,
+                                   pl.stage, pl.emax, st));
+      ++launches;
+    }
+    mark(3);
+  }
+  bool any_final = false;
+  for (const Group &g : e->groups) {
+    if (!g.adaptive || g.sweeps <= 0) continue;   // the residual after the last allowed sweep
+    const int n = (int)g.members.size();
+    batch_launch(BATCH_RESIDUAL, 1, g.dP, segs(g, BATCH_RESIDUAL), n, g.total[BATCH_RESIDUAL], g.sweeps, st);
+    ++launches;
+    any_final = true;
+  }
+  if (any_final) mark(4);
+  for (const Group &g : e->groups) {
+    const int n = (int)g.members.size();
+    if (g.any_singular) {
+      batch_launch(BATCH_GAUGE_SUM, 0, g.dP, segs(g, BATCH_GAUGE_SUM), n, g.total[BATCH_GAUGE_SUM], 0, st);
+      ++launches;
+    }
+    batch_launch(BATCH_FINALIZE, 0, g.dP, segs(g, BATCH_FINALIZE), n, g.total[BATCH_FINALIZE], 0, st);
+    ++launches;
+  }
+  mark(5);
+  for (const Group &g : e->groups) {
+    const int n = (int)g.members.size();
+    batch_launch(BATCH_GRADIENT, g.dim * 10 + g.vdtype, g.dP, segs(g, BATCH_GRADIENT), n, g.total[BATCH_GRADIENT], 0,
+                 st);
+    ++launches;
+  }
+  mark(6);
+  if (prof) count_launch(prof, launches);
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
 }
@@ -215,18 +294,20 @@ pc_status build_groups(Exec *e) {
     Plan *p = e->plans[i];
     if (!batchable(p)) { e->singles.push_back(i); continue; }
     const int sweeps = p->precision == PC_PREC_MIXED ? p->refine_iters : 0;
+    const bool adaptive = p->precision == PC_PREC_MIXED && p->refine_tol > 0.0 && sweeps > 0;
     const int K = (p->K == 12 || p->K == 27) ? p->K : 0;
     Group *g = nullptr;
     for (Group &c : e->groups)
-      if (c.dim == p->dim && c.vdtype == p->vdtype && c.K == K && c.sweeps == sweeps) g = &c;
+      if (c.dim == p->dim && c.vdtype == p->vdtype && c.K == K && c.sweeps == sweeps && c.adaptive == adaptive) g = &c;
     if (!g) {
       e->groups.emplace_back();
       g = &e->groups.back();
-      g->dim = p->dim; g->vdtype = p->vdtype; g->K = K; g->sweeps = sweeps;
+      g->dim = p->dim; g->vdtype = p->vdtype; g->K = K; g->sweeps = sweeps; g->adaptive = adaptive;
     }
     g->members.push_back(i);
   }
   for (Group &g : e->groups) PC_TRY(build_group(e, g));
+  if (!e->groups.empty()) PC_TRY(build_passes(e));
   return PC_OK;
 }
 
@@ -235,9 +316,7 @@ pc_status build_exec(Exec *e) {
   PC_CUDA_TRY(cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking));
   if (!e->groups.empty()) {
     PC_CUDA_TRY(cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal));
-    pc_status s = PC_OK;
-    for (const Group &g : e->groups)
-      if (s == PC_OK) s = record_group(e, g, e->cap);
+    pc_status s = record_exec(e, e->cap);
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(e->cap, &graph);
     if (s != PC_OK || ce != cudaSuccess) {
@@ -366,7 +445,16 @@ extern "C" pc_status pc_project_batch(int count, pc_plan *const *plans, const pc
     }
     e->stamp = ++g_clock;
   }
-  if (e->exec) PC_CUDA_TRY(cudaGraphLaunch(e->exec, st));
+  // a batch whose plans include a profiled one runs its stages directly and records their
+  // boundaries into the first such plan's profiler (pc_profile_read)
+  Plan *prof = nullptr;
+  for (int i = 0; i < count && !prof; ++i)
+    if (reinterpret_cast<Plan *>(plans[i])->prof) prof = reinterpret_cast<Plan *>(plans[i]);
+  if (prof && !e->groups.empty()) {
+    PC_TRY(record_exec(e, st, prof));
+  } else if (e->exec) {
+    PC_CUDA_TRY(cudaGraphLaunch(e->exec, st));
+  }
   return run_singles(*e, plans, args, cuda_stream);
 }
 
@@ -428,7 +516,10 @@ extern "C" pc_status pc_batcher_launch(pc_batcher *batcher, int count, pc_plan *
   PC_TRY(build_groups(&e));
   if (e.arena->used > 0)
     PC_CUDA_TRY(cudaMemcpyAsync(sl.arena.dev, sl.arena.host, e.arena->used, cudaMemcpyHostToDevice, st));
-  for (const Group &g : e.groups) PC_TRY(record_group(&e, g, st));
+  Plan *prof = nullptr;
+  for (int i = 0; i < count && !prof; ++i)
+    if (reinterpret_cast<Plan *>(plans[i])->prof) prof = reinterpret_cast<Plan *>(plans[i]);
+  if (!e.groups.empty()) PC_TRY(record_exec(&e, st, prof));
   PC_CUDA_TRY(cudaEventRecord(sl.done, st));
   sl.pending = true;
   return run_singles(e, plans, args, cuda_stream);

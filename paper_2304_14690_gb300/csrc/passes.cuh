@@ -12,6 +12,7 @@ enum SrcMode { SRC_F32 = 0, SRC_F64 = 1, SRC_WORK = 2 };
 
 constexpr int kMaxPassThreads = 512;   // CTA size limit of the transform passes
 constexpr int kBatchPassEmax = 16;     // largest slots per thread of a batched pass kernel
+constexpr int kPersistentThreads = 256; // CTA size of the persistent batched pass (3 resident per SM)
 // DST_PAIR_*: the refinement iterate of the FP32 solves, kept as FP32 (hi, lo) pairs
 // (double-float): SET stores the pass result, ADD adds it to the stored pair.
 enum DstMode { DST_WORK = 0, DST_F64_SET = 1, DST_F64_ADD = 2, DST_PAIR_SET = 3, DST_PAIR_ADD = 4 };
@@ -42,6 +43,9 @@ struct PassArgs {
   void *dst;
   Real out_scale;       // normalisation of the inverse (2/n)
   double *f64;          // nullable (pair modes): also store the pair's value in FP64
+  const unsigned *skip; // nullable: the pass does nothing when *skip is nonzero (a refinement
+                        // sweep after the device-side stopping rule ended the refinement)
+  unsigned *err;        // nullable: the problem's status word (DevStats::flags) for device errors
 };
 
 // One pass of a solve: axis, phases, source and destination.
@@ -53,12 +57,14 @@ struct PassSpec {
   int dst_mode;
   void *dst;
   double *f64;          // nullable (pair modes): also store the result in FP64
+  const unsigned *skip; // nullable: skip flag of PassArgs
 };
 
 // The passes of one solve of plan p from src to dst, in launch order; f64 (nullable) goes to
 // the final pass.
 std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, const void *src,
-                                       int dst_mode, void *dst, double *f64 = nullptr);
+                                       int dst_mode, void *dst, double *f64 = nullptr,
+                                       const unsigned *skip = nullptr);
 // Fill the kernel arguments and launch shape of one pass (no launch). batch_threads > 0 sizes
 // the tile to fill a CTA of that many threads (batched launches); 0 sizes it so that the
 // problem alone fills the GPU.
@@ -74,17 +80,13 @@ pc_status launch_pass_f32_family2(const PassArgs<float> &A, long long tiles, int
 pc_status prepare_pass_f32_family0(int lim);
 pc_status prepare_pass_f32_family1(int lim);
 pc_status prepare_pass_f32_family2(int lim);
-// Batched FP32 passes of one family (pow2: every line length of the items is a power of two).
-pc_status launch_batched_f32_family0(const PassArgs<float> *dargs, const int2 *ditems, int nitems, int threads,
-                                     size_t smem, int emax, bool pow2, cudaStream_t st);
-pc_status launch_batched_f32_family1(const PassArgs<float> *dargs, const int2 *ditems, int nitems, int threads,
-                                     size_t smem, int emax, bool pow2, cudaStream_t st);
-pc_status launch_batched_f32_family2(const PassArgs<float> *dargs, const int2 *ditems, int nitems, int threads,
-                                     size_t smem, int emax, bool pow2, cudaStream_t st);
-inline int pass_family(int kind) { return kind == KIND_PP ? 0 : ((kind == KIND_NN || kind == KIND_DD) ? 1 : 2); }
-// One launch of the batched FP32 pass kernel over items (args index, tile) of one family;
-// emax: the largest slots per thread among the items' passes (selects the kernel instance).
-pc_status launch_batched_pass_f32(int family, bool pow2, const PassArgs<float> *dargs, const int2 *ditems,
-                                  int nitems, int threads, size_t smem, int emax, cudaStream_t st);
+// Persistent FP32 pass over a work list of (args index, tile) items of any family and length
+// (one launch per pass for a whole batch); grid: CTAs, at most the resident ones; stage_bytes:
+// shared memory for staging the next tile's input (0: no staging).
+pc_status launch_persistent_f32(const PassArgs<float> *dargs, const int2 *ditems, int nitems, int grid, int threads,
+                                size_t smem, int stage_bytes, int emax, cudaStream_t st);
+int persistent_f32_ctas_per_sm(int emax, int threads, size_t smem);
+pc_status prepare_persistent_f32(int lim);
+__host__ __device__ inline int pass_family(int kind) { return kind == KIND_PP ? 0 : ((kind == KIND_NN || kind == KIND_DD) ? 1 : 2); }
 
 }  // namespace pc

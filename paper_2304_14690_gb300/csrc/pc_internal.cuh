@@ -20,7 +20,7 @@ constexpr long long kMaxRows = (1LL << 31) - (1LL << 16);
 constexpr int kMaxRefine = 8;
 
 // Device-side status word values (written by kernels, read at the next sync point).
-enum DeviceFlag { FLAG_WLS_SINGULAR = 1, FLAG_KNN_SHORT = 2, FLAG_NONFINITE = 4 };
+enum DeviceFlag { FLAG_WLS_SINGULAR = 1, FLAG_KNN_SHORT = 2, FLAG_NONFINITE = 4, FLAG_TIMEOUT = 8 };
 
 struct AxisInfo {
   int kind = 0;
@@ -59,6 +59,11 @@ struct DevStats {
   double ib_prev;          //   and of |f_old|^2
   unsigned int flags;
   unsigned int pad;
+  // refinement stopping rule (MIXED with refine_tol > 0), written by the deciding residual
+  unsigned int refine_stop;  // nonzero: no further sweep (later sweeps' kernels exit at once)
+  int sweeps_done;           // sweeps run when the rule decided
+  int refine_conv;           // the rule was met (tolerance or rounding floor)
+  int pad2;
 };
 
 // Per-call event record of the optional profiler: segment i (between events i and i+1) belongs
@@ -122,7 +127,8 @@ struct Plan {
   int Kg = 9;                  // cells of a node (gradient) stencil: 3^dim
   double eps = 6.3, support_factor = 3.0, beta = 1.5;
   int precision = PC_PREC_FP64;
-  int refine_iters = 2;
+  int refine_iters = 2;        // MIXED: largest number of refinement sweeps
+  double refine_tol = 0.0;     // MIXED: stopping rule tolerance (<= 0: refine_iters sweeps, no rule)
   int gauge = 0;
   int vdtype = PC_DTYPE_F64;
   bool singular = false;
@@ -260,7 +266,7 @@ inline int grid_for(int64_t work, int threads) {
 // destination modes are those of passes.cuh (FP32 or FP64 source; FP64 set or accumulate).
 pc_status solve_fp64_grid(Plan *p, const double *s, double *pout, cudaStream_t st);
 pc_status solve_fp32_grid(Plan *p, int src_mode, const void *s, int dst_mode, void *dst,
-                          cudaStream_t st, double *f64 = nullptr);
+                          cudaStream_t st, double *f64 = nullptr, const unsigned *skip = nullptr);
 // Drops the plan's captured CUDA graphs and batch executables (after a schedule change).
 void plan_drop_graphs(Plan *p);
 // ----------------------------------------------------------------------------- batches
@@ -291,6 +297,8 @@ struct GridDev {
 struct BatchProblem {
   GridDev g;
   int dim, vdtype, N, ncells, K, Kg, singular, gmode;
+  int kmax;            // refinement sweeps at most; adaptive when tol2 > 0
+  double tol2;         // squared refinement tolerance (<= 0: fixed sweep count)
   const void *u, *f;
   void *uo, *fo;
   double *p;

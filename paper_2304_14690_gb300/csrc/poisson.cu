@@ -184,6 +184,8 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   A.dst = dst;
   A.out_scale = (Real)inv_scale(ax.kind, ax.n);
   A.f64 = ps.f64;
+  A.skip = ps.skip;
+  A.err = p->dstats ? &p->dstats->flags : nullptr;
   threads = L * tpl;
   if (threads > kMaxPassThreads || L * M > budget)
     return fail(PC_ERR_UNSUPPORTED, "axis %d: tile of %d x %d too large", axis, L, M);
@@ -217,40 +219,34 @@ static pc_status launch_pass(Plan *p, const PassSpec &ps, cudaStream_t st) {
   return PC_OK;
 }
 
-pc_status launch_batched_pass_f32(int family, bool pow2, const PassArgs<float> *dargs, const int2 *ditems,
-                                  int nitems, int threads, size_t smem, int emax, cudaStream_t st) {
-  if (family == 0) return launch_batched_f32_family0(dargs, ditems, nitems, threads, smem, emax, pow2, st);
-  if (family == 1) return launch_batched_f32_family1(dargs, ditems, nitems, threads, smem, emax, pow2, st);
-  return launch_batched_f32_family2(dargs, ditems, nitems, threads, smem, emax, pow2, st);
-}
-
 // Kernel attributes set once per device, before any stream capture.
 pc_status prepare_kernels() {
   const int lim = 200 * 1024;
   PC_TRY(prepare_pass_f32_family0(lim));
   PC_TRY(prepare_pass_f32_family1(lim));
   PC_TRY(prepare_pass_f32_family2(lim));
+  PC_TRY(prepare_persistent_f32(lim));
   PC_TRY((prepare_axis_pass_spec<double, -1, false>(lim)));
   return PC_OK;
 }
 
 std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, const void *src,
-                                       int dst_mode, void *dst, double *f64) {
+                                       int dst_mode, void *dst, double *f64, const unsigned *skip) {
   std::vector<PassSpec> v;
   void *work = fp32 ? (void *)p->work32 : (void *)p->work64;
   const int d = p->dim;
   int cur_mode = src_mode;
   const void *cur = src;
   for (int a = d - 1; a >= 1; --a) {     // forward passes: last axis down to axis 1
-    v.push_back(PassSpec{a, true, false, false, cur_mode, cur, DST_WORK, work, nullptr});
+    v.push_back(PassSpec{a, true, false, false, cur_mode, cur, DST_WORK, work, nullptr, skip});
     cur_mode = SRC_WORK;
     cur = work;
   }
-  v.push_back(PassSpec{0, true, true, true, cur_mode, cur, DST_WORK, work, nullptr});   // axis 0, division
+  v.push_back(PassSpec{0, true, true, true, cur_mode, cur, DST_WORK, work, nullptr, skip});   // axis 0, division
   for (int a = 1; a < d; ++a) {         // inverse passes: axis 1 up to the last axis
     const bool final_pass = (a == d - 1);
     v.push_back(PassSpec{a, false, false, true, SRC_WORK, work, final_pass ? dst_mode : DST_WORK,
-                         final_pass ? dst : work, final_pass ? f64 : nullptr});
+                         final_pass ? dst : work, final_pass ? f64 : nullptr, skip});
   }
   return v;
 }
@@ -258,9 +254,9 @@ std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, c
 // Full solve with Real precision: src (cells, src_mode) -> dst (dst_mode).
 template <typename Real>
 static pc_status solve_real(Plan *p, int src_mode, const void *src, int dst_mode, void *dst,
-                            cudaStream_t st, double *f64 = nullptr) {
+                            cudaStream_t st, double *f64 = nullptr, const unsigned *skip = nullptr) {
   if (p->dim < 2) return fail(PC_ERR_UNSUPPORTED, "dim 1");
-  for (const PassSpec &ps : solve_pass_specs(p, sizeof(Real) == 4, src_mode, src, dst_mode, dst, f64))
+  for (const PassSpec &ps : solve_pass_specs(p, sizeof(Real) == 4, src_mode, src, dst_mode, dst, f64, skip))
     PC_TRY(launch_pass<Real>(p, ps, st));
   return PC_OK;
 }
@@ -270,8 +266,8 @@ pc_status solve_fp64_grid(Plan *p, const double *s, double *pout, cudaStream_t s
 }
 
 pc_status solve_fp32_grid(Plan *p, int src_mode, const void *s, int dst_mode, void *dst,
-                          cudaStream_t st, double *f64) {
-  return solve_real<float>(p, src_mode, s, dst_mode, dst, st, f64);
+                          cudaStream_t st, double *f64, const unsigned *skip) {
+  return solve_real<float>(p, src_mode, s, dst_mode, dst, st, f64, skip);
 }
 
 }  // namespace pc

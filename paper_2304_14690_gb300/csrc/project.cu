@@ -482,11 +482,41 @@ __device__ __forceinline__ DF df_neg_(DF a) { return DF{-a.hi, -a.lo}; }
 // so its ~2^-44 relative rounding bounds the attainable accuracy far below the 1e-10 target.
 // SV, PV: storage of s and p, double or a float2 (hi, lo) pair (the refinement keeps both as
 // pairs; FP64 arrays come from pc_solve_poisson and from the statistics of FP64 plans).
+// Refinement step of a residual launch: k sweeps are done before it (res2 = &stats->res2[k]);
+// with decide set, the thread that completes ||r_k||^2 applies the stopping rule (at most kmax
+// sweeps, squared tolerance tol2); with skip set, the launch does nothing once the rule stopped.
+struct RefineStep {
+  int k, kmax, decide, skip;
+  double tol2;
+};
+
+// Refinement runs adaptively (MIXED with refine_tol > 0 and sweeps allowed): every residual
+// measures its norm and the deciding thread applies the stopping rule; later sweeps' kernels
+// exit at once, and every solve writes p in FP64 since any of them may be the last.
+static bool refine_adaptive(const Plan *p) {
+  return p->precision == PC_PREC_MIXED && p->refine_tol > 0.0 && p->refine_iters > 0;
+}
+
+// The stopping rule after residual k: converged when ||r_k||^2 <= tol2 ||s||^2; at the rounding
+// floor of the residual's own evaluation when, from the second sweep on, ||r_k|| exceeds 16 times
+// the first sweep's contraction ||r_1|| / ||r_0|| applied to ||r_{k-1}|| (squared: 256); stop
+// after kmax sweeps either way. Later sweeps' kernels read refine_stop and exit.
+__device__ __forceinline__ void refine_decide(DevStats *st, const RefineStep &rs) {
+  const double r2 = st->res2[rs.k];
+  const bool conv = r2 <= rs.tol2 * st->sum_s2;
+  bool floor_hit = false;
+  if (rs.k >= 2 && st->res2[0] > 0.0) floor_hit = r2 > 256.0 * (st->res2[1] / st->res2[0]) * st->res2[rs.k - 1];
+  st->sweeps_done = rs.k;
+  st->refine_conv = (conv || floor_hit) ? 1 : 0;
+  if (conv || floor_hit || rs.k >= rs.kmax) st->refine_stop = 1u;
+}
+
 template <int DIM, bool SINGULAR, bool WRITE_R, bool NORM, typename SV, typename PV>
 __device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, const SV *__restrict__ s,
                                               const PV *__restrict__ p, float *__restrict__ r,
-                                              const DevStats *stats, double *res2, double *partials,
-                                              unsigned int *counter) {
+                                              DevStats *stats, double *res2, double *partials,
+                                              unsigned int *counter, RefineStep rs = RefineStep{0, 0, 0, 0, 0.0}) {
+  if (rs.skip && __ldcg(&stats->refine_stop)) return;   // the refinement already stopped
   int x, row0;
   tile_pos(g, b, x, row0);
   double nrm = 0.0;
@@ -524,14 +554,16 @@ __device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, cons
       }
     }
   }
-  if (NORM) grid_sum(nrm, partials, counter, res2, tile_block(g, b));
+  if (NORM) {
+    if (grid_sum(nrm, partials, counter, res2, tile_block(g, b)) && rs.decide) refine_decide(stats, rs);
+  }
 }
 template <int DIM, bool SINGULAR, bool WRITE_R, bool NORM, typename SV, typename PV>
 __global__ void residual_kernel(GridDev g, const SV *__restrict__ s, const PV *__restrict__ p,
-                                float *__restrict__ r, const DevStats *stats, double *res2,
-                                double *partials, unsigned int *counter) {
+                                float *__restrict__ r, DevStats *stats, double *res2,
+                                double *partials, unsigned int *counter, RefineStep rs) {
   pdl_enter();
-  residual_body<DIM, SINGULAR, WRITE_R, NORM, SV, PV>(blockIdx.x, g, s, p, r, stats, res2, partials, counter);
+  residual_body<DIM, SINGULAR, WRITE_R, NORM, SV, PV>(blockIdx.x, g, s, p, r, stats, res2, partials, counter, rs);
 }
 
 // ----------------------------------------------------------------------------- gauge
@@ -1028,26 +1060,41 @@ __global__ void batch_divergence(const BatchProblem *__restrict__ P, const int *
   if (q.g.dim == 2)
     divergence_body<2>(lb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, nullptr, reinterpret_cast<float2 *>(q.s64),
                        q.s32, q.ds, q.partials, q.counters,
-                       q.singular, q.inv_ncells);
+                       q.tol2 > 0.0 ? 2 : q.singular, q.inv_ncells);
   else
     divergence_body<3>(lb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, nullptr, reinterpret_cast<float2 *>(q.s64),
                        q.s32, q.ds, q.partials, q.counters,
-                       q.singular, q.inv_ncells);
+                       q.tol2 > 0.0 ? 2 : q.singular, q.inv_ncells);
 }
 
-__global__ void batch_residual(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
+// Residual k of every problem (k sweeps done). Problems with an adaptive refinement (tol2 > 0)
+// measure ||r_k|| and apply the stopping rule, and skip the launch once it stopped; FINAL: the
+// residual after the last allowed sweep (adaptive problems only, the rule's last decision).
+template <bool FINAL>
+__global__ void batch_residual(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count, int k) {
   pdl_enter();
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
   const unsigned lb = blockIdx.x - seg[pi];
   const float2 *s2 = reinterpret_cast<const float2 *>(q.s64);
+  const bool ad = q.tol2 > 0.0;
+  if (FINAL && !ad) return;
+  const RefineStep rs{k, q.kmax, ad ? 1 : 0, ad ? 1 : 0, q.tol2};
+  double *res2 = &q.ds->res2[k];
+#define PC_BRES(D, S)                                                                                            \
+  do {                                                                                                           \
+    if (FINAL) residual_body<D, S, false, true>(lb, q.g, s2, q.p2, q.r32, q.ds, res2, q.partials, q.counters, rs); \
+    else if (ad) residual_body<D, S, true, true>(lb, q.g, s2, q.p2, q.r32, q.ds, res2, q.partials, q.counters, rs); \
+    else residual_body<D, S, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters);      \
+  } while (0)
   if (q.g.dim == 2) {
-    if (q.singular) residual_body<2, true, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters);
-    else residual_body<2, false, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters);
+    if (q.singular) PC_BRES(2, true);
+    else PC_BRES(2, false);
   } else {
-    if (q.singular) residual_body<3, true, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters);
-    else residual_body<3, false, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters);
+    if (q.singular) PC_BRES(3, true);
+    else PC_BRES(3, false);
   }
+#undef PC_BRES
 }
 
 __global__ void batch_gauge_sum(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
@@ -1092,7 +1139,10 @@ void batch_launch(int stage, int variant, const BatchProblem *P, const int *seg,
       else launch_pdl(batch_transfer<0>, total_blocks, T, 0, st, P, seg, count, extra);
       break;
     case BATCH_DIVERGENCE: launch_pdl(batch_divergence, total_blocks, T, 0, st, P, seg, count); break;
-    case BATCH_RESIDUAL: launch_pdl(batch_residual, total_blocks, T, 0, st, P, seg, count); break;
+    case BATCH_RESIDUAL:
+      if (variant) launch_pdl(batch_residual<true>, total_blocks, T, 0, st, P, seg, count, extra);
+      else launch_pdl(batch_residual<false>, total_blocks, T, 0, st, P, seg, count, extra);
+      break;
     case BATCH_GAUGE_SUM: launch_pdl(batch_gauge_sum, total_blocks, T, 0, st, P, seg, count); break;
     case BATCH_FINALIZE: launch_pdl(batch_finalize, total_blocks, T, 0, st, P, seg, count); break;
     case BATCH_GRADIENT:
@@ -1124,6 +1174,8 @@ void batch_problem_fill(const Plan *p, const pc_project_args &a, BatchProblem &q
   q.dim = p->dim; q.vdtype = p->vdtype; q.N = (int)p->N; q.ncells = (int)p->ncells; q.K = p->K; q.Kg = p->Kg;
   q.singular = p->singular;
   q.gmode = p->singular ? (p->gauge == 1 ? 2 : 1) : 0;
+  q.kmax = p->precision == PC_PREC_MIXED ? p->refine_iters : 0;
+  q.tol2 = refine_adaptive(p) ? p->refine_tol * p->refine_tol : 0.0;
   q.u = a.u_star; q.f = a.f_ib_in; q.uo = a.u_out; q.fo = a.f_ib_out; q.p = a.p_out;
   q.dt = a.dt; q.inv_dt = 1.0 / a.dt; q.beta = p->beta; q.inv_bdt = 1.0 / (p->beta * a.dt);
   q.inv_ncells = 1.0 / (double)p->ncells;
@@ -1208,13 +1260,13 @@ static bool is_device_ptr(const void *ptr) {
 template <typename SV, typename PV>
 static void launch_residual(bool singular, bool write_r, bool norm, cudaStream_t st, const GridDev &g,
                             const SV *s, const PV *p, float *r, DevStats *ds, double *res2, double *partials,
-                            unsigned int *counters) {
+                            unsigned int *counters, RefineStep rs = RefineStep{0, 0, 0, 0, 0.0}) {
 #define PC_RES(S, W, N)                                                                                       \
   do {                                                                                                        \
     if (g.dim == 2)                                                                                           \
-      launch_pdl(residual_kernel<2, S, W, N, SV, PV>, g.nblk, 256, 0, st, g, s, p, r, ds, res2, partials, counters); \
+      launch_pdl(residual_kernel<2, S, W, N, SV, PV>, g.nblk, 256, 0, st, g, s, p, r, ds, res2, partials, counters, rs); \
     else                                                                                                      \
-      launch_pdl(residual_kernel<3, S, W, N, SV, PV>, g.nblk, 256, 0, st, g, s, p, r, ds, res2, partials, counters); \
+      launch_pdl(residual_kernel<3, S, W, N, SV, PV>, g.nblk, 256, 0, st, g, s, p, r, ds, res2, partials, counters, rs); \
   } while (0)
   if (singular) {
     if (write_r) { if (norm) PC_RES(true, true, true); else PC_RES(true, true, false); }
@@ -1249,35 +1301,54 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
     PC_TRY(solve_fp64_grid(p, s64, pout, st));
     prof_mark(p, st, 3);
   } else {
-    int sweeps = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
-    if (s32) PC_TRY(solve_fp32_grid(p, SRC_F32_, s32, DST_PAIR_SET_, p->p2, st, sweeps ? nullptr : pout));
-    else PC_TRY(solve_fp32_grid(p, SRC_F64_, s64, DST_PAIR_SET_, p->p2, st, sweeps ? nullptr : pout));
+    const int sweeps = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
+    const bool adaptive = refine_adaptive(p);
+    const unsigned *skip = adaptive ? &p->dstats->refine_stop : nullptr;
+    const double tol2 = adaptive ? p->refine_tol * p->refine_tol : 0.0;
+    auto step = [&](int k, bool decide) { return RefineStep{k, sweeps, decide ? 1 : 0, adaptive ? 1 : 0, tol2}; };
+    const bool norm = want_final_residual || adaptive;
+    double *first_out = (sweeps == 0 || adaptive) ? pout : nullptr;
+    if (s32) PC_TRY(solve_fp32_grid(p, SRC_F32_, s32, DST_PAIR_SET_, p->p2, st, first_out));
+    else PC_TRY(solve_fp32_grid(p, SRC_F64_, s64, DST_PAIR_SET_, p->p2, st, first_out));
     prof_mark(p, st, 3);
     for (int it = 0; it < sweeps; ++it) {
       float *r32 = reinterpret_cast<float *>(p->work64);   // work64 is free in mixed mode
       if (s2)
-        launch_residual(p->singular, true, want_final_residual, st, g, s2, (const float2 *)p->p2, r32, p->dstats,
-                        &p->dstats->res2[it], p->partials, p->counters);
+        launch_residual(p->singular, true, norm, st, g, s2, (const float2 *)p->p2, r32, p->dstats,
+                        &p->dstats->res2[it], p->partials, p->counters, step(it, adaptive));
       else
-        launch_residual(p->singular, true, want_final_residual, st, g, s64, (const float2 *)p->p2, r32, p->dstats,
-                        &p->dstats->res2[it], p->partials, p->counters);
+        launch_residual(p->singular, true, norm, st, g, s64, (const float2 *)p->p2, r32, p->dstats,
+                        &p->dstats->res2[it], p->partials, p->counters, step(it, adaptive));
       count_launch(p);
       prof_mark(p, st, 4);
-      PC_TRY(solve_fp32_grid(p, SRC_F32_, r32, DST_PAIR_ADD_, p->p2, st, it == sweeps - 1 ? pout : nullptr));
+      PC_TRY(solve_fp32_grid(p, SRC_F32_, r32, DST_PAIR_ADD_, p->p2, st,
+                             (adaptive || it == sweeps - 1) ? pout : nullptr, skip));
       prof_mark(p, st, 3);
     }
+    // the residual after the last sweep: the rule's last decision, and the statistics
+    if (sweeps > 0 && norm) {
+      if (s2)
+        launch_residual(p->singular, false, true, st, g, s2, (const float2 *)p->p2, (float *)nullptr, p->dstats,
+                        &p->dstats->res2[sweeps], p->partials, p->counters, step(sweeps, adaptive));
+      else
+        launch_residual(p->singular, false, true, st, g, s64, (const float2 *)p->p2, (float *)nullptr, p->dstats,
+                        &p->dstats->res2[sweeps], p->partials, p->counters, step(sweeps, adaptive));
+      count_launch(p);
+      prof_mark(p, st, adaptive ? 4 : 7);
+    }
   }
-  if (want_final_residual && p->eigen == PC_EIG_FD) {   // the residual of L_h: FD solves only
-    int it = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
+  // the residual of an FP64 or unrefined FP32 solve (statistics; the residual of L_h: FD solves only)
+  const bool refined = p->precision == PC_PREC_MIXED && p->refine_iters > 0;
+  if (want_final_residual && p->eigen == PC_EIG_FD && !refined) {
     if (p->precision == PC_PREC_FP64)
       launch_residual(p->singular, false, true, st, g, s64, (const double *)pout, (float *)nullptr, p->dstats,
-                      &p->dstats->res2[it], p->partials, p->counters);
+                      &p->dstats->res2[0], p->partials, p->counters);
     else if (s2)
       launch_residual(p->singular, false, true, st, g, s2, (const float2 *)p->p2, (float *)nullptr, p->dstats,
-                      &p->dstats->res2[it], p->partials, p->counters);
+                      &p->dstats->res2[0], p->partials, p->counters);
     else
       launch_residual(p->singular, false, true, st, g, s64, (const float2 *)p->p2, (float *)nullptr, p->dstats,
-                      &p->dstats->res2[it], p->partials, p->counters);
+                      &p->dstats->res2[0], p->partials, p->counters);
     count_launch(p);
     prof_mark(p, st, 7);
   }
@@ -1308,9 +1379,12 @@ static pc_status fill_stats(Plan *p, pc_stats *stats, cudaStream_t st) {
   const bool zero_mode = p->vertex ? p->problem_singular : p->singular;
   stats->removed_mean = zero_mode ? ds.sum_s / nc : 0.0;
   stats->source_norm = std::sqrt(fmax(ds.sum_s2, 0.0));
+  const bool adaptive = refine_adaptive(p);
   int its = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
+  if (adaptive) its = ds.sweeps_done;
   for (int i = 0; i <= its && i < 9; ++i) stats->residual_norm[i] = std::sqrt(fmax(ds.res2[i], 0.0));
   stats->refine_iters_done = its;
+  stats->refine_converged = adaptive ? ds.refine_conv : 1;
   stats->max_div_after = ds.max_div;
   stats->max_abs_u_star = ds.max_u;
   const int gmode = gauge_mode(p);
@@ -1318,6 +1392,9 @@ static pc_status fill_stats(Plan *p, pc_stats *stats, cudaStream_t st) {
   // a NaN or infinity anywhere in u~ reaches the source sums (the maxima above skip NaN)
   if (!std::isfinite(ds.sum_s) || !std::isfinite(ds.sum_s2))
     return fail(PC_ERR_INVALID_ARG, "non-finite source: u_star, f_ib_in or dt hold a NaN or infinity");
+  if (adaptive && !ds.refine_conv)
+    return fail(PC_ERR_NOT_CONVERGED, "refinement: ||r||/||s|| = %.3g after %d sweeps (tolerance %.3g)",
+                std::sqrt(fmax(ds.res2[its], 0.0)) / fmax(stats->source_norm, 1e-300), its, p->refine_tol);
   return PC_OK;
 }
 
@@ -1392,7 +1469,7 @@ static pc_status vertex_pass_solve(Plan *p, cudaStream_t st, double inv_bdt, dou
   count_launch(p);
   // the source sums: the mean the residual removes (zero-mode problems; an odd extension has
   // mean zero) and the statistics
-  if (want_stats || p->problem_singular) {
+  if (want_stats || p->problem_singular || refine_adaptive(p)) {
     launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, (const double *)p->s64, p->dstats,
                p->partials, p->counters);
     count_launch(p);
@@ -1444,7 +1521,7 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   if (p->vertex) {
     PC_TRY(vertex_pass_solve(p, st, 1.0 / (p->beta * dt), dp, stats != nullptr));
   } else if (p->divmode == PC_DIV_WLS_DIRECT) {
-    launch_direct_div(p, st, 1.0 / (p->beta * dt), stats ? 2 : (p->singular ? 1 : 0));
+    launch_direct_div(p, st, 1.0 / (p->beta * dt), (stats || refine_adaptive(p)) ? 2 : (p->singular ? 1 : 0));
     count_launch(p);
     prof_mark(p, st, 2);
   }
@@ -1469,7 +1546,7 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
     launch_pdl(divk, g.nblk, 256, 0, st, g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt),
                mixed ? nullptr : p->s64, mixed ? reinterpret_cast<float2 *>(p->s64) : nullptr,
                mixed ? reinterpret_cast<float *>(p->work64) : nullptr, p->dstats, p->partials, p->counters,
-               stats ? 2 : (p->singular ? 1 : 0), 1.0 / (double)nc);
+               (stats || refine_adaptive(p)) ? 2 : (p->singular ? 1 : 0), 1.0 / (double)nc);
     count_launch(p);
     prof_mark(p, st, 2);
   }

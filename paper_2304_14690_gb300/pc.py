@@ -58,6 +58,7 @@ class ProblemDesc(ctypes.Structure):
         ("eigenvalues", ctypes.c_int),
         ("divergence", ctypes.c_int),
         ("grid_type", ctypes.c_int),
+        ("refine_tol", ctypes.c_double),
     ]
 
 
@@ -70,6 +71,7 @@ class Stats(ctypes.Structure):
         ("max_div_after", ctypes.c_double),
         ("max_abs_u_star", ctypes.c_double),
         ("gauge_shift", ctypes.c_double),
+        ("refine_converged", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -77,7 +79,7 @@ class Stats(ctypes.Structure):
         return dict(removed_mean=self.removed_mean, source_norm=self.source_norm,
                     residual_norm=list(self.residual_norm[: n + 1]), refine_iters_done=n,
                     max_div_after=self.max_div_after, max_abs_u_star=self.max_abs_u_star,
-                    gauge_shift=self.gauge_shift)
+                    gauge_shift=self.gauge_shift, refine_converged=bool(self.refine_converged))
 
 
 class Profile(ctypes.Structure):
@@ -110,6 +112,7 @@ class GridDesc(ctypes.Structure):
         ("refine_iters", ctypes.c_int),
         ("gauge", ctypes.c_int),
         ("eigenvalues", ctypes.c_int),
+        ("refine_tol", ctypes.c_double),
     ]
 
 
@@ -183,9 +186,13 @@ def load():
     return lib
 
 
-def _check(status):
+def _check(status, stats=None):
+    """Raise PcError for a failed call; stats (a filled Stats, nullable) travel with the error,
+    e.g. the residual norms of a refinement that did not converge."""
     if status != 0:
-        raise PcError(status, load().pc_last_error_message().decode())
+        err = PcError(status, load().pc_last_error_message().decode())
+        err.stats = stats.as_dict() if stats is not None else None
+        raise err
 
 
 def _ptr(x, shape=None, dtype=None, name="array"):
@@ -232,8 +239,15 @@ EIGENVALUES = {"fd": 0, "spectral": 1}
 DIVERGENCE = {"faces": 0, "wls_direct": 1}
 
 
-def make_desc(problem, precision="fp64", refine_iters=2, gauge=0, velocity_dtype=None,
-              node_xyz=None, node_type=None, eigenvalues="fd", div_mode="faces", grid_type="cells"):
+# Refinement defaults: at most 4 sweeps, stopping at ||r|| <= 1e-13 ||s|| or at the residual's
+# rounding floor (pc_problem_desc.refine_tol).
+REFINE_ITERS = 4
+REFINE_TOL = 1e-13
+
+
+def make_desc(problem, precision="fp64", refine_iters=REFINE_ITERS, gauge=0, velocity_dtype=None,
+              node_xyz=None, node_type=None, eigenvalues="fd", div_mode="faces", grid_type="cells",
+              refine_tol=REFINE_TOL):
     d = ProblemDesc()
     d.dim = problem.dim
     for a in range(3):
@@ -253,6 +267,7 @@ def make_desc(problem, precision="fp64", refine_iters=2, gauge=0, velocity_dtype
     d.beta = float(problem.beta)
     d.precision = PRECISION[precision]
     d.refine_iters = int(refine_iters)
+    d.refine_tol = float(refine_tol)
     d.gauge = int(gauge)
     if velocity_dtype is None:
         velocity_dtype = "f32" if problem.u_star.dtype == np.float32 else "f64"
@@ -266,8 +281,9 @@ def make_desc(problem, precision="fp64", refine_iters=2, gauge=0, velocity_dtype
 class Plan:
     """A libpc plan for one problem geometry (nodes, grid, boundaries)."""
 
-    def __init__(self, problem, precision="fp64", refine_iters=2, gauge=0, device=0,
-                 budget_bytes=0, stream=None, eigenvalues="fd", div_mode="faces", grid_type="cells"):
+    def __init__(self, problem, precision="fp64", refine_iters=REFINE_ITERS, gauge=0, device=0,
+                 budget_bytes=0, stream=None, eigenvalues="fd", div_mode="faces", grid_type="cells",
+                 refine_tol=REFINE_TOL):
         import torch
         lib = load()
         self.problem = problem
@@ -278,7 +294,7 @@ class Plan:
         typ = torch.as_tensor(np.ascontiguousarray(problem.node_type, dtype=np.uint8), device=self.device)
         self._desc = make_desc(problem, precision, refine_iters, gauge,
                                "f32" if self.vdtype == torch.float32 else "f64", xyz, typ, eigenvalues, div_mode,
-                               grid_type)
+                               grid_type, refine_tol)
         h = ctypes.c_void_p()
         _check(lib.pc_plan_create(ctypes.byref(self._desc), device, budget_bytes,
                                   _stream_handle(stream), ctypes.byref(h)))
@@ -402,7 +418,7 @@ class Plan:
                               _ptr(f_ib, vshape, self.vdtype, "f_ib"),
                               _ptr(p, self.shape, None, "p_out"), _ptr(u, vshape, self.vdtype, "u_out"),
                               _ptr(f, vshape, self.vdtype, "f_out"),
-                              ctypes.byref(st) if st is not None else None, _stream_handle(stream)))
+                              ctypes.byref(st) if st is not None else None, _stream_handle(stream)), st)
         return p, u, f, (st.as_dict() if st is not None else None)
 
     def set_rhs_mask(self, mask, stream=None):
@@ -443,7 +459,7 @@ class Plan:
         st = Stats() if stats else None
         _check(lib.pc_solve_poisson(self.handle, _ptr(s, self.shape, torch.float64, "s"),
                                     _ptr(p_out, self.shape, torch.float64, "p_out"),
-                                    ctypes.byref(st) if st is not None else None, _stream_handle(stream)))
+                                    ctypes.byref(st) if st is not None else None, _stream_handle(stream)), st)
         return p_out, (st.as_dict() if st is not None else None)
 
 
@@ -452,8 +468,8 @@ class GridPlan(Plan):
     the vertex pressure grid. solve_poisson, autotune and the schedule controls apply; the node
     entry points do not."""
 
-    def __init__(self, dim, n, h, bc_lo, bc_hi, grid_type="cells", precision="fp64", refine_iters=2,
-                 gauge=0, eigenvalues="fd", device=0, stream=None):
+    def __init__(self, dim, n, h, bc_lo, bc_hi, grid_type="cells", precision="fp64", refine_iters=REFINE_ITERS,
+                 gauge=0, eigenvalues="fd", device=0, stream=None, refine_tol=REFINE_TOL):
         import torch
         lib = load()
         d = GridDesc()
@@ -466,6 +482,7 @@ class GridPlan(Plan):
         d.grid_type = GRID_TYPE[grid_type]
         d.precision = PRECISION[precision]
         d.refine_iters = int(refine_iters)
+        d.refine_tol = float(refine_tol)
         d.gauge = int(gauge)
         d.eigenvalues = EIGENVALUES[eigenvalues]
         self._gdesc = d

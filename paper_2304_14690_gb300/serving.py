@@ -11,7 +11,10 @@ Requests for projections on different grids arrive over time. The server:
     pipeline stage for all its problems) on a free stream, so that while batches run on the
     device the next one is assembled from the requests that arrived meanwhile and launched as
     soon as an in-flight slot frees: batches overlap on the device;
-  - records each request's completion from a CUDA event recorded behind its batch.
+  - records each request's completion from a CUDA event recorded behind its batch;
+  - bounds latency under overload: an arrival that finds max_queue requests already waiting is
+    refused at once (backpressure), and a waiting request not launched within deadline_s of its
+    arrival is dropped (load shedding). Shed requests are counted and never computed.
 A request's result does not depend on the batch it rides in: the batched kernels keep the
 single-call decomposition, so results equal those of a pc_project call on the same plan.
 """
@@ -36,6 +39,7 @@ class Request:
     done: float = math.nan
     cold: bool = False      # its plan was built when it was admitted
     batch: int = -1
+    shed: str = ""          # "queue" (refused on arrival) or "deadline" (dropped while waiting)
 
     @property
     def latency(self):
@@ -160,18 +164,22 @@ class _Batch:
 class Server:
     """Continuous-batching request loop over a pool of geometries (workloads.Problem)."""
 
-    def __init__(self, geometries, budget_bytes, precision="mixed", refine=2, max_batch=64,
-                 max_inflight=2, max_instances=4, clone_headroom=8 << 30, device=0,
-                 keep_outputs=False, batched=True, tune=False):
+    def __init__(self, geometries, budget_bytes, precision="mixed", refine=4, max_batch=64,
+                 max_inflight=4, max_instances=4, clone_headroom=8 << 30, device=0,
+                 keep_outputs=False, batched=True, tune=False, refine_tol=1e-13, max_queue=None,
+                 deadline_s=None):
         import torch
         self.torch = torch
         self.geoms = geometries
         self.precision = precision
         self.refine = refine
+        self.refine_tol = refine_tol
         self.max_batch = max_batch if batched else 1
         self.max_inflight = max_inflight
         self.device = torch.device("cuda", device)
-        self.keep_outputs = keep_outputs
+        self.keep_outputs = keep_outputs  # True: every request's outputs; a set: those request ids
+        self.max_queue = max_queue        # waiting requests beyond which arrivals are refused
+        self.deadline_s = deadline_s      # a request not launched this long after arrival is dropped
         self.batched = batched
         self.tune = tune
         self.base_u = {}
@@ -201,7 +209,7 @@ class Server:
 
     def _make_plan(self, gid, budget):
         prob = self.geoms[gid]
-        plan = pc.Plan(prob, precision=self.precision, refine_iters=self.refine,
+        plan = pc.Plan(prob, precision=self.precision, refine_iters=self.refine, refine_tol=self.refine_tol,
                        device=self.device.index, budget_bytes=int(budget))
         if self.tune:
             plan.autotune()
@@ -290,12 +298,25 @@ class Server:
         i = ndone = nbatch = 0
         self.host_s = 0.0          # host time assembling and launching batches
         self.gpu_s = 0.0           # sum of batch durations on the device (overlaps counted twice)
+        self.shed = 0
         while ndone < len(reqs):
             now = time.perf_counter() - t0
             while i < len(reqs) and reqs[i].arrival <= now:
-                queues[reqs[i].geometry].append(reqs[i])
-                waiting += 1
+                if self.max_queue is not None and waiting >= self.max_queue:
+                    reqs[i].shed = "queue"           # backpressure: refused on arrival
+                    ndone += 1
+                    self.shed += 1
+                else:
+                    queues[reqs[i].geometry].append(reqs[i])
+                    waiting += 1
                 i += 1
+            if self.deadline_s is not None and waiting:
+                for q in queues.values():
+                    while q and now - q[0].arrival > self.deadline_s:
+                        q.popleft().shed = "deadline"    # load shedding: dropped while waiting
+                        waiting -= 1
+                        ndone += 1
+                        self.shed += 1
             for b in list(inflight):
                 if b.end.query():
                     t_done = start.elapsed_time(b.end) * 1e-3
@@ -304,7 +325,8 @@ class Server:
                         r.done = t_done
                     if self.keep_outputs:
                         for rid, p_out, u_out, f_out, _ in b.outputs:
-                            self.outputs[rid] = (p_out.cpu(), u_out.cpu(), f_out.cpu())
+                            if self.keep_outputs is True or rid in self.keep_outputs:
+                                self.outputs[rid] = (p_out.cpu(), u_out.cpu(), f_out.cpu())
                     self.io_used -= b.io_bytes
                     inflight.remove(b)
                     ndone += len(b.reqs)
@@ -354,15 +376,22 @@ class _OwnedPlan:
 
 
 def summarize(reqs, geoms):
-    """Throughput and latency of a served trace."""
-    lat = np.array([r.latency for r in reqs]) * 1e3
-    cells = sum(geoms[r.geometry].num_cells for r in reqs)
+    """Throughput and latency of a served trace (latency over the requests that were served;
+    shed requests are counted apart)."""
+    served = [r for r in reqs if not r.shed]
+    out = {"requests": len(reqs), "served": len(served),
+           "shed": {"queue": sum(r.shed == "queue" for r in reqs),
+                    "deadline": sum(r.shed == "deadline" for r in reqs)}}
+    if not served:
+        return out
+    lat = np.array([r.latency for r in served]) * 1e3
+    cells = sum(geoms[r.geometry].num_cells for r in served)
     t_first = min(r.arrival for r in reqs)
-    t_last = max(r.done for r in reqs)
-    return {"requests": len(reqs), "cells": int(cells),
-            "value": cells / (t_last - t_first), "unit": "grid-points/s",
-            "seconds": round(t_last - t_first, 4),
-            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
-                           "p99": round(float(np.percentile(lat, 99)), 3),
-                           "mean": round(float(lat.mean()), 3), "max": round(float(lat.max()), 3)},
-            "cold_requests": int(sum(r.cold for r in reqs))}
+    t_last = max(r.done for r in served)
+    out.update({"cells": int(cells), "value": cells / (t_last - t_first), "unit": "grid-points/s",
+                "seconds": round(t_last - t_first, 4),
+                "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                               "p99": round(float(np.percentile(lat, 99)), 3),
+                               "mean": round(float(lat.mean()), 3), "max": round(float(lat.max()), 3)},
+                "cold_requests": int(sum(r.cold for r in served))})
+    return out

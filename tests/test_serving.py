@@ -107,3 +107,28 @@ def test_clone_shares_rows_and_matches(env, pool):
     twin.close()
     root.close()
     bat.close()
+
+
+def test_overload_is_shed_and_latency_bounded(env, pool):
+    """Offered far above capacity, with a bounded queue and a deadline: arrivals that find the
+    queue full are refused, waiting requests past the deadline are dropped, every other request
+    is served within deadline + the time of the batches ahead of it, and served results still
+    equal single calls."""
+    pc, serving, torch = env
+    trace = wl.serving_trace(count=400, rate=2.0e6, pool_size=len(pool), seed=9)
+    srv = serving.Server(pool, budget_bytes=40 << 30, keep_outputs=True, max_queue=16, deadline_s=0.002,
+                         max_batch=8)
+    srv.warm(range(len(pool)))
+    reqs = srv.run(trace)
+    s = serving.summarize(reqs, pool)
+    assert s["shed"]["queue"] > 0                # the burst overflowed the queue
+    assert s["served"] + s["shed"]["queue"] + s["shed"]["deadline"] == len(reqs)
+    assert 0 < s["served"] < len(reqs)
+    served = [r for r in reqs if not r.shed]
+    assert all(np.isfinite(r.done) and r.launched - r.arrival <= 0.002 + 0.02 for r in served)
+    assert all(r.rid not in srv.outputs for r in reqs if r.shed)
+    for r in served[:20]:
+        ref = _alone(srv, torch, r.geometry, r.scale)
+        for a, b in zip(srv.outputs[r.rid], ref):
+            assert torch.equal(a, b), r
+    srv.close()
