@@ -130,16 +130,19 @@ typedef struct {
                                vertices with value 0), and p_out, the RHS mask and the rows of
                                pc_plan_rows(dim + 1) are in the unknowns' layout. The solve length
                                per axis is that of the vertex extension (pc_grid_plan_create) */
-  double refine_tol;        /* MIXED: stopping rule of the refinement (§8 S6 reading), decided on the
-                               device after each residual r_k = s - mean - L_h p_k (k sweeps done):
-                               stop when ||r_k|| <= refine_tol ||s|| (converged); or when k >= 2 and
-                               ||r_k|| > 16 (||r_1|| / ||r_0||) ||r_{k-1}||: the residual no longer
-                               falls at the rate of a sweep, it has reached the rounding floor of
-                               its own evaluation (about 1e-12 to 1e-10 of ||s|| on 256^2 to
-                               4096 x 1024 grids), and the iterate's error is then below the
+  double refine_tol;        /* MIXED: stopping rule of the refinement, decided on the device after
+                               each residual r_k = s - mean - L_h p_k (k sweeps done), on max
+                               norms: stop when ||r_k|| <= refine_tol ||s|| (converged); or when
+                               k >= 2 and ||r_k|| > 16 (||r_1|| / ||r_0||) ||r_{k-1}||: the residual
+                               no longer falls at the rate of a sweep, it has reached the rounding
+                               floor of its own evaluation (about 1e-12 to 1e-10 of ||s|| on 256^2
+                               to 4096 x 1024 grids) and the iterate's error is then below the
                                previous one's by about that rate (converged at the floor); or after
-                               refine_iters sweeps (not converged). Sweeps past the stop are still
-                               launched and exit at once, so graphs and batches keep one shape.
+                               refine_iters sweeps. Sweeps past the stop are still launched and
+                               exit at once, so graphs and batches keep one shape. The verdict is
+                               reported with statistics (pc_stats.refine_converged; a call whose
+                               sweeps ran out returns PC_ERR_NOT_CONVERGED); without statistics the
+                               call does not wait and reports nothing.
                                refine_tol <= 0: exactly refine_iters sweeps, no rule */
 } pc_problem_desc;
 

@@ -233,7 +233,7 @@ __device__ __forceinline__ void axis_pass_body(const PassArgs<Real> &A, const in
 template <typename Real, int EMAX, int KC, bool POW2>
 __global__ void __launch_bounds__(kMaxPassThreads) axis_pass(PassArgs<Real> A) {
   pdl_enter();
-  if (A.skip && __ldcg(A.skip)) return;   // the refinement already stopped on the device
+  if (A.gate.st && refine_stopped_before(A.gate.st, A.gate.j, A.gate.tol)) return;   // refinement already ended
   extern __shared__ __align__(16) unsigned char smem_raw[];
   axis_pass_body<Real, EMAX, KC, POW2>(A, blockIdx.x, smem_raw);
 }
@@ -273,6 +273,15 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                : "memory");
 }
 
+// Whether the pass *G (in global memory) belongs to a refinement sweep that the stopping rule
+// already ended: every thread reading it gets the same answer.
+template <typename Real>
+__device__ __forceinline__ bool gate_closed(const PassArgs<Real> *G) {
+  const DevStats *st =
+      reinterpret_cast<const DevStats *>(__ldg(reinterpret_cast<const unsigned long long *>(&G->gate.st)));
+  return st && refine_stopped_before(st, __ldg(&G->gate.j), __ldg(&G->gate.tol));
+}
+
 // Warp 0 of the CTA: stage the input of tile t of pass *G into stg, if the pass reads 4-byte
 // elements whose tile rows start on 16-byte boundaries (row tiles: n % 4 == 0; column tiles:
 // stride and lines per tile multiples of 4) and its problem is not skipped. Returns (uniformly
@@ -283,8 +292,6 @@ __device__ __noinline__ bool stage_tile(const PassArgs<Real> *G, int t, Real *st
   const int src_mode = __ldg(&G->src_mode);
   const char *src = reinterpret_cast<const char *>(__ldg(reinterpret_cast<const unsigned long long *>(&G->src)));
   if (src_mode == SRC_F64 || (reinterpret_cast<unsigned long long>(src) & 15)) return false;
-  const unsigned *skip = reinterpret_cast<const unsigned *>(__ldg(reinterpret_cast<const unsigned long long *>(&G->skip)));
-  if (skip && __ldcg(skip)) return false;
   const int n = __ldg(&G->n), L = __ldg(&G->L), col = __ldg(&G->col), stride = __ldg(&G->stride);
   const int lane = threadIdx.x & 31;
   if (col) {
@@ -325,28 +332,41 @@ __device__ __noinline__ bool stage_tile(const PassArgs<Real> *G, int t, Real *st
 // launch covers every problem of a batch whatever its transform family, line length and
 // dimension; the work list is sorted by family and length, so the CTAs resident at one time run
 // the same code, one body per (family, power-of-two length) as in the single-problem kernel.
-// Each tile is transformed exactly as by the single-problem kernel. Dynamic shared
-// memory: the staging buffer (stage_bytes) then the body's buffers.
+// Each tile is transformed exactly as by the single-problem kernel. Dynamic shared memory: the
+// gate table (gate_bytes), the staging buffer (stage_bytes), then the body's buffers.
+// Gated launches (refinement sweeps under the stopping rule): the items' pass arguments are
+// args[a0, a0 + nargs); each CTA first evaluates every one's gate into the table, one byte per
+// pass, so an item is checked with one shared-memory read (passes beyond the table's bytes are
+// checked in global memory).
 template <typename Real, int EMAX>
 __global__ void __launch_bounds__(kPersistentThreads, 3) axis_pass_persistent(const PassArgs<Real> *__restrict__ args,
                                                                         const int2 *__restrict__ items, int nitems,
-                                                                        int stage_bytes) {
+                                                                        int stage_bytes, int gate_bytes, int a0,
+                                                                        int nargs, int gated) {
   pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) PassArgs<Real> A;
   __shared__ __align__(8) unsigned long long bar;
   __shared__ int s_staged, s_ok;
-  Real *stg = reinterpret_cast<Real *>(smem_raw);   // 16-byte aligned: the bulk copies' rule
-  unsigned char *body_smem = smem_raw + stage_bytes;
+  unsigned char *gates = smem_raw;
+  Real *stg = reinterpret_cast<Real *>(smem_raw + gate_bytes);   // 16-byte aligned: the bulk copies' rule
+  unsigned char *body_smem = smem_raw + gate_bytes + stage_bytes;
   const bool use_stage = stage_bytes > 0;
+  if (gated)
+    for (int a = threadIdx.x; a < nargs && a < gate_bytes; a += blockDim.x) gates[a] = gate_closed(args + a0 + a) ? 1 : 0;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     s_staged = 0;
   }
   __syncthreads();
+  auto closed = [&](int ai) -> bool {
+    if (!gated) return false;
+    const int g = ai - a0;
+    return (g >= 0 && g < gate_bytes && g < nargs) ? gates[g] != 0 : gate_closed(args + ai);
+  };
   if (use_stage && threadIdx.x < 32 && (int)blockIdx.x < nitems) {
     const int2 w0 = items[blockIdx.x];
-    const bool st = stage_tile(args + w0.x, w0.y, stg, &bar);
+    const bool st = !closed(w0.x) && stage_tile(args + w0.x, w0.y, stg, &bar);
     if (threadIdx.x == 0) s_staged = st ? 1 : 0;
   }
   unsigned phase = 0;
@@ -356,9 +376,7 @@ __global__ void __launch_bounds__(kPersistentThreads, 3) axis_pass_persistent(co
     // an item of a problem whose refinement already stopped is passed over without a barrier:
     // every thread reads the same flag (set by an earlier kernel), and such an item is never
     // staged, so the staging state carries over to the next item unchanged
-    const unsigned *sk =
-        reinterpret_cast<const unsigned *>(__ldg(reinterpret_cast<const unsigned long long *>(&args[w.x].skip)));
-    if (sk && __ldcg(sk)) continue;
+    if (closed(w.x)) continue;
     __syncthreads();   // the previous tile no longer reads A or the buffers; s_staged is set
     if (w.x != cur) {
       const unsigned *src = reinterpret_cast<const unsigned *>(args + w.x);
@@ -384,7 +402,7 @@ __global__ void __launch_bounds__(kPersistentThreads, 3) axis_pass_persistent(co
     const int next = it + gridDim.x;
     auto after_load = [&]() {
       if (use_stage && threadIdx.x < 32) {
-        const bool st = next < nitems && stage_tile(args + items[next].x, items[next].y, stg, &bar);
+        const bool st = next < nitems && !closed(items[next].x) && stage_tile(args + items[next].x, items[next].y, stg, &bar);
         if (threadIdx.x == 0) s_staged = st ? 1 : 0;
       }
     };
@@ -404,16 +422,21 @@ __global__ void __launch_bounds__(kPersistentThreads, 3) axis_pass_persistent(co
 
 template <typename Real>
 pc_status launch_persistent(const PassArgs<Real> *dargs, const int2 *ditems, int nitems, int grid, int threads,
-                            size_t smem, int stage_bytes, int emax, cudaStream_t st) {
+                            size_t smem, int stage_bytes, int gate_bytes, int a0, int nargs, int gated, int emax,
+                            cudaStream_t st) {
   if (nitems <= 0) return PC_OK;
-  const size_t sm = smem + (size_t)stage_bytes;
+  const size_t sm = smem + (size_t)stage_bytes + (size_t)gate_bytes;
+#define PC_PERS(E)                                                                                                  \
+  launch_pdl(axis_pass_persistent<Real, E>, (unsigned)grid, threads, sm, st, dargs, ditems, nitems, stage_bytes, \
+             gate_bytes, a0, nargs, gated)
   switch (emax) {
-    case 1: case 2: launch_pdl(axis_pass_persistent<Real, 2>, (unsigned)grid, threads, sm, st, dargs, ditems, nitems, stage_bytes); break;
-    case 4: launch_pdl(axis_pass_persistent<Real, 4>, (unsigned)grid, threads, sm, st, dargs, ditems, nitems, stage_bytes); break;
-    case 8: launch_pdl(axis_pass_persistent<Real, 8>, (unsigned)grid, threads, sm, st, dargs, ditems, nitems, stage_bytes); break;
-    case 16: launch_pdl(axis_pass_persistent<Real, 16>, (unsigned)grid, threads, sm, st, dargs, ditems, nitems, stage_bytes); break;
+    case 1: case 2: PC_PERS(2); break;
+    case 4: PC_PERS(4); break;
+    case 8: PC_PERS(8); break;
+    case 16: PC_PERS(16); break;
     default: return fail(PC_ERR_UNSUPPORTED, "no persistent transform kernel for %d slots per thread", emax);
   }
+#undef PC_PERS
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
 }

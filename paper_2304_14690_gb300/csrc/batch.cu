@@ -34,6 +34,9 @@ struct PassLaunch {
   int grid = 1;          // CTAs: the resident ones, or fewer items
   size_t smem = 0;       // the pass body's shared memory
   int stage = 0;         // bytes of the tile staging buffer (the largest tile's input)
+  int a0 = 0, nargs = 0; // the launch's pass arguments: args[a0, a0 + nargs)
+  int gated = 0;         // a refinement sweep under the stopping rule: items check their gate
+  int gate_bytes = 0;    // shared-memory gate table (one byte per pass argument, capped)
 };
 
 // Problems that share the templated per-stage kernels (dimension, velocity type, neighbour
@@ -167,9 +170,10 @@ pc_status build_passes(Exec *e) {
         // single calls do), and with the stopping rule every solve does (any may be the last)
         // and the sweeps' passes skip once the rule stopped
         double *f64 = (j == g.sweeps || g.adaptive) ? e->args[m].p_out : nullptr;
-        const unsigned *skip = g.adaptive ? &p->dstats->refine_stop : nullptr;
+        const RefineGate gate = (g.adaptive && j > 0) ? RefineGate{p->dstats, j, (float)p->refine_tol}
+                                                       : RefineGate{nullptr, 0, 0.0f};
         specs.emplace_back(p, solve_pass_specs(p, true, SRC_F32, src, j == 0 ? DST_PAIR_SET : DST_PAIR_ADD, p->p2,
-                                               f64, skip));
+                                               f64, gate));
         npass = std::max(npass, specs.back().second.size());
       }
     }
@@ -179,6 +183,7 @@ pc_status build_passes(Exec *e) {
       std::vector<Entry> list;
       PassLaunch pl;
       pl.items_off = (int)items.size();
+      pl.a0 = (int)args.size();
       for (const auto &ps : specs) {
         if (k >= ps.second.size()) continue;
         PassArgs<float> A;
@@ -193,14 +198,18 @@ pc_status build_passes(Exec *e) {
         pl.smem = std::max(pl.smem, smem);
         pl.emax = std::max(pl.emax, A.emax);
         pl.stage = std::max(pl.stage, (A.L * A.n * (int)sizeof(float) + 127) & ~127);
+        if (A.gate.st) pl.gated = 1;
       }
       if (list.empty()) continue;
+      pl.nargs = (int)args.size() - pl.a0;
+      pl.gate_bytes = pl.gated ? (std::min(pl.nargs, 16384) + 127) & ~127 : 0;
       std::stable_sort(list.begin(), list.end(), [](const Entry &a, const Entry &b) { return a.key < b.key; });
       for (const Entry &en : list)
         for (long long t = 0; t < en.tiles; ++t) items.push_back(make_int2(en.ai, (int)t));
       pl.nitems = (int)items.size() - pl.items_off;
       pl.smem = (pl.smem + 127) & ~(size_t)127;
-      const long long resident = (long long)persistent_f32_ctas_per_sm(pl.emax, kBatchThreads, pl.smem + pl.stage) * nsm;
+      const long long resident =
+          (long long)persistent_f32_ctas_per_sm(pl.emax, kBatchThreads, pl.smem + pl.stage + pl.gate_bytes) * nsm;
       pl.grid = (int)std::min<long long>(pl.nitems, resident);
       launches.push_back(pl);
     }
@@ -251,20 +260,11 @@ pc_status record_exec(Exec *e, cudaStream_t st, Plan *prof = nullptr) {
     }
     for (const PassLaunch &pl : e->passes[j]) {
       PC_TRY(launch_persistent_f32(e->dargs, e->ditems + pl.items_off, pl.nitems, pl.grid, kBatchThreads, pl.smem,
-                                   pl.stage, pl.emax, st));
+                                   pl.stage, pl.gate_bytes, pl.a0, pl.nargs, pl.gated, pl.emax, st));
       ++launches;
     }
     mark(3);
   }
-  bool any_final = false;
-  for (const Group &g : e->groups) {
-    if (!g.adaptive || g.sweeps <= 0) continue;   // the residual after the last allowed sweep
-    const int n = (int)g.members.size();
-    batch_launch(BATCH_RESIDUAL, 1, g.dP, segs(g, BATCH_RESIDUAL), n, g.total[BATCH_RESIDUAL], g.sweeps, st);
-    ++launches;
-    any_final = true;
-  }
-  if (any_final) mark(4);
   for (const Group &g : e->groups) {
     const int n = (int)g.members.size();
     if (g.any_singular) {

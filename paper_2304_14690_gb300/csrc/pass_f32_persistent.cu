@@ -5,8 +5,10 @@
 namespace pc {
 
 pc_status launch_persistent_f32(const PassArgs<float> *dargs, const int2 *ditems, int nitems, int grid, int threads,
-                                size_t smem, int stage_bytes, int emax, cudaStream_t st) {
-  return launch_persistent<float>(dargs, ditems, nitems, grid, threads, smem, stage_bytes, emax, st);
+                                size_t smem, int stage_bytes, int gate_bytes, int a0, int nargs, int gated, int emax,
+                                cudaStream_t st) {
+  return launch_persistent<float>(dargs, ditems, nitems, grid, threads, smem, stage_bytes, gate_bytes, a0, nargs, gated,
+                                  emax, st);
 }
 
 int persistent_f32_ctas_per_sm(int emax, int threads, size_t smem) {

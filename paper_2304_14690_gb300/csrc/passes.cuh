@@ -43,8 +43,7 @@ struct PassArgs {
   void *dst;
   Real out_scale;       // normalisation of the inverse (2/n)
   double *f64;          // nullable (pair modes): also store the pair's value in FP64
-  const unsigned *skip; // nullable: the pass does nothing when *skip is nonzero (a refinement
-                        // sweep after the device-side stopping rule ended the refinement)
+  RefineGate gate;      // a refinement sweep's pass: nothing to do once the stopping rule ended it
   unsigned *err;        // nullable: the problem's status word (DevStats::flags) for device errors
 };
 
@@ -57,14 +56,14 @@ struct PassSpec {
   int dst_mode;
   void *dst;
   double *f64;          // nullable (pair modes): also store the result in FP64
-  const unsigned *skip; // nullable: skip flag of PassArgs
+  RefineGate gate;      // stopping-rule gate of PassArgs
 };
 
 // The passes of one solve of plan p from src to dst, in launch order; f64 (nullable) goes to
 // the final pass.
 std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, const void *src,
                                        int dst_mode, void *dst, double *f64 = nullptr,
-                                       const unsigned *skip = nullptr);
+                                       RefineGate gate = RefineGate{nullptr, 0, 0.0f});
 // Fill the kernel arguments and launch shape of one pass (no launch). batch_threads > 0 sizes
 // the tile to fill a CTA of that many threads (batched launches); 0 sizes it so that the
 // problem alone fills the GPU.
@@ -82,9 +81,11 @@ pc_status prepare_pass_f32_family1(int lim);
 pc_status prepare_pass_f32_family2(int lim);
 // Persistent FP32 pass over a work list of (args index, tile) items of any family and length
 // (one launch per pass for a whole batch); grid: CTAs, at most the resident ones; stage_bytes:
-// shared memory for staging the next tile's input (0: no staging).
+// shared memory for staging the next tile's input (0: no staging); gated launches (refinement
+// sweeps under the stopping rule) cache the gates of their args[a0, a0 + nargs) in gate_bytes.
 pc_status launch_persistent_f32(const PassArgs<float> *dargs, const int2 *ditems, int nitems, int grid, int threads,
-                                size_t smem, int stage_bytes, int emax, cudaStream_t st);
+                                size_t smem, int stage_bytes, int gate_bytes, int a0, int nargs, int gated, int emax,
+                                cudaStream_t st);
 int persistent_f32_ctas_per_sm(int emax, int threads, size_t smem);
 pc_status prepare_persistent_f32(int lim);
 __host__ __device__ inline int pass_family(int kind) { return kind == KIND_PP ? 0 : ((kind == KIND_NN || kind == KIND_DD) ? 1 : 2); }

@@ -59,11 +59,61 @@ struct DevStats {
   double ib_prev;          //   and of |f_old|^2
   unsigned int flags;
   unsigned int pad;
-  // refinement stopping rule (MIXED with refine_tol > 0), written by the deciding residual
-  unsigned int refine_stop;  // nonzero: no further sweep (later sweeps' kernels exit at once)
-  int sweeps_done;           // sweeps run when the rule decided
-  int refine_conv;           // the rule was met (tolerance or rounding floor)
-  int pad2;
+  // stopping rule of the refinement (MIXED with refine_tol > 0): max norms of the residual after
+  // k sweeps and of the source, FP32, reduced with order-independent atomic maxima of their bits
+  float rmax[kMaxRefine + 1];
+  float smax;
+};
+
+// The refinement's stopping rule on the stored max norms: residual k (after k sweeps) ends the
+// refinement when ||r_k|| <= tol ||s||, or, from k = 2, when ||r_k|| > 16 (||r_1|| / ||r_0||)
+// ||r_{k-1}||: the residual no longer falls at the rate of a sweep, it has reached the rounding
+// floor of its own evaluation. FP32 operations in a fixed order (no fused multiply-add is
+// possible), so the device kernels and the host report take the same decision.
+__host__ __device__ inline bool refine_stop_at(const float *rmax, float smax, int k, float tol) {
+  const float rk = rmax[k];
+  if (rk <= tol * smax) return true;
+  if (k >= 2 && rmax[0] > 0.0f) {
+    const float rho = rmax[1] / rmax[0];
+    const float bound = (16.0f * rho) * rmax[k - 1];
+    if (rk > bound) return true;
+  }
+  return false;
+}
+#ifdef __CUDACC__
+// On the device: whether a residual before sweep j already ended the refinement (the kernels of
+// sweep j, its solve and its residual, then do nothing). Read past L1: written by earlier kernels.
+// The same operations as refine_stop_at applied to k = 0, 1, ..., j - 1. Every norm is loaded
+// up front (one round trip to L2, not one per residual), and the loops are unrolled over
+// constant indices so the values stay in registers (no local memory in the kernels calling it).
+__device__ __forceinline__ bool refine_stopped_before(const DevStats *st, int j, float tol) {
+  if (j <= 0) return false;
+  float r[kMaxRefine + 1];
+#pragma unroll
+  for (int k = 0; k <= kMaxRefine; ++k) r[k] = (k < j) ? __ldcg(&st->rmax[k]) : 0.0f;
+  const float bound_tol = tol * __ldcg(&st->smax);
+  bool stop = false;
+#pragma unroll
+  for (int k = 0; k <= kMaxRefine; ++k) {
+    if (k < j) {
+      if (r[k] <= bound_tol) stop = true;
+      if (k >= 2 && r[0] > 0.0f) {
+        const float rho = r[1] / r[0];
+        const float bound = (16.0f * rho) * r[k - 1];
+        if (r[k] > bound) stop = true;
+      }
+    }
+  }
+  return stop;
+}
+#endif
+
+// A pass or residual of refinement sweep j under the stopping rule: it does nothing once
+// refine_stopped_before(st, j, tol). st == nullptr: no rule.
+struct RefineGate {
+  const DevStats *st;
+  int j;
+  float tol;
 };
 
 // Per-call event record of the optional profiler: segment i (between events i and i+1) belongs
@@ -266,7 +316,7 @@ inline int grid_for(int64_t work, int threads) {
 // destination modes are those of passes.cuh (FP32 or FP64 source; FP64 set or accumulate).
 pc_status solve_fp64_grid(Plan *p, const double *s, double *pout, cudaStream_t st);
 pc_status solve_fp32_grid(Plan *p, int src_mode, const void *s, int dst_mode, void *dst,
-                          cudaStream_t st, double *f64 = nullptr, const unsigned *skip = nullptr);
+                          cudaStream_t st, double *f64 = nullptr, RefineGate gate = RefineGate{nullptr, 0, 0.0f});
 // Drops the plan's captured CUDA graphs and batch executables (after a schedule change).
 void plan_drop_graphs(Plan *p);
 // ----------------------------------------------------------------------------- batches
@@ -297,8 +347,8 @@ struct GridDev {
 struct BatchProblem {
   GridDev g;
   int dim, vdtype, N, ncells, K, Kg, singular, gmode;
-  int kmax;            // refinement sweeps at most; adaptive when tol2 > 0
-  double tol2;         // squared refinement tolerance (<= 0: fixed sweep count)
+  int kmax;            // refinement sweeps at most; under the stopping rule when tol > 0
+  float tol;           // the rule's tolerance (<= 0: a fixed sweep count)
   const void *u, *f;
   void *uo, *fo;
   double *p;

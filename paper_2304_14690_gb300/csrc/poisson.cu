@@ -184,7 +184,7 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   A.dst = dst;
   A.out_scale = (Real)inv_scale(ax.kind, ax.n);
   A.f64 = ps.f64;
-  A.skip = ps.skip;
+  A.gate = ps.gate;
   A.err = p->dstats ? &p->dstats->flags : nullptr;
   threads = L * tpl;
   if (threads > kMaxPassThreads || L * M > budget)
@@ -231,22 +231,22 @@ pc_status prepare_kernels() {
 }
 
 std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, const void *src,
-                                       int dst_mode, void *dst, double *f64, const unsigned *skip) {
+                                       int dst_mode, void *dst, double *f64, RefineGate gate) {
   std::vector<PassSpec> v;
   void *work = fp32 ? (void *)p->work32 : (void *)p->work64;
   const int d = p->dim;
   int cur_mode = src_mode;
   const void *cur = src;
   for (int a = d - 1; a >= 1; --a) {     // forward passes: last axis down to axis 1
-    v.push_back(PassSpec{a, true, false, false, cur_mode, cur, DST_WORK, work, nullptr, skip});
+    v.push_back(PassSpec{a, true, false, false, cur_mode, cur, DST_WORK, work, nullptr, gate});
     cur_mode = SRC_WORK;
     cur = work;
   }
-  v.push_back(PassSpec{0, true, true, true, cur_mode, cur, DST_WORK, work, nullptr, skip});   // axis 0, division
+  v.push_back(PassSpec{0, true, true, true, cur_mode, cur, DST_WORK, work, nullptr, gate});   // axis 0, division
   for (int a = 1; a < d; ++a) {         // inverse passes: axis 1 up to the last axis
     const bool final_pass = (a == d - 1);
     v.push_back(PassSpec{a, false, false, true, SRC_WORK, work, final_pass ? dst_mode : DST_WORK,
-                         final_pass ? dst : work, final_pass ? f64 : nullptr, skip});
+                         final_pass ? dst : work, final_pass ? f64 : nullptr, gate});
   }
   return v;
 }
@@ -254,9 +254,9 @@ std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, c
 // Full solve with Real precision: src (cells, src_mode) -> dst (dst_mode).
 template <typename Real>
 static pc_status solve_real(Plan *p, int src_mode, const void *src, int dst_mode, void *dst,
-                            cudaStream_t st, double *f64 = nullptr, const unsigned *skip = nullptr) {
+                            cudaStream_t st, double *f64 = nullptr, RefineGate gate = RefineGate{nullptr, 0, 0.0f}) {
   if (p->dim < 2) return fail(PC_ERR_UNSUPPORTED, "dim 1");
-  for (const PassSpec &ps : solve_pass_specs(p, sizeof(Real) == 4, src_mode, src, dst_mode, dst, f64, skip))
+  for (const PassSpec &ps : solve_pass_specs(p, sizeof(Real) == 4, src_mode, src, dst_mode, dst, f64, gate))
     PC_TRY(launch_pass<Real>(p, ps, st));
   return PC_OK;
 }
@@ -266,8 +266,8 @@ pc_status solve_fp64_grid(Plan *p, const double *s, double *pout, cudaStream_t s
 }
 
 pc_status solve_fp32_grid(Plan *p, int src_mode, const void *s, int dst_mode, void *dst,
-                          cudaStream_t st, double *f64, const unsigned *skip) {
-  return solve_real<float>(p, src_mode, s, dst_mode, dst, st, f64, skip);
+                          cudaStream_t st, double *f64, RefineGate gate) {
+  return solve_real<float>(p, src_mode, s, dst_mode, dst, st, f64, gate);
 }
 
 }  // namespace pc

@@ -482,44 +482,48 @@ __device__ __forceinline__ DF df_neg_(DF a) { return DF{-a.hi, -a.lo}; }
 // so its ~2^-44 relative rounding bounds the attainable accuracy far below the 1e-10 target.
 // SV, PV: storage of s and p, double or a float2 (hi, lo) pair (the refinement keeps both as
 // pairs; FP64 arrays come from pc_solve_poisson and from the statistics of FP64 plans).
-// Refinement step of a residual launch: k sweeps are done before it (res2 = &stats->res2[k]);
-// with decide set, the thread that completes ||r_k||^2 applies the stopping rule (at most kmax
-// sweeps, squared tolerance tol2); with skip set, the launch does nothing once the rule stopped.
+// Refinement step of a residual launch: k sweeps are done before it. With rule set (the
+// stopping rule is on), the launch does nothing once a residual before it ended the refinement
+// (refine_stopped_before), and otherwise records the max norm of r_k (and, for k = 0, of s) for
+// the rule; tol: the rule's tolerance.
 struct RefineStep {
-  int k, kmax, decide, skip;
-  double tol2;
+  int k, rule;
+  float tol;
 };
 
-// Refinement runs adaptively (MIXED with refine_tol > 0 and sweeps allowed): every residual
-// measures its norm and the deciding thread applies the stopping rule; later sweeps' kernels
-// exit at once, and every solve writes p in FP64 since any of them may be the last.
+// Refinement runs under the stopping rule (MIXED with refine_tol > 0 and sweeps allowed): every
+// residual records its max norm, the kernels of a sweep that the rule ended exit at once, and
+// every solve writes p in FP64 since any of them may be the last.
 static bool refine_adaptive(const Plan *p) {
   return p->precision == PC_PREC_MIXED && p->refine_tol > 0.0 && p->refine_iters > 0;
 }
 
-// The stopping rule after residual k: converged when ||r_k||^2 <= tol2 ||s||^2; at the rounding
-// floor of the residual's own evaluation when, from the second sweep on, ||r_k|| exceeds 16 times
-// the first sweep's contraction ||r_1|| / ||r_0|| applied to ||r_{k-1}|| (squared: 256); stop
-// after kmax sweeps either way. Later sweeps' kernels read refine_stop and exit.
-__device__ __forceinline__ void refine_decide(DevStats *st, const RefineStep &rs) {
-  const double r2 = st->res2[rs.k];
-  const bool conv = r2 <= rs.tol2 * st->sum_s2;
-  bool floor_hit = false;
-  if (rs.k >= 2 && st->res2[0] > 0.0) floor_hit = r2 > 256.0 * (st->res2[1] / st->res2[0]) * st->res2[rs.k - 1];
-  st->sweeps_done = rs.k;
-  st->refine_conv = (conv || floor_hit) ? 1 : 0;
-  if (conv || floor_hit || rs.k >= rs.kmax) st->refine_stop = 1u;
+// Block-wide maximum of non-negative v merged into *dst with one atomic maximum of its bits (the
+// order of the blocks does not matter, so the result is reproducible).
+__device__ __forceinline__ void block_max_bits(float v, float *dst) {
+  __shared__ float sh[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) atomicMax(reinterpret_cast<unsigned *>(dst), __float_as_uint(v));
+  }
 }
 
 template <int DIM, bool SINGULAR, bool WRITE_R, bool NORM, typename SV, typename PV>
 __device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, const SV *__restrict__ s,
                                               const PV *__restrict__ p, float *__restrict__ r,
                                               DevStats *stats, double *res2, double *partials,
-                                              unsigned int *counter, RefineStep rs = RefineStep{0, 0, 0, 0, 0.0}) {
-  if (rs.skip && __ldcg(&stats->refine_stop)) return;   // the refinement already stopped
+                                              unsigned int *counter, RefineStep rs = RefineStep{0, 0, 0.0f}) {
+  if (rs.rule && refine_stopped_before(stats, rs.k, rs.tol)) return;   // the refinement already ended
   int x, row0;
   tile_pos(g, b, x, row0);
   double nrm = 0.0;
+  float rmx = 0.0f, smx = 0.0f;
   if (x < g.n[DIM - 1]) {
     DF mean{0.0f, 0.0f};
     if (SINGULAR) mean = df_of(stats->mean_s);
@@ -545,18 +549,22 @@ __device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, cons
         acc = df_add(acc, df_mul(t, DF{g.ih2_hi[a], g.ih2_lo[a]}));
       }
       DF sc = to_df(s[c]);
+      if (rs.rule && rs.k == 0) smx = fmaxf(smx, fabsf(sc.hi));
       if (SINGULAR) sc = df_sub(sc, mean);
       const DF v = df_sub(sc, acc);
       if (WRITE_R) r[c] = v.hi;
+      if (rs.rule) rmx = fmaxf(rmx, fabsf(v.hi));
       if (NORM) {
         const double vd = f2d_bits(v.hi) + f2d_bits(v.lo);
         nrm = fma(vd, vd, nrm);
       }
     }
   }
-  if (NORM) {
-    if (grid_sum(nrm, partials, counter, res2, tile_block(g, b)) && rs.decide) refine_decide(stats, rs);
+  if (rs.rule) {
+    block_max_bits(rmx, &stats->rmax[rs.k]);
+    if (rs.k == 0) block_max_bits(smx, &stats->smax);
   }
+  if (NORM) grid_sum(nrm, partials, counter, res2, tile_block(g, b));
 }
 template <int DIM, bool SINGULAR, bool WRITE_R, bool NORM, typename SV, typename PV>
 __global__ void residual_kernel(GridDev g, const SV *__restrict__ s, const PV *__restrict__ p,
@@ -1060,41 +1068,29 @@ __global__ void batch_divergence(const BatchProblem *__restrict__ P, const int *
   if (q.g.dim == 2)
     divergence_body<2>(lb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, nullptr, reinterpret_cast<float2 *>(q.s64),
                        q.s32, q.ds, q.partials, q.counters,
-                       q.tol2 > 0.0 ? 2 : q.singular, q.inv_ncells);
+                       q.singular, q.inv_ncells);
   else
     divergence_body<3>(lb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, nullptr, reinterpret_cast<float2 *>(q.s64),
                        q.s32, q.ds, q.partials, q.counters,
-                       q.tol2 > 0.0 ? 2 : q.singular, q.inv_ncells);
+                       q.singular, q.inv_ncells);
 }
 
-// Residual k of every problem (k sweeps done). Problems with an adaptive refinement (tol2 > 0)
-// measure ||r_k|| and apply the stopping rule, and skip the launch once it stopped; FINAL: the
-// residual after the last allowed sweep (adaptive problems only, the rule's last decision).
-template <bool FINAL>
+// Residual k of every problem (k sweeps done). Problems under the stopping rule (tol > 0)
+// record the max norm of r_k and skip the launch once the rule ended their refinement.
 __global__ void batch_residual(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count, int k) {
   pdl_enter();
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
   const unsigned lb = blockIdx.x - seg[pi];
   const float2 *s2 = reinterpret_cast<const float2 *>(q.s64);
-  const bool ad = q.tol2 > 0.0;
-  if (FINAL && !ad) return;
-  const RefineStep rs{k, q.kmax, ad ? 1 : 0, ad ? 1 : 0, q.tol2};
-  double *res2 = &q.ds->res2[k];
-#define PC_BRES(D, S)                                                                                            \
-  do {                                                                                                           \
-    if (FINAL) residual_body<D, S, false, true>(lb, q.g, s2, q.p2, q.r32, q.ds, res2, q.partials, q.counters, rs); \
-    else if (ad) residual_body<D, S, true, true>(lb, q.g, s2, q.p2, q.r32, q.ds, res2, q.partials, q.counters, rs); \
-    else residual_body<D, S, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters);      \
-  } while (0)
+  const RefineStep rs{k, q.tol > 0.0f ? 1 : 0, q.tol};
   if (q.g.dim == 2) {
-    if (q.singular) PC_BRES(2, true);
-    else PC_BRES(2, false);
+    if (q.singular) residual_body<2, true, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
+    else residual_body<2, false, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
   } else {
-    if (q.singular) PC_BRES(3, true);
-    else PC_BRES(3, false);
+    if (q.singular) residual_body<3, true, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
+    else residual_body<3, false, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
   }
-#undef PC_BRES
 }
 
 __global__ void batch_gauge_sum(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
@@ -1139,10 +1135,7 @@ void batch_launch(int stage, int variant, const BatchProblem *P, const int *seg,
       else launch_pdl(batch_transfer<0>, total_blocks, T, 0, st, P, seg, count, extra);
       break;
     case BATCH_DIVERGENCE: launch_pdl(batch_divergence, total_blocks, T, 0, st, P, seg, count); break;
-    case BATCH_RESIDUAL:
-      if (variant) launch_pdl(batch_residual<true>, total_blocks, T, 0, st, P, seg, count, extra);
-      else launch_pdl(batch_residual<false>, total_blocks, T, 0, st, P, seg, count, extra);
-      break;
+    case BATCH_RESIDUAL: launch_pdl(batch_residual, total_blocks, T, 0, st, P, seg, count, extra); break;
     case BATCH_GAUGE_SUM: launch_pdl(batch_gauge_sum, total_blocks, T, 0, st, P, seg, count); break;
     case BATCH_FINALIZE: launch_pdl(batch_finalize, total_blocks, T, 0, st, P, seg, count); break;
     case BATCH_GRADIENT:
@@ -1175,7 +1168,7 @@ void batch_problem_fill(const Plan *p, const pc_project_args &a, BatchProblem &q
   q.singular = p->singular;
   q.gmode = p->singular ? (p->gauge == 1 ? 2 : 1) : 0;
   q.kmax = p->precision == PC_PREC_MIXED ? p->refine_iters : 0;
-  q.tol2 = refine_adaptive(p) ? p->refine_tol * p->refine_tol : 0.0;
+  q.tol = refine_adaptive(p) ? (float)p->refine_tol : 0.0f;
   q.u = a.u_star; q.f = a.f_ib_in; q.uo = a.u_out; q.fo = a.f_ib_out; q.p = a.p_out;
   q.dt = a.dt; q.inv_dt = 1.0 / a.dt; q.beta = p->beta; q.inv_bdt = 1.0 / (p->beta * a.dt);
   q.inv_ncells = 1.0 / (double)p->ncells;
@@ -1260,7 +1253,7 @@ static bool is_device_ptr(const void *ptr) {
 template <typename SV, typename PV>
 static void launch_residual(bool singular, bool write_r, bool norm, cudaStream_t st, const GridDev &g,
                             const SV *s, const PV *p, float *r, DevStats *ds, double *res2, double *partials,
-                            unsigned int *counters, RefineStep rs = RefineStep{0, 0, 0, 0, 0.0}) {
+                            unsigned int *counters, RefineStep rs = RefineStep{0, 0, 0.0f}) {
 #define PC_RES(S, W, N)                                                                                       \
   do {                                                                                                        \
     if (g.dim == 2)                                                                                           \
@@ -1303,10 +1296,12 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
   } else {
     const int sweeps = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
     const bool adaptive = refine_adaptive(p);
-    const unsigned *skip = adaptive ? &p->dstats->refine_stop : nullptr;
-    const double tol2 = adaptive ? p->refine_tol * p->refine_tol : 0.0;
-    auto step = [&](int k, bool decide) { return RefineStep{k, sweeps, decide ? 1 : 0, adaptive ? 1 : 0, tol2}; };
-    const bool norm = want_final_residual || adaptive;
+    const float tol = adaptive ? (float)p->refine_tol : 0.0f;
+    // residual k (after k sweeps) and the solve of sweep j run only while the rule has not
+    // ended the refinement at an earlier residual
+    auto step = [&](int k) { return RefineStep{k, adaptive ? 1 : 0, tol}; };
+    auto gate = [&](int j) { return adaptive ? RefineGate{p->dstats, j, tol} : RefineGate{nullptr, 0, 0.0f}; };
+    const bool norm = want_final_residual;
     double *first_out = (sweeps == 0 || adaptive) ? pout : nullptr;
     if (s32) PC_TRY(solve_fp32_grid(p, SRC_F32_, s32, DST_PAIR_SET_, p->p2, st, first_out));
     else PC_TRY(solve_fp32_grid(p, SRC_F64_, s64, DST_PAIR_SET_, p->p2, st, first_out));
@@ -1315,26 +1310,26 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
       float *r32 = reinterpret_cast<float *>(p->work64);   // work64 is free in mixed mode
       if (s2)
         launch_residual(p->singular, true, norm, st, g, s2, (const float2 *)p->p2, r32, p->dstats,
-                        &p->dstats->res2[it], p->partials, p->counters, step(it, adaptive));
+                        &p->dstats->res2[it], p->partials, p->counters, step(it));
       else
         launch_residual(p->singular, true, norm, st, g, s64, (const float2 *)p->p2, r32, p->dstats,
-                        &p->dstats->res2[it], p->partials, p->counters, step(it, adaptive));
+                        &p->dstats->res2[it], p->partials, p->counters, step(it));
       count_launch(p);
       prof_mark(p, st, 4);
       PC_TRY(solve_fp32_grid(p, SRC_F32_, r32, DST_PAIR_ADD_, p->p2, st,
-                             (adaptive || it == sweeps - 1) ? pout : nullptr, skip));
+                             (adaptive || it == sweeps - 1) ? pout : nullptr, gate(it + 1)));
       prof_mark(p, st, 3);
     }
-    // the residual after the last sweep: the rule's last decision, and the statistics
-    if (sweeps > 0 && norm) {
+    // the residual after the last allowed sweep (statistics, and the rule's verdict on them)
+    if (sweeps > 0 && want_final_residual) {
       if (s2)
         launch_residual(p->singular, false, true, st, g, s2, (const float2 *)p->p2, (float *)nullptr, p->dstats,
-                        &p->dstats->res2[sweeps], p->partials, p->counters, step(sweeps, adaptive));
+                        &p->dstats->res2[sweeps], p->partials, p->counters, step(sweeps));
       else
         launch_residual(p->singular, false, true, st, g, s64, (const float2 *)p->p2, (float *)nullptr, p->dstats,
-                        &p->dstats->res2[sweeps], p->partials, p->counters, step(sweeps, adaptive));
+                        &p->dstats->res2[sweeps], p->partials, p->counters, step(sweeps));
       count_launch(p);
-      prof_mark(p, st, adaptive ? 4 : 7);
+      prof_mark(p, st, 7);
     }
   }
   // the residual of an FP64 or unrefined FP32 solve (statistics; the residual of L_h: FD solves only)
@@ -1381,10 +1376,19 @@ static pc_status fill_stats(Plan *p, pc_stats *stats, cudaStream_t st) {
   stats->source_norm = std::sqrt(fmax(ds.sum_s2, 0.0));
   const bool adaptive = refine_adaptive(p);
   int its = (p->precision == PC_PREC_MIXED) ? p->refine_iters : 0;
-  if (adaptive) its = ds.sweeps_done;
+  bool conv = true;
+  if (adaptive) {   // the device's decisions, replayed on the stored max norms
+    conv = false;
+    for (int k = 0; k <= its; ++k)
+      if (refine_stop_at(ds.rmax, ds.smax, k, (float)p->refine_tol)) {
+        its = k;
+        conv = true;
+        break;
+      }
+  }
   for (int i = 0; i <= its && i < 9; ++i) stats->residual_norm[i] = std::sqrt(fmax(ds.res2[i], 0.0));
   stats->refine_iters_done = its;
-  stats->refine_converged = adaptive ? ds.refine_conv : 1;
+  stats->refine_converged = conv ? 1 : 0;
   stats->max_div_after = ds.max_div;
   stats->max_abs_u_star = ds.max_u;
   const int gmode = gauge_mode(p);
@@ -1392,9 +1396,9 @@ static pc_status fill_stats(Plan *p, pc_stats *stats, cudaStream_t st) {
   // a NaN or infinity anywhere in u~ reaches the source sums (the maxima above skip NaN)
   if (!std::isfinite(ds.sum_s) || !std::isfinite(ds.sum_s2))
     return fail(PC_ERR_INVALID_ARG, "non-finite source: u_star, f_ib_in or dt hold a NaN or infinity");
-  if (adaptive && !ds.refine_conv)
-    return fail(PC_ERR_NOT_CONVERGED, "refinement: ||r||/||s|| = %.3g after %d sweeps (tolerance %.3g)",
-                std::sqrt(fmax(ds.res2[its], 0.0)) / fmax(stats->source_norm, 1e-300), its, p->refine_tol);
+  if (!conv)
+    return fail(PC_ERR_NOT_CONVERGED, "refinement: max |r| / max |s| = %.3g after %d sweeps (tolerance %.3g)",
+                (double)ds.rmax[its] / fmax((double)ds.smax, 1e-300), its, p->refine_tol);
   return PC_OK;
 }
 
@@ -1469,7 +1473,7 @@ static pc_status vertex_pass_solve(Plan *p, cudaStream_t st, double inv_bdt, dou
   count_launch(p);
   // the source sums: the mean the residual removes (zero-mode problems; an odd extension has
   // mean zero) and the statistics
-  if (want_stats || p->problem_singular || refine_adaptive(p)) {
+  if (want_stats || p->problem_singular) {
     launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, (const double *)p->s64, p->dstats,
                p->partials, p->counters);
     count_launch(p);
@@ -1521,7 +1525,7 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   if (p->vertex) {
     PC_TRY(vertex_pass_solve(p, st, 1.0 / (p->beta * dt), dp, stats != nullptr));
   } else if (p->divmode == PC_DIV_WLS_DIRECT) {
-    launch_direct_div(p, st, 1.0 / (p->beta * dt), (stats || refine_adaptive(p)) ? 2 : (p->singular ? 1 : 0));
+    launch_direct_div(p, st, 1.0 / (p->beta * dt), stats ? 2 : (p->singular ? 1 : 0));
     count_launch(p);
     prof_mark(p, st, 2);
   }
@@ -1546,7 +1550,7 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
     launch_pdl(divk, g.nblk, 256, 0, st, g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt),
                mixed ? nullptr : p->s64, mixed ? reinterpret_cast<float2 *>(p->s64) : nullptr,
                mixed ? reinterpret_cast<float *>(p->work64) : nullptr, p->dstats, p->partials, p->counters,
-               (stats || refine_adaptive(p)) ? 2 : (p->singular ? 1 : 0), 1.0 / (double)nc);
+               stats ? 2 : (p->singular ? 1 : 0), 1.0 / (double)nc);
     count_launch(p);
     prof_mark(p, st, 2);
   }
