@@ -4,9 +4,9 @@
 // settings) among plans in mixed or FP32 precision. For each group every per-cell and per-node
 // stage of the pipeline (prep, transfer per axis, divergence, residuals, gauge, split, gradient)
 // is ONE kernel launch over all problems of the group: a segment table maps each block to its
-// problem and problem-local block. Each transform pass is ONE persistent launch over the
-// problems of every group, 2D and 3D, all transform families and line lengths together: its
-// CTAs walk a work list of (pass arguments, tile) items. The whole sequence is captured once per
+// problem and problem-local block. Each transform pass is ONE launch over the problems of every
+// group, 2D and 3D, all transform families and line lengths together: each CTA takes one item
+// of a work list of (pass arguments, tile) items. The whole sequence is captured once per
 // batch composition into a CUDA graph and replayed. Each problem keeps the block decomposition
 // of its single-problem launches and each line is transformed as in a single call, so batch
 // results are bitwise those of separate pc_project calls. Plans in FP64 precision, and plans
@@ -24,19 +24,15 @@ namespace pc {
 namespace {
 
 constexpr int kBatchThreads = 256;   // CTA size of the batched transform passes
+constexpr int kBatchChunk = 4;       // tiles of one problem per CTA of a batched pass
 
-// One persistent launch of a batched transform pass: its items in the work list, over every
-// problem of the batch that has this pass (any family, line length and dimension).
+// One launch of a batched transform pass: its items in the work list, over every problem of the
+// batch that has this pass (any family, line length and dimension).
 struct PassLaunch {
   int items_off = 0;
   int nitems = 0;
   int emax = 1;          // largest slots per thread among the items' passes (kernel instance)
-  int grid = 1;          // CTAs: the resident ones, or fewer items
-  size_t smem = 0;       // the pass body's shared memory
-  int stage = 0;         // bytes of the tile staging buffer (the largest tile's input)
-  int a0 = 0, nargs = 0; // the launch's pass arguments: args[a0, a0 + nargs)
-  int gated = 0;         // a refinement sweep under the stopping rule: items check their gate
-  int gate_bytes = 0;    // shared-memory gate table (one byte per pass argument, capped)
+  size_t smem = 0;       // the pass body's shared memory (the largest item's)
 };
 
 // Problems that share the templated per-stage kernels (dimension, velocity type, neighbour
@@ -66,7 +62,7 @@ struct Exec {
   std::vector<Group> groups;
   std::vector<int> singles;             // problems run through pc_project
   PassArgs<float> *dargs = nullptr;     // transform passes of every problem and solve
-  int2 *ditems = nullptr;               // work list: (args index, tile)
+  int4 *ditems = nullptr;               // work list: (args index, first tile, tiles, 0)
   std::vector<std::vector<PassLaunch>> passes;   // [solve][pass]
   cudaStream_t cap = nullptr;
   cudaGraph_t graph = nullptr;
@@ -145,18 +141,13 @@ pc_status build_group(Exec *e, Group &g) {
 }
 
 // The transform passes of every problem of every group: pass k of solve j of all problems that
-// have it is one persistent launch, its items sorted by transform family, power-of-two length
+// have it is one launch, its items sorted by transform family, power-of-two length
 // and line length so the CTAs resident together run the same code.
 pc_status build_passes(Exec *e) {
-  int nsm = 152;
-  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, e->device) != cudaSuccess) {
-    cudaGetLastError();
-    nsm = 152;
-  }
   int jmax = -1;
   for (const Group &g : e->groups) jmax = std::max(jmax, g.sweeps);
   std::vector<PassArgs<float>> args;
-  std::vector<int2> items;
+  std::vector<int4> items;
   for (int j = 0; j <= jmax; ++j) {
     // pass specs of solve j of every problem that runs it
     std::vector<std::pair<const Plan *, std::vector<PassSpec>>> specs;
@@ -183,7 +174,6 @@ pc_status build_passes(Exec *e) {
       std::vector<Entry> list;
       PassLaunch pl;
       pl.items_off = (int)items.size();
-      pl.a0 = (int)args.size();
       for (const auto &ps : specs) {
         if (k >= ps.second.size()) continue;
         PassArgs<float> A;
@@ -197,20 +187,15 @@ pc_status build_passes(Exec *e) {
         args.push_back(A);
         pl.smem = std::max(pl.smem, smem);
         pl.emax = std::max(pl.emax, A.emax);
-        pl.stage = std::max(pl.stage, (A.L * A.n * (int)sizeof(float) + 127) & ~127);
-        if (A.gate.st) pl.gated = 1;
+
       }
       if (list.empty()) continue;
-      pl.nargs = (int)args.size() - pl.a0;
-      pl.gate_bytes = pl.gated ? (std::min(pl.nargs, 16384) + 127) & ~127 : 0;
       std::stable_sort(list.begin(), list.end(), [](const Entry &a, const Entry &b) { return a.key < b.key; });
+      // consecutive tiles of a problem, kBatchChunk per CTA
       for (const Entry &en : list)
-        for (long long t = 0; t < en.tiles; ++t) items.push_back(make_int2(en.ai, (int)t));
+        for (long long t = 0; t < en.tiles; t += kBatchChunk)
+          items.push_back(make_int4(en.ai, (int)t, (int)std::min<long long>(kBatchChunk, en.tiles - t), 0));
       pl.nitems = (int)items.size() - pl.items_off;
-      pl.smem = (pl.smem + 127) & ~(size_t)127;
-      const long long resident =
-          (long long)persistent_f32_ctas_per_sm(pl.emax, kBatchThreads, pl.smem + pl.stage + pl.gate_bytes) * nsm;
-      pl.grid = (int)std::min<long long>(pl.nitems, resident);
       launches.push_back(pl);
     }
     e->passes.push_back(launches);
@@ -220,7 +205,7 @@ pc_status build_passes(Exec *e) {
   return PC_OK;
 }
 
-// The whole batch on one stream: the per-group stages, and one persistent launch per transform
+// The whole batch on one stream: the per-group stages, and one launch per transform
 // pass for every group. prof (nullable): a plan whose profiler records the phase boundaries
 // (direct launches only, not under capture), with the phase tags of pc_profile_read.
 pc_status record_exec(Exec *e, cudaStream_t st, Plan *prof = nullptr) {
@@ -259,8 +244,7 @@ pc_status record_exec(Exec *e, cudaStream_t st, Plan *prof = nullptr) {
       mark(4);
     }
     for (const PassLaunch &pl : e->passes[j]) {
-      PC_TRY(launch_persistent_f32(e->dargs, e->ditems + pl.items_off, pl.nitems, pl.grid, kBatchThreads, pl.smem,
-                                   pl.stage, pl.gate_bytes, pl.a0, pl.nargs, pl.gated, pl.emax, st));
+      PC_TRY(launch_batched_f32(e->dargs, e->ditems + pl.items_off, pl.nitems, kBatchThreads, pl.smem, pl.emax, st));
       ++launches;
     }
     mark(3);

@@ -12,7 +12,7 @@ enum SrcMode { SRC_F32 = 0, SRC_F64 = 1, SRC_WORK = 2 };
 
 constexpr int kMaxPassThreads = 512;   // CTA size limit of the transform passes
 constexpr int kBatchPassEmax = 16;     // largest slots per thread of a batched pass kernel
-constexpr int kPersistentThreads = 256; // CTA size of the persistent batched pass (3 resident per SM)
+constexpr int kBatchedThreads = 256;    // CTA size of the batched pass (4 resident per SM)
 // DST_PAIR_*: the refinement iterate of the FP32 solves, kept as FP32 (hi, lo) pairs
 // (double-float): SET stores the pass result, ADD adds it to the stored pair.
 enum DstMode { DST_WORK = 0, DST_F64_SET = 1, DST_F64_ADD = 2, DST_PAIR_SET = 3, DST_PAIR_ADD = 4 };
@@ -44,7 +44,6 @@ struct PassArgs {
   Real out_scale;       // normalisation of the inverse (2/n)
   double *f64;          // nullable (pair modes): also store the pair's value in FP64
   RefineGate gate;      // a refinement sweep's pass: nothing to do once the stopping rule ended it
-  unsigned *err;        // nullable: the problem's status word (DevStats::flags) for device errors
 };
 
 // One pass of a solve: axis, phases, source and destination.
@@ -79,15 +78,11 @@ pc_status launch_pass_f32_family2(const PassArgs<float> &A, long long tiles, int
 pc_status prepare_pass_f32_family0(int lim);
 pc_status prepare_pass_f32_family1(int lim);
 pc_status prepare_pass_f32_family2(int lim);
-// Persistent FP32 pass over a work list of (args index, tile) items of any family and length
-// (one launch per pass for a whole batch); grid: CTAs, at most the resident ones; stage_bytes:
-// shared memory for staging the next tile's input (0: no staging); gated launches (refinement
-// sweeps under the stopping rule) cache the gates of their args[a0, a0 + nargs) in gate_bytes.
-pc_status launch_persistent_f32(const PassArgs<float> *dargs, const int2 *ditems, int nitems, int grid, int threads,
-                                size_t smem, int stage_bytes, int gate_bytes, int a0, int nargs, int gated, int emax,
-                                cudaStream_t st);
-int persistent_f32_ctas_per_sm(int emax, int threads, size_t smem);
-pc_status prepare_persistent_f32(int lim);
+// Batched FP32 pass over a work list of (args index, first tile, tiles) items of any family,
+// length and dimension (one launch per pass for a whole batch, one CTA per item).
+pc_status launch_batched_f32(const PassArgs<float> *dargs, const int4 *ditems, int nitems, int threads, size_t smem,
+                             int emax, cudaStream_t st);
+pc_status prepare_batched_f32(int lim);
 __host__ __device__ inline int pass_family(int kind) { return kind == KIND_PP ? 0 : ((kind == KIND_NN || kind == KIND_DD) ? 1 : 2); }
 
 }  // namespace pc

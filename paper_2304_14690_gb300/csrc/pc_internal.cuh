@@ -20,7 +20,7 @@ constexpr long long kMaxRows = (1LL << 31) - (1LL << 16);
 constexpr int kMaxRefine = 8;
 
 // Device-side status word values (written by kernels, read at the next sync point).
-enum DeviceFlag { FLAG_WLS_SINGULAR = 1, FLAG_KNN_SHORT = 2, FLAG_NONFINITE = 4, FLAG_TIMEOUT = 8 };
+enum DeviceFlag { FLAG_WLS_SINGULAR = 1, FLAG_KNN_SHORT = 2, FLAG_NONFINITE = 4 };
 
 struct AxisInfo {
   int kind = 0;

@@ -185,7 +185,6 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   A.out_scale = (Real)inv_scale(ax.kind, ax.n);
   A.f64 = ps.f64;
   A.gate = ps.gate;
-  A.err = p->dstats ? &p->dstats->flags : nullptr;
   threads = L * tpl;
   if (threads > kMaxPassThreads || L * M > budget)
     return fail(PC_ERR_UNSUPPORTED, "axis %d: tile of %d x %d too large", axis, L, M);
@@ -225,7 +224,7 @@ pc_status prepare_kernels() {
   PC_TRY(prepare_pass_f32_family0(lim));
   PC_TRY(prepare_pass_f32_family1(lim));
   PC_TRY(prepare_pass_f32_family2(lim));
-  PC_TRY(prepare_persistent_f32(lim));
+  PC_TRY(prepare_batched_f32(lim));
   PC_TRY((prepare_axis_pass_spec<double, -1, false>(lim)));
   return PC_OK;
 }

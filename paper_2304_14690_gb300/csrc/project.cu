@@ -484,8 +484,8 @@ __device__ __forceinline__ DF df_neg_(DF a) { return DF{-a.hi, -a.lo}; }
 // pairs; FP64 arrays come from pc_solve_poisson and from the statistics of FP64 plans).
 // Refinement step of a residual launch: k sweeps are done before it. With rule set (the
 // stopping rule is on), the launch does nothing once a residual before it ended the refinement
-// (refine_stopped_before), and otherwise records the max norm of r_k (and, for k = 0, of s) for
-// the rule; tol: the rule's tolerance.
+// (refine_stopped_before; rule 2: the caller already checked), and otherwise records the max norm
+// of r_k (and, for k = 0, of s) for the rule; tol: the rule's tolerance.
 struct RefineStep {
   int k, rule;
   float tol;
@@ -519,7 +519,7 @@ __device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, cons
                                               const PV *__restrict__ p, float *__restrict__ r,
                                               DevStats *stats, double *res2, double *partials,
                                               unsigned int *counter, RefineStep rs = RefineStep{0, 0, 0.0f}) {
-  if (rs.rule && refine_stopped_before(stats, rs.k, rs.tol)) return;   // the refinement already ended
+  if (rs.rule == 1 && refine_stopped_before(stats, rs.k, rs.tol)) return;   // the refinement already ended
   int x, row0;
   tile_pos(g, b, x, row0);
   double nrm = 0.0;
@@ -1076,20 +1076,29 @@ __global__ void batch_divergence(const BatchProblem *__restrict__ P, const int *
 }
 
 // Residual k of every problem (k sweeps done). Problems under the stopping rule (tol > 0)
-// record the max norm of r_k and skip the launch once the rule ended their refinement.
+// record the max norm of r_k and skip the launch once the rule ended their refinement. A CTA
+// evaluates kResidualChunk consecutive blocks of its problem's single-call decomposition (the
+// residual per cell and its max norm do not depend on how blocks are grouped), so a skipped
+// launch costs a quarter of the CTAs.
+constexpr int kResidualChunk = 4;
 __global__ void batch_residual(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count, int k) {
   pdl_enter();
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
-  const unsigned lb = blockIdx.x - seg[pi];
   const float2 *s2 = reinterpret_cast<const float2 *>(q.s64);
-  const RefineStep rs{k, q.tol > 0.0f ? 1 : 0, q.tol};
-  if (q.g.dim == 2) {
-    if (q.singular) residual_body<2, true, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
-    else residual_body<2, false, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
-  } else {
-    if (q.singular) residual_body<3, true, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
-    else residual_body<3, false, true, false>(lb, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
+  const bool rule = q.tol > 0.0f;
+  if (rule && refine_stopped_before(q.ds, k, q.tol)) return;
+  const RefineStep rs{k, rule ? 2 : 0, q.tol};
+  const int b0 = (int)(blockIdx.x - seg[pi]) * kResidualChunk;
+  const int b1 = min(b0 + kResidualChunk, q.g.nblk);
+  for (int b = b0; b < b1; ++b) {
+    if (q.g.dim == 2) {
+      if (q.singular) residual_body<2, true, true, false>(b, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
+      else residual_body<2, false, true, false>(b, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
+    } else {
+      if (q.singular) residual_body<3, true, true, false>(b, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
+      else residual_body<3, false, true, false>(b, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
+    }
   }
 }
 
@@ -1155,7 +1164,7 @@ void batch_block_counts(const Plan *p, int *nb) {
   nb[BATCH_PREP] = grid_for((long long)p->dim * N, kFlatPerBlock);
   for (int a = 0; a < 3; ++a) nb[BATCH_TRANSFER + a] = a < p->dim ? grid_for(p->nface_total[a], 256) : 0;
   nb[BATCH_DIVERGENCE] = g.nblk;
-  nb[BATCH_RESIDUAL] = g.nblk;
+  nb[BATCH_RESIDUAL] = (g.nblk + kResidualChunk - 1) / kResidualChunk;
   nb[BATCH_GAUGE_SUM] = p->singular ? grid_for(nc, kFlatPerBlock) : 0;
   nb[BATCH_FINALIZE] = p->singular ? grid_for(nc, kFlatPerBlock) : 0;   // else split by the last pass
   nb[BATCH_GRADIENT] = grid_for(N, 256);
