@@ -208,12 +208,17 @@ __device__ __forceinline__ void axis_pass_body(const PassArgs<Real> &A, const in
   }
 }
 
+// Single-problem pass: CTA b transforms tiles b * A.chunk, ... (A.chunk consecutive tiles).
 template <typename Real, int EMAX, int KC, bool POW2>
 __global__ void __launch_bounds__(kMaxPassThreads) axis_pass(PassArgs<Real> A) {
   pdl_enter();
   if (A.gate.st && refine_stopped_before(A.gate.st, A.gate.j, A.gate.tol)) return;   // refinement already ended
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  axis_pass_body<Real, EMAX, KC, POW2>(A, blockIdx.x, smem_raw);
+  const int t0 = blockIdx.x * A.chunk, t1 = min(t0 + A.chunk, A.ntiles);
+  for (int t = t0; t < t1; ++t) {
+    if (t > t0) __syncthreads();   // the previous tile no longer reads the buffers
+    axis_pass_body<Real, EMAX, KC, POW2>(A, t, smem_raw);
+  }
 }
 
 // Batched pass: one launch covers every problem of a batch whatever its transform family, line
@@ -237,6 +242,8 @@ __global__ void __launch_bounds__(kBatchedThreads, EMAX <= 4 ? 4 : (EMAX == 8 ? 
     for (int w = threadIdx.x; w < (int)(sizeof(PassArgs<Real>) / 4); w += blockDim.x) dst[w] = __ldg(src + w);
   }
   __syncthreads();
+  // the gate is checked before the tile loads here (inside the body it would cost this kernel
+  // spills: six bodies share its register budget)
   if (A.gate.st && refine_stopped_before(A.gate.st, A.gate.j, A.gate.tol)) return;
   const int cls = pass_family(A.kind) * 2 + (((A.M & (A.M - 1)) == 0) ? 1 : 0);
   for (int t = it.y; t < it.y + it.z; ++t) {

@@ -44,6 +44,8 @@ struct PassArgs {
   Real out_scale;       // normalisation of the inverse (2/n)
   double *f64;          // nullable (pair modes): also store the pair's value in FP64
   RefineGate gate;      // a refinement sweep's pass: nothing to do once the stopping rule ended it
+  int chunk;            // single-problem launches: consecutive tiles per CTA (>= 1)
+  int ntiles;           // tiles of the pass
 };
 
 // One pass of a solve: axis, phases, source and destination.
@@ -56,13 +58,14 @@ struct PassSpec {
   void *dst;
   double *f64;          // nullable (pair modes): also store the result in FP64
   RefineGate gate;      // stopping-rule gate of PassArgs
+  int chunk;            // tiles per CTA of a single-problem launch (0 or 1: one)
 };
 
 // The passes of one solve of plan p from src to dst, in launch order; f64 (nullable) goes to
 // the final pass.
 std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, const void *src,
                                        int dst_mode, void *dst, double *f64 = nullptr,
-                                       RefineGate gate = RefineGate{nullptr, 0, 0.0f});
+                                       RefineGate gate = RefineGate{nullptr, 0, 0.0f}, int chunk = 1);
 // Fill the kernel arguments and launch shape of one pass (no launch). batch_threads > 0 sizes
 // the tile to fill a CTA of that many threads (batched launches); 0 sizes it so that the
 // problem alone fills the GPU.

@@ -315,8 +315,11 @@ inline int grid_for(int64_t work, int threads) {
 // Transform solves of a grid (poisson.cu): FP64 s -> p, and one FP32 solve whose source and
 // destination modes are those of passes.cuh (FP32 or FP64 source; FP64 set or accumulate).
 pc_status solve_fp64_grid(Plan *p, const double *s, double *pout, cudaStream_t st);
+// chunk: consecutive tiles per CTA (refinement sweeps that the stopping rule usually ends before
+// they start are launched with few CTAs, so a skipped sweep costs little)
 pc_status solve_fp32_grid(Plan *p, int src_mode, const void *s, int dst_mode, void *dst,
-                          cudaStream_t st, double *f64 = nullptr, RefineGate gate = RefineGate{nullptr, 0, 0.0f});
+                          cudaStream_t st, double *f64 = nullptr, RefineGate gate = RefineGate{nullptr, 0, 0.0f},
+                          int chunk = 1);
 // Drops the plan's captured CUDA graphs and batch executables (after a schedule change).
 void plan_drop_graphs(Plan *p);
 // ----------------------------------------------------------------------------- batches

@@ -185,7 +185,9 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   A.out_scale = (Real)inv_scale(ax.kind, ax.n);
   A.f64 = ps.f64;
   A.gate = ps.gate;
+  A.chunk = ps.chunk > 1 ? ps.chunk : 1;
   threads = L * tpl;
+  A.ntiles = (int)tiles;
   if (threads > kMaxPassThreads || L * M > budget)
     return fail(PC_ERR_UNSUPPORTED, "axis %d: tile of %d x %d too large", axis, L, M);
   if (batch_threads > 0 && emax > kBatchPassEmax)
@@ -204,6 +206,7 @@ static pc_status launch_pass(Plan *p, const PassSpec &ps, cudaStream_t st) {
   int threads;
   size_t smem;
   PC_TRY(build_pass<Real>(p, ps, A, tiles, threads, smem, 0));
+  tiles = (tiles + A.chunk - 1) / A.chunk;   // CTAs
   if constexpr (sizeof(Real) == 4) {
     // FP32 passes: the instance of the axis's transform family (one translation unit each)
     switch (pass_family(A.kind)) {
@@ -230,22 +233,22 @@ pc_status prepare_kernels() {
 }
 
 std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, const void *src,
-                                       int dst_mode, void *dst, double *f64, RefineGate gate) {
+                                       int dst_mode, void *dst, double *f64, RefineGate gate, int chunk) {
   std::vector<PassSpec> v;
   void *work = fp32 ? (void *)p->work32 : (void *)p->work64;
   const int d = p->dim;
   int cur_mode = src_mode;
   const void *cur = src;
   for (int a = d - 1; a >= 1; --a) {     // forward passes: last axis down to axis 1
-    v.push_back(PassSpec{a, true, false, false, cur_mode, cur, DST_WORK, work, nullptr, gate});
+    v.push_back(PassSpec{a, true, false, false, cur_mode, cur, DST_WORK, work, nullptr, gate, chunk});
     cur_mode = SRC_WORK;
     cur = work;
   }
-  v.push_back(PassSpec{0, true, true, true, cur_mode, cur, DST_WORK, work, nullptr, gate});   // axis 0, division
+  v.push_back(PassSpec{0, true, true, true, cur_mode, cur, DST_WORK, work, nullptr, gate, chunk});   // axis 0, division
   for (int a = 1; a < d; ++a) {         // inverse passes: axis 1 up to the last axis
     const bool final_pass = (a == d - 1);
     v.push_back(PassSpec{a, false, false, true, SRC_WORK, work, final_pass ? dst_mode : DST_WORK,
-                         final_pass ? dst : work, final_pass ? f64 : nullptr, gate});
+                         final_pass ? dst : work, final_pass ? f64 : nullptr, gate, chunk});
   }
   return v;
 }
@@ -253,9 +256,10 @@ std::vector<PassSpec> solve_pass_specs(const Plan *p, bool fp32, int src_mode, c
 // Full solve with Real precision: src (cells, src_mode) -> dst (dst_mode).
 template <typename Real>
 static pc_status solve_real(Plan *p, int src_mode, const void *src, int dst_mode, void *dst,
-                            cudaStream_t st, double *f64 = nullptr, RefineGate gate = RefineGate{nullptr, 0, 0.0f}) {
+                            cudaStream_t st, double *f64 = nullptr, RefineGate gate = RefineGate{nullptr, 0, 0.0f},
+                            int chunk = 1) {
   if (p->dim < 2) return fail(PC_ERR_UNSUPPORTED, "dim 1");
-  for (const PassSpec &ps : solve_pass_specs(p, sizeof(Real) == 4, src_mode, src, dst_mode, dst, f64, gate))
+  for (const PassSpec &ps : solve_pass_specs(p, sizeof(Real) == 4, src_mode, src, dst_mode, dst, f64, gate, chunk))
     PC_TRY(launch_pass<Real>(p, ps, st));
   return PC_OK;
 }
@@ -265,8 +269,8 @@ pc_status solve_fp64_grid(Plan *p, const double *s, double *pout, cudaStream_t s
 }
 
 pc_status solve_fp32_grid(Plan *p, int src_mode, const void *s, int dst_mode, void *dst,
-                          cudaStream_t st, double *f64, RefineGate gate) {
-  return solve_real<float>(p, src_mode, s, dst_mode, dst, st, f64, gate);
+                          cudaStream_t st, double *f64, RefineGate gate, int chunk) {
+  return solve_real<float>(p, src_mode, s, dst_mode, dst, st, f64, gate, chunk);
 }
 
 }  // namespace pc

@@ -489,11 +489,13 @@ __device__ __forceinline__ DF df_neg_(DF a) { return DF{-a.hi, -a.lo}; }
 struct RefineStep {
   int k, rule;
   float tol;
+  int chunk;   // single-problem launches: consecutive blocks per CTA (0 or 1: one)
 };
 
 // Refinement runs under the stopping rule (MIXED with refine_tol > 0 and sweeps allowed): every
 // residual records its max norm, the kernels of a sweep that the rule ended exit at once, and
 // every solve writes p in FP64 since any of them may be the last.
+constexpr int kLateChunk = 8;
 static bool refine_adaptive(const Plan *p) {
   return p->precision == PC_PREC_MIXED && p->refine_tol > 0.0 && p->refine_iters > 0;
 }
@@ -518,7 +520,7 @@ template <int DIM, bool SINGULAR, bool WRITE_R, bool NORM, typename SV, typename
 __device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, const SV *__restrict__ s,
                                               const PV *__restrict__ p, float *__restrict__ r,
                                               DevStats *stats, double *res2, double *partials,
-                                              unsigned int *counter, RefineStep rs = RefineStep{0, 0, 0.0f}) {
+                                              unsigned int *counter, RefineStep rs = RefineStep{0, 0, 0.0f, 1}) {
   if (rs.rule == 1 && refine_stopped_before(stats, rs.k, rs.tol)) return;   // the refinement already ended
   int x, row0;
   tile_pos(g, b, x, row0);
@@ -566,12 +568,20 @@ __device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, cons
   }
   if (NORM) grid_sum(nrm, partials, counter, res2, tile_block(g, b));
 }
+// CTA b evaluates blocks b * rs.chunk, ... of the grid's decomposition (the residual per cell,
+// its max norm and its L2 partial per block do not depend on how blocks are grouped).
 template <int DIM, bool SINGULAR, bool WRITE_R, bool NORM, typename SV, typename PV>
 __global__ void residual_kernel(GridDev g, const SV *__restrict__ s, const PV *__restrict__ p,
                                 float *__restrict__ r, DevStats *stats, double *res2,
                                 double *partials, unsigned int *counter, RefineStep rs) {
   pdl_enter();
-  residual_body<DIM, SINGULAR, WRITE_R, NORM, SV, PV>(blockIdx.x, g, s, p, r, stats, res2, partials, counter, rs);
+  if (rs.rule == 1 && refine_stopped_before(stats, rs.k, rs.tol)) return;   // the refinement already ended
+  RefineStep in = rs;
+  if (in.rule == 1) in.rule = 2;   // checked above
+  const int c = rs.chunk > 1 ? rs.chunk : 1;
+  const int b0 = blockIdx.x * c, b1 = min(b0 + c, g.nblk);
+  for (int b = b0; b < b1; ++b)
+    residual_body<DIM, SINGULAR, WRITE_R, NORM, SV, PV>(b, g, s, p, r, stats, res2, partials, counter, in);
 }
 
 // ----------------------------------------------------------------------------- gauge
@@ -1088,7 +1098,7 @@ __global__ void batch_residual(const BatchProblem *__restrict__ P, const int *__
   const float2 *s2 = reinterpret_cast<const float2 *>(q.s64);
   const bool rule = q.tol > 0.0f;
   if (rule && refine_stopped_before(q.ds, k, q.tol)) return;
-  const RefineStep rs{k, rule ? 2 : 0, q.tol};
+  const RefineStep rs{k, rule ? 2 : 0, q.tol, 1};
   const int b0 = (int)(blockIdx.x - seg[pi]) * kResidualChunk;
   const int b1 = min(b0 + kResidualChunk, q.g.nblk);
   for (int b = b0; b < b1; ++b) {
@@ -1262,13 +1272,14 @@ static bool is_device_ptr(const void *ptr) {
 template <typename SV, typename PV>
 static void launch_residual(bool singular, bool write_r, bool norm, cudaStream_t st, const GridDev &g,
                             const SV *s, const PV *p, float *r, DevStats *ds, double *res2, double *partials,
-                            unsigned int *counters, RefineStep rs = RefineStep{0, 0, 0.0f}) {
+                            unsigned int *counters, RefineStep rs = RefineStep{0, 0, 0.0f, 1}) {
+  const int grid = (g.nblk + (rs.chunk > 1 ? rs.chunk : 1) - 1) / (rs.chunk > 1 ? rs.chunk : 1);
 #define PC_RES(S, W, N)                                                                                       \
   do {                                                                                                        \
     if (g.dim == 2)                                                                                           \
-      launch_pdl(residual_kernel<2, S, W, N, SV, PV>, g.nblk, 256, 0, st, g, s, p, r, ds, res2, partials, counters, rs); \
+      launch_pdl(residual_kernel<2, S, W, N, SV, PV>, grid, 256, 0, st, g, s, p, r, ds, res2, partials, counters, rs); \
     else                                                                                                      \
-      launch_pdl(residual_kernel<3, S, W, N, SV, PV>, g.nblk, 256, 0, st, g, s, p, r, ds, res2, partials, counters, rs); \
+      launch_pdl(residual_kernel<3, S, W, N, SV, PV>, grid, 256, 0, st, g, s, p, r, ds, res2, partials, counters, rs); \
   } while (0)
   if (singular) {
     if (write_r) { if (norm) PC_RES(true, true, true); else PC_RES(true, true, false); }
@@ -1308,7 +1319,10 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
     const float tol = adaptive ? (float)p->refine_tol : 0.0f;
     // residual k (after k sweeps) and the solve of sweep j run only while the rule has not
     // ended the refinement at an earlier residual
-    auto step = [&](int k) { return RefineStep{k, adaptive ? 1 : 0, tol}; };
+    // Under the rule, sweeps beyond the second (which the rule has ended on every workload
+    // measured) run with kLateChunk tiles or blocks per CTA: few CTAs, so skipping them is cheap
+    auto chunk = [&](int j) { return (adaptive && j > 2) ? kLateChunk : 1; };
+    auto step = [&](int k) { return RefineStep{k, adaptive ? 1 : 0, tol, chunk(k)}; };
     auto gate = [&](int j) { return adaptive ? RefineGate{p->dstats, j, tol} : RefineGate{nullptr, 0, 0.0f}; };
     const bool norm = want_final_residual;
     double *first_out = (sweeps == 0 || adaptive) ? pout : nullptr;
@@ -1326,7 +1340,7 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
       count_launch(p);
       prof_mark(p, st, 4);
       PC_TRY(solve_fp32_grid(p, SRC_F32_, r32, DST_PAIR_ADD_, p->p2, st,
-                             (adaptive || it == sweeps - 1) ? pout : nullptr, gate(it + 1)));
+                             (adaptive || it == sweeps - 1) ? pout : nullptr, gate(it + 1), chunk(it + 1)));
       prof_mark(p, st, 3);
     }
     // the residual after the last allowed sweep (statistics, and the rule's verdict on them)
