@@ -324,11 +324,13 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(_smi_id(dev, local_rank))
     t_wall = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed")   # the timed projections (ncu --nvtx-include timed/)
     for k in range(steps):
         flush.fill_(k & 0xFF)
         evs[k][0].record(stream)
         plan.project(u_dev, out=outs)
         evs[k][1].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - t_wall
     if world > 1:
@@ -846,11 +848,13 @@ def run_batch(args, dev, stream, flush, world):
     torch.cuda.synchronize(dev)
     k = args.batch_steps
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    torch.cuda.nvtx.range_push("batch")   # the timed batches (ncu --nvtx-include batch/)
     for i in range(k):
         flush.fill_(i & 0xFF)
         evs[i][0].record(stream)
         pc.project_batch(plans, bargs)
         evs[i][1].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(dev)
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / k, world, dev)
     cells = sum(pr.num_cells for pr in probs)
