@@ -664,8 +664,8 @@ def run_variants(args, prob, u_dev, stream, dev, flush, ms_step, reps=50):
         return sum(a.elapsed_time(b) for a, b in ev) / reps
 
     # the regular (vertex) grid: the 400x400 periodic grid of the cylinder results, and an all-wall
-    # 512x512 vertex grid (513^2 unknowns, solved as its 1024^2 even extension), each against the
-    # cell-centred solve of the same cells
+    # 512x512 vertex grid (513^2 unknowns, DCT-I along both axes), each against the cell-centred
+    # solve of the same cells
     vert = {}
     for tag, n, lo, hi in (("periodic_400x400", (400, 400), ("P", "P"), ("P", "P")),
                            ("walls_512x512", (512, 512), ("W", "W"), ("W", "W"))):
@@ -682,7 +682,7 @@ def run_variants(args, prob, u_dev, stream, dev, flush, ms_step, reps=50):
         vert[tag] = row
     out["vertex_grid_solve"] = vert
     # the whole pass on the vertex grid of the same workload (direct divergence at the vertex
-    # unknowns; the I-D axis extends to 4n, the wall pair to 2n: 8x the cells of the transforms)
+    # unknowns; quarter-wave transforms along the I-D axis, DCT-I along the wall pair)
     vp = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, refine_tol=args.refine_tol, device=dev.index,
                  div_mode="wls_direct", grid_type="vertices")
     vp.autotune()

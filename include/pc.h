@@ -128,8 +128,8 @@ typedef struct {
                                divergence at the vertex unknowns, the node gradient uses the 3^d
                                block of lattice vertices around each node (Dirichlet boundary
                                vertices with value 0), and p_out, the RHS mask and the rows of
-                               pc_plan_rows(dim + 1) are in the unknowns' layout. The solve length
-                               per axis is that of the vertex extension (pc_grid_plan_create) */
+                               pc_plan_rows(dim + 1) are in the unknowns' layout. The transform
+                               limits per axis are those of pc_grid_plan_create's vertex grids */
   double refine_tol;        /* MIXED: stopping rule of the refinement, decided on the device after
                                each residual r_k = s - mean - L_h p_k (k sweeps done), on max
                                norms: stop when ||r_k|| <= refine_tol ||s|| (converged); or when
@@ -279,13 +279,16 @@ pc_status pc_plan_set_rhs_mask(pc_plan *plan, const uint8_t *mask, void *cuda_st
  * "regular" grid of §2.3, used for the results of §3.2). On a vertex grid with n cells per axis
  * the unknowns of an axis are, per boundary pair (lo-hi): P-P vertices 0..n-1; N-N 0..n (mirror
  * ghosts p_{-1} = p_1, p_{n+1} = p_{n-1}); D-D 1..n-1 (p_0 = p_n = 0); N-D 0..n-1 (p_n = 0);
- * D-N 1..n (p_0 = 0). The eigenbases are DCT-I (N-N), DST-I (D-D) and the quarter-wave
- * cosine/sine pairs (N-D, D-N); they are computed as the real DFT of the source extended evenly
- * about Neumann ends and oddly about Dirichlet ends, i.e. the periodic cell-grid solve of 2n
- * (N-N, D-D) or 4n (N-D, D-N) cells per axis, whose length must satisfy the transform limits
- * (even, half of it 2^a 3^b 5^c <= 2048). When every axis is P-P or N-N the constant mode is
- * dropped (on N-N axes it is the trapezoid-weighted mean) and reported in removed_mean; the
- * corner gauge zeroes the first unknown. Only pc_solve_poisson, the schedule, profiling and
+ * D-N 1..n (p_0 = 0). The eigenbases are DCT-I (N-N), DST-I (D-D), the real DFT (P-P) and the
+ * quarter-wave cosine/sine bases cos(pi (k + 1/2) j/n), sin(pi (k + 1/2) j/n) (N-D, D-N). The
+ * solve runs on the unknowns with one transform pass per axis as on the cell grid: DCT-I and
+ * DST-I through the real DFT of length 2n of the line extended evenly or oddly in shared memory
+ * (n must be 2^a 3^b 5^c <= 2048), the quarter-wave pairs as the DCT-III / DST-III analysis and
+ * DCT-II / DST-II synthesis of length n, and P-P as on the cell grid (n even, n/2 2^a 3^b 5^c
+ * <= 2048 for both). When every axis is P-P or N-N the constant mode is dropped (on N-N axes it
+ * is the trapezoid-weighted mean) and reported in removed_mean, and the solution has no
+ * constant part (trapezoid-weighted mean zero); the corner gauge zeroes the first unknown
+ * instead. Only pc_solve_poisson, the schedule, profiling and
  * pc_destroy apply to a grid-only plan; the node entry points and pc_plan_clone return
  * PC_ERR_INVALID_ARG.
  * pc_grid_plan_create reads desc during the call only; the plan belongs to the caller until
@@ -313,9 +316,9 @@ pc_status pc_grid_plan_create(const pc_grid_desc *desc, int device, void *cuda_s
 pc_status pc_solve_poisson(pc_plan *plan, const double *s, double *p_out, pc_stats *stats,
                            void *cuda_stream);
 /* (On a vertex-grid plan s and p_out have the unknowns' shape, C order. The statistics are those
- * of the extended periodic solve; removed_mean is the dropped zero-mode coefficient of the vertex
- * problem (0 when an axis has a Dirichlet end), gauge_shift the constant the gauge took from the
- * extended solution: on problems without a zero mode only the mean that rounding left.) */
+ * of the solve on the unknowns: source_norm and the residual norms are plain L2 norms over them,
+ * removed_mean is the dropped zero-mode coefficient (the trapezoid-weighted mean of s; 0 when an
+ * axis has a Dirichlet end) and gauge_shift the constant the gauge took from p.) */
 
 /* Allocation-free grid-level Poisson solve (the paper has no counterpart: this is a service of
  * the library, not a step of the method). Solves L_h p = s in FP64 with the same transform

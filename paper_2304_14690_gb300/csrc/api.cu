@@ -62,6 +62,7 @@ static void plan_free(Plan *p, void *ptr, size_t bytes) {
 }
 
 bool axis_length_supported(int n);
+bool vertex_axis_supported(int kind, int m);
 pc_status prepare_kernels();
 
 void prof_begin(Plan *p, cudaStream_t st) {
@@ -160,23 +161,26 @@ static bool host_ptr(const void *ptr) {
 }
 
 // Two partial sums per block of the largest reduction launch (cell grid or flat grid).
-// Sizes of a vertex-grid axis of n cells and boundary pair kind: the length of its periodic
-// symmetric extension (2n on N-N and D-D, 4n on N-D and D-N, n on P-P), the unknowns, the
-// lattice index of the first unknown and the lattice vertices.
-static void vertex_axis(int kind, int n, int &next, int &nunk, int &j0, int &nlat) {
-  next = kind == KIND_PP ? n : ((kind == KIND_NN || kind == KIND_DD) ? 2 * n : 4 * n);
+// Sizes of a vertex-grid axis of n cells and boundary pair kind: the unknowns, the lattice
+// index of the first unknown and the lattice vertices.
+static void vertex_axis(int kind, int n, int &nunk, int &j0, int &nlat) {
   nunk = kind == KIND_NN ? n + 1 : (kind == KIND_DD ? n - 1 : n);
   j0 = (kind == KIND_DD || kind == KIND_DN) ? 1 : 0;
   nlat = kind == KIND_PP ? n : n + 1;
 }
+// Transform kind of a vertex-grid axis with boundary pair kind.
+static int vertex_kind(int kind) {
+  switch (kind) {
+    case KIND_NN: return KIND_VNN;
+    case KIND_DD: return KIND_VDD;
+    case KIND_ND: return KIND_VND;
+    case KIND_DN: return KIND_VDN;
+    default: return KIND_PP;
+  }
+}
 
 static size_t partial_slots(const Plan *p) {
-  long long last = p->n[p->dim - 1];
-  if (p->vertex) {   // the transform grid is the extension: the longer last axis, fewer rows
-    int next, nunk, j0, nlat;
-    vertex_axis(p->vkind[p->dim - 1], p->vn[p->dim - 1], next, nunk, j0, nlat);
-    last = next;
-  }
+  const long long last = p->n[p->dim - 1];
   const long long cells_launch = ((last + 255) / 256) * (p->ncells / last);
   const long long flat_launch = (p->ncells + 255) / 256;
   return (size_t)(2 * (cells_launch > flat_launch ? cells_launch : flat_launch) + 64);
@@ -188,10 +192,12 @@ static size_t partial_slots(const Plan *p) {
 static pc_status alloc_workspace(Plan *p, cudaStream_t st) {
   const bool mixed = p->precision != PC_PREC_FP64;
   const long long N = p->N, nc = p->ncells;
+  // a vertex pass also holds p on the whole lattice for the gradient, in work64 (FP64) and p2
+  const long long nl = (p->vertex && p->nftot > nc) ? p->nftot : nc;
   const int dd = p->dim;
   for (int a = 0; a < dd; ++a)
     if (plan_alloc(p, (void **)&p->U64[a], p->nface_total[a] * 8) != PC_OK) return PC_ERR_OUT_OF_MEMORY;
-  if (plan_alloc(p, (void **)&p->s64, nc * 8) != PC_OK || plan_alloc(p, (void **)&p->work64, nc * 8) != PC_OK ||
+  if (plan_alloc(p, (void **)&p->s64, nc * 8) != PC_OK || plan_alloc(p, (void **)&p->work64, nl * 8) != PC_OK ||
       plan_alloc(p, (void **)&p->work32, nc * 4) != PC_OK ||
       plan_alloc(p, (void **)&p->dstats, sizeof(DevStats)) != PC_OK ||
       plan_alloc(p, (void **)&p->partials, partial_slots(p) * sizeof(double)) != PC_OK ||
@@ -199,7 +205,7 @@ static pc_status alloc_workspace(Plan *p, cudaStream_t st) {
       plan_alloc(p, (void **)&p->stage_p, nc * 8) != PC_OK || plan_alloc(p, (void **)&p->stage_s, nc * 8) != PC_OK)
     return PC_ERR_OUT_OF_MEMORY;
   if (mixed) {
-    if (plan_alloc(p, (void **)&p->p2, nc * 8) != PC_OK || plan_alloc(p, (void **)&p->u2, dd * N * 8) != PC_OK)
+    if (plan_alloc(p, (void **)&p->p2, nl * 8) != PC_OK || plan_alloc(p, (void **)&p->u2, dd * N * 8) != PC_OK)
       return PC_ERR_OUT_OF_MEMORY;
   } else {
     if (plan_alloc(p, (void **)&p->ut64, dd * N * 8) != PC_OK) return PC_ERR_OUT_OF_MEMORY;
@@ -214,21 +220,15 @@ static pc_status alloc_workspace(Plan *p, cudaStream_t st) {
   return PC_OK;
 }
 
-// A vertex plan's axes become the periodic cell grid of the extension (after the node rows
-// have been built on the physical grid).
+// A vertex plan's pressure grid is its lattice of unknowns, with the vertex transform kinds
+// (set after the node rows have been built on the physical grid).
 static void vertex_switch_axes(Plan *p) {
   for (int a = 0; a < p->dim; ++a) {
-    int next, nunk, j0, nlat;
-    vertex_axis(p->vkind[a], p->vn[a], next, nunk, j0, nlat);
     AxisInfo &ax = p->ax[a];
-    ax.n = next;
-    ax.L = (double)next * ax.h;
-    ax.bc_lo = ax.bc_hi = PC_BC_PERIODIC;
-    ax.periodic = true;
+    ax.n = p->nv[a];
+    ax.kind = vertex_kind(p->vkind[a]);
     ax.nfaces = ax.n;
-    ax.kind = axis_kind(PC_BC_PERIODIC, PC_BC_PERIODIC);
-    p->n[a] = next;
-    p->bc_lo[a] = p->bc_hi[a] = PC_BC_PERIODIC;
+    p->n[a] = ax.n;
     p->nface_total[a] = 0;
   }
 }
@@ -271,11 +271,18 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
     if ((d->bc_lo[a] == PC_BC_PERIODIC) != (d->bc_hi[a] == PC_BC_PERIODIC))
       return fail(PC_ERR_INVALID_ARG, "periodic must pair with periodic (axis %d)", a);
     vk[a] = axis_kind(d->bc_lo[a], d->bc_hi[a]);
-    if (vert) vertex_axis(vk[a], (int)d->n[a], nint[a], nv[a], vj0[a], nf[a]);
-    else nint[a] = nv[a] = nf[a] = (int)d->n[a];
-    if (!axis_length_supported(nint[a]))
-      return fail(PC_ERR_UNSUPPORTED, "axis %d: the solve length %d must be even with half of it 2^a 3^b 5^c <= 2048",
-                  a, nint[a]);
+    if (vert) {
+      vertex_axis(vk[a], (int)d->n[a], nv[a], vj0[a], nf[a]);
+      nint[a] = nv[a];
+      if (!vertex_axis_supported(vertex_kind(vk[a]), (int)d->n[a]))
+        return fail(PC_ERR_UNSUPPORTED, "vertex axis %d of %d cells: N-N and D-D axes need 2^a 3^b 5^c <= 2048 "
+                    "cells, the others an even count with half of it 2^a 3^b 5^c <= 2048", a, (int)d->n[a]);
+    } else {
+      nint[a] = nv[a] = nf[a] = (int)d->n[a];
+      if (!axis_length_supported(nint[a]))
+        return fail(PC_ERR_UNSUPPORTED, "axis %d: the solve length %d must be even with half of it 2^a 3^b 5^c <= 2048",
+                    a, nint[a]);
+    }
     ncells *= nint[a];
     nvtot *= nv[a];
     nftot *= nf[a];
@@ -348,7 +355,6 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
     if (d->bc_lo[a] == PC_BC_DIRICHLET || d->bc_hi[a] == PC_BC_DIRICHLET) p->singular = false;
   }
   p->problem_singular = p->singular;
-  if (vert) p->singular = true;   // the extension is periodic on every axis
   for (int a = 0; a < d->dim; ++a) {
     p->phys_L[a] = p->ax[a].L;
     p->phys_periodic[a] = p->ax[a].periodic;
@@ -370,10 +376,10 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
   const long long Kg = p->Kg;
   need += (size_t)N * Kg * (4 + dd * 8) + N;
   need += (size_t)nc * (8 + 8 + 4 + (mixed ? 8 : 0) + 8 + 8);
+  if (vert && nftot > nc) need += (size_t)(nftot - nc) * (mixed ? 16 : 8);   // lattice copies of p
   need += (size_t)dd * N * 8;
   need += (size_t)dd * N * 8;                             // node coordinates (setup only)
   if (p->divmode == PC_DIV_WLS_DIRECT) need += (size_t)p->npts * K * (4 + dd * 8);   // point rows
-  if (vert) need += (size_t)nvtot * 16;
   if (budget && need > budget)
     return bail(fail(PC_ERR_BUDGET, "plan needs %zu bytes, budget is %zu", need, budget));
 
@@ -396,7 +402,6 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
        (!mixed && plan_alloc(p, (void **)&p->cD64, dd * np * K * 8) != PC_OK) ||
        (mixed && plan_alloc(p, (void **)&p->cD2, dd * np * K * 8) != PC_OK)))
     return bail(PC_ERR_OUT_OF_MEMORY);
-  if (vert && plan_alloc(p, (void **)&p->vstage, (size_t)nvtot * 16) != PC_OK) return bail(PC_ERR_OUT_OF_MEMORY);
   {
     pc_status ws = alloc_workspace(p, st);
     if (ws != PC_OK) return bail(ws);
@@ -424,7 +429,7 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
     if (hb & 2u) return bail(fail(PC_ERR_INVALID_ARG, "node_type values must be 0, 1 or 2"));
   }
   if (prepare_kernels() != PC_OK) return bail(PC_ERR_CUDA);
-  // rows on the physical grid, then (vertex plans) the transform axes of the extension
+  // rows on the physical grid, then (vertex plans) the transform axes of the unknowns
   pc_status s = build_rows(p, xyz_dev, st);
   if (s != PC_OK) return bail(s);
   if (vert) vertex_switch_axes(p);
@@ -437,10 +442,9 @@ static pc_status create(const pc_problem_desc *d, int device, size_t budget, cud
 }
 
 
-// Grid-only plan: the transform tables and the cell workspace, no nodes. A vertex grid becomes
-// the periodic cell grid of its symmetric extension: 2n cells on N-N and D-D axes, 4n on N-D
-// and D-N axes (n on P-P axes); the extension and the restriction to the vertex unknowns are
-// kernels of pc_solve_poisson.
+// Grid-only plan: the transform tables and the cell workspace, no nodes. A vertex grid is
+// solved on its unknowns (n + 1 on N-N axes, n - 1 on D-D axes, n otherwise) with the vertex
+// transforms.
 static pc_status create_grid(const pc_grid_desc *d, int device, cudaStream_t st, Plan **out) {
   if (!d || !out) return fail(PC_ERR_INVALID_ARG, "desc and out_plan are required");
   *out = nullptr;
@@ -469,13 +473,17 @@ static pc_status create_grid(const pc_grid_desc *d, int device, cudaStream_t st,
     vk[a] = axis_kind(d->bc_lo[a], d->bc_hi[a]);
     if (vert) {
       int j0, nlat;
-      vertex_axis(vk[a], n, nint[a], nv[a], j0, nlat);
+      vertex_axis(vk[a], n, nv[a], j0, nlat);
+      nint[a] = nv[a];
+      if (!vertex_axis_supported(vertex_kind(vk[a]), n))
+        return fail(PC_ERR_UNSUPPORTED, "vertex axis %d of %d cells: N-N and D-D axes need 2^a 3^b 5^c <= 2048 "
+                    "cells, the others an even count with half of it 2^a 3^b 5^c <= 2048", a, n);
     } else {
       nint[a] = nv[a] = n;
+      if (!axis_length_supported(nint[a]))
+        return fail(PC_ERR_UNSUPPORTED, "axis %d: the solve length %d must be even with half of it 2^a 3^b 5^c <= 2048",
+                    a, nint[a]);
     }
-    if (!axis_length_supported(nint[a]))
-      return fail(PC_ERR_UNSUPPORTED, "axis %d: the solve length %d must be even with half of it 2^a 3^b 5^c <= 2048",
-                  a, nint[a]);
     ncells *= nint[a];
     nvtot *= nv[a];
   }
@@ -502,21 +510,21 @@ static pc_status create_grid(const pc_grid_desc *d, int device, cudaStream_t st,
   p->eigen = d->eigenvalues;
   p->ncells = ncells;
   p->problem_singular = psing;
-  p->singular = vert ? true : psing;   // the extension is periodic on every axis
+  p->singular = psing;
   p->nvtot = nvtot;
   for (int a = 0; a < 3; ++a) {
     const bool on = a < d->dim;
     p->n[a] = on ? nint[a] : 1;
     p->lo[a] = 0.0;
     p->h[a] = on ? d->h[a] : 1.0;
-    p->bc_lo[a] = on ? (vert ? PC_BC_PERIODIC : d->bc_lo[a]) : 0;
-    p->bc_hi[a] = on ? (vert ? PC_BC_PERIODIC : d->bc_hi[a]) : 0;
+    p->bc_lo[a] = on ? d->bc_lo[a] : 0;
+    p->bc_hi[a] = on ? d->bc_hi[a] : 0;
     p->vkind[a] = vk[a];
     p->vn[a] = on ? (int)d->n[a] : 1;
     p->nv[a] = nv[a];
     if (on && vert) {
-      int next, nunk;
-      vertex_axis(vk[a], (int)d->n[a], next, nunk, p->vj0[a], p->nf[a]);
+      int nunk;
+      vertex_axis(vk[a], (int)d->n[a], nunk, p->vj0[a], p->nf[a]);
     }
   }
   p->nftot = 1;
@@ -530,13 +538,12 @@ static pc_status create_grid(const pc_grid_desc *d, int device, cudaStream_t st,
     ax.bc_hi = p->bc_hi[a];
     ax.periodic = ax.bc_lo == PC_BC_PERIODIC;
     ax.nfaces = ax.periodic ? ax.n : ax.n + 1;
-    ax.kind = axis_kind(ax.bc_lo, ax.bc_hi);
+    ax.kind = vert ? vertex_kind(vk[a]) : axis_kind(ax.bc_lo, ax.bc_hi);
     p->nface_total[a] = 0;   // no faces: the plan has no transfer
   }
   auto bail = [&](pc_status s) { destroy_plan(p); return s; };
   pc_status s = alloc_workspace(p, st);
   if (s != PC_OK) return bail(s);
-  if (vert && plan_alloc(p, (void **)&p->vstage, (size_t)nvtot * 16) != PC_OK) return bail(PC_ERR_OUT_OF_MEMORY);
   if (prepare_kernels() != PC_OK) return bail(PC_ERR_CUDA);
   s = build_axis_tables(p);
   if (s != PC_OK) return bail(s);
@@ -610,8 +617,6 @@ extern "C" pc_status pc_plan_clone(pc_plan *plan, void *cuda_stream, pc_plan **o
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   pc_status s = alloc_workspace(p, st);
-  if (s == PC_OK && p->vertex && plan_alloc(p, (void **)&p->vstage, (size_t)p->nvtot * 16) != PC_OK)
-    s = PC_ERR_OUT_OF_MEMORY;
   if (s == PC_OK && cudaStreamSynchronize(st) != cudaSuccess) s = fail(PC_ERR_CUDA, "clone setup failed");
   if (s != PC_OK) {
     destroy_plan(p);

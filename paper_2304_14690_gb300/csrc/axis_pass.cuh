@@ -15,12 +15,16 @@
 
 namespace pc {
 
-// Transform kind of a pass: fixed by the family where the family has one member, else read.
+// Transform kind of a pass: fixed by the family where the family has one member, else read
+// (KC = -1: any cell-grid kind).
 template <int KC>
 __device__ __forceinline__ int pass_kind(int k) {
   if (KC == 0) return KIND_PP;
   if (KC == 1) return k == KIND_DD ? KIND_DD : KIND_NN;
   if (KC == 2) return k == KIND_DN ? KIND_DN : KIND_ND;
+  if (KC == 3) return k == KIND_VDD ? KIND_VDD : KIND_VNN;
+  if (KC == 4) return k == KIND_VDN ? KIND_VDN : KIND_VND;
+  __builtin_assume(k >= KIND_PP && k <= KIND_DN);
   return k;
 }
 
@@ -38,6 +42,52 @@ __device__ __forceinline__ Real load_src(const PassArgs<Real> &A, int gi) {
   return static_cast<const Real *>(A.src)[gi];
 }
 
+// I3: store the n outputs of this thread's line, in chunks of 8 (the old values of an
+// accumulating store are loaded together). get(s, i) is output i, the s-th of this thread.
+template <typename Real, int EMAX, typename Get>
+__device__ __forceinline__ void store_line(const PassArgs<Real> &A, const TileGeom &g, int base, int n, Get get) {
+  const int stride = A.stride;
+  constexpr int kChunk = 8;
+#pragma unroll
+  for (int c0 = 0; c0 < 2 * EMAX; c0 += kChunk) {
+    Real x[kChunk];
+    // previous value of an accumulating store: an FP64 value or a (hi, lo) pair, 8 bytes either way
+    unsigned long long old[kChunk];
+    const bool acc = A.dst_mode == DST_F64_ADD || A.dst_mode == DST_PAIR_ADD;
+#pragma unroll
+    for (int b = 0; b < kChunk; ++b) {
+      const int i = g.lane + (c0 + b) * g.tpl;
+      x[b] = (i < n) ? get(c0 + b, i) : (Real)0;
+      old[b] = (acc && i < n) ? static_cast<const unsigned long long *>(A.dst)[base + i * stride] : 0ULL;
+    }
+#pragma unroll
+    for (int b = 0; b < kChunk; ++b) {
+      const int i = g.lane + (c0 + b) * g.tpl;
+      if (i >= n) continue;
+      const int gi = base + i * stride;
+      if (A.dst_mode == DST_WORK) {
+        static_cast<Real *>(A.dst)[gi] = x[b];
+      } else if (A.dst_mode == DST_PAIR_SET || A.dst_mode == DST_PAIR_ADD) {
+        // FP32 passes only: the pair (hi, lo) += x with Knuth's TwoSum, renormalised
+        float hi = (float)x[b], lo = 0.0f;
+        if (A.dst_mode == DST_PAIR_ADD) {
+          const float a = __uint_as_float((unsigned)old[b]), alo = __uint_as_float((unsigned)(old[b] >> 32));
+          const float bb = hi;
+          const float s1 = __fadd_rn(a, bb), z = __fsub_rn(s1, a);
+          const float e = __fadd_rn(__fadd_rn(__fsub_rn(a, __fsub_rn(s1, z)), __fsub_rn(bb, z)), alo);
+          hi = __fadd_rn(s1, e);
+          lo = __fsub_rn(e, __fsub_rn(hi, s1));
+        }
+        static_cast<float2 *>(A.dst)[gi] = make_float2(hi, lo);
+        if (A.f64) A.f64[gi] = f2d_bits(hi) + f2d_bits(lo);
+      } else {
+        static_cast<double *>(A.dst)[gi] =
+            (A.dst_mode == DST_F64_SET) ? to_f64(x[b]) : __longlong_as_double((long long)old[b]) + to_f64(x[b]);
+      }
+    }
+  }
+}
+
 // One axis pass over a tile of lines: [forward transform] [eigenvalue division] [inverse].
 // Dynamic shared memory: two buffers of L*M complex slots (the FFT ping-pongs between them),
 // then per line the eigenvalue sum of the other axes, the line's base cell index (-1 for lines
@@ -47,6 +97,10 @@ __device__ __forceinline__ Real load_src(const PassArgs<Real> &A, int gi) {
 //             or -> real coefficients in the other buffer with the division fused |
 //   inverse:  (inverse-only: load coefficients -> other buffer |) pre-process -> slots |
 //             FFT stages | normalise and store.
+// The quarter-wave vertex kinds (family 4) run the cell grid's DCT-II/DST-II pair in the other
+// order: analysis through its inverse (stage | pre-process | FFT | coefficients, divided, kept
+// in registers |), synthesis through its forward (scatter | FFT | post-process -> other buffer
+// | store).
 template <typename Real, int EMAX, int KC = -1, bool POW2 = false>
 __device__ __forceinline__ void axis_pass_body(const PassArgs<Real> &A, const int tile, unsigned char *smem_raw) {
   using T = typename Cplx<Real>::T;
@@ -108,103 +162,128 @@ __device__ __forceinline__ void axis_pass_body(const PassArgs<Real> &A, const in
     const int j = g.lane + b * g.tpl;
     xin[b] = (valid && j < n) ? load_src(A, base + j * stride) : (Real)0;
   }
-  T *res;        // buffer with the latest slots
-  T *coef;       // buffer with the real coefficients for the inverse
-  if (A.do_fwd) {
-    // F1: scatter the real line into the complex slots (Makhoul / DCT-IV ordering).
+
+  if constexpr (KC == 4) {
+    const int bk = (kind == KIND_VDN) ? KIND_DD : KIND_NN;   // the cell grid's pair, reversed
+    if (A.do_fwd) {
+      // analysis: the DCT-III / DST-III of the line (the cell grid's inverse), times 1/M
+#pragma unroll
+      for (int b = 0; b < 2 * EMAX; ++b) {
+        const int j = g.lane + b * g.tpl;
+        if (j < n) realref(buf1, g, line, j) = xin[b];
+      }
+      __syncthreads();
+      if (valid) inv_pre(buf0, g, bk, n, A.tw, [&](int i) -> Real { return realref(buf1, g, line, i); });
+      __syncthreads();
+      T *res = fft_run<T, EMAX, true, POW2>(buf0, buf1, g, A.st, A.nst, A.tw, nullptr);
+      const Real lo = A.do_div ? lamo[line] : (Real)0;
+      const bool z = A.do_div && A.singular && lzero[line];
+      const Real *la = A.lam[A.axis];
+#pragma unroll
+      for (int b = 0; b < 2 * EMAX; ++b) {
+        const int i = g.lane + b * g.tpl;
+        Real c = (valid && i < n) ? inv_out(res, g, bk, n, A.tw, i) * A.out_scale : (Real)0;
+        if (A.do_div && valid && i < n) c = (z && i == 0) ? (Real)0 : c / (__ldg(la + i) + lo);
+        xin[b] = c;
+      }
+      if (!A.do_inv) {
+        // forward-only pass: the coefficients go to global memory (DST_WORK)
+        if (valid) store_line<Real, EMAX>(A, g, base, n, [&](int s, int) -> Real { return s < 2 * EMAX ? xin[s] : (Real)0; });
+        return;
+      }
+      __syncthreads();   // every thread has read the FFT result: both buffers are free
+    }
+    // synthesis: the DCT-II / DST-II of the coefficients in xin (the cell grid's forward)
 #pragma unroll
     for (int b = 0; b < 2 * EMAX; ++b) {
-      const int j = g.lane + b * g.tpl;
-      if (j < n) {
+      const int i = g.lane + b * g.tpl;
+      if (i < n) {
         int q, comp;
         bool neg;
-        fwd_slot_of(kind, n, j, q, comp, neg);
+        fwd_slot_of(bk, n, i, q, comp, neg);
         reinterpret_cast<Real *>(&slot(buf0, g, line, q))[comp] = neg ? -xin[b] : xin[b];
       }
     }
     __syncthreads();
-    res = fft_run<T, EMAX, false, POW2>(buf0, buf1, g, A.st, A.nst, A.tw, dct4 ? A.tw + tw_dct4pre(A.M) : nullptr);
-    if (!A.do_inv) {
-      // forward-only pass: the coefficients go straight to global memory (DST_WORK)
-      if (valid) {
-        Real *dst = static_cast<Real *>(A.dst);
-        fwd_post(res, g, kind, n, A.tw, [&](int pos, Real X) { dst[base + pos * stride] = X; });
-      }
-      return;
-    }
-    coef = (res == buf0) ? buf1 : buf0;
-    if (valid) {
-      // p^ = s^ / (lambda_axis(j) + sum of the other axes' eigenvalues); zero mode -> 0
-      const Real lo = lamo[line];
-      const bool z = A.singular && lzero[line];
-      const Real *la = A.lam[A.axis];
-      const bool dv = A.do_div;
-      fwd_post(res, g, kind, n, A.tw, [&](int pos, Real X) {
-        if (dv) X = (z && pos == 0) ? (Real)0 : X / (__ldg(la + pos) + lo);
-        realref(coef, g, line, pos) = X;
-      });
-    }
+    T *res = fft_run<T, EMAX, false, POW2>(buf0, buf1, g, A.st, A.nst, A.tw, nullptr);
+    T *outb = (res == buf0) ? buf1 : buf0;
+    if (valid) fwd_post(res, g, bk, n, A.tw, [&](int pos, Real X) { realref(outb, g, line, pos) = X; });
     __syncthreads();
+    if (valid) store_line<Real, EMAX>(A, g, base, n, [&](int, int i) -> Real { return realref(outb, g, line, i); });
+    return;
   } else {
-    // inverse-only pass: the coefficients are staged in shared memory first
-    coef = buf1;
-    res = buf0;
+    T *res;        // buffer with the latest slots
+    T *coef;       // buffer with the real coefficients for the inverse
+    if (A.do_fwd) {
+      // F1: scatter the real line into the complex slots (Makhoul / DCT-IV ordering; the even or
+      // odd extension of a vertex DCT-I / DST-I line)
+      if (kind == KIND_VNN || kind == KIND_VDD) {
 #pragma unroll
-    for (int b = 0; b < 2 * EMAX; ++b) {
-      const int j = g.lane + b * g.tpl;
-      if (j < n) realref(coef, g, line, j) = xin[b];
-    }
-    __syncthreads();
-  }
-  if (!A.do_inv) return;
-  // I1: coefficients -> slots (into the buffer the forward FFT result came from)
-  T *slots = (coef == buf0) ? buf1 : buf0;
-  if (valid) inv_pre(slots, g, kind, n, A.tw, [&](int i) -> Real { return realref(coef, g, line, i); });
-  __syncthreads();
-  if (dct4) res = fft_run<T, EMAX, false, POW2>(slots, coef, g, A.st, A.nst, A.tw, nullptr);
-  else res = fft_run<T, EMAX, true, POW2>(slots, coef, g, A.st, A.nst, A.tw, nullptr);
-  if (!valid) return;
-  // I3: normalise and store, in chunks of 8 outputs (the old values of an accumulating store
-  // are loaded together)
-  const Real scale = A.out_scale;
-  constexpr int kChunk = 8;
-#pragma unroll
-  for (int c0 = 0; c0 < 2 * EMAX; c0 += kChunk) {
-    Real x[kChunk];
-    // previous value of an accumulating store: an FP64 value or a (hi, lo) pair, 8 bytes either way
-    unsigned long long old[kChunk];
-    const bool acc = A.dst_mode == DST_F64_ADD || A.dst_mode == DST_PAIR_ADD;
-#pragma unroll
-    for (int b = 0; b < kChunk; ++b) {
-      const int i = g.lane + (c0 + b) * g.tpl;
-      x[b] = (i < n) ? inv_out(res, g, kind, n, A.tw, i) * scale : (Real)0;
-      old[b] = (acc && i < n) ? static_cast<const unsigned long long *>(A.dst)[base + i * stride] : 0ULL;
-    }
-#pragma unroll
-    for (int b = 0; b < kChunk; ++b) {
-      const int i = g.lane + (c0 + b) * g.tpl;
-      if (i >= n) continue;
-      const int gi = base + i * stride;
-      if (A.dst_mode == DST_WORK) {
-        static_cast<Real *>(A.dst)[gi] = x[b];
-      } else if (A.dst_mode == DST_PAIR_SET || A.dst_mode == DST_PAIR_ADD) {
-        // FP32 passes only: the pair (hi, lo) += x with Knuth's TwoSum, renormalised
-        float hi = (float)x[b], lo = 0.0f;
-        if (A.dst_mode == DST_PAIR_ADD) {
-          const float a = __uint_as_float((unsigned)old[b]), alo = __uint_as_float((unsigned)(old[b] >> 32));
-          const float bb = hi;
-          const float s1 = __fadd_rn(a, bb), z = __fsub_rn(s1, a);
-          const float e = __fadd_rn(__fadd_rn(__fsub_rn(a, __fsub_rn(s1, z)), __fsub_rn(bb, z)), alo);
-          hi = __fadd_rn(s1, e);
-          lo = __fsub_rn(e, __fsub_rn(hi, s1));
+        for (int b = 0; b < 2 * EMAX; ++b) {
+          const int j = g.lane + b * g.tpl;
+          if (j < n) ext_scatter(buf0, g, line, kind, j, xin[b]);
         }
-        static_cast<float2 *>(A.dst)[gi] = make_float2(hi, lo);
-        if (A.f64) A.f64[gi] = f2d_bits(hi) + f2d_bits(lo);
+        if (kind == KIND_VDD && g.lane == 0) {   // the zeros of the odd extension
+          realref(buf0, g, line, 0) = (Real)0;
+          realref(buf0, g, line, g.M) = (Real)0;
+        }
       } else {
-        static_cast<double *>(A.dst)[gi] =
-            (A.dst_mode == DST_F64_SET) ? to_f64(x[b]) : __longlong_as_double((long long)old[b]) + to_f64(x[b]);
+#pragma unroll
+        for (int b = 0; b < 2 * EMAX; ++b) {
+          const int j = g.lane + b * g.tpl;
+          if (j < n) {
+            int q, comp;
+            bool neg;
+            fwd_slot_of(kind, n, j, q, comp, neg);
+            reinterpret_cast<Real *>(&slot(buf0, g, line, q))[comp] = neg ? -xin[b] : xin[b];
+          }
+        }
       }
+      __syncthreads();
+      res = fft_run<T, EMAX, false, POW2>(buf0, buf1, g, A.st, A.nst, A.tw, dct4 ? A.tw + tw_dct4pre(A.M) : nullptr);
+      if (!A.do_inv) {
+        // forward-only pass: the coefficients go straight to global memory (DST_WORK)
+        if (valid) {
+          Real *dst = static_cast<Real *>(A.dst);
+          fwd_post(res, g, kind, n, A.tw, [&](int pos, Real X) { dst[base + pos * stride] = X; });
+        }
+        return;
+      }
+      coef = (res == buf0) ? buf1 : buf0;
+      if (valid) {
+        // p^ = s^ / (lambda_axis(j) + sum of the other axes' eigenvalues); zero mode -> 0
+        const Real lo = lamo[line];
+        const bool z = A.singular && lzero[line];
+        const Real *la = A.lam[A.axis];
+        const bool dv = A.do_div;
+        fwd_post(res, g, kind, n, A.tw, [&](int pos, Real X) {
+          if (dv) X = (z && pos == 0) ? (Real)0 : X / (__ldg(la + pos) + lo);
+          realref(coef, g, line, pos) = X;
+        });
+      }
+      __syncthreads();
+    } else {
+      // inverse-only pass: the coefficients are staged in shared memory first
+      coef = buf1;
+      res = buf0;
+#pragma unroll
+      for (int b = 0; b < 2 * EMAX; ++b) {
+        const int j = g.lane + b * g.tpl;
+        if (j < n) realref(coef, g, line, j) = xin[b];
+      }
+      __syncthreads();
     }
+    if (!A.do_inv) return;
+    // I1: coefficients -> slots (into the buffer the forward FFT result came from)
+    T *slots = (coef == buf0) ? buf1 : buf0;
+    if (valid) inv_pre(slots, g, kind, n, A.tw, [&](int i) -> Real { return realref(coef, g, line, i); });
+    __syncthreads();
+    if (dct4) res = fft_run<T, EMAX, false, POW2>(slots, coef, g, A.st, A.nst, A.tw, nullptr);
+    else res = fft_run<T, EMAX, true, POW2>(slots, coef, g, A.st, A.nst, A.tw, nullptr);
+    if (!valid) return;
+    // I3: normalise and store
+    const Real scale = A.out_scale;
+    store_line<Real, EMAX>(A, g, base, n, [&](int, int i) -> Real { return inv_out(res, g, kind, n, A.tw, i) * scale; });
   }
 }
 

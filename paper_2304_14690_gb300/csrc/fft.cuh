@@ -15,6 +15,16 @@
 //   Dir-Dir     DST-II / DST-III (DCT-II of the sign-alternated line, reversed)
 //   Neu-Dir     DCT-IV (self-inverse up to 2/n), half-length complex FFT with pre/post twiddles
 //   Dir-Neu     DST-IV (DCT-IV of the reversed line with alternating output signs)
+// The vertex (regular) grid of §2.3 has its own transforms, on lines of unknowns at the lattice
+// vertices (m cells along the axis):
+//   Neu-Neu     DCT-I of the m+1 unknowns: the real DFT of length 2m of their even extension,
+//               formed in shared memory (M = m); the spectrum is real, X_k = Re V_k
+//   Dir-Dir     DST-I of the m-1 unknowns: the real DFT of their odd extension (M = m); the
+//               spectrum is imaginary, X_{k-1} = -Im V_k
+//   Neu-Dir     quarter-wave cosine basis cos(pi (k + 1/2) j/m): its analysis is the DCT-III
+//               and its synthesis the DCT-II of length m, the cell grid's Neu-Neu pair run in
+//               the other order (M = m/2)
+//   Dir-Neu     quarter-wave sine basis, likewise the cell grid's Dir-Dir pair in the other order
 // The FFT is a mixed-radix Stockham autosort (radices 16, 8, 4, 2, 3, 5) between two shared
 // buffers: every stage reads its butterflies' inputs from one buffer into registers and writes
 // the outputs to the other, one barrier per stage. The radix-8 and radix-16 butterflies run in
@@ -280,6 +290,18 @@ __device__ __forceinline__ void fwd_slot_of(int kind, int n, int j, int &q, int 
   if (kind == KIND_DN) comp ^= 1;
 }
 
+// F1 of the vertex DCT-I / DST-I: input x_j (unknown j of the line) enters the real line of
+// length 2M at its own position and at the mirrored one (even extension for DCT-I, odd for DST-I,
+// whose unknown j is vertex j + 1). The caller writes the two zeros of the odd extension.
+template <typename T>
+__device__ __forceinline__ void ext_scatter(T *buf, const TileGeom &g, int line, int kind, int j,
+                                            decltype(T::x) x) {
+  const int M = g.M;
+  const int r = (kind == KIND_VDD) ? j + 1 : j;
+  realref(buf, g, line, r) = x;
+  if (r > 0 && r < M) realref(buf, g, line, 2 * M - r) = (kind == KIND_VDD) ? -x : x;
+}
+
 // F4: FFT output (slots of buf) -> real spectral coefficients in natural order, handed to
 // emit(position, value). A thread reads only the slots of its own outputs.
 template <typename T, typename Emit>
@@ -310,6 +332,11 @@ __device__ __forceinline__ void fwd_post(const T *buf, const TileGeom &g, int ki
       if (kind == KIND_PP) {
         emit(0, V0);
         emit(1, VM);
+      } else if (kind == KIND_VNN) {
+        emit(0, V0);
+        emit(M, VM);
+      } else if (kind == KIND_VDD) {
+        // V_0 = V_M = 0 for an odd extension: no coefficient
       } else {
         const T tM = cscale(ldg(&wq[M]), VM);
         emit(dd ? n - 1 : 0, V0);
@@ -334,6 +361,14 @@ __device__ __forceinline__ void fwd_post(const T *buf, const TileGeom &g, int ki
         emit(2 * km, Vm.x);
         emit(2 * km + 1, Vm.y);
       }
+    } else if (kind == KIND_VNN) {
+      // even extension: V_k real, the DCT-I coefficient k
+      emit(k, Vk.x);
+      if (km != k) emit(km, Vm.x);
+    } else if (kind == KIND_VDD) {
+      // odd extension: V_k = -i X, the DST-I coefficient of sin(pi k j/M) stored at k - 1
+      emit(k - 1, -Vk.y);
+      if (km != k) emit(km - 1, -Vm.y);
     } else {
       // DCT-II (DST-II by reversal): t_k = e^{-i pi k/(2n)} V_k; X_k = Re t_k, X_{n-k} = -Im t_k
       const T tk = cmul(Vk, ldg(&wq[k]));
@@ -385,6 +420,12 @@ __device__ __forceinline__ void inv_pre(T *buf, const TileGeom &g, int kind, int
       if (kind == KIND_PP) {
         a = fetch(0);   // X_0
         b = fetch(1);   // X_M
+      } else if (kind == KIND_VNN) {
+        a = fetch(0);
+        b = fetch(M);
+      } else if (kind == KIND_VDD) {
+        a = (R)0;
+        b = (R)0;
       } else {
         a = X(0);
         b = V(M).x;     // real: sqrt(2) X_M
@@ -397,6 +438,12 @@ __device__ __forceinline__ void inv_pre(T *buf, const TileGeom &g, int kind, int
     if (kind == KIND_PP) {
       xk = cmk<T>(fetch(2 * k), fetch(2 * k + 1));
       xm = cmk<T>(fetch(2 * km), fetch(2 * km + 1));
+    } else if (kind == KIND_VNN) {   // the real, even spectrum of the even extension
+      xk = cmk<T>(fetch(k), (R)0);
+      xm = cmk<T>(fetch(km), (R)0);
+    } else if (kind == KIND_VDD) {   // the imaginary, odd spectrum of the odd extension
+      xk = cmk<T>((R)0, -fetch(k - 1));
+      xm = cmk<T>((R)0, -fetch(km - 1));
     } else {
       xk = V(k);
       xm = V(km);
@@ -418,9 +465,10 @@ template <typename T>
 __device__ __forceinline__ decltype(T::x) inv_out(const T *buf, const TileGeom &g, int kind, int n, const T *tw,
                                                   int i) {
   const int base = g.line * g.ls;
-  if (kind == KIND_PP) {
-    const T z = buf[base + (i >> 1) * g.es];
-    return (i & 1) ? z.y : z.x;
+  if (kind == KIND_PP || kind == KIND_VNN || kind == KIND_VDD) {
+    const int r = (kind == KIND_VDD) ? i + 1 : i;   // position in the (extended) real line
+    const T z = buf[base + (r >> 1) * g.es];
+    return (r & 1) ? z.y : z.x;
   }
   if (kind == KIND_NN || kind == KIND_DD) {
     const int j = (i & 1) ? (n - 1 - (i >> 1)) : (i >> 1);
@@ -436,7 +484,8 @@ __device__ __forceinline__ decltype(T::x) inv_out(const T *buf, const TileGeom &
 }
 
 // Normalisation of every inverse: 1/M of the half-length inverse FFT for the real DFT and
-// DCT-III/DST-III wrappers, 2/n for DCT-IV/DST-IV; both equal 2/n.
-__host__ __device__ inline double inv_scale(int, int n) { return 2.0 / n; }
+// DCT-III/DST-III wrappers, 2/n = 1/M for DCT-IV/DST-IV; 1/M too for the vertex transforms (the
+// real DFT of the length-2M extension, and the quarter-wave pairs of length 2M).
+__host__ __device__ inline double inv_scale(int M) { return 1.0 / M; }
 
 }  // namespace pc

@@ -74,18 +74,30 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
                      size_t &smem, int batch_threads);
 // Single-problem FP32 pass of transform family 0 (real DFT), 1 (DCT-II/DST-II) or 2
 // (DCT-IV/DST-IV), each compiled in its own translation unit (pass_f32_family*.cu), and the
-// shared-memory attributes of their kernel instances.
+// shared-memory attributes of their kernel instances. Families 3 and 4 (vertex grids) have
+// their own unit.
 pc_status launch_pass_f32_family0(const PassArgs<float> &A, long long tiles, int threads, size_t smem, cudaStream_t st);
 pc_status launch_pass_f32_family1(const PassArgs<float> &A, long long tiles, int threads, size_t smem, cudaStream_t st);
 pc_status launch_pass_f32_family2(const PassArgs<float> &A, long long tiles, int threads, size_t smem, cudaStream_t st);
 pc_status prepare_pass_f32_family0(int lim);
 pc_status prepare_pass_f32_family1(int lim);
 pc_status prepare_pass_f32_family2(int lim);
+// Passes along vertex-grid axes (families 3 and 4, pass_vertex.cu), FP32 and FP64.
+pc_status launch_pass_vertex_f32(const PassArgs<float> &A, long long tiles, int threads, size_t smem, cudaStream_t st);
+pc_status launch_pass_vertex_f64(const PassArgs<double> &A, long long tiles, int threads, size_t smem, cudaStream_t st);
+pc_status prepare_pass_vertex(int lim);
 // Batched FP32 pass over a work list of (args index, first tile, tiles) items of any family,
 // length and dimension (one launch per pass for a whole batch, one CTA per item).
 pc_status launch_batched_f32(const PassArgs<float> *dargs, const int4 *ditems, int nitems, int threads, size_t smem,
                              int emax, cudaStream_t st);
 pc_status prepare_batched_f32(int lim);
-__host__ __device__ inline int pass_family(int kind) { return kind == KIND_PP ? 0 : ((kind == KIND_NN || kind == KIND_DD) ? 1 : 2); }
+// Transform family of a kind: 0 real DFT, 1 DCT-II/DST-II, 2 DCT-IV/DST-IV, 3 vertex DCT-I/DST-I,
+// 4 vertex quarter-wave bases.
+__host__ __device__ inline int pass_family(int kind) {
+  if (kind == KIND_PP) return 0;
+  if (kind == KIND_NN || kind == KIND_DD) return 1;
+  if (kind == KIND_ND || kind == KIND_DN) return 2;
+  return (kind == KIND_VNN || kind == KIND_VDD) ? 3 : 4;
+}
 
 }  // namespace pc

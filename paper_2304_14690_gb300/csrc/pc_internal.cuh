@@ -11,7 +11,10 @@ namespace pc {
 
 // Transform kind of one axis, from its boundary pair (§2.3: the transform follows the grid
 // type and the boundary conditions).
-enum AxisKind { KIND_PP = 0, KIND_NN = 1, KIND_DD = 2, KIND_ND = 3, KIND_DN = 4 };
+// Transform kind of an axis: its boundary pair on the cell grid (0-4), or on the vertex grid
+// (5-8; a vertex P-P axis is KIND_PP): DCT-I, DST-I and the two quarter-wave bases.
+enum AxisKind { KIND_PP = 0, KIND_NN = 1, KIND_DD = 2, KIND_ND = 3, KIND_DN = 4,
+                KIND_VNN = 5, KIND_VDD = 6, KIND_VND = 7, KIND_VDN = 8 };
 
 constexpr int kMaxRadices = 24;
 constexpr int kMaxK = 32;
@@ -24,8 +27,9 @@ enum DeviceFlag { FLAG_WLS_SINGULAR = 1, FLAG_KNN_SHORT = 2, FLAG_NONFINITE = 4 
 
 struct AxisInfo {
   int kind = 0;
-  int n = 0;        // cells
-  int M = 0;        // complex FFT length n/2
+  int n = 0;        // pressure points along the axis: cells, or vertex unknowns
+  int M = 0;        // complex FFT length: n/2 (cell kinds, quarter-wave vertex kinds), the
+                    // vertex cells m for DCT-I (n = m + 1) and DST-I (n = m - 1)
   // Slots per thread of the transform passes along this axis, per precision (powers of two):
   // they fix the threads per line and the radix schedule (see build_pass), chosen when the
   // plan is built and shared by single and batched calls.
@@ -252,7 +256,6 @@ struct Plan {
   long long npts = 0;            // pressure points with direct-divergence rows (cells or unknowns)
   double phys_L[3] = {1.0, 1.0, 1.0};   // the physical box (a vertex plan's axes hold the extension)
   int phys_periodic[3] = {0, 0, 0};
-  double *vstage = nullptr;      // vertex plans: [2][unknowns], source and host staging of p
   int32_t *ccol = nullptr;     // direct divergence: [K][cells] node index
   double *cD64 = nullptr;      //   [dim][K][cells] derivative-row weights (FP64 plans)
   float2 *cD2 = nullptr;       //   (hi, lo) pairs (mixed and FP32 plans)
@@ -337,7 +340,10 @@ struct GridDev {
   int cs[3];          // cell strides
   int fs[3][3];       // fs[a][b]: stride of axis b in the face array of axis a
   int periodic[3];
-  int lo_kind[3], hi_kind[3];   // 0 Neumann, 1 Dirichlet (ghost sign), ignored when periodic
+  // ghost rule at each end, ignored when periodic: 0 Neumann (ghost = edge value), 1 Dirichlet
+  // (ghost = -edge value; cell grids), 2 Neumann about a vertex (ghost = the next value inward),
+  // 3 Dirichlet vertex (ghost = 0; vertex grids)
+  int lo_kind[3], hi_kind[3];
   double inv_h[3], inv_h2[3];
   float ih2_hi[3], ih2_lo[3];   // inv_h2 as an FP32 pair (double-float residual)
   // cell tiles of the cell kernels (project.cu): rows of the last axis, tile width 2^tw_bits,

@@ -40,26 +40,41 @@ static int ilog2(int v) {
   return b;
 }
 
-bool axis_length_supported(int n) {
-  if (n < 2 || (n & 1)) return false;
-  int m = n / 2;
+// A complex FFT length the passes take: 2^a 3^b 5^c, at most 2048.
+static bool fft_length_supported(int M) {
+  if (M < 2 || M > 2048) return false;
+  int m = M;
   for (int r : {2, 3, 5}) while (m % r == 0) m /= r;
-  return m == 1 && n / 2 <= 2048;
+  return m == 1;
+}
+
+bool axis_length_supported(int n) { return n >= 2 && (n & 1) == 0 && fft_length_supported(n / 2); }
+
+int fft_length_of(int kind, int n) {
+  if (kind == KIND_VNN) return n - 1;   // DCT-I of m + 1 unknowns: real DFT of length 2m
+  if (kind == KIND_VDD) return n + 1;   // DST-I of m - 1 unknowns: real DFT of length 2m
+  return n / 2;
+}
+
+bool vertex_axis_supported(int kind, int m) {
+  if (kind == KIND_VNN || kind == KIND_VDD) return fft_length_supported(m);
+  return axis_length_supported(m);   // P-P and the quarter-wave pairs: length m, m even
 }
 
 pc_status build_axis_tables(Plan *p) {
   for (int a = 0; a < p->dim; ++a) {
     AxisInfo &ax = p->ax[a];
-    const int n = ax.n, M = n / 2;
+    const int n = ax.n, M = fft_length_of(ax.kind, n);
+    const int nt = 2 * M;   // length of the real transform the FFT serves (n for cell kinds)
     ax.M = M;
     std::vector<double2> tw(tw_total(M));
     auto put = [&](int off, int k, double ang) { tw[off + k] = make_double2(std::cos(ang), std::sin(ang)); };
     const double pi = 3.14159265358979323846;
     for (int k = 0; k < M; ++k) put(0, k, -2.0 * pi * k / M);
-    for (int k = 0; k <= M; ++k) put(tw_rdft(M), k, -2.0 * pi * k / n);
-    for (int k = 0; k <= M; ++k) put(tw_quarter(M), k, -pi * k / (2.0 * n));
-    for (int k = 0; k < M; ++k) put(tw_dct4pre(M), k, -pi * (4.0 * k + 1.0) / (4.0 * n));
-    for (int k = 0; k < M; ++k) put(tw_dct4post(M), k, -pi * k / (double)n);
+    for (int k = 0; k <= M; ++k) put(tw_rdft(M), k, -2.0 * pi * k / nt);
+    for (int k = 0; k <= M; ++k) put(tw_quarter(M), k, -pi * k / (2.0 * nt));
+    for (int k = 0; k < M; ++k) put(tw_dct4pre(M), k, -pi * (4.0 * k + 1.0) / (4.0 * nt));
+    for (int k = 0; k < M; ++k) put(tw_dct4post(M), k, -pi * k / (double)nt);
     std::vector<float2> tw32(tw.size());
     for (size_t i = 0; i < tw.size(); ++i) tw32[i] = make_float2((float)tw[i].x, (float)tw[i].y);
     // eigenvalues per spectral index with the angle theta of each basis vector (th = theta/2):
@@ -77,7 +92,11 @@ pc_status build_axis_tables(Plan *p) {
         }
         case KIND_NN: th = pi * m / (2.0 * n); break;
         case KIND_DD: th = pi * (m + 1.0) / (2.0 * n); break;
-        default: th = pi * (2.0 * m + 1.0) / (4.0 * n); break;
+        // vertex grids: M cells on DCT-I / DST-I axes, basis cos(pi k j/M) and sin(pi (k+1) j/M)
+        // for coefficient k; n cells on quarter-wave axes, theta = pi (k + 1/2)/n
+        case KIND_VNN: th = pi * m / (2.0 * M); break;
+        case KIND_VDD: th = pi * (m + 1.0) / (2.0 * M); break;
+        default: th = pi * (2.0 * m + 1.0) / (4.0 * n); break;   // ND, DN, VND, VDN
       }
       double s = std::sin(th);
       lam[m] = p->eigen == PC_EIG_SPECTRAL ? -(2.0 * th / ax.h) * (2.0 * th / ax.h) : c * s * s;
@@ -182,7 +201,7 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   A.src = src;
   A.dst_mode = dst_mode;
   A.dst = dst;
-  A.out_scale = (Real)inv_scale(ax.kind, ax.n);
+  A.out_scale = (Real)inv_scale(ax.M);
   A.f64 = ps.f64;
   A.gate = ps.gate;
   A.chunk = ps.chunk > 1 ? ps.chunk : 1;
@@ -212,10 +231,12 @@ static pc_status launch_pass(Plan *p, const PassSpec &ps, cudaStream_t st) {
     switch (pass_family(A.kind)) {
       case 0: PC_TRY(launch_pass_f32_family0(A, tiles, threads, smem, st)); break;
       case 1: PC_TRY(launch_pass_f32_family1(A, tiles, threads, smem, st)); break;
-      default: PC_TRY(launch_pass_f32_family2(A, tiles, threads, smem, st)); break;
+      case 2: PC_TRY(launch_pass_f32_family2(A, tiles, threads, smem, st)); break;
+      default: PC_TRY(launch_pass_vertex_f32(A, tiles, threads, smem, st)); break;
     }
   } else {
-    PC_TRY((launch_axis_pass_spec<Real, -1, false>(A, tiles, threads, smem, st)));
+    if (pass_family(A.kind) >= 3) PC_TRY(launch_pass_vertex_f64(A, tiles, threads, smem, st));
+    else PC_TRY((launch_axis_pass_spec<Real, -1, false>(A, tiles, threads, smem, st)));
   }
   count_launch(p);
   return PC_OK;
@@ -227,6 +248,7 @@ pc_status prepare_kernels() {
   PC_TRY(prepare_pass_f32_family0(lim));
   PC_TRY(prepare_pass_f32_family1(lim));
   PC_TRY(prepare_pass_f32_family2(lim));
+  PC_TRY(prepare_pass_vertex(lim));
   PC_TRY(prepare_batched_f32(lim));
   PC_TRY((prepare_axis_pass_spec<double, -1, false>(lim)));
   return PC_OK;

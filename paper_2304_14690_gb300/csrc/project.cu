@@ -432,28 +432,52 @@ __global__ void direct_div_kernel(int nc, int K, const int32_t *__restrict__ col
 }
 
 // ----------------------------------------------------------------------------- flat kernels
-// Sum and sum of squares of a cell array (the source of pc_solve_poisson), and its mean.
+// Weights of the mean of a vertex grid with N-N axes: the DCT-I basis is orthogonal in the
+// trapezoid inner product (weight 1/2 at both end vertices of each such axis), so the part of
+// the source outside the range of the operator (the compatibility constant) and the constant
+// part of a solution are means in those weights. dim = 0: unit weights (cell grids).
+struct TrapWeights {
+  int dim;
+  int n[3];      // points per axis (C order, last axis fastest)
+  int trap[3];   // 1: N-N vertex axis
+  double total;  // sum of the weights
+};
+__device__ __forceinline__ double trap_weight(const TrapWeights &w, long long c) {
+  double wt = 1.0;
+  for (int a = w.dim - 1; a >= 0; --a) {
+    const long long q = c / w.n[a];
+    const int i = (int)(c - q * w.n[a]);
+    c = q;
+    if (w.trap[a] && (i == 0 || i == w.n[a] - 1)) wt *= 0.5;
+  }
+  return wt;
+}
+
+// Sum (weighted, see TrapWeights) and sum of squares of a cell array (the source of
+// pc_solve_poisson), and its mean.
 __device__ __forceinline__ void sum_kernel_body(unsigned b, unsigned nblk, long long count, const double *x,
-                                                DevStats *stats, double *partials, unsigned int *counter) {
+                                                DevStats *stats, double *partials, unsigned int *counter,
+                                                const TrapWeights &w) {
   double v1 = 0.0, v2 = 0.0;
 #pragma unroll
   for (int k = 0; k < kFlatPerThread; ++k) {
     const long long c = (long long)b * kFlatPerBlock + k * kFlatThreads + threadIdx.x;
     if (c < count) {
       const double v = x[c];
-      v1 += v;
+      v1 += w.dim ? trap_weight(w, c) * v : v;
       v2 = fma(v, v, v2);
     }
   }
   const VBlock vb{b, 0u, 0u, nblk, 1u, 1u};
-  if (grid_sum(v1, partials, counter, &stats->sum_s, vb)) stats->mean_s = stats->sum_s / (double)count;
+  if (grid_sum(v1, partials, counter, &stats->sum_s, vb))
+    stats->mean_s = stats->sum_s / (w.dim ? w.total : (double)count);
   grid_sum(v2, partials + nblk, counter + 1, &stats->sum_s2, vb);
 }
 
 __global__ void sum_kernel(long long count, const double *x, DevStats *stats, double *partials,
-                           unsigned int *counter) {
+                           unsigned int *counter, TrapWeights w) {
   pdl_enter();
-  sum_kernel_body(blockIdx.x, gridDim.x, count, x, stats, partials, counter);
+  sum_kernel_body(blockIdx.x, gridDim.x, count, x, stats, partials, counter, w);
 }
 
 // ----------------------------------------------------------------------------- residual
@@ -475,6 +499,15 @@ __device__ __forceinline__ void neighbours(const GridDev &g, const double *p, co
 __device__ __forceinline__ DF to_df(double v) { return df_of(v); }
 __device__ __forceinline__ DF to_df(float2 v) { return DF{v.x, v.y}; }
 __device__ __forceinline__ DF df_neg_(DF a) { return DF{-a.hi, -a.lo}; }
+// Ghost value beyond a non-periodic end (GridDev lo_kind / hi_kind): from the edge value dc, or
+// the value at inner (the next point inward, which the end mirrors on a vertex grid).
+template <typename PV>
+__device__ __forceinline__ DF ghost_df(int kind, DF dc, const PV *__restrict__ p, int inner) {
+  if (kind == 0) return dc;
+  if (kind == 1) return df_neg_(dc);
+  if (kind == 2) return to_df(p[inner]);
+  return DF{0.0f, 0.0f};
+}
 
 // r = s - mean(s) - L_h p, evaluated in double-float arithmetic (about 48 significant bits:
 // the FP64 pipe of this GPU runs at 1/64 of the FP32 rate) and stored as FP32 for the next
@@ -538,15 +571,16 @@ __device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, cons
       DF acc{0.0f, 0.0f};
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
-        // neighbours with the ghost rules: Neumann p_ghost = p_edge, Dirichlet -p_edge, periodic wrap
+        // neighbours with the ghost rules: Neumann p_ghost = p_edge, Dirichlet -p_edge (cell
+        // grids), the next value inward (Neumann about a vertex), 0 (Dirichlet vertex), periodic wrap
         const int st = g.cs[a];
         DF pl, pr;
         if (i[a] > 0) pl = to_df(p[c - st]);
         else if (g.periodic[a]) pl = to_df(p[c + (g.n[a] - 1) * st]);
-        else pl = g.lo_kind[a] ? df_neg_(dc) : dc;
+        else pl = ghost_df(g.lo_kind[a], dc, p, c + st);
         if (i[a] < g.n[a] - 1) pr = to_df(p[c + st]);
         else if (g.periodic[a]) pr = to_df(p[c - (g.n[a] - 1) * st]);
-        else pr = g.hi_kind[a] ? df_neg_(dc) : dc;
+        else pr = ghost_df(g.hi_kind[a], dc, p, c - st);
         const DF t = df_add(df_sub(pl, dc), df_sub(pr, dc));
         acc = df_add(acc, df_mul(t, DF{g.ih2_hi[a], g.ih2_lo[a]}));
       }
@@ -585,28 +619,30 @@ __global__ void residual_kernel(GridDev g, const SV *__restrict__ s, const PV *_
 }
 
 // ----------------------------------------------------------------------------- gauge
-// Sum of p (and the corner value); the reducing block stores the gauge constant.
+// Sum of p (weighted, see TrapWeights; and the corner value); the reducing block stores the
+// gauge constant.
 __device__ __forceinline__ void gauge_sum_body(unsigned b, unsigned nblk, long long ncells, const double *p,
                                                DevStats *stats, double *partials, unsigned int *counter,
-                                               int gauge_mode) {
+                                               int gauge_mode, const TrapWeights &w) {
   DF acc{0.0f, 0.0f};
 #pragma unroll
   for (int k = 0; k < kFlatPerThread; ++k) {
     const long long c = (long long)b * kFlatPerBlock + k * kFlatThreads + threadIdx.x;
     if (c < ncells) {
-      const double v = p[c];
+      double v = p[c];
       if (c == 0) stats->corner_p = v;
+      if (w.dim) v *= trap_weight(w, c);   // a power of two: exact
       acc = df_add(acc, df_of(v));
     }
   }
   if (grid_sum(f2d_bits(acc.hi) + f2d_bits(acc.lo), partials, counter, &stats->sum_p, VBlock{b, 0u, 0u, nblk, 1u, 1u}))
-    stats->shift = (gauge_mode == 1) ? stats->sum_p / (double)ncells : p[0];
+    stats->shift = (gauge_mode == 1) ? stats->sum_p / (w.dim ? w.total : (double)ncells) : p[0];
 }
 
 __global__ void gauge_sum_kernel(long long ncells, const double *p, DevStats *stats, double *partials,
-                                 unsigned int *counter, int gauge_mode) {
+                                 unsigned int *counter, int gauge_mode, TrapWeights w) {
   pdl_enter();
-  gauge_sum_body(blockIdx.x, gridDim.x, ncells, p, stats, partials, counter, gauge_mode);
+  gauge_sum_body(blockIdx.x, gridDim.x, ncells, p, stats, partials, counter, gauge_mode, w);
 }
 
 // p -= shift (gauge), and the (hi, lo) FP32 split of p for the compensated gradient.
@@ -914,44 +950,14 @@ __global__ void ib_guard_kernel(IbCtl *ctl, int max_iters, cudaGraphConditionalH
 }
 
 // ----------------------------------------------------------------------------- vertex grids
-// A vertex grid is solved as the periodic cell grid of its symmetric extension (grid-only
-// plans): the source is extended evenly about Neumann ends and oddly about Dirichlet ends, the
-// extended solution is restricted to the vertex unknowns. The real DFT of such an extension is
-// the DCT-I, DST-I or quarter-wave transform of the vertex values.
+// A vertex grid is solved on its unknowns with the vertex transforms (DCT-I, DST-I, the
+// quarter-wave bases; fft.cuh). The gradient of a pass reads p on the whole lattice, where a
+// Dirichlet boundary vertex holds its known value 0.
 struct VertexGrid {
   int dim;
-  int kind[3], n[3], m[3], nv[3];   // boundary pair, vertex-grid cells, extended length, unknowns
+  int nv[3];                        // unknowns per axis
   int j0[3], nf[3];                 // lattice index of the first unknown, lattice vertices
 };
-// The vertex unknown held by extended cell e of an axis, with its sign, or -1 where the
-// extension is zero (a Dirichlet end).
-__device__ __forceinline__ int vertex_fold(int kind, int n, int e, double &sign) {
-  sign = 1.0;
-  switch (kind) {
-    case KIND_PP: return e;
-    case KIND_NN: return e <= n ? e : 2 * n - e;
-    case KIND_DD:
-      if (e == 0 || e == n) return -1;
-      if (e < n) return e - 1;
-      sign = -1.0;
-      return 2 * n - e - 1;
-    case KIND_ND:   // even about 0, odd about n: period 4n
-      if (e < n) return e;
-      if (e == n || e == 3 * n) return -1;
-      sign = -1.0;
-      if (e <= 2 * n) return 2 * n - e;
-      if (e < 3 * n) return e - 2 * n;
-      sign = 1.0;
-      return 4 * n - e;
-    default:        // KIND_DN: odd about 0, even about n
-      if (e == 0 || e == 2 * n) return -1;
-      if (e <= n) return e - 1;
-      if (e < 2 * n) return 2 * n - e - 1;
-      sign = -1.0;
-      if (e <= 3 * n) return e - 2 * n - 1;
-      return 4 * n - e - 1;
-  }
-}
 // Both kernels run on a grid whose x covers the last axis and whose y (and z) are the indices of
 // the other axes, so no thread divides to find its position.
 __device__ __forceinline__ void grid_position(int dim, int *idx) {
@@ -959,51 +965,27 @@ __device__ __forceinline__ void grid_position(int dim, int *idx) {
   idx[dim - 2] = blockIdx.y;
   if (dim == 3) idx[0] = blockIdx.z;
 }
-__global__ void vertex_extend_kernel(VertexGrid V, const double *__restrict__ sv, double *__restrict__ se) {
-  pdl_enter();
-  int idx[3];
-  grid_position(V.dim, idx);
-  if (idx[V.dim - 1] >= V.m[V.dim - 1]) return;
-  int e = 0, u = 0;
-  bool zero = false, neg = false;
-  for (int a = 0; a < V.dim; ++a) {
-    double sa;
-    const int ua = vertex_fold(V.kind[a], V.n[a], idx[a], sa);
-    e = e * V.m[a] + idx[a];
-    if (ua < 0) zero = true;
-    else {
-      u = u * V.nv[a] + ua;
-      neg ^= sa < 0.0;
-    }
-  }
-  double v = zero ? 0.0 : sv[u];
-  se[e] = neg ? -v : v;
-}
-// The extended solution on the vertex lattice (vertex j of an axis is extended cell j), less the
-// gauge constant of the extension (stats->shift, zeroed with the statistics of every call). Writes
-// any of: the unknowns (pv), the whole lattice in FP64 (pl, Dirichlet boundary vertices exactly
-// 0) and as FP32 (hi, lo) pairs (pl2) for the compensated gradient.
-__global__ void vertex_restrict_kernel(VertexGrid V, const double *__restrict__ pe, const DevStats *stats,
-                                       double *__restrict__ pv, double *__restrict__ pl, float2 *__restrict__ pl2) {
+// p at the unknowns (pv) -> p on the lattice in FP64 (pl) and as FP32 (hi, lo) pairs (pl2) for
+// the compensated gradient; Dirichlet boundary vertices are exactly 0.
+__global__ void vertex_embed_kernel(VertexGrid V, const double *__restrict__ pv, double *__restrict__ pl,
+                                    float2 *__restrict__ pl2) {
   pdl_enter();
   int idx[3];
   grid_position(V.dim, idx);
   if (idx[V.dim - 1] >= V.nf[V.dim - 1]) return;
-  int e = 0, u = 0, l = 0;
+  int u = 0, l = 0;
   bool unknown = true;
   for (int a = 0; a < V.dim; ++a) {
-    e = e * V.m[a] + idx[a];
     l = l * V.nf[a] + idx[a];
     const int ua = idx[a] - V.j0[a];
     if (ua < 0 || ua >= V.nv[a]) unknown = false;   // a Dirichlet boundary vertex
     u = u * V.nv[a] + (ua < 0 ? 0 : ua);
   }
-  const double v = unknown ? pe[e] - stats->shift : 0.0;   // the gauge of the extension (0 without one)
-  if (pv && unknown) pv[u] = v;
+  const double v = unknown ? pv[u] : 0.0;
   if (pl) pl[l] = v;
   if (pl2) pl2[l] = as_pair(v);
 }
-// Launch shapes of the two kernels: x over the last axis, y and z over the others.
+// Launch shape: x over the last axis, y and z over the others.
 static dim3 vertex_grid_dims(int dim, const int *shape, int threads) {
   return dim3((unsigned)((shape[dim - 1] + threads - 1) / threads), (unsigned)shape[dim - 2],
               dim == 3 ? (unsigned)shape[0] : 1u);
@@ -1015,14 +997,33 @@ static VertexGrid vertex_grid(const Plan *p) {
   VertexGrid V{};
   V.dim = p->dim;
   for (int a = 0; a < 3; ++a) {
-    V.kind[a] = p->vkind[a];
-    V.n[a] = p->vn[a];
-    V.m[a] = a < p->dim ? p->ax[a].n : 1;
     V.nv[a] = p->nv[a];
     V.j0[a] = p->vj0[a];
     V.nf[a] = p->nf[a];
   }
   return V;
+}
+
+// Mean weights of a plan: trapezoid weights on the N-N axes of a vertex grid, else unit.
+static TrapWeights trap_weights(const Plan *p) {
+  TrapWeights w{};
+  if (!p->vertex) return w;
+  double total = 1.0;
+  bool any = false;
+  for (int a = 0; a < p->dim; ++a) {
+    w.n[a] = p->ax[a].n;
+    w.trap[a] = p->ax[a].kind == KIND_VNN;
+    any |= w.trap[a] != 0;
+    total *= w.trap[a] ? (double)(w.n[a] - 1) : (double)w.n[a];
+  }
+  if (!any) return TrapWeights{};
+  w.dim = p->dim;
+  w.total = total;
+  return w;
+}
+static double mean_weight_total(const Plan *p) {
+  const TrapWeights w = trap_weights(p);
+  return w.dim ? w.total : (double)p->ncells;
 }
 
 
@@ -1116,7 +1117,8 @@ __global__ void batch_gauge_sum(const BatchProblem *__restrict__ P, const int *_
   pdl_enter();
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
-  gauge_sum_body(blockIdx.x - seg[pi], seg[pi + 1] - seg[pi], q.ncells, q.p, q.ds, q.partials, q.counters, q.gmode);
+  gauge_sum_body(blockIdx.x - seg[pi], seg[pi + 1] - seg[pi], q.ncells, q.p, q.ds, q.partials, q.counters, q.gmode,
+                 TrapWeights{});
 }
 
 __global__ void batch_finalize(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
@@ -1214,8 +1216,15 @@ static GridDev grid_dev(const Plan *p) {
       g.n[a] = ax.n;
       g.nf[a] = ax.nfaces;
       g.periodic[a] = ax.periodic;
-      g.lo_kind[a] = ax.bc_lo == PC_BC_DIRICHLET;
-      g.hi_kind[a] = ax.bc_hi == PC_BC_DIRICHLET;
+      switch (ax.kind) {   // vertex grids: 2 mirror about the end vertex, 3 the known zero
+        case KIND_VNN: g.lo_kind[a] = 2; g.hi_kind[a] = 2; break;
+        case KIND_VDD: g.lo_kind[a] = 3; g.hi_kind[a] = 3; break;
+        case KIND_VND: g.lo_kind[a] = 2; g.hi_kind[a] = 3; break;
+        case KIND_VDN: g.lo_kind[a] = 3; g.hi_kind[a] = 2; break;
+        default:
+          g.lo_kind[a] = ax.bc_lo == PC_BC_DIRICHLET;
+          g.hi_kind[a] = ax.bc_hi == PC_BC_DIRICHLET;
+      }
       g.inv_h[a] = 1.0 / ax.h;
       g.inv_h2[a] = 1.0 / (ax.h * ax.h);
       g.ih2_hi[a] = (float)g.inv_h2[a];
@@ -1294,14 +1303,12 @@ static void launch_residual(bool singular, bool write_r, bool norm, cudaStream_t
 // s2 (nullable): the source as (hi, lo) pairs (projections); otherwise s64 in FP64
 // (pc_solve_poisson). FP32 solves keep the refinement iterate in p->p2 as (hi, lo) pairs, read
 // by the residual and the gradient; the last solve also writes p in FP64 to pout.
-// Gauge of the solved p: 0 none, 1 zero mean, 2 zero first cell. Problems with a zero mode take
-// the plan's gauge. The periodic extension of a vertex problem without one (an odd extension on
-// some axis) has an exactly mean-free solution; its mean is removed all the same, since the
-// refinement cannot correct the mean that FP32 rounding leaves (L_h of a constant is zero) and
-// that offset would break the odd symmetry the restriction relies on.
+// Gauge of the solved p: 0 none, 1 zero mean (trapezoid-weighted on the N-N axes of a vertex
+// grid: no constant part in the DCT-I expansion), 2 zero first point. Problems with a zero mode
+// take the plan's gauge: the refinement cannot correct the constant that FP32 rounding leaves
+// (L_h of a constant is zero).
 static int gauge_mode(const Plan *p) {
   if (!p->singular) return 0;
-  if (p->vertex && !p->problem_singular) return 1;
   return p->gauge == 1 ? 2 : 1;
 }
 
@@ -1373,13 +1380,14 @@ static pc_status solve_grid(Plan *p, const double *s64, double *pout, bool want_
   // gauge, then the FP32 split of p for the mixed gradient
   const int gmode = gauge_mode(p);
   if (gmode) {
-    launch_pdl(gauge_sum_kernel, grid_for(nc, kFlatPerBlock), T, 0, st, nc, pout, p->dstats, p->partials, p->counters, gmode);
+    launch_pdl(gauge_sum_kernel, grid_for(nc, kFlatPerBlock), T, 0, st, nc, pout, p->dstats, p->partials, p->counters,
+               gmode, trap_weights(p));
     count_launch(p);
   }
   bool mixed = p->precision != PC_PREC_FP64;
-  if (gmode && !p->vertex) {   // a vertex plan's restriction subtracts the shift itself
+  if (gmode) {   // a vertex plan splits p on the lattice afterwards (vertex_embed_kernel)
     const int G = grid_for(nc, kFlatPerBlock);
-    if (gmode && mixed) launch_pdl(finalize_p_kernel<true, true>, G, T, 0, st, (int)nc, pout, p->dstats, p->p2);
+    if (mixed && !p->vertex) launch_pdl(finalize_p_kernel<true, true>, G, T, 0, st, (int)nc, pout, p->dstats, p->p2);
     else launch_pdl(finalize_p_kernel<true, false>, G, T, 0, st, (int)nc, pout, p->dstats, nullptr);
     count_launch(p);
   }
@@ -1393,8 +1401,8 @@ static pc_status fill_stats(Plan *p, pc_stats *stats, cudaStream_t st) {
   PC_CUDA_TRY(cudaMemcpyAsync(&ds, p->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, st));
   PC_CUDA_TRY(cudaStreamSynchronize(st));
   memset(stats, 0, sizeof(*stats));
-  const double nc = (double)p->ncells;
-  const bool zero_mode = p->vertex ? p->problem_singular : p->singular;
+  const double nc = mean_weight_total(p);   // cells, or the trapezoid weights of a vertex grid
+  const bool zero_mode = p->singular;
   stats->removed_mean = zero_mode ? ds.sum_s / nc : 0.0;
   stats->source_norm = std::sqrt(fmax(ds.sum_s2, 0.0));
   const bool adaptive = refine_adaptive(p);
@@ -1474,15 +1482,14 @@ static void launch_direct_div(Plan *p, cudaStream_t st, double inv_bdt, int want
 }
 
 // The source and solve of a pass on a vertex-grid plan: the direct divergence at the vertex
-// unknowns (FP64, into the first half of vstage), its symmetric extension (s64), the solve of
-// the periodic extension (stage_p), and the restriction to the unknowns (dp) and to the whole
-// lattice (work64 in FP64, p2 as pairs in mixed and FP32 plans), which the gradient reads.
+// unknowns (FP64, into s64), the solve on the unknowns (dp), and p on the whole lattice
+// (work64 in FP64, p2 as pairs in mixed and FP32 plans), which the gradient reads.
 static pc_status vertex_pass_solve(Plan *p, cudaStream_t st, double inv_bdt, double *dp, bool want_stats) {
   const long long nc = p->ncells, npt = p->npts;
   const bool mixed = p->precision != PC_PREC_FP64;
   const int T = 256, G = grid_for(npt, T);
   const uint8_t *mask = p->rhs_mask_on ? p->rhs_mask : nullptr;
-  double *sv = p->vstage;
+  double *sv = p->s64;
   if (p->dim == 2) {
     if (mixed) launch_pdl(direct_div_kernel<2, true>, G, T, 0, st, (int)npt, p->K, p->ccol, p->cD64, p->cD2, p->ut64, p->u2, (int)p->N, inv_bdt, mask, sv, (float2 *)nullptr, (float *)nullptr, p->dstats, p->partials, p->counters, 0, 0.0);
     else launch_pdl(direct_div_kernel<2, false>, G, T, 0, st, (int)npt, p->K, p->ccol, p->cD64, p->cD2, p->ut64, p->u2, (int)p->N, inv_bdt, mask, sv, (float2 *)nullptr, (float *)nullptr, p->dstats, p->partials, p->counters, 0, 0.0);
@@ -1491,20 +1498,18 @@ static pc_status vertex_pass_solve(Plan *p, cudaStream_t st, double inv_bdt, dou
     else launch_pdl(direct_div_kernel<3, false>, G, T, 0, st, (int)npt, p->K, p->ccol, p->cD64, p->cD2, p->ut64, p->u2, (int)p->N, inv_bdt, mask, sv, (float2 *)nullptr, (float *)nullptr, p->dstats, p->partials, p->counters, 0, 0.0);
   }
   count_launch(p);
-  const VertexGrid V = vertex_grid(p);
-  launch_pdl(vertex_extend_kernel, vertex_grid_dims(p->dim, V.m, T), T, 0, st, V, (const double *)sv, p->s64);
-  count_launch(p);
-  // the source sums: the mean the residual removes (zero-mode problems; an odd extension has
-  // mean zero) and the statistics
-  if (want_stats || p->problem_singular) {
+  // the source sums: the (weighted) mean the residual removes on zero-mode problems, and the
+  // statistics
+  if (want_stats || p->singular) {
     launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, (const double *)p->s64, p->dstats,
-               p->partials, p->counters);
+               p->partials, p->counters, trap_weights(p));
     count_launch(p);
   }
   prof_mark(p, st, 2);
-  PC_TRY(solve_grid(p, p->s64, p->stage_p, want_stats, st));
-  launch_pdl(vertex_restrict_kernel, vertex_grid_dims(p->dim, V.nf, T), T, 0, st, V, (const double *)p->stage_p,
-             (const DevStats *)p->dstats, dp, p->work64, mixed ? reinterpret_cast<float2 *>(p->p2) : (float2 *)nullptr);
+  PC_TRY(solve_grid(p, p->s64, dp, want_stats, st));
+  const VertexGrid V = vertex_grid(p);
+  launch_pdl(vertex_embed_kernel, vertex_grid_dims(p->dim, V.nf, T), T, 0, st, V, (const double *)dp, p->work64,
+             mixed ? reinterpret_cast<float2 *>(p->p2) : (float2 *)nullptr);
   count_launch(p);
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
@@ -1527,7 +1532,7 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   if ((hu || (f_in && hf) || huo || (f_out && hfo)) && !p->stage_u) PC_TRY(plan_node_staging(p));
   if (hu) { PC_CUDA_TRY(cudaMemcpyAsync(p->stage_u, u_star, vbytes, cudaMemcpyHostToDevice, st)); du = p->stage_u; }
   if (f_in && hf) { PC_CUDA_TRY(cudaMemcpyAsync(p->stage_f, f_in, vbytes, cudaMemcpyHostToDevice, st)); df = p->stage_f; }
-  if (hp) dp = p->vertex ? p->vstage + p->nvtot : p->stage_p;
+  if (hp) dp = p->stage_p;
   const long long np_out = p->vertex ? p->nvtot : nc;   // pressure values returned
   if (huo) duo = p->stage_uo;
   if (f_out && hfo) dfo = p->stage_fo;
@@ -1644,40 +1649,35 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
 // statistics): source sums, transform solve, gauge. Used by the allocation-free entry point.
 pc_status solve_grid_device(Plan *p, const double *s, double *pout, cudaStream_t st) {
   const long long nc = p->ncells;
-  launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, s, p->dstats, p->partials, p->counters);
+  launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, s, p->dstats, p->partials, p->counters,
+             TrapWeights{});
   count_launch(p);
   PC_CUDA_TRY(cudaGetLastError());
   return solve_grid(p, s, pout, false, st);
 }
 
-// pc_solve_poisson on a vertex-grid plan: extend the source, solve the periodic extension,
-// restrict the solution to the vertex unknowns.
+// pc_solve_poisson on a vertex-grid plan: the solve on the unknowns, with the trapezoid-weighted
+// mean on N-N axes.
 static pc_status vertex_solve(Plan *p, const double *s, double *p_out, pc_stats *stats, cudaStream_t st,
                               bool all_device = false) {
-  const long long nc = p->ncells, nvt = p->nvtot;
+  const long long nc = p->ncells;
   const bool hs = !all_device && !is_device_ptr(s), hp = !all_device && !is_device_ptr(p_out);
   const double *ds = s;
   double *dp = p_out;
   if (hs) {
-    PC_CUDA_TRY(cudaMemcpyAsync(p->vstage, s, nvt * sizeof(double), cudaMemcpyHostToDevice, st));
-    ds = p->vstage;
+    PC_CUDA_TRY(cudaMemcpyAsync(p->stage_s, s, nc * sizeof(double), cudaMemcpyHostToDevice, st));
+    ds = p->stage_s;
   }
-  if (hp) dp = p->vstage + nvt;
-  const VertexGrid V = vertex_grid(p);
+  if (hp) dp = p->stage_p;
   prof_begin(p, st);
   PC_CUDA_TRY(cudaMemsetAsync(p->dstats, 0, sizeof(DevStats), st));
-  vertex_extend_kernel<<<vertex_grid_dims(p->dim, V.m, 256), 256, 0, st>>>(V, ds, p->stage_s);
-  count_launch(p);
-  launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, (const double *)p->stage_s, p->dstats,
-             p->partials, p->counters);
+  launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, ds, p->dstats, p->partials,
+             p->counters, trap_weights(p));
   count_launch(p);
   prof_mark(p, st, 2);
-  PC_TRY(solve_grid(p, p->stage_s, p->stage_p, stats != nullptr, st));
-  vertex_restrict_kernel<<<vertex_grid_dims(p->dim, V.nf, 256), 256, 0, st>>>(V, p->stage_p, p->dstats, dp, nullptr,
-                                                                               nullptr);
-  count_launch(p);
+  PC_TRY(solve_grid(p, ds, dp, stats != nullptr, st));
   PC_CUDA_TRY(cudaGetLastError());
-  if (hp) PC_CUDA_TRY(cudaMemcpyAsync(p_out, dp, nvt * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (hp) PC_CUDA_TRY(cudaMemcpyAsync(p_out, dp, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (stats) PC_TRY(fill_stats(p, stats, st));
   if (hp) PC_CUDA_TRY(cudaStreamSynchronize(st));
   return PC_OK;
@@ -1693,7 +1693,8 @@ static pc_status solve_impl(Plan *p, const double *s, double *p_out, pc_stats *s
   if (hp) dp = p->stage_p;
   prof_begin(p, st);
   PC_CUDA_TRY(cudaMemsetAsync(p->dstats, 0, sizeof(DevStats), st));
-  launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, ds, p->dstats, p->partials, p->counters);
+  launch_pdl(sum_kernel, grid_for(nc, kFlatPerBlock), kFlatThreads, 0, st, nc, ds, p->dstats, p->partials, p->counters,
+             TrapWeights{});
   count_launch(p);
   prof_mark(p, st, 2);
   PC_TRY(solve_grid(p, ds, dp, stats != nullptr, st));

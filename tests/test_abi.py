@@ -132,7 +132,8 @@ def _grid_desc(**over):
     (dict(n=(3, 16)), 1),
     (dict(h=(0.1, -1.0)), 1),
     (dict(bc_lo=(0, 1)), 1),                          # periodic paired with a wall
-    (dict(bc_lo=(3, 1), n=(2048, 16)), 2),            # a D-N vertex axis extends to 4n = 8192
+    (dict(bc_lo=(3, 1), n=(15, 16)), 2),              # a D-N vertex axis: quarter-wave pair of odd length
+    (dict(n=(4096, 16)), 2),                          # an N-N vertex axis of 4096 cells: DCT-I FFT of 4096
     (dict(n=(14, 16)), 2),                            # a cell axis of 14 (half 7): no transform
 ])
 def test_grid_descriptor_validation(lib, over, status):

@@ -2,7 +2,7 @@
 
 The channel workload also runs on the vertex grid (one pass and the IB iteration against the
 oracle's vertex pass) and through the AB2 predictor (two steps against the oracle); vertex
-solves run at the largest extension the transforms take.
+solves run at the largest axes the vertex transforms take.
 
 Channel with cylinder, 1024x512 cells, ~4.0e5 nodes (the benchmark workload): the oracle runs
 the whole projection, and the IB-force iteration at tolerance 1e-3, so p, u and f are compared
@@ -100,7 +100,7 @@ def test_channel_ib_iteration(env, channel):
 
 def test_channel_vertex_projection(env, channel):
     """The channel workload on the regular (vertex) pressure grid (1024 x 513 unknowns, N-D by
-    N-N; transforms on the 4096 x 1024 extension), in the benchmark's launch configuration:
+    N-N: quarter-wave and DCT-I transforms), in the benchmark's launch configuration:
     one pass against the oracle's vertex pass, p, u, f element by element."""
     from oracle import vertex as V
     pc, torch, dev = env
@@ -164,14 +164,14 @@ def test_channel_predictor_full_size(env, channel):
 
 
 @pytest.mark.parametrize("kinds", [(("I", "D"), ("W", "W")), (("D", "W"), ("P", "P"))])
-def test_vertex_solve_maximum_extension(env, kinds):
-    """Vertex-grid solves at the largest extension the transforms take (4096 per axis): a
-    1024-cell N-D or D-N axis (4n) with a 2048-cell N-N or P-P axis, against the oracle's
-    DCT-I / quarter-wave expansion."""
+def test_vertex_solve_maximum_sizes(env, kinds):
+    """Vertex-grid solves at the largest axes the vertex transforms take: a 4096-cell N-D or D-N
+    axis (quarter-wave pair, FFT of 2048) with a 2048-cell N-N axis (DCT-I, FFT of 2048 on the
+    even extension) or a 1024-cell P-P axis, against the oracle's DCT-I / quarter-wave expansion."""
     from oracle import vertex as V
     pc, torch, dev = env
     (lo0, hi0), (lo1, hi1) = kinds
-    n = (1024, 2048) if lo1 != "P" else (1024, 4096)
+    n = (4096, 2048) if lo1 != "P" else (4096, 1024)
     h = (1.0 / n[0], 1.0 / n[1])
     lo, hi = (lo0, lo1), (hi0, hi1)
     shape = tuple(V.unknowns(V.axis_kind(lo[a], hi[a]), n[a])[0] for a in range(2))

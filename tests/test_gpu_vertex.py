@@ -1,8 +1,10 @@
 """The vertex ("regular") pressure grid of §2.3 (the grid of the §3.2 results) against the oracle.
 
 Grid-only plans: the Poisson solve for every boundary pairing, and the cell-centred solve without
-nodes. The vertex solve goes through the symmetric extension to a periodic cell grid on the device;
-the oracle expands in the DCT-I / DST-I / quarter-wave eigenvectors directly.
+nodes. On the device the vertex solve runs one transform pass per axis on the unknowns (DCT-I and
+DST-I through the real DFT of the even or odd extension of each line in shared memory, the
+quarter-wave bases through the DCT-II / DST-II pair in the other order); the oracle expands in the
+DCT-I / DST-I / quarter-wave eigenvectors with dense bases.
 
 Vertex-grid projection plans: the WLS rows at the vertex unknowns and at the nodes, one pass, the
 IB-force iteration, host arrays, clones and the RHS mask."""
@@ -68,6 +70,31 @@ def test_vertex_poisson_matches_oracle(env, n, precision, tol):
         # the dropped zero-mode coefficient of the vertex problem (0 when a Dirichlet end exists)
         assert abs(st["removed_mean"] - removed) <= 1e-12 * (1 + np.abs(s).max()), (kinds, st["removed_mean"], removed)
         plan.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-10), ("fp32", 1e-5)])
+def test_vertex_odd_lengths(env, precision, tol):
+    """DCT-I and DST-I axes of an odd number of cells (an FFT of odd length 15 or 25 on the
+    extension, radices 3 and 5 only), and a quarter-wave axis of 30 cells (FFT of 15)."""
+    pc, torch, dev = env
+    cases = [((15, 25), ("NN", "DD")), ((25, 15), ("DD", "NN")), ((15, 15), ("NN", "NN")),
+             ((30, 25), ("ND", "NN")), ((25, 30), ("DD", "DN")), ((15, 9, 25), ("NN", "DD", "NN"))]
+    for i, (n, kinds) in enumerate(cases):
+        h, lo, hi, s = _vertex_case(kinds, n, 8000 + i)
+        ref, removed = V.solve(s, n, h, lo, hi)
+        plan = pc.GridPlan(len(n), n, h, lo, hi, grid_type="vertices", precision=precision)
+        p, st = plan.solve_poisson(torch.as_tensor(s, device=dev), stats=True)
+        assert rel(p.cpu().numpy(), ref) <= tol, (kinds, n, precision, rel(p.cpu().numpy(), ref))
+        assert abs(st["removed_mean"] - removed) <= 1e-12 * (1 + np.abs(s).max()), (kinds, st["removed_mean"], removed)
+        plan.close()
+
+
+def test_vertex_quarter_wave_odd_length_refused(env):
+    """A quarter-wave axis runs a DCT-II/DST-II pair of its own length, which must be even."""
+    pc, torch, dev = env
+    with pytest.raises(pc.PcError) as e:
+        pc.GridPlan(2, (15, 16), (0.1, 0.1), ("W", "W"), ("D", "W"), grid_type="vertices")
+    assert e.value.status == 2
 
 
 @pytest.mark.parametrize("n", [(24, 20), (10, 8, 12)])
