@@ -134,12 +134,16 @@ __device__ __forceinline__ void axis_pass_body(const PassArgs<Real> &A, const in
     }
     lbase[t] = valid ? base : -1;
     if (A.do_div && valid) {
+      // the line's index along each axis (loops over constant indices: registers, no local array)
       int rem = base, idx[3] = {0, 0, 0};
-      for (int b = A.dim - 1; b >= 0; --b) { idx[b] = rem % A.shape[b]; rem /= A.shape[b]; }
+#pragma unroll
+      for (int b = 2; b >= 0; --b)
+        if (b < A.dim) { idx[b] = rem % A.shape[b]; rem /= A.shape[b]; }
       Real lo = 0;
       int zero = 1;
-      for (int b = 0; b < A.dim; ++b) {
-        if (b == A.axis) continue;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (b >= A.dim || b == A.axis) continue;
         lo += A.lam[b][idx[b]];
         zero &= idx[b] == 0;
       }

@@ -444,7 +444,9 @@ struct TrapWeights {
 };
 __device__ __forceinline__ double trap_weight(const TrapWeights &w, long long c) {
   double wt = 1.0;
-  for (int a = w.dim - 1; a >= 0; --a) {
+#pragma unroll
+  for (int a = 2; a >= 0; --a) {   // constant indices: the weights stay in registers
+    if (a >= w.dim) continue;
     const long long q = c / w.n[a];
     const int i = (int)(c - q * w.n[a]);
     c = q;
@@ -961,9 +963,15 @@ struct VertexGrid {
 // Both kernels run on a grid whose x covers the last axis and whose y (and z) are the indices of
 // the other axes, so no thread divides to find its position.
 __device__ __forceinline__ void grid_position(int dim, int *idx) {
-  idx[dim - 1] = blockIdx.x * blockDim.x + threadIdx.x;
-  idx[dim - 2] = blockIdx.y;
-  if (dim == 3) idx[0] = blockIdx.z;
+  if (dim == 3) {
+    idx[2] = blockIdx.x * blockDim.x + threadIdx.x;
+    idx[1] = blockIdx.y;
+    idx[0] = blockIdx.z;
+  } else {
+    idx[1] = blockIdx.x * blockDim.x + threadIdx.x;
+    idx[0] = blockIdx.y;
+    idx[2] = 0;
+  }
 }
 // p at the unknowns (pv) -> p on the lattice in FP64 (pl) and as FP32 (hi, lo) pairs (pl2) for
 // the compensated gradient; Dirichlet boundary vertices are exactly 0.
@@ -972,10 +980,12 @@ __global__ void vertex_embed_kernel(VertexGrid V, const double *__restrict__ pv,
   pdl_enter();
   int idx[3];
   grid_position(V.dim, idx);
-  if (idx[V.dim - 1] >= V.nf[V.dim - 1]) return;
+  if ((V.dim == 3 ? idx[2] : idx[1]) >= (V.dim == 3 ? V.nf[2] : V.nf[1])) return;
   int u = 0, l = 0;
   bool unknown = true;
-  for (int a = 0; a < V.dim; ++a) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= V.dim) continue;
     l = l * V.nf[a] + idx[a];
     const int ua = idx[a] - V.j0[a];
     if (ua < 0 || ua >= V.nv[a]) unknown = false;   // a Dirichlet boundary vertex
