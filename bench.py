@@ -587,17 +587,21 @@ def run_variants(args, prob, u_dev, stream, dev, flush, ms_step, reps=50):
     import torch
     from paper_2304_14690_gb300 import pc
 
-    def timed(plan):
+    def timed(plan, tag=None):
         outs = plan.alloc_outputs()
         for _ in range(3):
             plan.project(u_dev, out=outs)
         torch.cuda.synchronize(dev)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        if tag:
+            torch.cuda.nvtx.range_push(tag)   # ncu --nvtx-include <tag>/
         for k in range(reps):
             flush.fill_(k & 0xFF)
             ev[k][0].record(stream)
             plan.project(u_dev, out=outs)
             ev[k][1].record(stream)
+        if tag:
+            torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize(dev)
         plan.profile(True)                  # phases from a second run, per-phase events on
         for k in range(reps):
@@ -686,7 +690,7 @@ def run_variants(args, prob, u_dev, stream, dev, flush, ms_step, reps=50):
     vp = pc.Plan(prob, precision=args.precision, refine_iters=args.refine, refine_tol=args.refine_tol, device=dev.index,
                  div_mode="wls_direct", grid_type="vertices")
     vp.autotune()
-    ms_vp, ph_vp = timed(vp)
+    ms_vp, ph_vp = timed(vp, "vertex")
     out["vertex_grid_project"] = {"ms_per_step": round(ms_vp, 5), "unknowns": int(np.prod(vp.shape)),
                                   "phase_ms": {k: round(v, 5) for k, v in ph_vp.items()}}
     vp.close()
