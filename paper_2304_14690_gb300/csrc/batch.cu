@@ -229,7 +229,7 @@ pc_status record_exec(Exec *e, cudaStream_t st, Plan *prof = nullptr) {
   mark(1);
   for (const Group &g : e->groups) {
     const int n = (int)g.members.size();
-    batch_launch(BATCH_DIVERGENCE, 0, g.dP, segs(g, BATCH_DIVERGENCE), n, g.total[BATCH_DIVERGENCE], 0, st);
+    batch_launch(BATCH_DIVERGENCE, g.dim, g.dP, segs(g, BATCH_DIVERGENCE), n, g.total[BATCH_DIVERGENCE], 0, st);
     ++launches;
   }
   mark(2);
@@ -238,7 +238,7 @@ pc_status record_exec(Exec *e, cudaStream_t st, Plan *prof = nullptr) {
       for (const Group &g : e->groups) {
         if (g.sweeps < (int)j) continue;
         const int n = (int)g.members.size();
-        batch_launch(BATCH_RESIDUAL, 0, g.dP, segs(g, BATCH_RESIDUAL), n, g.total[BATCH_RESIDUAL], (int)j - 1, st);
+        batch_launch(BATCH_RESIDUAL, g.dim, g.dP, segs(g, BATCH_RESIDUAL), n, g.total[BATCH_RESIDUAL], (int)j - 1, st);
         ++launches;
       }
       mark(4);

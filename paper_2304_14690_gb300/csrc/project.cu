@@ -519,8 +519,9 @@ __device__ __forceinline__ DF ghost_df(int kind, DF dc, const PV *__restrict__ p
 // pairs; FP64 arrays come from pc_solve_poisson and from the statistics of FP64 plans).
 // Refinement step of a residual launch: k sweeps are done before it. With rule set (the
 // stopping rule is on), the launch does nothing once a residual before it ended the refinement
-// (refine_stopped_before; rule 2: the caller already checked), and otherwise records the max norm
-// of r_k (and, for k = 0, of s) for the rule; tol: the rule's tolerance.
+// (refine_stopped_before, checked by the kernel: rule 1 by the single-problem kernel, rule 2 by a
+// caller that already did), and otherwise records the max norm of r_k (and, for k = 0, of s)
+// for the rule; tol: the rule's tolerance.
 struct RefineStep {
   int k, rule;
   float tol;
@@ -555,8 +556,8 @@ template <int DIM, bool SINGULAR, bool WRITE_R, bool NORM, typename SV, typename
 __device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, const SV *__restrict__ s,
                                               const PV *__restrict__ p, float *__restrict__ r,
                                               DevStats *stats, double *res2, double *partials,
-                                              unsigned int *counter, RefineStep rs = RefineStep{0, 0, 0.0f, 1}) {
-  if (rs.rule == 1 && refine_stopped_before(stats, rs.k, rs.tol)) return;   // the refinement already ended
+                                              unsigned int *counter, RefineStep rs, float &rmx_acc,
+                                              float &smx_acc) {
   int x, row0;
   tile_pos(g, b, x, row0);
   double nrm = 0.0;
@@ -598,11 +599,16 @@ __device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, cons
       }
     }
   }
-  if (rs.rule) {
-    block_max_bits(rmx, &stats->rmax[rs.k]);
-    if (rs.k == 0) block_max_bits(smx, &stats->smax);
-  }
+  rmx_acc = fmaxf(rmx_acc, rmx);
+  smx_acc = fmaxf(smx_acc, smx);
   if (NORM) grid_sum(nrm, partials, counter, res2, tile_block(g, b));
+}
+// The rule's max norms of a CTA's blocks, merged once per CTA (a maximum is exact and
+// order-independent, so the grouping of blocks does not change it).
+__device__ __forceinline__ void residual_record(const RefineStep &rs, float rmx, float smx, DevStats *stats) {
+  if (!rs.rule) return;
+  block_max_bits(rmx, &stats->rmax[rs.k]);
+  if (rs.k == 0) block_max_bits(smx, &stats->smax);
 }
 // CTA b evaluates blocks b * rs.chunk, ... of the grid's decomposition (the residual per cell,
 // its max norm and its L2 partial per block do not depend on how blocks are grouped).
@@ -612,12 +618,12 @@ __global__ void residual_kernel(GridDev g, const SV *__restrict__ s, const PV *_
                                 double *partials, unsigned int *counter, RefineStep rs) {
   pdl_enter();
   if (rs.rule == 1 && refine_stopped_before(stats, rs.k, rs.tol)) return;   // the refinement already ended
-  RefineStep in = rs;
-  if (in.rule == 1) in.rule = 2;   // checked above
   const int c = rs.chunk > 1 ? rs.chunk : 1;
   const int b0 = blockIdx.x * c, b1 = min(b0 + c, g.nblk);
+  float rmx = 0.0f, smx = 0.0f;
   for (int b = b0; b < b1; ++b)
-    residual_body<DIM, SINGULAR, WRITE_R, NORM, SV, PV>(b, g, s, p, r, stats, res2, partials, counter, in);
+    residual_body<DIM, SINGULAR, WRITE_R, NORM, SV, PV>(b, g, s, p, r, stats, res2, partials, counter, rs, rmx, smx);
+  residual_record(rs, rmx, smx, stats);
 }
 
 // ----------------------------------------------------------------------------- gauge
@@ -1081,19 +1087,15 @@ __global__ void batch_transfer(const BatchProblem *__restrict__ P, const int *__
                                  q.U64[a]);
 }
 
+// Cell and residual stages of a group (one dimension per group: DIM is a template parameter).
+template <int DIM>
 __global__ void batch_divergence(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
   pdl_enter();
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
   const unsigned lb = blockIdx.x - seg[pi];
-  if (q.g.dim == 2)
-    divergence_body<2>(lb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, nullptr, reinterpret_cast<float2 *>(q.s64),
-                       q.s32, q.ds, q.partials, q.counters,
-                       q.singular, q.inv_ncells);
-  else
-    divergence_body<3>(lb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, nullptr, reinterpret_cast<float2 *>(q.s64),
-                       q.s32, q.ds, q.partials, q.counters,
-                       q.singular, q.inv_ncells);
+  divergence_body<DIM>(lb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, nullptr, reinterpret_cast<float2 *>(q.s64),
+                       q.s32, q.ds, q.partials, q.counters, q.singular, q.inv_ncells);
 }
 
 // Residual k of every problem (k sweeps done). Problems under the stopping rule (tol > 0)
@@ -1102,6 +1104,7 @@ __global__ void batch_divergence(const BatchProblem *__restrict__ P, const int *
 // residual per cell and its max norm do not depend on how blocks are grouped), so a skipped
 // launch costs a quarter of the CTAs.
 constexpr int kResidualChunk = 4;
+template <int DIM>
 __global__ void batch_residual(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count, int k) {
   pdl_enter();
   const int pi = batch_problem_of(seg, count, blockIdx.x);
@@ -1112,15 +1115,12 @@ __global__ void batch_residual(const BatchProblem *__restrict__ P, const int *__
   const RefineStep rs{k, rule ? 2 : 0, q.tol, 1};
   const int b0 = (int)(blockIdx.x - seg[pi]) * kResidualChunk;
   const int b1 = min(b0 + kResidualChunk, q.g.nblk);
+  float rmx = 0.0f, smx = 0.0f;
   for (int b = b0; b < b1; ++b) {
-    if (q.g.dim == 2) {
-      if (q.singular) residual_body<2, true, true, false>(b, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
-      else residual_body<2, false, true, false>(b, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
-    } else {
-      if (q.singular) residual_body<3, true, true, false>(b, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
-      else residual_body<3, false, true, false>(b, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs);
-    }
+    if (q.singular) residual_body<DIM, true, true, false>(b, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs, rmx, smx);
+    else residual_body<DIM, false, true, false>(b, q.g, s2, q.p2, q.r32, q.ds, nullptr, q.partials, q.counters, rs, rmx, smx);
   }
+  residual_record(rs, rmx, smx, q.ds);
 }
 
 __global__ void batch_gauge_sum(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
@@ -1165,8 +1165,14 @@ void batch_launch(int stage, int variant, const BatchProblem *P, const int *seg,
       else if (variant == 27) launch_pdl(batch_transfer<27>, total_blocks, T, 0, st, P, seg, count, extra);
       else launch_pdl(batch_transfer<0>, total_blocks, T, 0, st, P, seg, count, extra);
       break;
-    case BATCH_DIVERGENCE: launch_pdl(batch_divergence, total_blocks, T, 0, st, P, seg, count); break;
-    case BATCH_RESIDUAL: launch_pdl(batch_residual, total_blocks, T, 0, st, P, seg, count, extra); break;
+    case BATCH_DIVERGENCE:   // variant: the group's dimension
+      if (variant == 3) launch_pdl(batch_divergence<3>, total_blocks, T, 0, st, P, seg, count);
+      else launch_pdl(batch_divergence<2>, total_blocks, T, 0, st, P, seg, count);
+      break;
+    case BATCH_RESIDUAL:
+      if (variant == 3) launch_pdl(batch_residual<3>, total_blocks, T, 0, st, P, seg, count, extra);
+      else launch_pdl(batch_residual<2>, total_blocks, T, 0, st, P, seg, count, extra);
+      break;
     case BATCH_GAUGE_SUM: launch_pdl(batch_gauge_sum, total_blocks, T, 0, st, P, seg, count); break;
     case BATCH_FINALIZE: launch_pdl(batch_finalize, total_blocks, T, 0, st, P, seg, count); break;
     case BATCH_GRADIENT:
