@@ -1088,13 +1088,24 @@ __global__ void batch_transfer(const BatchProblem *__restrict__ P, const int *__
 }
 
 // Cell and residual stages of a group (one dimension per group: DIM is a template parameter).
+// The problem's grid description is copied into shared memory first: its fields are then
+// shared-memory operands, as a kernel parameter's are constant-bank operands in the single call.
+__device__ __forceinline__ const GridDev &stage_grid(const GridDev &src) {
+  __shared__ __align__(16) GridDev gs;
+  const unsigned *a = reinterpret_cast<const unsigned *>(&src);
+  unsigned *b = reinterpret_cast<unsigned *>(&gs);
+  for (int w = threadIdx.x; w < (int)(sizeof(GridDev) / 4); w += blockDim.x) b[w] = __ldg(a + w);
+  __syncthreads();
+  return gs;
+}
 template <int DIM>
 __global__ void batch_divergence(const BatchProblem *__restrict__ P, const int *__restrict__ seg, int count) {
   pdl_enter();
   const int pi = batch_problem_of(seg, count, blockIdx.x);
   const BatchProblem &q = P[pi];
   const unsigned lb = blockIdx.x - seg[pi];
-  divergence_body<DIM>(lb, q.g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, nullptr, reinterpret_cast<float2 *>(q.s64),
+  const GridDev &g = stage_grid(q.g);
+  divergence_body<DIM>(lb, g, q.U64[0], q.U64[1], q.U64[2], q.inv_bdt, nullptr, reinterpret_cast<float2 *>(q.s64),
                        q.s32, q.ds, q.partials, q.counters, q.singular, q.inv_ncells);
 }
 
@@ -1280,6 +1291,17 @@ static GridDev grid_dev(const Plan *p) {
   return g;
 }
 
+// The same tiling with cr rows per thread. A launch whose results do not depend on its blocks
+// (no grid sums: the residual's values and max norms, a divergence without sums) may take more,
+// smaller blocks when it runs alone; a batch keeps four rows per thread.
+static GridDev with_rows_per_thread(GridDev g, int cr) {
+  const long long rpb = (long long)cr << g.th_bits;
+  g.cr = cr;
+  g.nblk = (int)((long long)g.gx * ((g.rows + rpb - 1) / rpb));
+  return g;
+}
+constexpr int kSingleRows = 2;   // rows per thread of those single-problem launches
+
 // Launch shape covering every cell: x over the last axis, y/z over the others.
 
 
@@ -1295,9 +1317,12 @@ static bool is_device_ptr(const void *ptr) {
 
 // Grid-level solve: s64 (device) -> p (device, FP64), gauge applied; fills dstats fields.
 template <typename SV, typename PV>
-static void launch_residual(bool singular, bool write_r, bool norm, cudaStream_t st, const GridDev &g,
+static void launch_residual(bool singular, bool write_r, bool norm, cudaStream_t st, const GridDev &g0,
                             const SV *s, const PV *p, float *r, DevStats *ds, double *res2, double *partials,
                             unsigned int *counters, RefineStep rs = RefineStep{0, 0, 0.0f, 1}) {
+  // the values and max norms do not depend on the blocks; the L2 norm (statistics) is reported
+  // by single calls only
+  const GridDev g = with_rows_per_thread(g0, kSingleRows);
   const int grid = (g.nblk + (rs.chunk > 1 ? rs.chunk : 1) - 1) / (rs.chunk > 1 ? rs.chunk : 1);
 #define PC_RES(S, W, N)                                                                                       \
   do {                                                                                                        \
@@ -1591,10 +1616,12 @@ static pc_status project_impl(Plan *p, double dt, const void *u_star, const void
   if (p->divmode == PC_DIV_FACES) {
     prof_mark(p, st, 1);
     auto divk = (d == 2) ? divergence_kernel<2> : divergence_kernel<3>;
-    launch_pdl(divk, g.nblk, 256, 0, st, g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt),
+    const int sums = stats ? 2 : (p->singular ? 1 : 0);
+    const GridDev gd = sums ? g : with_rows_per_thread(g, kSingleRows);
+    launch_pdl(divk, gd.nblk, 256, 0, st, gd, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt),
                mixed ? nullptr : p->s64, mixed ? reinterpret_cast<float2 *>(p->s64) : nullptr,
                mixed ? reinterpret_cast<float *>(p->work64) : nullptr, p->dstats, p->partials, p->counters,
-               stats ? 2 : (p->singular ? 1 : 0), 1.0 / (double)nc);
+               sums, 1.0 / (double)nc);
     count_launch(p);
     prof_mark(p, st, 2);
   }
@@ -1971,7 +1998,8 @@ static pc_status ib_pass(Plan *p, bool first, double dt, const VT *du, double *d
     prof_mark(p, st, 1);
     GridDev g = grid_dev(p);
     auto divk = (d == 2) ? divergence_kernel<2> : divergence_kernel<3>;
-    launch_pdl(divk, g.nblk, 256, 0, st, g, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt),
+    const GridDev gd = p->singular ? g : with_rows_per_thread(g, kSingleRows);
+    launch_pdl(divk, gd.nblk, 256, 0, st, gd, p->U64[0], p->U64[1], p->U64[2], 1.0 / (p->beta * dt),
                mixed ? nullptr : p->s64, mixed ? reinterpret_cast<float2 *>(p->s64) : nullptr,
                mixed ? reinterpret_cast<float *>(p->work64) : nullptr, p->dstats, p->partials, p->counters,
                p->singular ? 1 : 0, 1.0 / (double)nc);
