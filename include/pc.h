@@ -389,8 +389,13 @@ pc_status pc_set_graphs(pc_plan *plan, int on);
  * then 3 and 5). `precision` selects the FP64 passes (PC_PREC_FP64) or the FP32 passes (the
  * other two). A schedule is part of the plan: single and batched calls use it alike, and changing
  * it drops the plan's captured CUDA graphs. Results change only by rounding between schedules.
+ * FP32 passes also take slots = 0 and 1: the compile-time pass of the axis's line length, where
+ * the length has one (cell-grid transforms, n = 2M with M in {16, 32, 48, 64, 96, 128, 192, 256,
+ * 384, 512}; its slots per thread are fixed by M: variant 0 with the most slots per thread and
+ * the fewest instructions, variant 1 with fewer slots and more threads per line, for grids too
+ * small to hide latency with variant 0), else 4 slots.
  * Errors: PC_ERR_INVALID_ARG for a bad axis or slot count; a schedule whose tile does not fit the
- * kernels fails at the next call with PC_ERR_UNSUPPORTED. Defaults: 4 (FP32), 2 (FP64). */
+ * kernels fails at the next call with PC_ERR_UNSUPPORTED. Defaults: 0 (FP32), 2 (FP64). */
 pc_status pc_plan_set_transform_slots(pc_plan *plan, int axis, pc_precision precision, int slots);
 pc_status pc_plan_get_transform_slots(const pc_plan *plan, int axis, pc_precision precision,
                                       int *slots_out);

@@ -33,6 +33,7 @@ struct PassLaunch {
   int nitems = 0;
   int emax = 1;          // largest slots per thread among the items' passes (kernel instance)
   size_t smem = 0;       // the pass body's shared memory (the largest item's)
+  int lean = 0;          // 0: general passes; else the lean kernel id (lean_pass.cuh)
 };
 
 // Problems that share the templated per-stage kernels (dimension, velocity type, neighbour
@@ -171,9 +172,9 @@ pc_status build_passes(Exec *e) {
     std::vector<PassLaunch> launches;
     for (size_t k = 0; k < npass; ++k) {
       struct Entry { long long key; int ai; long long tiles; };
-      std::vector<Entry> list;
-      PassLaunch pl;
-      pl.items_off = (int)items.size();
+      // one launch per kernel: the general passes, and the lean passes of each lean kernel
+      std::vector<Entry> list[7];
+      PassLaunch pl[7];
       for (const auto &ps : specs) {
         if (k >= ps.second.size()) continue;
         PassArgs<float> A;
@@ -183,20 +184,26 @@ pc_status build_passes(Exec *e) {
         PC_TRY(build_pass<float>(ps.first, ps.second[k], A, tiles, threads, smem, kBatchThreads));
         const bool pow2 = (A.M & (A.M - 1)) == 0;
         const long long key = ((long long)pass_family(A.kind) * 2 + (pow2 ? 0 : 1)) * 65536 + (65535 - A.M);
-        list.push_back(Entry{key, (int)args.size(), tiles});
+        const int c = A.lean;
+        list[c].push_back(Entry{key, (int)args.size(), tiles});
         args.push_back(A);
-        pl.smem = std::max(pl.smem, smem);
-        pl.emax = std::max(pl.emax, A.emax);
-
+        pl[c].smem = std::max(pl[c].smem, smem);
+        pl[c].emax = std::max(pl[c].emax, A.emax);
+        pl[c].lean = c;
       }
-      if (list.empty()) continue;
-      std::stable_sort(list.begin(), list.end(), [](const Entry &a, const Entry &b) { return a.key < b.key; });
-      // consecutive tiles of a problem, kBatchChunk per CTA
-      for (const Entry &en : list)
-        for (long long t = 0; t < en.tiles; t += kBatchChunk)
-          items.push_back(make_int4(en.ai, (int)t, (int)std::min<long long>(kBatchChunk, en.tiles - t), 0));
-      pl.nitems = (int)items.size() - pl.items_off;
-      launches.push_back(pl);
+      for (int c = 0; c < 7; ++c) {
+        if (list[c].empty()) continue;
+        std::stable_sort(list[c].begin(), list[c].end(), [](const Entry &a, const Entry &b) { return a.key < b.key; });
+        pl[c].items_off = (int)items.size();
+        // consecutive tiles of a problem per CTA: kBatchChunk small tiles of the general passes,
+        // one (larger) tile of the lean passes
+        const int chunk = c == 0 ? kBatchChunk : 1;
+        for (const Entry &en : list[c])
+          for (long long t = 0; t < en.tiles; t += chunk)
+            items.push_back(make_int4(en.ai, (int)t, (int)std::min<long long>(chunk, en.tiles - t), 0));
+        pl[c].nitems = (int)items.size() - pl[c].items_off;
+        launches.push_back(pl[c]);
+      }
     }
     e->passes.push_back(launches);
   }
@@ -244,7 +251,13 @@ pc_status record_exec(Exec *e, cudaStream_t st, Plan *prof = nullptr) {
       mark(4);
     }
     for (const PassLaunch &pl : e->passes[j]) {
-      PC_TRY(launch_batched_f32(e->dargs, e->ditems + pl.items_off, pl.nitems, kBatchThreads, pl.smem, pl.emax, st));
+      if (pl.lean) {
+        PassArgs<float> none;
+        memset(&none, 0, sizeof(none));
+        PC_TRY(launch_lean(pl.lean, none, e->dargs, e->ditems + pl.items_off, (unsigned)pl.nitems, kBatchThreads, pl.smem, st));
+      } else {
+        PC_TRY(launch_batched_f32(e->dargs, e->ditems + pl.items_off, pl.nitems, kBatchThreads, pl.smem, pl.emax, st));
+      }
       ++launches;
     }
     mark(3);

@@ -46,6 +46,7 @@ struct PassArgs {
   RefineGate gate;      // a refinement sweep's pass: nothing to do once the stopping rule ended it
   int chunk;            // single-problem launches: consecutive tiles per CTA (>= 1)
   int ntiles;           // tiles of the pass
+  int lean;             // 0: general pass (axis_pass.cuh); else the lean kernel id (lean_pass.cuh)
 };
 
 // One pass of a solve: axis, phases, source and destination.
@@ -91,6 +92,47 @@ pc_status prepare_pass_vertex(int lim);
 pc_status launch_batched_f32(const PassArgs<float> *dargs, const int4 *ditems, int nitems, int threads, size_t smem,
                              int emax, cudaStream_t st);
 pc_status prepare_batched_f32(int lim);
+// Lean FP32 passes (compile-time line length, lean_pass.cuh): one kernel per register class
+// (r) and transform family (f) serves single-problem passes (dargs == ditems == nullptr, A the
+// pass) and batched ones (one CTA per work item).
+pc_status launch_lean_r0f0(const PassArgs<float> &A, const PassArgs<float> *dargs, const int4 *ditems,
+                            unsigned grid, int threads, size_t smem, cudaStream_t st);
+pc_status prepare_lean_r0f0(int lim);
+pc_status launch_lean_r0f1(const PassArgs<float> &A, const PassArgs<float> *dargs, const int4 *ditems,
+                            unsigned grid, int threads, size_t smem, cudaStream_t st);
+pc_status prepare_lean_r0f1(int lim);
+pc_status launch_lean_r0f2(const PassArgs<float> &A, const PassArgs<float> *dargs, const int4 *ditems,
+                            unsigned grid, int threads, size_t smem, cudaStream_t st);
+pc_status prepare_lean_r0f2(int lim);
+pc_status launch_lean_r1f0(const PassArgs<float> &A, const PassArgs<float> *dargs, const int4 *ditems,
+                            unsigned grid, int threads, size_t smem, cudaStream_t st);
+pc_status prepare_lean_r1f0(int lim);
+pc_status launch_lean_r1f1(const PassArgs<float> &A, const PassArgs<float> *dargs, const int4 *ditems,
+                            unsigned grid, int threads, size_t smem, cudaStream_t st);
+pc_status prepare_lean_r1f1(int lim);
+pc_status launch_lean_r1f2(const PassArgs<float> &A, const PassArgs<float> *dargs, const int4 *ditems,
+                            unsigned grid, int threads, size_t smem, cudaStream_t st);
+pc_status prepare_lean_r1f2(int lim);
+// Launch of lean kernel id (PassArgs::lean: 1 + 3 * register class + family).
+inline pc_status launch_lean(int id, const PassArgs<float> &A, const PassArgs<float> *dargs, const int4 *ditems,
+                             unsigned grid, int threads, size_t smem, cudaStream_t st) {
+  switch (id) {
+    case 1: return launch_lean_r0f0(A, dargs, ditems, grid, threads, smem, st);
+    case 2: return launch_lean_r0f1(A, dargs, ditems, grid, threads, smem, st);
+    case 3: return launch_lean_r0f2(A, dargs, ditems, grid, threads, smem, st);
+    case 4: return launch_lean_r1f0(A, dargs, ditems, grid, threads, smem, st);
+    case 5: return launch_lean_r1f1(A, dargs, ditems, grid, threads, smem, st);
+    default: return launch_lean_r1f2(A, dargs, ditems, grid, threads, smem, st);
+  }
+}
+inline pc_status prepare_lean(int lim) {
+  PC_TRY(prepare_lean_r0f0(lim));
+  PC_TRY(prepare_lean_r0f1(lim));
+  PC_TRY(prepare_lean_r0f2(lim));
+  PC_TRY(prepare_lean_r1f0(lim));
+  PC_TRY(prepare_lean_r1f1(lim));
+  return prepare_lean_r1f2(lim);
+}
 // Transform family of a kind: 0 real DFT, 1 DCT-II/DST-II, 2 DCT-IV/DST-IV, 3 vertex DCT-I/DST-I,
 // 4 vertex quarter-wave bases.
 __host__ __device__ inline int pass_family(int kind) {

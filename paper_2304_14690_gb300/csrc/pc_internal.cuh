@@ -33,7 +33,8 @@ struct AxisInfo {
   // Slots per thread of the transform passes along this axis, per precision (powers of two):
   // they fix the threads per line and the radix schedule (see build_pass), chosen when the
   // plan is built and shared by single and batched calls.
-  int slots32 = 4, slots64 = 2;
+  // slots32 = 0: the lean FP32 pass of the length where it has one (lean_pass.cuh), else 4
+  int slots32 = 0, slots64 = 2;
   int ctas32 = 2, ctas64 = 2;    // CTAs per SM the single-problem passes aim for (tile lines)
   double h = 0.0;
   double L = 0.0;   // n * h

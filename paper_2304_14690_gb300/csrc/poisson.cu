@@ -15,7 +15,7 @@
 #include <cstring>
 #include <vector>
 
-#include "axis_pass.cuh"
+#include "lean_pass.cuh"
 
 namespace pc {
 
@@ -130,15 +130,20 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   A.n = ax.n;
   A.M = ax.M;
   const int M = ax.M;
-  // threads per line: a power of two with at most E slots per thread; the kernel instance is
-  // the smallest power of two >= M / tpl
+  // slots per thread; 0 and 1 (FP32 only): variant 0 or 1 of the lean pass of the length
+  // (lean_pass.cuh) where it has one, else 4
   int E = (sizeof(Real) == 8) ? ax.slots64 : ax.slots32;
-  // a line must fit one CTA: longer lines take more slots per thread (up to 16)
+  const bool lean = sizeof(Real) == 4 && E <= 1 && pass_family(ax.kind) <= 2 && lean::length_ok(M);
+  const int lv = E == 1 ? 1 : 0;
+  if (E <= 1) E = 4;
+  // threads per line: a power of two with at most E slots per thread; the kernel instance is
+  // the smallest power of two >= M / tpl. A line must fit one CTA: longer lines take more
+  // slots per thread (up to 16)
   while (E < 16 && (M + E - 1) / E > kMaxPassThreads) E *= 2;
   const int tpl = 1 << ilog2((M + E - 1) / E);
   const int emax = 1 << ilog2((M + tpl - 1) / tpl);
   A.emax = emax;
-  {
+  if (!lean) {
     int radix[kMaxRadices], nr;
     radix_plan(M, emax, radix, nr);
     A.nst = nr;
@@ -161,6 +166,40 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   A.stride = stride;
   const int last = p->dim - 1;
   A.col = axis != last;
+  A.do_fwd = fwd;
+  A.do_div = div;
+  A.do_inv = inv;
+  for (int b = 0; b < p->dim; ++b)
+    A.lam[b] = (const Real *)(sizeof(Real) == 8 ? (const void *)p->ax[b].lam64 : (const void *)p->ax[b].lam32);
+  A.singular = p->singular;
+  A.src_mode = src_mode;
+  A.src = src;
+  A.dst_mode = dst_mode;
+  A.dst = dst;
+  A.out_scale = (Real)inv_scale(ax.M);
+  A.f64 = ps.f64;
+  A.gate = ps.gate;
+  A.chunk = ps.chunk > 1 ? ps.chunk : 1;
+  if (lean) {
+    // compile-time tile: L lines of T = M / E threads each, 256 threads
+    const int L = lean::lines_of(M, lv);
+    if (A.col) {
+      const long long outer = p->ncells / ((long long)stride * ax.n);
+      A.inner = stride;
+      A.tiles_per_outer = (stride + L - 1) / L;
+      tiles = outer * A.tiles_per_outer;
+    } else {
+      const long long lines = p->ncells / ax.n;
+      A.lines = (int)lines;
+      tiles = (lines + L - 1) / L;
+    }
+    A.L = L;
+    A.lean = lean::lean_id(M, pass_family(ax.kind));
+    threads = lean::kThreads;
+    A.ntiles = (int)tiles;
+    smem = lean::smem_of(M, lv);
+    return PC_OK;
+  }
   const int max_threads = batch_threads > 0 ? batch_threads : 256;
   const int max_lines = max_threads / tpl > 0 ? max_threads / tpl : 1;
   const int budget = 8192;          // complex slots per tile (two buffers: 2 x 64 KB in FP32)
@@ -191,20 +230,6 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   A.L = L;
   A.lbits = ilog2(L);
   A.tpl_bits = ilog2(tpl);
-  A.do_fwd = fwd;
-  A.do_div = div;
-  A.do_inv = inv;
-  for (int b = 0; b < p->dim; ++b)
-    A.lam[b] = (const Real *)(sizeof(Real) == 8 ? (const void *)p->ax[b].lam64 : (const void *)p->ax[b].lam32);
-  A.singular = p->singular;
-  A.src_mode = src_mode;
-  A.src = src;
-  A.dst_mode = dst_mode;
-  A.dst = dst;
-  A.out_scale = (Real)inv_scale(ax.M);
-  A.f64 = ps.f64;
-  A.gate = ps.gate;
-  A.chunk = ps.chunk > 1 ? ps.chunk : 1;
   threads = L * tpl;
   A.ntiles = (int)tiles;
   if (threads > kMaxPassThreads || L * M > budget)
@@ -227,6 +252,11 @@ static pc_status launch_pass(Plan *p, const PassSpec &ps, cudaStream_t st) {
   PC_TRY(build_pass<Real>(p, ps, A, tiles, threads, smem, 0));
   tiles = (tiles + A.chunk - 1) / A.chunk;   // CTAs
   if constexpr (sizeof(Real) == 4) {
+    if (A.lean) {
+      PC_TRY(launch_lean(A.lean, A, nullptr, nullptr, (unsigned)tiles, threads, smem, st));
+      count_launch(p);
+      return PC_OK;
+    }
     // FP32 passes: the instance of the axis's transform family (one translation unit each)
     switch (pass_family(A.kind)) {
       case 0: PC_TRY(launch_pass_f32_family0(A, tiles, threads, smem, st)); break;
@@ -250,6 +280,7 @@ pc_status prepare_kernels() {
   PC_TRY(prepare_pass_f32_family2(lim));
   PC_TRY(prepare_pass_vertex(lim));
   PC_TRY(prepare_batched_f32(lim));
+  PC_TRY(prepare_lean(lim));
   PC_TRY((prepare_axis_pass_spec<double, -1, false>(lim)));
   return PC_OK;
 }

@@ -10,7 +10,9 @@
 
 namespace pc {
 
-static bool valid_slots(int s) { return s == 2 || s == 4 || s == 8 || s == 16; }
+// 0 and 1 (FP32 only): variant 0 or 1 of the lean pass of the axis length where it has one
+// (lean_pass.cuh), else 4
+static bool valid_slots(int s, bool fp64) { return s == 2 || s == 4 || s == 8 || s == 16 || (s <= 1 && s >= 0 && !fp64); }
 
 static int &slots_ref(Plan *p, int axis, bool fp64) {
   return fp64 ? p->ax[axis].slots64 : p->ax[axis].slots32;
@@ -63,8 +65,8 @@ static pc_status autotune(Plan *p, cudaStream_t st, double *best_out) {
       // the two knobs of the axis in turn: slots per thread, then CTAs per SM
       for (int knob = 0; knob < 2; ++knob) {
         int &s = knob == 0 ? slots_ref(p, a, fp64) : ctas_ref(p, a, fp64);
-        for (int cand : {1, 2, 4, 8, 16}) {
-          if (cand == s || (knob == 0 ? !valid_slots(cand) : !valid_ctas(cand))) continue;
+        for (int cand : {0, 1, 2, 4, 8, 16}) {
+          if (cand == s || (knob == 0 ? !valid_slots(cand, fp64) : !valid_ctas(cand))) continue;
           const int keep = s;
           s = cand;
           float t = 0.0f;
@@ -99,7 +101,8 @@ extern "C" pc_status pc_plan_set_transform_slots(pc_plan *plan, int axis, pc_pre
   pc::Plan *p = reinterpret_cast<pc::Plan *>(plan);
   if (!p) return pc::fail(PC_ERR_INVALID_ARG, "plan is NULL");
   if (axis < 0 || axis >= p->dim) return pc::fail(PC_ERR_INVALID_ARG, "axis %d out of range", axis);
-  if (!pc::valid_slots(slots)) return pc::fail(PC_ERR_INVALID_ARG, "slots must be 2, 4, 8 or 16 (got %d)", slots);
+  if (!pc::valid_slots(slots, precision == PC_PREC_FP64))
+    return pc::fail(PC_ERR_INVALID_ARG, "slots must be 2, 4, 8 or 16, or 0 or 1 for FP32 (got %d)", slots);
   pc::slots_ref(p, axis, precision == PC_PREC_FP64) = slots;
   pc::plan_drop_graphs(p);
   return PC_OK;

@@ -342,7 +342,9 @@ class Plan:
         return PRECISION[precision if precision is not None else self.precision]
 
     def set_slots(self, axis, slots, precision=None):
-        """Slots per thread of the transform passes along axis (2, 4, 8 or 16)."""
+        """Slots per thread of the transform passes along axis (2, 4, 8 or 16; for FP32 passes
+        also 0 and 1: variant 0 or 1 of the compile-time pass of the axis length where it has
+        one; 0 is the default)."""
         _check(load().pc_plan_set_transform_slots(self.handle, axis, self._prec_code(precision), slots))
 
     def slots(self, precision=None):
