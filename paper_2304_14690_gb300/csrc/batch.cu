@@ -197,7 +197,8 @@ pc_status build_passes(Exec *e) {
         pl[c].items_off = (int)items.size();
         // consecutive tiles of a problem per CTA: kBatchChunk small tiles of the general passes,
         // one (larger) tile of the lean passes
-        const int chunk = c == 0 ? kBatchChunk : 1;
+        // (sweeps from the third on, which the stopping rule usually skips: 8 tiles per CTA)
+        const int chunk = c == 0 ? kBatchChunk : (j >= 3 ? 8 : 1);
         for (const Entry &en : list[c])
           for (long long t = 0; t < en.tiles; t += chunk)
             items.push_back(make_int4(en.ai, (int)t, (int)std::min<long long>(chunk, en.tiles - t), 0));

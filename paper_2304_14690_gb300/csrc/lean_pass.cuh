@@ -172,7 +172,7 @@ __device__ __forceinline__ void stage(float2 *buf, int u, int l, const float2 *_
 }
 
 // The forward FFT of every line of the tile (stages S, S + 1, ...); natural order in the slots.
-template <int M, int V, int S = 0>
+template <int M, int V, int S>
 __device__ __forceinline__ void fft(float2 *buf, int u, int l, const float2 *__restrict__ tw,
                                     const float2 *__restrict__ pre) {
   if constexpr (radix_of(M, V, S) > 0) {
@@ -180,26 +180,12 @@ __device__ __forceinline__ void fft(float2 *buf, int u, int l, const float2 *__r
     fft<M, V, S + 1>(buf, u, l, tw, nullptr);
   }
 }
-
-// Real position p of line l in the buffer (slot p / 2, real part for even p).
+// Out of line, so that a pass's forward and inverse halves share one copy of the stages (the
+// unrolled stages are large, and instruction fetch is the first stall of these passes).
 template <int M, int V>
-__device__ __forceinline__ float &re_at(float2 *buf, int l, int p) {
-  return reinterpret_cast<float *>(buf)[2 * ((p >> 1) * Geo<M, V>::LP + l) + (p & 1)];
-}
-
-// Where input x_j of a forward transform goes among the real positions of the slots (the
-// complex slot q holds positions 2q, 2q + 1), and its sign.
-template <int FAM>
-__device__ __forceinline__ int fwd_pos(int kind, int n, int j, bool &neg) {
-  neg = false;
-  if constexpr (FAM == 0) return j;
-  if constexpr (FAM == 1) {
-    neg = (kind == KIND_DD) && (j & 1);                 // DST-II: (-1)^j x_j
-    return (j & 1) ? n - 1 - (j >> 1) : (j >> 1);       // Makhoul's reordering
-  }
-  // DCT-IV: z_q = (x_2q, x_{n-1-2q}); DST-IV swaps the two
-  if (kind == KIND_ND) return (j & 1) ? n - j : j;
-  return (j & 1) ? n - 1 - j : j + 1;
+__device__ __noinline__ void fft_all(float2 *buf, int u, int l, const float2 *__restrict__ tw,
+                                     const float2 *__restrict__ pre) {
+  fft<M, V, 0>(buf, u, l, tw, pre);
 }
 
 // Natural coefficient index -> position in the pass's coefficient layout (DST-II reversed).
@@ -211,14 +197,14 @@ __device__ __forceinline__ int coef_pos(int kind, int n, int i) {
 // The four coefficient positions of pair k (k in [0, M/2)) in the order fwd_pair and inv_pair
 // use: family 0 the packed real DFT [X0, X_{n/2}, Re X1, Im X1, ...] (k = 0: X0, X_{n/2} and
 // the self-paired V_{M/2}); family 1 X_k, X_{n-k}, X_{M-k}, X_{M+k} (k = 0: X_0, X_M, X_{M/2},
-// X_{n-M/2}), DST-II reversed; family 2 X_2q, X_{n-1-2q} for q = k and q = k + M/2.
+// X_{n-M/2}), DST-II reversed; family 2 X_2q, X_{n-1-2q} for q = k and q = M - 1 - k.
 template <int M, int FAM>
 __device__ __forceinline__ void pair_positions(int k, int kind, int (&pos)[4]) {
   constexpr int n = 2 * M;
   if constexpr (FAM == 2) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int q = k + h * (M / 2);
+      const int q = h == 0 ? k : M - 1 - k;
       pos[2 * h] = 2 * q;
       pos[2 * h + 1] = n - 1 - 2 * q;
     }
@@ -237,7 +223,7 @@ __device__ __forceinline__ void pair_positions(int k, int kind, int (&pos)[4]) {
 
 // Forward post-processing of pair k (k in [0, M/2)) of line l: the four coefficients it
 // yields, as (position, value). Family 0: real DFT in packed order [X0, X_{n/2}, Re X1, Im X1,
-// ...]; family 1: DCT-II (DST-II reversed); family 2: DCT-IV / DST-IV of slots k and k + M/2.
+// ...]; family 1: DCT-II (DST-II reversed); family 2: DCT-IV / DST-IV of slots k and M - 1 - k.
 template <int M, int V, int FAM>
 __device__ __forceinline__ void fwd_pair(const float2 *buf, int l, int k, int kind, const float2 *__restrict__ tw,
                                          int (&pos)[4], float (&val)[4]) {
@@ -247,7 +233,7 @@ __device__ __forceinline__ void fwd_pair(const float2 *buf, int l, int k, int ki
     const float2 *tp = tw + tw_dct4post(M);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int q = k + h * (M / 2);
+      const int q = h == 0 ? k : M - 1 - k;
       const float2 y = cmul(buf[q * LP + l], __ldg(tp + q));
       val[2 * h] = y.x;
       val[2 * h + 1] = (kind == KIND_ND) ? -y.y : y.y;
@@ -307,7 +293,7 @@ __device__ __forceinline__ void inv_pair(float2 *buf, int l, int k, int kind, co
     const float2 *t4 = tw + tw_dct4pre(M);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int q = k + h * (M / 2);
+      const int q = h == 0 ? k : M - 1 - k;
       const float x0 = val[2 * h], x1 = val[2 * h + 1];   // X_2q, X_{n-1-2q}
       const float2 z = (kind == KIND_ND) ? make_float2(x0, x1) : make_float2(x1, x0);
       buf[q * LP + l] = cmul(z, __ldg(t4 + q));
@@ -349,245 +335,303 @@ __device__ __forceinline__ void inv_pair(float2 *buf, int l, int k, int kind, co
   buf[(M - k) * LP + l] = make_float2(Eh.x + O.y, Eh.y - O.x);     // E - i O
 }
 
-// Output i of a line after the final FFT (before the 1/M normalisation).
-template <int M, int V, int FAM>
-__device__ __forceinline__ float inv_value(const float2 *buf, int l, int i, int kind, const float2 *__restrict__ tw) {
-  constexpr int LP = Geo<M, V>::LP, n = 2 * M;
-  if constexpr (FAM == 0) {
-    const float2 z = buf[(i >> 1) * LP + l];
-    return (i & 1) ? -z.y : z.x;
-  } else if constexpr (FAM == 1) {
-    const int j = (i & 1) ? n - 1 - (i >> 1) : (i >> 1);
-    const float2 z = buf[(j >> 1) * LP + l];
-    const float v = (j & 1) ? -z.y : z.x;
-    return (kind == KIND_DD && (i & 1)) ? -v : v;
-  } else {
-    const int q = (i & 1) ? ((n - 1 - i) >> 1) : (i >> 1);
-    const float2 y = cmul(buf[q * LP + l], __ldg(tw + tw_dct4post(M) + q));
-    if ((i & 1) == 0) return y.x;
-    return (kind == KIND_ND) ? -y.y : y.y;
-  }
-}
-
-// Global element i (i < 2E) of this thread in a load or store phase of tile `tile`: its line,
-// position along the line, global index and validity. Row tiles are one contiguous run of
-// L lines (consecutive threads on consecutive cells); column tiles put the line index fast
-// (consecutive threads on adjacent lines, one global row segment per position).
-template <int M, int V, bool COL>
-struct ElemMap {
-  using G = Geo<M, V>;
-  int t, l, u, rowbase, rowend, stride;
-  const int *lbase;
-  __device__ __forceinline__ void at(int i, int &line, int &pos, int &gi, bool &valid) const {
-    if constexpr (COL) {
-      line = l;
-      pos = u + G::T * i;
-      const int b = lbase[l];
-      valid = b >= 0;
-      gi = b + pos * stride;
-    } else {
-      const int e = t + G::NT * i;
-      line = e / G::N;
-      pos = e - line * G::N;
-      gi = rowbase + e;
-      valid = gi < rowend;
-    }
-  }
+// ----------------------------------------------------------------------------- global I/O
+// A thread moves its line's values in quads of four consecutive positions 4 qd .. 4 qd + 3
+// (one 16-byte access on row tiles, four coalesced scalar accesses on column tiles) and its
+// coefficients in the pairs of pair_positions. Where a line lives: `gb` its first cell and
+// `gs` the element stride along it (1 on row tiles).
+struct LineRef {
+  int gb, gs;
+  bool valid;
 };
 
-// Load phase: elements c0 .. c0 + CH - 1 of this thread, from A.src by A.src_mode, handed to
-// put(line, pos, value) once all of the chunk's loads are issued. CH divides the 2E elements.
-template <int M, int V>
-__host__ __device__ constexpr int load_chunk_of() { return (2 * slots_of(M, V)) % 16 == 0 ? 16 : 8; }
-template <int M, int V, bool COL, typename Put>
-__device__ __forceinline__ void load_chunk(const PassArgs<float> &A, const ElemMap<M, V, COL> &em, int c0, Put put) {
-  constexpr int kChunk = load_chunk_of<M, V>();
-  float x[kChunk];
+// Load the quad at position 4 qd of a line from A.src (FP64 sources truncated to FP32).
+template <bool COL>
+__device__ __forceinline__ float4 load_quad(const PassArgs<float> &A, const LineRef &lr, int qd) {
+  if (!lr.valid) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const int g = lr.gb + 4 * qd * lr.gs;
   if (A.src_mode == SRC_F64) {
-    const double *src = static_cast<const double *>(A.src);
-#pragma unroll
-    for (int b = 0; b < kChunk; ++b) {
-      int line, pos, gi;
-      bool valid;
-      em.at(c0 + b, line, pos, gi, valid);
-      x[b] = valid ? d2f_rz_bits(__ldg(src + gi)) : 0.0f;
-    }
-  } else {
-    const float *src = static_cast<const float *>(A.src);
-#pragma unroll
-    for (int b = 0; b < kChunk; ++b) {
-      int line, pos, gi;
-      bool valid;
-      em.at(c0 + b, line, pos, gi, valid);
-      x[b] = valid ? src[gi] : 0.0f;
+    const double *s = static_cast<const double *>(A.src);
+    if constexpr (COL) {
+      return make_float4(d2f_rz_bits(__ldg(s + g)), d2f_rz_bits(__ldg(s + g + lr.gs)),
+                         d2f_rz_bits(__ldg(s + g + 2 * lr.gs)), d2f_rz_bits(__ldg(s + g + 3 * lr.gs)));
+    } else {
+      const double2 a = __ldg(reinterpret_cast<const double2 *>(s + g));
+      const double2 b = __ldg(reinterpret_cast<const double2 *>(s + g + 2));
+      return make_float4(d2f_rz_bits(a.x), d2f_rz_bits(a.y), d2f_rz_bits(b.x), d2f_rz_bits(b.y));
     }
   }
-#pragma unroll
-  for (int b = 0; b < kChunk; ++b) {
-    int line, pos, gi;
-    bool valid;
-    em.at(c0 + b, line, pos, gi, valid);
-    put(line, pos, x[b]);
+  const float *s = static_cast<const float *>(A.src);
+  if constexpr (COL) return make_float4(s[g], s[g + lr.gs], s[g + 2 * lr.gs], s[g + 3 * lr.gs]);
+  else return *reinterpret_cast<const float4 *>(s + g);
+}
+
+// Forward scatter of the quad at position 4 qd into the slots of line l: input x_j at real
+// position j of the slots (real DFT); at Makhoul's position j/2 (j even) or n - 1 - j/2 (j odd),
+// times (-1)^j for DST-II, so that positions 4qd and 4qd + 2 share slot qd and positions
+// 4qd + 1 and 4qd + 3 slot M - 1 - qd; or DCT-IV's z_q = (x_2q, x_{n-1-2q}), swapped for DST-IV.
+template <int M, int V, int FAM>
+__device__ __forceinline__ void scatter_quad(float2 *buf, int l, int qd, int kind, float4 x) {
+  constexpr int LP = Geo<M, V>::LP;
+  float *re = reinterpret_cast<float *>(buf);
+  if constexpr (FAM == 0) {
+    buf[(2 * qd) * LP + l] = make_float2(x.x, x.y);
+    buf[(2 * qd + 1) * LP + l] = make_float2(x.z, x.w);
+  } else if constexpr (FAM == 1) {
+    const float sg = (kind == KIND_DD) ? -1.0f : 1.0f;   // DST-II: (-1)^j x_j
+    buf[qd * LP + l] = make_float2(x.x, x.z);
+    buf[(M - 1 - qd) * LP + l] = make_float2(sg * x.w, sg * x.y);
+  } else {
+    // z_q = (x_2q, x_{n-1-2q}) (DCT-IV), swapped (DST-IV)
+    const int c = (kind == KIND_ND) ? 0 : 1;
+    re[2 * ((2 * qd) * LP + l) + c] = x.x;
+    re[2 * ((2 * qd + 1) * LP + l) + c] = x.z;
+    re[2 * ((M - 1 - 2 * qd) * LP + l) + (c ^ 1)] = x.y;
+    re[2 * ((M - 2 - 2 * qd) * LP + l) + (c ^ 1)] = x.w;
   }
 }
 
-// Store phase: every element of the tile through get(line, pos) into A.dst by A.dst_mode, in
-// chunks (the old values of an accumulating store are loaded together).
-template <int M, int V, bool COL, typename Get>
-__device__ __forceinline__ void store_phase(const PassArgs<float> &A, const ElemMap<M, V, COL> &em, Get get) {
-  constexpr int NE = 2 * Geo<M, V>::E, kC = NE < 8 ? NE : 8;
+// Outputs 4 qd .. 4 qd + 3 of a line after the final FFT (before the 1/M normalisation): the
+// conjugated slots of the inverse real DFT / DCT-III / DST-III, or DCT-IV / DST-IV post-twiddled.
+template <int M, int V, int FAM>
+__device__ __forceinline__ float4 gather_quad(const float2 *buf, int l, int qd, int kind, const float2 *__restrict__ tw) {
+  constexpr int LP = Geo<M, V>::LP;
+  if constexpr (FAM == 0) {
+    const float2 a = buf[(2 * qd) * LP + l], b = buf[(2 * qd + 1) * LP + l];
+    return make_float4(a.x, -a.y, b.x, -b.y);
+  } else if constexpr (FAM == 1) {
+    const float2 zq = buf[qd * LP + l], zm = buf[(M - 1 - qd) * LP + l];
+    if (kind == KIND_DD) return make_float4(zq.x, zm.y, -zq.y, -zm.x);
+    return make_float4(zq.x, -zm.y, -zq.y, zm.x);
+  } else {
+    const float2 *tp = tw + tw_dct4post(M);
+    const int qa = 2 * qd, qb = M - 1 - 2 * qd, qc = 2 * qd + 1, qe = M - 2 - 2 * qd;
+    const float2 ya = cmul(buf[qa * LP + l], __ldg(tp + qa)), yb = cmul(buf[qb * LP + l], __ldg(tp + qb));
+    const float2 yc = cmul(buf[qc * LP + l], __ldg(tp + qc)), ye = cmul(buf[qe * LP + l], __ldg(tp + qe));
+    const float sg = (kind == KIND_ND) ? -1.0f : 1.0f;
+    return make_float4(ya.x, sg * yb.y, yc.x, sg * ye.y);
+  }
+}
+
+// Store the quad at position 4 qd of a line into A.dst by A.dst_mode (op: the old pairs of an
+// accumulating store, load_old_pairs).
+template <bool COL>
+__device__ __forceinline__ void store_quad(const PassArgs<float> &A, const LineRef &lr, int qd, float4 x,
+                                           const float4 (&op)[2]) {
+  if (!lr.valid) return;
+  const int g = lr.gb + 4 * qd * lr.gs;
   const int mode = A.dst_mode;
-#pragma unroll 1
-  for (int c0 = 0; c0 < NE; c0 += kC) {
-    float x[kC];
-#pragma unroll
-    for (int b = 0; b < kC; ++b) {
-      int line, pos, gi;
-      bool valid;
-      em.at(c0 + b, line, pos, gi, valid);
-      x[b] = get(line, pos);
+  if (mode == DST_WORK) {
+    float *d = static_cast<float *>(A.dst);
+    if constexpr (COL) {
+      d[g] = x.x; d[g + lr.gs] = x.y; d[g + 2 * lr.gs] = x.z; d[g + 3 * lr.gs] = x.w;
+    } else {
+      *reinterpret_cast<float4 *>(d + g) = x;
     }
-    if (mode == DST_WORK) {
-      float *dst = static_cast<float *>(A.dst);
+    return;
+  }
+  const float xv[4] = {x.x, x.y, x.z, x.w};
+  if (mode == DST_PAIR_SET || mode == DST_PAIR_ADD) {
+    // the FP32 pair (hi, lo) of the refinement iterate += x with Knuth's TwoSum, renormalised
+    float2 *d = static_cast<float2 *>(A.dst);
+    const float2 old[4] = {make_float2(op[0].x, op[0].y), make_float2(op[0].z, op[0].w),
+                           make_float2(op[1].x, op[1].y), make_float2(op[1].z, op[1].w)};
+    float2 r[4];
 #pragma unroll
-      for (int b = 0; b < kC; ++b) {
-        int line, pos, gi;
-        bool valid;
-        em.at(c0 + b, line, pos, gi, valid);
-        if (valid) dst[gi] = x[b];
+    for (int c = 0; c < 4; ++c) {
+      float hi = xv[c], lo = 0.0f;
+      if (mode == DST_PAIR_ADD) {
+        const float a = old[c].x, alo = old[c].y, bb = hi;
+        const float s1 = __fadd_rn(a, bb), z = __fsub_rn(s1, a);
+        const float e = __fadd_rn(__fadd_rn(__fsub_rn(a, __fsub_rn(s1, z)), __fsub_rn(bb, z)), alo);
+        hi = __fadd_rn(s1, e);
+        lo = __fsub_rn(e, __fsub_rn(hi, s1));
       }
-    } else if (mode == DST_PAIR_SET || mode == DST_PAIR_ADD) {
-      // the FP32 pair (hi, lo) of the refinement iterate += x with Knuth's TwoSum, renormalised
-      float2 *dst = static_cast<float2 *>(A.dst);
-      float2 old[kC];
+      r[c] = make_float2(hi, lo);
+    }
+    if constexpr (COL) {
 #pragma unroll
-      for (int b = 0; b < kC; ++b) {
-        int line, pos, gi;
-        bool valid;
-        em.at(c0 + b, line, pos, gi, valid);
-        old[b] = (mode == DST_PAIR_ADD && valid) ? dst[gi] : make_float2(0.0f, 0.0f);
-      }
-#pragma unroll
-      for (int b = 0; b < kC; ++b) {
-        int line, pos, gi;
-        bool valid;
-        em.at(c0 + b, line, pos, gi, valid);
-        float hi = x[b], lo = 0.0f;
-        if (mode == DST_PAIR_ADD) {
-          const float a = old[b].x, alo = old[b].y, bb = hi;
-          const float s1 = __fadd_rn(a, bb), z = __fsub_rn(s1, a);
-          const float e = __fadd_rn(__fadd_rn(__fsub_rn(a, __fsub_rn(s1, z)), __fsub_rn(bb, z)), alo);
-          hi = __fadd_rn(s1, e);
-          lo = __fsub_rn(e, __fsub_rn(hi, s1));
-        }
-        if (valid) {
-          dst[gi] = make_float2(hi, lo);
-          if (A.f64) A.f64[gi] = f2d_bits(hi) + f2d_bits(lo);
-        }
+      for (int c = 0; c < 4; ++c) {
+        d[g + c * lr.gs] = r[c];
+        if (A.f64) A.f64[g + c * lr.gs] = f2d_bits(r[c].x) + f2d_bits(r[c].y);
       }
     } else {
-      // FP64 destination (set or accumulate): not on the projection's path
-      double *dst = static_cast<double *>(A.dst);
-#pragma unroll 1
-      for (int b = 0; b < kC; ++b) {
-        int line, pos, gi;
-        bool valid;
-        em.at(c0 + b, line, pos, gi, valid);
-        if (valid) dst[gi] = (mode == DST_F64_SET) ? f2d_bits(x[b]) : dst[gi] + f2d_bits(x[b]);
+      *reinterpret_cast<float4 *>(d + g) = make_float4(r[0].x, r[0].y, r[1].x, r[1].y);
+      *reinterpret_cast<float4 *>(d + g + 2) = make_float4(r[2].x, r[2].y, r[3].x, r[3].y);
+      if (A.f64) {
+        double2 *f = reinterpret_cast<double2 *>(A.f64 + g);
+        f[0] = make_double2(f2d_bits(r[0].x) + f2d_bits(r[0].y), f2d_bits(r[1].x) + f2d_bits(r[1].y));
+        f[1] = make_double2(f2d_bits(r[2].x) + f2d_bits(r[2].y), f2d_bits(r[3].x) + f2d_bits(r[3].y));
       }
     }
+    return;
+  }
+  // FP64 destination (set or accumulate): not on the projection's path
+  double *d = static_cast<double *>(A.dst);
+#pragma unroll 1
+  for (int c = 0; c < 4; ++c) {
+    const int gi = g + c * lr.gs;
+    d[gi] = (mode == DST_F64_SET) ? f2d_bits(xv[c]) : d[gi] + f2d_bits(xv[c]);
+  }
+}
+
+// Coefficients of pair k at positions pos (pair_positions) of a line: stored to A.dst
+// (forward-only passes, DST_WORK) or loaded from A.src (inverse-only passes, FP32). Row tiles
+// move the position pairs that are adjacent (families 0 and 2) as 8-byte accesses.
+template <int FAM, bool COL>
+__device__ __forceinline__ void store_pair(const PassArgs<float> &A, const LineRef &lr, const int (&pos)[4],
+                                           const float (&val)[4]) {
+  if (!lr.valid) return;
+  float *d = static_cast<float *>(A.dst);
+  if constexpr (!COL && FAM == 0) {   // (pos0, pos0 + 1), (pos2, pos2 + 1)
+    *reinterpret_cast<float2 *>(d + lr.gb + pos[0]) = make_float2(val[0], val[1]);
+    *reinterpret_cast<float2 *>(d + lr.gb + pos[2]) = make_float2(val[2], val[3]);
+  } else if constexpr (!COL && FAM == 2) {   // (2k, 2k + 1) = pos 0, 3; (n-2-2k, n-1-2k) = pos 2, 1
+    *reinterpret_cast<float2 *>(d + lr.gb + pos[0]) = make_float2(val[0], val[3]);
+    *reinterpret_cast<float2 *>(d + lr.gb + pos[2]) = make_float2(val[2], val[1]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) d[lr.gb + pos[c] * lr.gs] = val[c];
+  }
+}
+template <int FAM, bool COL>
+__device__ __forceinline__ void load_pair(const PassArgs<float> &A, const LineRef &lr, const int (&pos)[4],
+                                          float (&val)[4]) {
+  if (!lr.valid) {
+    val[0] = val[1] = val[2] = val[3] = 0.0f;
+    return;
+  }
+  const float *s = static_cast<const float *>(A.src);
+  if constexpr (!COL && FAM == 0) {
+    const float2 a = *reinterpret_cast<const float2 *>(s + lr.gb + pos[0]);
+    const float2 b = *reinterpret_cast<const float2 *>(s + lr.gb + pos[2]);
+    val[0] = a.x; val[1] = a.y; val[2] = b.x; val[3] = b.y;
+  } else if constexpr (!COL && FAM == 2) {
+    const float2 a = *reinterpret_cast<const float2 *>(s + lr.gb + pos[0]);
+    const float2 b = *reinterpret_cast<const float2 *>(s + lr.gb + pos[2]);
+    val[0] = a.x; val[3] = a.y; val[2] = b.x; val[1] = b.y;
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) val[c] = s[lr.gb + pos[c] * lr.gs];
+  }
+}
+
+// Old pairs of an accumulating store (DST_PAIR_ADD) at the quad at position 4 qd.
+template <bool COL>
+__device__ __forceinline__ void load_old_pairs(const PassArgs<float> &A, const LineRef &lr, int qd, float4 (&o)[2]) {
+  o[0] = o[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (!lr.valid || A.dst_mode != DST_PAIR_ADD) return;
+  const float2 *d = static_cast<const float2 *>(A.dst);
+  const int g = lr.gb + 4 * qd * lr.gs;
+  if constexpr (COL) {
+    const float2 a = d[g], b = d[g + lr.gs], c = d[g + 2 * lr.gs], e = d[g + 3 * lr.gs];
+    o[0] = make_float4(a.x, a.y, b.x, b.y);
+    o[1] = make_float4(c.x, c.y, e.x, e.y);
+  } else {
+    o[0] = *reinterpret_cast<const float4 *>(d + g);
+    o[1] = *reinterpret_cast<const float4 *>(d + g + 2);
   }
 }
 
 // One pass over tile `tile`: [forward transform] [division] [inverse transform] as A asks
-// (a division always sits between a forward and an inverse transform). Out of line: one
-// function per length, family and layout keeps the compile time linear in their number.
+// (a division always sits between a forward and an inverse transform). The FFT maps threads
+// line-fast; the quads and pairs map them line-fast on column tiles (coalesced across lines)
+// and position-fast on row tiles (coalesced along the line). Out of line: one function per
+// length, variant, family and layout keeps the compile time linear in their number.
 template <int M, int V, int FAM, bool COL>
 __device__ __noinline__ void body_layout(const PassArgs<float> &A, int tile, float2 *buf, const float *lamo,
                                          const int *lbase, const int *lzero) {
   using G = Geo<M, V>;
-  constexpr int E = G::E, T = G::T, L = G::L, n = G::N, NE = 2 * E;
+  constexpr int E = G::E, T = G::T, L = G::L, n = G::N, NQ = E / 2;
   const int t = threadIdx.x;
-  const int l = t % L, u = t / L;   // FFT and pair map: line fast
+  const int l = t % L, u = t / L;                     // FFT map
+  const int pl = COL ? l : t / T, pu = COL ? u : t % T;   // quad and pair map
   const int kind = pass_kind<FAM>(A.kind);
   const float2 *tw = A.tw;
-  ElemMap<M, V, COL> em;
-  em.t = t; em.l = l; em.u = u; em.stride = A.stride; em.lbase = lbase;
-  em.rowbase = tile * (L * n);
-  em.rowend = A.lines * n;
+  LineRef lr;
+  if constexpr (COL) {
+    lr.gb = lbase[pl];
+    lr.valid = lr.gb >= 0;
+    lr.gs = A.stride;
+  } else {
+    const int line = tile * L + pl;
+    lr.valid = line < A.lines;
+    lr.gb = line * n;
+    lr.gs = 1;
+  }
 
   if (A.do_fwd) {
-    // load (a chunk's loads issued together), scatter into the slots
-#pragma unroll 1
-    for (int c0 = 0; c0 < NE; c0 += load_chunk_of<M, V>())
-      load_chunk<M, V, COL>(A, em, c0, [&](int line, int pos, float x) {
-        bool neg;
-        const int p = fwd_pos<FAM>(kind, n, pos, neg);
-        re_at<M, V>(buf, line, p) = neg ? -x : x;
-      });
+    float4 xq[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) xq[i] = load_quad<COL>(A, lr, pu + T * i);
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) scatter_quad<M, V, FAM>(buf, pl, pu + T * i, kind, xq[i]);
     __syncthreads();
-    fft<M, V>(buf, u, l, tw, FAM == 2 ? tw + tw_dct4pre(M) : nullptr);
+    fft_all<M, V>(buf, u, l, tw, FAM == 2 ? tw + tw_dct4pre(M) : nullptr);
     if (!A.do_inv) {
-      // forward-only pass: coefficients -> their positions in the buffer -> global
-      float val[E / 2][4];
+      // forward-only pass: the coefficients of each pair straight to global memory
 #pragma unroll
-      for (int i = 0; i < E / 2; ++i) {
+      for (int i = 0; i < NQ; ++i) {
         int pos[4];
-        fwd_pair<M, V, FAM>(buf, l, u + T * i, kind, tw, pos, val[i]);
+        float val[4];
+        fwd_pair<M, V, FAM>(buf, pl, pu + T * i, kind, tw, pos, val);
+        store_pair<FAM, COL>(A, lr, pos, val);
       }
-      __syncthreads();
-#pragma unroll
-      for (int i = 0; i < E / 2; ++i) {
-        int pos[4];
-        pair_positions<M, FAM>(u + T * i, kind, pos);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) re_at<M, V>(buf, l, pos[c]) = val[i][c];
-      }
-      __syncthreads();
-      store_phase<M, V, COL>(A, em, [&](int line, int p) { return re_at<M, V>(buf, line, p); });
       return;
     }
-    // forward post-processing, division, inverse pre-processing: per pair, in registers
-    const float lo = A.do_div ? lamo[l] : 0.0f;
-    const bool zm = A.do_div && A.singular && lzero[l];
-    const float *la = A.lam[A.axis];
+    // forward post-processing, division, inverse pre-processing: per pair, in registers (a
+    // pair's slots are read and rewritten by the same thread)
     const bool dv = A.do_div;
+    const float lo = dv ? lamo[pl] : 0.0f;
+    const bool zm = dv && A.singular && lzero[pl];
+    const float *la = A.lam[A.axis];
 #pragma unroll 1
-    for (int i = 0; i < E / 2; ++i) {
-      const int k = u + T * i;
+    for (int i = 0; i < NQ; ++i) {
+      const int k = pu + T * i;
       int pos[4];
       float val[4];
-      fwd_pair<M, V, FAM>(buf, l, k, kind, tw, pos, val);
+      fwd_pair<M, V, FAM>(buf, pl, k, kind, tw, pos, val);
       if (dv) {
 #pragma unroll
         for (int c = 0; c < 4; ++c)
           val[c] = (zm && pos[c] == 0) ? 0.0f : __fdividef(val[c], __ldg(la + pos[c]) + lo);
       }
-      inv_pair<M, V, FAM>(buf, l, k, kind, tw, val);
+      inv_pair<M, V, FAM>(buf, pl, k, kind, tw, val);
     }
     __syncthreads();
   } else {
-    // inverse-only pass: coefficients -> buffer positions, then the pairs' pre-processing
+    // inverse-only pass: each pair's coefficients from global memory, pre-processed into its
+    // slots; two pairs per iteration (their loads issued together)
 #pragma unroll 1
-    for (int c0 = 0; c0 < NE; c0 += load_chunk_of<M, V>())
-      load_chunk<M, V, COL>(A, em, c0, [&](int line, int pos, float x) { re_at<M, V>(buf, line, pos) = x; });
-    __syncthreads();
-    float val[E / 2][4];
+    for (int i = 0; i < NQ; i += 2) {
+      float val[2][4];
 #pragma unroll
-    for (int i = 0; i < E / 2; ++i) {
-      int pos[4];
-      pair_positions<M, FAM>(u + T * i, kind, pos);
+      for (int h = 0; h < 2; ++h) {
+        int pos[4];
+        pair_positions<M, FAM>(pu + T * (i + h), kind, pos);
+        load_pair<FAM, COL>(A, lr, pos, val[h]);
+      }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) val[i][c] = re_at<M, V>(buf, l, pos[c]);
+      for (int h = 0; h < 2; ++h) inv_pair<M, V, FAM>(buf, pl, pu + T * (i + h), kind, tw, val[h]);
     }
     __syncthreads();
-#pragma unroll
-    for (int i = 0; i < E / 2; ++i) inv_pair<M, V, FAM>(buf, l, u + T * i, kind, tw, val[i]);
-    __syncthreads();
   }
-  fft<M, V>(buf, u, l, tw, nullptr);
+  fft_all<M, V>(buf, u, l, tw, nullptr);
   const float scale = A.out_scale;
-  store_phase<M, V, COL>(A, em, [&](int line, int p) { return inv_value<M, V, FAM>(buf, line, p, kind, tw) * scale; });
+  // outputs, two quads at a time (the old values of an accumulating store loaded first)
+#pragma unroll 1
+  for (int i = 0; i < NQ; i += 2) {
+    float4 o[2][2];
+    load_old_pairs<COL>(A, lr, pu + T * i, o[0]);
+    load_old_pairs<COL>(A, lr, pu + T * (i + 1), o[1]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int qd = pu + T * (i + h);
+      float4 x = gather_quad<M, V, FAM>(buf, pl, qd, kind, tw);
+      x = make_float4(x.x * scale, x.y * scale, x.z * scale, x.w * scale);
+      store_quad<COL>(A, lr, qd, x, o[h]);
+    }
+  }
 }
 
 // One tile of a lean pass: per-line set-up (base cell, eigenvalue sum of the other axes, zero

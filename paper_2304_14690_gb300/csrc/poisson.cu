@@ -11,6 +11,7 @@
 // Mixed precision: the transforms run in FP32; the iterate p is kept in FP64 and corrected by
 // sweeps p += solve32(s - L_h p) whose residual is formed in FP64 (iterative refinement).
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -133,7 +134,13 @@ pc_status build_pass(const Plan *p, const PassSpec &ps, PassArgs<Real> &A, long 
   // slots per thread; 0 and 1 (FP32 only): variant 0 or 1 of the lean pass of the length
   // (lean_pass.cuh) where it has one, else 4
   int E = (sizeof(Real) == 8) ? ax.slots64 : ax.slots32;
-  const bool lean = sizeof(Real) == 4 && E <= 1 && pass_family(ax.kind) <= 2 && lean::length_ok(M);
+  // the lean passes move row tiles in 16-byte accesses (16-byte aligned arrays), store forward
+  // coefficients as FP32 work and read inverse-only coefficients in FP32
+  auto al16 = [](const void *q) { return ((uintptr_t)q & 15) == 0; };
+  const bool row = axis == p->dim - 1;
+  const bool lean_io = (!fwd || inv || dst_mode == DST_WORK) && (fwd || src_mode != SRC_F64) &&
+                       (!row || (al16(src) && al16(dst) && al16(ps.f64)));
+  const bool lean = sizeof(Real) == 4 && E <= 1 && pass_family(ax.kind) <= 2 && lean::length_ok(M) && lean_io;
   const int lv = E == 1 ? 1 : 0;
   if (E <= 1) E = 4;
   // threads per line: a power of two with at most E slots per thread; the kernel instance is
