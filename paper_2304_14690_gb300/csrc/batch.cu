@@ -34,7 +34,37 @@ struct PassLaunch {
   int emax = 1;          // largest slots per thread among the items' passes (kernel instance)
   size_t smem = 0;       // the pass body's shared memory (the largest item's)
   int lean = 0;          // 0: general passes; else the lean kernel id (lean_pass.cuh)
+  int pass = 0;          // the pass of the solve: launches of one pass run side by side
 };
+
+// Auxiliary streams and events that run the launches of one batched pass side by side (they
+// transform disjoint problems), joined back into the caller's stream before the next pass. In a
+// captured graph they become parallel branches.
+constexpr int kForkWays = 6;
+struct Fork {
+  cudaStream_t aux[kForkWays] = {};
+  cudaEvent_t fork = nullptr, join[kForkWays] = {};
+};
+
+pc_status fork_create(Fork &f) {
+  for (int i = 0; i < kForkWays; ++i) {
+    PC_CUDA_TRY(cudaStreamCreateWithFlags(&f.aux[i], cudaStreamNonBlocking));
+    PC_CUDA_TRY(cudaEventCreateWithFlags(&f.join[i], cudaEventDisableTiming));
+  }
+  PC_CUDA_TRY(cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming));
+  return PC_OK;
+}
+
+void fork_destroy(Fork &f) {
+  for (int i = 0; i < kForkWays; ++i) {
+    if (f.aux[i]) cudaStreamDestroy(f.aux[i]);
+    if (f.join[i]) cudaEventDestroy(f.join[i]);
+    f.aux[i] = nullptr;
+    f.join[i] = nullptr;
+  }
+  if (f.fork) cudaEventDestroy(f.fork);
+  f.fork = nullptr;
+}
 
 // Problems that share the templated per-stage kernels (dimension, velocity type, neighbour
 // count) and the refinement settings.
@@ -66,6 +96,8 @@ struct Exec {
   int4 *ditems = nullptr;               // work list: (args index, first tile, tiles, 0)
   std::vector<std::vector<PassLaunch>> passes;   // [solve][pass]
   cudaStream_t cap = nullptr;
+  Fork own;                             // streams of the side-by-side pass launches (cached executors)
+  Fork *fork = nullptr;                 // the streams used: own, or the batch executor's
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<void *> allocs;
@@ -86,6 +118,7 @@ void free_exec(Exec *e) {
   if (e->exec) cudaGraphExecDestroy(e->exec);
   if (e->graph) cudaGraphDestroy(e->graph);
   if (e->cap) cudaStreamDestroy(e->cap);
+  fork_destroy(e->own);
   for (void *a : e->allocs) cudaFree(a);
   if (cur >= 0) cudaSetDevice(cur);
   delete e;
@@ -190,6 +223,7 @@ pc_status build_passes(Exec *e) {
         pl[c].smem = std::max(pl[c].smem, smem);
         pl[c].emax = std::max(pl[c].emax, A.emax);
         pl[c].lean = c;
+        pl[c].pass = (int)k;
       }
       for (int c = 0; c < 7; ++c) {
         if (list[c].empty()) continue;
@@ -251,15 +285,34 @@ pc_status record_exec(Exec *e, cudaStream_t st, Plan *prof = nullptr) {
       }
       mark(4);
     }
-    for (const PassLaunch &pl : e->passes[j]) {
-      if (pl.lean) {
-        PassArgs<float> none;
-        memset(&none, 0, sizeof(none));
-        PC_TRY(launch_lean(pl.lean, none, e->dargs, e->ditems + pl.items_off, (unsigned)pl.nitems, kBatchThreads, pl.smem, st));
-      } else {
-        PC_TRY(launch_batched_f32(e->dargs, e->ditems + pl.items_off, pl.nitems, kBatchThreads, pl.smem, pl.emax, st));
+    // the launches of one pass (one per kernel) side by side, then joined
+    const std::vector<PassLaunch> &pv = e->passes[j];
+    for (size_t a = 0; a < pv.size();) {
+      size_t b = a + 1;
+      while (b < pv.size() && pv[b].pass == pv[a].pass) ++b;
+      const int ways = (int)(b - a);
+      const bool side = e->fork && ways > 1 && ways <= kForkWays + 1;
+      if (side) PC_CUDA_TRY(cudaEventRecord(e->fork->fork, st));
+      for (size_t i = a; i < b; ++i) {
+        const PassLaunch &pl = pv[i];
+        cudaStream_t ls = st;
+        if (side && i > a) {
+          ls = e->fork->aux[i - a - 1];
+          PC_CUDA_TRY(cudaStreamWaitEvent(ls, e->fork->fork, 0));
+        }
+        if (pl.lean) {
+          PassArgs<float> none;
+          memset(&none, 0, sizeof(none));
+          PC_TRY(launch_lean(pl.lean, none, e->dargs, e->ditems + pl.items_off, (unsigned)pl.nitems, kBatchThreads, pl.smem, ls));
+        } else {
+          PC_TRY(launch_batched_f32(e->dargs, e->ditems + pl.items_off, pl.nitems, kBatchThreads, pl.smem, pl.emax, ls));
+        }
+        if (side && i > a) PC_CUDA_TRY(cudaEventRecord(e->fork->join[i - a - 1], ls));
+        ++launches;
       }
-      ++launches;
+      if (side)
+        for (size_t i = a + 1; i < b; ++i) PC_CUDA_TRY(cudaStreamWaitEvent(st, e->fork->join[i - a - 1], 0));
+      a = b;
     }
     mark(3);
   }
@@ -312,6 +365,8 @@ pc_status build_groups(Exec *e) {
 pc_status build_exec(Exec *e) {
   PC_TRY(build_groups(e));
   PC_CUDA_TRY(cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking));
+  PC_TRY(fork_create(e->own));
+  e->fork = &e->own;
   if (!e->groups.empty()) {
     PC_CUDA_TRY(cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal));
     pc_status s = record_exec(e, e->cap);
@@ -396,6 +451,7 @@ struct Slot {
 
 struct Batcher {
   int device = 0;
+  Fork fork;
   std::vector<Slot> slots;
   size_t next = 0;
   std::mutex m;
@@ -467,8 +523,9 @@ extern "C" pc_status pc_batcher_create(int device, size_t table_bytes, int slots
   Batcher *b = new Batcher();
   b->device = device;
   b->slots.resize(slots);
-  pc_status s = PC_OK;
+  pc_status s = fork_create(b->fork);
   for (Slot &sl : b->slots) {
+    if (s != PC_OK) break;
     sl.arena.cap = table_bytes;
     if (cudaMallocHost(reinterpret_cast<void **>(&sl.arena.host), table_bytes) != cudaSuccess ||
         cudaMalloc(reinterpret_cast<void **>(&sl.arena.dev), table_bytes) != cudaSuccess ||
@@ -507,6 +564,7 @@ extern "C" pc_status pc_batcher_launch(pc_batcher *batcher, int count, pc_plan *
   e.arena = &sl.arena;
   e.arena->used = 0;
   e.device = device;
+  e.fork = &b->fork;
   for (int i = 0; i < count; ++i) {
     e.plans.push_back(reinterpret_cast<Plan *>(plans[i]));
     e.args.push_back(args[i]);
@@ -536,6 +594,7 @@ extern "C" pc_status pc_batcher_destroy(pc_batcher *batcher) {
     if (sl.arena.dev) cudaFree(sl.arena.dev);
     if (sl.arena.host) cudaFreeHost(sl.arena.host);
   }
+  fork_destroy(b->fork);
   if (cur >= 0) cudaSetDevice(cur);
   delete b;
   return PC_OK;
