@@ -334,8 +334,8 @@ __device__ __forceinline__ DF df_mul(DF a, DF b) {
 }
 
 // ----------------------------------------------------------------------------- divergence
-// s = D_h U / (beta dt) (FP64), its FP32 copy; want_sums 1: sum(s) and the mean, 2: also
-// sum(s^2) (statistics).
+// s = D_h U / (beta dt) (FP64; as an FP32 pair in double-float arithmetic on the mixed path),
+// its FP32 copy; want_sums 1: sum(s) and the mean, 2: also sum(s^2) (statistics).
 template <int DIM>
 __device__ __forceinline__ void divergence_body(unsigned b, const GridDev &g, const double *U0, const double *U1,
                                                 const double *U2, double inv_bdt, double *s, float2 *s2, float *s32,
@@ -348,7 +348,36 @@ __device__ __forceinline__ void divergence_body(unsigned b, const GridDev &g, co
 #pragma unroll
   for (int a = 0; a < DIM; ++a) c[a] = g.inv_h[a] * inv_bdt;
   double sum = 0.0, sum2 = 0.0;
-  if (x < g.n[DIM - 1]) {
+  if (s2 && x < g.n[DIM - 1]) {
+    // mixed path: the source is kept as an FP32 pair, so it is formed in double-float arithmetic
+    // (FP32 operations with error-free transformations, about 48 bits) from the FP64 faces: the
+    // FP64 pipe runs at a small fraction of the FP32 rate on this GPU
+    DF cd[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) cd[a] = df_of(c[a]);
+    DF sd{0.0f, 0.0f}, sd2{0.0f, 0.0f};
+    const int rend = min(row0 + g.cr, g.rows);
+    for (int row = row0; row < rend; ++row) {
+      int i[3];
+      cell_at<DIM>(g, row, x, i);
+      DF v{0.0f, 0.0f};
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        int hi = i[a] + 1;
+        if (g.periodic[a] && hi == g.n[a]) hi = 0;
+        const DF d = df_sub(df_of(U[a][face_index(g, a, i, hi)]), df_of(U[a][face_index(g, a, i, i[a])]));
+        v = (a == 0) ? df_mul(d, cd[0]) : df_add(v, df_mul(d, cd[a]));
+      }
+      const int ci = cell_index(g, i);
+      if (g.mask && !g.mask[ci]) v = DF{0.0f, 0.0f};   // outside the flow domain (RHS mask)
+      s2[ci] = make_float2(v.hi, v.lo);
+      if (s32) s32[ci] = v.hi;   // FP32 copy read by the first FP32 transform pass
+      if (want_sums) sd = df_add(sd, v);
+      if (want_sums > 1) sd2 = df_add(sd2, df_mul(v, v));
+    }
+    sum = f2d_bits(sd.hi) + f2d_bits(sd.lo);
+    sum2 = f2d_bits(sd2.hi) + f2d_bits(sd2.lo);
+  } else if (x < g.n[DIM - 1]) {
     const int rend = min(row0 + g.cr, g.rows);
     for (int row = row0; row < rend; ++row) {
       int i[3];
