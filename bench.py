@@ -250,7 +250,7 @@ def transform_kernel_hash():
     edits keep a capture valid."""
     csrc = os.path.join(ROOT, "paper_2304_14690_gb300", "csrc")
     h = hashlib.sha1()
-    for f in ("fft.cuh", "axis_pass.cuh"):
+    for f in ("fft.cuh", "axis_pass.cuh", "lean_pass.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:12]
 
