@@ -129,3 +129,26 @@ def test_lean_batch_equals_single(env, slots):
             assert torch.equal(got, want), (i, name)
     for plan in plans:
         plan.close()
+
+
+def test_lean_misaligned_arrays_fall_back(env):
+    """Row tiles of the compile-time passes use 16-byte accesses; a source or result array that
+    is only 8-byte aligned (a view one element into a buffer) takes the general passes instead,
+    and the solve still matches the oracle and the aligned call."""
+    pc, torch, dev = env
+    for kinds in (("NN", "PP"), ("ND", "DD")):
+        g, s = _case(kinds, (64, 128), 6100 + len(kinds[0]))
+        ref, _ = P.solve(s, g)
+        for precision, tol in (("fp32", 1e-5), ("mixed", 1e-10)):
+            plan = _plan(pc, g, precision)
+            aligned, _ = plan.solve_poisson(torch.as_tensor(s, device=dev))
+            sb = torch.zeros(s.size + 1, dtype=torch.float64, device=dev)
+            pb = torch.zeros(s.size + 1, dtype=torch.float64, device=dev)
+            s_view = sb[1:].view(g.shape)
+            s_view.copy_(torch.as_tensor(s, device=dev))
+            p_view = pb[1:].view(g.shape)
+            plan.solve_poisson(s_view, p_out=p_view)
+            torch.cuda.synchronize()
+            assert rel(p_view.cpu().numpy(), ref) <= tol, (kinds, precision)
+            assert rel(p_view.cpu().numpy(), aligned.cpu().numpy()) <= tol, (kinds, precision)
+            plan.close()
