@@ -1323,15 +1323,15 @@ static GridDev grid_dev(const Plan *p) {
 }
 
 // The same tiling with cr rows per thread. A launch whose results do not depend on its blocks
-// (no grid sums: the residual's values and max norms, a divergence without sums) may take more,
-// smaller blocks when it runs alone; a batch keeps four rows per thread.
+// (no grid sums: a divergence without sums) may take more, smaller blocks when it runs alone; a
+// batch keeps four rows per thread.
 static GridDev with_rows_per_thread(GridDev g, int cr) {
   const long long rpb = (long long)cr << g.th_bits;
   g.cr = cr;
   g.nblk = (int)((long long)g.gx * ((g.rows + rpb - 1) / rpb));
   return g;
 }
-constexpr int kSingleRows = 2;   // rows per thread of those single-problem launches
+constexpr int kSingleRows = 2;   // rows per thread of the sum-free single-problem divergence
 
 // Launch shape covering every cell: x over the last axis, y/z over the others.
 
@@ -1351,9 +1351,9 @@ template <typename SV, typename PV>
 static void launch_residual(bool singular, bool write_r, bool norm, cudaStream_t st, const GridDev &g0,
                             const SV *s, const PV *p, float *r, DevStats *ds, double *res2, double *partials,
                             unsigned int *counters, RefineStep rs = RefineStep{0, 0, 0.0f, 1}) {
-  // the values and max norms do not depend on the blocks; the L2 norm (statistics) is reported
-  // by single calls only
-  const GridDev g = with_rows_per_thread(g0, kSingleRows);
+  // four rows per thread, the grid's own tiling: on the 256x128x128 box it took 0.194 ms for
+  // three residuals against 0.290 ms with two rows per thread (the channel is unchanged)
+  const GridDev g = g0;
   const int grid = (g.nblk + (rs.chunk > 1 ? rs.chunk : 1) - 1) / (rs.chunk > 1 ? rs.chunk : 1);
 #define PC_RES(S, W, N)                                                                                       \
   do {                                                                                                        \
