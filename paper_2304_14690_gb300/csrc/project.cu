@@ -613,9 +613,10 @@ __device__ __forceinline__ void residual_body(unsigned b, const GridDev &g, cons
         if (i[a] < g.n[a] - 1) pr = to_df(p[c + st]);
         else if (g.periodic[a]) pr = to_df(p[c - (g.n[a] - 1) * st]);
         else pr = ghost_df(g.hi_kind[a], dc, p, c - st);
-        // (pl - dc) + (pr - dc) as (pl + pr) - 2 dc: one double-float addition fewer (the
-        // doubling is exact), the same absolute error (about 2^-48 of the values)
-        const DF t = df_sub(df_add(pl, pr), DF{2.0f * dc.hi, 2.0f * dc.lo});
+        // the differences first: pl - dc and pr - dc cancel before any rounding of the sum
+        // (forming pl + pr first raised the refinement floor: p 9.4e-13 from the FP64 path on
+        // the channel instead of 1.5e-14)
+        const DF t = df_add(df_sub(pl, dc), df_sub(pr, dc));
         acc = df_add(acc, df_mul(t, DF{g.ih2_hi[a], g.ih2_lo[a]}));
       }
       DF sc = to_df(s[c]);
