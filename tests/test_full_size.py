@@ -64,6 +64,7 @@ def test_channel_full_projection(env, channel):
     prob, oplan = channel
     ref = PR.project(oplan, prob.dt, prob.u_star)
     u = torch.as_tensor(prob.u_star, device=dev)
+    got = {}
     for precision, tol in (("fp64", 1e-12), ("mixed", 1e-10)):
         plan = pc.Plan(prob, precision=precision)
         if precision == "mixed":
@@ -73,7 +74,13 @@ def test_channel_full_projection(env, channel):
         assert rel(uo.cpu().numpy(), ref["u"]) <= tol, precision
         assert rel(fo.cpu().numpy(), ref["f"]) <= tol, precision
         assert st["max_div_after"] * min(prob.h) / st["max_abs_u_star"] <= 1e-9
+        got[precision] = p.cpu().numpy()
         plan.close()
+    # The refinement reaches the floor of its double-float residual (about 2^-44 of the source):
+    # mixed against the FP64 GPU path measured 4.5e-15 to 1.5e-14 on this grid.
+    # 1e-13 keeps a margin and catches a residual or source whose rounding raises that floor
+    # (a second difference formed as (p_l + p_r) - 2 p_c gave 9.4e-13).
+    assert rel(got["mixed"], got["fp64"]) <= 1e-13
 
 
 def test_channel_ib_iteration(env, channel):
