@@ -246,12 +246,17 @@ def measured_peaks():
 
 
 def transform_kernel_hash():
-    """Hash of the transform kernel's device code (fft.cuh and axis_pass.cuh), so host-only
-    edits keep a capture valid."""
+    """Hash of the transform kernels' device code (fft.cuh, axis_pass.cuh, lean_pass.cuh) with
+    whole-line comments and blank lines left out, so host-only edits and comment edits keep a
+    capture valid."""
     csrc = os.path.join(ROOT, "paper_2304_14690_gb300", "csrc")
     h = hashlib.sha1()
     for f in ("fft.cuh", "axis_pass.cuh", "lean_pass.cuh"):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        for line in open(os.path.join(csrc, f), encoding="utf-8"):
+            t = line.strip()
+            if t and not t.startswith("//"):
+                h.update(t.encode())
+                h.update(b"\n")
     return h.hexdigest()[:12]
 
 

@@ -7,16 +7,21 @@
 // thread instructions per cell and pass. Here every one of these is a compile-time constant:
 //   - a tile is L lines x M complex slots in shared memory, slot-major with the line index fast
 //     (slot q of line l at q * LP + l, LP = L + 1), so the FFT's accesses (every thread of a
-//     half-warp on another line, the same slot) are conflict-free whatever the slot pattern,
-//     and position-fast accesses of one line (row loads and stores) are too (LP odd);
+//     half-warp on another line, the same slot) are conflict-free whatever the slot pattern;
 //   - each line is served by T = M / E threads holding E complex values in registers; the FFT
 //     is a Stockham autosort whose stages (radix 16, 8, 4, 2 and a final 3) each read E slots,
-//     twiddle, run the small DFTs in registers and write E slots (two barriers, one buffer);
+//     twiddle, run the small DFTs in registers and write E slots (two barriers, one buffer).
+//     Two schedules per length: variant 0 with the most slots per thread (fewest instructions)
+//     and variant 1 with fewer (more warps for small grids);
 //   - the inverse transform runs the same forward FFT on conjugated slots (conj(FFT(conj Z))
-//     is the inverse DFT), so a length has one FFT body;
+//     is the inverse DFT), so a length has one FFT body, out of line and shared by a pass's
+//     forward and inverse halves;
 //   - in a pass that divides (forward, division, inverse), each thread post-processes a pair of
-//     slots (k, M - k) into four coefficients, divides them and pre-processes the same pair for
-//     the inverse in registers, with no barrier in between.
+//     slots (k, M - k; DCT-IV: k, M - 1 - k) into four coefficients, divides them and
+//     pre-processes the same pair for the inverse in registers, with no barrier in between;
+//   - global memory moves in quads of four consecutive cells (16-byte accesses on row tiles,
+//     four coalesced scalar accesses across lines on column tiles); forward-only passes store
+//     each pair's coefficients, and inverse-only passes load them, straight from global memory.
 // The thread-to-slot maps of the real-to-real wrappers follow fft.cuh (Makhoul's reordering;
 // DCT-IV through a half-length FFT with pre- and post-twiddles).
 #pragma once
